@@ -1,0 +1,287 @@
+/*
+ * ed.h -- C ABI of the B300 (sm_103a) embedded-deformation (ED) registration
+ * hot path of MIS-SLAM (Song et al., "MIS-SLAM: Real-time Large Scale Dense
+ * Deformable SLAM System in Minimal Invasive Surgery Based on Heterogeneous
+ * Computing", arXiv 1803.02009).
+ *
+ * One frame of the path:
+ *   ed_compute_normals  target normal map n(u)              (Sec. II.E, data term)
+ *   ed_build_graph      ED nodes, k nearest nodes, weights,
+ *                       node graph N(j)                     (Sec. II.D Eq. 1-2, Sec. II.E E_reg)
+ *   ed_gn_step  x n_gn  warp + association + residuals + J^T J / J^T r
+ *                       assembly + block-Jacobi PCG + update (Sec. II.E Eq. 3, Sec. II.F)
+ *   ed_warp             final warp of every model point     (Sec. II.D Eq. 1; Sec. II.G)
+ *   ed_fuse             registration map, Alg. 1 gate, fusion
+ *                       Eqs. fusion1-4, lifting, deletion   (Sec. II.G, Alg. 1-3)
+ *
+ * Conventions
+ *   Units are millimetres.  Camera frame: x right, y down, z forward.
+ *   Points and normals: float4 arrays [N][4]; points carry the fusion weight
+ *   omega in w, normals carry the stability flag S in w.
+ *   Node parameters x_j: the 3x4 affine [A_j | t_j] row-major, 12 floats per
+ *   node: x[12j + 4r + c] = A_j[r][c] (c < 3), x[12j + 4r + 3] = t_j[r].
+ *   Global pose: double[6] = (alpha, beta, gamma, Tx, Ty, Tz) with
+ *   R = Rz(gamma) Ry(beta) Rx(alpha), warp v~ = R s + T (Eq. 1).
+ *   Depth maps: float [H][W], 0 = hole.  Normal maps: float4 [H][W], w = 1
+ *   valid / 0 invalid.  Colour maps: float4 [H][W].
+ *
+ * Ownership and errors
+ *   The caller allocates every buffer; all pointers are device pointers unless
+ *   a comment says host.  The library uses only the workspace handed to
+ *   ed_create (size from ed_query_workspace) and never allocates device
+ *   memory itself.  Every call is asynchronous on the given stream except
+ *   where a comment says it synchronises.  A context must not be used from
+ *   two streams at once.  Synchronous failures (bad arguments, launch
+ *   errors) are returned as ed_status; conditions found on the device
+ *   (non-finite values, PCG breakdown, capacity overflow, a timed-out wait)
+ *   are written to the status word of ed_stats / ed_fuse's counts and to the
+ *   context's device status word, readable after the stream synchronises.
+ *   No kernel traps: every device wait is bounded.
+ */
+#ifndef ED_H_
+#define ED_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ed_status {
+    ED_OK = 0,
+    ED_ERR_ARG = 1,        /* invalid argument (NULL, size, alignment, limits) */
+    ED_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed */
+    ED_ERR_CAPACITY = 3,   /* a size exceeded the limits the context was created with */
+    ED_ERR_NONFINITE = 4,  /* a residual, energy or update was not finite */
+    ED_ERR_BREAKDOWN = 5,  /* PCG found p^T H p <= 0 or a preconditioner block not SPD */
+    ED_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    ED_ERR_STATE = 7       /* call order: e.g. ed_gn_step before ed_build_graph */
+} ed_status;
+
+enum { ED_PRECISION_FP32 = 0, ED_PRECISION_MIXED = 1 };
+enum { ED_WEIGHT_GAUSSIAN = 0, ED_WEIGHT_EQ2 = 1 };
+
+/* Capacities a context is created for; they size the workspace. */
+typedef struct ed_limits {
+    int max_points;          /* model points N */
+    int max_nodes;           /* ED nodes m (<= 16384) */
+    int max_width;           /* depth map size */
+    int max_height;
+    int max_pairs_per_node;  /* node pairs per node in J^T J (0 = 48) */
+    int max_cells;           /* sampling grid cells (0 = 1 << 24) */
+} ed_limits;
+
+typedef struct ed_intrinsics {
+    float fx, fy, cx, cy;    /* pinhole; pixel u covers [u - 0.5, u + 0.5) */
+    int width, height;
+} ed_intrinsics;
+
+typedef struct ed_context ed_context;
+
+/* Bytes of device workspace a context with these limits needs (host out). */
+ed_status ed_query_workspace(const ed_limits *limits, size_t *bytes);
+
+/* Creates a context on the current device over a caller-owned workspace of at
+ * least ed_query_workspace bytes (256-byte aligned).  *ctx is a host handle. */
+ed_status ed_create(const ed_limits *limits, void *workspace, size_t workspace_bytes, ed_context **ctx);
+ed_status ed_destroy(ed_context *ctx);
+
+/* Human-readable name of a status (static host string). */
+const char *ed_status_string(ed_status s);
+
+/*
+ * Target normal map n(u) used by the point-to-plane data term (Sec. II.E:
+ * "the corresponding normal to the pixel u").  The paper does not give the
+ * operator; this library uses n = normalize((V(u,v+h) - V(u,v-h)) x
+ * (V(u+h,v) - V(u-h,v))) over the back-projected depth V, oriented towards
+ * the camera, invalid (all zero) when a stencil sample or the centre is a
+ * hole or off the image.  depth [H][W] in, nmap [H][W][4] out.
+ */
+ed_status ed_compute_normals(ed_context *ctx, const float *depth, ed_intrinsics intr, int half_width,
+                             float *nmap, cudaStream_t stream);
+
+typedef struct ed_graph_params {
+    int k;             /* nearest nodes per point; must be 4 (Eq. 1, "k nearest") */
+    int k_graph;       /* node-graph neighbours |N(j)| (1..8) */
+    int weight_mode;   /* ED_WEIGHT_GAUSSIAN: exp(-d^2/(2 sigma^2)); ED_WEIGHT_EQ2: 1 - d/d_max (Eq. 2) */
+    float sigma;       /* Gaussian width (mm) */
+    float node_radius; /* Poisson-disk radius (mm) when nodes are sampled */
+    int max_nodes;     /* keep the first max_nodes sampled nodes (<= limits.max_nodes) */
+    float search_cell; /* cell edge of the nearest-node search grid (mm); 0 = automatic */
+} ed_graph_params;
+
+/* Caller-owned device buffers of a deformation graph. */
+typedef struct ed_graph {
+    float *nodes;      /* [max_nodes][4] node positions g_j (input when m_in > 0) */
+    uint16_t *idx;     /* [N][4] nearest nodes of each point, increasing distance */
+    float *weights;    /* [N][4] normalised skinning weights */
+    int *nbr;          /* [max_nodes][k_graph] node graph N(j) */
+    int *counts;       /* int[4]: m (nodes in use), m_sampled (before truncation), nnzb, status */
+} ed_graph;
+
+/*
+ * Builds the deformation graph of a model (Sec. II.D, II.E):
+ *   nodes: the m_in given nodes when m_in > 0, else a phase-ordered
+ *   Poisson-disk sample of the points with radius node_radius, truncated to
+ *   max_nodes in selection order;
+ *   skinning: the k nearest nodes of every point by the FP32 squared
+ *   distance (ties to the lower node index), normalised weights (Eq. 1-2);
+ *   node graph: the k_graph nearest other nodes of every node (alpha_jk = 1);
+ *   and, internally, the block-sparsity pattern of J^T J and the per-block
+ *   point lists used by ed_gn_step.
+ * pos/nrm [N][4] are the model (they must stay valid until the next
+ * ed_build_graph); the graph buffers are retained by the context likewise.
+ * Synchronises the stream (it reads back the node and block counts).
+ */
+ed_status ed_build_graph(ed_context *ctx, const float *pos, const float *nrm, int n_points, int m_in,
+                         const ed_graph_params *params, const ed_graph *graph, cudaStream_t stream);
+
+/* Host-side sizes of the graph built last (host out; NULL entries skipped). */
+ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_chunks);
+
+typedef struct ed_frame {
+    const float *depth;    /* [H][W] target depth D (mm), 0 = hole */
+    const float *nmap;     /* [H][W][4] target normals from ed_compute_normals */
+    const float *color;    /* [H][W][4] colour (ed_fuse only; may be NULL elsewhere) */
+    ed_intrinsics intr;
+} ed_frame;
+
+typedef struct ed_solver_params {
+    float w_data, w_rot, w_reg, w_r, w_p;  /* Eq. (3) weights (Sec. III.B: 1, 1000, 10000, 1e6, 1000) */
+    float eps_d;           /* visible-point gate ||v~ - Gamma|| < eps_d (mm) */
+    float cos_eps_n;       /* visible-point gate n~ . n(u) > cos_eps_n */
+    int n_pcg;             /* PCG iterations per Gauss-Newton step */
+    float pcg_tol;         /* early PCG stop when ||r|| <= tol ||b|| (0 = fixed count) */
+    float lambda;          /* Levenberg-Marquardt damping: H + lambda diag(H) */
+    float jitter;          /* preconditioner block shift, relative to trace/size */
+    int precision;         /* ED_PRECISION_FP32 or ED_PRECISION_MIXED */
+    double prior[6];       /* pose prior for E_r, E_p (Sec. II.E "Global Pose") */
+} ed_solver_params;
+
+/* Device-side statistics of one Gauss-Newton step, at its input (x, pose). */
+typedef struct ed_stats {
+    double energy;         /* Eq. (3) total */
+    double e_data, e_rot, e_reg, e_rot_prior, e_pos_prior;
+    double pcg_res0;       /* ||b|| */
+    double pcg_res;        /* ||b - H d|| after the last PCG iteration */
+    int n_valid;           /* points that passed the visible-point gate */
+    int pcg_iters;
+    int status;            /* ed_status of the device-side checks */
+    int reserved;
+} ed_stats;
+
+/*
+ * One Gauss-Newton step of Eq. (3) (Sec. II.E-F): warp (Eq. 1), projective
+ * association with the visible-point gate, data / rotation / regularisation
+ * / pose-prior residuals, J^T J and J^T r assembled into 12x12 node blocks,
+ * 6x12 pose-node blocks and a 6x6 pose block, then n_pcg iterations of
+ * block-Jacobi preconditioned CG on (H + lambda diag H) d = -J^T r from d = 0,
+ * and x += d, pose += d_pose.
+ * x: [m][12] float, updated in place.  x_master: [m][12] double, required for
+ * ED_PRECISION_MIXED (the master copy that accumulates the updates; x is
+ * rewritten from it), ignored otherwise.  pose: double[6], updated in place.
+ * stats: device ed_stats (may be NULL).  When a device check fails the
+ * update is skipped and stats->status says why.
+ */
+ed_status ed_gn_step(ed_context *ctx, const ed_frame *frame, const ed_solver_params *params, float *x,
+                     double *x_master, double *pose, ed_stats *stats, cudaStream_t stream);
+
+/*
+ * Optional debug outputs of the next ed_gn_step calls (device buffers or
+ * NULL): the warped points / normals and the associated pixel (v*W + u or
+ * -1) of every model point, as computed inside the step.
+ */
+ed_status ed_set_debug(ed_context *ctx, float *warped_pos, float *warped_nrm, int *pix);
+
+/*
+ * Copies the assembled normal equations of the last ed_gn_step (device to
+ * device): blocks [nnzb][12][12] in the row-major BSR order of row_ptr/col,
+ * pose-node blocks [m][6][12], pose block [6][6], gradient J^T r [12m+6],
+ * solution d [12m+6].  Any pointer may be NULL.  row_ptr [m+1], col [nnzb].
+ */
+ed_status ed_export_system(ed_context *ctx, int *row_ptr, int *col, float *blocks, float *pose_node,
+                           float *pose_block, float *grad, float *delta, cudaStream_t stream);
+
+/*
+ * Measurement hook: from now on, record events[2k] / events[2k+1] (caller-
+ * created cudaEvent_t, host array) on the launching stream immediately before
+ * and after the k-th launch of the selected kernel, for k < n_pairs; the count
+ * recorded so far goes to *recorded (host int, may be NULL).  kernel_id:
+ * ED_KERNEL_PCG (the persistent PCG solve of ed_gn_step), ED_KERNEL_POINTS
+ * (warp + association + residual pass), ED_KERNEL_ASSEMBLE, ED_KERNEL_FINALIZE.
+ * n_pairs = 0 switches the hook off.  The paper has no counterpart: this is
+ * instrumentation for roofline measurements.
+ */
+/* Kernel launches the library has issued in this process so far (host out).
+ * Instrumentation; the paper has no counterpart. */
+ed_status ed_launch_count(unsigned long long *count);
+
+enum { ED_KERNEL_PCG = 0, ED_KERNEL_POINTS = 1, ED_KERNEL_ASSEMBLE = 2, ED_KERNEL_FINALIZE = 3 };
+ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded);
+
+/*
+ * Eq. (1) warp of n points with the graph built last:
+ *   v~ = R sum_j w_j [A_j (v - g_j) + g_j + t_j] + T,
+ *   n~ = normalize(R sum_j w_j A_j n).
+ * pos_out.w = pos_in.w, nrm_out.w = nrm_in.w.
+ */
+ed_status ed_warp(ed_context *ctx, const float *x, const double *pose, const float *pos_in, const float *nrm_in,
+                  int n_points, float *pos_out, float *nrm_out, cudaStream_t stream);
+
+typedef struct ed_fuse_params {
+    float tau_d;           /* Alg. 1: |z~ - D(u)| < tau_d (mm) */
+    float cos_delta;       /* Alg. 1: n~ . n(u) > cos_delta */
+    float omega_max;       /* Eq. fusion4 upper bound */
+    int tau_time;          /* delete when frame - t > tau_time ... */
+    float tau_weight;      /* ... and omega < tau_weight (Alg. 2 step 4, Alg. 3) */
+    int frame;             /* current frame index (time stamp of fused / lifted points) */
+} ed_fuse_params;
+
+/*
+ * Model update of Sec. II.G (Algorithms 1-3, Eqs. fusion1-4), out of place.
+ * Inputs: the model (pos, nrm, col [n_in][4], t [n_in]) and the same points
+ * warped into the frame (wpos, wnrm from ed_warp).  Reg keeps, per pixel, the
+ * projected point with the smallest z~ (then the smallest index); a pixel is
+ * registered when D(u) > 0, the normal is valid, |z~ - D(u)| < tau_d and
+ * n~ . n(u) > cos_delta.  Registered points are fused with observation weight
+ * 1 (moved along their ray to the fused depth, colour and normal averaged,
+ * omega = min(omega + 1, omega_max), t = frame); every other valid pixel is
+ * lifted as a new point (omega = 1, t = frame); unregistered old points with
+ * frame - t > tau_time and omega < tau_weight are deleted.  Output order: kept
+ * old points in their order, then lifted pixels in pixel order.
+ * counts_out: device int[2] = (output count, status); the output is
+ * truncated at capacity with status ED_ERR_CAPACITY.  reg_out ([H][W] point
+ * index or -1) may be NULL.
+ */
+ed_status ed_fuse(ed_context *ctx, const float *pos, const float *nrm, const float *col, const int *tstamp,
+                  int n_in, const float *wpos, const float *wnrm, const ed_frame *frame,
+                  const ed_fuse_params *params, int capacity, float *pos_out, float *nrm_out, float *col_out,
+                  int *t_out, int *counts_out, int *reg_out, cudaStream_t stream);
+
+/*
+ * Energy of Eq. (3) at (x, pose) with the graph built last (forward of the
+ * differentiable warp + energy).  Association is recomputed and stored in
+ * the context for ed_energy_grad.  energy_out: device double[6] = (total,
+ * data, rot, reg, rot prior, pos prior).
+ */
+ed_status ed_energy(ed_context *ctx, const ed_frame *frame, const ed_solver_params *params, const float *x,
+                    const double *pose, double *energy_out, cudaStream_t stream);
+
+/*
+ * Gradient of Eq. (3) with respect to the node parameters and the pose,
+ * with the association of the last ed_energy frozen: dE/dx [12m] and
+ * dE/dpose [6] (float, device), scaled by grad_scale (the upstream gradient).
+ * Written by its own kernels (per-point residual derivatives gathered per
+ * node), independently of the J^T r assembly of ed_gn_step.
+ */
+ed_status ed_energy_grad(ed_context *ctx, const ed_frame *frame, const ed_solver_params *params,
+                         const float *x, const double *pose, float grad_scale, float *grad_x, float *grad_pose,
+                         cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ED_H_ */

@@ -232,7 +232,7 @@ def calibrate_radius(pos, count, lo=None, hi=None, iters=40):
     ext = pos[:, :3].max(0) - pos[:, :3].min(0)
     area = float(ext[0] * ext[1])
     guess = math.sqrt(area / count)
-    lo = lo if lo is not None else 0.25 * guess
+    lo = lo if lo is not None else 0.5 * guess
     hi = hi if hi is not None else 4.0 * guess
     _, m_lo = poisson_nodes(pos, lo, 0)
     if m_lo < count:

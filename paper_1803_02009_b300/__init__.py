@@ -1,0 +1,438 @@
+"""B300-native ED registration hot path of MIS-SLAM (arXiv 1803.02009).
+
+Thin ctypes binding of libed.so (the C ABI in include/ed.h).  Every step of
+the path runs in the library's CUDA kernels; PyTorch only supplies device
+memory and the current stream.  There is no CPU fallback: importing this
+package on a machine without the built library, or calling it without a CUDA
+device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+import os
+from typing import Optional
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libed.so")
+
+ED_PRECISION_FP32, ED_PRECISION_MIXED = 0, 1
+ED_WEIGHT_GAUSSIAN, ED_WEIGHT_EQ2 = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "capacity exceeded", 4: "non-finite value",
+          5: "PCG breakdown", 6: "device wait timed out", 7: "invalid call order"}
+
+_lib = None
+
+
+class EDError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+# ----------------------------------------------------------------------------
+# C structures (mirror include/ed.h)
+# ----------------------------------------------------------------------------
+
+class Limits(C.Structure):
+    _fields_ = [("max_points", C.c_int), ("max_nodes", C.c_int), ("max_width", C.c_int), ("max_height", C.c_int),
+                ("max_pairs_per_node", C.c_int), ("max_cells", C.c_int)]
+
+
+class Intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int),
+                ("height", C.c_int)]
+
+
+class GraphParams(C.Structure):
+    _fields_ = [("k", C.c_int), ("k_graph", C.c_int), ("weight_mode", C.c_int), ("sigma", C.c_float),
+                ("node_radius", C.c_float), ("max_nodes", C.c_int), ("search_cell", C.c_float)]
+
+
+class GraphBuf(C.Structure):
+    _fields_ = [("nodes", C.c_void_p), ("idx", C.c_void_p), ("weights", C.c_void_p), ("nbr", C.c_void_p),
+                ("counts", C.c_void_p)]
+
+
+class Frame(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("nmap", C.c_void_p), ("color", C.c_void_p), ("intr", Intrinsics)]
+
+
+class SolverParamsC(C.Structure):
+    _fields_ = [("w_data", C.c_float), ("w_rot", C.c_float), ("w_reg", C.c_float), ("w_r", C.c_float),
+                ("w_p", C.c_float), ("eps_d", C.c_float), ("cos_eps_n", C.c_float), ("n_pcg", C.c_int),
+                ("pcg_tol", C.c_float), ("lam", C.c_float), ("jitter", C.c_float), ("precision", C.c_int),
+                ("prior", C.c_double * 6)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("e_data", C.c_double), ("e_rot", C.c_double), ("e_reg", C.c_double),
+                ("e_rot_prior", C.c_double), ("e_pos_prior", C.c_double), ("pcg_res0", C.c_double),
+                ("pcg_res", C.c_double), ("n_valid", C.c_int), ("pcg_iters", C.c_int), ("status", C.c_int),
+                ("reserved", C.c_int)]
+
+
+STATS_BYTES = C.sizeof(Stats)
+
+
+class FuseParamsC(C.Structure):
+    _fields_ = [("tau_d", C.c_float), ("cos_delta", C.c_float), ("omega_max", C.c_float), ("tau_time", C.c_int),
+                ("tau_weight", C.c_float), ("frame", C.c_int)]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "ed_query_workspace": [C.POINTER(Limits), C.POINTER(C.c_size_t)],
+    "ed_create": [C.POINTER(Limits), _vp, C.c_size_t, C.POINTER(_vp)],
+    "ed_destroy": [_vp],
+    "ed_compute_normals": [_vp, _vp, Intrinsics, C.c_int, _vp, _vp],
+    "ed_build_graph": [_vp, _vp, _vp, C.c_int, C.c_int, C.POINTER(GraphParams), C.POINTER(GraphBuf), _vp],
+    "ed_graph_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "ed_gn_step": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, _vp, _vp, _vp],
+    "ed_set_debug": [_vp, _vp, _vp, _vp],
+    "ed_export_system": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "ed_warp": [_vp, _vp, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp],
+    "ed_fuse": [_vp, _vp, _vp, _vp, _vp, C.c_int, _vp, _vp, C.POINTER(Frame), C.POINTER(FuseParamsC), C.c_int, _vp,
+                _vp, _vp, _vp, _vp, _vp, _vp],
+    "ed_energy": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, _vp, _vp],
+    "ed_energy_grad": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, C.c_float, _vp, _vp, _vp],
+    "ed_set_timing": [_vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)],
+    "ed_launch_count": [C.POINTER(C.c_ulonglong)],
+}
+ED_KERNEL_PCG, ED_KERNEL_POINTS, ED_KERNEL_ASSEMBLE, ED_KERNEL_FINALIZE = 0, 1, 2, 3
+
+
+def lib():
+    """Loads libed.so; raises when it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libed.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.ed_status_string.argtypes = [C.c_int]
+        L.ed_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(fn, status):
+    if status != 0:
+        raise EDError(fn, status)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def intrinsics(intr) -> Intrinsics:
+    fx, fy, cx, cy, W, H = intr
+    return Intrinsics(fx, fy, cx, cy, int(W), int(H))
+
+
+# ----------------------------------------------------------------------------
+# parameters (defaults: Sec. III.B of the paper)
+# ----------------------------------------------------------------------------
+
+def cos_deg_f32(deg: float) -> float:
+    import numpy as np
+    return float(np.float32(math.cos(math.radians(deg))))
+
+
+@dataclasses.dataclass
+class SolverParams:
+    w_data: float = 1.0
+    w_rot: float = 1000.0
+    w_reg: float = 10000.0
+    w_r: float = 1.0e6
+    w_p: float = 1000.0
+    eps_d: float = 15.0
+    eps_n_deg: float = 10.0
+    n_pcg: int = 20
+    pcg_tol: float = 0.0
+    lam: float = 0.0
+    jitter: float = 1e-6
+    precision: int = ED_PRECISION_FP32
+    prior: tuple = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+
+    def c(self) -> SolverParamsC:
+        p = SolverParamsC()
+        p.w_data, p.w_rot, p.w_reg, p.w_r, p.w_p = self.w_data, self.w_rot, self.w_reg, self.w_r, self.w_p
+        p.eps_d = self.eps_d
+        p.cos_eps_n = cos_deg_f32(self.eps_n_deg)
+        p.n_pcg, p.pcg_tol, p.lam, p.jitter, p.precision = self.n_pcg, self.pcg_tol, self.lam, self.jitter, self.precision
+        for i in range(6):
+            p.prior[i] = float(self.prior[i])
+        return p
+
+
+@dataclasses.dataclass
+class FuseParams:
+    tau_d: float = 10.0
+    delta_deg: float = 10.0
+    omega_max: float = 20.0
+    tau_time: int = 10
+    tau_weight: float = 3.0
+    frame: int = 1
+
+    def c(self) -> FuseParamsC:
+        return FuseParamsC(self.tau_d, cos_deg_f32(self.delta_deg), self.omega_max, int(self.tau_time),
+                           self.tau_weight, int(self.frame))
+
+
+@dataclasses.dataclass
+class Graph:
+    nodes: torch.Tensor     # float32 [max_nodes, 4]
+    idx: torch.Tensor       # int16 storage of uint16 [N, 4]
+    weights: torch.Tensor   # float32 [N, 4]
+    nbr: torch.Tensor       # int32 [max_nodes, kg]
+    counts: torch.Tensor    # int32 [4]
+    m: int = 0
+    nnzb: int = 0
+
+    def idx_long(self):
+        return self.idx.to(torch.int32) & 0xFFFF
+
+
+class Context:
+    """A library context over a torch-allocated workspace on the current device."""
+
+    def __init__(self, max_points, max_nodes, max_width, max_height, max_pairs_per_node=0, max_cells=0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the ED hot path needs a CUDA device")
+        L = lib()
+        self.limits = Limits(int(max_points), int(max_nodes), int(max_width), int(max_height),
+                             int(max_pairs_per_node), int(max_cells))
+        nbytes = C.c_size_t(0)
+        _check("ed_query_workspace", L.ed_query_workspace(C.byref(self.limits), C.byref(nbytes)))
+        self.ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        h = C.c_void_p()
+        _check("ed_create", L.ed_create(C.byref(self.limits), _ptr(self.ws), nbytes.value, C.byref(h)))
+        self.h = h
+        self.graph: Optional[Graph] = None
+        self._keep = []
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                lib().ed_destroy(self.h)
+        except Exception:
+            pass
+
+    # -- steps ---------------------------------------------------------------
+
+    def compute_normals(self, depth, intr, half_width, out=None, stream=None):
+        H, W = int(intr[5]), int(intr[4])
+        nmap = out if out is not None else torch.empty((H, W, 4), dtype=torch.float32, device=depth.device)
+        _check("ed_compute_normals", lib().ed_compute_normals(self.h, _ptr(depth), intrinsics(intr), int(half_width),
+                                                              _ptr(nmap), _stream(stream)))
+        return nmap
+
+    def build_graph(self, pos, nrm, nodes=None, node_radius=0.0, max_nodes=0, k_graph=4,
+                    weight_mode=ED_WEIGHT_GAUSSIAN, sigma=1.0, search_cell=0.0, stream=None) -> Graph:
+        dev = pos.device
+        N = pos.shape[0]
+        cap = int(self.limits.max_nodes)
+        g = Graph(nodes=torch.zeros((cap, 4), dtype=torch.float32, device=dev),
+                  idx=torch.empty((N, 4), dtype=torch.int16, device=dev),
+                  weights=torch.empty((N, 4), dtype=torch.float32, device=dev),
+                  nbr=torch.empty((cap, k_graph), dtype=torch.int32, device=dev),
+                  counts=torch.zeros(4, dtype=torch.int32, device=dev))
+        m_in = 0
+        if nodes is not None:
+            m_in = nodes.shape[0]
+            g.nodes[:m_in].copy_(nodes)
+        prm = GraphParams(4, int(k_graph), int(weight_mode), float(sigma), float(node_radius),
+                          int(max_nodes if max_nodes else cap), float(search_cell))
+        gb = GraphBuf(g.nodes.data_ptr(), g.idx.data_ptr(), g.weights.data_ptr(), g.nbr.data_ptr(),
+                      g.counts.data_ptr())
+        _check("ed_build_graph", lib().ed_build_graph(self.h, _ptr(pos), _ptr(nrm), int(N), int(m_in),
+                                                      C.byref(prm), C.byref(gb), _stream(stream)))
+        m, nnzb, ne, nc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check("ed_graph_info", lib().ed_graph_info(self.h, C.byref(m), C.byref(nnzb), C.byref(ne), C.byref(nc)))
+        g.m, g.nnzb = m.value, nnzb.value
+        self.n_entries, self.n_chunks = ne.value, nc.value
+        self.graph = g
+        self._keep = [pos, nrm]          # the context reads them until the next build
+        return g
+
+    def identity_x(self, m=None):
+        m = self.graph.m if m is None else m
+        x = torch.zeros((m, 12), dtype=torch.float32, device="cuda")
+        x[:, 0] = x[:, 5] = x[:, 10] = 1.0
+        return x
+
+    def gn_step(self, frame: Frame, params: SolverParams, x, pose, x_master=None, stats=None, stream=None):
+        p = params.c()
+        _check("ed_gn_step", lib().ed_gn_step(self.h, C.byref(frame), C.byref(p), _ptr(x), _ptr(x_master),
+                                              _ptr(pose), _ptr(stats), _stream(stream)))
+
+    def set_debug(self, wpos=None, wnrm=None, pix=None):
+        _check("ed_set_debug", lib().ed_set_debug(self.h, _ptr(wpos), _ptr(wnrm), _ptr(pix)))
+
+    def export_system(self, stream=None):
+        g = self.graph
+        m, nnzb = g.m, g.nnzb
+        dev = "cuda"
+        out = dict(row_ptr=torch.empty(m + 1, dtype=torch.int32, device=dev),
+                   col=torch.empty(nnzb, dtype=torch.int32, device=dev),
+                   blocks=torch.empty((nnzb, 12, 12), dtype=torch.float32, device=dev),
+                   pose_node=torch.empty((m, 6, 12), dtype=torch.float32, device=dev),
+                   pose_block=torch.empty((6, 6), dtype=torch.float32, device=dev),
+                   grad=torch.empty(12 * m + 6, dtype=torch.float32, device=dev),
+                   delta=torch.empty(12 * m + 6, dtype=torch.float32, device=dev))
+        _check("ed_export_system", lib().ed_export_system(
+            self.h, _ptr(out["row_ptr"]), _ptr(out["col"]), _ptr(out["blocks"]), _ptr(out["pose_node"]),
+            _ptr(out["pose_block"]), _ptr(out["grad"]), _ptr(out["delta"]), _stream(stream)))
+        return out
+
+    def warp(self, x, pose, pos, nrm, pos_out=None, nrm_out=None, stream=None):
+        n = pos.shape[0]
+        po = pos_out if pos_out is not None else torch.empty_like(pos)
+        no = nrm_out if nrm_out is not None else torch.empty_like(nrm)
+        _check("ed_warp", lib().ed_warp(self.h, _ptr(x), _ptr(pose), _ptr(pos), _ptr(nrm), int(n), _ptr(po), _ptr(no),
+                                        _stream(stream)))
+        return po, no
+
+    def fuse(self, pos, nrm, col, tstamp, wpos, wnrm, frame: Frame, params: FuseParams, capacity, out=None,
+             reg=None, stream=None):
+        dev = pos.device
+        if out is None:
+            out = dict(pos=torch.empty((capacity, 4), dtype=torch.float32, device=dev),
+                       nrm=torch.empty((capacity, 4), dtype=torch.float32, device=dev),
+                       col=torch.empty((capacity, 4), dtype=torch.float32, device=dev),
+                       t=torch.empty(capacity, dtype=torch.int32, device=dev),
+                       counts=torch.zeros(2, dtype=torch.int32, device=dev))
+        fp = params.c()
+        _check("ed_fuse", lib().ed_fuse(self.h, _ptr(pos), _ptr(nrm), _ptr(col), _ptr(tstamp), int(pos.shape[0]),
+                                        _ptr(wpos), _ptr(wnrm), C.byref(frame), C.byref(fp), int(capacity),
+                                        _ptr(out["pos"]), _ptr(out["nrm"]), _ptr(out["col"]), _ptr(out["t"]),
+                                        _ptr(out["counts"]), _ptr(reg), _stream(stream)))
+        return out
+
+    def set_timing(self, kernel_id, events):
+        """Record torch.cuda.Event pairs around launches of one library kernel."""
+        self._tm_events = events
+        n = len(events) // 2
+        for e in events:          # torch creates the CUDA event at its first record
+            e.record()
+        if events:
+            torch.cuda.synchronize()
+        self._tm_arr = (C.c_void_p * max(1, len(events)))(*[e.cuda_event for e in events]) if n else None
+        self._tm_rec = C.c_int(0)
+        _check("ed_set_timing", lib().ed_set_timing(self.h, int(kernel_id), self._tm_arr, n, C.byref(self._tm_rec)))
+
+    def timing_count(self):
+        return self._tm_rec.value
+
+    def energy(self, frame: Frame, params: SolverParams, x, pose, out=None, stream=None):
+        e = out if out is not None else torch.empty(6, dtype=torch.float64, device="cuda")
+        p = params.c()
+        _check("ed_energy", lib().ed_energy(self.h, C.byref(frame), C.byref(p), _ptr(x), _ptr(pose), _ptr(e),
+                                            _stream(stream)))
+        return e
+
+    def energy_grad(self, frame: Frame, params: SolverParams, x, pose, scale=1.0, stream=None):
+        gx = torch.empty_like(x)
+        gp = torch.empty(6, dtype=torch.float32, device="cuda")
+        p = params.c()
+        _check("ed_energy_grad", lib().ed_energy_grad(self.h, C.byref(frame), C.byref(p), _ptr(x), _ptr(pose),
+                                                      float(scale), _ptr(gx), _ptr(gp), _stream(stream)))
+        return gx, gp
+
+
+def calibrate_radius(ctx: Context, pos, nrm, count, iters=40):
+    """Largest FP32 Poisson-disk radius whose node set has at least `count`
+    nodes, by bisection over ed_build_graph's sampled count (the set is then
+    truncated to `count` in selection order).  A set-up step: the stated 4 mm
+    node density and the 2048-node count of the workload disagree on this
+    surface, and the count is what the workload fixes."""
+    import numpy as np
+    p = pos[:, :3].cpu().numpy()
+    ext = p.max(0) - p.min(0)
+    guess = math.sqrt(float(ext[0] * ext[1]) / count)
+    lo, hi = 0.5 * guess, 4.0 * guess
+
+    def sampled(r):
+        g = ctx.build_graph(pos, nrm, node_radius=r, max_nodes=count, sigma=r)
+        return int(g.counts[1].item())
+
+    if sampled(lo) < count:
+        raise RuntimeError("lower radius bound yields too few nodes")
+    for _ in range(iters):
+        mid = float(np.float32(0.5 * (lo + hi)))
+        if mid == lo or mid == hi:
+            break
+        if sampled(mid) >= count:
+            lo = mid
+        else:
+            hi = mid
+    return float(np.float32(lo))
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libed in this process so far."""
+    v = C.c_ulonglong(0)
+    _check("ed_launch_count", lib().ed_launch_count(C.byref(v)))
+    return int(v.value)
+
+
+def make_frame(depth, nmap, intr, color=None) -> Frame:
+    f = Frame()
+    f.depth = depth.data_ptr()
+    f.nmap = nmap.data_ptr()
+    f.color = color.data_ptr() if color is not None else None
+    f.intr = intrinsics(intr)
+    return f
+
+
+def new_stats(count=1):
+    """Device buffer for ed_stats (raw bytes); read with read_stats."""
+    return torch.zeros((count, STATS_BYTES), dtype=torch.uint8, device="cuda")
+
+
+def read_stats(buf) -> list:
+    raw = buf.cpu().numpy().tobytes()
+    out = []
+    for k in range(len(raw) // STATS_BYTES):
+        s = Stats.from_buffer_copy(raw[k * STATS_BYTES:(k + 1) * STATS_BYTES])
+        out.append({f[0]: getattr(s, f[0]) for f in Stats._fields_})
+    return out
+
+
+class EDEnergy(torch.autograd.Function):
+    """Energy of Eq. (3) as a differentiable function of the node parameters
+    x [m, 12] and the pose [6] (float64); the backward is the library's own
+    gradient kernel (association frozen at the forward)."""
+
+    @staticmethod
+    def forward(ctxa, x, pose, context: Context, frame: Frame, params: SolverParams):
+        e = context.energy(frame, params, x.detach().contiguous(), pose.detach().contiguous())
+        ctxa.save_for_backward(x, pose)
+        ctxa.context, ctxa.frame, ctxa.params = context, frame, params
+        return e[0]
+
+    @staticmethod
+    def backward(ctxa, grad_out):
+        x, pose = ctxa.saved_tensors
+        gx, gp = ctxa.context.energy_grad(ctxa.frame, ctxa.params, x.detach().contiguous(),
+                                          pose.detach().contiguous(), scale=1.0)
+        s = grad_out.to(torch.float32)
+        return gx * s, (gp * s).to(pose.dtype), None, None, None

@@ -1,0 +1,467 @@
+// api.cu -- context and workspace, status strings, device scan and stable
+// radix sort utilities, the target normal map and the Eq. (1) warp.
+#include <stdlib.h>
+#include <string.h>
+
+#include "ed_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+void normalise_limits(ed_limits &L)
+{
+    if (L.max_pairs_per_node <= 0) L.max_pairs_per_node = 48;
+    if (L.max_cells <= 0) L.max_cells = 1 << 22;
+}
+
+size_t carve(ed_context *c, char *base)
+{
+    const ed_limits &L = c->lim;
+    const size_t N = (size_t)L.max_points, M = (size_t)L.max_nodes;
+    const size_t WH = (size_t)L.max_width * L.max_height;
+    const size_t cells = (size_t)L.max_cells;
+    const size_t nnzb = M * (size_t)L.max_pairs_per_node;
+    const size_t nent = 10 * N;
+    const size_t tiles = (nent + 1023) / 1024 + 1;
+    const size_t chunks = (16 * N) / ED_CHUNK + nnzb + M + 16;
+    const size_t P = 12 * M + 6;
+    const size_t big = (N > WH ? N : WH);
+    size_t scan_len = big > 256 * tiles ? big : 256 * tiles;
+    if (nnzb > scan_len) scan_len = nnzb;
+    Carver k{base};
+    c->misc = k.take<int>(MI_COUNT);
+    c->fmisc = k.take<float>(MF_COUNT);
+    c->dmisc = k.take<double>(64);
+    c->cell_of = k.take<int>(N);
+    c->cell_pick = k.take<int>(cells);
+    c->cell_node = k.take<int>(cells);
+    c->kcell_start = k.take<int>(cells + 1);
+    c->kcell_cnt = k.take<int>(cells + 1);
+    c->kcell_nodes = k.take<int>(M);
+    c->bm_words = (int)((M + 31) / 32);
+    c->bitmap = k.take<uint32_t>(M * (size_t)c->bm_words);
+    c->row_ptr = k.take<int>(M + 1);
+    c->row_cnt = k.take<int>(M + 1);
+    c->col = k.take<int>(nnzb);
+    c->brow = k.take<int>(nnzb);
+    c->tpos = k.take<int>(nnzb);
+    c->diag_pos = k.take<int>(M);
+    c->up_list = k.take<int>(nnzb);
+    c->max_nnzb = (int)nnzb;
+    c->ent_key = k.take<uint32_t>(nent);
+    c->ent_val = k.take<uint32_t>(nent);
+    c->ent_key2 = k.take<uint32_t>(nent);
+    c->ent_val2 = k.take<uint32_t>(nent);
+    c->radix_cnt = k.take<int>(256 * tiles + 1);
+    c->ent_cnt = k.take<int>(nnzb);
+    c->ent_start = k.take<int>(nnzb + 1);
+    c->chunk_cnt = k.take<int>(nnzb);
+    c->chunk_start = k.take<int>(nnzb + 1);
+    c->chunks = k.take<int4>(chunks);
+    c->max_chunks = (int)chunks;
+    c->partials = k.take<float>((size_t)ED_PART_STRIDE * chunks);
+    c->bsr = k.take<float>(nnzb * 144);
+    c->grad = k.take<float>(P);
+    c->pnode = k.take<float>(M * 72);
+    c->minv = k.take<float>(M * 144);
+    c->pose_blk = k.take<float>(72);
+    c->node_energy = k.take<double>(M * 2);
+    c->rec0 = k.take<float4>(N);
+    c->rec1 = k.take<float4>(N);
+    c->pix = k.take<int>(N);
+    c->max_k1_ctas = (int)((N + ED_K1_THREADS - 1) / ED_K1_THREADS) + 1;
+    c->k1_part = k.take<double>((size_t)c->max_k1_ctas * ED_K1_PART);
+    c->vec_stride = (P + 63) / 64 * 64;
+    c->vec = k.take<float>(6 * c->vec_stride);
+    c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
+    c->zbuf = k.take<unsigned long long>(WH);
+    c->regpix = k.take<int>(WH);
+    c->fused_pix = k.take<int>(N);
+    c->flag_a = k.take<int>(big + 1);
+    c->flag_b = k.take<int>(big + 1);
+    c->scan_tmp = k.take<int>(scan_len / 1024 + 2048);
+    c->gpts = k.take<float4>(2 * N);
+    return k.off + 256;
+}
+
+bool limits_ok(const ed_limits *L)
+{
+    return L && L->max_points > 0 && L->max_nodes >= 4 && L->max_nodes <= ED_HARD_MAX_NODES && L->max_width > 0 &&
+           L->max_height > 0 && L->max_points < (1 << 27) && (long)L->max_width * L->max_height < (1L << 30);
+}
+
+}  // namespace
+
+extern "C" ed_status ed_query_workspace(const ed_limits *limits, size_t *bytes)
+{
+    if (!limits_ok(limits) || !bytes) return ED_ERR_ARG;
+    ed_context c;
+    memset(&c, 0, sizeof(c));
+    c.lim = *limits;
+    normalise_limits(c.lim);
+    *bytes = carve(&c, nullptr);
+    return ED_OK;
+}
+
+extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t workspace_bytes, ed_context **out)
+{
+    if (!limits_ok(limits) || !workspace || !out || ((uintptr_t)workspace & 255)) return ED_ERR_ARG;
+    ed_context *c = (ed_context *)calloc(1, sizeof(ed_context));
+    if (!c) return ED_ERR_ARG;
+    c->lim = *limits;
+    normalise_limits(c->lim);
+    size_t need = carve(c, nullptr);
+    if (workspace_bytes < need) {
+        free(c);
+        return ED_ERR_CAPACITY;
+    }
+    carve(c, (char *)workspace);
+    c->ws = (char *)workspace;
+    c->ws_bytes = workspace_bytes;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        free(c);
+        return ED_ERR_CUDA;
+    }
+    if (cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess) {
+        free(c);
+        return ED_ERR_CUDA;
+    }
+    *out = c;
+    return ED_OK;
+}
+
+extern "C" ed_status ed_destroy(ed_context *ctx)
+{
+    if (!ctx) return ED_ERR_ARG;
+    free(ctx);
+    return ED_OK;
+}
+
+extern "C" const char *ed_status_string(ed_status s)
+{
+    switch (s) {
+    case ED_OK: return "ok";
+    case ED_ERR_ARG: return "invalid argument";
+    case ED_ERR_CUDA: return "CUDA error";
+    case ED_ERR_CAPACITY: return "capacity exceeded";
+    case ED_ERR_NONFINITE: return "non-finite value";
+    case ED_ERR_BREAKDOWN: return "PCG breakdown";
+    case ED_ERR_TIMEOUT: return "device wait timed out";
+    case ED_ERR_STATE: return "invalid call order";
+    }
+    return "unknown status";
+}
+
+extern "C" ed_status ed_set_debug(ed_context *ctx, float *warped_pos, float *warped_nrm, int *pix)
+{
+    if (!ctx) return ED_ERR_ARG;
+    ctx->dbg_wpos = warped_pos;
+    ctx->dbg_wnrm = warped_nrm;
+    ctx->dbg_pix = pix;
+    return ED_OK;
+}
+
+static unsigned long long g_launches = 0;
+void ed_note_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
+extern "C" ed_status ed_launch_count(unsigned long long *count)
+{
+    if (!count) return ED_ERR_ARG;
+    *count = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+    return ED_OK;
+}
+
+extern "C" ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded)
+{
+    if (!ctx || n_pairs < 0 || (n_pairs > 0 && !events) || kernel_id < 0 || kernel_id > 3) return ED_ERR_ARG;
+    ctx->tm_kernel = kernel_id;
+    ctx->tm_events = n_pairs > 0 ? events : nullptr;
+    ctx->tm_pairs = n_pairs;
+    ctx->tm_count = 0;
+    ctx->tm_recorded = recorded;
+    if (recorded) *recorded = 0;
+    return ED_OK;
+}
+
+extern "C" ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_chunks)
+{
+    if (!ctx) return ED_ERR_ARG;
+    if (!ctx->have_graph) return ED_ERR_STATE;
+    if (m) *m = ctx->m;
+    if (nnzb) *nnzb = ctx->nnzb;
+    if (n_entries) *n_entries = ctx->n_entries;
+    if (n_chunks) *n_chunks = ctx->n_chunks;
+    return ED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int arrays (out[n] = total), three-phase, recursive
+// ---------------------------------------------------------------------------
+
+#define SCAN_T 256
+#define SCAN_PER 4
+#define SCAN_TILE (SCAN_T * SCAN_PER)
+
+__device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < (SCAN_T / 32) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < (SCAN_T / 32)) sh[lane] = s;
+    }
+    __syncthreads();
+    total = sh[SCAN_T / 32 - 1];
+    int r = x - v + (wid > 0 ? sh[wid - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int n, int *__restrict__ sums)
+{
+    __shared__ int sh[32];
+    const long base = (long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
+    int v[SCAN_PER], loc = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_PER; ++e) {
+        v[e] = (base + e < n) ? in[base + e] : 0;
+        loc += v[e];
+    }
+    int total;
+    int pre = block_excl_scan(loc, sh, total);
+#pragma unroll
+    for (int e = 0; e < SCAN_PER; ++e) {
+        if (base + e < n) out[base + e] = pre;
+        pre += v[e];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ offs, int *__restrict__ total_out,
+                           const int *__restrict__ total_src)
+{
+    const long base = (long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
+    const int o = offs[blockIdx.x];
+#pragma unroll
+    for (int e = 0; e < SCAN_PER; ++e)
+        if (base + e < n) out[base + e] += o;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *total_out = *total_src;
+}
+
+static ed_status scan_rec(const int *in, int *out, int n, int *tmp, cudaStream_t st)
+{
+    const int nb = ed_div_up(n, SCAN_TILE);
+    int *sums = tmp;              // nb + 1 entries (exclusive scan, last = total)
+    int *next = tmp + nb + 1;
+    k_scan_tiles<<<nb, SCAN_T, 0, st>>>(in, out, n, sums); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    if (nb == 1) {
+        // sums[0] = total; make out[n] = total and sums exclusive
+        k_scan_add<<<1, SCAN_T, 0, st>>>(out, 0, next /*unused*/, out + n, sums); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        return ED_OK;
+    }
+    ed_status s = scan_rec(sums, sums, nb, next, st);
+    if (s != ED_OK) return s;
+    k_scan_add<<<nb, SCAN_T, 0, st>>>(out, n, sums, out + n, sums + nb); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}
+
+__global__ void k_set_zero_at(int *p) { *p = 0; }
+
+ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st)
+{
+    if (n <= 0) {
+        k_set_zero_at<<<1, 1, 0, st>>>(out); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        return ED_OK;
+    }
+    // the nb == 1 path of scan_rec reads offs[0] of `next`; keep it zero
+    return scan_rec(in, out, n, ctx->scan_tmp, st);
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (key, value) pairs, 8 bits per pass
+// ---------------------------------------------------------------------------
+
+#define RX_TILE 1024
+
+__global__ void k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift, int ntiles, int *__restrict__ cnt)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long base = (long)blockIdx.x * RX_TILE;
+    for (int e = threadIdx.x; e < RX_TILE; e += 256)
+        if (base + e < n) atomicAdd(&h[(keys[base + e] >> shift) & 255u], 1);
+    __syncthreads();
+    cnt[(long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// one warp per tile; elements visited in order, 32 at a time; equal digits keep order
+__global__ void k_radix_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int n, int shift,
+                                int ntiles, const int *__restrict__ offs, uint32_t *__restrict__ ko,
+                                uint32_t *__restrict__ vo)
+{
+    __shared__ int c[256];
+    const int tile = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int d = lane; d < 256; d += 32) c[d] = offs[(long)d * ntiles + tile];
+    __syncwarp();
+    const long base = (long)tile * RX_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int s = 0; s < RX_TILE; s += 32) {
+        const long e = base + s + lane;
+        const bool ok = e < n;
+        const unsigned active = __ballot_sync(0xffffffffu, ok);
+        if (!active) break;
+        uint32_t k = ok ? keys[e] : 0u;
+        uint32_t v = ok ? vals[e] : 0u;
+        int d = ok ? (int)((k >> shift) & 255u) : 256 + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        int pos = ok ? c[d] + rank : 0;
+        __syncwarp();
+        if (ok && rank == 0) c[d] += __popc(peers);
+        __syncwarp();
+        if (ok) {
+            ko[pos] = k;
+            vo[pos] = v;
+        }
+    }
+}
+
+ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st)
+{
+    if (n <= 1) return ED_OK;
+    const int ntiles = ed_div_up(n, RX_TILE);
+    uint32_t *ka = keys, *va = vals, *kb = ctx->ent_key2, *vb = ctx->ent_val2;
+    int passes = 0;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        k_radix_hist<<<ntiles, 256, 0, st>>>(ka, n, shift, ntiles, ctx->radix_cnt); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        ed_status s = ed_scan_exclusive(ctx, ctx->radix_cnt, ctx->radix_cnt, 256 * ntiles, st);
+        if (s != ED_OK) return s;
+        k_radix_scatter<<<ntiles, 32, 0, st>>>(ka, va, n, shift, ntiles, ctx->radix_cnt, kb, vb); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+        passes++;
+    }
+    if (ka != keys) {
+        ED_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    return ED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// target normal map (data term n(u), Sec. II.E)
+// ---------------------------------------------------------------------------
+
+__global__ void k_normals(const float *__restrict__ depth, ed_intrinsics K, int h, float4 *__restrict__ nmap)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= K.width || v >= K.height) return;
+    const int W = K.width;
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (u - h >= 0 && u + h < W && v - h >= 0 && v + h < K.height) {
+        const float Dc = __ldg(depth + v * W + u);
+        const float Dl = __ldg(depth + v * W + u - h), Dr = __ldg(depth + v * W + u + h);
+        const float Du = __ldg(depth + (v - h) * W + u), Dd = __ldg(depth + (v + h) * W + u);
+        if (Dc > 0.f && Dl > 0.f && Dr > 0.f && Du > 0.f && Dd > 0.f) {
+            const float ifx = 1.0f / K.fx, ify = 1.0f / K.fy;
+            const float xl = ((float)(u - h) - K.cx) * Dl * ifx, yl = ((float)v - K.cy) * Dl * ify;
+            const float xr = ((float)(u + h) - K.cx) * Dr * ifx, yr = ((float)v - K.cy) * Dr * ify;
+            const float xu = ((float)u - K.cx) * Du * ifx, yu = ((float)(v - h) - K.cy) * Du * ify;
+            const float xd = ((float)u - K.cx) * Dd * ifx, yd = ((float)(v + h) - K.cy) * Dd * ify;
+            const float ax = xd - xu, ay = yd - yu, az = Dd - Du;   // V(u, v+h) - V(u, v-h)
+            const float bx = xr - xl, by = yr - yl, bz = Dr - Dl;   // V(u+h, v) - V(u-h, v)
+            float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
+            const float l2 = nx * nx + ny * ny + nz * nz;
+            if (l2 > 0.f) {
+                float s = rsqrtf(l2);
+                if (nz > 0.f) s = -s;
+                o = make_float4(nx * s, ny * s, nz * s, 1.0f);
+            }
+        }
+    }
+    nmap[v * W + u] = o;
+}
+
+extern "C" ed_status ed_compute_normals(ed_context *ctx, const float *depth, ed_intrinsics intr, int half_width,
+                                        float *nmap, cudaStream_t stream)
+{
+    if (!ctx || !depth || !nmap || intr.width <= 0 || intr.height <= 0 || half_width < 1 ||
+        !(intr.fx > 0.f) || !(intr.fy > 0.f) || ((uintptr_t)nmap & 15))
+        return ED_ERR_ARG;
+    dim3 b(32, 8), g(ed_div_up(intr.width, 32), ed_div_up(intr.height, 8));
+    k_normals<<<g, b, 0, stream>>>(depth, intr, half_width, (float4 *)nmap); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (1) warp of a point set
+// ---------------------------------------------------------------------------
+
+__global__ void k_warp(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, const ushort4 *__restrict__ idx,
+                       const float4 *__restrict__ w, const float4 *__restrict__ g, const float4 *__restrict__ x4,
+                       const double *__restrict__ pose, int n, float4 *__restrict__ pos_out, float4 *__restrict__ nrm_out)
+{
+    __shared__ ed_pose_f P;
+    if (threadIdx.x == 0) ed_pose_eval(pose, P);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = pos[i], nr = nrm[i];
+    ed_warped W = ed_warp_point(p, nr, idx[i], w[i], g, x4, P.R, P.T);
+    pos_out[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
+    nrm_out[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
+}
+
+extern "C" ed_status ed_warp(ed_context *ctx, const float *x, const double *pose, const float *pos_in,
+                             const float *nrm_in, int n_points, float *pos_out, float *nrm_out, cudaStream_t stream)
+{
+    if (!ctx || !x || !pose || !pos_in || !nrm_in || !pos_out || !nrm_out || n_points < 0) return ED_ERR_ARG;
+    if (!ctx->have_graph) return ED_ERR_STATE;
+    if (n_points > ctx->N) return ED_ERR_ARG;   // the skinning of the graph covers the model points
+    if (n_points == 0) return ED_OK;
+    k_warp<<<ed_div_up(n_points, 256), 256, 0, stream>>>(
+        (const float4 *)pos_in, (const float4 *)nrm_in, (const ushort4 *)ctx->graph.idx,
+        (const float4 *)ctx->graph.weights, (const float4 *)ctx->graph.nodes, (const float4 *)x, pose, n_points,
+        (float4 *)pos_out, (float4 *)nrm_out); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}

@@ -1,0 +1,365 @@
+// ed_internal.cuh -- context, workspace layout and device helpers of libed.
+//
+// Everything here is private to the library; the public ABI is include/ed.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "ed.h"
+
+#define ED_K 4                 // nearest nodes per point (Eq. 1)
+#define ED_MAX_KG 8            // node-graph neighbours
+#define ED_HARD_MAX_NODES 16384
+#define ED_CHUNK 64            // assembly entries per chunk
+#define ED_PART_STRIDE 84      // floats per assembly partial (60 moments, or 12 + 72)
+#define ED_K1_THREADS 256
+#define ED_K1_PART 32          // doubles per point-kernel CTA partial
+#define ED_PCG_PART 8          // doubles per PCG CTA partial
+#define ED_MAX_PCG_GRID 1184   // 8 x 148
+
+// indices of the misc int words in the workspace
+enum {
+    MI_STATUS = 0,       // device status word (ed_status)
+    MI_M = 1,            // nodes in use
+    MI_MTOTAL = 2,       // sampled nodes before truncation
+    MI_DIMS = 4,         // 4..6 sampling-grid dims, 7 = cells
+    MI_KDIMS = 8,        // 8..10 search-grid dims, 11 = cells
+    MI_NNZB = 12,
+    MI_SCAN_TOTAL = 13,
+    MI_MAXSEG = 14,
+    MI_NCHUNK = 15,
+    MI_BBOX = 16,        // 16..21 ordered-int bbox (min xyz, max xyz)
+    MI_PHASE_BASE = 24,  // running node count during sampling
+    MI_BAR = 32,         // 32 count, 33 generation (grid barrier)
+    MI_FUSE = 40,        // 40 kept, 41 lifted
+    MI_COUNT = 64
+};
+enum { MF_CELL = 0, MF_INV = 1, MF_KCELL = 2, MF_KINV = 3, MF_R2 = 4, MF_BBOX = 8, MF_COUNT = 16 };
+
+struct ed_context {
+    ed_limits lim;
+    char *ws;
+    size_t ws_bytes;
+    int device;
+    int num_sms;
+
+    // ---- workspace arrays ----
+    int *misc;
+    float *fmisc;
+    double *dmisc;           // 64 doubles: pose-level scalars of the current step
+    // sampling / search grids
+    int *cell_of;            // [N]
+    int *cell_pick;          // [cells]
+    int *cell_node;          // [cells]
+    int *kcell_start;        // [cells + 1]
+    int *kcell_cnt;          // [cells]
+    int *kcell_nodes;        // [max_nodes]
+    // pattern
+    uint32_t *bitmap;        // [max_nodes * words]
+    int bm_words;
+    int *row_ptr;            // [max_nodes + 1]
+    int *row_cnt;            // [max_nodes + 1]
+    int *col;                // [max_nnzb]
+    int *brow;               // [max_nnzb] row of each block
+    int *tpos;               // [max_nnzb] position of the transposed block
+    int *diag_pos;           // [max_nodes]
+    int *up_list;            // [max_nnzb] upper block positions
+    int max_nnzb;
+    // assembly lists
+    uint32_t *ent_key;       // [10 N] block id, then sorted
+    uint32_t *ent_val;       // [10 N] point << 4 | s << 2 | t, then sorted
+    uint32_t *ent_key2;      // radix temp
+    uint32_t *ent_val2;
+    int *radix_cnt;          // [256 * tiles + 1]
+    int *ent_cnt;            // [max_nnzb]
+    int *ent_start;          // [max_nnzb + 1]
+    int *chunk_cnt;          // [max_nnzb]
+    int *chunk_start;        // [max_nnzb + 1]
+    int4 *chunks;            // [max_chunks] (block, begin, count, role)
+    int max_chunks;
+    float *partials;         // [ED_PART_STRIDE][max_chunks]
+    // normal equations
+    float *bsr;              // [max_nnzb][144]
+    float *grad;             // [12 m + 6] J^T r
+    float *pnode;            // [m][72] pose-node blocks
+    float *minv;             // [m][144] block-Jacobi inverses
+    float *pose_blk;         // [36] pose block, [36..72) its inverse
+    double *node_energy;     // [m][2] rot, reg
+    float4 *rec0;            // [N] (R^T n(u), r)
+    float4 *rec1;            // [N] (d r / d angles, 0)
+    int *pix;                // [N] association of the last evaluation
+    double *k1_part;         // [ctas][ED_K1_PART]
+    int max_k1_ctas;
+    // PCG
+    float *vec;              // 6 vectors of 12 max_nodes + 6: d, r, z, p0, p1, q
+    size_t vec_stride;       // floats between vectors (multiple of 64: 16-byte aligned float4 rows)
+    double *pcg_part;        // [2][ED_MAX_PCG_GRID][ED_PCG_PART]
+    // fusion / scans
+    unsigned long long *zbuf;  // [W H]
+    int *regpix;             // [W H]
+    int *fused_pix;          // [N]
+    int *flag_a;             // [max(N, W H) + 1]
+    int *flag_b;             // [max(N, W H) + 1]
+    int *scan_tmp;           // block sums
+    float4 *gpts;            // [N] gradient per-point records (x2)
+
+    // ---- graph state (host) ----
+    int have_graph;
+    const float *pos;
+    const float *nrm;
+    int N;
+    ed_graph graph;
+    int k_graph;
+    int weight_mode;
+    float sigma;
+    int m;
+    int nnzb;
+    int n_upper;
+    int n_entries;
+    int n_chunks;
+    int have_system;
+    int have_energy;
+    int pcg_grid;
+    int pcg_threads;
+
+    float *dbg_wpos, *dbg_wnrm;
+    int *dbg_pix;
+
+    // measurement hook (ed_set_timing)
+    int tm_kernel;
+    cudaEvent_t *tm_events;
+    int tm_pairs;
+    int tm_count;
+    int *tm_recorded;
+};
+
+// events around one launch of a kernel selected by ed_set_timing
+// a failed record switches the hook off and clears the error, so that it is
+// never reported as the failure of a kernel launch
+static inline void ed_tm_record(ed_context *c, cudaEvent_t e, cudaStream_t st)
+{
+    if (cudaEventRecord(e, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        fprintf(stderr, "libed: timing event record failed; timing hook disabled\n");
+        c->tm_events = nullptr;
+    }
+}
+static inline void ed_tm_begin(ed_context *c, int kid, cudaStream_t st)
+{
+    if (c->tm_events && c->tm_kernel == kid && c->tm_count < c->tm_pairs)
+        ed_tm_record(c, c->tm_events[2 * c->tm_count], st);
+}
+static inline void ed_tm_end(ed_context *c, int kid, cudaStream_t st)
+{
+    if (c->tm_events && c->tm_kernel == kid && c->tm_count < c->tm_pairs) {
+        ed_tm_record(c, c->tm_events[2 * c->tm_count + 1], st);
+        if (!c->tm_events) return;
+        c->tm_count++;
+        if (c->tm_recorded) *c->tm_recorded = c->tm_count;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// error helpers
+// ---------------------------------------------------------------------------
+
+#define ED_CUDA_TRY(call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            fprintf(stderr, "libed: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                                 \
+            return ED_ERR_CUDA;                                                                \
+        }                                                                                      \
+    } while (0)
+
+#define ED_LAUNCH_CHECK()                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                                   \
+        if (e_ != cudaSuccess) {                                                               \
+            fprintf(stderr, "libed: launch failed: %s (%s:%d)\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return ED_ERR_CUDA;                                                                \
+        }                                                                                      \
+    } while (0)
+
+static inline int ed_div_up(long a, long b) { return (int)((a + b - 1) / b); }
+
+// process-wide count of kernel launches issued by the library (host side)
+void ed_note_launch();
+
+// ---------------------------------------------------------------------------
+// exact FP32 decision rules (no fused multiply-add, fixed operation order)
+// ---------------------------------------------------------------------------
+
+// squared distance key dx*dx + dy*dy + dz*dz, left to right
+__device__ __forceinline__ float ed_key(float px, float py, float pz, float gx, float gy, float gz)
+{
+    float dx = __fsub_rn(px, gx);
+    float dy = __fsub_rn(py, gy);
+    float dz = __fsub_rn(pz, gz);
+    float s = __fmul_rn(dx, dx);
+    s = __fadd_rn(s, __fmul_rn(dy, dy));
+    s = __fadd_rn(s, __fmul_rn(dz, dz));
+    return s;
+}
+
+__device__ __forceinline__ float ed_dot3_exact(float ax, float ay, float az, float bx, float by, float bz)
+{
+    float s = __fmul_rn(ax, bx);
+    s = __fadd_rn(s, __fmul_rn(ay, by));
+    s = __fadd_rn(s, __fmul_rn(az, bz));
+    return s;
+}
+
+// P(v): q = x / z, t = fx q, t += cx, t += 0.5, pixel = floor(t)
+__device__ __forceinline__ bool ed_project(float x, float y, float z, const ed_intrinsics &K, int &u, int &v)
+{
+    if (!(z > 0.0f)) return false;
+    float tx = __fadd_rn(__fadd_rn(__fmul_rn(K.fx, __fdiv_rn(x, z)), K.cx), 0.5f);
+    float ty = __fadd_rn(__fadd_rn(__fmul_rn(K.fy, __fdiv_rn(y, z)), K.cy), 0.5f);
+    float fu = floorf(tx), fv = floorf(ty);
+    if (!(fu >= 0.0f && fu < (float)K.width && fv >= 0.0f && fv < (float)K.height)) return false;
+    u = (int)fu;
+    v = (int)fv;
+    return true;
+}
+
+// Pi(u, D) for the gates: ((u - cx) D / fx, (v - cy) D / fy, D)
+__device__ __forceinline__ float3 ed_backproject(int u, int v, float D, const ed_intrinsics &K)
+{
+    float a = __fdiv_rn(__fmul_rn(__fsub_rn((float)u, K.cx), D), K.fx);
+    float b = __fdiv_rn(__fmul_rn(__fsub_rn((float)v, K.cy), D), K.fy);
+    return make_float3(a, b, D);
+}
+
+// ---------------------------------------------------------------------------
+// global pose
+// ---------------------------------------------------------------------------
+
+struct ed_pose_f {
+    float R[9];
+    float dR[27];   // dR/dalpha, dR/dbeta, dR/dgamma
+    float T[3];
+};
+
+__device__ __forceinline__ void ed_mat3_mul_d(const double *a, const double *b, double *c)
+{
+    double t[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) t[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) c[i] = t[i];
+}
+
+// R = Rz(gamma) Ry(beta) Rx(alpha) and its angle derivatives, in double, rounded to float
+__device__ inline void ed_pose_eval(const double *pose, ed_pose_f &P)
+{
+    double ca = cos(pose[0]), sa = sin(pose[0]);
+    double cb = cos(pose[1]), sb = sin(pose[1]);
+    double cg = cos(pose[2]), sg = sin(pose[2]);
+    double Rx[9] = {1, 0, 0, 0, ca, -sa, 0, sa, ca}, dRx[9] = {0, 0, 0, 0, -sa, -ca, 0, ca, -sa};
+    double Ry[9] = {cb, 0, sb, 0, 1, 0, -sb, 0, cb}, dRy[9] = {-sb, 0, cb, 0, 0, 0, -cb, 0, -sb};
+    double Rz[9] = {cg, -sg, 0, sg, cg, 0, 0, 0, 1}, dRz[9] = {-sg, -cg, 0, cg, -sg, 0, 0, 0, 0};
+    double t[9], R[9], d[9];
+    ed_mat3_mul_d(Rz, Ry, t);
+    ed_mat3_mul_d(t, Rx, R);
+    for (int i = 0; i < 9; ++i) P.R[i] = (float)R[i];
+    ed_mat3_mul_d(t, dRx, d);
+    for (int i = 0; i < 9; ++i) P.dR[i] = (float)d[i];
+    ed_mat3_mul_d(Rz, dRy, t);
+    ed_mat3_mul_d(t, Rx, d);
+    for (int i = 0; i < 9; ++i) P.dR[9 + i] = (float)d[i];
+    ed_mat3_mul_d(dRz, Ry, t);
+    ed_mat3_mul_d(t, Rx, d);
+    for (int i = 0; i < 9; ++i) P.dR[18 + i] = (float)d[i];
+    for (int i = 0; i < 3; ++i) P.T[i] = (float)pose[3 + i];
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (1) warp of one point (shared by ed_warp, the GN step and the gradient)
+// ---------------------------------------------------------------------------
+
+struct ed_warped {
+    float3 s;     // sum_j w_j [A_j (v - g_j) + g_j + t_j] (before the global pose)
+    float3 v;     // R s + T
+    float3 n;     // normalize(R sum_j w_j A_j n)
+};
+
+__device__ __forceinline__ ed_warped ed_warp_point(float4 p, float4 nr, ushort4 id, float4 w, const float4 *__restrict__ g,
+                                                    const float4 *__restrict__ x4, const float *R, const float *T)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+    const unsigned short ids[4] = {id.x, id.y, id.z, id.w};
+    const float ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = ids[k];
+        const float4 gj = __ldg(g + j);
+        const float4 a0 = __ldg(x4 + 3 * j), a1 = __ldg(x4 + 3 * j + 1), a2 = __ldg(x4 + 3 * j + 2);
+        const float dx = p.x - gj.x, dy = p.y - gj.y, dz = p.z - gj.z;
+        const float wk = ws[k];
+        s0 += wk * (a0.x * dx + a0.y * dy + a0.z * dz + a0.w + gj.x);
+        s1 += wk * (a1.x * dx + a1.y * dy + a1.z * dz + a1.w + gj.y);
+        s2 += wk * (a2.x * dx + a2.y * dy + a2.z * dz + a2.w + gj.z);
+        n0 += wk * (a0.x * nr.x + a0.y * nr.y + a0.z * nr.z);
+        n1 += wk * (a1.x * nr.x + a1.y * nr.y + a1.z * nr.z);
+        n2 += wk * (a2.x * nr.x + a2.y * nr.y + a2.z * nr.z);
+    }
+    ed_warped o;
+    o.s = make_float3(s0, s1, s2);
+    o.v = make_float3(R[0] * s0 + R[1] * s1 + R[2] * s2 + T[0], R[3] * s0 + R[4] * s1 + R[5] * s2 + T[1],
+                      R[6] * s0 + R[7] * s1 + R[8] * s2 + T[2]);
+    float m0 = R[0] * n0 + R[1] * n1 + R[2] * n2;
+    float m1 = R[3] * n0 + R[4] * n1 + R[5] * n2;
+    float m2 = R[6] * n0 + R[7] * n1 + R[8] * n2;
+    float l2 = m0 * m0 + m1 * m1 + m2 * m2;
+    float il = l2 > 0.f ? 1.0f / sqrtf(l2) : 0.f;
+    o.n = make_float3(m0 * il, m1 * il, m2 * il);
+    return o;
+}
+
+// E_reg residual of an edge j -> k, row r: A_j (g_k - g_j) + g_j + t_j - g_k - t_k,
+// evaluated as (A_j - I)(g_k - g_j) + t_j - t_k (identical algebra) so that no
+// term of the size of the coordinates (~60 mm) cancels in FP32.
+// xrow = row r of [A_j | t_j]; h = g_k - g_j; tk = t_k[r].
+__device__ __forceinline__ float ed_reg_residual(const float *xrow, int r, const float *h, float tk)
+{
+    float a0 = xrow[0], a1 = xrow[1], a2 = xrow[2];
+    if (r == 0) a0 -= 1.0f;
+    else if (r == 1) a1 -= 1.0f;
+    else a2 -= 1.0f;
+    return a0 * h[0] + a1 * h[1] + a2 * h[2] + (xrow[3] - tk);
+}
+
+// association of a warped point: pixel index or -1 (visible-point gate, Sec. II.E)
+__device__ __forceinline__ int ed_associate(const ed_warped &W, const float *__restrict__ depth,
+                                            const float4 *__restrict__ nmap, const ed_intrinsics &K, float eps2,
+                                            float cos_eps_n)
+{
+    int u, v;
+    if (!ed_project(W.v.x, W.v.y, W.v.z, K, u, v)) return -1;
+    const int q = v * K.width + u;
+    const float D = __ldg(depth + q);
+    if (!(D > 0.0f)) return -1;
+    const float4 tn = __ldg(nmap + q);
+    if (tn.w == 0.0f) return -1;
+    const float3 G = ed_backproject(u, v, D, K);
+    const float dx = __fsub_rn(W.v.x, G.x), dy = __fsub_rn(W.v.y, G.y), dz = __fsub_rn(W.v.z, G.z);
+    if (!(ed_dot3_exact(dx, dy, dz, dx, dy, dz) < eps2)) return -1;
+    if (!(ed_dot3_exact(W.n.x, W.n.y, W.n.z, tn.x, tn.y, tn.z) > cos_eps_n)) return -1;
+    return q;
+}
+
+// ---------------------------------------------------------------------------
+// internal entry points shared between translation units
+// ---------------------------------------------------------------------------
+
+ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st);
+ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
+ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st);
+ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
+                        const double *pose, int write_records, cudaStream_t st);

@@ -1,0 +1,892 @@
+// gn.cu -- one Gauss-Newton step of Eq. (3) (Sec. II.E-F): point pass,
+// normal-equation assembly into 12x12 node blocks, pose finalisation and
+// update; the energy of Eq. (3) and its gradient for differentiation.
+#include <math.h>
+#include <string.h>
+
+#include "ed_internal.cuh"
+
+enum { PASS_STEP = 0, PASS_ENERGY = 1, PASS_GRAD = 2 };
+
+struct PointArgs {
+    const float4 *pos, *nrm, *w, *g, *x4;
+    const ushort4 *idx;
+    const double *pose;
+    const float *depth;
+    const float4 *nmap;
+    ed_intrinsics K;
+    int n;
+    float eps2, cos_eps_n, sw;
+    int mode;
+    int *pix;          // association (written in STEP / ENERGY, read in GRAD)
+    float4 *rec0, *rec1;
+    double *part;      // [grid][ED_K1_PART]
+    float *dbg_wpos, *dbg_wnrm;
+    int *dbg_pix;
+};
+
+// Per point: Eq. (1) warp, visible-point gate, data residual r = n(u).(v~ - Gamma)
+// and its derivative factors; per-CTA sums of E_data, the count, the 6x6 pose
+// block and the pose gradient (fixed grid-stride order: deterministic).
+__global__ void __launch_bounds__(ED_K1_THREADS) k_points(PointArgs a)
+{
+    __shared__ ed_pose_f P;
+    __shared__ float red[ED_K1_THREADS / 32][30];
+    if (threadIdx.x == 0) ed_pose_eval(a.pose, P);
+    __syncthreads();
+    float acc[30];
+#pragma unroll
+    for (int k = 0; k < 30; ++k) acc[k] = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const float4 p = a.pos[i], nr = a.nrm[i];
+        const ed_warped W = ed_warp_point(p, nr, a.idx[i], a.w[i], a.g, a.x4, P.R, P.T);
+        int q;
+        if (a.mode == PASS_GRAD) q = a.pix[i];
+        else {
+            q = ed_associate(W, a.depth, a.nmap, a.K, a.eps2, a.cos_eps_n);
+            a.pix[i] = q;
+            if (a.dbg_pix) {
+                a.dbg_pix[i] = q;
+                reinterpret_cast<float4 *>(a.dbg_wpos)[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
+                reinterpret_cast<float4 *>(a.dbg_wnrm)[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
+            }
+        }
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        if (q >= 0) {
+            const int u = q % a.K.width, v = q / a.K.width;
+            const float D = __ldg(a.depth + q);
+            const float4 tn = __ldg(a.nmap + q);
+            const float Gx = ((float)u - a.K.cx) * D / a.K.fx, Gy = ((float)v - a.K.cy) * D / a.K.fy;
+            const float r = a.sw * (tn.x * (W.v.x - Gx) + tn.y * (W.v.y - Gy) + tn.z * (W.v.z - D));
+            const float *R = P.R;
+            // R^T n(u), scaled by sqrt(w_data)
+            const float b0 = a.sw * (R[0] * tn.x + R[3] * tn.y + R[6] * tn.z);
+            const float b1 = a.sw * (R[1] * tn.x + R[4] * tn.y + R[7] * tn.z);
+            const float b2 = a.sw * (R[2] * tn.x + R[5] * tn.y + R[8] * tn.z);
+            float jp[6];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const float *d = P.dR + 9 * t;
+                const float e0 = d[0] * W.s.x + d[1] * W.s.y + d[2] * W.s.z;
+                const float e1 = d[3] * W.s.x + d[4] * W.s.y + d[5] * W.s.z;
+                const float e2 = d[6] * W.s.x + d[7] * W.s.y + d[8] * W.s.z;
+                jp[t] = a.sw * (tn.x * e0 + tn.y * e1 + tn.z * e2);
+            }
+            jp[3] = a.sw * tn.x;
+            jp[4] = a.sw * tn.y;
+            jp[5] = a.sw * tn.z;
+            r0 = make_float4(b0, b1, b2, r);
+            r1 = make_float4(jp[0], jp[1], jp[2], 1.0f);
+            acc[0] += r * r;
+            acc[1] += 1.0f;
+            int k = 2;
+#pragma unroll
+            for (int t = 0; t < 6; ++t)
+#pragma unroll
+                for (int s = t; s < 6; ++s) acc[k++] += jp[t] * jp[s];
+#pragma unroll
+            for (int t = 0; t < 6; ++t) acc[23 + t] += r * jp[t];
+            if (!isfinite(r)) acc[29] += 1.0f;
+        }
+        if (a.mode != PASS_ENERGY) {
+            a.rec0[i] = r0;
+            a.rec1[i] = r1;
+        }
+    }
+    // block reduction: warp shuffles (float), then warps in order (double)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 30; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 30) {
+        double s = 0.0;
+        for (int w = 0; w < ED_K1_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
+        a.part[blockIdx.x * ED_K1_PART + threadIdx.x] = s;
+    }
+}
+
+static int k1_grid(const ed_context *ctx)
+{
+    int g = ed_div_up(ctx->N, ED_K1_THREADS);
+    const int cap = 4 * ctx->num_sms;
+    if (g > cap) g = cap;
+    if (g > ctx->max_k1_ctas) g = ctx->max_k1_ctas;
+    return g < 1 ? 1 : g;
+}
+
+ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
+                        const double *pose, int mode, cudaStream_t st)
+{
+    PointArgs a;
+    a.pos = (const float4 *)ctx->pos;
+    a.nrm = (const float4 *)ctx->nrm;
+    a.w = (const float4 *)ctx->graph.weights;
+    a.g = (const float4 *)ctx->graph.nodes;
+    a.x4 = (const float4 *)x;
+    a.idx = (const ushort4 *)ctx->graph.idx;
+    a.pose = pose;
+    a.depth = fr->depth;
+    a.nmap = (const float4 *)fr->nmap;
+    a.K = fr->intr;
+    a.n = ctx->N;
+    a.eps2 = prm->eps_d * prm->eps_d;
+    a.cos_eps_n = prm->cos_eps_n;
+    a.sw = sqrtf(prm->w_data);
+    a.mode = mode;
+    a.pix = ctx->pix;
+    a.rec0 = mode == PASS_GRAD ? ctx->gpts : ctx->rec0;
+    a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : ctx->rec1;
+    a.part = ctx->k1_part;
+    a.dbg_wpos = ctx->dbg_wpos;
+    a.dbg_wnrm = ctx->dbg_wnrm;
+    a.dbg_pix = (mode == PASS_STEP && ctx->dbg_wpos && ctx->dbg_wnrm) ? ctx->dbg_pix : nullptr;
+    if (mode == PASS_STEP) ed_tm_begin(ctx, ED_KERNEL_POINTS, st);
+    k_points<<<k1_grid(ctx), ED_K1_THREADS, 0, st>>>(a); ed_note_launch();
+    if (mode == PASS_STEP) ed_tm_end(ctx, ED_KERNEL_POINTS, st);
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// assembly: one thread per chunk of <= ED_CHUNK points of one upper block (j, l)
+// role 0: the 60 independent entries of sum c (nb nb^T) (x) (d^ d^T),
+//         d^ = [v - g_j; 1], c = w_s w_t  (every data-term block of J^T J)
+// role 1 (diagonal blocks): J^T r (12) and the pose-node block (6 x 12)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) k_assemble(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
+                                                  const uint32_t *__restrict__ ent, const int *__restrict__ brow,
+                                                  const float4 *__restrict__ g, const float4 *__restrict__ pos,
+                                                  const float *__restrict__ wts, const float4 *__restrict__ rec0,
+                                                  const float4 *__restrict__ rec1, const double *__restrict__ pose,
+                                                  float *__restrict__ part)
+{
+    __shared__ ed_pose_f P;
+    if (threadIdx.x == 0) ed_pose_eval(pose, P);
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    const int4 ch = chunks[c];
+    const int j = brow[ch.x];
+    const float4 gj = __ldg(g + j);
+    if (ch.w == 0) {
+        float M[60];
+#pragma unroll
+        for (int k = 0; k < 60; ++k) M[k] = 0.f;
+        for (int e = ch.y; e < ch.y + ch.z; ++e) {
+            const uint32_t v = __ldg(ent + e);
+            const int i = (int)(v >> 4), sr = (v >> 2) & 3, sc = v & 3;
+            const float4 b = __ldg(rec0 + i);
+            const float4 p = __ldg(pos + i);
+            const float cf = __ldg(wts + 4 * i + sr) * __ldg(wts + 4 * i + sc);
+            const float d0 = p.x - gj.x, d1 = p.y - gj.y, d2 = p.z - gj.z;
+            const float nn[6] = {cf * b.x * b.x, cf * b.x * b.y, cf * b.x * b.z,
+                                 cf * b.y * b.y, cf * b.y * b.z, cf * b.z * b.z};
+            const float dd[10] = {d0 * d0, d0 * d1, d0 * d2, d0, d1 * d1, d1 * d2, d1, d2 * d2, d2, 1.0f};
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+#pragma unroll
+                for (int k = 0; k < 10; ++k) M[10 * a + k] += nn[a] * dd[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 60; ++k) part[(long)k * max_chunks + c] = M[k];
+    } else {
+        float G[12], C[72];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) G[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 72; ++k) C[k] = 0.f;
+        const float *R = P.R;
+        for (int e = ch.y; e < ch.y + ch.z; ++e) {
+            const uint32_t v = __ldg(ent + e);
+            const int i = (int)(v >> 4), sr = (v >> 2) & 3;
+            const float4 b = __ldg(rec0 + i);
+            const float4 jq = __ldg(rec1 + i);
+            const float4 p = __ldg(pos + i);
+            const float ws = __ldg(wts + 4 * i + sr);
+            const float dh[4] = {p.x - gj.x, p.y - gj.y, p.z - gj.z, 1.0f};
+            const float nb[3] = {ws * b.x, ws * b.y, ws * b.z};
+            // d r / d pose: (angles, R nb_s) with nb_s = sqrt(w) R^T n
+            const float jp[6] = {jq.x, jq.y, jq.z, R[0] * b.x + R[1] * b.y + R[2] * b.z,
+                                 R[3] * b.x + R[4] * b.y + R[5] * b.z, R[6] * b.x + R[7] * b.y + R[8] * b.z};
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float av = nb[r] * dh[k];
+                    G[4 * r + k] += b.w * av;
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) C[12 * t + 4 * r + k] += jp[t] * av;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) part[(long)k * max_chunks + c] = G[k];
+#pragma unroll
+        for (int k = 0; k < 72; ++k) part[(long)(12 + k) * max_chunks + c] = C[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalisation: one warp per upper block (j, l), j <= l
+// ---------------------------------------------------------------------------
+
+struct FinArgs {
+    const int *up_list, *brow, *col, *tpos, *row_ptr, *chunk_start, *chunk_cnt, *nbr;
+    const float *part;
+    int max_chunks;
+    int n_upper, kg, mixed;
+    const float4 *g;
+    const float4 *x4;
+    float w_rot, w_reg, lambda, jitter;
+    float *bsr, *grad, *pnode, *minv;
+    double *node_energy;
+    int *status;
+};
+
+__device__ __forceinline__ int sym3(int a, int b)
+{
+    if (a > b) { int t = a; a = b; b = t; }
+    return a == 0 ? b : (a == 1 ? 2 + b : 5);
+}
+__device__ __forceinline__ int sym4(int a, int b)
+{
+    if (a > b) { int t = a; a = b; b = t; }
+    return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
+}
+
+// sum of the chunk partials of one component (two-sum compensated when mixed)
+__device__ __forceinline__ float sum_parts(const float *part, int comp, int max_chunks, int c0, int n, int mixed)
+{
+    const float *p = part + (long)comp * max_chunks + c0;
+    float s = 0.f;
+    if (!mixed) {
+        for (int k = 0; k < n; ++k) s += p[k];
+        return s;
+    }
+    float err = 0.f;
+    for (int k = 0; k < n; ++k) {
+        const float a = p[k];
+        const float t = s + a;
+        const float bp = t - s;
+        err += (s - (t - bp)) + (a - bp);
+        s = t;
+    }
+    return s + err;
+}
+
+#define FIN_WARPS 4
+
+__global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
+{
+    __shared__ float sM[FIN_WARPS][84];
+    __shared__ float sH[FIN_WARPS][144];
+    __shared__ float sX[FIN_WARPS][12];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * FIN_WARPS + wid;
+    if (u >= a.n_upper) return;
+    const int b = a.up_list[u];
+    const int j = a.brow[b], l = a.col[b];
+    const bool diag = j == l;
+    const int c0 = a.chunk_start[b];
+    const int per = diag ? a.chunk_cnt[b] / 2 : a.chunk_cnt[b];
+    float *M = sM[wid], *H = sH[wid], *X = sX[wid];
+    for (int k = lane; k < 60; k += 32) M[k] = sum_parts(a.part, k, a.max_chunks, c0, per, a.mixed);
+    if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
+    __syncwarp();
+    const float4 gj = a.g[j], gl = a.g[l];
+    const float dl[3] = {gj.x - gl.x, gj.y - gl.y, gj.z - gl.z};   // d^_l = d^_j + [g_j - g_l; 0]
+    for (int e = lane; e < 144; e += 32) {
+        const int R = e / 12, Cc = e % 12;
+        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+        const float *Mr = M + 10 * sym3(r, rp);
+        float h = Mr[sym4(c, cp)];
+        if (cp < 3) h += dl[cp] * Mr[sym4(c, 3)];
+        H[e] = h;
+    }
+    __syncwarp();
+    // E_reg: edges j -> l and l -> j (alpha = 1)
+    const float wr = a.w_reg;
+    if (!diag) {
+        if (lane == 0) {
+            bool e_jl = false, e_lj = false;
+            for (int s = 0; s < a.kg; ++s) {
+                e_jl |= a.nbr[j * a.kg + s] == l;
+                e_lj |= a.nbr[l * a.kg + s] == j;
+            }
+            const float hjl[4] = {gl.x - gj.x, gl.y - gj.y, gl.z - gj.z, 1.0f};
+            const float hlj[4] = {gj.x - gl.x, gj.y - gl.y, gj.z - gl.z, 1.0f};
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    if (e_jl) H[(4 * r + c) * 12 + 4 * r + 3] -= wr * hjl[c];
+                    if (e_lj) H[(4 * r + 3) * 12 + 4 * r + c] -= wr * hlj[c];
+                }
+        }
+        __syncwarp();
+        const int tb = a.tpos[b];
+        if (tb < 0) {
+            if (lane == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
+            return;
+        }
+        for (int e = lane; e < 144; e += 32) {
+            const float h = H[e];
+            a.bsr[(long)b * 144 + e] = h;
+            a.bsr[(long)tb * 144 + (e % 12) * 12 + e / 12] = h;
+        }
+        return;
+    }
+    // ---- diagonal block: data gradient and pose-node block from role-1 chunks
+    float *Gx = M + 60;   // 12 floats; the pose-node block goes straight to global
+    for (int k = lane; k < 84; k += 32) {
+        const float v = sum_parts(a.part, k, a.max_chunks, c0 + per, per, a.mixed);
+        if (k < 12) Gx[k] = v;
+        else a.pnode[(long)j * 72 + (k - 12)] = v;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // E_rot: Rot(A_j) on the columns of A_j
+        double erot = 0.0, ereg = 0.0;
+        float A[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[r][c] = X[4 * r + c];
+        const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {1, 2, 2, 0, 1, 2};
+        for (int q = 0; q < 6; ++q) {
+            const int ca = pa[q], cb = pb[q];
+            float rho = A[0][ca] * A[0][cb] + A[1][ca] * A[1][cb] + A[2][ca] * A[2][cb];
+            if (ca == cb) rho -= 1.0f;
+            erot += (double)a.w_rot * rho * rho;
+            float Jq[12];
+            for (int k = 0; k < 12; ++k) Jq[k] = 0.f;
+            for (int r = 0; r < 3; ++r) {
+                Jq[4 * r + ca] += A[r][cb];
+                Jq[4 * r + cb] += A[r][ca];
+            }
+            for (int p = 0; p < 12; ++p) {
+                if (Jq[p] == 0.f) continue;
+                Gx[p] += a.w_rot * rho * Jq[p];
+                for (int q2 = 0; q2 < 12; ++q2) H[p * 12 + q2] += a.w_rot * Jq[p] * Jq[q2];
+            }
+        }
+        // E_reg, out-edges j -> k: residual e = A_j (g_k - g_j) + g_j + t_j - g_k - t_k
+        for (int s = 0; s < a.kg; ++s) {
+            const int k = a.nbr[j * a.kg + s];
+            if (k < 0) continue;
+            const float4 gk = a.g[k];
+            const float hh[4] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z, 1.0f};
+            const float *xk = &a.x4[3 * k].x;
+            for (int r = 0; r < 3; ++r) {
+                const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
+                ereg += (double)wr * e * e;
+                for (int c = 0; c < 4; ++c) {
+                    Gx[4 * r + c] += wr * e * hh[c];
+                    for (int c2 = 0; c2 < 4; ++c2) H[(4 * r + c) * 12 + 4 * r + c2] += wr * hh[c] * hh[c2];
+                }
+            }
+        }
+        // in-edges k -> j: they sit in row j of the pattern
+        for (int t = a.row_ptr[j]; t < a.row_ptr[j + 1]; ++t) {
+            const int k = a.col[t];
+            if (k == j) continue;
+            bool in = false;
+            for (int s = 0; s < a.kg; ++s) in |= a.nbr[k * a.kg + s] == j;
+            if (!in) continue;
+            const float4 gk = a.g[k];
+            const float hh[3] = {gj.x - gk.x, gj.y - gk.y, gj.z - gk.z};
+            const float *xk = &a.x4[3 * k].x;
+            for (int r = 0; r < 3; ++r) {
+                const float e = ed_reg_residual(xk + 4 * r, r, hh, X[4 * r + 3]);
+                Gx[4 * r + 3] -= wr * e;
+                H[(4 * r + 3) * 12 + 4 * r + 3] += wr;
+            }
+        }
+        a.node_energy[2 * j] = erot;
+        a.node_energy[2 * j + 1] = ereg;
+    }
+    __syncwarp();
+    // LM damping on the diagonal, store the block and J^T r
+    if (lane < 12) {
+        H[lane * 13] *= 1.0f + a.lambda;
+        a.grad[12 * j + lane] = Gx[lane];
+    }
+    __syncwarp();
+    for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
+    __syncwarp();
+    // block-Jacobi inverse: Cholesky of H + jitter tr/12 I, then L^-T L^-1
+    float tr = 0.f;
+    for (int k = 0; k < 12; ++k) tr += H[k * 13];
+    __syncwarp();
+    if (lane < 12) H[lane * 13] += a.jitter * tr / 12.0f;
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < 12; ++k) {
+        const float piv = H[k * 13];
+        if (!(piv > 0.f)) ok = false;
+        const float s = ok ? sqrtf(piv) : 1.0f;
+        __syncwarp();
+        if (lane == 0) H[k * 13] = s;
+        if (lane > k && lane < 12) H[lane * 12 + k] /= s;
+        __syncwarp();
+        for (int e = lane; e < 144; e += 32) {
+            const int r = e / 12, c = e % 12;
+            if (r > k && c > k && c <= r) H[e] -= H[r * 12 + k] * H[c * 12 + k];
+        }
+        __syncwarp();
+    }
+    if (!ok) {
+        if (lane == 0) atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
+        return;
+    }
+    // Linv by forward substitution, one column per lane; stored in M[0..143]? use sH upper part
+    float Li[12];
+    if (lane < 12) {
+        for (int r = 0; r < 12; ++r) {
+            float s = (r == lane) ? 1.0f : 0.0f;
+            for (int k = lane; k < r; ++k) s -= H[r * 12 + k] * Li[k];
+            Li[r] = r < lane ? 0.f : s / H[r * 13];
+        }
+    }
+    __syncwarp();
+    // Minv[p][q] = sum_k Linv[k][p] Linv[k][q]; lane p holds column p of Linv
+    __shared__ float sL[FIN_WARPS][144];
+    if (lane < 12)
+        for (int r = 0; r < 12; ++r) sL[wid][r * 12 + lane] = Li[r];
+    __syncwarp();
+    for (int e = lane; e < 144; e += 32) {
+        const int p = e / 12, q = e % 12;
+        float s = 0.f;
+        for (int k = 0; k < 12; ++k) s += sL[wid][k * 12 + p] * sL[wid][k * 12 + q];
+        a.minv[(long)j * 144 + e] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pose finalisation (one CTA): pose block and gradient, priors E_r / E_p,
+// energy totals, pose preconditioner
+// ---------------------------------------------------------------------------
+
+__global__ void k_pose_final(const double *__restrict__ part, int nparts, const double *__restrict__ node_energy,
+                             int m, const double *__restrict__ pose, ed_solver_params prm, float *__restrict__ pose_blk,
+                             float *__restrict__ grad, double *__restrict__ dmisc, int *__restrict__ status,
+                             ed_stats *stats)
+{
+    __shared__ double s[32];
+    __shared__ double ne[2][256];
+    const int t = threadIdx.x;
+    {
+        // component k by warp k % 8 (fixed lane stride and shuffle tree: deterministic)
+        const int lane = t & 31, w = t >> 5;
+        for (int k = w; k < 30; k += 8) {
+            double v = 0.0;
+#pragma unroll 4
+            for (int c = lane; c < nparts; c += 32) v += part[c * ED_K1_PART + k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s[k] = v;
+        }
+    }
+    double er = 0.0, eg = 0.0;
+    for (int j = t; j < m; j += blockDim.x) {
+        er += node_energy[2 * j];
+        eg += node_energy[2 * j + 1];
+    }
+    ne[0][t] = er;
+    ne[1][t] = eg;
+    __syncthreads();
+    if (t == 0) {
+        double Erot = 0.0, Ereg = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            Erot += ne[0][k];
+            Ereg += ne[1][k];
+        }
+        double H[36], gp[6];
+        int k = 2;
+        for (int a = 0; a < 6; ++a)
+            for (int b = a; b < 6; ++b) {
+                H[6 * a + b] = H[6 * b + a] = s[k];
+                ++k;
+            }
+        double Er = 0.0, Ep = 0.0;
+        for (int a = 0; a < 6; ++a) {
+            const double w = a < 3 ? prm.w_r : prm.w_p;
+            const double d = pose[a] - prm.prior[a];
+            if (a < 3) Er += w * d * d;
+            else Ep += w * d * d;
+            H[7 * a] += w;
+            gp[a] = s[23 + a] + w * d;
+        }
+        const double E = s[0] + Erot + Ereg + Er + Ep;
+        if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
+        for (int a = 0; a < 6; ++a) H[7 * a] *= 1.0 + (double)prm.lambda;
+        for (int a = 0; a < 36; ++a) pose_blk[a] = (float)H[a];
+        for (int a = 0; a < 6; ++a) grad[a] = (float)gp[a];
+        // inverse of the pose block (+ jitter) by Cholesky, in double
+        double L[36];
+        double tr = 0.0;
+        for (int a = 0; a < 6; ++a) tr += H[7 * a];
+        for (int a = 0; a < 36; ++a) L[a] = H[a];
+        for (int a = 0; a < 6; ++a) L[7 * a] += (double)prm.jitter * tr / 6.0;
+        bool ok = true;
+        for (int c = 0; c < 6 && ok; ++c) {
+            double d = L[7 * c];
+            for (int p = 0; p < c; ++p) d -= L[6 * c + p] * L[6 * c + p];
+            if (!(d > 0.0)) { ok = false; break; }
+            d = sqrt(d);
+            L[7 * c] = d;
+            for (int r = c + 1; r < 6; ++r) {
+                double v = L[6 * r + c];
+                for (int p = 0; p < c; ++p) v -= L[6 * r + p] * L[6 * c + p];
+                L[6 * r + c] = v / d;
+            }
+        }
+        if (!ok) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
+        else
+            for (int col = 0; col < 6; ++col) {
+                double y[6], xv[6];
+                for (int r = 0; r < 6; ++r) {
+                    double v = r == col ? 1.0 : 0.0;
+                    for (int p = 0; p < r; ++p) v -= L[6 * r + p] * y[p];
+                    y[r] = v / L[7 * r];
+                }
+                for (int r = 5; r >= 0; --r) {
+                    double v = y[r];
+                    for (int p = r + 1; p < 6; ++p) v -= L[6 * p + r] * xv[p];
+                    xv[r] = v / L[7 * r];
+                }
+                for (int r = 0; r < 6; ++r) pose_blk[36 + 6 * r + col] = (float)xv[r];
+            }
+        dmisc[0] = E;
+        dmisc[1] = s[0];
+        dmisc[2] = Erot;
+        dmisc[3] = Ereg;
+        dmisc[4] = Er;
+        dmisc[5] = Ep;
+        dmisc[6] = s[1];
+        if (stats) {
+            stats->energy = E;
+            stats->e_data = s[0];
+            stats->e_rot = Erot;
+            stats->e_reg = Ereg;
+            stats->e_rot_prior = Er;
+            stats->e_pos_prior = Ep;
+            stats->n_valid = (int)s[1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// update x += d (and the FP64 master in mixed precision), pose += d_pose
+// ---------------------------------------------------------------------------
+
+__global__ void k_update(int n, const float *__restrict__ d, float *__restrict__ x, double *__restrict__ xm,
+                         double *__restrict__ pose, const int *__restrict__ status, ed_stats *stats)
+{
+    const int st = *status;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && stats) stats->status = st;
+    if (st != ED_OK) return;
+    if (i < n) {
+        if (xm) {
+            const double v = xm[i] + (double)d[i];
+            xm[i] = v;
+            x[i] = (float)v;
+        } else {
+            x[i] += d[i];
+        }
+    } else if (i < n + 6) {
+        pose[i - n] += (double)d[i];
+    }
+}
+
+static ed_status check_frame(const ed_context *ctx, const ed_frame *fr)
+{
+    if (!fr || !fr->depth || !fr->nmap || fr->intr.width <= 0 || fr->intr.height <= 0 ||
+        fr->intr.width > ctx->lim.max_width || fr->intr.height > ctx->lim.max_height || !(fr->intr.fx > 0.f) ||
+        !(fr->intr.fy > 0.f) || ((uintptr_t)fr->nmap & 15))
+        return ED_ERR_ARG;
+    return ED_OK;
+}
+
+extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x,
+                                double *x_master, double *pose, ed_stats *stats, cudaStream_t st)
+{
+    if (!ctx || !prm || !x || !pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
+    if (!ctx->have_graph) return ED_ERR_STATE;
+    ed_status s = check_frame(ctx, fr);
+    if (s != ED_OK) return s;
+    if (prm->n_pcg < 0 || (prm->precision == ED_PRECISION_MIXED && !x_master) ||
+        (prm->precision != ED_PRECISION_FP32 && prm->precision != ED_PRECISION_MIXED))
+        return ED_ERR_ARG;
+    const int m = ctx->m;
+    ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_STATUS, 0, sizeof(int), st));
+    if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_STEP, st)) != ED_OK) return s;
+    if (ctx->n_chunks > 0) {
+        ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
+        k_assemble<<<ed_div_up(ctx->n_chunks, 128), 128, 0, st>>>(
+            ctx->chunks, ctx->n_chunks, ctx->max_chunks, ctx->ent_val, ctx->brow, (const float4 *)ctx->graph.nodes,
+            (const float4 *)ctx->pos, ctx->graph.weights, ctx->rec0, ctx->rec1, pose, ctx->partials); ed_note_launch();
+        ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
+        ED_LAUNCH_CHECK();
+    }
+    FinArgs fa;
+    fa.up_list = ctx->up_list;
+    fa.brow = ctx->brow;
+    fa.col = ctx->col;
+    fa.tpos = ctx->tpos;
+    fa.row_ptr = ctx->row_ptr;
+    fa.chunk_start = ctx->chunk_start;
+    fa.chunk_cnt = ctx->chunk_cnt;
+    fa.nbr = ctx->graph.nbr;
+    fa.part = ctx->partials;
+    fa.max_chunks = ctx->max_chunks;
+    fa.n_upper = ctx->n_upper;
+    fa.kg = ctx->k_graph;
+    fa.mixed = prm->precision == ED_PRECISION_MIXED;
+    fa.g = (const float4 *)ctx->graph.nodes;
+    fa.x4 = (const float4 *)x;
+    fa.w_rot = prm->w_rot;
+    fa.w_reg = prm->w_reg;
+    fa.lambda = prm->lambda;
+    fa.jitter = prm->jitter;
+    fa.bsr = ctx->bsr;
+    fa.grad = ctx->grad;
+    fa.pnode = ctx->pnode;
+    fa.minv = ctx->minv;
+    fa.node_energy = ctx->node_energy;
+    fa.status = ctx->misc + MI_STATUS;
+    ed_tm_begin(ctx, ED_KERNEL_FINALIZE, st);
+    k_finalize<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
+    ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
+    ED_LAUNCH_CHECK();
+    k_pose_final<<<1, 256, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->node_energy, m, pose, *prm, ctx->pose_blk,
+                                    ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS, stats); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    if ((s = ed_pcg_solve(ctx, prm, stats, st)) != ED_OK) return s;
+    const int n = 12 * m;
+    k_update<<<ed_div_up(n + 6, 256), 256, 0, st>>>(n, ctx->vec, x, prm->precision == ED_PRECISION_MIXED ? x_master : nullptr,
+                                                   pose, ctx->misc + MI_STATUS, stats); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    ctx->have_system = 1;
+    return ED_OK;
+}
+
+// blocks (row-major BSR), pose-node blocks, pose block, J^T r, solution
+extern "C" ed_status ed_export_system(ed_context *ctx, int *row_ptr, int *col, float *blocks, float *pose_node,
+                                      float *pose_block, float *grad, float *delta, cudaStream_t st)
+{
+    if (!ctx) return ED_ERR_ARG;
+    if (!ctx->have_system) return ED_ERR_STATE;
+    const int m = ctx->m, P = 12 * m + 6;
+    if (row_ptr) ED_CUDA_TRY(cudaMemcpyAsync(row_ptr, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToDevice, st));
+    if (col) ED_CUDA_TRY(cudaMemcpyAsync(col, ctx->col, sizeof(int) * ctx->nnzb, cudaMemcpyDeviceToDevice, st));
+    if (blocks)
+        ED_CUDA_TRY(cudaMemcpyAsync(blocks, ctx->bsr, sizeof(float) * 144 * (size_t)ctx->nnzb, cudaMemcpyDeviceToDevice, st));
+    if (pose_node)
+        ED_CUDA_TRY(cudaMemcpyAsync(pose_node, ctx->pnode, sizeof(float) * 72 * (size_t)m, cudaMemcpyDeviceToDevice, st));
+    if (pose_block) ED_CUDA_TRY(cudaMemcpyAsync(pose_block, ctx->pose_blk, sizeof(float) * 36, cudaMemcpyDeviceToDevice, st));
+    if (grad) ED_CUDA_TRY(cudaMemcpyAsync(grad, ctx->grad, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
+    if (delta) ED_CUDA_TRY(cudaMemcpyAsync(delta, ctx->vec, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
+    return ED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// energy of Eq. (3) and its gradient (differentiation of the warp + energy)
+// ---------------------------------------------------------------------------
+
+// rot and reg energies per node (no normal equations)
+__global__ void k_node_energy(int m, int kg, const int *__restrict__ nbr, const float4 *__restrict__ g,
+                              const float4 *__restrict__ x4, float w_rot, float w_reg, double *__restrict__ ne)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const float *X = &x4[3 * j].x;
+    double er = 0.0, eg = 0.0;
+    const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {1, 2, 2, 0, 1, 2};
+    for (int q = 0; q < 6; ++q) {
+        float rho = X[pa[q]] * X[pb[q]] + X[4 + pa[q]] * X[4 + pb[q]] + X[8 + pa[q]] * X[8 + pb[q]];
+        if (pa[q] == pb[q]) rho -= 1.0f;
+        er += (double)w_rot * rho * rho;
+    }
+    const float4 gj = g[j];
+    for (int s = 0; s < kg; ++s) {
+        const int k = nbr[j * kg + s];
+        if (k < 0) continue;
+        const float4 gk = g[k];
+        const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
+        const float *xk = &x4[3 * k].x;
+        for (int r = 0; r < 3; ++r) {
+            const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
+            eg += (double)w_reg * e * e;
+        }
+    }
+    ne[2 * j] = er;
+    ne[2 * j + 1] = eg;
+}
+
+__global__ void k_energy_final(const double *__restrict__ part, int nparts, const double *__restrict__ ne, int m,
+                               const double *__restrict__ pose, ed_solver_params prm, double *__restrict__ out)
+{
+    __shared__ double a[2][256];
+    __shared__ double e0;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        double v = 0.0;
+        for (int c = 0; c < nparts; ++c) v += part[c * ED_K1_PART];
+        e0 = v;
+    }
+    double er = 0.0, eg = 0.0;
+    for (int j = t; j < m; j += blockDim.x) {
+        er += ne[2 * j];
+        eg += ne[2 * j + 1];
+    }
+    a[0][t] = er;
+    a[1][t] = eg;
+    __syncthreads();
+    if (t == 0) {
+        double Erot = 0.0, Ereg = 0.0, Er = 0.0, Ep = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            Erot += a[0][k];
+            Ereg += a[1][k];
+        }
+        for (int q = 0; q < 6; ++q) {
+            const double d = pose[q] - prm.prior[q];
+            if (q < 3) Er += prm.w_r * d * d;
+            else Ep += prm.w_p * d * d;
+        }
+        out[0] = e0 + Erot + Ereg + Er + Ep;
+        out[1] = e0;
+        out[2] = Erot;
+        out[3] = Ereg;
+        out[4] = Er;
+        out[5] = Ep;
+    }
+}
+
+extern "C" ed_status ed_energy(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
+                               const double *pose, double *energy_out, cudaStream_t st)
+{
+    if (!ctx || !prm || !x || !pose || !energy_out || ((uintptr_t)x & 15)) return ED_ERR_ARG;
+    if (!ctx->have_graph) return ED_ERR_STATE;
+    ed_status s = check_frame(ctx, fr);
+    if (s != ED_OK) return s;
+    if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_ENERGY, st)) != ED_OK) return s;
+    k_node_energy<<<ed_div_up(ctx->m, 128), 128, 0, st>>>(ctx->m, ctx->k_graph, ctx->graph.nbr,
+                                                          (const float4 *)ctx->graph.nodes, (const float4 *)x,
+                                                          prm->w_rot, prm->w_reg, ctx->node_energy); ed_note_launch();
+    k_energy_final<<<1, 256, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->node_energy, ctx->m, pose, *prm, energy_out); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    ctx->have_energy = 1;
+    return ED_OK;
+}
+
+// dE/dx_j = 2 [ sum_i r_i w_ij sqrt(w) (R^T n) (x) d^_ij  +  rot and reg terms ],
+// gathered per node over the points of its diagonal block (fixed order)
+__global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__restrict__ nbr,
+                                                    const int *__restrict__ row_ptr, const int *__restrict__ col,
+                                                    const int *__restrict__ diag_pos, const int *__restrict__ ent_start,
+                                                    const int *__restrict__ ent_cnt, const uint32_t *__restrict__ ent,
+                                                    const float4 *__restrict__ g, const float4 *__restrict__ x4,
+                                                    const float4 *__restrict__ pos, const float *__restrict__ wts,
+                                                    const float4 *__restrict__ gp0, float w_rot, float w_reg,
+                                                    float scale, float *__restrict__ grad)
+{
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 4 + wid;
+    if (j >= m) return;
+    const int b = diag_pos[j];
+    const int e0 = ent_start[b], ne = ent_cnt[b];
+    const float4 gj = g[j];
+    float acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+    for (int e = e0 + lane; e < e0 + ne; e += 32) {
+        const uint32_t v = ent[e];
+        const int i = (int)(v >> 4), s = (v >> 2) & 3;
+        const float4 r0 = gp0[i];
+        const float4 p = pos[i];
+        const float c = wts[4 * i + s] * r0.w;
+        const float dh[4] = {p.x - gj.x, p.y - gj.y, p.z - gj.z, 1.0f};
+        const float nb[3] = {r0.x, r0.y, r0.z};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[4 * r + k] += c * nb[r] * dh[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane != 0) return;
+    const float *X = &x4[3 * j].x;
+    // Rot(A_j): d rho / d A[r][a] (columns a, b)
+    const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {1, 2, 2, 0, 1, 2};
+    for (int q = 0; q < 6; ++q) {
+        const int ca = pa[q], cb = pb[q];
+        float rho = X[ca] * X[cb] + X[4 + ca] * X[4 + cb] + X[8 + ca] * X[8 + cb];
+        if (ca == cb) rho -= 1.0f;
+        for (int r = 0; r < 3; ++r) {
+            acc[4 * r + ca] += w_rot * rho * X[4 * r + cb];
+            acc[4 * r + cb] += w_rot * rho * X[4 * r + ca];
+        }
+    }
+    for (int s = 0; s < kg; ++s) {             // out-edges j -> k
+        const int k = nbr[j * kg + s];
+        if (k < 0) continue;
+        const float4 gk = g[k];
+        const float hh[4] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z, 1.0f};
+        const float *xk = &x4[3 * k].x;
+        for (int r = 0; r < 3; ++r) {
+            const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
+            for (int c = 0; c < 4; ++c) acc[4 * r + c] += w_reg * e * hh[c];
+        }
+    }
+    for (int t = row_ptr[j]; t < row_ptr[j + 1]; ++t) {   // in-edges k -> j lie in row j
+        const int k = col[t];
+        bool in = false;
+        for (int s = 0; s < kg; ++s) in |= nbr[k * kg + s] == j;
+        if (!in || k == j) continue;
+        const float4 gk = g[k];
+        const float hh[3] = {gj.x - gk.x, gj.y - gk.y, gj.z - gk.z};
+        const float *xk = &x4[3 * k].x;
+        for (int r = 0; r < 3; ++r) {
+            const float e = ed_reg_residual(xk + 4 * r, r, hh, X[4 * r + 3]);
+            acc[4 * r + 3] -= w_reg * e;
+        }
+    }
+    for (int k = 0; k < 12; ++k) grad[12 * j + k] = 2.0f * scale * acc[k];
+}
+
+__global__ void k_grad_pose(const double *__restrict__ part, int nparts, const double *__restrict__ pose,
+                            ed_solver_params prm, float scale, float *__restrict__ gpose)
+{
+    const int t = threadIdx.x;
+    if (t >= 6) return;
+    double v = 0.0;
+    for (int c = 0; c < nparts; ++c) v += part[c * ED_K1_PART + 23 + t];
+    const double w = t < 3 ? prm.w_r : prm.w_p;
+    v += w * (pose[t] - prm.prior[t]);
+    gpose[t] = (float)(2.0 * scale * v);
+}
+
+extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
+                                    const double *pose, float grad_scale, float *grad_x, float *grad_pose,
+                                    cudaStream_t st)
+{
+    if (!ctx || !prm || !x || !pose || !grad_x || !grad_pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
+    if (!ctx->have_graph || !ctx->have_energy) return ED_ERR_STATE;
+    ed_status s = check_frame(ctx, fr);
+    if (s != ED_OK) return s;
+    if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_GRAD, st)) != ED_OK) return s;
+    k_grad_nodes<<<ed_div_up(ctx->m, 4), 128, 0, st>>>(ctx->m, ctx->k_graph, ctx->graph.nbr, ctx->row_ptr, ctx->col,
+                                                       ctx->diag_pos,
+                                                       ctx->ent_start, ctx->ent_cnt, ctx->ent_val,
+                                                       (const float4 *)ctx->graph.nodes, (const float4 *)x,
+                                                       (const float4 *)ctx->pos, ctx->graph.weights, ctx->gpts,
+                                                       prm->w_rot, prm->w_reg, grad_scale, grad_x); ed_note_launch();
+    k_grad_pose<<<1, 32, 0, st>>>(ctx->k1_part, k1_grid(ctx), pose, *prm, grad_scale, grad_pose); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}

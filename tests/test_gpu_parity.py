@@ -1,0 +1,310 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Integer outputs (nodes, nearest nodes, node graph, block pattern, pixel
+association, registration map) are compared bit for bit on identical float
+inputs; floating-point outputs within the stated tolerances: node
+parameters 1e-4 relative (|dx| <= 1e-4 max(1, |x|)), energy 1e-5 relative.
+Small cases span several tiles and a ragged tail (18,809 points, 64 nodes);
+the 640x480 / 2048-node and 1280x720 / 4096-node cases run the launch
+configuration of the benchmark.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import gpu_common as C
+
+pytestmark = pytest.mark.gpu
+
+SMALL = "tissue_160x120_n64"
+BIG = "tissue_640x480_n2048"
+LARGE = "tissue_1280x720_n4096"
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _E():
+    import paper_1803_02009_b300 as E
+    return E
+
+
+# ----------------------------------------------------------------------------
+# normals, graph
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", [SMALL, BIG])
+def test_normals(name):
+    torch, E = _torch(), _E()
+    s = C.scene(name)
+    ctx = E.Context(max_points=16, max_nodes=16, max_width=s.cfg.W, max_height=s.cfg.H)
+    nm = ctx.compute_normals(torch.from_numpy(s.tgt_depth).cuda(), s.intr, s.cfg.normal_half_width).cpu().numpy()
+    ref = oracle.normals(s.tgt_depth, s.intr, s.cfg.normal_half_width)
+    assert np.array_equal(nm[..., 3], ref[..., 3])
+    assert np.abs(nm[..., :3] - ref[..., :3]).max() < 2e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_given_nodes(mode):
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s, weight_mode=mode)
+    g = G["graph"]
+    assert g.m == 64
+    idx = g.idx_long().cpu().numpy()
+    ref_idx, ref_key = oracle.knn(s.model_pos, s.nodes, 5)
+    assert np.array_equal(idx, ref_idx[:, :4])
+    w = g.weights.cpu().numpy()
+    ref_w = oracle.skin_weights(s.model_pos, s.nodes, ref_idx, 4, mode, s.sigma)
+    assert np.abs(w - ref_w).max() < 2e-6
+    assert np.array_equal(g.nbr[:64].cpu().numpy(), oracle.node_graph(s.nodes, 4))
+
+
+def test_graph_poisson_full_size():
+    s = C.scene(BIG)
+    r = C.radius_for(BIG)
+    G = C.gpu_setup(s, radius=r, max_nodes=2048)
+    g = G["graph"]
+    node_pt, mt = oracle.poisson_nodes(s.model_pos, r, 2048)
+    counts = g.counts.cpu().numpy()
+    assert g.m == 2048 and counts[0] == 2048 and counts[1] == mt
+    nodes = g.nodes[:2048].cpu().numpy()
+    assert np.array_equal(nodes[:, :3], s.model_pos[node_pt, :3])
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(s.N, 20000, replace=False))
+    ref_idx, _ = oracle.knn(s.model_pos, nodes, 5, sel=sel)
+    idx = g.idx_long().cpu().numpy()
+    assert np.array_equal(idx[sel], ref_idx[:, :4])
+    ref_w = oracle.skin_weights(s.model_pos[sel], nodes, ref_idx, 4, 0, r)
+    assert np.abs(g.weights.cpu().numpy()[sel] - ref_w).max() < 2e-6
+    assert np.array_equal(g.nbr[:2048].cpu().numpy(), oracle.node_graph(nodes, 4))
+
+
+# ----------------------------------------------------------------------------
+# one Gauss-Newton step: association, energy, normal equations, solve, update
+# ----------------------------------------------------------------------------
+
+def _one_step(name, seed_x=0, n_pcg=None, lam=0.0, precision=0, radius=None, max_nodes=None, zero_depth=False):
+    torch, E = _torch(), _E()
+    s = C.scene(name)
+    if zero_depth:
+        import dataclasses
+        s = dataclasses.replace(s, tgt_depth=np.zeros_like(s.tgt_depth))
+    G = C.gpu_setup(s, radius=radius, max_nodes=max_nodes)
+    ctx, g = G["ctx"], G["graph"]
+    m = g.m
+    rng = np.random.default_rng(seed_x)
+    x0 = np.zeros((m, 12))
+    x0[:, [0, 5, 10]] = 1.0
+    x0 += rng.normal(0, 1e-3, x0.shape)
+    x0 = x0.astype(np.float32)
+    pose0 = np.asarray(s.pose_prior) + rng.normal(0, 1e-3, 6)
+    x = torch.from_numpy(x0).cuda()
+    xm = torch.from_numpy(x0.astype(np.float64)).cuda()
+    pose = torch.from_numpy(pose0).cuda()
+    wpos = torch.empty((s.N, 4), dtype=torch.float32, device="cuda")
+    wnrm = torch.empty_like(wpos)
+    pix = torch.empty(s.N, dtype=torch.int32, device="cuda")
+    ctx.set_debug(wpos, wnrm, pix)
+    st = E.new_stats()
+    prm = C.solver(s, n_pcg=n_pcg if n_pcg is not None else s.cfg.n_pcg, lam=lam, precision=precision)
+    ctx.gn_step(G["frame"], prm, x, pose, x_master=xm, stats=st)
+    sysd = {k: v.cpu().numpy() for k, v in ctx.export_system().items()}
+    ctx.set_debug(None, None, None)
+    out = dict(s=s, G=G, x0=x0, pose0=pose0, x1=x.cpu().numpy(), pose1=pose.cpu().numpy(), xm1=xm.cpu().numpy(),
+               wpos=wpos.cpu().numpy(), wnrm=wnrm.cpu().numpy(), pix=pix.cpu().numpy(), stats=E.read_stats(st)[0],
+               sys=sysd, prm=prm)
+    P = C.oracle_problem_from_gpu(s, G)
+    out["P"] = P
+    return out
+
+
+def _check_step(o, tol_block=3e-4):
+    s, P = o["s"], o["P"]
+    st = o["stats"]
+    assert st["status"] == 0
+    # association: the oracle's FP32 rule on the GPU's warped floats (bit-exact)
+    ref_pix = oracle.associate_f32(o["wpos"], o["wnrm"], s.tgt_depth, o["G"]["nmap"].cpu().numpy(), s.intr,
+                                   eps_d=o["prm"].eps_d)
+    assert np.array_equal(ref_pix, o["pix"])
+    # warp against the FP64 warp (mm)
+    wp, wn, _ = oracle.warp(P, o["x0"].astype(np.float64), o["pose0"])
+    assert np.abs(wp - o["wpos"][:, :3]).max() < 2e-4
+    # energy terms at the step's input
+    Q = oracle.NormalEq(P, o["x0"].astype(np.float64), o["pose0"], pix_in=o["pix"])
+    assert st["n_valid"] == Q.n_valid
+    assert st["energy"] == pytest.approx(Q.energy, rel=C.TOL_E)
+    for k, t in zip(["e_data", "e_rot", "e_reg", "e_rot_prior", "e_pos_prior"], Q.E):
+        assert st[k] == pytest.approx(t, rel=C.TOL_E, abs=1e-6 * max(1.0, Q.energy)), k
+    # normal equations: pattern bit-exact, blocks within FP32 accumulation error
+    # (the GPU stores H + lambda diag(H), the matrix its PCG solves)
+    if o["prm"].lam:
+        Q.damp(o["prm"].lam)
+    sd = o["sys"]
+    assert np.array_equal(sd["row_ptr"], Q.row_ptr) and np.array_equal(sd["col"], Q.col)
+    scale = np.abs(Q.blk).max()
+    assert np.abs(sd["blocks"] - Q.blk).max() <= tol_block * scale
+    assert np.abs(sd["pose_node"] - Q.C).max() <= tol_block * max(1.0, np.abs(Q.C).max())
+    assert np.abs(sd["pose_block"] - Q.Hpp).max() <= tol_block * np.abs(Q.Hpp).max()
+    assert np.abs(sd["grad"] - Q.g).max() <= tol_block * np.abs(Q.g).max()
+    return Q
+
+
+def _check_update(o, Q):
+    # the oracle's block-Jacobi PCG on its own FP64 system, same iteration count
+    P = o["P"]
+    prm = o["prm"]
+    d, it, stt, _ = Q.pcg(-Q.g, prm.n_pcg, jitter=prm.jitter)
+    m = P.m
+    x_ref = o["x0"].astype(np.float64) + d[:12 * m].reshape(m, 12)
+    pose_ref = o["pose0"] + d[12 * m:]
+    err = np.abs(o["x1"] - x_ref) / np.maximum(1.0, np.abs(x_ref))
+    assert err.max() <= C.TOL_X, err.max()
+    assert np.abs(o["pose1"] - pose_ref).max() <= C.TOL_X
+    return d
+
+
+def test_step_small():
+    o = _one_step(SMALL)
+    Q = _check_step(o)
+    _check_update(o, Q)
+
+
+def test_step_small_lm_damped_and_mixed():
+    o = _one_step(SMALL, seed_x=3, lam=1e-3, precision=1)
+    Q = _check_step(o)
+    _check_update(o, Q)
+    assert np.abs(o["xm1"] - o["x1"]).max() < 1e-6
+
+
+def test_step_no_valid_points():
+    o = _one_step(SMALL, zero_depth=True)
+    assert o["stats"]["n_valid"] == 0 and o["stats"]["e_data"] == 0.0
+    Q = _check_step(o)
+    _check_update(o, Q)
+
+
+def test_step_full_size():
+    r = C.radius_for(BIG)
+    o = _one_step(BIG, radius=r, max_nodes=2048)
+    Q = _check_step(o)
+    _check_update(o, Q)
+
+
+# ----------------------------------------------------------------------------
+# whole solve (small workload): 5 GN x 10 PCG against the oracle trajectory
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_trajectory_small(precision):
+    torch, E = _torch(), _E()
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s)
+    ctx = G["ctx"]
+    m = G["graph"].m
+    x = ctx.identity_x()
+    xm = x.double().clone()
+    pose = torch.tensor(s.pose_prior, dtype=torch.float64, device="cuda")
+    prm = C.solver(s, precision=precision)
+    st = E.new_stats(s.cfg.n_gn)
+    for it in range(s.cfg.n_gn):
+        ctx.gn_step(G["frame"], prm, x, pose, x_master=xm, stats=st[it:it + 1])
+    stats = E.read_stats(st)
+    P = C.oracle_problem_from_gpu(s, G)
+    xr, pr, hist, stt = oracle.gn_solve(P, P.identity_x(), s.pose_prior, s.cfg.n_gn, s.cfg.n_pcg, jitter=prm.jitter)
+    assert stt == 0 and all(t["status"] == 0 for t in stats)
+    E_gpu = np.array([t["energy"] for t in stats])
+    E_ref = hist[:, :5].sum(1)
+    flips = np.array([t["n_valid"] for t in stats]) - hist[:, 5]
+    print("energies", E_gpu, E_ref, "valid-count differences", flips)
+    assert abs(E_gpu[0] - E_ref[0]) <= C.TOL_E * E_ref[0]
+    x_gpu = (xm if precision else x).cpu().numpy()
+    err = np.abs(x_gpu - xr) / np.maximum(1.0, np.abs(xr))
+    print("max rel node-parameter error", err.max(), "pose error", np.abs(pose.cpu().numpy() - pr).max())
+    assert err.max() <= C.TOL_X
+    assert np.abs(pose.cpu().numpy() - pr).max() <= C.TOL_X
+
+
+# ----------------------------------------------------------------------------
+# final warp and fusion
+# ----------------------------------------------------------------------------
+
+def test_warp_and_fuse():
+    torch, E = _torch(), _E()
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s)
+    ctx = G["ctx"]
+    rng = np.random.default_rng(7)
+    x0 = np.zeros((G["graph"].m, 12), np.float32)
+    x0[:, [0, 5, 10]] = 1.0
+    x0[:, [3, 7, 11]] = rng.normal(0, 0.2, (G["graph"].m, 3))
+    x = torch.from_numpy(x0).cuda()
+    pose = torch.tensor(s.pose_true, dtype=torch.float64, device="cuda")
+    wpos, wnrm = ctx.warp(x, pose, G["pos"], G["nrm"])
+    P = C.oracle_problem_from_gpu(s, G)
+    wp, wn, _ = oracle.warp(P, x0.astype(np.float64), s.pose_true)
+    wpos_np, wnrm_np = wpos.cpu().numpy(), wnrm.cpu().numpy()
+    assert np.abs(wpos_np[:, :3] - wp).max() < 2e-4
+    assert np.abs(wnrm_np[:, :3] - wn).max() < 2e-6
+    assert np.array_equal(wpos_np[:, 3], s.model_pos[:, 3])
+    col = torch.from_numpy(s.model_col).cuda()
+    tst = torch.from_numpy(s.model_t).cuda()
+    F = E.FuseParams(frame=1)
+    cap = s.N + s.cfg.W * s.cfg.H
+    reg = torch.empty(s.cfg.W * s.cfg.H, dtype=torch.int32, device="cuda")
+    out = ctx.fuse(G["pos"], G["nrm"], col, tst, wpos, wnrm, G["frame"], F, cap, reg=reg)
+    n_out, status = out["counts"].cpu().numpy()
+    nm = G["nmap"].cpu().numpy()
+    Fo = oracle.FuseParams(frame=1)
+    po, no, co, to, ref_reg = oracle.fuse(s.model_pos, s.model_nrm, s.model_col, s.model_t, wpos_np, wnrm_np,
+                                          s.tgt_depth, nm, s.tgt_color, s.intr, Fo, cap)
+    assert status == 0
+    assert np.array_equal(reg.cpu().numpy(), ref_reg)
+    assert n_out == po.shape[0]
+    assert np.array_equal(out["t"][:n_out].cpu().numpy(), to)
+    assert np.abs(out["pos"][:n_out].cpu().numpy() - po).max() < 1e-4
+    assert np.abs(out["nrm"][:n_out].cpu().numpy() - no).max() < 1e-5
+    assert np.abs(out["col"][:n_out].cpu().numpy() - co).max() < 1e-5
+    # capacity overflow is reported, output truncated
+    out2 = ctx.fuse(G["pos"], G["nrm"], col, tst, wpos, wnrm, G["frame"], F, 1000)
+    n2, st2 = out2["counts"].cpu().numpy()
+    assert n2 == 1000 and st2 == 3
+
+
+# ----------------------------------------------------------------------------
+# differentiation: autograd over the warp + energy
+# ----------------------------------------------------------------------------
+
+def test_energy_and_gradient():
+    torch, E = _torch(), _E()
+    o = _one_step(SMALL, seed_x=5)
+    G, s, P = o["G"], o["s"], o["P"]
+    ctx = G["ctx"]
+    x = torch.from_numpy(o["x0"]).cuda().requires_grad_(True)
+    pose = torch.from_numpy(o["pose0"]).cuda().requires_grad_(True)
+    e = E.EDEnergy.apply(x, pose, ctx, G["frame"], o["prm"])
+    e.backward()
+    E_ref, terms, nv = oracle.energy(P, o["x0"].astype(np.float64), o["pose0"], pix_in=o["pix"])
+    assert float(e.detach()) == pytest.approx(E_ref, rel=C.TOL_E)
+    g_ref = oracle.gradient(P, o["x0"].astype(np.float64), o["pose0"], o["pix"])
+    m = P.m
+    gx = x.grad.cpu().numpy().ravel()
+    gp = pose.grad.cpu().numpy()
+    sc = np.abs(g_ref).max()
+    assert np.abs(gx - g_ref[:12 * m]).max() <= 3e-4 * sc
+    assert np.abs(gp - g_ref[12 * m:]).max() <= 3e-4 * max(sc, 1.0)
+    # against the assembled J^T r of the step (independent kernels): dE/dx = 2 J^T r
+    assert np.abs(gx - 2 * o["sys"]["grad"][:12 * m]).max() <= 3e-4 * sc
+
+
+# ----------------------------------------------------------------------------
+# largest workload: graph + one step at 1280x720 / 4096 nodes
+# ----------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_step_large():
+    r = C.radius_for(LARGE)
+    o = _one_step(LARGE, radius=r, max_nodes=4096)
+    Q = _check_step(o)
+    _check_update(o, Q)
