@@ -280,6 +280,34 @@ ed_status ed_energy_grad(ed_context *ctx, const ed_frame *frame, const ed_solver
                          const float *x, const double *pose, float grad_scale, float *grad_x, float *grad_pose,
                          cudaStream_t stream);
 
+/*
+ * The energy of ed_energy for callers that cannot allocate device memory
+ * (host frameworks that own every device allocation and hand a plugin only
+ * its buffers, code running during CUDA stream capture, real-time loops that
+ * forbid allocation after start-up).  The paper has no counterpart: this is a
+ * deployment variant of ed_energy's reduction.
+ * It needs no context and no workspace: the caller passes the model (pos,
+ * nrm [n][4]), its skinning (idx [n][4], weights [n][4]), the nodes [m][4],
+ * the node graph nbr [m][k_graph], the frame, the parameters, x [m][12] and
+ * the pose, and receives energy_out (device double[6]: total, data, rot, reg,
+ * rot prior, pos prior), as from ed_energy.  The only scratch, the partial
+ * sums of the reduction (133,120 bytes), is a fixed array in device global
+ * memory inside the library, held by every GPU that loads it until the
+ * process exits; no allocation routine is called.
+ * Limits: n_points <= 2,097,152 and m <= 32,768; larger sizes return
+ * ED_ERR_CAPACITY (with a message on stderr) before any launch.
+ * The first call on a device looks up the device address of that array
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call writes every scratch slot it reads,
+ * so stale contents never matter, but all calls share the one array: calls
+ * that overlap on the GPU (different streams, or different host threads on
+ * one device) race and must be serialised by the caller.
+ */
+ed_status ed_energy_noalloc(const float *pos, const float *nrm, const uint16_t *idx, const float *weights,
+                            int n_points, const float *nodes, const int *nbr, int m, int k_graph,
+                            const ed_frame *frame, const ed_solver_params *params, const float *x,
+                            const double *pose, double *energy_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
