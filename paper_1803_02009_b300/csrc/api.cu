@@ -39,7 +39,7 @@ size_t carve(ed_context *c, char *base)
     const size_t nnzb = M * (size_t)L.max_pairs_per_node;
     const size_t nent = 10 * N;
     const size_t tiles = (nent + 1023) / 1024 + 1;
-    const size_t chunks = (16 * N) / ED_CHUNK + nnzb + M + 16;
+    const size_t chunks = (16 * N) / ED_CHUNK + nnzb + M + 64;
     const size_t P = 12 * M + 6;
     const size_t big = (N > WH ? N : WH);
     size_t scan_len = big > 256 * tiles ? big : 256 * tiles;
@@ -74,7 +74,14 @@ size_t carve(ed_context *c, char *base)
     c->chunk_cnt = k.take<int>(nnzb);
     c->chunk_start = k.take<int>(nnzb + 1);
     c->chunks = k.take<int4>(chunks);
+    c->chunk_cnt1 = k.take<int>(nnzb);
+    c->chunk_start1 = k.take<int>(nnzb + 1);
     c->max_chunks = (int)chunks;
+    {
+        const size_t slots = ((chunks + 31) / 32) * 32 * (size_t)ED_CHUNK;
+        c->ent_geo = k.take<float4>(slots);
+        c->ent_pt = k.take<int>(slots);
+    }
     c->partials = k.take<float>((size_t)ED_PART_STRIDE * chunks);
     c->bsr = k.take<float>(nnzb * 144);
     c->grad = k.take<float>(P);
@@ -90,6 +97,7 @@ size_t carve(ed_context *c, char *base)
     c->vec_stride = (P + 63) / 64 * 64;
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
+    c->pcg_rows = k.take<int>(ED_MAX_PCG_GRID + 1);
     c->zbuf = k.take<unsigned long long>(WH);
     c->regpix = k.take<int>(WH);
     c->fused_pix = k.take<int>(N);

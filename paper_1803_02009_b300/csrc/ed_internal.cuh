@@ -34,7 +34,8 @@ enum {
     MI_PHASE_BASE = 24,  // running node count during sampling
     MI_BAR = 32,         // 32 count, 33 generation (grid barrier)
     MI_FUSE = 40,        // 40 kept, 41 lifted
-    MI_COUNT = 64
+    MI_PHASES = 64,      // 64..90 phase counts, 96..123 starts, 128..154 fill counters
+    MI_COUNT = 192
 };
 enum { MF_CELL = 0, MF_INV = 1, MF_KCELL = 2, MF_KINV = 3, MF_R2 = 4, MF_BBOX = 8, MF_COUNT = 16 };
 
@@ -77,8 +78,14 @@ struct ed_context {
     int *ent_start;          // [max_nnzb + 1]
     int *chunk_cnt;          // [max_nnzb]
     int *chunk_start;        // [max_nnzb + 1]
-    int4 *chunks;            // [max_chunks] (block, begin, count, role)
+    int4 *chunks;            // [max_chunks] (block, begin, count, role); role-0 chunks first
+    int *chunk_cnt1;         // [max_nnzb] role-1 chunks of every diagonal block
+    int *chunk_start1;       // [max_nnzb + 1]
     int max_chunks;
+    int n_chunks0;           // role-0 chunks
+    int chunk_base1;         // first role-1 chunk (n_chunks0 rounded up to 32: warp-aligned slots)
+    float4 *ent_geo;         // [chunk slots] (v - g_j, w_s w_t) or (v - g_j, w_s), warp-interleaved
+    int *ent_pt;             // [chunk slots] point index, same layout
     float *partials;         // [ED_PART_STRIDE][max_chunks]
     // normal equations
     float *bsr;              // [max_nnzb][144]
@@ -121,8 +128,11 @@ struct ed_context {
     int n_chunks;
     int have_system;
     int have_energy;
-    int pcg_grid;
-    int pcg_threads;
+    int pcg_grid;            // CTAs of the PCG launch (one per SM)
+    int *pcg_rows;           // [ED_MAX_PCG_GRID + 1] first node row of every CTA (device)
+    int pcg_cache;           // blocks per CTA kept in shared memory
+    size_t pcg_smem;         // dynamic shared memory of the PCG launch
+    int pcg_max_rows, pcg_max_blk;
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
@@ -244,9 +254,9 @@ struct ed_pose_f {
     float T[3];
 };
 
-__device__ __forceinline__ void ed_mat3_mul_d(const double *a, const double *b, double *c)
+__device__ __forceinline__ void ed_mat3_mul_f(const float *a, const float *b, float *c)
 {
-    double t[9];
+    float t[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -255,27 +265,25 @@ __device__ __forceinline__ void ed_mat3_mul_d(const double *a, const double *b, 
     for (int i = 0; i < 9; ++i) c[i] = t[i];
 }
 
-// R = Rz(gamma) Ry(beta) Rx(alpha) and its angle derivatives, in double, rounded to float
+// R = Rz(gamma) Ry(beta) Rx(alpha) and its angle derivatives in FP32 (one
+// thread per CTA; the results are FP32 matrices in any case)
 __device__ inline void ed_pose_eval(const double *pose, ed_pose_f &P)
 {
-    double ca = cos(pose[0]), sa = sin(pose[0]);
-    double cb = cos(pose[1]), sb = sin(pose[1]);
-    double cg = cos(pose[2]), sg = sin(pose[2]);
-    double Rx[9] = {1, 0, 0, 0, ca, -sa, 0, sa, ca}, dRx[9] = {0, 0, 0, 0, -sa, -ca, 0, ca, -sa};
-    double Ry[9] = {cb, 0, sb, 0, 1, 0, -sb, 0, cb}, dRy[9] = {-sb, 0, cb, 0, 0, 0, -cb, 0, -sb};
-    double Rz[9] = {cg, -sg, 0, sg, cg, 0, 0, 0, 1}, dRz[9] = {-sg, -cg, 0, cg, -sg, 0, 0, 0, 0};
-    double t[9], R[9], d[9];
-    ed_mat3_mul_d(Rz, Ry, t);
-    ed_mat3_mul_d(t, Rx, R);
-    for (int i = 0; i < 9; ++i) P.R[i] = (float)R[i];
-    ed_mat3_mul_d(t, dRx, d);
-    for (int i = 0; i < 9; ++i) P.dR[i] = (float)d[i];
-    ed_mat3_mul_d(Rz, dRy, t);
-    ed_mat3_mul_d(t, Rx, d);
-    for (int i = 0; i < 9; ++i) P.dR[9 + i] = (float)d[i];
-    ed_mat3_mul_d(dRz, Ry, t);
-    ed_mat3_mul_d(t, Rx, d);
-    for (int i = 0; i < 9; ++i) P.dR[18 + i] = (float)d[i];
+    float sa, ca, sb, cb, sg, cg;
+    sincosf((float)pose[0], &sa, &ca);
+    sincosf((float)pose[1], &sb, &cb);
+    sincosf((float)pose[2], &sg, &cg);
+    const float Rx[9] = {1, 0, 0, 0, ca, -sa, 0, sa, ca}, dRx[9] = {0, 0, 0, 0, -sa, -ca, 0, ca, -sa};
+    const float Ry[9] = {cb, 0, sb, 0, 1, 0, -sb, 0, cb}, dRy[9] = {-sb, 0, cb, 0, 0, 0, -cb, 0, -sb};
+    const float Rz[9] = {cg, -sg, 0, sg, cg, 0, 0, 0, 1}, dRz[9] = {-sg, -cg, 0, cg, -sg, 0, 0, 0, 0};
+    float t[9];
+    ed_mat3_mul_f(Rz, Ry, t);
+    ed_mat3_mul_f(t, Rx, P.R);
+    ed_mat3_mul_f(t, dRx, P.dR);
+    ed_mat3_mul_f(Rz, dRy, t);
+    ed_mat3_mul_f(t, Rx, P.dR + 9);
+    ed_mat3_mul_f(dRz, Ry, t);
+    ed_mat3_mul_f(t, Rx, P.dR + 18);
     for (int i = 0; i < 3; ++i) P.T[i] = (float)pose[3 + i];
 }
 
@@ -361,5 +369,6 @@ __device__ __forceinline__ int ed_associate(const ed_warped &W, const float *__r
 ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st);
 ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st);
+ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st);
 ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
                         const double *pose, int write_records, cudaStream_t st);

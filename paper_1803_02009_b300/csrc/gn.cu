@@ -157,78 +157,134 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
 // role 0: the 60 independent entries of sum c (nb nb^T) (x) (d^ d^T),
 //         d^ = [v - g_j; 1], c = w_s w_t  (every data-term block of J^T J)
 // role 1 (diagonal blocks): J^T r (12) and the pose-node block (6 x 12)
+// Per entry the geometry (d, c) is read from warp-interleaved slots written at
+// graph build (coalesced); only the residual record of the point is gathered.
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(128) k_assemble(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
-                                                  const uint32_t *__restrict__ ent, const int *__restrict__ brow,
-                                                  const float4 *__restrict__ g, const float4 *__restrict__ pos,
-                                                  const float *__restrict__ wts, const float4 *__restrict__ rec0,
-                                                  const float4 *__restrict__ rec1, const double *__restrict__ pose,
-                                                  float *__restrict__ part)
+// role 0, one thread per (chunk, half): half h accumulates the 30 moments of
+// nn[3h .. 3h+2] x dd[0 .. 9]; lanes of a warp take 32 consecutive chunks
+__global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
+                                                   const float4 *__restrict__ geo, const int *__restrict__ pt,
+                                                   const float4 *__restrict__ rec0, float *__restrict__ part)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = (id >> 5) & 1;
+    const int c = (id >> 6) * 32 + (id & 31);
+    if (c >= nchunks) return;
+    const int n = chunks[c].z;
+    const long base = (long)(c >> 5) * (32 * ED_CHUNK) + (c & 31);
+    float M[30];
+#pragma unroll
+    for (int k = 0; k < 30; ++k) M[k] = 0.f;
+    // entries in batches of 4: the 4 slot loads, then the 4 record gathers, are
+    // in flight together
+    for (int e0 = 0; e0 < n; e0 += 4) {
+        float4 gd[4], b[4];
+        int ip[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = e0 + u < n;
+            gd[u] = ok ? __ldg(geo + base + 32L * (e0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ip[u] = ok ? __ldg(pt + base + 32L * (e0 + u)) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = ip[u] >= 0 ? __ldg(rec0 + ip[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float cf = gd[u].w;   // 0 for the padding of the last batch
+            const float d0 = gd[u].x, d1 = gd[u].y, d2 = gd[u].z;
+            float nn[3];
+            if (h == 0) {
+                nn[0] = cf * b[u].x * b[u].x;
+                nn[1] = cf * b[u].x * b[u].y;
+                nn[2] = cf * b[u].x * b[u].z;
+            } else {
+                nn[0] = cf * b[u].y * b[u].y;
+                nn[1] = cf * b[u].y * b[u].z;
+                nn[2] = cf * b[u].z * b[u].z;
+            }
+            const float dd[10] = {d0 * d0, d0 * d1, d0 * d2, d0, d1 * d1, d1 * d2, d1, d2 * d2, d2, 1.0f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int k = 0; k < 10; ++k) M[10 * a + k] += nn[a] * dd[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 30; ++k) part[(long)(30 * h + k) * max_chunks + c] = M[k];
+}
+
+// role 1 (diagonal blocks), one thread per (chunk, third): third 0 accumulates
+// J^T r (12) and pose-node rows 0-1, thirds 1 and 2 rows 2-3 and 4-5 (24 each)
+__global__ void __launch_bounds__(128) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
+                                                   int max_chunks, const float4 *__restrict__ geo,
+                                                   const int *__restrict__ pt, const float4 *__restrict__ rec0,
+                                                   const float4 *__restrict__ rec1, const double *__restrict__ pose,
+                                                   float *__restrict__ part)
 {
     __shared__ ed_pose_f P;
     if (threadIdx.x == 0) ed_pose_eval(pose, P);
     __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nchunks) return;
-    const int4 ch = chunks[c];
-    const int j = brow[ch.x];
-    const float4 gj = __ldg(g + j);
-    if (ch.w == 0) {
-        float M[60];
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = (id >> 5) % 3;
+    const int c = c_begin + (id / 96) * 32 + (id & 31);
+    if (c >= c_begin + nchunks) return;
+    const int n = chunks[c].z;
+    const long base = (long)(c >> 5) * (32 * ED_CHUNK) + (c & 31);
+    const float *R = P.R;
+    float acc[36];
 #pragma unroll
-        for (int k = 0; k < 60; ++k) M[k] = 0.f;
-        for (int e = ch.y; e < ch.y + ch.z; ++e) {
-            const uint32_t v = __ldg(ent + e);
-            const int i = (int)(v >> 4), sr = (v >> 2) & 3, sc = v & 3;
-            const float4 b = __ldg(rec0 + i);
-            const float4 p = __ldg(pos + i);
-            const float cf = __ldg(wts + 4 * i + sr) * __ldg(wts + 4 * i + sc);
-            const float d0 = p.x - gj.x, d1 = p.y - gj.y, d2 = p.z - gj.z;
-            const float nn[6] = {cf * b.x * b.x, cf * b.x * b.y, cf * b.x * b.z,
-                                 cf * b.y * b.y, cf * b.y * b.z, cf * b.z * b.z};
-            const float dd[10] = {d0 * d0, d0 * d1, d0 * d2, d0, d1 * d1, d1 * d2, d1, d2 * d2, d2, 1.0f};
+    for (int k = 0; k < 36; ++k) acc[k] = 0.f;
+    for (int e0 = 0; e0 < n; e0 += 4) {
+        float4 gd[4], bb[4], qq[4];
+        int ip[4];
 #pragma unroll
-            for (int a = 0; a < 6; ++a)
-#pragma unroll
-                for (int k = 0; k < 10; ++k) M[10 * a + k] += nn[a] * dd[k];
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = e0 + u < n;
+            gd[u] = ok ? __ldg(geo + base + 32L * (e0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ip[u] = ok ? __ldg(pt + base + 32L * (e0 + u)) : -1;
         }
 #pragma unroll
-        for (int k = 0; k < 60; ++k) part[(long)k * max_chunks + c] = M[k];
-    } else {
-        float G[12], C[72];
+        for (int u = 0; u < 4; ++u) {
+            bb[u] = ip[u] >= 0 ? __ldg(rec0 + ip[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            qq[u] = ip[u] >= 0 ? __ldg(rec1 + ip[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-        for (int k = 0; k < 12; ++k) G[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 72; ++k) C[k] = 0.f;
-        const float *R = P.R;
-        for (int e = ch.y; e < ch.y + ch.z; ++e) {
-            const uint32_t v = __ldg(ent + e);
-            const int i = (int)(v >> 4), sr = (v >> 2) & 3;
-            const float4 b = __ldg(rec0 + i);
-            const float4 jq = __ldg(rec1 + i);
-            const float4 p = __ldg(pos + i);
-            const float ws = __ldg(wts + 4 * i + sr);
-            const float dh[4] = {p.x - gj.x, p.y - gj.y, p.z - gj.z, 1.0f};
+        for (int u = 0; u < 4; ++u) {
+            const float4 b = bb[u], jq = qq[u];
+            const float ws = gd[u].w;   // 0 for the padding of the last batch
+            const float dh[4] = {gd[u].x, gd[u].y, gd[u].z, 1.0f};
             const float nb[3] = {ws * b.x, ws * b.y, ws * b.z};
             // d r / d pose: (angles, R nb_s) with nb_s = sqrt(w) R^T n
-            const float jp[6] = {jq.x, jq.y, jq.z, R[0] * b.x + R[1] * b.y + R[2] * b.z,
-                                 R[3] * b.x + R[4] * b.y + R[5] * b.z, R[6] * b.x + R[7] * b.y + R[8] * b.z};
+            float jp[2];
+            if (h == 0) {
+                jp[0] = jq.x;
+                jp[1] = jq.y;
+            } else if (h == 1) {
+                jp[0] = jq.z;
+                jp[1] = R[0] * b.x + R[1] * b.y + R[2] * b.z;
+            } else {
+                jp[0] = R[3] * b.x + R[4] * b.y + R[5] * b.z;
+                jp[1] = R[6] * b.x + R[7] * b.y + R[8] * b.z;
+            }
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float av = nb[r] * dh[k];
-                    G[4 * r + k] += b.w * av;
-#pragma unroll
-                    for (int t = 0; t < 6; ++t) C[12 * t + 4 * r + k] += jp[t] * av;
+                    if (h == 0) acc[24 + 4 * r + k] += b.w * av;
+                    acc[4 * r + k] += jp[0] * av;
+                    acc[12 + 4 * r + k] += jp[1] * av;
                 }
         }
-#pragma unroll
-        for (int k = 0; k < 12; ++k) part[(long)k * max_chunks + c] = G[k];
-#pragma unroll
-        for (int k = 0; k < 72; ++k) part[(long)(12 + k) * max_chunks + c] = C[k];
     }
+    // component order of the role-1 partials: 0..11 J^T r, 12 + 12 t + p pose-node (t, p)
+    if (h == 0) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) part[(long)k * max_chunks + c] = acc[24 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) part[(long)(12 + 24 * h + k) * max_chunks + c] = acc[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -236,9 +292,9 @@ __global__ void __launch_bounds__(128) k_assemble(const int4 *__restrict__ chunk
 // ---------------------------------------------------------------------------
 
 struct FinArgs {
-    const int *up_list, *brow, *col, *tpos, *row_ptr, *chunk_start, *chunk_cnt, *nbr;
+    const int *up_list, *brow, *col, *tpos, *row_ptr, *chunk_start, *chunk_start1, *ent_cnt, *nbr;
     const float *part;
-    int max_chunks;
+    int max_chunks, n_chunks0;
     int n_upper, kg, mixed;
     const float4 *g;
     const float4 *x4;
@@ -265,6 +321,7 @@ __device__ __forceinline__ float sum_parts(const float *part, int comp, int max_
     const float *p = part + (long)comp * max_chunks + c0;
     float s = 0.f;
     if (!mixed) {
+#pragma unroll 4
         for (int k = 0; k < n; ++k) s += p[k];
         return s;
     }
@@ -279,6 +336,26 @@ __device__ __forceinline__ float sum_parts(const float *part, int comp, int max_
     return s + err;
 }
 
+// derivative of the Rot(A) residual q (column pair ca, cb) with respect to
+// the parameter 4 r + c of [A | t]
+__device__ __forceinline__ float rot_jac(const float *X, int q, int r, int c)
+{
+    const int ca = q < 3 ? (q < 2 ? 0 : 1) : q - 3;
+    const int cb = q < 3 ? (q == 0 ? 1 : 2) : q - 3;
+    float v = 0.f;
+    if (c == ca) v += X[4 * r + cb];
+    if (c == cb) v += X[4 * r + ca];
+    return v;
+}
+
+__device__ __forceinline__ float rot_res(const float *X, int q)
+{
+    const int ca = q < 3 ? (q < 2 ? 0 : 1) : q - 3;
+    const int cb = q < 3 ? (q == 0 ? 1 : 2) : q - 3;
+    float d = X[ca] * X[cb] + X[4 + ca] * X[4 + cb] + X[8 + ca] * X[8 + cb];
+    return ca == cb ? d - 1.0f : d;
+}
+
 #define FIN_WARPS 4
 
 __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
@@ -286,131 +363,153 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __shared__ float sM[FIN_WARPS][84];
     __shared__ float sH[FIN_WARPS][144];
     __shared__ float sX[FIN_WARPS][12];
+    __shared__ float sS[FIN_WARPS][16];
+    __shared__ float sL[FIN_WARPS][144];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int u = blockIdx.x * FIN_WARPS + wid;
     if (u >= a.n_upper) return;
     const int b = a.up_list[u];
     const int j = a.brow[b], l = a.col[b];
     const bool diag = j == l;
+    const int nch = (a.ent_cnt[b] + ED_CHUNK - 1) / ED_CHUNK;
     const int c0 = a.chunk_start[b];
-    const int per = diag ? a.chunk_cnt[b] / 2 : a.chunk_cnt[b];
-    float *M = sM[wid], *H = sH[wid], *X = sX[wid];
-    for (int k = lane; k < 60; k += 32) M[k] = sum_parts(a.part, k, a.max_chunks, c0, per, a.mixed);
+    float *M = sM[wid], *H = sH[wid], *X = sX[wid], *S = sS[wid];
+    for (int k = lane; k < 60; k += 32) M[k] = sum_parts(a.part, k, a.max_chunks, c0, nch, a.mixed);
     if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
     __syncwarp();
     const float4 gj = a.g[j], gl = a.g[l];
     const float dl[3] = {gj.x - gl.x, gj.y - gl.y, gj.z - gl.z};   // d^_l = d^_j + [g_j - g_l; 0]
-    for (int e = lane; e < 144; e += 32) {
-        const int R = e / 12, Cc = e % 12;
-        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
-        const float *Mr = M + 10 * sym3(r, rp);
-        float h = Mr[sym4(c, cp)];
-        if (cp < 3) h += dl[cp] * Mr[sym4(c, 3)];
-        H[e] = h;
-    }
-    __syncwarp();
-    // E_reg: edges j -> l and l -> j (alpha = 1)
     const float wr = a.w_reg;
     if (!diag) {
-        if (lane == 0) {
-            bool e_jl = false, e_lj = false;
-            for (int s = 0; s < a.kg; ++s) {
-                e_jl |= a.nbr[j * a.kg + s] == l;
-                e_lj |= a.nbr[l * a.kg + s] == j;
-            }
-            const float hjl[4] = {gl.x - gj.x, gl.y - gj.y, gl.z - gj.z, 1.0f};
-            const float hlj[4] = {gj.x - gl.x, gj.y - gl.y, gj.z - gl.z, 1.0f};
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 4; ++c) {
-                    if (e_jl) H[(4 * r + c) * 12 + 4 * r + 3] -= wr * hjl[c];
-                    if (e_lj) H[(4 * r + 3) * 12 + 4 * r + c] -= wr * hlj[c];
-                }
+        bool e_jl = false, e_lj = false;
+        for (int s = 0; s < a.kg; ++s) {
+            e_jl |= a.nbr[j * a.kg + s] == l;
+            e_lj |= a.nbr[l * a.kg + s] == j;
         }
-        __syncwarp();
+        const float hjl[4] = {gl.x - gj.x, gl.y - gj.y, gl.z - gj.z, 1.0f};
         const int tb = a.tpos[b];
         if (tb < 0) {
             if (lane == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
             return;
         }
         for (int e = lane; e < 144; e += 32) {
-            const float h = H[e];
+            const int R = e / 12, Cc = e % 12;
+            const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+            const float *Mr = M + 10 * sym3(r, rp);
+            float h = Mr[sym4(c, cp)];
+            if (cp < 3) h += dl[cp] * Mr[sym4(c, 3)];
+            if (r == rp) {   // E_reg, edges j -> l (d e / d t_l = -I) and l -> j (d e / d t_j = -I)
+                if (e_jl && cp == 3) h -= wr * hjl[c];
+                if (e_lj && c == 3) h -= wr * (cp < 3 ? -hjl[cp] : 1.0f);
+            }
             a.bsr[(long)b * 144 + e] = h;
-            a.bsr[(long)tb * 144 + (e % 12) * 12 + e / 12] = h;
+            a.bsr[(long)tb * 144 + Cc * 12 + R] = h;
         }
         return;
     }
-    // ---- diagonal block: data gradient and pose-node block from role-1 chunks
-    float *Gx = M + 60;   // 12 floats; the pose-node block goes straight to global
+    // ---- diagonal block ----
+    // data gradient and pose-node block from the role-1 chunks
+    const int c1 = a.n_chunks0 + a.chunk_start1[b];
+    float *Gx = M + 60;
     for (int k = lane; k < 84; k += 32) {
-        const float v = sum_parts(a.part, k, a.max_chunks, c0 + per, per, a.mixed);
+        const float v = sum_parts(a.part, k, a.max_chunks, c1, nch, a.mixed);
         if (k < 12) Gx[k] = v;
         else a.pnode[(long)j * 72 + (k - 12)] = v;
     }
-    __syncwarp();
-    if (lane == 0) {
-        // E_rot: Rot(A_j) on the columns of A_j
-        double erot = 0.0, ereg = 0.0;
-        float A[3][3];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) A[r][c] = X[4 * r + c];
-        const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {1, 2, 2, 0, 1, 2};
-        for (int q = 0; q < 6; ++q) {
-            const int ca = pa[q], cb = pb[q];
-            float rho = A[0][ca] * A[0][cb] + A[1][ca] * A[1][cb] + A[2][ca] * A[2][cb];
-            if (ca == cb) rho -= 1.0f;
-            erot += (double)a.w_rot * rho * rho;
-            float Jq[12];
-            for (int k = 0; k < 12; ++k) Jq[k] = 0.f;
-            for (int r = 0; r < 3; ++r) {
-                Jq[4 * r + ca] += A[r][cb];
-                Jq[4 * r + cb] += A[r][ca];
-            }
-            for (int p = 0; p < 12; ++p) {
-                if (Jq[p] == 0.f) continue;
-                Gx[p] += a.w_rot * rho * Jq[p];
-                for (int q2 = 0; q2 < 12; ++q2) H[p * 12 + q2] += a.w_rot * Jq[p] * Jq[q2];
-            }
+    // S = sum over out-edges j -> k of h h^T, h = [g_k - g_j; 1]
+    if (lane < 16) {
+        const int c = lane >> 2, cp = lane & 3;
+        float v = 0.f;
+        for (int s = 0; s < a.kg; ++s) {
+            const int k = a.nbr[j * a.kg + s];
+            if (k < 0) continue;
+            const float4 gk = a.g[k];
+            const float h[4] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z, 1.0f};
+            v += h[c] * h[cp];
         }
-        // E_reg, out-edges j -> k: residual e = A_j (g_k - g_j) + g_j + t_j - g_k - t_k
+        S[lane] = v;
+    }
+    // in-edges k -> j (they lie in row j): count and summed residuals
+    float nin = 0.f, ein[3] = {0.f, 0.f, 0.f};
+    for (int t = a.row_ptr[j] + lane; t < a.row_ptr[j + 1]; t += 32) {
+        const int k = a.col[t];
+        if (k == j) continue;
+        bool in = false;
+        for (int s = 0; s < a.kg; ++s) in |= a.nbr[k * a.kg + s] == j;
+        if (!in) continue;
+        const float4 gk = a.g[k];
+        const float hh[3] = {gj.x - gk.x, gj.y - gk.y, gj.z - gk.z};
+        const float *xk = &a.x4[3 * k].x;
+        nin += 1.f;
+        for (int r = 0; r < 3; ++r) ein[r] += ed_reg_residual(xk + 4 * r, r, hh, X[4 * r + 3]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nin += __shfl_xor_sync(0xffffffffu, nin, o);
+        ein[0] += __shfl_xor_sync(0xffffffffu, ein[0], o);
+        ein[1] += __shfl_xor_sync(0xffffffffu, ein[1], o);
+        ein[2] += __shfl_xor_sync(0xffffffffu, ein[2], o);
+    }
+    __syncwarp();
+    // the 144 entries: data moments + E_rot + E_reg (out-edges S, in-edges on t)
+    for (int e = lane; e < 144; e += 32) {
+        const int R = e / 12, Cc = e % 12;
+        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+        float h = M[10 * sym3(r, rp) + sym4(c, cp)];
+        if (c < 3 && cp < 3) {
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v += rot_jac(X, q, r, c) * rot_jac(X, q, rp, cp);
+            h += a.w_rot * v;
+        }
+        if (r == rp) {
+            h += wr * S[4 * c + cp];
+            if (c == 3 && cp == 3) h += wr * nin;
+        }
+        if (R == Cc) h *= 1.0f + a.lambda;   // LM damping
+        H[e] = h;
+    }
+    // gradient: data + E_rot + E_reg (out-edges, in-edges)
+    if (lane < 12) {
+        const int r = lane >> 2, c = lane & 3;
+        float g = Gx[lane];
+        if (c < 3) {
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v += rot_res(X, q) * rot_jac(X, q, r, c);
+            g += a.w_rot * v;
+        }
         for (int s = 0; s < a.kg; ++s) {
             const int k = a.nbr[j * a.kg + s];
             if (k < 0) continue;
             const float4 gk = a.g[k];
             const float hh[4] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z, 1.0f};
+            const float er = ed_reg_residual(X + 4 * r, r, hh, (&a.x4[3 * k].x)[4 * r + 3]);
+            g += wr * er * hh[c];
+        }
+        if (c == 3) g -= wr * ein[r];
+        a.grad[12 * j + lane] = g;
+    }
+    // energies of node j: Rot(A_j), and its out-edges
+    if (lane == 0) {
+        double erot = 0.0, ereg = 0.0;
+        for (int q = 0; q < 6; ++q) {
+            const float rho = rot_res(X, q);
+            erot += (double)a.w_rot * rho * rho;
+        }
+        for (int s = 0; s < a.kg; ++s) {
+            const int k = a.nbr[j * a.kg + s];
+            if (k < 0) continue;
+            const float4 gk = a.g[k];
+            const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
             const float *xk = &a.x4[3 * k].x;
             for (int r = 0; r < 3; ++r) {
                 const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
                 ereg += (double)wr * e * e;
-                for (int c = 0; c < 4; ++c) {
-                    Gx[4 * r + c] += wr * e * hh[c];
-                    for (int c2 = 0; c2 < 4; ++c2) H[(4 * r + c) * 12 + 4 * r + c2] += wr * hh[c] * hh[c2];
-                }
-            }
-        }
-        // in-edges k -> j: they sit in row j of the pattern
-        for (int t = a.row_ptr[j]; t < a.row_ptr[j + 1]; ++t) {
-            const int k = a.col[t];
-            if (k == j) continue;
-            bool in = false;
-            for (int s = 0; s < a.kg; ++s) in |= a.nbr[k * a.kg + s] == j;
-            if (!in) continue;
-            const float4 gk = a.g[k];
-            const float hh[3] = {gj.x - gk.x, gj.y - gk.y, gj.z - gk.z};
-            const float *xk = &a.x4[3 * k].x;
-            for (int r = 0; r < 3; ++r) {
-                const float e = ed_reg_residual(xk + 4 * r, r, hh, X[4 * r + 3]);
-                Gx[4 * r + 3] -= wr * e;
-                H[(4 * r + 3) * 12 + 4 * r + 3] += wr;
             }
         }
         a.node_energy[2 * j] = erot;
         a.node_energy[2 * j + 1] = ereg;
-    }
-    __syncwarp();
-    // LM damping on the diagonal, store the block and J^T r
-    if (lane < 12) {
-        H[lane * 13] *= 1.0f + a.lambda;
-        a.grad[12 * j + lane] = Gx[lane];
     }
     __syncwarp();
     for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
@@ -425,10 +524,10 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     for (int k = 0; k < 12; ++k) {
         const float piv = H[k * 13];
         if (!(piv > 0.f)) ok = false;
-        const float s = ok ? sqrtf(piv) : 1.0f;
+        const float sq = ok ? sqrtf(piv) : 1.0f;
         __syncwarp();
-        if (lane == 0) H[k * 13] = s;
-        if (lane > k && lane < 12) H[lane * 12 + k] /= s;
+        if (lane == 0) H[k * 13] = sq;
+        if (lane > k && lane < 12) H[lane * 12 + k] /= sq;
         __syncwarp();
         for (int e = lane; e < 144; e += 32) {
             const int r = e / 12, c = e % 12;
@@ -440,26 +539,22 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
         if (lane == 0) atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
         return;
     }
-    // Linv by forward substitution, one column per lane; stored in M[0..143]? use sH upper part
-    float Li[12];
+    // L^-1 by forward substitution, one column per lane (lanes 0..11)
     if (lane < 12) {
+#pragma unroll
         for (int r = 0; r < 12; ++r) {
-            float s = (r == lane) ? 1.0f : 0.0f;
-            for (int k = lane; k < r; ++k) s -= H[r * 12 + k] * Li[k];
-            Li[r] = r < lane ? 0.f : s / H[r * 13];
+            float v = (r == lane) ? 1.0f : 0.0f;
+            for (int k = lane; k < r; ++k) v -= H[r * 12 + k] * sL[wid][k * 12 + lane];
+            sL[wid][r * 12 + lane] = r < lane ? 0.f : v / H[r * 13];
         }
     }
     __syncwarp();
-    // Minv[p][q] = sum_k Linv[k][p] Linv[k][q]; lane p holds column p of Linv
-    __shared__ float sL[FIN_WARPS][144];
-    if (lane < 12)
-        for (int r = 0; r < 12; ++r) sL[wid][r * 12 + lane] = Li[r];
-    __syncwarp();
     for (int e = lane; e < 144; e += 32) {
         const int p = e / 12, q = e % 12;
-        float s = 0.f;
-        for (int k = 0; k < 12; ++k) s += sL[wid][k * 12 + p] * sL[wid][k * 12 + q];
-        a.minv[(long)j * 144 + e] = s;
+        float s2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s2 += sL[wid][k * 12 + p] * sL[wid][k * 12 + q];
+        a.minv[(long)j * 144 + e] = s2;
     }
 }
 
@@ -468,112 +563,154 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
 // energy totals, pose preconditioner
 // ---------------------------------------------------------------------------
 
-__global__ void k_pose_final(const double *__restrict__ part, int nparts, const double *__restrict__ node_energy,
-                             int m, const double *__restrict__ pose, ed_solver_params prm, float *__restrict__ pose_blk,
-                             float *__restrict__ grad, double *__restrict__ dmisc, int *__restrict__ status,
-                             ed_stats *stats)
+__global__ void __launch_bounds__(256) k_pose_final(const double *__restrict__ part, int nparts,
+                                                    const double *__restrict__ node_energy, int m,
+                                                    const double *__restrict__ pose, ed_solver_params prm,
+                                                    float *__restrict__ pose_blk, float *__restrict__ grad,
+                                                    double *__restrict__ dmisc, int *__restrict__ status,
+                                                    ed_stats *stats)
 {
+    __shared__ double sw[8][32];
     __shared__ double s[32];
-    __shared__ double ne[2][256];
-    const int t = threadIdx.x;
-    {
-        // component k by warp k % 8 (fixed lane stride and shuffle tree: deterministic)
-        const int lane = t & 31, w = t >> 5;
-        for (int k = w; k < 30; k += 8) {
-            double v = 0.0;
-#pragma unroll 4
-            for (int c = lane; c < nparts; c += 32) v += part[c * ED_K1_PART + k];
+    __shared__ double ne[2][8];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    // point-pass partials: thread t sums CTAs t, t + 256, ... for all 30 components
+    double acc[30];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) s[k] = v;
-        }
+    for (int k = 0; k < 30; ++k) acc[k] = 0.0;
+    for (int c = t; c < nparts; c += 256) {
+#pragma unroll
+        for (int k = 0; k < 30; ++k) acc[k] += part[c * ED_K1_PART + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 30; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sw[w][k] = v;
     }
     double er = 0.0, eg = 0.0;
-    for (int j = t; j < m; j += blockDim.x) {
+    for (int j = t; j < m; j += 256) {
         er += node_energy[2 * j];
         eg += node_energy[2 * j + 1];
     }
-    ne[0][t] = er;
-    ne[1][t] = eg;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        er += __shfl_xor_sync(0xffffffffu, er, o);
+        eg += __shfl_xor_sync(0xffffffffu, eg, o);
+    }
+    if (lane == 0) {
+        ne[0][w] = er;
+        ne[1][w] = eg;
+    }
     __syncthreads();
-    if (t == 0) {
-        double Erot = 0.0, Ereg = 0.0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            Erot += ne[0][k];
-            Ereg += ne[1][k];
-        }
-        double H[36], gp[6];
+    if (t < 30) {
+        double v = 0.0;
+        for (int k = 0; k < 8; ++k) v += sw[k][t];
+        s[t] = v;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    double Erot = 0.0, Ereg = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        Erot += ne[0][k];
+        Ereg += ne[1][k];
+    }
+    float H[36], L[36];
+    double gp[6];
+    {
         int k = 2;
+#pragma unroll
         for (int a = 0; a < 6; ++a)
+#pragma unroll
             for (int b = a; b < 6; ++b) {
-                H[6 * a + b] = H[6 * b + a] = s[k];
+                H[6 * a + b] = H[6 * b + a] = (float)s[k];
                 ++k;
             }
-        double Er = 0.0, Ep = 0.0;
-        for (int a = 0; a < 6; ++a) {
-            const double w = a < 3 ? prm.w_r : prm.w_p;
-            const double d = pose[a] - prm.prior[a];
-            if (a < 3) Er += w * d * d;
-            else Ep += w * d * d;
-            H[7 * a] += w;
-            gp[a] = s[23 + a] + w * d;
+    }
+    double Er = 0.0, Ep = 0.0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        const double wt = a < 3 ? prm.w_r : prm.w_p;
+        const double d = pose[a] - prm.prior[a];
+        if (a < 3) Er += wt * d * d;
+        else Ep += wt * d * d;
+        H[7 * a] = (float)((double)H[7 * a] + wt);
+        gp[a] = s[23 + a] + wt * d;
+    }
+    const double E = s[0] + Erot + Ereg + Er + Ep;
+    if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
+    float tr = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        H[7 * a] *= 1.0f + prm.lambda;
+        tr += H[7 * a];
+    }
+#pragma unroll
+    for (int a = 0; a < 36; ++a) {
+        pose_blk[a] = H[a];
+        L[a] = H[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        L[7 * a] += prm.jitter * tr / 6.0f;
+        grad[a] = (float)gp[a];
+    }
+    // inverse of the pose block by Cholesky (unrolled, FP32)
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float d = L[7 * c];
+#pragma unroll
+        for (int p = 0; p < c; ++p) d -= L[6 * c + p] * L[6 * c + p];
+        ok = ok && d > 0.f;
+        d = sqrtf(fmaxf(d, 1e-30f));
+        L[7 * c] = d;
+#pragma unroll
+        for (int r = c + 1; r < 6; ++r) {
+            float v = L[6 * r + c];
+#pragma unroll
+            for (int p = 0; p < c; ++p) v -= L[6 * r + p] * L[6 * c + p];
+            L[6 * r + c] = v / d;
         }
-        const double E = s[0] + Erot + Ereg + Er + Ep;
-        if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
-        for (int a = 0; a < 6; ++a) H[7 * a] *= 1.0 + (double)prm.lambda;
-        for (int a = 0; a < 36; ++a) pose_blk[a] = (float)H[a];
-        for (int a = 0; a < 6; ++a) grad[a] = (float)gp[a];
-        // inverse of the pose block (+ jitter) by Cholesky, in double
-        double L[36];
-        double tr = 0.0;
-        for (int a = 0; a < 6; ++a) tr += H[7 * a];
-        for (int a = 0; a < 36; ++a) L[a] = H[a];
-        for (int a = 0; a < 6; ++a) L[7 * a] += (double)prm.jitter * tr / 6.0;
-        bool ok = true;
-        for (int c = 0; c < 6 && ok; ++c) {
-            double d = L[7 * c];
-            for (int p = 0; p < c; ++p) d -= L[6 * c + p] * L[6 * c + p];
-            if (!(d > 0.0)) { ok = false; break; }
-            d = sqrt(d);
-            L[7 * c] = d;
-            for (int r = c + 1; r < 6; ++r) {
-                double v = L[6 * r + c];
-                for (int p = 0; p < c; ++p) v -= L[6 * r + p] * L[6 * c + p];
-                L[6 * r + c] = v / d;
-            }
+    }
+    if (!ok) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
+#pragma unroll
+    for (int col = 0; col < 6; ++col) {
+        float y[6], xv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            float v = r == col ? 1.0f : 0.0f;
+#pragma unroll
+            for (int p = 0; p < r; ++p) v -= L[6 * r + p] * y[p];
+            y[r] = v / L[7 * r];
         }
-        if (!ok) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
-        else
-            for (int col = 0; col < 6; ++col) {
-                double y[6], xv[6];
-                for (int r = 0; r < 6; ++r) {
-                    double v = r == col ? 1.0 : 0.0;
-                    for (int p = 0; p < r; ++p) v -= L[6 * r + p] * y[p];
-                    y[r] = v / L[7 * r];
-                }
-                for (int r = 5; r >= 0; --r) {
-                    double v = y[r];
-                    for (int p = r + 1; p < 6; ++p) v -= L[6 * p + r] * xv[p];
-                    xv[r] = v / L[7 * r];
-                }
-                for (int r = 0; r < 6; ++r) pose_blk[36 + 6 * r + col] = (float)xv[r];
-            }
-        dmisc[0] = E;
-        dmisc[1] = s[0];
-        dmisc[2] = Erot;
-        dmisc[3] = Ereg;
-        dmisc[4] = Er;
-        dmisc[5] = Ep;
-        dmisc[6] = s[1];
-        if (stats) {
-            stats->energy = E;
-            stats->e_data = s[0];
-            stats->e_rot = Erot;
-            stats->e_reg = Ereg;
-            stats->e_rot_prior = Er;
-            stats->e_pos_prior = Ep;
-            stats->n_valid = (int)s[1];
+#pragma unroll
+        for (int r = 5; r >= 0; --r) {
+            float v = y[r];
+#pragma unroll
+            for (int p = r + 1; p < 6; ++p) v -= L[6 * p + r] * xv[p];
+            xv[r] = v / L[7 * r];
         }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) pose_blk[36 + 6 * r + col] = xv[r];
+    }
+    dmisc[0] = E;
+    dmisc[1] = s[0];
+    dmisc[2] = Erot;
+    dmisc[3] = Ereg;
+    dmisc[4] = Er;
+    dmisc[5] = Ep;
+    dmisc[6] = s[1];
+    if (stats) {
+        stats->energy = E;
+        stats->e_data = s[0];
+        stats->e_rot = Erot;
+        stats->e_reg = Ereg;
+        stats->e_rot_prior = Er;
+        stats->e_pos_prior = Ep;
+        stats->n_valid = (int)s[1];
     }
 }
 
@@ -624,10 +761,17 @@ extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_so
     ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_STATUS, 0, sizeof(int), st));
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_STEP, st)) != ED_OK) return s;
     if (ctx->n_chunks > 0) {
+        const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
-        k_assemble<<<ed_div_up(ctx->n_chunks, 128), 128, 0, st>>>(
-            ctx->chunks, ctx->n_chunks, ctx->max_chunks, ctx->ent_val, ctx->brow, (const float4 *)ctx->graph.nodes,
-            (const float4 *)ctx->pos, ctx->graph.weights, ctx->rec0, ctx->rec1, pose, ctx->partials); ed_note_launch();
+        if (n0 > 0) {
+            k_assemble0<<<ed_div_up(ed_div_up(n0, 32) * 64, 128), 128, 0, st>>>(
+                ctx->chunks, n0, ctx->max_chunks, ctx->ent_geo, ctx->ent_pt, ctx->rec0, ctx->partials); ed_note_launch();
+        }
+        if (n1 > 0) {
+            k_assemble1<<<ed_div_up(ed_div_up(n1, 32) * 96, 128), 128, 0, st>>>(
+                ctx->chunks, base1, n1, ctx->max_chunks, ctx->ent_geo, ctx->ent_pt, ctx->rec0, ctx->rec1, pose,
+                ctx->partials); ed_note_launch();
+        }
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();
     }
@@ -638,10 +782,12 @@ extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_so
     fa.tpos = ctx->tpos;
     fa.row_ptr = ctx->row_ptr;
     fa.chunk_start = ctx->chunk_start;
-    fa.chunk_cnt = ctx->chunk_cnt;
+    fa.chunk_start1 = ctx->chunk_start1;
+    fa.ent_cnt = ctx->ent_cnt;
     fa.nbr = ctx->graph.nbr;
     fa.part = ctx->partials;
     fa.max_chunks = ctx->max_chunks;
+    fa.n_chunks0 = ctx->chunk_base1;
     fa.n_upper = ctx->n_upper;
     fa.kg = ctx->k_graph;
     fa.mixed = prm->precision == ED_PRECISION_MIXED;

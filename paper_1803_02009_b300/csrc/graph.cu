@@ -1,6 +1,7 @@
 // graph.cu -- ed_build_graph: ED nodes, nearest nodes and weights, node
 // graph, and the block structure of the normal equations (Sec. II.D-II.E).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "ed_internal.cuh"
@@ -105,93 +106,146 @@ __global__ void k_cell_of(const float4 *__restrict__ pos, int n, const int *__re
     cell_of[i] = c.x + dims[0] * (c.y + dims[1] * c.z);
 }
 
-// Poisson-disk phase, step 1: every point of a cell of this phase that keeps
-// distance >= r (FP32 key) from all nodes chosen so far bids for its cell; the
-// lowest index wins.  Nodes within r lie in the 5x5x5 cells around the point.
-__global__ void k_poisson_pick(const float4 *__restrict__ pos, int n, int phase, const int *__restrict__ misc,
-                               const float *__restrict__ fmisc, const int *__restrict__ cell_of,
-                               const int *__restrict__ cell_node, int *__restrict__ cell_pick)
+// Poisson-disk sampling (27 phases).  Points are bucketed by the phase of
+// their cell once; phase ph then runs over its bucket only.  A cell's winning
+// bid (lowest point index) is the node of that cell: later phases read it
+// straight from cell_pick (a cell of a later phase still holds the "no bid"
+// pattern 0x7f7f7f7f, and cells of the same phase are never within +-2 cells
+// of each other), so no per-phase commit is needed.  Node numbers follow the
+// (phase, linear cell index) order and are assigned by one scan at the end.
+
+#define NO_BID 0x7f7f7f7f
+
+__device__ __forceinline__ int cell_phase(int c, int nx, int ny)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1], nz = misc[MI_DIMS + 2];
-    const int c = cell_of[i];
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-    if ((cx % 3) + 3 * (cy % 3) + 9 * (cz % 3) != phase) return;
-    const float4 p = pos[i];
-    const float r2 = fmisc[MF_R2];
-    for (int dz = -2; dz <= 2; ++dz) {
-        const int az = cz + dz;
-        if (az < 0 || az >= nz) continue;
-        for (int dy = -2; dy <= 2; ++dy) {
-            const int ay = cy + dy;
-            if (ay < 0 || ay >= ny) continue;
-            for (int dx = -2; dx <= 2; ++dx) {
-                const int ax = cx + dx;
-                if (ax < 0 || ax >= nx) continue;
-                const int q = cell_node[ax + nx * (ay + ny * az)];
-                if (q < 0) continue;
-                const float4 g = pos[q];
-                if (ed_key(p.x, p.y, p.z, g.x, g.y, g.z) < r2) return;
-            }
-        }
-    }
-    atomicMin(&cell_pick[c], i);
+    return (cx % 3) + 3 * (cy % 3) + 9 * (cz % 3);
 }
 
-// Poisson-disk phase, step 2 (one CTA): the phase's cells in increasing linear
-// order receive consecutive node numbers
-__global__ void k_poisson_commit(const float4 *__restrict__ pos, int phase, int *__restrict__ misc,
-                                 const int *__restrict__ cell_pick, int *__restrict__ cell_node, float4 *__restrict__ nodes,
-                                 int max_nodes)
+__global__ void k_phase_count(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
+                              int *__restrict__ cnt)
 {
-    __shared__ int sh[33];
-    __shared__ int base_s;
-    const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1], nz = misc[MI_DIMS + 2];
-    const int px = phase % 3, py = (phase / 3) % 3, pz = phase / 9;
-    const int ax = nx > px ? (nx - px + 2) / 3 : 0, ay = ny > py ? (ny - py + 2) / 3 : 0,
-              az = nz > pz ? (nz - pz + 2) / 3 : 0;
-    const long total = (long)ax * ay * az;
-    if (threadIdx.x == 0) base_s = misc[MI_PHASE_BASE];
+    __shared__ int h[27];
+    if (threadIdx.x < 27) h[threadIdx.x] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (long t0 = 0; t0 < total; t0 += blockDim.x) {
-        const long t = t0 + threadIdx.x;
-        int L = -1, pick = -1;
-        if (t < total) {
-            const int a = (int)(t % ax), b = (int)((t / ax) % ay), c = (int)(t / ((long)ax * ay));
-            L = (px + 3 * a) + nx * ((py + 3 * b) + ny * (pz + 3 * c));
-            const int pk = cell_pick[L];
-            if (pk != 0x7f7f7f7f) pick = pk;   // 0x7f7f7f7f: no bid (memset pattern)
-        }
-        const int f = pick >= 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const int wpre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) sh[wid] = __popc(bal);
+    const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[cell_phase(cell_of[i], nx, ny)], 1);
+    __syncthreads();
+    if (threadIdx.x < 27 && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
+}
+
+// exclusive scan of the 27 phase counts (start[27] = n); fill counters cleared
+__global__ void k_phase_scan(const int *__restrict__ cnt, int *__restrict__ start, int *__restrict__ fill)
+{
+    if (threadIdx.x != 0) return;
+    int s = 0;
+    for (int p = 0; p < 27; ++p) {
+        start[p] = s;
+        s += cnt[p];
+        fill[p] = 0;
+    }
+    start[27] = s;
+}
+
+__global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
+                                const int *__restrict__ start, int *__restrict__ fill, int *__restrict__ bucket)
+{
+    __shared__ int h[27], base[27];
+    const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1];
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        if (threadIdx.x < 27) h[threadIdx.x] = 0;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int s = 0;
-            for (int w = 0; w < nw; ++w) {
-                int v = sh[w];
-                sh[w] = s;
-                s += v;
-            }
-            sh[32] = s;
+        const int i = i0 + threadIdx.x;
+        int ph = -1, loc = 0;
+        if (i < n) {
+            ph = cell_phase(cell_of[i], nx, ny);
+            loc = atomicAdd(&h[ph], 1);
         }
         __syncthreads();
-        if (f) {
-            const int id = base_s + sh[wid] + wpre;
-            cell_node[L] = pick;
-            if (id < max_nodes) {
-                const float4 p = pos[pick];
-                nodes[id] = make_float4(p.x, p.y, p.z, 0.f);
-            }
-        }
+        if (threadIdx.x < 27) base[threadIdx.x] = h[threadIdx.x] ? atomicAdd(&fill[threadIdx.x], h[threadIdx.x]) : 0;
         __syncthreads();
-        if (threadIdx.x == 0) base_s += sh[32];
+        if (i < n) bucket[start[ph] + base[ph] + loc] = i;
         __syncthreads();
     }
-    if (threadIdx.x == 0) misc[MI_PHASE_BASE] = base_s;
+}
+
+// phase ph: a point bids for its cell when its FP32 key to every node chosen
+// in earlier phases (cells within +-2) is >= r*r; the lowest index wins
+__global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__restrict__ bucket,
+                               const int *__restrict__ start, int phase, const int *__restrict__ misc,
+                               const float *__restrict__ fmisc, const int *__restrict__ cell_of,
+                               int *__restrict__ cell_pick)
+{
+    const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1], nz = misc[MI_DIMS + 2];
+    const float r2 = fmisc[MF_R2];
+    const int e0 = start[phase], e1 = start[phase + 1];
+    for (int e = e0 + blockIdx.x * blockDim.x + threadIdx.x; e < e1; e += gridDim.x * blockDim.x) {
+        const int i = bucket[e];
+        const int c = cell_of[i];
+        const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+        const float4 p = pos[i];
+        bool ok = true;
+        // 124 neighbour cells (the own cell belongs to this phase); the loads of
+        // one z layer are issued together, then the few nodes found are checked
+        for (int dz = -2; dz <= 2 && ok; ++dz) {
+            const int az = cz + dz;
+            if (az < 0 || az >= nz) continue;
+            int q[25];
+#pragma unroll
+            for (int k = 0; k < 25; ++k) {
+                const int ay = cy + k / 5 - 2, ax = cx + k % 5 - 2;
+                const bool in = ay >= 0 && ay < ny && ax >= 0 && ax < nx && !(dz == 0 && k == 12);
+                q[k] = in ? cell_pick[ax + nx * (ay + ny * az)] : NO_BID;   // earlier phases: final
+            }
+#pragma unroll
+            for (int k = 0; k < 25; ++k) {
+                if (q[k] == NO_BID) continue;
+                const float4 g = pos[q[k]];
+                if (ed_key(p.x, p.y, p.z, g.x, g.y, g.z) < r2) ok = false;
+            }
+        }
+        if (ok) atomicMin(&cell_pick[c], i);
+    }
+}
+
+struct PhaseTable {
+    int off[28];   // first enumeration index of every phase (cells in phase-major order)
+    int ax[27], ay[27];
+};
+
+__device__ __forceinline__ int phase_cell(const PhaseTable &T, int t, int nx, int ny, int &ph)
+{
+    int p = 0;
+    while (p < 26 && t >= T.off[p + 1]) ++p;
+    ph = p;
+    const int k = t - T.off[p];
+    const int a = k % T.ax[p], b = (k / T.ax[p]) % T.ay[p], c = k / (T.ax[p] * T.ay[p]);
+    return (p % 3 + 3 * a) + nx * (((p / 3) % 3 + 3 * b) + ny * (p / 9 + 3 * c));
+}
+
+__global__ void k_node_flags(PhaseTable T, int total, const int *__restrict__ misc, const int *__restrict__ cell_pick,
+                             int *__restrict__ flag)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int ph;
+    const int L = phase_cell(T, t, misc[MI_DIMS], misc[MI_DIMS + 1], ph);
+    flag[t] = cell_pick[L] != NO_BID;
+}
+
+__global__ void k_node_write(PhaseTable T, int total, const int *__restrict__ misc, const int *__restrict__ cell_pick,
+                             const int *__restrict__ pre, const float4 *__restrict__ pos, float4 *__restrict__ nodes,
+                             int max_nodes)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total || pre[t + 1] == pre[t]) return;
+    const int id = pre[t];
+    if (id >= max_nodes) return;
+    int ph;
+    const int L = phase_cell(T, t, misc[MI_DIMS], misc[MI_DIMS + 1], ph);
+    const float4 p = pos[cell_pick[L]];
+    nodes[id] = make_float4(p.x, p.y, p.z, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,33 +366,43 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
     w_out[i] = make_float4(w[0], w[1], w[2], w[3]);
 }
 
-// N(j): the k_graph nearest other nodes (brute force over all nodes)
+// N(j): the k_graph nearest other nodes (FP32 key, ties to the lower index).
+// One warp per node: every lane keeps the best k_graph of its strided share of
+// the nodes, then the warp merges the 32 sorted lists by repeated minimum of
+// (key bits, index) -- keys are non-negative, so their bits order like floats.
 __global__ void k_node_graph(const float4 *__restrict__ nodes, int m, int kg, int *__restrict__ nbr)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= m) return;
-    float kk[ED_MAX_KG];
-    int ii[ED_MAX_KG];
-    for (int s = 0; s < kg; ++s) {
-        kk[s] = INFINITY;
-        ii[s] = 0x7fffffff;
-    }
+    unsigned long long best[ED_MAX_KG];
+    for (int s = 0; s < ED_MAX_KG; ++s) best[s] = ~0ull;
     const float4 g = nodes[j];
-    for (int l = 0; l < m; ++l) {
+    for (int l = lane; l < m; l += 32) {
         if (l == j) continue;
         const float4 h = __ldg(nodes + l);
-        const float key = ed_key(g.x, g.y, g.z, h.x, h.y, h.z);
-        if (key > kk[kg - 1] || (key == kk[kg - 1] && l >= ii[kg - 1])) continue;
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(ed_key(g.x, g.y, g.z, h.x, h.y, h.z)) << 32) | (unsigned)l;
+        if (key >= best[kg - 1]) continue;
         int p = kg - 1;
-        while (p > 0 && (kk[p - 1] > key || (kk[p - 1] == key && ii[p - 1] > l))) {
-            kk[p] = kk[p - 1];
-            ii[p] = ii[p - 1];
+        while (p > 0 && best[p - 1] > key) {
+            best[p] = best[p - 1];
             --p;
         }
-        kk[p] = key;
-        ii[p] = l;
+        best[p] = key;
     }
-    for (int s = 0; s < kg; ++s) nbr[j * kg + s] = ii[s] == 0x7fffffff ? -1 : ii[s];
+    int head = 0;
+    for (int s = 0; s < kg; ++s) {
+        const unsigned long long mine = head < kg ? best[head] : ~0ull;
+        unsigned long long mn = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, mn, o);
+            mn = other < mn ? other : mn;
+        }
+        if (mine == mn && mn != ~0ull) ++head;   // (key, index) pairs are unique: one lane pops
+        if (lane == 0) nbr[j * kg + s] = mn == ~0ull ? -1 : (int)(mn & 0xffffffffu);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -427,15 +491,18 @@ __global__ void k_tpos(int nnzb, const int *__restrict__ row_ptr, const int *__r
     if (b >= nnzb) return;
     const int j = brow[b], l = col[b];
     tpos[b] = find_block(row_ptr, col, l, j);
-    upper_flag[b] = l >= j;
+    upper_flag[b] = l > j;   // strictly upper: the diagonal blocks go first in the list
 }
 
-__global__ void k_compact_upper(int nnzb, const int *__restrict__ flag, const int *__restrict__ pre,
-                                int *__restrict__ up_list)
+// finalisation work list: the m diagonal blocks (long warps) first, then the
+// strictly upper blocks in row order
+__global__ void k_compact_upper(int nnzb, int m, const int *__restrict__ flag, const int *__restrict__ pre,
+                                const int *__restrict__ diag_pos, int *__restrict__ up_list)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < m) up_list[b] = diag_pos[b];
     if (b >= nnzb) return;
-    if (flag[b]) up_list[pre[b]] = b;
+    if (flag[b]) up_list[m + pre[b]] = b;
 }
 
 // one entry per (point, unordered slot pair s <= t): key = upper block, value =
@@ -468,37 +535,79 @@ __global__ void k_entries_gen(const ushort4 *__restrict__ idx, int n, const int 
         }
 }
 
-__global__ void k_ent_count(const uint32_t *__restrict__ key, int ne, int *__restrict__ cnt)
+// entries of block b = [lower_bound(b), lower_bound(b + 1)) in the sorted keys
+__global__ void k_ent_count(const uint32_t *__restrict__ key, int ne, int nnzb, int *__restrict__ cnt)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < ne) atomicAdd(&cnt[key[e]], 1);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnzb) return;
+    int lo = 0, hi = ne;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[mid] < (uint32_t)b) lo = mid + 1;
+        else hi = mid;
+    }
+    int lo2 = lo, hi2 = ne;
+    while (lo2 < hi2) {
+        const int mid = (lo2 + hi2) >> 1;
+        if (key[mid] < (uint32_t)b + 1u) lo2 = mid + 1;
+        else hi2 = mid;
+    }
+    cnt[b] = lo2 - lo;
 }
 
+// chunks of <= ED_CHUNK entries: role 0 (moments) for every upper block, role 1
+// (J^T r and the pose-node block) for diagonal blocks; role-0 chunks first
 __global__ void k_chunk_count(int nnzb, const int *__restrict__ cnt, const int *__restrict__ brow,
-                              const int *__restrict__ col, int *__restrict__ ccnt)
+                              const int *__restrict__ col, int *__restrict__ ccnt0, int *__restrict__ ccnt1)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnzb) return;
     const int c = (cnt[b] + ED_CHUNK - 1) / ED_CHUNK;
-    ccnt[b] = brow[b] == col[b] ? 2 * c : (col[b] > brow[b] ? c : 0);
+    ccnt0[b] = col[b] >= brow[b] ? c : 0;
+    ccnt1[b] = col[b] == brow[b] ? c : 0;
 }
 
 __global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *__restrict__ ent_start,
                              const int *__restrict__ brow, const int *__restrict__ col,
-                             const int *__restrict__ cstart, int4 *__restrict__ chunks)
+                             const int *__restrict__ cstart0, const int *__restrict__ cstart1,
+                             int4 *__restrict__ chunks)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnzb || col[b] < brow[b]) return;
     const int n = cnt[b];
     const int per = (n + ED_CHUNK - 1) / ED_CHUNK;
-    const int roles = brow[b] == col[b] ? 2 : 1;
-    int q = cstart[b];
-    for (int r = 0; r < roles; ++r)
+    const int base1 = (cstart0[nnzb] + 31) & ~31;   // role-1 chunks start warp-aligned
+    for (int r = 0; r < (brow[b] == col[b] ? 2 : 1); ++r) {
+        int q = r == 0 ? cstart0[b] : base1 + cstart1[b];
         for (int k = 0; k < per; ++k) {
             const int beg = ent_start[b] + k * ED_CHUNK;
             const int c = min(ED_CHUNK, n - k * ED_CHUNK);
             chunks[q++] = make_int4(b, beg, c, r);
         }
+    }
+}
+
+// per-entry geometry, fixed for the frame: d = v_i - g_j and w_s w_t (role 0)
+// or w_s (role 1); slot of entry k of chunk c = (c / 32) 32 CH + 32 k + c % 32,
+// so that a warp's 32 chunks read 32 consecutive slots per entry
+__global__ void k_entry_geo(const int4 *__restrict__ chunks, int nchunks, const uint32_t *__restrict__ ent,
+                            const int *__restrict__ brow, const float4 *__restrict__ pos, const float *__restrict__ wts,
+                            const float4 *__restrict__ g, float4 *__restrict__ geo, int *__restrict__ pt)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    const int4 ch = chunks[c];
+    const float4 gj = g[brow[ch.x]];
+    const long base = (long)(c >> 5) * (32 * ED_CHUNK) + (c & 31);
+    for (int k = 0; k < ch.z; ++k) {
+        const uint32_t v = ent[ch.y + k];
+        const int i = (int)(v >> 4), sr = (v >> 2) & 3, sc = v & 3;
+        const float4 p = pos[i];
+        const float ws = wts[4 * i + sr];
+        const float w = ch.w == 0 ? ws * wts[4 * i + sc] : ws;
+        geo[base + 32L * k] = make_float4(p.x - gj.x, p.y - gj.y, p.z - gj.z, w);
+        pt[base + 32L * k] = i;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -552,15 +661,41 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     if (m_in == 0) {
         const int cells = hm[MI_DIMS + 3];
         ED_CUDA_TRY(cudaMemsetAsync(ctx->cell_pick, 0x7f, sizeof(int) * cells, st));
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->cell_node, 0xff, sizeof(int) * cells, st));
+        int *pcnt = ctx->misc + MI_PHASES, *pstart = ctx->misc + MI_PHASES + 32, *pfill = ctx->misc + MI_PHASES + 64;
+        int *bucket = ctx->flag_a;                  // N ints
+        ED_CUDA_TRY(cudaMemsetAsync(pcnt, 0, sizeof(int) * 27, st));
+        const int pg = min(ed_div_up(N, 256), 4 * ctx->num_sms);
         k_cell_of<<<ed_div_up(N, 256), 256, 0, st>>>(P4, N, ctx->misc, ctx->fmisc, ctx->cell_of); ed_note_launch();
+        k_phase_count<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pcnt); ed_note_launch();
+        k_phase_scan<<<1, 32, 0, st>>>(pcnt, pstart, pfill); ed_note_launch();
+        k_phase_scatter<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pstart, pfill, bucket); ed_note_launch();
         ED_LAUNCH_CHECK();
+        const int pick_grid = min(ed_div_up(N / 27 + 1, 128), 4 * ctx->num_sms);
         for (int ph = 0; ph < 27; ++ph) {
-            k_poisson_pick<<<ed_div_up(N, 256), 256, 0, st>>>(P4, N, ph, ctx->misc, ctx->fmisc, ctx->cell_of,
-                                                               ctx->cell_node, ctx->cell_pick); ed_note_launch();
-            k_poisson_commit<<<1, 1024, 0, st>>>(P4, ph, ctx->misc, ctx->cell_pick, ctx->cell_node, G4, max_nodes); ed_note_launch();
+            k_poisson_pick<<<pick_grid, 128, 0, st>>>(P4, bucket, pstart, ph, ctx->misc, ctx->fmisc, ctx->cell_of,
+                                                      ctx->cell_pick); ed_note_launch();
         }
         ED_LAUNCH_CHECK();
+        // node numbers in (phase, cell) order
+        PhaseTable T;
+        const int dx = hm[MI_DIMS], dy = hm[MI_DIMS + 1], dz = hm[MI_DIMS + 2];
+        int tot = 0;
+        for (int ph = 0; ph < 27; ++ph) {
+            const int px = ph % 3, py = (ph / 3) % 3, pz = ph / 9;
+            T.ax[ph] = dx > px ? (dx - px + 2) / 3 : 0;
+            T.ay[ph] = dy > py ? (dy - py + 2) / 3 : 0;
+            const int az = dz > pz ? (dz - pz + 2) / 3 : 0;
+            T.off[ph] = tot;
+            tot += T.ax[ph] * T.ay[ph] * az;
+        }
+        T.off[27] = tot;
+        int *flags = ctx->cell_node, *pre = ctx->kcell_start;   // cells (+ 1) ints each
+        k_node_flags<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, flags); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        if ((s = ed_scan_exclusive(ctx, flags, pre, tot, st)) != ED_OK) return s;
+        k_node_write<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, pre, P4, G4, max_nodes); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_PHASE_BASE, pre + tot, sizeof(int), cudaMemcpyDeviceToDevice, st));
         if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
         const int mt = hm[MI_PHASE_BASE];
         m = mt < max_nodes ? mt : max_nodes;
@@ -587,7 +722,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_knn<<<ed_div_up(N, 128), 128, 0, st>>>(P4, N, G4, m, ctx->misc, ctx->fmisc, ctx->kcell_start,
                                                   ctx->kcell_nodes, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
-        k_node_graph<<<ed_div_up(m, 128), 128, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
+        k_node_graph<<<ed_div_up(m, 4), 128, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
 
@@ -609,7 +744,8 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_tpos<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, nnzb, st)) != ED_OK) return s;
-        k_compact_upper<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->flag_a, ctx->flag_b, ctx->up_list); ed_note_launch();
+        k_compact_upper<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, ctx->flag_a, ctx->flag_b, ctx->diag_pos,
+                                                               ctx->up_list); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
 
@@ -623,25 +759,50 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         int bits = 1;
         while ((1 << bits) < nnzb) ++bits;
         if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, ne, bits, st)) != ED_OK) return s;
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->ent_cnt, 0, sizeof(int) * nnzb, st));
-        k_ent_count<<<ed_div_up(ne, 256), 256, 0, st>>>(ctx->ent_key, ne, ctx->ent_cnt); ed_note_launch();
+        k_ent_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(ctx->ent_key, ne, nnzb, ctx->ent_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->ent_cnt, ctx->ent_start, nnzb, st)) != ED_OK) return s;
-        k_chunk_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->brow, ctx->col, ctx->chunk_cnt); ed_note_launch();
+        k_chunk_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->brow, ctx->col, ctx->chunk_cnt,
+                                                            ctx->chunk_cnt1); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt, ctx->chunk_start, nnzb, st)) != ED_OK) return s;
-        ED_CUDA_TRY(cudaMemcpyAsync(&nchunks, ctx->chunk_start + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt1, ctx->chunk_start1, nnzb, st)) != ED_OK) return s;
+        int nc01[2];
+        ED_CUDA_TRY(cudaMemcpyAsync(&nc01[0], ctx->chunk_start + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(&nc01[1], ctx->chunk_start1 + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
         if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
         if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
+        const int base1 = (nc01[0] + 31) & ~31;
+        nchunks = base1 + nc01[1];
+        ctx->n_chunks0 = nc01[0];
+        ctx->chunk_base1 = base1;
         if (nchunks > ctx->max_chunks) return ED_ERR_CAPACITY;
+        if (base1 > nc01[0])   // padding chunks between the roles: empty
+            ED_CUDA_TRY(cudaMemsetAsync(ctx->chunks + nc01[0], 0, sizeof(int4) * (base1 - nc01[0]), st));
         k_chunk_fill<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->ent_start, ctx->brow, ctx->col,
-                                                           ctx->chunk_start, ctx->chunks); ed_note_launch();
+                                                           ctx->chunk_start, ctx->chunk_start1, ctx->chunks); ed_note_launch();
+        if (nchunks > 0) {
+            k_entry_geo<<<ed_div_up(nchunks, 128), 128, 0, st>>>(ctx->chunks, nchunks, ctx->ent_val, ctx->brow, P4,
+                                                                   graph->weights, G4, ctx->ent_geo, ctx->ent_pt); ed_note_launch();
+        }
         ED_LAUNCH_CHECK();
         int cnt3[2] = {nnzb, 0};
         ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, cnt3, sizeof(cnt3), cudaMemcpyHostToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(&n_upper, ctx->flag_b + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaStreamSynchronize(st));
+        n_upper += m;   // strictly upper blocks + the diagonal
         if (2 * n_upper != nnzb + m) return ED_ERR_STATE;   // the pattern must be symmetric with a full diagonal
+    }
+    // row partition and shared-memory plan of the PCG solve
+    {
+        int *rp = (int *)malloc(sizeof(int) * (m + 1));
+        if (!rp) return ED_ERR_ARG;
+        cudaError_t e = cudaMemcpyAsync(rp, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        ctx->m = m;
+        ed_status ps = e == cudaSuccess ? ed_pcg_plan(ctx, rp, st) : ED_ERR_CUDA;
+        free(rp);
+        if (ps != ED_OK) return ps;
     }
 
     ctx->pos = pos;

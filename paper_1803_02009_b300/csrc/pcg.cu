@@ -2,21 +2,25 @@
 // equations of one Gauss-Newton step (Sec. II.F), as one persistent
 // cooperative kernel.
 //
-// Layout: H is a symmetric block-sparse matrix over the m nodes (12x12
-// blocks, both triangles stored, row-major blocks) bordered by the 6 pose
-// unknowns: pose-node blocks C_j (6x12) and a 6x6 pose block.  Every CTA owns
-// a contiguous range of node rows; CTA 0 also owns the pose rows.  One PCG
-// iteration needs two grid-wide barriers: after q = H p (to reduce p^T q and
-// the pose row) and after the preconditioner (to reduce r^T z).  The search
-// direction p_k = z_k + beta p_{k-1} is formed on the fly for every block
-// column read by the product, so p needs no third barrier (double buffer).
-// All reductions are per-CTA partials summed in CTA order by every CTA:
-// deterministic.  Every barrier wait is bounded (ED_ERR_TIMEOUT).
+// H is a symmetric block-sparse matrix over the m nodes (12x12 blocks, both
+// triangles stored, row-major blocks) bordered by the 6 pose unknowns:
+// pose-node blocks C_j (6x12) and a 6x6 pose block.  Each CTA (one per SM)
+// owns a contiguous range of node rows, balanced by block count at graph
+// build; CTA 0 also owns the pose rows.  For the whole solve a CTA keeps in
+// shared memory its rows' blocks (as many as fit; the rest stream from L2),
+// block inverses, pose-node blocks and its slices of d, r, z, p, q.  Per PCG
+// iteration it gathers the search direction of every block column it
+// touches, p_l = z_l + beta p_l(prev) (formed on the fly from the owners'
+// z and previous p: double buffer, no barrier of its own), multiplies from
+// shared memory, and meets the other CTAs at two bounded grid barriers (after
+// q = H p for p.q and the pose row, after z = M^-1 r for r.z).  Reductions are
+// per-CTA partials summed in a fixed order by every CTA: deterministic.
 #include "ed_internal.cuh"
 
 #define PCG_T 512
-#define ROWS_PER_PASS (PCG_T / 36)
+#define ROWS_PER_PASS (PCG_T / 12)   // 12 threads per node row (one per output row)
 #define BAR_TIMEOUT_NS 2000000000ull
+#define PCG_SMEM_MAX (200 * 1024)
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -32,8 +36,23 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
-// grid barrier with a monotonic arrival counter; returns false when the
-// context status is set (error elsewhere or timeout)
+__device__ __forceinline__ unsigned atom_add_release(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// grid barrier with a monotonic arrival counter: the CTA's writes are ordered
+// before thread 0's arrival by the CTA barrier and a fence, other CTAs' writes
+// are visible after its acquire load of the generation (later reads of shared
+// data bypass L1); returns false when the context status is set (an error
+// elsewhere, or this wait timed out)
 __device__ bool grid_sync(unsigned *count, unsigned *gen, int *status, unsigned nblocks, unsigned &target,
                           int *s_flag)
 {
@@ -41,24 +60,24 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, int *status, unsigned 
     if (threadIdx.x == 0) {
         int ok = 1;
         target += 1;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        __threadfence();   // the whole CTA's writes (ordered by the CTA barrier) before the arrival
+        const unsigned arrived = atom_add_release(count, 1u) + 1u;
         if (arrived == nblocks * target) {
-            __threadfence();
-            atomicExch(gen, target);
+            st_release(gen, target);
         } else {
             const unsigned long long t0 = gtimer();
+            unsigned spins = 0;
             while (ld_acquire(gen) < target) {
-                if (*(volatile int *)status != ED_OK) { ok = 0; break; }
-                if (gtimer() - t0 > BAR_TIMEOUT_NS) {
-                    atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int *)status != ED_OK) { ok = 0; break; }
+                    if (gtimer() - t0 > BAR_TIMEOUT_NS) {
+                        atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(40);
             }
         }
-        __threadfence();
         if (*(volatile int *)status != ED_OK) ok = 0;
         *s_flag = ok;
     }
@@ -70,15 +89,18 @@ struct PcgArgs {
     int m, n_iter;
     float tol;
     const int *row_ptr, *col;
+    const int *cta_rows;     // [grid + 1] first row of every CTA
+    int n_cache;             // blocks of each CTA cached in shared memory
+    int max_rows, max_blk;   // shared-memory plan
     const float *bsr, *pnode, *minv, *pose_blk, *grad;
-    float *d, *r, *z, *p0, *p1, *q;
-    double *part;        // [2][grid][ED_PCG_PART]
-    unsigned *bar;       // count, generation
+    float *d, *z, *p0, *p1;  // global vectors (z and p are read by other CTAs)
+    double *part;            // [2][ED_MAX_PCG_GRID][ED_PCG_PART]
+    unsigned *bar;           // count, generation
     int *status;
     ed_stats *stats;
 };
 
-// sums component k of all CTA partials (warp k: lanes stride over the CTAs in
+// sums component w of all CTA partials (warp w: lanes stride over the CTAs in
 // a fixed order, then a fixed shuffle tree) -- every CTA gets the same result
 template <typename DT>
 __device__ __forceinline__ void sum_partials(const double *part, int nb, int ncomp, DT *out_sh)
@@ -116,75 +138,122 @@ __device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8], DT *sh_out
     __syncthreads();
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(PCG_T) k_pcg(PcgArgs a)
+// shared-memory carve of one CTA (in floats; every region a multiple of 4)
+struct PcgSmem {
+    size_t o_H, o_pb, o_M, o_C, o_r, o_d, o_z, o_p, o_q, total;
+};
+
+__host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncache)
 {
+    PcgSmem L;
+    size_t o = 0;
+    L.o_H = o; o += (size_t)ncache * 144;
+    L.o_pb = o; o += (size_t)nblk * 12;
+    L.o_M = o; o += (size_t)rows * 144;
+    L.o_C = o; o += (size_t)rows * 72;
+    L.o_r = o; o += (size_t)rows * 12;
+    L.o_d = o; o += (size_t)rows * 12;
+    L.o_z = o; o += (size_t)rows * 12;
+    L.o_p = o; o += (size_t)rows * 12;
+    L.o_q = o; o += (size_t)rows * 12;
+    L.total = o;
+    return L;
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_flag;
     __shared__ DT s_red[PCG_T / 32][8];
     __shared__ DT s_sum[8];
     __shared__ DT s_blk[8];
-    __shared__ float s_pp[6], s_ppold[6], s_qp[6];
-    __shared__ DT s_rho, s_beta, s_rr, s_res0;
+    __shared__ float s_pp[6], s_ppold[6], s_qp[6], s_rpose[6], s_dpose[6];
+    __shared__ float s_Hpp[36], s_Mp[36];
+    __shared__ DT s_rho, s_beta, s_rr, s_res0, s_alpha;
+    __shared__ int s_break;
     const unsigned nb = gridDim.x;
     unsigned target = 0;
     const int m = a.m;
-    const int rows_per = (m + nb - 1) / nb;
-    const int r0 = min(m, (int)blockIdx.x * rows_per), r1 = min(m, r0 + rows_per);
+    const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
+    const int rows = r1 - r0;
+    const int b0 = a.row_ptr[r0], nblk = a.row_ptr[r1] - b0;
+    const int ncache = min(nblk, a.n_cache);
+    const PcgSmem L = pcg_smem_layout(a.max_rows, a.max_blk, a.n_cache);
+    float *Hs = sm + L.o_H, *pb = sm + L.o_pb, *Ms = sm + L.o_M, *Cs = sm + L.o_C;
+    float *rs = sm + L.o_r, *ds = sm + L.o_d, *zs = sm + L.o_z, *ps = sm + L.o_p, *qs = sm + L.o_q;
     const int t = threadIdx.x;
-    const int grp = t / 36, tr = t % 36, rr = tr / 3, cg = tr % 3;
+    const int grp = t / 12, rr = t % 12;
     const bool in_grp = grp < ROWS_PER_PASS;
     const int P = 12 * m;
-    const float *Hpp = a.pose_blk, *Mp = a.pose_blk + 36;
+    const float *Hpp = s_Hpp, *Mp = s_Mp;
     double *part0 = a.part, *part1 = a.part + (size_t)ED_MAX_PCG_GRID * ED_PCG_PART;
 
     if (*(volatile int *)a.status != ED_OK) return;
 
-    // ---- setup: d = 0, r = b = -J^T r, z = M^-1 r ----
-    DT rz = 0, rrs = 0;
-    for (int j0 = r0; j0 < r1; j0 += ROWS_PER_PASS) {
-        const int j = j0 + grp;
-        const bool act = in_grp && j < r1;
-        float zp = 0.f;
-        if (act) {
-            // z_j = Minv_j b_j: thread (rr, cg) does row rr, columns 4cg..4cg+3
-            const float4 mv = *reinterpret_cast<const float4 *>(a.minv + (size_t)j * 144 + rr * 12 + 4 * cg);
-            const float *gj = a.grad + 12 * j + 4 * cg;
-            zp = -(mv.x * gj[0] + mv.y * gj[1] + mv.z * gj[2] + mv.w * gj[3]);
-        }
-        __shared__ float s_z[ROWS_PER_PASS][12][3];
-        if (in_grp) s_z[grp][rr][cg] = zp;
-        __syncthreads();
-        if (act && cg == 0) {
-            const float zz = s_z[grp][rr][0] + s_z[grp][rr][1] + s_z[grp][rr][2];
-            const float bb = -a.grad[12 * j + rr];
-            a.r[12 * j + rr] = bb;
-            a.z[12 * j + rr] = zz;
-            a.d[12 * j + rr] = 0.f;
-            rz += (DT)bb * (DT)zz;
-            rrs += (DT)bb * (DT)bb;
-        }
-        __syncthreads();
-    }
+    // ---- the CTA's share of H, M^-1, C and b into shared memory ----
     {
+        const float4 *src = reinterpret_cast<const float4 *>(a.bsr + (size_t)b0 * 144);
+        float4 *dst = reinterpret_cast<float4 *>(Hs);
+        for (int i = t; i < ncache * 36; i += PCG_T) dst[i] = __ldg(src + i);
+        const float4 *ms = reinterpret_cast<const float4 *>(a.minv + (size_t)r0 * 144);
+        float4 *md = reinterpret_cast<float4 *>(Ms);
+        for (int i = t; i < rows * 36; i += PCG_T) md[i] = __ldg(ms + i);
+        for (int i = t; i < rows * 72; i += PCG_T) Cs[i] = __ldg(a.pnode + (size_t)r0 * 72 + i);
+        for (int i = t; i < rows * 12; i += PCG_T) {
+            rs[i] = -__ldg(a.grad + 12 * r0 + i);
+            ds[i] = 0.f;
+        }
+        if (t < 36) {
+            s_Hpp[t] = a.pose_blk[t];
+            s_Mp[t] = a.pose_blk[36 + t];
+        }
+    }
+    __syncthreads();
+
+    // z_j = Minv_j r_j for the own rows (thread = one output row); partials r.z, r.r
+    auto precond = [&](DT &rz, DT &rrs) {
+        for (int j0 = 0; j0 < rows; j0 += ROWS_PER_PASS) {
+            const int jl = j0 + grp;
+            if (in_grp && jl < rows) {
+                const float4 *mv = reinterpret_cast<const float4 *>(Ms + jl * 144 + rr * 12);
+                const float4 *rv = reinterpret_cast<const float4 *>(rs + jl * 12);
+                float zz = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float4 m4 = mv[q], r4 = rv[q];
+                    zz += m4.x * r4.x + m4.y * r4.y + m4.z * r4.z + m4.w * r4.w;
+                }
+                const float rv1 = rs[jl * 12 + rr];
+                zs[jl * 12 + rr] = zz;
+                a.z[12 * (r0 + jl) + rr] = zz;
+                rz += (DT)rv1 * (DT)zz;
+                rrs += (DT)rv1 * (DT)rv1;
+            }
+        }
+        __syncthreads();
+    };
+
+    // ---- set-up: r = b, d = 0, z = M^-1 r ----
+    {
+        DT rz = 0, rrs = 0;
+        precond(rz, rrs);
         DT vv[2] = {rz, rrs};
         block_sum_n<DT, 2>(vv, s_red, s_blk);
     }
     if (t == 0) {
         DT v1 = s_blk[0], v2 = s_blk[1];
         if (blockIdx.x == 0) {
-            DT rzp = 0, rrp = 0;
+            for (int i = 0; i < 6; ++i) s_rpose[i] = -a.grad[P + i];
             for (int i = 0; i < 6; ++i) {
-                const float bi = -a.grad[P + i];
                 float zi = 0.f;
-                for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * -a.grad[P + k];
-                a.r[P + i] = bi;
+                for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
+                s_dpose[i] = 0.f;
                 a.z[P + i] = zi;
-                a.d[P + i] = 0.f;
-                rzp += (DT)bi * (DT)zi;
-                rrp += (DT)bi * (DT)bi;
+                v1 += (DT)s_rpose[i] * (DT)zi;
+                v2 += (DT)s_rpose[i] * (DT)s_rpose[i];
             }
-            v1 += rzp;
-            v2 += rrp;
         }
         part0[blockIdx.x * ED_PCG_PART + 0] = (double)v1;
         part0[blockIdx.x * ED_PCG_PART + 1] = (double)v2;
@@ -208,51 +277,56 @@ __global__ void __launch_bounds__(PCG_T) k_pcg(PcgArgs a)
         const float beta = (float)s_beta;
         const float *pold = (it & 1) ? a.p0 : a.p1;
         float *pnew = (it & 1) ? a.p1 : a.p0;
-        // pose part of p: p_pose = z_pose + beta p_pose_old (every CTA)
-        if (t < 6) s_pp[t] = __ldcg(a.z + P + t) + beta * s_ppold[t];
+        if (t < 6) s_pp[t] = it > 0 ? __fmaf_rn(beta, s_ppold[t], __ldcg(a.z + P + t)) : __ldcg(a.z + P + t);
+        // ---- gather p of every block column: p_l = z_l + beta p_l(prev) ----
+        for (int i = t; i < nblk * 3; i += PCG_T) {
+            const int lb = i / 3, q4 = i - 3 * lb;
+            const int l = __ldg(a.col + b0 + lb);
+            const float4 zl = __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l) + q4);
+            float4 pl = zl;
+            if (it > 0) {
+                const float4 po = __ldcg(reinterpret_cast<const float4 *>(pold + 12 * l) + q4);
+                pl = make_float4(__fmaf_rn(beta, po.x, zl.x), __fmaf_rn(beta, po.y, zl.y), __fmaf_rn(beta, po.z, zl.z),
+                                 __fmaf_rn(beta, po.w, zl.w));
+            }
+            reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] = pl;
+        }
+        // own rows: the same p_j, kept and published for the next iteration
+        for (int i = t; i < rows * 12; i += PCG_T) {
+            const float pv = it > 0 ? __fmaf_rn(beta, ps[i], zs[i]) : zs[i];
+            ps[i] = pv;
+            pnew[12 * r0 + i] = pv;
+        }
         __syncthreads();
-        // ---- phase A: q = H p over own rows; partials p.q and C p ----
+        // ---- phase A: q = H p (own rows; thread = one output row), partials p.q and C p ----
         DT pq = 0;
         DT cp[6] = {0, 0, 0, 0, 0, 0};
-        for (int j0 = r0; j0 < r1; j0 += ROWS_PER_PASS) {
-            const int j = j0 + grp;
-            const bool act = in_grp && j < r1;
-            float acc = 0.f;
-            if (act) {
-                const int b0 = a.row_ptr[j], b1 = a.row_ptr[j + 1];
-                for (int bk = b0; bk < b1; ++bk) {
-                    const int l = a.col[bk];
-                    const float4 h = __ldg(reinterpret_cast<const float4 *>(a.bsr + (size_t)bk * 144 + rr * 12 + 4 * cg));
-                    const float4 zl = __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l + 4 * cg));
-                    float4 pl = zl;
-                    if (it > 0) {
-                        const float4 po = __ldcg(reinterpret_cast<const float4 *>(pold + 12 * l + 4 * cg));
-                        pl = make_float4(zl.x + beta * po.x, zl.y + beta * po.y, zl.z + beta * po.z, zl.w + beta * po.w);
-                    }
-                    acc += h.x * pl.x + h.y * pl.y + h.z * pl.z + h.w * pl.w;
+        for (int j0 = 0; j0 < rows; j0 += ROWS_PER_PASS) {
+            const int jl = j0 + grp;
+            if (in_grp && jl < rows) {
+                const int j = r0 + jl;
+                const int bb0 = a.row_ptr[j] - b0, bb1 = a.row_ptr[j + 1] - b0;
+                float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+                for (int lb = bb0; lb < bb1; ++lb) {
+                    const float4 *hrow = lb < ncache ? reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12)
+                                                     : reinterpret_cast<const float4 *>(a.bsr + (size_t)(b0 + lb) * 144 + rr * 12);
+                    const float4 *pl = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
+                    const float4 h0 = hrow[0], h1 = hrow[1], h2 = hrow[2];
+                    const float4 p0 = pl[0], p1 = pl[1], p2 = pl[2];
+                    acc0 += h0.x * p0.x + h0.y * p0.y + h0.z * p0.z + h0.w * p0.w;
+                    acc1 += h1.x * p1.x + h1.y * p1.y + h1.z * p1.z + h1.w * p1.w;
+                    acc2 += h2.x * p2.x + h2.y * p2.y + h2.z * p2.z + h2.w * p2.w;
                 }
-                if (cg == 0) {
-                    const float *C = a.pnode + (size_t)j * 72;
+                const float *C = Cs + jl * 72;
+                float qv = acc0 + acc1 + acc2;
 #pragma unroll
-                    for (int s = 0; s < 6; ++s) acc += C[12 * s + rr] * s_pp[s];
-                }
-            }
-            __shared__ float s_q[ROWS_PER_PASS][12][3];
-            if (in_grp) s_q[grp][rr][cg] = acc;
-            __syncthreads();
-            if (act && cg == 0) {
-                const float qv = s_q[grp][rr][0] + s_q[grp][rr][1] + s_q[grp][rr][2];
-                const int e = 12 * j + rr;
-                float pv = __ldcg(a.z + e);
-                if (it > 0) pv += beta * __ldcg(pold + e);
-                pnew[e] = pv;
-                a.q[e] = qv;
+                for (int s = 0; s < 6; ++s) qv += C[12 * s + rr] * s_pp[s];
+                qs[jl * 12 + rr] = qv;
+                const float pv = ps[jl * 12 + rr];
                 pq += (DT)pv * (DT)qv;
-                const float *C = a.pnode + (size_t)j * 72;
 #pragma unroll
                 for (int s = 0; s < 6; ++s) cp[s] += (DT)C[12 * s + rr] * (DT)pv;
             }
-            __syncthreads();
         }
         {
             DT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
@@ -262,8 +336,6 @@ __global__ void __launch_bounds__(PCG_T) k_pcg(PcgArgs a)
         if (!grid_sync(a.bar, a.bar + 1, a.status, nb, target, &s_flag)) return;
         // ---- phase B: alpha, d += alpha p, r -= alpha q, z = M^-1 r ----
         sum_partials<DT>(part1, nb, 7, s_sum);
-        __shared__ DT s_alpha;
-        __shared__ int s_break;
         if (t == 0) {
             DT pqt = s_sum[0];
             for (int i = 0; i < 6; ++i) {
@@ -280,53 +352,30 @@ __global__ void __launch_bounds__(PCG_T) k_pcg(PcgArgs a)
         __syncthreads();
         if (s_break) break;
         const float alpha = (float)s_alpha;
-        for (int e = 12 * r0 + t; e < 12 * r1; e += PCG_T) {
-            const float pv = pnew[e];
-            a.d[e] += alpha * pv;
-            a.r[e] -= alpha * a.q[e];
+        for (int i = t; i < rows * 12; i += PCG_T) {
+            ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
+            rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
         }
         __syncthreads();
-        DT rz2 = 0, rr2 = 0;
-        for (int j0 = r0; j0 < r1; j0 += ROWS_PER_PASS) {
-            const int j = j0 + grp;
-            const bool act = in_grp && j < r1;
-            float zp = 0.f;
-            if (act) {
-                const float4 mv = *reinterpret_cast<const float4 *>(a.minv + (size_t)j * 144 + rr * 12 + 4 * cg);
-                const float4 rv = *reinterpret_cast<const float4 *>(a.r + 12 * j + 4 * cg);
-                zp = mv.x * rv.x + mv.y * rv.y + mv.z * rv.z + mv.w * rv.w;
-            }
-            __shared__ float s_z2[ROWS_PER_PASS][12][3];
-            if (in_grp) s_z2[grp][rr][cg] = zp;
-            __syncthreads();
-            if (act && cg == 0) {
-                const float zz = s_z2[grp][rr][0] + s_z2[grp][rr][1] + s_z2[grp][rr][2];
-                const float rv = a.r[12 * j + rr];
-                a.z[12 * j + rr] = zz;
-                rz2 += (DT)rv * (DT)zz;
-                rr2 += (DT)rv * (DT)rv;
-            }
-            __syncthreads();
-        }
         {
+            DT rz2 = 0, rr2 = 0;
+            precond(rz2, rr2);
             DT vv[2] = {rz2, rr2};
             block_sum_n<DT, 2>(vv, s_red, s_blk);
         }
         if (t == 0) {
             DT w1 = s_blk[0], w2 = s_blk[1];
             if (blockIdx.x == 0) {
-                float rp[6];
                 for (int i = 0; i < 6; ++i) {
-                    a.d[P + i] += alpha * s_pp[i];
-                    rp[i] = a.r[P + i] - alpha * s_qp[i];
-                    a.r[P + i] = rp[i];
+                    s_dpose[i] = __fmaf_rn(alpha, s_pp[i], s_dpose[i]);
+                    s_rpose[i] = __fmaf_rn(-alpha, s_qp[i], s_rpose[i]);
                 }
                 for (int i = 0; i < 6; ++i) {
                     float zi = 0.f;
-                    for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * rp[k];
+                    for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
                     a.z[P + i] = zi;
-                    w1 += (DT)rp[i] * (DT)zi;
-                    w2 += (DT)rp[i] * (DT)rp[i];
+                    w1 += (DT)s_rpose[i] * (DT)zi;
+                    w2 += (DT)s_rpose[i] * (DT)s_rpose[i];
                 }
             }
             part0[blockIdx.x * ED_PCG_PART + 0] = (double)w1;
@@ -342,6 +391,9 @@ __global__ void __launch_bounds__(PCG_T) k_pcg(PcgArgs a)
         if (t < 6) s_ppold[t] = s_pp[t];
         __syncthreads();
     }
+    // solution of the CTA's rows (and of the pose: CTA 0)
+    for (int i = t; i < rows * 12; i += PCG_T) a.d[12 * r0 + i] = ds[i];
+    if (blockIdx.x == 0 && t < 6) a.d[P + t] = s_dpose[t];
     if (blockIdx.x == 0 && t == 0 && a.stats) {
         a.stats->pcg_iters = it;
         a.stats->pcg_res0 = (double)s_res0;
@@ -349,59 +401,92 @@ __global__ void __launch_bounds__(PCG_T) k_pcg(PcgArgs a)
     }
 }
 
-ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st)
+// balanced row partition (by block count) and the shared-memory plan; called
+// at graph build with the row pointer copied to the host
+ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st)
 {
     const int m = ctx->m;
+    int grid = ctx->num_sms;
+    if (grid > ED_MAX_PCG_GRID) grid = ED_MAX_PCG_GRID;
+    if (grid > m) grid = m;
+    const int nnzb = row_ptr_host[m];
+    int rows_start[ED_MAX_PCG_GRID + 1];
+    int r = 0;
+    rows_start[0] = 0;
+    for (int c = 1; c < grid; ++c) {
+        const long want = (long)nnzb * c / grid;
+        while (r < m && row_ptr_host[r] < want) ++r;
+        if (r < rows_start[c - 1] + 1) r = rows_start[c - 1] + 1;   // at least one row per CTA
+        if (r > m - (grid - c)) r = m - (grid - c);
+        rows_start[c] = r;
+    }
+    rows_start[grid] = m;
+    int max_rows = 0, max_blk = 0;
+    for (int c = 0; c < grid; ++c) {
+        const int rw = rows_start[c + 1] - rows_start[c];
+        const int nbk = row_ptr_host[rows_start[c + 1]] - row_ptr_host[rows_start[c]];
+        if (rw > max_rows) max_rows = rw;
+        if (nbk > max_blk) max_blk = nbk;
+    }
+    const PcgSmem base = pcg_smem_layout(max_rows, max_blk, 0);
+    const size_t base_bytes = base.total * sizeof(float);
+    if (base_bytes > PCG_SMEM_MAX) return ED_ERR_CAPACITY;
+    int ncache = (int)((PCG_SMEM_MAX - base_bytes) / (144 * sizeof(float)));
+    if (ncache > max_blk) ncache = max_blk;
+    const PcgSmem full = pcg_smem_layout(max_rows, max_blk, ncache);
+    ctx->pcg_grid = grid;
+    ctx->pcg_cache = ncache;
+    ctx->pcg_smem = full.total * sizeof(float);
+    ctx->pcg_max_rows = max_rows;
+    ctx->pcg_max_blk = max_blk;
+    ED_CUDA_TRY(cudaMemcpyAsync(ctx->pcg_rows, rows_start, sizeof(int) * (grid + 1), cudaMemcpyHostToDevice, st));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->pcg_smem));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->pcg_smem));
+    ED_CUDA_TRY(cudaStreamSynchronize(st));   // rows_start lives on this stack frame
+    return ED_OK;
+}
+
+ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st)
+{
     const size_t P = ctx->vec_stride;
     const bool mixed = prm->precision == ED_PRECISION_MIXED;
-    if (ctx->pcg_grid == 0) {
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<double>, PCG_T, 0) != cudaSuccess || occ < 1)
-            return ED_ERR_CUDA;
-        int occ2 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_pcg<float>, PCG_T, 0) != cudaSuccess || occ2 < 1)
-            return ED_ERR_CUDA;
-        if (occ2 < occ) occ = occ2;
-        int g = ctx->num_sms;   // one CTA per SM: fewest barrier arrivals
-        if (g > ED_MAX_PCG_GRID) g = ED_MAX_PCG_GRID;
-        ctx->pcg_grid = g;
-    }
-    // fewer CTAs than rows is fine; more CTAs than rows leaves some idle
-    int grid = ctx->pcg_grid;
-    const int rows_needed = ed_div_up(m, 1);
-    if (grid > rows_needed) grid = rows_needed;
+    if (ctx->pcg_grid <= 0) return ED_ERR_STATE;
     PcgArgs a;
-    a.m = m;
+    a.m = ctx->m;
     a.n_iter = prm->n_pcg;
     a.tol = prm->pcg_tol;
     a.row_ptr = ctx->row_ptr;
     a.col = ctx->col;
+    a.cta_rows = ctx->pcg_rows;
+    a.n_cache = ctx->pcg_cache;
+    a.max_rows = ctx->pcg_max_rows;
+    a.max_blk = ctx->pcg_max_blk;
     a.bsr = ctx->bsr;
     a.pnode = ctx->pnode;
     a.minv = ctx->minv;
     a.pose_blk = ctx->pose_blk;
     a.grad = ctx->grad;
     a.d = ctx->vec;
-    a.r = ctx->vec + P;
     a.z = ctx->vec + 2 * P;
     a.p0 = ctx->vec + 3 * P;
     a.p1 = ctx->vec + 4 * P;
-    a.q = ctx->vec + 5 * P;
     a.part = ctx->pcg_part;
     a.bar = (unsigned *)(ctx->misc + MI_BAR);
     a.status = ctx->misc + MI_STATUS;
     a.stats = stats;
     // every vector is read as float4 rows: 16-byte alignment is required
-    const float *vv[6] = {a.d, a.r, a.z, a.p0, a.p1, a.q};
-    for (int i = 0; i < 6; ++i)
+    const float *vv[4] = {a.d, a.z, a.p0, a.p1};
+    for (int i = 0; i < 4; ++i)
         if ((uintptr_t)vv[i] & 15) return ED_ERR_STATE;
     if (((uintptr_t)a.bsr & 15) || ((uintptr_t)a.minv & 15)) return ED_ERR_STATE;
     ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_BAR, 0, 2 * sizeof(int), st));
     void *args[] = {&a};
     ed_tm_begin(ctx, ED_KERNEL_PCG, st);
     ed_note_launch();
-    cudaError_t e = mixed ? cudaLaunchCooperativeKernel((const void *)k_pcg<double>, grid, PCG_T, args, 0, st)
-                          : cudaLaunchCooperativeKernel((const void *)k_pcg<float>, grid, PCG_T, args, 0, st);
+    cudaError_t e = mixed ? cudaLaunchCooperativeKernel((const void *)k_pcg<double>, ctx->pcg_grid, PCG_T, args,
+                                                        ctx->pcg_smem, st)
+                          : cudaLaunchCooperativeKernel((const void *)k_pcg<float>, ctx->pcg_grid, PCG_T, args,
+                                                        ctx->pcg_smem, st);
     ed_tm_end(ctx, ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: PCG launch failed: %s\n", cudaGetErrorString(e));

@@ -193,37 +193,89 @@ def test_step_full_size():
 
 
 # ----------------------------------------------------------------------------
-# whole solve (small workload): 5 GN x 10 PCG against the oracle trajectory
+# whole solve (small workload): 5 GN x 10 PCG
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_trajectory_small(precision):
+def _gpu_trajectory(s, G, precision):
     torch, E = _torch(), _E()
-    s = C.scene(SMALL)
-    G = C.gpu_setup(s)
     ctx = G["ctx"]
-    m = G["graph"].m
     x = ctx.identity_x()
     xm = x.double().clone()
     pose = torch.tensor(s.pose_prior, dtype=torch.float64, device="cuda")
     prm = C.solver(s, precision=precision)
+    wpos = torch.empty((s.N, 4), dtype=torch.float32, device="cuda")
+    wnrm = torch.empty_like(wpos)
+    pix = torch.empty(s.N, dtype=torch.int32, device="cuda")
+    ctx.set_debug(wpos, wnrm, pix)
     st = E.new_stats(s.cfg.n_gn)
+    states = []
     for it in range(s.cfg.n_gn):
+        xin = (xm if precision else x).cpu().numpy().astype(np.float64)
+        pin = pose.cpu().numpy().copy()
         ctx.gn_step(G["frame"], prm, x, pose, x_master=xm, stats=st[it:it + 1])
-    stats = E.read_stats(st)
+        states.append(dict(x=xin, xf=x.cpu().numpy() if not precision else None, pose=pin, pix=pix.cpu().numpy(),
+                           wpos=wpos.cpu().numpy(), wnrm=wnrm.cpu().numpy()))
+    ctx.set_debug(None, None, None)
+    final = dict(x=(xm if precision else x).cpu().numpy().astype(np.float64), pose=pose.cpu().numpy())
+    return states, E.read_stats(st), final, prm
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_trajectory_locked_small(precision):
+    """Every GN step of the GPU trajectory against the oracle step taken from
+    the GPU's own state and association: strict parity at each iteration."""
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s)
+    states, stats, final, prm = _gpu_trajectory(s, G, precision)
     P = C.oracle_problem_from_gpu(s, G)
-    xr, pr, hist, stt = oracle.gn_solve(P, P.identity_x(), s.pose_prior, s.cfg.n_gn, s.cfg.n_pcg, jitter=prm.jitter)
-    assert stt == 0 and all(t["status"] == 0 for t in stats)
+    nm = G["nmap"].cpu().numpy()
+    m = P.m
+    for it, stt in enumerate(states):
+        assert stats[it]["status"] == 0
+        ref_pix = oracle.associate_f32(stt["wpos"], stt["wnrm"], s.tgt_depth, nm, s.intr)
+        assert np.array_equal(ref_pix, stt["pix"]), it
+        Q = oracle.NormalEq(P, stt["x"], stt["pose"], pix_in=stt["pix"])
+        assert stats[it]["energy"] == pytest.approx(Q.energy, rel=C.TOL_E), it
+        d, _, _, _ = Q.pcg(-Q.g, prm.n_pcg, jitter=prm.jitter)
+        x_ref = stt["x"] + d[:12 * m].reshape(m, 12)
+        x_next = states[it + 1]["x"] if it + 1 < len(states) else final["x"]
+        p_next = states[it + 1]["pose"] if it + 1 < len(states) else final["pose"]
+        err = np.abs(x_next - x_ref) / np.maximum(1.0, np.abs(x_ref))
+        assert err.max() <= C.TOL_X, (it, err.max())
+        assert np.abs(p_next - (stt["pose"] + d[12 * m:])).max() <= C.TOL_X, it
+
+
+def test_trajectory_free_small():
+    """The GPU trajectory against the oracle's own FP64 trajectory.  Both take
+    their gate decisions in FP32 on their own warped points, so a point lying on
+    a gate boundary can be decided differently; every such flip is counted and
+    must be rare, and the trajectories must stay close."""
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s)
+    states, stats, final, prm = _gpu_trajectory(s, G, 0)
+    P = C.oracle_problem_from_gpu(s, G)
+    x, pose = P.identity_x(), np.asarray(s.pose_prior, dtype=np.float64).copy()
+    m = P.m
+    flips, E_ref = [], []
+    for it, stt in enumerate(states):
+        Q = oracle.NormalEq(P, x, pose)
+        flips.append(int(np.count_nonzero(Q.pix != stt["pix"])))
+        E_ref.append(Q.energy)
+        d, _, _, _ = Q.pcg(-Q.g, prm.n_pcg, jitter=prm.jitter)
+        x = x + d[:12 * m].reshape(m, 12)
+        pose = pose + d[12 * m:]
     E_gpu = np.array([t["energy"] for t in stats])
-    E_ref = hist[:, :5].sum(1)
-    flips = np.array([t["n_valid"] for t in stats]) - hist[:, 5]
-    print("energies", E_gpu, E_ref, "valid-count differences", flips)
-    assert abs(E_gpu[0] - E_ref[0]) <= C.TOL_E * E_ref[0]
-    x_gpu = (xm if precision else x).cpu().numpy()
-    err = np.abs(x_gpu - xr) / np.maximum(1.0, np.abs(xr))
-    print("max rel node-parameter error", err.max(), "pose error", np.abs(pose.cpu().numpy() - pr).max())
-    assert err.max() <= C.TOL_X
-    assert np.abs(pose.cpu().numpy() - pr).max() <= C.TOL_X
+    err = np.abs(final["x"] - x) / np.maximum(1.0, np.abs(x))
+    print("association flips per iteration", flips, "of", [t["n_valid"] for t in stats])
+    print("energies gpu", E_gpu, "oracle", np.array(E_ref))
+    print("final max rel node-parameter error", err.max(), "pose error", np.abs(final["pose"] - pose).max())
+    assert flips[0] == 0 and E_gpu[0] == pytest.approx(E_ref[0], rel=C.TOL_E)
+    assert all(f <= 1e-3 * t["n_valid"] for f, t in zip(flips, stats))
+    assert np.allclose(E_gpu, E_ref, rtol=1e-3)
+    if sum(flips) == 0:
+        assert err.max() <= C.TOL_X
+    else:
+        assert err.max() <= 1e-2
 
 
 # ----------------------------------------------------------------------------
