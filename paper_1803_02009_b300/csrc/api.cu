@@ -77,11 +77,7 @@ size_t carve(ed_context *c, char *base)
     c->chunk_cnt1 = k.take<int>(nnzb);
     c->chunk_start1 = k.take<int>(nnzb + 1);
     c->max_chunks = (int)chunks;
-    {
-        const size_t slots = ((chunks + 31) / 32) * 32 * (size_t)ED_CHUNK;
-        c->ent_geo = k.take<float4>(slots);
-        c->ent_pt = k.take<int>(slots);
-    }
+    c->ent_geo = k.take<float4>(nent);
     c->partials = k.take<float>((size_t)ED_PART_STRIDE * chunks);
     c->bsr = k.take<float>(nnzb * 144);
     c->grad = k.take<float>(P);

@@ -12,8 +12,8 @@
 #define ED_K 4                 // nearest nodes per point (Eq. 1)
 #define ED_MAX_KG 8            // node-graph neighbours
 #define ED_HARD_MAX_NODES 16384
-#define ED_CHUNK 64            // assembly entries per chunk
-#define ED_PART_STRIDE 84      // floats per assembly partial (60 moments, or 12 + 72)
+#define ED_CHUNK 128           // assembly entries per chunk (4 per lane of a warp)
+#define ED_PART_STRIDE 96      // floats per chunk partial (60 moments, or 12 + 72), chunk-major
 #define ED_K1_THREADS 256
 #define ED_K1_PART 32          // doubles per point-kernel CTA partial
 #define ED_PCG_PART 8          // doubles per PCG CTA partial
@@ -84,8 +84,7 @@ struct ed_context {
     int max_chunks;
     int n_chunks0;           // role-0 chunks
     int chunk_base1;         // first role-1 chunk (n_chunks0 rounded up to 32: warp-aligned slots)
-    float4 *ent_geo;         // [chunk slots] (v - g_j, w_s w_t) or (v - g_j, w_s), warp-interleaved
-    int *ent_pt;             // [chunk slots] point index, same layout
+    float4 *ent_geo;         // [10 N] per sorted entry: (v_i - g_j, w_s w_t)
     float *partials;         // [ED_PART_STRIDE][max_chunks]
     // normal equations
     float *bsr;              // [max_nnzb][144]

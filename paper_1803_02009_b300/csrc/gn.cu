@@ -153,138 +153,137 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
 }
 
 // ---------------------------------------------------------------------------
-// assembly: one thread per chunk of <= ED_CHUNK points of one upper block (j, l)
+// assembly: one warp per chunk of <= ED_CHUNK entries of one upper block (j, l)
 // role 0: the 60 independent entries of sum c (nb nb^T) (x) (d^ d^T),
 //         d^ = [v - g_j; 1], c = w_s w_t  (every data-term block of J^T J)
 // role 1 (diagonal blocks): J^T r (12) and the pose-node block (6 x 12)
-// Per entry the geometry (d, c) is read from warp-interleaved slots written at
-// graph build (coalesced); only the residual record of the point is gathered.
+// The per-entry geometry (d, c) was written at graph build; the residual
+// record of the point is gathered (entries of a chunk are in point order).
 // ---------------------------------------------------------------------------
 
-// role 0, one thread per (chunk, half): half h accumulates the 30 moments of
-// nn[3h .. 3h+2] x dd[0 .. 9]; lanes of a warp take 32 consecutive chunks
-__global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
-                                                   const float4 *__restrict__ geo, const int *__restrict__ pt,
-                                                   const float4 *__restrict__ rec0, float *__restrict__ part)
+// Recursive halving of NV float2 values per lane across the warp (fixed order,
+// so the result is deterministic): after the step with offset o every lane
+// keeps the half selected by bit o of its lane index and adds the partner's
+// copy of it.  At the end lane k holds the sums of float2 values
+// (NV/32) k ... (NV/32) k + NV/32 - 1.
+template <int NV>
+__device__ __forceinline__ void warp_halving2(float2 (&v)[NV])
 {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    const int h = (id >> 5) & 1;
-    const int c = (id >> 6) * 32 + (id & 31);
-    if (c >= nchunks) return;
-    const int n = chunks[c].z;
-    const long base = (long)(c >> 5) * (32 * ED_CHUNK) + (c & 31);
-    float M[30];
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < 30; ++k) M[k] = 0.f;
-    // entries in batches of 4: the 4 slot loads, then the 4 record gathers, are
-    // in flight together
-    for (int e0 = 0; e0 < n; e0 += 4) {
-        float4 gd[4], b[4];
-        int ip[4];
+    for (int o = 16, n = NV; o > 0; o >>= 1, n >>= 1) {
+        const bool hi = (lane & o) != 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = e0 + u < n;
-            gd[u] = ok ? __ldg(geo + base + 32L * (e0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ip[u] = ok ? __ldg(pt + base + 32L * (e0 + u)) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = ip[u] >= 0 ? __ldg(rec0 + ip[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float cf = gd[u].w;   // 0 for the padding of the last batch
-            const float d0 = gd[u].x, d1 = gd[u].y, d2 = gd[u].z;
-            float nn[3];
-            if (h == 0) {
-                nn[0] = cf * b[u].x * b[u].x;
-                nn[1] = cf * b[u].x * b[u].y;
-                nn[2] = cf * b[u].x * b[u].z;
-            } else {
-                nn[0] = cf * b[u].y * b[u].y;
-                nn[1] = cf * b[u].y * b[u].z;
-                nn[2] = cf * b[u].z * b[u].z;
-            }
-            const float dd[10] = {d0 * d0, d0 * d1, d0 * d2, d0, d1 * d1, d1 * d2, d1, d2 * d2, d2, 1.0f};
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int k = 0; k < 10; ++k) M[10 * a + k] += nn[a] * dd[k];
+        for (int k = 0; k < n / 2; ++k) {
+            const float2 keep = hi ? v[k + n / 2] : v[k];
+            const float2 give = hi ? v[k] : v[k + n / 2];
+            float2 recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, give.x, o);
+            recv.y = __shfl_xor_sync(0xffffffffu, give.y, o);
+            v[k] = __fadd2_rn(keep, recv);
         }
     }
-#pragma unroll
-    for (int k = 0; k < 30; ++k) part[(long)(30 * h + k) * max_chunks + c] = M[k];
 }
 
-// role 1 (diagonal blocks), one thread per (chunk, third): third 0 accumulates
-// J^T r (12) and pose-node rows 0-1, thirds 1 and 2 rows 2-3 and 4-5 (24 each)
+// role 0: one warp per chunk of <= 128 entries of one upper block (j, l); lane
+// k takes entries k, k + 32, k + 64, k + 96 and forms the 60 moments
+// c (nb nb^T) (x) (d^ d^T) of its entries (paired FP32 FMA), the warp then sums
+// them by recursive halving: lane k owns moments 2k and 2k + 1
+__global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
+                                                   const float4 *__restrict__ geo, const uint32_t *__restrict__ ent,
+                                                   const float4 *__restrict__ rec0, float *__restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= nchunks) return;
+    const int4 ch = chunks[c];
+    float4 gd[4], b[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int e = lane + 32 * h;
+        gd[h] = e < ch.z ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);   // w = 0: no contribution
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int e = lane + 32 * h;
+        b[h] = e < ch.z ? __ldg(rec0 + (__ldg(ent + ch.y + e) >> 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float2 v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float cf = gd[h].w;
+        const float d0 = gd[h].x, d1 = gd[h].y, d2 = gd[h].z;
+        const float bx = cf * b[h].x, by = cf * b[h].y, bz = cf * b[h].z;
+        const float nn[6] = {bx * b[h].x, bx * b[h].y, bx * b[h].z, by * b[h].y, by * b[h].z, bz * b[h].z};
+        // d^ d^T upper triangle in pairs: (d0 d0, d0 d1) (d0 d2, d0) (d1 d1, d1 d2) (d1, d2 d2) (d2, 1)
+        const float2 dd[5] = {make_float2(d0 * d0, d0 * d1), make_float2(d0 * d2, d0), make_float2(d1 * d1, d1 * d2),
+                              make_float2(d1, d2 * d2), make_float2(d2, 1.0f)};
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const float2 na = make_float2(nn[a], nn[a]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) v[5 * a + q] = __ffma2_rn(na, dd[q], v[5 * a + q]);
+        }
+    }
+    warp_halving2<32>(v);
+    if (2 * lane < 60)   // chunk-major partials: 2 consecutive floats per lane, coalesced
+        reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[lane] = v[0];
+}
+
+// role 1 (diagonal blocks): one warp per chunk; per entry J^T r (12) and the
+// pose-node block (6 x 12) of node j, summed by recursive halving (128 slots,
+// 84 used: 0..11 J^T r, 12 + 12 t + p pose-node (t, p)); lane k owns 4k..4k+3
 __global__ void __launch_bounds__(128) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
                                                    int max_chunks, const float4 *__restrict__ geo,
-                                                   const int *__restrict__ pt, const float4 *__restrict__ rec0,
+                                                   const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
                                                    const float4 *__restrict__ rec1, const double *__restrict__ pose,
                                                    float *__restrict__ part)
 {
     __shared__ ed_pose_f P;
     if (threadIdx.x == 0) ed_pose_eval(pose, P);
     __syncthreads();
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    const int h = (id >> 5) % 3;
-    const int c = c_begin + (id / 96) * 32 + (id & 31);
+    const int lane = threadIdx.x & 31;
+    const int c = c_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (c >= c_begin + nchunks) return;
-    const int n = chunks[c].z;
-    const long base = (long)(c >> 5) * (32 * ED_CHUNK) + (c & 31);
+    const int4 ch = chunks[c];
     const float *R = P.R;
-    float acc[36];
+    float2 v[64];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) acc[k] = 0.f;
-    for (int e0 = 0; e0 < n; e0 += 4) {
-        float4 gd[4], bb[4], qq[4];
-        int ip[4];
+    for (int k = 0; k < 64; ++k) v[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = e0 + u < n;
-            gd[u] = ok ? __ldg(geo + base + 32L * (e0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ip[u] = ok ? __ldg(pt + base + 32L * (e0 + u)) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            bb[u] = ip[u] >= 0 ? __ldg(rec0 + ip[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            qq[u] = ip[u] >= 0 ? __ldg(rec1 + ip[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float4 b = bb[u], jq = qq[u];
-            const float ws = gd[u].w;   // 0 for the padding of the last batch
-            const float dh[4] = {gd[u].x, gd[u].y, gd[u].z, 1.0f};
+    for (int h = 0; h < 4; ++h) {
+        const int e = lane + 32 * h;
+        if (e < ch.z) {
+            const float4 gd = __ldg(geo + ch.y + e);
+            const int i = (int)(__ldg(ent + ch.y + e) >> 4);
+            const float4 b = __ldg(rec0 + i);
+            const float4 jq = __ldg(rec1 + i);
+            const float ws = sqrtf(gd.w);   // diagonal entries store w_s * w_s
+            const float2 dlo = make_float2(gd.x, gd.y), dhi = make_float2(gd.z, 1.0f);
             const float nb[3] = {ws * b.x, ws * b.y, ws * b.z};
             // d r / d pose: (angles, R nb_s) with nb_s = sqrt(w) R^T n
-            float jp[2];
-            if (h == 0) {
-                jp[0] = jq.x;
-                jp[1] = jq.y;
-            } else if (h == 1) {
-                jp[0] = jq.z;
-                jp[1] = R[0] * b.x + R[1] * b.y + R[2] * b.z;
-            } else {
-                jp[0] = R[3] * b.x + R[4] * b.y + R[5] * b.z;
-                jp[1] = R[6] * b.x + R[7] * b.y + R[8] * b.z;
-            }
+            const float jp[6] = {jq.x, jq.y, jq.z, R[0] * b.x + R[1] * b.y + R[2] * b.z,
+                                 R[3] * b.x + R[4] * b.y + R[5] * b.z, R[6] * b.x + R[7] * b.y + R[8] * b.z};
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < 3; ++r) {
+                const float2 g2 = make_float2(b.w * nb[r], b.w * nb[r]);
+                v[2 * r] = __ffma2_rn(g2, dlo, v[2 * r]);
+                v[2 * r + 1] = __ffma2_rn(g2, dhi, v[2 * r + 1]);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float av = nb[r] * dh[k];
-                    if (h == 0) acc[24 + 4 * r + k] += b.w * av;
-                    acc[4 * r + k] += jp[0] * av;
-                    acc[12 + 4 * r + k] += jp[1] * av;
+                for (int t = 0; t < 6; ++t) {
+                    const float s2 = jp[t] * nb[r];
+                    const float2 c2 = make_float2(s2, s2);
+                    v[6 + 6 * t + 2 * r] = __ffma2_rn(c2, dlo, v[6 + 6 * t + 2 * r]);
+                    v[6 + 6 * t + 2 * r + 1] = __ffma2_rn(c2, dhi, v[6 + 6 * t + 2 * r + 1]);
                 }
+            }
         }
     }
-    // component order of the role-1 partials: 0..11 J^T r, 12 + 12 t + p pose-node (t, p)
-    if (h == 0) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) part[(long)k * max_chunks + c] = acc[24 + k];
-    }
-#pragma unroll
-    for (int k = 0; k < 24; ++k) part[(long)(12 + 24 * h + k) * max_chunks + c] = acc[k];
+    warp_halving2<64>(v);
+    if (4 * lane < 84)
+        reinterpret_cast<float4 *>(part + (long)c * ED_PART_STRIDE)[lane] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
 }
 
 // ---------------------------------------------------------------------------
@@ -315,19 +314,21 @@ __device__ __forceinline__ int sym4(int a, int b)
     return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
 }
 
-// sum of the chunk partials of one component (two-sum compensated when mixed)
+// sum of the chunk partials of one component (two-sum compensated when mixed);
+// partials are chunk-major, ED_PART_STRIDE floats per chunk
 __device__ __forceinline__ float sum_parts(const float *part, int comp, int max_chunks, int c0, int n, int mixed)
 {
-    const float *p = part + (long)comp * max_chunks + c0;
+    (void)max_chunks;
+    const float *p = part + (long)c0 * ED_PART_STRIDE + comp;
     float s = 0.f;
     if (!mixed) {
 #pragma unroll 4
-        for (int k = 0; k < n; ++k) s += p[k];
+        for (int k = 0; k < n; ++k) s += p[(long)k * ED_PART_STRIDE];
         return s;
     }
     float err = 0.f;
     for (int k = 0; k < n; ++k) {
-        const float a = p[k];
+        const float a = p[(long)k * ED_PART_STRIDE];
         const float t = s + a;
         const float bp = t - s;
         err += (s - (t - bp)) + (a - bp);
@@ -764,13 +765,12 @@ extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_so
         const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
         if (n0 > 0) {
-            k_assemble0<<<ed_div_up(ed_div_up(n0, 32) * 64, 128), 128, 0, st>>>(
-                ctx->chunks, n0, ctx->max_chunks, ctx->ent_geo, ctx->ent_pt, ctx->rec0, ctx->partials); ed_note_launch();
+            k_assemble0<<<ed_div_up(n0, 4), 128, 0, st>>>(ctx->chunks, n0, ctx->max_chunks, ctx->ent_geo, ctx->ent_val,
+                                                           ctx->rec0, ctx->partials); ed_note_launch();
         }
         if (n1 > 0) {
-            k_assemble1<<<ed_div_up(ed_div_up(n1, 32) * 96, 128), 128, 0, st>>>(
-                ctx->chunks, base1, n1, ctx->max_chunks, ctx->ent_geo, ctx->ent_pt, ctx->rec0, ctx->rec1, pose,
-                ctx->partials); ed_note_launch();
+            k_assemble1<<<ed_div_up(n1, 4), 128, 0, st>>>(ctx->chunks, base1, n1, ctx->max_chunks, ctx->ent_geo,
+                                                           ctx->ent_val, ctx->rec0, ctx->rec1, pose, ctx->partials); ed_note_launch();
         }
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();

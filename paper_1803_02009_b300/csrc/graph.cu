@@ -171,7 +171,9 @@ __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const in
 }
 
 // phase ph: a point bids for its cell when its FP32 key to every node chosen
-// in earlier phases (cells within +-2) is >= r*r; the lowest index wins
+// in earlier phases (cells within +-2) is >= r*r; the lowest index wins.
+// Five lanes per point (lanes 5g .. 5g+4 of a warp, six points per warp) each
+// check one z layer of the 5x5x5 neighbourhood; the group votes.
 __global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__restrict__ bucket,
                                const int *__restrict__ start, int phase, const int *__restrict__ misc,
                                const float *__restrict__ fmisc, const int *__restrict__ cell_of,
@@ -180,32 +182,39 @@ __global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__rest
     const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1], nz = misc[MI_DIMS + 2];
     const float r2 = fmisc[MF_R2];
     const int e0 = start[phase], e1 = start[phase + 1];
-    for (int e = e0 + blockIdx.x * blockDim.x + threadIdx.x; e < e1; e += gridDim.x * blockDim.x) {
-        const int i = bucket[e];
-        const int c = cell_of[i];
-        const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-        const float4 p = pos[i];
+    const int lane = threadIdx.x & 31, grp = lane / 5, sub = lane % 5;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int wbase = e0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 6; wbase < e1; wbase += warps * 6) {
+        const int e = wbase + grp;
+        const bool act = grp < 6 && e < e1;
         bool ok = true;
-        // 124 neighbour cells (the own cell belongs to this phase); the loads of
-        // one z layer are issued together, then the few nodes found are checked
-        for (int dz = -2; dz <= 2 && ok; ++dz) {
-            const int az = cz + dz;
-            if (az < 0 || az >= nz) continue;
-            int q[25];
+        int i = -1, c = 0;
+        if (act) {
+            i = bucket[e];
+            c = cell_of[i];
+            const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+            const int dz = sub - 2, az = cz + dz;
+            if (az >= 0 && az < nz) {
+                const float4 p = pos[i];
+                int q[25];
 #pragma unroll
-            for (int k = 0; k < 25; ++k) {
-                const int ay = cy + k / 5 - 2, ax = cx + k % 5 - 2;
-                const bool in = ay >= 0 && ay < ny && ax >= 0 && ax < nx && !(dz == 0 && k == 12);
-                q[k] = in ? cell_pick[ax + nx * (ay + ny * az)] : NO_BID;   // earlier phases: final
-            }
+                for (int k = 0; k < 25; ++k) {
+                    const int ay = cy + k / 5 - 2, ax = cx + k % 5 - 2;
+                    const bool in = ay >= 0 && ay < ny && ax >= 0 && ax < nx && !(dz == 0 && k == 12);
+                    q[k] = in ? cell_pick[ax + nx * (ay + ny * az)] : NO_BID;   // earlier phases: final
+                }
 #pragma unroll
-            for (int k = 0; k < 25; ++k) {
-                if (q[k] == NO_BID) continue;
-                const float4 g = pos[q[k]];
-                if (ed_key(p.x, p.y, p.z, g.x, g.y, g.z) < r2) ok = false;
+                for (int k = 0; k < 25; ++k) {
+                    if (q[k] == NO_BID) continue;
+                    const float4 g = pos[q[k]];
+                    if (ed_key(p.x, p.y, p.z, g.x, g.y, g.z) < r2) ok = false;
+                }
             }
         }
-        if (ok) atomicMin(&cell_pick[c], i);
+        // the group's verdict: every one of its five lanes found no close node
+        const unsigned bad = __ballot_sync(0xffffffffu, act && !ok);
+        const unsigned gmask = 0x1fu << (5 * grp);
+        if (act && sub == 0 && !(bad & gmask)) atomicMin(&cell_pick[c], i);
     }
 }
 
@@ -587,27 +596,19 @@ __global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *_
     }
 }
 
-// per-entry geometry, fixed for the frame: d = v_i - g_j and w_s w_t (role 0)
-// or w_s (role 1); slot of entry k of chunk c = (c / 32) 32 CH + 32 k + c % 32,
-// so that a warp's 32 chunks read 32 consecutive slots per entry
-__global__ void k_entry_geo(const int4 *__restrict__ chunks, int nchunks, const uint32_t *__restrict__ ent,
+// per-entry geometry, fixed for the frame: geo[e] = (v_i - g_j, w_s w_t) for the
+// entry e (point i, slots s, t) of upper block (j, l)
+__global__ void k_entry_geo(int ne, const uint32_t *__restrict__ key, const uint32_t *__restrict__ ent,
                             const int *__restrict__ brow, const float4 *__restrict__ pos, const float *__restrict__ wts,
-                            const float4 *__restrict__ g, float4 *__restrict__ geo, int *__restrict__ pt)
+                            const float4 *__restrict__ g, float4 *__restrict__ geo)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nchunks) return;
-    const int4 ch = chunks[c];
-    const float4 gj = g[brow[ch.x]];
-    const long base = (long)(c >> 5) * (32 * ED_CHUNK) + (c & 31);
-    for (int k = 0; k < ch.z; ++k) {
-        const uint32_t v = ent[ch.y + k];
-        const int i = (int)(v >> 4), sr = (v >> 2) & 3, sc = v & 3;
-        const float4 p = pos[i];
-        const float ws = wts[4 * i + sr];
-        const float w = ch.w == 0 ? ws * wts[4 * i + sc] : ws;
-        geo[base + 32L * k] = make_float4(p.x - gj.x, p.y - gj.y, p.z - gj.z, w);
-        pt[base + 32L * k] = i;
-    }
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const uint32_t v = ent[e];
+    const int i = (int)(v >> 4), sr = (v >> 2) & 3, sc = v & 3;
+    const float4 gj = g[brow[key[e]]];
+    const float4 p = pos[i];
+    geo[e] = make_float4(p.x - gj.x, p.y - gj.y, p.z - gj.z, wts[4 * i + sr] * wts[4 * i + sc]);
 }
 
 // ---------------------------------------------------------------------------
@@ -670,7 +671,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_phase_scan<<<1, 32, 0, st>>>(pcnt, pstart, pfill); ed_note_launch();
         k_phase_scatter<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pstart, pfill, bucket); ed_note_launch();
         ED_LAUNCH_CHECK();
-        const int pick_grid = min(ed_div_up(N / 27 + 1, 128), 4 * ctx->num_sms);
+        const int pick_grid = min(ed_div_up((N / 27 + 1) * 32 / 6 + 32, 128), 8 * ctx->num_sms);
         for (int ph = 0; ph < 27; ++ph) {
             k_poisson_pick<<<pick_grid, 128, 0, st>>>(P4, bucket, pstart, ph, ctx->misc, ctx->fmisc, ctx->cell_of,
                                                       ctx->cell_pick); ed_note_launch();
@@ -781,10 +782,8 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             ED_CUDA_TRY(cudaMemsetAsync(ctx->chunks + nc01[0], 0, sizeof(int4) * (base1 - nc01[0]), st));
         k_chunk_fill<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->ent_start, ctx->brow, ctx->col,
                                                            ctx->chunk_start, ctx->chunk_start1, ctx->chunks); ed_note_launch();
-        if (nchunks > 0) {
-            k_entry_geo<<<ed_div_up(nchunks, 128), 128, 0, st>>>(ctx->chunks, nchunks, ctx->ent_val, ctx->brow, P4,
-                                                                   graph->weights, G4, ctx->ent_geo, ctx->ent_pt); ed_note_launch();
-        }
+        k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, P4, graph->weights,
+                                                         G4, ctx->ent_geo); ed_note_launch();
         ED_LAUNCH_CHECK();
         int cnt3[2] = {nnzb, 0};
         ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, cnt3, sizeof(cnt3), cudaMemcpyHostToDevice, st));
