@@ -32,7 +32,7 @@ enum {
     MI_NCHUNK = 15,
     MI_BBOX = 16,        // 16..21 ordered-int bbox (min xyz, max xyz)
     MI_PHASE_BASE = 24,  // running node count during sampling
-    MI_BAR = 32,         // 32 count, 33 generation (grid barrier)
+    MI_BAR = 32,         // grid barrier arrival count (33 unused)
     MI_FUSE = 40,        // 40 kept, 41 lifted
     MI_PHASES = 64,      // 64..90 phase counts, 96..123 starts, 128..154 fill counters
     MI_COUNT = 192
@@ -101,7 +101,7 @@ struct ed_context {
     // PCG
     float *vec;              // 6 vectors of 12 max_nodes + 6: d, r, z, p0, p1, q
     size_t vec_stride;       // floats between vectors (multiple of 64: 16-byte aligned float4 rows)
-    double *pcg_part;        // [2][ED_MAX_PCG_GRID][ED_PCG_PART]
+    double *pcg_part;        // [2][ED_PCG_PART][ED_MAX_PCG_GRID] (component-major)
     // fusion / scans
     unsigned long long *zbuf;  // [W H]
     int *regpix;             // [W H]

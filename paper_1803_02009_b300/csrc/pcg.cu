@@ -9,12 +9,14 @@
 // build; CTA 0 also owns the pose rows.  For the whole solve a CTA keeps in
 // shared memory its rows' blocks (as many as fit; the rest stream from L2),
 // block inverses, pose-node blocks and its slices of d, r, z, p, q.  Per PCG
-// iteration it gathers the search direction of every block column it
-// touches, p_l = z_l + beta p_l(prev) (formed on the fly from the owners'
-// z and previous p: double buffer, no barrier of its own), multiplies from
-// shared memory, and meets the other CTAs at two bounded grid barriers (after
-// q = H p for p.q and the pose row, after z = M^-1 r for r.z).  Reductions are
-// per-CTA partials summed in a fixed order by every CTA: deterministic.
+// iteration it forms the search direction of every block column it touches,
+// p_l = z_l + beta p_l(prev), from the owners' z and previous p (double
+// buffer), which it loads in the same round of loads as the reduction that
+// follows the second barrier; multiplies from shared memory (several thread
+// groups per row when a CTA has few rows) and meets the other CTAs at two
+// bounded grid barriers (after q = H p for p.q and the pose row, after
+// z = M^-1 r for r.z).  Reductions are per-CTA partials summed in a fixed
+// order by every CTA: deterministic.
 #include "ed_internal.cuh"
 
 #define PCG_T 512
@@ -48,33 +50,34 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// grid barrier with a monotonic arrival counter: the CTA's writes are ordered
-// before thread 0's arrival by the CTA barrier and a fence, other CTAs' writes
-// are visible after its acquire load of the generation (later reads of shared
-// data bypass L1); returns false when the context status is set (an error
-// elsewhere, or this wait timed out)
-__device__ bool grid_sync(unsigned *count, unsigned *gen, int *status, unsigned nblocks, unsigned &target,
-                          int *s_flag)
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// grid barrier on a monotonic arrival counter that every CTA polls: the CTA's
+// writes are ordered before thread 0's arrival by the CTA barrier and a fence,
+// other CTAs' writes are visible after its acquire load of the count (later
+// reads of shared data bypass L1); returns false when the context status is
+// set (an error elsewhere, or this wait timed out)
+__device__ bool grid_sync(unsigned *count, int *status, unsigned nblocks, unsigned &target, int *s_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         target += 1;
         __threadfence();   // the whole CTA's writes (ordered by the CTA barrier) before the arrival
-        const unsigned arrived = atom_add_release(count, 1u) + 1u;
-        if (arrived == nblocks * target) {
-            st_release(gen, target);
-        } else {
-            const unsigned long long t0 = gtimer();
-            unsigned spins = 0;
-            while (ld_acquire(gen) < target) {
-                if ((++spins & 63u) == 0) {
-                    if (*(volatile int *)status != ED_OK) { ok = 0; break; }
-                    if (gtimer() - t0 > BAR_TIMEOUT_NS) {
-                        atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        red_add_release(count, 1u);
+        const unsigned goal = nblocks * target;
+        const unsigned long long t0 = gtimer();
+        unsigned spins = 0;
+        while (ld_acquire(count) < goal) {
+            if ((++spins & 63u) == 0) {
+                if (*(volatile int *)status != ED_OK) { ok = 0; break; }
+                if (gtimer() - t0 > BAR_TIMEOUT_NS) {
+                    atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
         }
@@ -94,25 +97,41 @@ struct PcgArgs {
     int max_rows, max_blk;   // shared-memory plan
     const float *bsr, *pnode, *minv, *pose_blk, *grad;
     float *d, *z, *p0, *p1;  // global vectors (z and p are read by other CTAs)
-    double *part;            // [2][ED_MAX_PCG_GRID][ED_PCG_PART]
-    unsigned *bar;           // count, generation
+    double *part;            // [2][ED_PCG_PART][ED_MAX_PCG_GRID], component-major
+    unsigned *bar;           // arrival count
     int *status;
     ed_stats *stats;
 };
 
-// sums component w of all CTA partials (warp w: lanes stride over the CTAs in
-// a fixed order, then a fixed shuffle tree) -- every CTA gets the same result
-template <typename DT>
-__device__ __forceinline__ void sum_partials(const double *part, int nb, int ncomp, DT *out_sh)
+// component w of the partials of CTA c
+__device__ __forceinline__ double *part_at(double *part, int w, int c) { return part + (size_t)w * ED_MAX_PCG_GRID + c; }
+
+// sums the NC components of all CTA partials: PCG_T / NCP threads per
+// component stride over the CTAs (one round of loads for up to 4x that many
+// CTAs), then a fixed shuffle tree and a fixed-order sum of the warp results,
+// so every CTA gets the same result.  Called by all threads; result in out_sh.
+template <typename DT, int NC>
+__device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh)[8], DT *out_sh)
 {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w < ncomp) {
-        DT s = 0;
+    constexpr int NCP = NC <= 1 ? 1 : NC <= 2 ? 2 : NC <= 4 ? 4 : 8;
+    constexpr int TPC = PCG_T / NCP;    // threads per component
+    constexpr int WPC = TPC / 32;       // warps per component
+    const int lane = threadIdx.x & 31, w = threadIdx.x / TPC, sub = threadIdx.x % TPC;
+    DT s = 0;
+    if (w < NC) {
+        const double *src = part + (size_t)w * ED_MAX_PCG_GRID;
 #pragma unroll 4
-        for (int c = lane; c < nb; c += 32) s += (DT)__ldcg(part + c * ED_PCG_PART + w);
+        for (int c = sub; c < nb; c += TPC) s += (DT)__ldcg(src + c);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) out_sh[w] = s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[threadIdx.x >> 5][0] = s;
+    __syncthreads();
+    if (threadIdx.x < NC) {
+        DT r = 0;
+#pragma unroll
+        for (int k = 0; k < WPC; ++k) r += sh[threadIdx.x * WPC + k][0];
+        out_sh[threadIdx.x] = r;
     }
     __syncthreads();
 }
@@ -140,7 +159,7 @@ __device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8], DT *sh_out
 
 // shared-memory carve of one CTA (in floats; every region a multiple of 4)
 struct PcgSmem {
-    size_t o_H, o_pb, o_M, o_C, o_r, o_d, o_z, o_p, o_q, total;
+    size_t o_H, o_pb, o_po, o_lc, o_M, o_C, o_r, o_d, o_z, o_p, o_q, o_qs, total;
 };
 
 __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncache)
@@ -148,7 +167,9 @@ __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncach
     PcgSmem L;
     size_t o = 0;
     L.o_H = o; o += (size_t)ncache * 144;
-    L.o_pb = o; o += (size_t)nblk * 12;
+    L.o_pb = o; o += (size_t)nblk * 12;            // z of the block columns, then p
+    L.o_po = o; o += (size_t)nblk * 12;            // previous p of the block columns
+    L.o_lc = o; o += ((size_t)nblk + 3) / 4 * 4;   // block column indices (int)
     L.o_M = o; o += (size_t)rows * 144;
     L.o_C = o; o += (size_t)rows * 72;
     L.o_r = o; o += (size_t)rows * 12;
@@ -156,6 +177,7 @@ __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncach
     L.o_z = o; o += (size_t)rows * 12;
     L.o_p = o; o += (size_t)rows * 12;
     L.o_q = o; o += (size_t)rows * 12;
+    L.o_qs = o; o += (size_t)ROWS_PER_PASS * 12;   // split partial products of q
     L.total = o;
     return L;
 }
@@ -169,7 +191,7 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
     __shared__ DT s_red[PCG_T / 32][8];
     __shared__ DT s_sum[8];
     __shared__ DT s_blk[8];
-    __shared__ float s_pp[6], s_ppold[6], s_qp[6], s_rpose[6], s_dpose[6];
+    __shared__ float s_pp[6], s_zp[6], s_qp[6], s_rpose[6], s_dpose[6];
     __shared__ float s_Hpp[36], s_Mp[36];
     __shared__ DT s_rho, s_beta, s_rr, s_res0, s_alpha;
     __shared__ int s_break;
@@ -181,18 +203,23 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
     const int b0 = a.row_ptr[r0], nblk = a.row_ptr[r1] - b0;
     const int ncache = min(nblk, a.n_cache);
     const PcgSmem L = pcg_smem_layout(a.max_rows, a.max_blk, a.n_cache);
-    float *Hs = sm + L.o_H, *pb = sm + L.o_pb, *Ms = sm + L.o_M, *Cs = sm + L.o_C;
+    float *Hs = sm + L.o_H, *pb = sm + L.o_pb, *po = sm + L.o_po, *Ms = sm + L.o_M, *Cs = sm + L.o_C;
     float *rs = sm + L.o_r, *ds = sm + L.o_d, *zs = sm + L.o_z, *ps = sm + L.o_p, *qs = sm + L.o_q;
+    float *qsplit = sm + L.o_qs;
+    int *lc = reinterpret_cast<int *>(sm + L.o_lc);
     const int t = threadIdx.x;
     const int grp = t / 12, rr = t % 12;
     const bool in_grp = grp < ROWS_PER_PASS;
+    // q = H p: with few rows, S groups of 12 threads share the blocks of a row
+    const int S = rows <= ROWS_PER_PASS ? ROWS_PER_PASS / rows : 1;
+    const int rpp = ROWS_PER_PASS / S;   // rows per pass
     const int P = 12 * m;
     const float *Hpp = s_Hpp, *Mp = s_Mp;
     double *part0 = a.part, *part1 = a.part + (size_t)ED_MAX_PCG_GRID * ED_PCG_PART;
 
     if (*(volatile int *)a.status != ED_OK) return;
 
-    // ---- the CTA's share of H, M^-1, C and b into shared memory ----
+    // ---- the CTA's share of H, M^-1, C, block columns and b into shared memory ----
     {
         const float4 *src = reinterpret_cast<const float4 *>(a.bsr + (size_t)b0 * 144);
         float4 *dst = reinterpret_cast<float4 *>(Hs);
@@ -201,6 +228,7 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
         float4 *md = reinterpret_cast<float4 *>(Ms);
         for (int i = t; i < rows * 36; i += PCG_T) md[i] = __ldg(ms + i);
         for (int i = t; i < rows * 72; i += PCG_T) Cs[i] = __ldg(a.pnode + (size_t)r0 * 72 + i);
+        for (int i = t; i < nblk; i += PCG_T) lc[i] = __ldg(a.col + b0 + i);
         for (int i = t; i < rows * 12; i += PCG_T) {
             rs[i] = -__ldg(a.grad + 12 * r0 + i);
             ds[i] = 0.f;
@@ -232,7 +260,32 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
                 rrs += (DT)rv1 * (DT)rv1;
             }
         }
-        __syncthreads();
+    };
+
+    // pose rows (CTA 0, thread 0): z_p = Mp r_p; adds the pose terms of r.z and r.r
+    auto pose_precond = [&](DT &v1, DT &v2) {
+        for (int i = 0; i < 6; ++i) {
+            float zi = 0.f;
+            for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
+            a.z[P + i] = zi;
+            v1 += (DT)s_rpose[i] * (DT)zi;
+            v2 += (DT)s_rpose[i] * (DT)s_rpose[i];
+        }
+    };
+
+    // the block columns' z (and previous p) from their owners, issued together
+    // with the loads of the reduction that follows each barrier
+    auto stage_columns = [&](const float *pprev) {
+        for (int i = t; i < nblk * 3; i += PCG_T) {
+            const int lb = i / 3, q4 = i - 3 * lb;
+            const int l = lc[lb];
+            reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] =
+                __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l) + q4);
+            if (pprev)
+                reinterpret_cast<float4 *>(po + (size_t)lb * 12)[q4] =
+                    __ldcg(reinterpret_cast<const float4 *>(pprev + 12 * l) + q4);
+        }
+        if (t < 6) s_zp[t] = __ldcg(a.z + P + t);
     };
 
     // ---- set-up: r = b, d = 0, z = M^-1 r ----
@@ -245,28 +298,24 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
     if (t == 0) {
         DT v1 = s_blk[0], v2 = s_blk[1];
         if (blockIdx.x == 0) {
-            for (int i = 0; i < 6; ++i) s_rpose[i] = -a.grad[P + i];
             for (int i = 0; i < 6; ++i) {
-                float zi = 0.f;
-                for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
+                s_rpose[i] = -a.grad[P + i];
                 s_dpose[i] = 0.f;
-                a.z[P + i] = zi;
-                v1 += (DT)s_rpose[i] * (DT)zi;
-                v2 += (DT)s_rpose[i] * (DT)s_rpose[i];
             }
+            pose_precond(v1, v2);
         }
-        part0[blockIdx.x * ED_PCG_PART + 0] = (double)v1;
-        part0[blockIdx.x * ED_PCG_PART + 1] = (double)v2;
+        *part_at(part0, 0, blockIdx.x) = (double)v1;
+        *part_at(part0, 1, blockIdx.x) = (double)v2;
     }
-    if (!grid_sync(a.bar, a.bar + 1, a.status, nb, target, &s_flag)) return;
-    sum_partials<DT>(part0, nb, 2, s_sum);
+    if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+    stage_columns(nullptr);
+    sum_partials<DT, 2>(part0, nb, s_red, s_sum);
     if (t == 0) {
         s_rho = s_sum[0];
         s_rr = s_sum[1];
         s_res0 = sqrt((double)s_sum[1]);
         s_beta = 0;
     }
-    if (t < 6) s_ppold[t] = 0.f;
     __syncthreads();
 
     int it = 0;
@@ -275,39 +324,28 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
         if (!(rho > (DT)0)) break;
         if (a.tol > 0.f && sqrt((double)s_rr) <= (double)a.tol * (double)s_res0) break;
         const float beta = (float)s_beta;
-        const float *pold = (it & 1) ? a.p0 : a.p1;
         float *pnew = (it & 1) ? a.p1 : a.p0;
-        if (t < 6) s_pp[t] = it > 0 ? __fmaf_rn(beta, s_ppold[t], __ldcg(a.z + P + t)) : __ldcg(a.z + P + t);
-        // ---- gather p of every block column: p_l = z_l + beta p_l(prev) ----
-        for (int i = t; i < nblk * 3; i += PCG_T) {
-            const int lb = i / 3, q4 = i - 3 * lb;
-            const int l = __ldg(a.col + b0 + lb);
-            const float4 zl = __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l) + q4);
-            float4 pl = zl;
-            if (it > 0) {
-                const float4 po = __ldcg(reinterpret_cast<const float4 *>(pold + 12 * l) + q4);
-                pl = make_float4(__fmaf_rn(beta, po.x, zl.x), __fmaf_rn(beta, po.y, zl.y), __fmaf_rn(beta, po.z, zl.z),
-                                 __fmaf_rn(beta, po.w, zl.w));
-            }
-            reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] = pl;
-        }
-        // own rows: the same p_j, kept and published for the next iteration
+        // ---- p = z + beta p(prev): block columns (staged), own rows (published), pose ----
+        if (it > 0)
+            for (int i = t; i < nblk * 12; i += PCG_T) pb[i] = __fmaf_rn(beta, po[i], pb[i]);
         for (int i = t; i < rows * 12; i += PCG_T) {
             const float pv = it > 0 ? __fmaf_rn(beta, ps[i], zs[i]) : zs[i];
             ps[i] = pv;
             pnew[12 * r0 + i] = pv;
         }
+        if (t < 6) s_pp[t] = it > 0 ? __fmaf_rn(beta, s_pp[t], s_zp[t]) : s_zp[t];
         __syncthreads();
-        // ---- phase A: q = H p (own rows; thread = one output row), partials p.q and C p ----
+        // ---- phase A: q = H p for the own rows (thread = one output row of one
+        // of the S splits of a row's blocks), partials p.q and C p ----
         DT pq = 0;
         DT cp[6] = {0, 0, 0, 0, 0, 0};
-        for (int j0 = 0; j0 < rows; j0 += ROWS_PER_PASS) {
-            const int jl = j0 + grp;
-            if (in_grp && jl < rows) {
+        for (int j0 = 0; j0 < rows; j0 += rpp) {
+            const int jl = j0 + grp / S, sp = grp - (grp / S) * S;
+            if (in_grp && grp < rpp * S && jl < rows) {
                 const int j = r0 + jl;
                 const int bb0 = a.row_ptr[j] - b0, bb1 = a.row_ptr[j + 1] - b0;
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-                for (int lb = bb0; lb < bb1; ++lb) {
+                for (int lb = bb0 + sp; lb < bb1; lb += S) {
                     const float4 *hrow = lb < ncache ? reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12)
                                                      : reinterpret_cast<const float4 *>(a.bsr + (size_t)(b0 + lb) * 144 + rr * 12);
                     const float4 *pl = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
@@ -317,34 +355,42 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
                     acc1 += h1.x * p1.x + h1.y * p1.y + h1.z * p1.z + h1.w * p1.w;
                     acc2 += h2.x * p2.x + h2.y * p2.y + h2.z * p2.z + h2.w * p2.w;
                 }
-                const float *C = Cs + jl * 72;
-                float qv = acc0 + acc1 + acc2;
+                qsplit[grp * 12 + rr] = acc0 + acc1 + acc2;
+            }
+            __syncthreads();
+            // the S splits of a row in a fixed order, plus the pose coupling C_j^T p_pose
+            const int jr = j0 + grp;
+            if (in_grp && grp < rpp && jr < rows) {
+                float qv = 0.f;
+                for (int q = 0; q < S; ++q) qv += qsplit[(grp * S + q) * 12 + rr];
+                const float *C = Cs + jr * 72;
 #pragma unroll
                 for (int s = 0; s < 6; ++s) qv += C[12 * s + rr] * s_pp[s];
-                qs[jl * 12 + rr] = qv;
-                const float pv = ps[jl * 12 + rr];
+                qs[jr * 12 + rr] = qv;
+                const float pv = ps[jr * 12 + rr];
                 pq += (DT)pv * (DT)qv;
 #pragma unroll
                 for (int s = 0; s < 6; ++s) cp[s] += (DT)C[12 * s + rr] * (DT)pv;
             }
+            __syncthreads();
         }
         {
             DT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
             block_sum_n<DT, 7>(vv, s_red, s_blk);
-            if (t < 7) part1[blockIdx.x * ED_PCG_PART + t] = (double)s_blk[t];
+            if (t < 7) *part_at(part1, t, blockIdx.x) = (double)s_blk[t];
         }
-        if (!grid_sync(a.bar, a.bar + 1, a.status, nb, target, &s_flag)) return;
+        if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         // ---- phase B: alpha, d += alpha p, r -= alpha q, z = M^-1 r ----
-        sum_partials<DT>(part1, nb, 7, s_sum);
+        sum_partials<DT, 7>(part1, nb, s_red, s_sum);
+        if (t < 6) {
+            float qi = (float)s_sum[1 + t];
+            for (int k = 0; k < 6; ++k) qi += Hpp[6 * t + k] * s_pp[k];
+            s_qp[t] = qi;
+        }
+        __syncthreads();
         if (t == 0) {
             DT pqt = s_sum[0];
-            for (int i = 0; i < 6; ++i) {
-                float qi = 0.f;
-                for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
-                qi += (float)s_sum[1 + i];
-                s_qp[i] = qi;
-                pqt += (DT)s_pp[i] * (DT)qi;
-            }
+            for (int i = 0; i < 6; ++i) pqt += (DT)s_pp[i] * (DT)s_qp[i];
             s_break = !(pqt > (DT)0);
             s_alpha = rho / pqt;
             if (s_break && blockIdx.x == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
@@ -370,25 +416,19 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
                     s_dpose[i] = __fmaf_rn(alpha, s_pp[i], s_dpose[i]);
                     s_rpose[i] = __fmaf_rn(-alpha, s_qp[i], s_rpose[i]);
                 }
-                for (int i = 0; i < 6; ++i) {
-                    float zi = 0.f;
-                    for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
-                    a.z[P + i] = zi;
-                    w1 += (DT)s_rpose[i] * (DT)zi;
-                    w2 += (DT)s_rpose[i] * (DT)s_rpose[i];
-                }
+                pose_precond(w1, w2);
             }
-            part0[blockIdx.x * ED_PCG_PART + 0] = (double)w1;
-            part0[blockIdx.x * ED_PCG_PART + 1] = (double)w2;
+            *part_at(part0, 0, blockIdx.x) = (double)w1;
+            *part_at(part0, 1, blockIdx.x) = (double)w2;
         }
-        if (!grid_sync(a.bar, a.bar + 1, a.status, nb, target, &s_flag)) return;
-        sum_partials<DT>(part0, nb, 2, s_sum);
+        if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+        stage_columns(pnew);
+        sum_partials<DT, 2>(part0, nb, s_red, s_sum);
         if (t == 0) {
             s_beta = s_sum[0] / rho;
             s_rho = s_sum[0];
             s_rr = s_sum[1];
         }
-        if (t < 6) s_ppold[t] = s_pp[t];
         __syncthreads();
     }
     // solution of the CTA's rows (and of the pose: CTA 0)
