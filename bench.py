@@ -56,6 +56,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank):
+    """Every rank registers its own frame: independent problems, no data-path
+    collective (weak scaling)."""
+    return 1 + rank
+
+
+def max_over_ranks(seconds, dist=None, device="cpu"):
+    """The job's time is the slowest rank's; `dist` is torch.distributed or None."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, gn_per_step, seconds):
+    """GN iterations per second summed over all ranks (each rank did steps x gn_per_step)."""
+    return world * steps * gn_per_step / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -140,7 +161,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    s = synth.make_scene(args.config, seed=1 + rank)
+    s = synth.make_scene(args.config, seed=rank_seed(rank))
     cfg = s.cfg
     fx, fy, cx, cy, W, H = s.intr
     dev = "cuda"
@@ -236,12 +257,8 @@ def run_ours(args, rank, world, local):
     ctx.set_timing(E.ED_KERNEL_PCG, [])
     pcg_ms = [tm_ev[2 * i].elapsed_time(tm_ev[2 * i + 1]) for i in range(n_rec)]
     gn_ms = [a.elapsed_time(b) for a, b in gn_ev[-K:]]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * K * cfg.n_gn / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = whole_job_rate(world, K, cfg.n_gn, total_s)
 
     # end to end through the public API with host buffers
     h_depth = torch.from_numpy(s.tgt_depth).pin_memory()
@@ -266,12 +283,8 @@ def run_ours(args, rank, world, local):
         ev1.record()
         ev1.synchronize()
         e2e_ms.append(ev0.elapsed_time(ev1))
-    e2e_s = sum(e2e_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * K * cfg.n_gn / e2e_s
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
+    e2e_value = whole_job_rate(world, K, cfg.n_gn, e2e_s)
 
     peak, peak_kind = measured_peaks()
     byt = pcg_bytes_per_launch(g.m, g.nnzb, cfg.n_pcg)
@@ -296,7 +309,8 @@ def run_ours(args, rank, world, local):
                    "node_radius_mm": radius, "precision": args.precision,
                    "l2": "flushed between steps (512 MB write)",
                    "step": "normals + build_graph + 10 x gn_step + warp + fuse"},
-        "gn_only_iters_per_s": world * K * cfg.n_gn / (sum(gn_ms) / 1e3) if gn_ms else None,
+        "gn_only_iters_per_s": whole_job_rate(world, K, cfg.n_gn, max_over_ranks(sum(gn_ms) / 1e3, dist, dev))
+        if gn_ms else None,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
