@@ -308,6 +308,100 @@ ed_status ed_energy_noalloc(const float *pos, const float *nrm, const uint16_t *
                             const ed_frame *frame, const ed_solver_params *params, const float *x,
                             const double *pose, double *energy_out, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent problems.
+ *
+ * Each problem is one frame of the registration of Sec. II (its own model,
+ * node graph, depth map and pose prior) held in its own context, whose graph
+ * has been built with ed_build_graph.  One batched Gauss-Newton iteration
+ * does, for every problem, what ed_gn_step does (Eqs. 3-4 linearised, the
+ * normal equations solved by block-Jacobi PCG, the update applied); it runs
+ * the per-problem kernels up to the normal equations concurrently on
+ * internal streams, the PCG solves of a group of problems as ONE persistent
+ * cooperative launch in which each problem owns a range of CTAs with its own
+ * grid barrier, then the updates.  The paper registers one frame at a time;
+ * batching is a throughput variant of the same arithmetic.
+ * ------------------------------------------------------------------------ */
+typedef struct ed_batch ed_batch;
+
+typedef struct ed_batch_schedule {
+    int pcg_threads;          /* threads per PCG CTA: 512 (one CTA per SM) or 256 (two per SM) */
+    int problems_per_launch;  /* problems sharing one persistent PCG launch (1..32); more
+                                 problems per launch means fewer CTAs (more node rows) each */
+    int streams;              /* internal streams for the per-problem kernels */
+} ed_batch_schedule;
+
+/*
+ * Bytes of device workspace for a batch of `count` (1..64) problems: room
+ * for a copy of every problem's x, x_master and pose (used by the autotuner).
+ * Every context must hold a built graph (else ED_ERR_STATE).
+ */
+ed_status ed_batch_query_workspace(ed_context *const *ctxs, int count, size_t *bytes);
+
+/*
+ * Creates a batch over distinct contexts (ctxs[p] is problem p).  The caller
+ * owns the contexts and the workspace (256-byte aligned, at least the queried
+ * size), which must outlive the batch.  Creates `count` internal streams and
+ * events (no device memory is allocated).  The default schedule is 512-thread
+ * PCG CTAs, the largest power-of-two number of problems per launch whose CTA
+ * shares fit in shared memory, and min(count, 16) streams.  Rebuilding the
+ * graph of a member context invalidates the batch: destroy and create it
+ * again.  Returns ED_ERR_CAPACITY if no grouping fits.
+ */
+ed_status ed_batch_create(ed_context *const *ctxs, int count, void *workspace, size_t workspace_bytes,
+                          ed_batch **batch);
+ed_status ed_batch_destroy(ed_batch *batch);
+
+/*
+ * Sets the schedule (synchronises the device; drops a captured graph).
+ * ED_ERR_CAPACITY if a problem's CTA share does not fit in shared memory
+ * under it; the previous schedule then stays in force.
+ */
+ed_status ed_batch_set_schedule(ed_batch *batch, const ed_batch_schedule *schedule);
+ed_status ed_batch_get_schedule(const ed_batch *batch, ed_batch_schedule *schedule);
+
+/*
+ * One batched Gauss-Newton iteration, enqueued on `stream`.  Arrays of
+ * `count` entries, indexed by problem: frames, params (all with the same
+ * precision), x (device [m_p][12] float), x_master (host array of device
+ * pointers, or NULL for FP32; entries required in mixed precision), pose
+ * (device double[6]), stats (device ed_stats per problem, or NULL).  The host
+ * arrays are read during the call only.  Same per-problem results and errors
+ * as ed_gn_step; the block reductions of a batched PCG run over fewer CTAs,
+ * so results agree with ed_gn_step to rounding, not bit for bit.
+ */
+ed_status ed_batch_gn_step(ed_batch *batch, const ed_frame *frames, const ed_solver_params *params,
+                           float *const *x, double *const *x_master, double *const *pose, ed_stats *const *stats,
+                           cudaStream_t stream);
+
+/*
+ * Captures n_iters batched iterations with these arguments into a CUDA graph
+ * held by the batch (replacing any previous one); `stream` must be a created
+ * stream, not the default one (ED_ERR_ARG); stats[p] then points to
+ * n_iters consecutive ed_stats (one per iteration).  Nothing runs during the
+ * capture.  The device buffers named here must stay valid while the graph
+ * is replayed with ed_batch_launch, which enqueues all n_iters iterations
+ * on `stream` with one graph launch.  ED_ERR_STATE from ed_batch_launch when
+ * nothing was captured.
+ */
+ed_status ed_batch_capture(ed_batch *batch, const ed_frame *frames, const ed_solver_params *params,
+                           float *const *x, double *const *x_master, double *const *pose, ed_stats *const *stats,
+                           int n_iters, cudaStream_t stream);
+ed_status ed_batch_launch(ed_batch *batch, cudaStream_t stream);
+
+/*
+ * Autotuner: times one captured batched iteration under every feasible
+ * schedule (PCG threads 512 / 256; problems per launch 1, 2, 4, ... up to
+ * all; 4 or up to 16 streams), restoring every problem's x, x_master and
+ * pose after each run, and keeps the fastest, returned in `chosen` (with its
+ * time in ms in best_ms; either may be NULL).  Synchronises `stream` and the
+ * device; drops a captured graph; `stream` must be a created stream.  Run it with the arguments of the real
+ * iterations (the timings depend on the association of the current x).
+ */
+ed_status ed_batch_autotune(ed_batch *batch, const ed_frame *frames, const ed_solver_params *params,
+                            float *const *x, double *const *x_master, double *const *pose, ed_stats *const *stats,
+                            cudaStream_t stream, ed_batch_schedule *chosen, float *best_ms);
+
 #ifdef __cplusplus
 }
 #endif

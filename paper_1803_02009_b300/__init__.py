@@ -83,6 +83,14 @@ class FuseParamsC(C.Structure):
                 ("tau_weight", C.c_float), ("frame", C.c_int)]
 
 
+class BatchSchedule(C.Structure):
+    _fields_ = [("pcg_threads", C.c_int), ("problems_per_launch", C.c_int), ("streams", C.c_int)]
+
+    def as_dict(self):
+        return {"pcg_threads": self.pcg_threads, "problems_per_launch": self.problems_per_launch,
+                "streams": self.streams}
+
+
 _vp = C.c_void_p
 _SIGS = {
     "ed_query_workspace": [C.POINTER(Limits), C.POINTER(C.c_size_t)],
@@ -101,6 +109,15 @@ _SIGS = {
     "ed_energy_grad": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, C.c_float, _vp, _vp, _vp],
     "ed_set_timing": [_vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)],
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
+    "ed_batch_query_workspace": [_vp, C.c_int, C.POINTER(C.c_size_t)],
+    "ed_batch_create": [_vp, C.c_int, _vp, C.c_size_t, C.POINTER(_vp)],
+    "ed_batch_destroy": [_vp],
+    "ed_batch_set_schedule": [_vp, C.POINTER(BatchSchedule)],
+    "ed_batch_get_schedule": [_vp, C.POINTER(BatchSchedule)],
+    "ed_batch_gn_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "ed_batch_capture": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp],
+    "ed_batch_launch": [_vp, _vp],
+    "ed_batch_autotune": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(BatchSchedule), C.POINTER(C.c_float)],
 }
 ED_KERNEL_PCG, ED_KERNEL_POINTS, ED_KERNEL_ASSEMBLE, ED_KERNEL_FINALIZE = 0, 1, 2, 3
 
@@ -436,3 +453,94 @@ class EDEnergy(torch.autograd.Function):
                                           pose.detach().contiguous(), scale=1.0)
         s = grad_out.to(torch.float32)
         return gx * s, (gp * s).to(pose.dtype), None, None, None
+
+
+class Batch:
+    """Independent problems (one Context each, graphs built) advanced together:
+    one batched Gauss-Newton iteration runs every problem's per-problem kernels
+    concurrently and their PCG solves as one persistent launch; iterations can
+    be captured into a CUDA graph and replayed.  The argument lists fixed with
+    bind() are marshalled once into C arrays."""
+
+    def __init__(self, contexts):
+        L = lib()
+        self.contexts = list(contexts)
+        n = len(self.contexts)
+        self._ctx_arr = (C.c_void_p * n)(*[c.h.value for c in self.contexts])
+        nbytes = C.c_size_t(0)
+        _check("ed_batch_query_workspace", L.ed_batch_query_workspace(self._ctx_arr, n, C.byref(nbytes)))
+        self.ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device="cuda")
+        h = C.c_void_p()
+        _check("ed_batch_create", L.ed_batch_create(self._ctx_arr, n, _ptr(self.ws), self.ws.numel(), C.byref(h)))
+        self.h = h
+        self._args = None
+        # graphs are captured and replayed on a created stream (the default
+        # stream cannot be captured), ordered against the caller's stream
+        self.stream = torch.cuda.Stream()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                lib().ed_batch_destroy(self.h)
+        except Exception:
+            pass
+
+    def bind(self, frames, params, xs, poses, x_masters=None, stats=None):
+        """Fixes the per-problem arguments: frames (Frame), params
+        (SolverParams), xs (device [m][12] f32), poses (device [6] f64),
+        x_masters (device [m][12] f64, mixed precision), stats (device stats
+        buffers from new_stats)."""
+        n = len(self.contexts)
+        assert len(frames) == len(params) == len(xs) == len(poses) == n
+        fr = (Frame * n)(*frames)
+        pr = (SolverParamsC * n)(*[p.c() for p in params])
+        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        pa = (C.c_void_p * n)(*[q.data_ptr() for q in poses])
+        xm = (C.c_void_p * n)(*[q.data_ptr() for q in x_masters]) if x_masters is not None else None
+        sa = (C.c_void_p * n)(*[q.data_ptr() for q in stats]) if stats is not None else None
+        self._args = (fr, pr, xa, xm, pa, sa)
+        self._keep = (list(frames), list(xs), list(poses), x_masters, stats)
+
+    def _a(self):
+        if self._args is None:
+            raise RuntimeError("Batch.bind() first")
+        fr, pr, xa, xm, pa, sa = self._args
+        return fr, pr, xa, xm, pa, sa
+
+    def gn_step(self, stream=None):
+        fr, pr, xa, xm, pa, sa = self._a()
+        _check("ed_batch_gn_step", lib().ed_batch_gn_step(self.h, fr, pr, xa, xm, pa, sa, _stream(stream)))
+
+    def _on_own_stream(self, fn, stream=None):
+        caller = stream if stream is not None else torch.cuda.current_stream()
+        self.stream.wait_stream(caller)
+        r = fn(C.c_void_p(self.stream.cuda_stream))
+        caller.wait_stream(self.stream)
+        return r
+
+    def capture(self, n_iters=1, stream=None):
+        """Captures n_iters batched iterations into the batch's CUDA graph."""
+        fr, pr, xa, xm, pa, sa = self._a()
+        self._on_own_stream(lambda st: _check("ed_batch_capture", lib().ed_batch_capture(
+            self.h, fr, pr, xa, xm, pa, sa, int(n_iters), st)), stream)
+
+    def launch(self, stream=None):
+        """Replays the captured graph, ordered after the caller's stream."""
+        self._on_own_stream(lambda st: _check("ed_batch_launch", lib().ed_batch_launch(self.h, st)), stream)
+
+    def autotune(self, stream=None):
+        fr, pr, xa, xm, pa, sa = self._a()
+        sch = BatchSchedule()
+        ms = C.c_float(0.0)
+        self._on_own_stream(lambda st: _check("ed_batch_autotune", lib().ed_batch_autotune(
+            self.h, fr, pr, xa, xm, pa, sa, st, C.byref(sch), C.byref(ms))), stream)
+        return sch.as_dict(), ms.value
+
+    def schedule(self):
+        sch = BatchSchedule()
+        _check("ed_batch_get_schedule", lib().ed_batch_get_schedule(self.h, C.byref(sch)))
+        return sch.as_dict()
+
+    def set_schedule(self, pcg_threads, problems_per_launch, streams):
+        sch = BatchSchedule(int(pcg_threads), int(problems_per_launch), int(streams))
+        _check("ed_batch_set_schedule", lib().ed_batch_set_schedule(self.h, C.byref(sch)))

@@ -94,6 +94,7 @@ size_t carve(ed_context *c, char *base)
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
     c->pcg_rows = k.take<int>(ED_MAX_PCG_GRID + 1);
+    c->pcg_rows_b = k.take<int>(ED_MAX_PCG_GRID + 1);
     c->zbuf = k.take<unsigned long long>(WH);
     c->regpix = k.take<int>(WH);
     c->fused_pix = k.take<int>(N);
@@ -136,14 +137,17 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         return ED_ERR_CAPACITY;
     }
     carve(c, (char *)workspace);
+    c->row_ptr_host = (int *)malloc(sizeof(int) * ((size_t)c->lim.max_nodes + 1));
+    if (!c->row_ptr_host) {
+        free(c);
+        return ED_ERR_CAPACITY;
+    }
     c->ws = (char *)workspace;
     c->ws_bytes = workspace_bytes;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
-        free(c);
-        return ED_ERR_CUDA;
-    }
-    if (cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess) {
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess) {
+        free(c->row_ptr_host);
         free(c);
         return ED_ERR_CUDA;
     }
@@ -154,6 +158,7 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
 extern "C" ed_status ed_destroy(ed_context *ctx)
 {
     if (!ctx) return ED_ERR_ARG;
+    free(ctx->row_ptr_host);
     free(ctx);
     return ED_OK;
 }
@@ -184,6 +189,7 @@ extern "C" ed_status ed_set_debug(ed_context *ctx, float *warped_pos, float *war
 
 static unsigned long long g_launches = 0;
 void ed_note_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+void ed_note_launches(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
 
 extern "C" ed_status ed_launch_count(unsigned long long *count)
 {

@@ -17,6 +17,7 @@
 #define ED_K1_THREADS 256
 #define ED_K1_PART 32          // doubles per point-kernel CTA partial
 #define ED_PCG_PART 8          // doubles per PCG CTA partial
+#define ED_MAX_BATCH_LAUNCH 32 // problems in one batched PCG launch
 #define ED_MAX_PCG_GRID 1184   // 8 x 148
 
 // indices of the misc int words in the workspace
@@ -38,6 +39,23 @@ enum {
     MI_COUNT = 192
 };
 enum { MF_CELL = 0, MF_INV = 1, MF_KCELL = 2, MF_KINV = 3, MF_R2 = 4, MF_BBOX = 8, MF_COUNT = 16 };
+
+// launch plan of the PCG of one problem
+struct ed_pcg_plan_t {
+    int grid;                // CTAs
+    int nt;                  // threads per CTA (256 or 512)
+    int ncache;              // blocks per CTA kept in shared memory
+    int max_rows, max_blk;   // largest CTA share (rows, blocks)
+    size_t smem;             // dynamic shared memory per CTA
+};
+
+// several problems in one persistent PCG launch
+struct ed_pcg_batch_plan_t {
+    int count, nt, grid;
+    size_t smem;
+    int cta_first[ED_MAX_BATCH_LAUNCH + 1];
+    ed_pcg_plan_t plan[ED_MAX_BATCH_LAUNCH];
+};
 
 struct ed_context {
     ed_limits lim;
@@ -127,11 +145,10 @@ struct ed_context {
     int n_chunks;
     int have_system;
     int have_energy;
-    int pcg_grid;            // CTAs of the PCG launch (one per SM)
+    ed_pcg_plan_t pcg;       // single-problem PCG launch (one 512-thread CTA per SM)
     int *pcg_rows;           // [ED_MAX_PCG_GRID + 1] first node row of every CTA (device)
-    int pcg_cache;           // blocks per CTA kept in shared memory
-    size_t pcg_smem;         // dynamic shared memory of the PCG launch
-    int pcg_max_rows, pcg_max_blk;
+    int *pcg_rows_b;         // [ED_MAX_PCG_GRID + 1] the same for a batched launch (device)
+    int *row_ptr_host;       // [max_nodes + 1] host copy of the block row pointer
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
@@ -197,6 +214,7 @@ static inline int ed_div_up(long a, long b) { return (int)((a + b - 1) / b); }
 
 // process-wide count of kernel launches issued by the library (host side)
 void ed_note_launch();
+void ed_note_launches(unsigned long long n);   // kernels of a replayed CUDA graph
 
 // ---------------------------------------------------------------------------
 // exact FP32 decision rules (no fused multiply-add, fixed operation order)
@@ -369,5 +387,13 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
 ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st);
 ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st);
+ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x, double *x_master,
+                    double *pose, ed_stats *stats, cudaStream_t st);
+ed_status ed_gn_post(ed_context *ctx, const ed_solver_params *prm, float *x, double *x_master, double *pose,
+                     ed_stats *stats, cudaStream_t st);
+ed_status ed_pcg_make_plan(const int *row_ptr_host, int m, int grid, int nt, ed_pcg_plan_t *pl, int *rows_start);
+ed_status ed_pcg_batch_plan(ed_context *const *ctxs, int count, int nt, int grid_total, ed_pcg_batch_plan_t *bp);
+ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t *bp, const ed_solver_params *const *prm,
+                             ed_stats *const *stats, cudaStream_t st);
 ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
                         const double *pose, int write_records, cudaStream_t st);

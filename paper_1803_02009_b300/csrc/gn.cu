@@ -748,8 +748,10 @@ static ed_status check_frame(const ed_context *ctx, const ed_frame *fr)
     return ED_OK;
 }
 
-extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x,
-                                double *x_master, double *pose, ed_stats *stats, cudaStream_t st)
+// one Gauss-Newton iteration up to the normal equations: association,
+// residuals, assembly, block inverses, pose rows
+ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x, double *x_master,
+                    double *pose, ed_stats *stats, cudaStream_t st)
 {
     if (!ctx || !prm || !x || !pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
     if (!ctx->have_graph) return ED_ERR_STATE;
@@ -810,13 +812,28 @@ extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_so
     k_pose_final<<<1, 256, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->node_energy, m, pose, *prm, ctx->pose_blk,
                                     ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS, stats); ed_note_launch();
     ED_LAUNCH_CHECK();
-    if ((s = ed_pcg_solve(ctx, prm, stats, st)) != ED_OK) return s;
-    const int n = 12 * m;
+    return ED_OK;
+}
+
+// the update x += delta (and the pose) after the PCG solve
+ed_status ed_gn_post(ed_context *ctx, const ed_solver_params *prm, float *x, double *x_master, double *pose,
+                     ed_stats *stats, cudaStream_t st)
+{
+    const int n = 12 * ctx->m;
     k_update<<<ed_div_up(n + 6, 256), 256, 0, st>>>(n, ctx->vec, x, prm->precision == ED_PRECISION_MIXED ? x_master : nullptr,
                                                    pose, ctx->misc + MI_STATUS, stats); ed_note_launch();
     ED_LAUNCH_CHECK();
     ctx->have_system = 1;
     return ED_OK;
+}
+
+extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x,
+                                double *x_master, double *pose, ed_stats *stats, cudaStream_t st)
+{
+    ed_status s = ed_gn_pre(ctx, fr, prm, x, x_master, pose, stats, st);
+    if (s != ED_OK) return s;
+    if ((s = ed_pcg_solve(ctx, prm, stats, st)) != ED_OK) return s;
+    return ed_gn_post(ctx, prm, x, x_master, pose, stats, st);
 }
 
 // blocks (row-major BSR), pose-node blocks, pose block, J^T r, solution

@@ -17,12 +17,16 @@
 // bounded grid barriers (after q = H p for p.q and the pose row, after
 // z = M^-1 r for r.z).  Reductions are per-CTA partials summed in a fixed
 // order by every CTA: deterministic.
+#include <mutex>
+
 #include "ed_internal.cuh"
 
-#define PCG_T 512
-#define ROWS_PER_PASS (PCG_T / 12)   // 12 threads per node row (one per output row)
 #define BAR_TIMEOUT_NS 2000000000ull
-#define PCG_SMEM_MAX (200 * 1024)
+#define PCG_SMEM_MAX (200 * 1024)      // one 512-thread CTA per SM
+#define PCG_SMEM_MAX_256 (100 * 1024)  // two 256-thread CTAs per SM
+
+// 12 threads per node row (one per output row of a 12x12 block)
+template <int NT> struct RowsPerPass { static constexpr int v = NT / 12; };
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -106,15 +110,15 @@ struct PcgArgs {
 // component w of the partials of CTA c
 __device__ __forceinline__ double *part_at(double *part, int w, int c) { return part + (size_t)w * ED_MAX_PCG_GRID + c; }
 
-// sums the NC components of all CTA partials: PCG_T / NCP threads per
+// sums the NC components of all CTA partials: NT / NCP threads per
 // component stride over the CTAs (one round of loads for up to 4x that many
 // CTAs), then a fixed shuffle tree and a fixed-order sum of the warp results,
 // so every CTA gets the same result.  Called by all threads; result in out_sh.
-template <typename DT, int NC>
+template <typename DT, int NT, int NC>
 __device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh)[8], DT *out_sh)
 {
     constexpr int NCP = NC <= 1 ? 1 : NC <= 2 ? 2 : NC <= 4 ? 4 : 8;
-    constexpr int TPC = PCG_T / NCP;    // threads per component
+    constexpr int TPC = NT / NCP;       // threads per component
     constexpr int WPC = TPC / 32;       // warps per component
     const int lane = threadIdx.x & 31, w = threadIdx.x / TPC, sub = threadIdx.x % TPC;
     DT s = 0;
@@ -137,7 +141,7 @@ __device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh
 }
 
 // block reduction of NV values per thread; result in sh_out[0..NV) (all threads)
-template <typename DT, int NV>
+template <typename DT, int NT, int NV>
 __device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8], DT *sh_out)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -151,7 +155,7 @@ __device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8], DT *sh_out
     __syncthreads();
     if (threadIdx.x < NV) {
         DT s = 0;
-        for (int w = 0; w < PCG_T / 32; ++w) s += sh[w][threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) s += sh[w][threadIdx.x];
         sh_out[threadIdx.x] = s;
     }
     __syncthreads();
@@ -162,7 +166,7 @@ struct PcgSmem {
     size_t o_H, o_pb, o_po, o_lc, o_M, o_C, o_r, o_d, o_z, o_p, o_q, o_qs, total;
 };
 
-__host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncache)
+__host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncache, int nt)
 {
     PcgSmem L;
     size_t o = 0;
@@ -177,32 +181,33 @@ __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncach
     L.o_z = o; o += (size_t)rows * 12;
     L.o_p = o; o += (size_t)rows * 12;
     L.o_q = o; o += (size_t)rows * 12;
-    L.o_qs = o; o += (size_t)ROWS_PER_PASS * 12;   // split partial products of q
+    L.o_qs = o; o += (size_t)(nt / 12) * 12;       // split partial products of q
     L.total = o;
     return L;
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
+// the solve of one problem by CTA `cta` of the `nb` CTAs given to it
+template <typename DT, int NT>
+__device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const unsigned nb)
 {
+    constexpr int ROWS_PER_PASS = RowsPerPass<NT>::v;
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_flag;
-    __shared__ DT s_red[PCG_T / 32][8];
+    __shared__ DT s_red[NT / 32][8];
     __shared__ DT s_sum[8];
     __shared__ DT s_blk[8];
     __shared__ float s_pp[6], s_zp[6], s_qp[6], s_rpose[6], s_dpose[6];
     __shared__ float s_Hpp[36], s_Mp[36];
     __shared__ DT s_rho, s_beta, s_rr, s_res0, s_alpha;
     __shared__ int s_break;
-    const unsigned nb = gridDim.x;
     unsigned target = 0;
     const int m = a.m;
-    const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
+    const int r0 = a.cta_rows[cta], r1 = a.cta_rows[cta + 1];
     const int rows = r1 - r0;
     const int b0 = a.row_ptr[r0], nblk = a.row_ptr[r1] - b0;
     const int ncache = min(nblk, a.n_cache);
-    const PcgSmem L = pcg_smem_layout(a.max_rows, a.max_blk, a.n_cache);
+    const PcgSmem L = pcg_smem_layout(a.max_rows, a.max_blk, a.n_cache, NT);
     float *Hs = sm + L.o_H, *pb = sm + L.o_pb, *po = sm + L.o_po, *Ms = sm + L.o_M, *Cs = sm + L.o_C;
     float *rs = sm + L.o_r, *ds = sm + L.o_d, *zs = sm + L.o_z, *ps = sm + L.o_p, *qs = sm + L.o_q;
     float *qsplit = sm + L.o_qs;
@@ -223,13 +228,13 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
     {
         const float4 *src = reinterpret_cast<const float4 *>(a.bsr + (size_t)b0 * 144);
         float4 *dst = reinterpret_cast<float4 *>(Hs);
-        for (int i = t; i < ncache * 36; i += PCG_T) dst[i] = __ldg(src + i);
+        for (int i = t; i < ncache * 36; i += NT) dst[i] = __ldg(src + i);
         const float4 *ms = reinterpret_cast<const float4 *>(a.minv + (size_t)r0 * 144);
         float4 *md = reinterpret_cast<float4 *>(Ms);
-        for (int i = t; i < rows * 36; i += PCG_T) md[i] = __ldg(ms + i);
-        for (int i = t; i < rows * 72; i += PCG_T) Cs[i] = __ldg(a.pnode + (size_t)r0 * 72 + i);
-        for (int i = t; i < nblk; i += PCG_T) lc[i] = __ldg(a.col + b0 + i);
-        for (int i = t; i < rows * 12; i += PCG_T) {
+        for (int i = t; i < rows * 36; i += NT) md[i] = __ldg(ms + i);
+        for (int i = t; i < rows * 72; i += NT) Cs[i] = __ldg(a.pnode + (size_t)r0 * 72 + i);
+        for (int i = t; i < nblk; i += NT) lc[i] = __ldg(a.col + b0 + i);
+        for (int i = t; i < rows * 12; i += NT) {
             rs[i] = -__ldg(a.grad + 12 * r0 + i);
             ds[i] = 0.f;
         }
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
     // the block columns' z (and previous p) from their owners, issued together
     // with the loads of the reduction that follows each barrier
     auto stage_columns = [&](const float *pprev) {
-        for (int i = t; i < nblk * 3; i += PCG_T) {
+        for (int i = t; i < nblk * 3; i += NT) {
             const int lb = i / 3, q4 = i - 3 * lb;
             const int l = lc[lb];
             reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] =
@@ -293,23 +298,23 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
         DT rz = 0, rrs = 0;
         precond(rz, rrs);
         DT vv[2] = {rz, rrs};
-        block_sum_n<DT, 2>(vv, s_red, s_blk);
+        block_sum_n<DT, NT, 2>(vv, s_red, s_blk);
     }
     if (t == 0) {
         DT v1 = s_blk[0], v2 = s_blk[1];
-        if (blockIdx.x == 0) {
+        if (cta == 0) {
             for (int i = 0; i < 6; ++i) {
                 s_rpose[i] = -a.grad[P + i];
                 s_dpose[i] = 0.f;
             }
             pose_precond(v1, v2);
         }
-        *part_at(part0, 0, blockIdx.x) = (double)v1;
-        *part_at(part0, 1, blockIdx.x) = (double)v2;
+        *part_at(part0, 0, cta) = (double)v1;
+        *part_at(part0, 1, cta) = (double)v2;
     }
     if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
     stage_columns(nullptr);
-    sum_partials<DT, 2>(part0, nb, s_red, s_sum);
+    sum_partials<DT, NT, 2>(part0, nb, s_red, s_sum);
     if (t == 0) {
         s_rho = s_sum[0];
         s_rr = s_sum[1];
@@ -327,8 +332,8 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
         float *pnew = (it & 1) ? a.p1 : a.p0;
         // ---- p = z + beta p(prev): block columns (staged), own rows (published), pose ----
         if (it > 0)
-            for (int i = t; i < nblk * 12; i += PCG_T) pb[i] = __fmaf_rn(beta, po[i], pb[i]);
-        for (int i = t; i < rows * 12; i += PCG_T) {
+            for (int i = t; i < nblk * 12; i += NT) pb[i] = __fmaf_rn(beta, po[i], pb[i]);
+        for (int i = t; i < rows * 12; i += NT) {
             const float pv = it > 0 ? __fmaf_rn(beta, ps[i], zs[i]) : zs[i];
             ps[i] = pv;
             pnew[12 * r0 + i] = pv;
@@ -376,12 +381,12 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
         }
         {
             DT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
-            block_sum_n<DT, 7>(vv, s_red, s_blk);
-            if (t < 7) *part_at(part1, t, blockIdx.x) = (double)s_blk[t];
+            block_sum_n<DT, NT, 7>(vv, s_red, s_blk);
+            if (t < 7) *part_at(part1, t, cta) = (double)s_blk[t];
         }
         if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         // ---- phase B: alpha, d += alpha p, r -= alpha q, z = M^-1 r ----
-        sum_partials<DT, 7>(part1, nb, s_red, s_sum);
+        sum_partials<DT, NT, 7>(part1, nb, s_red, s_sum);
         if (t < 6) {
             float qi = (float)s_sum[1 + t];
             for (int k = 0; k < 6; ++k) qi += Hpp[6 * t + k] * s_pp[k];
@@ -393,12 +398,12 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
             for (int i = 0; i < 6; ++i) pqt += (DT)s_pp[i] * (DT)s_qp[i];
             s_break = !(pqt > (DT)0);
             s_alpha = rho / pqt;
-            if (s_break && blockIdx.x == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
+            if (s_break && cta == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
         }
         __syncthreads();
         if (s_break) break;
         const float alpha = (float)s_alpha;
-        for (int i = t; i < rows * 12; i += PCG_T) {
+        for (int i = t; i < rows * 12; i += NT) {
             ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
             rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
         }
@@ -407,23 +412,23 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
             DT rz2 = 0, rr2 = 0;
             precond(rz2, rr2);
             DT vv[2] = {rz2, rr2};
-            block_sum_n<DT, 2>(vv, s_red, s_blk);
+            block_sum_n<DT, NT, 2>(vv, s_red, s_blk);
         }
         if (t == 0) {
             DT w1 = s_blk[0], w2 = s_blk[1];
-            if (blockIdx.x == 0) {
+            if (cta == 0) {
                 for (int i = 0; i < 6; ++i) {
                     s_dpose[i] = __fmaf_rn(alpha, s_pp[i], s_dpose[i]);
                     s_rpose[i] = __fmaf_rn(-alpha, s_qp[i], s_rpose[i]);
                 }
                 pose_precond(w1, w2);
             }
-            *part_at(part0, 0, blockIdx.x) = (double)w1;
-            *part_at(part0, 1, blockIdx.x) = (double)w2;
+            *part_at(part0, 0, cta) = (double)w1;
+            *part_at(part0, 1, cta) = (double)w2;
         }
         if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         stage_columns(pnew);
-        sum_partials<DT, 2>(part0, nb, s_red, s_sum);
+        sum_partials<DT, NT, 2>(part0, nb, s_red, s_sum);
         if (t == 0) {
             s_beta = s_sum[0] / rho;
             s_rho = s_sum[0];
@@ -432,31 +437,72 @@ __global__ void __launch_bounds__(PCG_T, 1) k_pcg(PcgArgs a)
         __syncthreads();
     }
     // solution of the CTA's rows (and of the pose: CTA 0)
-    for (int i = t; i < rows * 12; i += PCG_T) a.d[12 * r0 + i] = ds[i];
-    if (blockIdx.x == 0 && t < 6) a.d[P + t] = s_dpose[t];
-    if (blockIdx.x == 0 && t == 0 && a.stats) {
+    for (int i = t; i < rows * 12; i += NT) a.d[12 * r0 + i] = ds[i];
+    if (cta == 0 && t < 6) a.d[P + t] = s_dpose[t];
+    if (cta == 0 && t == 0 && a.stats) {
         a.stats->pcg_iters = it;
         a.stats->pcg_res0 = (double)s_res0;
         a.stats->pcg_res = sqrt((double)s_rr);
     }
 }
 
-// balanced row partition (by block count) and the shared-memory plan; called
-// at graph build with the row pointer copied to the host
-ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st)
+template <typename DT, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_pcg(PcgArgs a)
 {
-    const int m = ctx->m;
-    int grid = ctx->num_sms;
-    if (grid > ED_MAX_PCG_GRID) grid = ED_MAX_PCG_GRID;
-    if (grid > m) grid = m;
+    pcg_body<DT, NT>(a, blockIdx.x, gridDim.x);
+}
+
+// many independent problems in one persistent launch: CTAs [cta_first[p],
+// cta_first[p+1]) solve problem p with their own barrier and partials
+struct PcgBatchParams {
+    int count;
+    int cta_first[ED_MAX_BATCH_LAUNCH + 1];
+    PcgArgs probs[ED_MAX_BATCH_LAUNCH];
+};
+
+template <typename DT, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_pcg_batch(const __grid_constant__ PcgBatchParams b)
+{
+    int p = 0;
+    while (p + 1 < b.count && (int)blockIdx.x >= b.cta_first[p + 1]) ++p;
+    pcg_body<DT, NT>(b.probs[p], (int)blockIdx.x - b.cta_first[p], (unsigned)(b.cta_first[p + 1] - b.cta_first[p]));
+}
+
+// the dynamic shared-memory limit of every PCG kernel, raised once per device
+static std::mutex g_attr_mutex;
+static bool g_attr_done[256];
+
+static ed_status pcg_set_attributes()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ED_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (g_attr_done[dev]) return ED_OK;
+    const int big = PCG_SMEM_MAX, small = PCG_SMEM_MAX_256;
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
+    g_attr_done[dev] = true;
+    return ED_OK;
+}
+
+// balanced row partition of one problem over `grid` CTAs (by block count, at
+// least one row each) and its shared-memory plan for NT threads per CTA
+ed_status ed_pcg_make_plan(const int *row_ptr_host, int m, int grid, int nt, ed_pcg_plan_t *pl, int *rows_start)
+{
+    if (grid < 1 || grid > m || grid > ED_MAX_PCG_GRID || (nt != 256 && nt != 512)) return ED_ERR_ARG;
     const int nnzb = row_ptr_host[m];
-    int rows_start[ED_MAX_PCG_GRID + 1];
     int r = 0;
     rows_start[0] = 0;
     for (int c = 1; c < grid; ++c) {
         const long want = (long)nnzb * c / grid;
         while (r < m && row_ptr_host[r] < want) ++r;
-        if (r < rows_start[c - 1] + 1) r = rows_start[c - 1] + 1;   // at least one row per CTA
+        if (r < rows_start[c - 1] + 1) r = rows_start[c - 1] + 1;
         if (r > m - (grid - c)) r = m - (grid - c);
         rows_start[c] = r;
     }
@@ -468,39 +514,54 @@ ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st)
         if (rw > max_rows) max_rows = rw;
         if (nbk > max_blk) max_blk = nbk;
     }
-    const PcgSmem base = pcg_smem_layout(max_rows, max_blk, 0);
+    const size_t smem_max = nt == 512 ? PCG_SMEM_MAX : PCG_SMEM_MAX_256;
+    const PcgSmem base = pcg_smem_layout(max_rows, max_blk, 0, nt);
     const size_t base_bytes = base.total * sizeof(float);
-    if (base_bytes > PCG_SMEM_MAX) return ED_ERR_CAPACITY;
-    int ncache = (int)((PCG_SMEM_MAX - base_bytes) / (144 * sizeof(float)));
+    if (base_bytes > smem_max) return ED_ERR_CAPACITY;
+    int ncache = (int)((smem_max - base_bytes) / (144 * sizeof(float)));
     if (ncache > max_blk) ncache = max_blk;
-    const PcgSmem full = pcg_smem_layout(max_rows, max_blk, ncache);
-    ctx->pcg_grid = grid;
-    ctx->pcg_cache = ncache;
-    ctx->pcg_smem = full.total * sizeof(float);
-    ctx->pcg_max_rows = max_rows;
-    ctx->pcg_max_blk = max_blk;
+    pl->grid = grid;
+    pl->nt = nt;
+    pl->ncache = ncache;
+    pl->max_rows = max_rows;
+    pl->max_blk = max_blk;
+    pl->smem = pcg_smem_layout(max_rows, max_blk, ncache, nt).total * sizeof(float);
+    return ED_OK;
+}
+
+// plan of the single-problem solve (one 512-thread CTA per SM); called at graph
+// build with the row pointer copied to the host
+ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st)
+{
+    ed_status s = pcg_set_attributes();
+    if (s != ED_OK) return s;
+    const int m = ctx->m;
+    int grid = ctx->num_sms;
+    if (grid > ED_MAX_PCG_GRID) grid = ED_MAX_PCG_GRID;
+    if (grid > m) grid = m;
+    int rows_start[ED_MAX_PCG_GRID + 1];
+    ed_pcg_plan_t pl;
+    if ((s = ed_pcg_make_plan(row_ptr_host, m, grid, 512, &pl, rows_start)) != ED_OK) return s;
+    ctx->pcg = pl;
+    memcpy(ctx->row_ptr_host, row_ptr_host, sizeof(int) * (m + 1));
     ED_CUDA_TRY(cudaMemcpyAsync(ctx->pcg_rows, rows_start, sizeof(int) * (grid + 1), cudaMemcpyHostToDevice, st));
-    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->pcg_smem));
-    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->pcg_smem));
     ED_CUDA_TRY(cudaStreamSynchronize(st));   // rows_start lives on this stack frame
     return ED_OK;
 }
 
-ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st)
+static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const int *cta_rows,
+                               const ed_solver_params *prm, ed_stats *stats, PcgArgs &a)
 {
     const size_t P = ctx->vec_stride;
-    const bool mixed = prm->precision == ED_PRECISION_MIXED;
-    if (ctx->pcg_grid <= 0) return ED_ERR_STATE;
-    PcgArgs a;
     a.m = ctx->m;
     a.n_iter = prm->n_pcg;
     a.tol = prm->pcg_tol;
     a.row_ptr = ctx->row_ptr;
     a.col = ctx->col;
-    a.cta_rows = ctx->pcg_rows;
-    a.n_cache = ctx->pcg_cache;
-    a.max_rows = ctx->pcg_max_rows;
-    a.max_blk = ctx->pcg_max_blk;
+    a.cta_rows = cta_rows;
+    a.n_cache = pl.ncache;
+    a.max_rows = pl.max_rows;
+    a.max_blk = pl.max_blk;
     a.bsr = ctx->bsr;
     a.pnode = ctx->pnode;
     a.minv = ctx->minv;
@@ -519,17 +580,127 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *s
     for (int i = 0; i < 4; ++i)
         if ((uintptr_t)vv[i] & 15) return ED_ERR_STATE;
     if (((uintptr_t)a.bsr & 15) || ((uintptr_t)a.minv & 15)) return ED_ERR_STATE;
+    return ED_OK;
+}
+
+static cudaError_t launch_coop(const void *fn, int grid, int nt, void **args, size_t smem, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st)
+{
+    const bool mixed = prm->precision == ED_PRECISION_MIXED;
+    if (ctx->pcg.grid <= 0) return ED_ERR_STATE;
+    PcgArgs a;
+    ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, stats, a);
+    if (s != ED_OK) return s;
     ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_BAR, 0, 2 * sizeof(int), st));
     void *args[] = {&a};
     ed_tm_begin(ctx, ED_KERNEL_PCG, st);
     ed_note_launch();
-    cudaError_t e = mixed ? cudaLaunchCooperativeKernel((const void *)k_pcg<double>, ctx->pcg_grid, PCG_T, args,
-                                                        ctx->pcg_smem, st)
-                          : cudaLaunchCooperativeKernel((const void *)k_pcg<float>, ctx->pcg_grid, PCG_T, args,
-                                                        ctx->pcg_smem, st);
+    const void *fn = mixed ? (const void *)k_pcg<double, 512> : (const void *)k_pcg<float, 512>;
+    cudaError_t e = launch_coop(fn, ctx->pcg.grid, 512, args, ctx->pcg.smem, st);
     ed_tm_end(ctx, ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: PCG launch failed: %s\n", cudaGetErrorString(e));
+        return ED_ERR_CUDA;
+    }
+    return ED_OK;
+}
+
+// Plan of one batched launch: CTAs split over the problems in proportion to
+// their stored blocks (at least one each, at most one per node row), each
+// problem's rows partitioned over its CTAs; row starts go to pcg_rows_b.
+ed_status ed_pcg_batch_plan(ed_context *const *ctxs, int count, int nt, int grid_total, ed_pcg_batch_plan_t *bp)
+{
+    ed_status s = pcg_set_attributes();
+    if (s != ED_OK) return s;
+    if (count < 1 || count > ED_MAX_BATCH_LAUNCH || (nt != 256 && nt != 512)) return ED_ERR_ARG;
+    if (grid_total < count) return ED_ERR_CAPACITY;
+    long tot = 0;
+    for (int p = 0; p < count; ++p) tot += ctxs[p]->nnzb;
+    int alloc[ED_MAX_BATCH_LAUNCH];
+    int used = 0;
+    for (int p = 0; p < count; ++p) {
+        long c = tot > 0 ? (long)grid_total * ctxs[p]->nnzb / tot : 1;
+        if (c < 1) c = 1;
+        if (c > ctxs[p]->m) c = ctxs[p]->m;
+        if (c > ED_MAX_PCG_GRID) c = ED_MAX_PCG_GRID;
+        alloc[p] = (int)c;
+        used += (int)c;
+    }
+    // trim or hand out the remainder, largest work per CTA first
+    while (used > grid_total) {
+        int best = -1;
+        for (int p = 0; p < count; ++p)
+            if (alloc[p] > 1 && (best < 0 || (double)ctxs[p]->nnzb / alloc[p] < (double)ctxs[best]->nnzb / alloc[best]))
+                best = p;
+        if (best < 0) return ED_ERR_CAPACITY;
+        --alloc[best];
+        --used;
+    }
+    while (used < grid_total) {
+        int best = -1;
+        for (int p = 0; p < count; ++p)
+            if (alloc[p] < ctxs[p]->m && alloc[p] < ED_MAX_PCG_GRID &&
+                (best < 0 || (double)ctxs[p]->nnzb / alloc[p] > (double)ctxs[best]->nnzb / alloc[best]))
+                best = p;
+        if (best < 0) break;
+        ++alloc[best];
+        ++used;
+    }
+    bp->count = count;
+    bp->nt = nt;
+    bp->smem = 0;
+    bp->cta_first[0] = 0;
+    static thread_local int rows_start[ED_MAX_PCG_GRID + 1];
+    for (int p = 0; p < count; ++p) {
+        ed_context *c = ctxs[p];
+        if (!c->have_graph) return ED_ERR_STATE;
+        if ((s = ed_pcg_make_plan(c->row_ptr_host, c->m, alloc[p], nt, &bp->plan[p], rows_start)) != ED_OK) return s;
+        ED_CUDA_TRY(cudaMemcpy(c->pcg_rows_b, rows_start, sizeof(int) * (alloc[p] + 1), cudaMemcpyHostToDevice));
+        bp->cta_first[p + 1] = bp->cta_first[p] + alloc[p];
+        if (bp->plan[p].smem > bp->smem) bp->smem = bp->plan[p].smem;
+    }
+    bp->grid = bp->cta_first[count];
+    return ED_OK;
+}
+
+// one persistent launch for the PCG solves of a planned group of problems
+ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t *bp, const ed_solver_params *const *prm,
+                             ed_stats *const *stats, cudaStream_t st)
+{
+    const int count = bp->count;
+    const bool mixed = prm[0]->precision == ED_PRECISION_MIXED;
+    PcgBatchParams b;
+    memset(&b, 0, sizeof(b));
+    b.count = count;
+    for (int p = 0; p <= count; ++p) b.cta_first[p] = bp->cta_first[p];
+    for (int p = 0; p < count; ++p) {
+        if ((prm[p]->precision == ED_PRECISION_MIXED) != mixed) return ED_ERR_ARG;
+        ed_status s = pcg_fill_args(ctxs[p], bp->plan[p], ctxs[p]->pcg_rows_b, prm[p], stats[p], b.probs[p]);
+        if (s != ED_OK) return s;
+        ED_CUDA_TRY(cudaMemsetAsync(ctxs[p]->misc + MI_BAR, 0, 2 * sizeof(int), st));
+    }
+    void *args[] = {&b};
+    const void *fn;
+    if (bp->nt == 512) fn = mixed ? (const void *)k_pcg_batch<double, 512> : (const void *)k_pcg_batch<float, 512>;
+    else fn = mixed ? (const void *)k_pcg_batch<double, 256> : (const void *)k_pcg_batch<float, 256>;
+    ed_note_launch();
+    cudaError_t e = launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "libed: batched PCG launch failed: %s\n", cudaGetErrorString(e));
         return ED_ERR_CUDA;
     }
     return ED_OK;

@@ -1,0 +1,209 @@
+"""Batched Gauss-Newton iterations over independent problems (one persistent
+PCG launch per group of problems, CUDA-graph replay, the measuring
+autotuner), checked against the single-problem path and the FP64 oracle."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import gpu_common as C
+
+pytestmark = pytest.mark.gpu
+
+N_IT = 2
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _E():
+    import paper_1803_02009_b300 as E
+    return E
+
+
+def _member_scenes():
+    """Two 160x120 scenes with the 8x8 node grid and three 320x240 scenes with
+    Poisson-disk nodes (200, 311, 405 nodes), one bump each."""
+    out = [(synth.make_scene("tissue_160x120_n64", seed), None) for seed in (1, 2)]
+    base = synth.CONFIGS["tissue_320x240"]
+    for i, m in enumerate((200, 311, 405)):
+        cfg = dataclasses.replace(base, name=f"tissue_320x240_b{i}", node_count=m, n_gn=N_IT, n_pcg=10)
+        out.append((synth.make_scene(cfg, 10 + i), m))
+    return out
+
+
+_CACHE = {}
+
+
+def _setup():
+    if "p" in _CACHE:
+        return _CACHE["p"]
+    torch, E = _torch(), _E()
+    probs = []
+    for k, (s, m) in enumerate(_member_scenes()):
+        fx, fy, cx, cy, W, H = s.intr
+        cap = 64 if m is None else m
+        ctx = E.Context(max_points=s.N, max_nodes=cap, max_width=W, max_height=H, max_cells=1 << 24)
+        pos = torch.from_numpy(s.model_pos).cuda()
+        nrm = torch.from_numpy(s.model_nrm).cuda()
+        depth = torch.from_numpy(s.tgt_depth).cuda()
+        nmap = ctx.compute_normals(depth, s.intr, s.cfg.normal_half_width)
+        if m is None:
+            g = ctx.build_graph(pos, nrm, nodes=torch.from_numpy(s.nodes).cuda(), sigma=s.sigma)
+        else:
+            r = E.calibrate_radius(ctx, pos, nrm, m)
+            g = ctx.build_graph(pos, nrm, node_radius=r, max_nodes=m, sigma=r)
+        rng = np.random.default_rng(100 + k)
+        x0 = np.zeros((g.m, 12))
+        x0[:, [0, 5, 10]] = 1.0
+        x0 = (x0 + rng.normal(0, 1e-3, x0.shape)).astype(np.float32)
+        pose0 = np.asarray(s.pose_prior) + rng.normal(0, 1e-3, 6)
+        prm = E.SolverParams(n_pcg=10, prior=tuple(float(v) for v in s.pose_prior))
+        probs.append(dict(s=s, ctx=ctx, pos=pos, nrm=nrm, depth=depth, nmap=nmap, graph=g,
+                          frame=E.make_frame(depth, nmap, s.intr), x0=x0, pose0=pose0, prm=prm))
+    torch.cuda.synchronize()
+    _CACHE["p"] = probs
+    return probs
+
+
+def _fresh_state(probs):
+    torch = _torch()
+    xs = [torch.from_numpy(p["x0"]).cuda() for p in probs]
+    poses = [torch.from_numpy(p["pose0"].copy()).cuda() for p in probs]
+    return xs, poses
+
+
+def _single_results(probs, n_it):
+    """Every problem alone through ed_gn_step."""
+    torch, E = _torch(), _E()
+    out = []
+    for p in probs:
+        x = torch.from_numpy(p["x0"]).cuda()
+        pose = torch.from_numpy(p["pose0"].copy()).cuda()
+        for _ in range(n_it):
+            p["ctx"].gn_step(p["frame"], p["prm"], x, pose)
+        out.append((x.cpu().numpy(), pose.cpu().numpy()))
+    torch.cuda.synchronize()
+    return out
+
+
+def _close(a, b, tol):
+    return (np.abs(a - b) / np.maximum(1.0, np.abs(b))).max() <= tol
+
+
+@pytest.fixture(scope="module")
+def batch_env():
+    torch, E = _torch(), _E()
+    probs = _setup()
+    B = E.Batch([p["ctx"] for p in probs])
+    xs, poses = _fresh_state(probs)
+    stats = [E.new_stats(N_IT) for _ in probs]
+    B.bind([p["frame"] for p in probs], [p["prm"] for p in probs], xs, poses, stats=stats)
+    return dict(probs=probs, B=B, xs=xs, poses=poses, stats=stats, single=_single_results(probs, N_IT))
+
+
+def _reset(env):
+    for p, x, q in zip(env["probs"], env["xs"], env["poses"]):
+        x.copy_(_torch().from_numpy(p["x0"]))
+        q.copy_(_torch().from_numpy(p["pose0"]))
+
+
+def test_batch_eager_matches_single_problem_path(batch_env):
+    torch, E = _torch(), _E()
+    env = batch_env
+    _reset(env)
+    for _ in range(N_IT):
+        env["B"].gn_step()
+    torch.cuda.synchronize()
+    for k, (x, q) in enumerate(zip(env["xs"], env["poses"])):
+        xs, ps = env["single"][k]
+        assert _close(x.cpu().numpy(), xs, C.TOL_X), k
+        assert _close(q.cpu().numpy(), ps, C.TOL_X), k
+        st = E.read_stats(env["stats"][k])[0]   # eager calls write entry 0
+        assert st["status"] == 0 and st["pcg_iters"] == 10
+    env["eager"] = [(x.cpu().numpy(), q.cpu().numpy()) for x, q in zip(env["xs"], env["poses"])]
+
+
+def test_batch_graph_replay_equals_eager(batch_env):
+    torch = _torch()
+    env = batch_env
+    if "eager" not in env:
+        pytest.skip("needs the eager run")
+    _reset(env)
+    env["B"].capture(n_iters=N_IT)
+    env["B"].launch()
+    torch.cuda.synchronize()
+    for k, (x, q) in enumerate(zip(env["xs"], env["poses"])):
+        # same schedule, same kernels, fixed-order reductions: bit for bit
+        assert np.array_equal(x.cpu().numpy(), env["eager"][k][0]), k
+        assert np.array_equal(q.cpu().numpy(), env["eager"][k][1]), k
+    # a second replay from the same start gives the same result again
+    _reset(env)
+    env["B"].launch()
+    torch.cuda.synchronize()
+    assert all(np.array_equal(x.cpu().numpy(), env["eager"][k][0]) for k, x in enumerate(env["xs"]))
+
+
+def test_batch_schedules_agree_and_autotune_restores_state(batch_env):
+    torch, E = _torch(), _E()
+    env = batch_env
+    B = env["B"]
+    n = len(env["probs"])
+    results = {}
+    for nt in (512, 256):
+        for ppl in (1, 2, n):
+            B.set_schedule(nt, ppl, 4)
+            _reset(env)
+            for _ in range(N_IT):
+                B.gn_step()
+            torch.cuda.synchronize()
+            results[(nt, ppl)] = [x.cpu().numpy() for x in env["xs"]]
+            for k in range(n):
+                assert _close(results[(nt, ppl)][k], env["single"][k][0], C.TOL_X), (nt, ppl, k)
+    _reset(env)
+    before = [(x.cpu().numpy(), q.cpu().numpy()) for x, q in zip(env["xs"], env["poses"])]
+    sched, ms = B.autotune()
+    torch.cuda.synchronize()
+    assert sched["pcg_threads"] in (256, 512) and 1 <= sched["problems_per_launch"] <= n and ms > 0
+    for k, (x, q) in enumerate(zip(env["xs"], env["poses"])):
+        assert np.array_equal(x.cpu().numpy(), before[k][0])
+        assert np.array_equal(q.cpu().numpy(), before[k][1])
+    assert B.schedule() == sched
+    with pytest.raises(E.EDError):
+        B.set_schedule(384, 1, 4)
+    assert B.schedule() == sched
+
+
+def test_batch_member_matches_oracle_one_step(batch_env):
+    """One batched iteration of a 320x240 member against the oracle's FP64
+    normal equations and block-Jacobi PCG at the GPU's association."""
+    torch, E = _torch(), _E()
+    env = batch_env
+    k = 3
+    p = env["probs"][k]
+    s = p["s"]
+    _reset(env)
+    wpos = torch.empty((s.N, 4), dtype=torch.float32, device="cuda")
+    wnrm = torch.empty_like(wpos)
+    pix = torch.empty(s.N, dtype=torch.int32, device="cuda")
+    p["ctx"].set_debug(wpos, wnrm, pix)
+    env["B"].gn_step()
+    torch.cuda.synchronize()
+    p["ctx"].set_debug(None, None, None)
+    ref_pix = oracle.associate_f32(wpos.cpu().numpy(), wnrm.cpu().numpy(), s.tgt_depth, p["nmap"].cpu().numpy(),
+                                   s.intr)
+    assert np.array_equal(ref_pix, pix.cpu().numpy())
+    G = dict(graph=p["graph"], nmap=p["nmap"])
+    P = C.oracle_problem_from_gpu(s, G)
+    Q = oracle.NormalEq(P, p["x0"].astype(np.float64), p["pose0"], pix_in=pix.cpu().numpy())
+    st = E.read_stats(env["stats"][k])[0]
+    assert st["energy"] == pytest.approx(Q.energy, rel=C.TOL_E)
+    d, _, _, _ = Q.pcg(-Q.g, p["prm"].n_pcg, jitter=p["prm"].jitter)
+    m = P.m
+    x_ref = p["x0"].astype(np.float64) + d[:12 * m].reshape(m, 12)
+    assert _close(env["xs"][k].cpu().numpy(), x_ref, C.TOL_X)
+    assert _close(env["poses"][k].cpu().numpy(), p["pose0"] + d[12 * m:], C.TOL_X)
