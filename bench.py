@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--workload", default="single", choices=["single", "batch16"],
+                    help="batch16: 16 independent problems (320x240 / 640x480 / 1280x720, 200-4096 nodes) "
+                         "as one batched, graph-captured GN iteration vs 16 sequential solves")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -78,55 +81,90 @@ def whole_job_rate(world, steps, gn_per_step, seconds):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """SM clocks and throttle reasons sampled through NVML every 2 ms during the
+    timed region (read-only queries); nvidia-smi is the fallback."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+    def __init__(self, cuda_index):
+        self.cuda_index = cuda_index
+        self.sm, self.reasons, self.smax = [], set(), None
+        self.stop_ev = threading.Event()
+        self.thread = None
+        self.mode = None
+
+    def _handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.cuda_index).uuid)
+            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode())
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.cuda_index)
+
+    def _poll_nvml(self, nv, h):
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_ev.is_set():
+            try:
+                self.sm.append(float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)))
+                bits = int(get_reasons(h))
+                for bit, name in self.REASONS.items():
+                    if bits & bit:
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            self.stop_ev.wait(0.002)
+
+    def _poll_smi(self):
+        fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            proc = subprocess.Popen(["nvidia-smi", f"--id={self.cuda_index}", f"--query-gpu={fields}",
+                                     "--format=csv,noheader,nounits", "-lms", "100"],
+                                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.proc = proc
+        for line in proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                self.sm.append(float(parts[0]))
+                self.smax = max(self.smax or 0.0, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    self.reasons.add(nm)
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            nv, h = self._handle()
+            self.smax = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            self.mode = "nvml"
+            self.thread = threading.Thread(target=self._poll_nvml, args=(nv, h), daemon=True)
         except Exception:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.mode = "nvidia-smi"
+            self.thread = threading.Thread(target=self._poll_smi, daemon=True)
+        try:
+            self.thread.start()
+        except Exception:
+            self.mode = None
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        if self.mode is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock query unavailable"]}
+        self.stop_ev.set()
+        if self.mode == "nvidia-smi" and getattr(self, "proc", None) is not None:
+            self.proc.terminate()
+        self.thread.join(timeout=5)
+        return {"sm_mhz": statistics.median(self.sm) if self.sm else None, "sm_max_mhz": self.smax,
+                "reasons": sorted(self.reasons), "samples": len(self.sm), "source": self.mode}
 
 
 def measured_peaks():
@@ -138,13 +176,21 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def pcg_bytes_per_launch(m, nnzb, n_pcg):
-    """Algorithmic bytes of one PCG launch: per iteration the 12x12 blocks,
-    pose-node blocks, block inverses and 11 vector passes of 12m+6 floats; plus
-    the set-up pass (inverses and 4 vector passes)."""
+def pcg_bytes_per_launch(m, n_upper, n_pcg):
+    """Algorithmic bytes of one PCG launch (n_pcg iterations): per iteration the
+    upper 12x12 blocks (576 B each), the block inverses (576 B per node) and 8
+    FP32 vector passes over the P = 12m + 6 unknowns."""
     P = 12 * m + 6
-    per_iter = nnzb * 576 + m * 288 + m * 576 + 11 * P * 4
-    return n_pcg * per_iter + m * 576 + 4 * P * 4
+    return n_pcg * (n_upper * 576 + m * 576 + 8 * P * 4)
+
+
+def gn_bytes_per_iteration(n_points, n_valid, m, n_upper, n_pcg):
+    """Algorithmic bytes of one Gauss-Newton iteration: the point pass (60 B per
+    associated point: position, normal, node indices, depth, target normal;
+    40 B per other point), writing the upper blocks and pose-node blocks, and
+    the PCG launch."""
+    return (n_valid * 60 + (n_points - n_valid) * 40 + n_upper * 576 + m * 288
+            + pcg_bytes_per_launch(m, n_upper, n_pcg))
 
 
 # ----------------------------------------------------------------------------
@@ -287,7 +333,11 @@ def run_ours(args, rank, world, local):
     e2e_value = whole_job_rate(world, K, cfg.n_gn, e2e_s)
 
     peak, peak_kind = measured_peaks()
-    byt = pcg_bytes_per_launch(g.m, g.nnzb, cfg.n_pcg)
+    n_upper = (g.nnzb + g.m) // 2          # symmetric pattern, every diagonal block present
+    byt = pcg_bytes_per_launch(g.m, n_upper, cfg.n_pcg)
+    n_valid_last = int(st_last[-1]["n_valid"])
+    gn_byt = gn_bytes_per_iteration(s.N, n_valid_last, g.m, n_upper, cfg.n_pcg)
+    gn_rate = whole_job_rate(world, K, cfg.n_gn, max_over_ranks(sum(gn_ms) / 1e3, dist, dev)) if gn_ms else None
     avg_pcg_s = (sum(pcg_ms) / len(pcg_ms)) / 1e3 if pcg_ms else float("nan")
     achieved = byt / avg_pcg_s / 1e9
     traffic = None
@@ -309,8 +359,7 @@ def run_ours(args, rank, world, local):
                    "node_radius_mm": radius, "precision": args.precision,
                    "l2": "flushed between steps (512 MB write)",
                    "step": "normals + build_graph + 10 x gn_step + warp + fuse"},
-        "gn_only_iters_per_s": whole_job_rate(world, K, cfg.n_gn, max_over_ranks(sum(gn_ms) / 1e3, dist, dev))
-        if gn_ms else None,
+        "gn_only_iters_per_s": gn_rate,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -318,20 +367,162 @@ def run_ours(args, rank, world, local):
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": byt,
                      "avg_launch_us": avg_pcg_s * 1e6, "launches_timed": len(pcg_ms)},
+        "gn_iteration_roofline": {"bound": "hbm", "algorithmic_bytes": gn_byt,
+                                  "achieved": gn_byt * gn_rate / world / 1e9 if gn_rate else None,
+                                  "peak": peak, "unit": "GB/s",
+                                  "frac": gn_byt * gn_rate / world / 1e9 / peak if gn_rate else None,
+                                  "note": "per GPU, over the GN iterations alone (no graph build, warp, fuse)"},
         "final_stats": {k: st_last[-1][k] for k in ("energy", "n_valid", "pcg_iters", "status")},
     }
     return out, s
 
 
 def kernel_rev():
-    """Content hash of the CUDA sources (ties an ncu traffic figure to a build)."""
+    """Content hash of the PCG kernel sources (ties an ncu traffic figure to a build)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1803_02009_b300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in ("pcg.cu", "ed_internal.cuh"):
         with open(os.path.join(d, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+# batched workload: many independent problems per GN iteration
+# ----------------------------------------------------------------------------
+
+def run_batch(args, rank, world, local):
+    import torch
+    import paper_1803_02009_b300 as E
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    members = synth.batch_scenes(16, seed0=1 + 16 * rank)
+    n_gn, n_pcg = members[0][0].cfg.n_gn, members[0][0].cfg.n_pcg
+    probs = []
+    for s, m in members:
+        fx, fy, cx, cy, W, H = s.intr
+        ctx = E.Context(max_points=s.N, max_nodes=m, max_width=W, max_height=H, max_cells=1 << 24)
+        pos = torch.from_numpy(s.model_pos).cuda()
+        nrm = torch.from_numpy(s.model_nrm).cuda()
+        depth = torch.from_numpy(s.tgt_depth).cuda()
+        nmap = ctx.compute_normals(depth, s.intr, s.cfg.normal_half_width)
+        r = E.calibrate_radius(ctx, pos, nrm, m)
+        g = ctx.build_graph(pos, nrm, node_radius=r, max_nodes=m, sigma=r)
+        x0 = torch.zeros((g.m, 12), dtype=torch.float32, device="cuda")
+        x0[:, 0] = 1.0
+        x0[:, 5] = 1.0
+        x0[:, 10] = 1.0
+        probs.append(dict(s=s, ctx=ctx, keep=(pos, nrm, depth, nmap), g=g, frame=E.make_frame(depth, nmap, s.intr),
+                          prm=E.SolverParams(n_pcg=n_pcg, prior=tuple(float(v) for v in s.pose_prior)),
+                          x0=x0, pose0=torch.tensor(s.pose_prior, dtype=torch.float64, device="cuda")))
+    xs = [p["x0"].clone() for p in probs]
+    poses = [p["pose0"].clone() for p in probs]
+
+    def reset():
+        for p, x, q in zip(probs, xs, poses):
+            x.copy_(p["x0"])
+            q.copy_(p["pose0"])
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    K = args.steps
+
+    # 16 sequential single-problem solves (ed_gn_step, no graph)
+    def sequential():
+        for p, x, q in zip(probs, xs, poses):
+            for _ in range(n_gn):
+                p["ctx"].gn_step(p["frame"], p["prm"], x, q)
+
+    for _ in range(args.warmup):
+        reset()
+        sequential()
+    torch.cuda.synchronize()
+    seq_ms = []
+    for k in range(K):
+        reset()
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sequential()
+        e1.record()
+        e1.synchronize()
+        seq_ms.append(e0.elapsed_time(e1))
+    seq_x = [x.cpu().numpy() for x in xs]
+    reset()
+    for p, x, q in zip(probs, xs, poses):
+        p["ctx"].gn_step(p["frame"], p["prm"], x, q)
+    seq_x1 = [x.cpu().numpy() for x in xs]
+
+    # batched: autotuned schedule, n_gn iterations captured as one CUDA graph
+    B = E.Batch([p["ctx"] for p in probs])
+    stats = [E.new_stats(n_gn) for _ in probs]
+    B.bind([p["frame"] for p in probs], [p["prm"] for p in probs], xs, poses, stats=stats)
+    reset()
+    sched, tune_ms = B.autotune()
+    reset()
+    B.gn_step()
+    torch.cuda.synchronize()
+    diff1 = max(float(np.max(np.abs(x.cpu().numpy() - xr) / np.maximum(1.0, np.abs(xr)))) for x, xr in zip(xs, seq_x1))
+    B.capture(n_iters=n_gn)
+    for _ in range(args.warmup):
+        reset()
+        B.launch()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = E.launch_count()
+    bat_ms = []
+    for k in range(K):
+        reset()
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.stream.wait_stream(torch.cuda.current_stream())   # reset and flush done before the clock starts
+        e0.record(B.stream)
+        B.launch(stream=B.stream)
+        e1.record(B.stream)
+        e1.synchronize()
+        bat_ms.append(e0.elapsed_time(e1))
+    launches = E.launch_count() - l0
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    diff = max(float(np.max(np.abs(x.cpu().numpy() - xr) / np.maximum(1.0, np.abs(xr)))) for x, xr in zip(xs, seq_x))
+    st = [E.read_stats(b)[-1] for b in stats]
+    units = len(probs) * n_gn
+    bat_s = max_over_ranks(sum(bat_ms) / 1e3, dist, "cuda")
+    seq_s = max_over_ranks(sum(seq_ms) / 1e3, dist, "cuda")
+    value = whole_job_rate(world, K, units, bat_s)
+    seq_value = whole_job_rate(world, K, units, seq_s)
+    peak, peak_kind = measured_peaks()
+    gn_bytes = sum(gn_bytes_per_iteration(p["s"].N, int(q["n_valid"]), p["g"].m, (p["g"].nnzb + p["g"].m) // 2, n_pcg)
+                   for p, q in zip(probs, st))
+    achieved = gn_bytes * (value / len(probs)) / world / 1e9    # batched iterations per second per GPU
+    return {
+        "metric": "batched ED GN iters/s (16 independent problems, one CUDA graph per frame)",
+        "value": value, "unit": "GN iters/s (summed over problems)", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": bat_s * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded stereo-scope tissue scenes)",
+        "config": {"workload": "batch16", "problems": [{"W": p["s"].cfg.W, "H": p["s"].cfg.H, "points": p["s"].N,
+                                                         "nodes": p["g"].m} for p in probs],
+                   "gn_iters": n_gn, "pcg_iters": n_pcg, "schedule": sched, "autotune_best_ms": tune_ms,
+                   "l2": "flushed between steps (512 MB write)",
+                   "step": "16 problems x n_gn GN iterations (graph build excluded)"},
+        "sequential": {"value": seq_value, "unit": "GN iters/s", "ms_per_step": seq_s * 1e3 / K,
+                       "what": "the same 16 problems solved one after another through ed_gn_step"},
+        "speedup_vs_sequential": value / seq_value,
+        "max_rel_diff_vs_sequential": {"after_1_gn_iter": diff1, f"after_{n_gn}_gn_iters": diff,
+                                        "note": "different PCG reduction partitions; later iterations re-associate"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "gn_iteration_roofline": {"bound": "hbm", "algorithmic_bytes_per_batched_iteration": gn_bytes,
+                                  "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                                  "frac": achieved / peak},
+        "final_status": [int(q["status"]) for q in st],
+    }
 
 
 # ----------------------------------------------------------------------------
@@ -397,6 +588,11 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
+            print(json.dumps(out))
+        return
+    if args.workload == "batch16":
+        out = run_batch(args, rank, world, local)
+        if rank == 0:
             print(json.dumps(out))
         return
     out, s = run_ours(args, rank, world, local)

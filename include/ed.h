@@ -263,7 +263,10 @@ ed_status ed_fuse(ed_context *ctx, const float *pos, const float *nrm, const flo
 /*
  * Energy of Eq. (3) at (x, pose) with the graph built last (forward of the
  * differentiable warp + energy).  Association is recomputed and stored in
- * the context for ed_energy_grad.  energy_out: device double[6] = (total,
+ * the context for ed_energy_grad.  With Gaussian weights (the graph's
+ * weight_mode) the skinning weights of Eq. (1) are recomputed from the node
+ * indices instead of read from the graph (the same values, bit for bit), here
+ * and in ed_energy_grad.  energy_out: device double[6] = (total,
  * data, rot, reg, rot prior, pos prior).
  */
 ed_status ed_energy(ed_context *ctx, const ed_frame *frame, const ed_solver_params *params, const float *x,

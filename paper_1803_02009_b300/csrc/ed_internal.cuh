@@ -314,6 +314,41 @@ struct ed_warped {
     float3 n;     // normalize(R sum_j w_j A_j n)
 };
 
+// Eq. (1) skinning weights, Gaussian mode, from the keys of the k = 4
+// nearest nodes (slots >= nvalid hold no node): w~_s = exp(-d_s^2 / 2 sigma^2),
+// normalised to sum 1 (1/4 each if all vanish).  Graph build and the
+// recomputation in the energy / gradient path both use this function, so
+// recomputed weights equal the stored ones bit for bit.
+__device__ __forceinline__ float4 ed_gauss_weights_from_keys(const float *kk, int nvalid, float sigma)
+{
+    float w[4], sum = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        float t = s < nvalid ? expf(-kk[s] / (2.0f * sigma * sigma)) : 0.f;
+        if (!(t > 0.f)) t = 0.f;
+        w[s] = t;
+        sum += t;
+    }
+    const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) w[s] = sum > 0.f ? w[s] * inv : 0.25f;
+    return make_float4(w[0], w[1], w[2], w[3]);
+}
+
+// the same weights recomputed from a point and its node indices
+__device__ __forceinline__ float4 ed_gauss_weights(float4 p, ushort4 id, const float4 *__restrict__ g, int m,
+                                                   float sigma)
+{
+    const unsigned short ids[4] = {id.x, id.y, id.z, id.w};
+    float kk[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float4 gs = __ldg(g + ids[s]);
+        kk[s] = ed_key(p.x, p.y, p.z, gs.x, gs.y, gs.z);
+    }
+    return ed_gauss_weights_from_keys(kk, m < 4 ? m : 4, sigma);
+}
+
 __device__ __forceinline__ ed_warped ed_warp_point(float4 p, float4 nr, ushort4 id, float4 w, const float4 *__restrict__ g,
                                                     const float4 *__restrict__ x4, const float *R, const float *T)
 {

@@ -18,6 +18,9 @@ struct PointArgs {
     int n;
     float eps2, cos_eps_n, sw;
     int mode;
+    int recompute_w;   // Gaussian weights recomputed from the node indices (energy / gradient path)
+    int m;
+    float sigma;
     int *pix;          // association (written in STEP / ENERGY, read in GRAD)
     float4 *rec0, *rec1;
     double *part;      // [grid][ED_K1_PART]
@@ -39,7 +42,9 @@ __global__ void __launch_bounds__(ED_K1_THREADS) k_points(PointArgs a)
     for (int k = 0; k < 30; ++k) acc[k] = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const float4 p = a.pos[i], nr = a.nrm[i];
-        const ed_warped W = ed_warp_point(p, nr, a.idx[i], a.w[i], a.g, a.x4, P.R, P.T);
+        const ushort4 id = a.idx[i];
+        const float4 wi = a.recompute_w ? ed_gauss_weights(p, id, a.g, a.m, a.sigma) : a.w[i];
+        const ed_warped W = ed_warp_point(p, nr, id, wi, a.g, a.x4, P.R, P.T);
         int q;
         if (a.mode == PASS_GRAD) q = a.pix[i];
         else {
@@ -138,6 +143,11 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.cos_eps_n = prm->cos_eps_n;
     a.sw = sqrtf(prm->w_data);
     a.mode = mode;
+    // the autograd path (energy, gradient) recomputes Gaussian skinning
+    // weights instead of reading the stored ones (bit-identical values)
+    a.recompute_w = mode != PASS_STEP && ctx->weight_mode == ED_WEIGHT_GAUSSIAN;
+    a.m = ctx->m;
+    a.sigma = ctx->sigma;
     a.pix = ctx->pix;
     a.rec0 = mode == PASS_GRAD ? ctx->gpts : ctx->rec0;
     a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : ctx->rec1;
@@ -945,7 +955,8 @@ extern "C" ed_status ed_energy(ed_context *ctx, const ed_frame *fr, const ed_sol
     return ED_OK;
 }
 
-// dE/dx_j = 2 [ sum_i r_i w_ij sqrt(w) (R^T n) (x) d^_ij  +  rot and reg terms ],
+// dE/dx_j = 2 [ sum_i r_i w_ij sqrt(w) (R^T n) (x) d^_ij  +  rot and reg terms ]
+// (Gaussian w_ij recomputed from the node indices, not read from the graph),
 // gathered per node over the points of its diagonal block (fixed order)
 __global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__restrict__ nbr,
                                                     const int *__restrict__ row_ptr, const int *__restrict__ col,
@@ -953,6 +964,7 @@ __global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__
                                                     const int *__restrict__ ent_cnt, const uint32_t *__restrict__ ent,
                                                     const float4 *__restrict__ g, const float4 *__restrict__ x4,
                                                     const float4 *__restrict__ pos, const float *__restrict__ wts,
+                                                    const ushort4 *__restrict__ idx, int recompute_w, float sigma,
                                                     const float4 *__restrict__ gp0, float w_rot, float w_reg,
                                                     float scale, float *__restrict__ grad)
 {
@@ -970,7 +982,14 @@ __global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__
         const int i = (int)(v >> 4), s = (v >> 2) & 3;
         const float4 r0 = gp0[i];
         const float4 p = pos[i];
-        const float c = wts[4 * i + s] * r0.w;
+        float ws;
+        if (recompute_w) {
+            const float4 w4 = ed_gauss_weights(p, idx[i], g, m, sigma);
+            ws = s == 0 ? w4.x : s == 1 ? w4.y : s == 2 ? w4.z : w4.w;
+        } else {
+            ws = wts[4 * i + s];
+        }
+        const float c = ws * r0.w;
         const float dh[4] = {p.x - gj.x, p.y - gj.y, p.z - gj.z, 1.0f};
         const float nb[3] = {r0.x, r0.y, r0.z};
 #pragma unroll
@@ -1047,7 +1066,9 @@ extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const e
                                                        ctx->diag_pos,
                                                        ctx->ent_start, ctx->ent_cnt, ctx->ent_val,
                                                        (const float4 *)ctx->graph.nodes, (const float4 *)x,
-                                                       (const float4 *)ctx->pos, ctx->graph.weights, ctx->gpts,
+                                                       (const float4 *)ctx->pos, ctx->graph.weights,
+                                                       (const ushort4 *)ctx->graph.idx,
+                                                       ctx->weight_mode == ED_WEIGHT_GAUSSIAN, ctx->sigma, ctx->gpts,
                                                        prm->w_rot, prm->w_reg, grad_scale, grad_x); ed_note_launch();
     k_grad_pose<<<1, 32, 0, st>>>(ctx->k1_part, k1_grid(ctx), pose, *prm, grad_scale, grad_pose); ed_note_launch();
     ED_LAUNCH_CHECK();

@@ -350,29 +350,34 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
             if (kk[need - 1] < b * b * 0.99999f) break;
         }
     }
-    // weights (Eq. 1 normalised; Gaussian or Eq. 2)
-    float w[4], sum = 0.f;
+    // weights (Eq. 1 normalised; Gaussian or Eq. 2); slots >= m hold no node
+    float4 wv;
+    if (mode == ED_WEIGHT_GAUSSIAN) {
+        wv = ed_gauss_weights_from_keys(kk, m < 4 ? m : 4, sigma);
+    } else {
+        float w[4], sum = 0.f;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        float t;
-        if (ii[s] == 0x7fffffff) t = 0.f;
-        else if (mode == ED_WEIGHT_GAUSSIAN) t = expf(-kk[s] / (2.0f * sigma * sigma));
-        else {
-            const float dmax = sqrtf(kk[4]);
-            t = dmax > 0.f ? 1.0f - sqrtf(kk[s]) / dmax : 1.0f;
+        for (int s = 0; s < 4; ++s) {
+            float t;
+            if (ii[s] == 0x7fffffff) t = 0.f;
+            else {
+                const float dmax = sqrtf(kk[4]);
+                t = dmax > 0.f ? 1.0f - sqrtf(kk[s]) / dmax : 1.0f;
+            }
+            if (!(t > 0.f)) t = 0.f;
+            w[s] = t;
+            sum += t;
         }
-        if (!(t > 0.f)) t = 0.f;
-        w[s] = t;
-        sum += t;
-    }
-    const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+        const float inv = sum > 0.f ? 1.0f / sum : 0.f;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) w[s] = sum > 0.f ? w[s] * inv : 0.25f;
+        for (int s = 0; s < 4; ++s) w[s] = sum > 0.f ? w[s] * inv : 0.25f;
+        wv = make_float4(w[0], w[1], w[2], w[3]);
+    }
     unsigned short id4[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) id4[s] = (unsigned short)(ii[s] == 0x7fffffff ? 0 : ii[s]);
     idx_out[i] = make_ushort4(id4[0], id4[1], id4[2], id4[3]);
-    w_out[i] = make_float4(w[0], w[1], w[2], w[3]);
+    w_out[i] = wv;
 }
 
 // N(j): the k_graph nearest other nodes (FP32 key, ties to the lower index).
