@@ -84,12 +84,12 @@ size_t carve(ed_context *c, char *base)
     c->pnode = k.take<float>(M * 72);
     c->minv = k.take<float>(M * 144);
     c->pose_blk = k.take<float>(72);
-    c->node_energy = k.take<double>(M * 2);
+    c->node_energy = k.take<float2>(M);
     c->rec0 = k.take<float4>(N);
     c->rec1 = k.take<float4>(N);
     c->pix = k.take<int>(N);
     c->max_k1_ctas = (int)((N + ED_K1_THREADS - 1) / ED_K1_THREADS) + 1;
-    c->k1_part = k.take<double>((size_t)c->max_k1_ctas * ED_K1_PART);
+    c->k1_part = k.take<float2>((size_t)c->max_k1_ctas * ED_K1_PART);
     c->vec_stride = (P + 63) / 64 * 64;
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);

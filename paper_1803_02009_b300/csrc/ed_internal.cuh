@@ -15,7 +15,7 @@
 #define ED_CHUNK 128           // assembly entries per chunk (4 per lane of a warp)
 #define ED_PART_STRIDE 96      // floats per chunk partial (60 moments, or 12 + 72), chunk-major
 #define ED_K1_THREADS 256
-#define ED_K1_PART 32          // doubles per point-kernel CTA partial
+#define ED_K1_PART 32          // components of a point-kernel CTA partial (30 used)
 #define ED_PCG_PART 8          // doubles per PCG CTA partial
 #define ED_MAX_BATCH_LAUNCH 32 // problems in one batched PCG launch
 #define ED_MAX_PCG_GRID 1184   // 8 x 148
@@ -110,11 +110,11 @@ struct ed_context {
     float *pnode;            // [m][72] pose-node blocks
     float *minv;             // [m][144] block-Jacobi inverses
     float *pose_blk;         // [36] pose block, [36..72) its inverse
-    double *node_energy;     // [m][2] rot, reg
+    float2 *node_energy;     // [m] (rot, reg) of every node
     float4 *rec0;            // [N] (R^T n(u), r)
     float4 *rec1;            // [N] (d r / d angles, 0)
     int *pix;                // [N] association of the last evaluation
-    double *k1_part;         // [ctas][ED_K1_PART]
+    float2 *k1_part;         // [ED_K1_PART][max_k1_ctas] float-float partials, component-major
     int max_k1_ctas;
     // PCG
     float *vec;              // 6 vectors of 12 max_nodes + 6: d, r, z, p0, p1, q
@@ -313,6 +313,36 @@ struct ed_warped {
     float3 v;     // R s + T
     float3 n;     // normalize(R sum_j w_j A_j n)
 };
+
+// Float-float accumulation (value = hi + lo): Knuth's error-free two-sum of
+// the high parts, the low parts added to its error, then a fast two-sum
+// renormalisation.  About 44 significant bits on the FP32 pipe (B300's FP64
+// rate is a small fraction of its FP32 rate); deterministic for a fixed order.
+__device__ __forceinline__ float2 ed_ff_add(float2 a, float2 b)
+{
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    const float lo = __fadd_rn(err, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(s, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+
+__device__ __forceinline__ float2 ed_ff_add1(float2 a, float b) { return ed_ff_add(a, make_float2(b, 0.f)); }
+
+__device__ __forceinline__ double ed_ff_value(float2 a) { return (double)a.x + (double)a.y; }
+
+// butterfly sum of one float-float value over the warp (lane 0's result is
+// the one used: a fixed pattern, so it is deterministic)
+__device__ __forceinline__ float2 ed_ff_warp_sum(float2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float2 u = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+        v = ed_ff_add(v, u);
+    }
+    return v;
+}
 
 // Eq. (1) skinning weights, Gaussian mode, from the keys of the k = 4
 // nearest nodes (slots >= nvalid hold no node): w~_s = exp(-d_s^2 / 2 sigma^2),

@@ -23,7 +23,8 @@ struct PointArgs {
     float sigma;
     int *pix;          // association (written in STEP / ENERGY, read in GRAD)
     float4 *rec0, *rec1;
-    double *part;      // [grid][ED_K1_PART]
+    float2 *part;      // [ED_K1_PART][pstride] float-float partials, component-major
+    int pstride;
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
 };
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS) k_points(PointArgs a)
             a.rec1[i] = r1;
         }
     }
-    // block reduction: warp shuffles (float), then warps in order (double)
+    // block reduction: warp shuffles (float), then the warps in order (float-float)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 30; ++k) {
@@ -109,9 +110,9 @@ __global__ void __launch_bounds__(ED_K1_THREADS) k_points(PointArgs a)
     }
     __syncthreads();
     if (threadIdx.x < 30) {
-        double s = 0.0;
-        for (int w = 0; w < ED_K1_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
-        a.part[blockIdx.x * ED_K1_PART + threadIdx.x] = s;
+        float2 s = make_float2(0.f, 0.f);
+        for (int w = 0; w < ED_K1_THREADS / 32; ++w) s = ed_ff_add1(s, red[w][threadIdx.x]);
+        a.part[(size_t)threadIdx.x * a.pstride + blockIdx.x] = s;
     }
 }
 
@@ -152,6 +153,7 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.rec0 = mode == PASS_GRAD ? ctx->gpts : ctx->rec0;
     a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : ctx->rec1;
     a.part = ctx->k1_part;
+    a.pstride = ctx->max_k1_ctas;
     a.dbg_wpos = ctx->dbg_wpos;
     a.dbg_wnrm = ctx->dbg_wnrm;
     a.dbg_pix = (mode == PASS_STEP && ctx->dbg_wpos && ctx->dbg_wnrm) ? ctx->dbg_pix : nullptr;
@@ -309,7 +311,7 @@ struct FinArgs {
     const float4 *x4;
     float w_rot, w_reg, lambda, jitter;
     float *bsr, *grad, *pnode, *minv;
-    double *node_energy;
+    float2 *node_energy;
     int *status;
 };
 
@@ -503,10 +505,10 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     }
     // energies of node j: Rot(A_j), and its out-edges
     if (lane == 0) {
-        double erot = 0.0, ereg = 0.0;
+        float erot = 0.f, ereg = 0.f;
         for (int q = 0; q < 6; ++q) {
             const float rho = rot_res(X, q);
-            erot += (double)a.w_rot * rho * rho;
+            erot += a.w_rot * rho * rho;
         }
         for (int s = 0; s < a.kg; ++s) {
             const int k = a.nbr[j * a.kg + s];
@@ -516,11 +518,10 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
             const float *xk = &a.x4[3 * k].x;
             for (int r = 0; r < 3; ++r) {
                 const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
-                ereg += (double)wr * e * e;
+                ereg += wr * e * e;
             }
         }
-        a.node_energy[2 * j] = erot;
-        a.node_energy[2 * j + 1] = ereg;
+        a.node_energy[j] = make_float2(erot, ereg);
     }
     __syncwarp();
     for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
@@ -574,154 +575,156 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
 // energy totals, pose preconditioner
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_pose_final(const double *__restrict__ part, int nparts,
-                                                    const double *__restrict__ node_energy, int m,
-                                                    const double *__restrict__ pose, ed_solver_params prm,
-                                                    float *__restrict__ pose_blk, float *__restrict__ grad,
-                                                    double *__restrict__ dmisc, int *__restrict__ status,
-                                                    ed_stats *stats)
+#define PF_THREADS 1024
+
+#define PF_BATCH 20   // loads in flight per lane (>= 4 * 148 / 32 partials: one round at 640x480)
+
+// sums of the point-pass partials (component k by warp k < 30, lanes striding
+// the CTAs, PF_BATCH loads in flight) and of the node energies (all threads,
+// then one warp over the warps); s[0..29], ne[0..1]
+__device__ __forceinline__ void pf_sums(const float2 *__restrict__ part, int nparts, int pstride,
+                                        const float2 *__restrict__ node_energy, int m, double *s, double *ne,
+                                        float2 (*wsum)[2])
 {
-    __shared__ double sw[8][32];
-    __shared__ double s[32];
-    __shared__ double ne[2][8];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    // point-pass partials: thread t sums CTAs t, t + 256, ... for all 30 components
-    double acc[30];
+    if (w < 30) {
+        const float2 *src = part + (size_t)w * pstride;
+        float2 v = make_float2(0.f, 0.f);
+        for (int c0 = 0; c0 < nparts; c0 += 32 * PF_BATCH) {
+            float2 buf[PF_BATCH];
 #pragma unroll
-    for (int k = 0; k < 30; ++k) acc[k] = 0.0;
-    for (int c = t; c < nparts; c += 256) {
-#pragma unroll
-        for (int k = 0; k < 30; ++k) acc[k] += part[c * ED_K1_PART + k];
-    }
-#pragma unroll
-    for (int k = 0; k < 30; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sw[w][k] = v;
-    }
-    double er = 0.0, eg = 0.0;
-    for (int j = t; j < m; j += 256) {
-        er += node_energy[2 * j];
-        eg += node_energy[2 * j + 1];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        er += __shfl_xor_sync(0xffffffffu, er, o);
-        eg += __shfl_xor_sync(0xffffffffu, eg, o);
-    }
-    if (lane == 0) {
-        ne[0][w] = er;
-        ne[1][w] = eg;
-    }
-    __syncthreads();
-    if (t < 30) {
-        double v = 0.0;
-        for (int k = 0; k < 8; ++k) v += sw[k][t];
-        s[t] = v;
-    }
-    __syncthreads();
-    if (t != 0) return;
-    double Erot = 0.0, Ereg = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        Erot += ne[0][k];
-        Ereg += ne[1][k];
-    }
-    float H[36], L[36];
-    double gp[6];
-    {
-        int k = 2;
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-            for (int b = a; b < 6; ++b) {
-                H[6 * a + b] = H[6 * b + a] = (float)s[k];
-                ++k;
+            for (int q = 0; q < PF_BATCH; ++q) {
+                const int c = c0 + lane + 32 * q;
+                buf[q] = c < nparts ? src[c] : make_float2(0.f, 0.f);
             }
-    }
-    double Er = 0.0, Ep = 0.0;
 #pragma unroll
-    for (int a = 0; a < 6; ++a) {
+            for (int q = 0; q < PF_BATCH; ++q) v = ed_ff_add(v, buf[q]);
+        }
+        v = ed_ff_warp_sum(v);
+        if (lane == 0) s[w] = ed_ff_value(v);
+    }
+    float2 er = make_float2(0.f, 0.f), eg = er;
+    for (int j = t; j < m; j += PF_THREADS) {
+        const float2 e = node_energy[j];
+        er = ed_ff_add1(er, e.x);
+        eg = ed_ff_add1(eg, e.y);
+    }
+    er = ed_ff_warp_sum(er);
+    eg = ed_ff_warp_sum(eg);
+    if (lane == 0) {
+        wsum[w][0] = er;
+        wsum[w][1] = eg;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const float2 a = ed_ff_warp_sum(wsum[lane][0]);
+        const float2 b = ed_ff_warp_sum(wsum[lane][1]);
+        if (lane == 0) {
+            ne[0] = ed_ff_value(a);
+            ne[1] = ed_ff_value(b);
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restrict__ part, int nparts, int pstride,
+                                                           const float2 *__restrict__ node_energy, int m,
+                                                           const double *__restrict__ pose, ed_solver_params prm,
+                                                           float *__restrict__ pose_blk, float *__restrict__ grad,
+                                                           double *__restrict__ dmisc, int *__restrict__ status,
+                                                           ed_stats *stats)
+{
+    __shared__ double s[32];
+    __shared__ double ne[2];
+    __shared__ double pri[6];
+    __shared__ float2 wsum[PF_THREADS / 32][2];
+    __shared__ float Ls[36];
+    __shared__ float rinv[6];
+    const int t = threadIdx.x, lane = t & 31;
+    static_assert(PF_BATCH * 32 * 1 >= 4 * 148, "one round of loads on a 148-SM part");
+    pf_sums(part, nparts, pstride, node_energy, m, s, ne, wsum);
+    // pose block (+ prior weights on the diagonal, LM damping), one entry per thread;
+    // priors and the pose gradient, one coordinate per thread
+    if (t < 36) {
+        const int a = t / 6, b = t % 6, lo = a < b ? a : b, hi = a < b ? b : a;
+        float h = (float)s[2 + 6 * lo - lo * (lo - 1) / 2 + (hi - lo)];
+        if (a == b) h = (float)((double)h + (a < 3 ? prm.w_r : prm.w_p)) * (1.0f + prm.lambda);
+        pose_blk[t] = h;
+        Ls[t] = h;
+    } else if (t >= 64 && t < 70) {
+        const int a = t - 64;
         const double wt = a < 3 ? prm.w_r : prm.w_p;
         const double d = pose[a] - prm.prior[a];
-        if (a < 3) Er += wt * d * d;
-        else Ep += wt * d * d;
-        H[7 * a] = (float)((double)H[7 * a] + wt);
-        gp[a] = s[23 + a] + wt * d;
+        pri[a] = wt * d * d;
+        grad[a] = (float)(s[23 + a] + wt * d);
     }
-    const double E = s[0] + Erot + Ereg + Er + Ep;
-    if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
-    float tr = 0.f;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        H[7 * a] *= 1.0f + prm.lambda;
-        tr += H[7 * a];
-    }
-#pragma unroll
-    for (int a = 0; a < 36; ++a) {
-        pose_blk[a] = H[a];
-        L[a] = H[a];
-    }
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-        L[7 * a] += prm.jitter * tr / 6.0f;
-        grad[a] = (float)gp[a];
-    }
-    // inverse of the pose block by Cholesky (unrolled, FP32)
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        float d = L[7 * c];
-#pragma unroll
-        for (int p = 0; p < c; ++p) d -= L[6 * c + p] * L[6 * c + p];
-        ok = ok && d > 0.f;
-        d = sqrtf(fmaxf(d, 1e-30f));
-        L[7 * c] = d;
-#pragma unroll
-        for (int r = c + 1; r < 6; ++r) {
-            float v = L[6 * r + c];
-#pragma unroll
-            for (int p = 0; p < c; ++p) v -= L[6 * r + p] * L[6 * c + p];
-            L[6 * r + c] = v / d;
+    __syncthreads();
+    // Cholesky factor of the pose block + jitter tr/6 I: warp 0, one row per lane
+    if (t < 32) {
+        const float tr = Ls[0] + Ls[7] + Ls[14] + Ls[21] + Ls[28] + Ls[35];
+        if (lane < 6) Ls[7 * lane] += prm.jitter * tr / 6.0f;
+        __syncwarp();
+        bool ok = true;
+        for (int c = 0; c < 6; ++c) {
+            if (lane == c) {
+                float d = Ls[7 * c];
+                for (int p = 0; p < c; ++p) d -= Ls[6 * c + p] * Ls[6 * c + p];
+                ok = d > 0.f;
+                d = sqrtf(fmaxf(d, 1e-30f));
+                Ls[7 * c] = d;
+                rinv[c] = 1.0f / d;
+            }
+            __syncwarp();
+            if (lane > c && lane < 6) {
+                float v = Ls[6 * lane + c];
+                for (int p = 0; p < c; ++p) v -= Ls[6 * lane + p] * Ls[6 * c + p];
+                Ls[6 * lane + c] = v * rinv[c];
+            }
+            __syncwarp();
         }
-    }
-    if (!ok) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
+        if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
+        __syncwarp();
+        // the inverse, one column per lane: forward then back substitution
+        if (lane < 6) {
+            const int col = lane;
+            float y[6], xv[6];
 #pragma unroll
-    for (int col = 0; col < 6; ++col) {
-        float y[6], xv[6];
+            for (int r = 0; r < 6; ++r) {
+                float v = r == col ? 1.0f : 0.0f;
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
-            float v = r == col ? 1.0f : 0.0f;
+                for (int p = 0; p < r; ++p) v -= Ls[6 * r + p] * y[p];
+                y[r] = v * rinv[r];
+            }
 #pragma unroll
-            for (int p = 0; p < r; ++p) v -= L[6 * r + p] * y[p];
-            y[r] = v / L[7 * r];
+            for (int r = 5; r >= 0; --r) {
+                float v = y[r];
+#pragma unroll
+                for (int p = r + 1; p < 6; ++p) v -= Ls[6 * p + r] * xv[p];
+                xv[r] = v * rinv[r];
+            }
+#pragma unroll
+            for (int r = 0; r < 6; ++r) pose_blk[36 + 6 * r + col] = xv[r];
         }
-#pragma unroll
-        for (int r = 5; r >= 0; --r) {
-            float v = y[r];
-#pragma unroll
-            for (int p = r + 1; p < 6; ++p) v -= L[6 * p + r] * xv[p];
-            xv[r] = v / L[7 * r];
+    } else if (t == 32) {
+        const double Er = pri[0] + pri[1] + pri[2], Ep = pri[3] + pri[4] + pri[5];
+        const double E = s[0] + ne[0] + ne[1] + Er + Ep;
+        if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
+        dmisc[0] = E;
+        dmisc[1] = s[0];
+        dmisc[2] = ne[0];
+        dmisc[3] = ne[1];
+        dmisc[4] = Er;
+        dmisc[5] = Ep;
+        dmisc[6] = s[1];
+        if (stats) {
+            stats->energy = E;
+            stats->e_data = s[0];
+            stats->e_rot = ne[0];
+            stats->e_reg = ne[1];
+            stats->e_rot_prior = Er;
+            stats->e_pos_prior = Ep;
+            stats->n_valid = (int)s[1];
         }
-#pragma unroll
-        for (int r = 0; r < 6; ++r) pose_blk[36 + 6 * r + col] = xv[r];
-    }
-    dmisc[0] = E;
-    dmisc[1] = s[0];
-    dmisc[2] = Erot;
-    dmisc[3] = Ereg;
-    dmisc[4] = Er;
-    dmisc[5] = Ep;
-    dmisc[6] = s[1];
-    if (stats) {
-        stats->energy = E;
-        stats->e_data = s[0];
-        stats->e_rot = Erot;
-        stats->e_reg = Ereg;
-        stats->e_rot_prior = Er;
-        stats->e_pos_prior = Ep;
-        stats->n_valid = (int)s[1];
     }
 }
 
@@ -819,7 +822,8 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     k_finalize<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
     ED_LAUNCH_CHECK();
-    k_pose_final<<<1, 256, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->node_energy, m, pose, *prm, ctx->pose_blk,
+    k_pose_final<<<1, PF_THREADS, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, ctx->node_energy, m, pose,
+                                           *prm, ctx->pose_blk,
                                     ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS, stats); ed_note_launch();
     ED_LAUNCH_CHECK();
     return ED_OK;
@@ -871,17 +875,17 @@ extern "C" ed_status ed_export_system(ed_context *ctx, int *row_ptr, int *col, f
 
 // rot and reg energies per node (no normal equations)
 __global__ void k_node_energy(int m, int kg, const int *__restrict__ nbr, const float4 *__restrict__ g,
-                              const float4 *__restrict__ x4, float w_rot, float w_reg, double *__restrict__ ne)
+                              const float4 *__restrict__ x4, float w_rot, float w_reg, float2 *__restrict__ ne)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     const float *X = &x4[3 * j].x;
-    double er = 0.0, eg = 0.0;
+    float er = 0.f, eg = 0.f;
     const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {1, 2, 2, 0, 1, 2};
     for (int q = 0; q < 6; ++q) {
         float rho = X[pa[q]] * X[pb[q]] + X[4 + pa[q]] * X[4 + pb[q]] + X[8 + pa[q]] * X[8 + pb[q]];
         if (pa[q] == pb[q]) rho -= 1.0f;
-        er += (double)w_rot * rho * rho;
+        er += w_rot * rho * rho;
     }
     const float4 gj = g[j];
     for (int s = 0; s < kg; ++s) {
@@ -892,47 +896,32 @@ __global__ void k_node_energy(int m, int kg, const int *__restrict__ nbr, const 
         const float *xk = &x4[3 * k].x;
         for (int r = 0; r < 3; ++r) {
             const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
-            eg += (double)w_reg * e * e;
+            eg += w_reg * e * e;
         }
     }
-    ne[2 * j] = er;
-    ne[2 * j + 1] = eg;
+    ne[j] = make_float2(er, eg);
 }
 
-__global__ void k_energy_final(const double *__restrict__ part, int nparts, const double *__restrict__ ne, int m,
-                               const double *__restrict__ pose, ed_solver_params prm, double *__restrict__ out)
+__global__ void __launch_bounds__(PF_THREADS) k_energy_final(const float2 *__restrict__ part, int nparts, int pstride,
+                                                              const float2 *__restrict__ node_energy, int m,
+                                                              const double *__restrict__ pose, ed_solver_params prm,
+                                                              double *__restrict__ out)
 {
-    __shared__ double a[2][256];
-    __shared__ double e0;
-    const int t = threadIdx.x;
-    if (t == 0) {
-        double v = 0.0;
-        for (int c = 0; c < nparts; ++c) v += part[c * ED_K1_PART];
-        e0 = v;
-    }
-    double er = 0.0, eg = 0.0;
-    for (int j = t; j < m; j += blockDim.x) {
-        er += ne[2 * j];
-        eg += ne[2 * j + 1];
-    }
-    a[0][t] = er;
-    a[1][t] = eg;
-    __syncthreads();
-    if (t == 0) {
-        double Erot = 0.0, Ereg = 0.0, Er = 0.0, Ep = 0.0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            Erot += a[0][k];
-            Ereg += a[1][k];
-        }
+    __shared__ double s[32];
+    __shared__ double ne[2];
+    __shared__ float2 wsum[PF_THREADS / 32][2];
+    pf_sums(part, nparts, pstride, node_energy, m, s, ne, wsum);
+    if (threadIdx.x == 0) {
+        double Er = 0.0, Ep = 0.0;
         for (int q = 0; q < 6; ++q) {
             const double d = pose[q] - prm.prior[q];
             if (q < 3) Er += prm.w_r * d * d;
             else Ep += prm.w_p * d * d;
         }
-        out[0] = e0 + Erot + Ereg + Er + Ep;
-        out[1] = e0;
-        out[2] = Erot;
-        out[3] = Ereg;
+        out[0] = s[0] + ne[0] + ne[1] + Er + Ep;
+        out[1] = s[0];
+        out[2] = ne[0];
+        out[3] = ne[1];
         out[4] = Er;
         out[5] = Ep;
     }
@@ -949,7 +938,8 @@ extern "C" ed_status ed_energy(ed_context *ctx, const ed_frame *fr, const ed_sol
     k_node_energy<<<ed_div_up(ctx->m, 128), 128, 0, st>>>(ctx->m, ctx->k_graph, ctx->graph.nbr,
                                                           (const float4 *)ctx->graph.nodes, (const float4 *)x,
                                                           prm->w_rot, prm->w_reg, ctx->node_energy); ed_note_launch();
-    k_energy_final<<<1, 256, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->node_energy, ctx->m, pose, *prm, energy_out); ed_note_launch();
+    k_energy_final<<<1, PF_THREADS, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, ctx->node_energy, ctx->m,
+                                              pose, *prm, energy_out); ed_note_launch();
     ED_LAUNCH_CHECK();
     ctx->have_energy = 1;
     return ED_OK;
@@ -1041,16 +1031,20 @@ __global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__
     for (int k = 0; k < 12; ++k) grad[12 * j + k] = 2.0f * scale * acc[k];
 }
 
-__global__ void k_grad_pose(const double *__restrict__ part, int nparts, const double *__restrict__ pose,
+__global__ void k_grad_pose(const float2 *__restrict__ part, int nparts, int pstride, const double *__restrict__ pose,
                             ed_solver_params prm, float scale, float *__restrict__ gpose)
 {
-    const int t = threadIdx.x;
+    const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;   // warp t: pose coordinate t
     if (t >= 6) return;
-    double v = 0.0;
-    for (int c = 0; c < nparts; ++c) v += part[c * ED_K1_PART + 23 + t];
-    const double w = t < 3 ? prm.w_r : prm.w_p;
-    v += w * (pose[t] - prm.prior[t]);
-    gpose[t] = (float)(2.0 * scale * v);
+    const float2 *src = part + (size_t)(23 + t) * pstride;
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int c = lane; c < nparts; c += 32) v = ed_ff_add(v, src[c]);
+    v = ed_ff_warp_sum(v);
+    if (lane == 0) {
+        const double w = t < 3 ? prm.w_r : prm.w_p;
+        gpose[t] = (float)(2.0 * scale * (ed_ff_value(v) + w * (pose[t] - prm.prior[t])));
+    }
 }
 
 extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
@@ -1070,7 +1064,7 @@ extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const e
                                                        (const ushort4 *)ctx->graph.idx,
                                                        ctx->weight_mode == ED_WEIGHT_GAUSSIAN, ctx->sigma, ctx->gpts,
                                                        prm->w_rot, prm->w_reg, grad_scale, grad_x); ed_note_launch();
-    k_grad_pose<<<1, 32, 0, st>>>(ctx->k1_part, k1_grid(ctx), pose, *prm, grad_scale, grad_pose); ed_note_launch();
+    k_grad_pose<<<1, 192, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, pose, *prm, grad_scale, grad_pose); ed_note_launch();
     ED_LAUNCH_CHECK();
     return ED_OK;
 }
