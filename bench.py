@@ -80,9 +80,38 @@ def whole_job_rate(world, steps, gn_per_step, seconds):
     return world * steps * gn_per_step / seconds
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, clock
+    event reasons) on the GPU with the given UUID."""
+
+    def __init__(self, uuid):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self._reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sm_mhz(self):
+        v = self.C.c_uint(0)
+        return float(v.value) if self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.C.byref(v)) == 0 else None
+
+    def sm_max_mhz(self):
+        v = self.C.c_uint(0)
+        return float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.C.byref(v)) == 0 else None
+
+    def reasons(self):
+        v = self.C.c_ulonglong(0)
+        return int(v.value) if self._reasons(self.h, self.C.byref(v)) == 0 else 0
+
+
 class ClockSampler:
-    """SM clocks and throttle reasons sampled through NVML every 2 ms during the
-    timed region (read-only queries); nvidia-smi is the fallback."""
+    """SM clocks and clock event reasons sampled every 2 ms during the timed
+    region (read-only NVML queries); nvidia-smi is the fallback."""
 
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
                0x80: "hw_power_brake_slowdown"}
@@ -93,29 +122,17 @@ class ClockSampler:
         self.stop_ev = threading.Event()
         self.thread = None
         self.mode = None
+        self.proc = None
 
-    def _handle(self):
-        import pynvml
-        pynvml.nvmlInit()
-        try:
-            import torch
-            uuid = str(torch.cuda.get_device_properties(self.cuda_index).uuid)
-            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode())
-        except Exception:
-            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.cuda_index)
-
-    def _poll_nvml(self, nv, h):
-        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+    def _poll_nvml(self, nv):
         while not self.stop_ev.is_set():
-            try:
-                self.sm.append(float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)))
-                bits = int(get_reasons(h))
-                for bit, name in self.REASONS.items():
-                    if bits & bit:
-                        self.reasons.add(name)
-            except Exception:
-                pass
+            v = nv.sm_mhz()
+            if v is not None:
+                self.sm.append(v)
+            bits = nv.reasons()
+            for bit, name in self.REASONS.items():
+                if bits & bit:
+                    self.reasons.add(name)
             self.stop_ev.wait(0.002)
 
     def _poll_smi(self):
@@ -123,13 +140,12 @@ class ClockSampler:
                   "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
-            proc = subprocess.Popen(["nvidia-smi", f"--id={self.cuda_index}", f"--query-gpu={fields}",
-                                     "--format=csv,noheader,nounits", "-lms", "100"],
-                                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.cuda_index}", f"--query-gpu={fields}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             return
-        self.proc = proc
-        for line in proc.stdout:
+        for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 6:
                 continue
@@ -144,23 +160,23 @@ class ClockSampler:
 
     def start(self):
         try:
-            nv, h = self._handle()
-            self.smax = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            import torch
+            nv = _Nvml(str(torch.cuda.get_device_properties(self.cuda_index).uuid))
+            self.smax = nv.sm_max_mhz()
             self.mode = "nvml"
-            self.thread = threading.Thread(target=self._poll_nvml, args=(nv, h), daemon=True)
+            self.thread = threading.Thread(target=self._poll_nvml, args=(nv,), daemon=True)
         except Exception:
             self.mode = "nvidia-smi"
             self.thread = threading.Thread(target=self._poll_smi, daemon=True)
-        try:
-            self.thread.start()
-        except Exception:
-            self.mode = None
+        self.thread.start()
+        if self.mode == "nvidia-smi":
+            time.sleep(0.5)   # nvidia-smi needs a moment before its first line
 
     def stop(self):
         if self.mode is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock query unavailable"]}
         self.stop_ev.set()
-        if self.mode == "nvidia-smi" and getattr(self, "proc", None) is not None:
+        if self.proc is not None:
             self.proc.terminate()
         self.thread.join(timeout=5)
         return {"sm_mhz": statistics.median(self.sm) if self.sm else None, "sm_max_mhz": self.smax,

@@ -133,7 +133,8 @@ typedef struct ed_graph {
  *   point lists used by ed_gn_step.
  * pos/nrm [N][4] are the model (they must stay valid until the next
  * ed_build_graph); the graph buffers are retained by the context likewise.
- * Synchronises the stream (it reads back the node and block counts).
+ * Synchronises the stream four times (it reads back the grid, node, block and
+ * chunk counts); the last kernels of the build are still queued on return.
  */
 ed_status ed_build_graph(ed_context *ctx, const float *pos, const float *nrm, int n_points, int m_in,
                          const ed_graph_params *params, const ed_graph *graph, cudaStream_t stream);

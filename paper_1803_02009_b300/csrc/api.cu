@@ -137,17 +137,21 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         return ED_ERR_CAPACITY;
     }
     carve(c, (char *)workspace);
-    c->row_ptr_host = (int *)malloc(sizeof(int) * ((size_t)c->lim.max_nodes + 1));
-    if (!c->row_ptr_host) {
+    // pinned host buffers: the row pointer read back at graph build and the
+    // staging of small host-to-device copies (no stream synchronisation)
+    if (cudaMallocHost((void **)&c->row_ptr_host, sizeof(int) * ((size_t)c->lim.max_nodes + 1)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->pinned, sizeof(int) * ED_PINNED_INTS) != cudaSuccess) {
+        if (c->row_ptr_host) cudaFreeHost(c->row_ptr_host);
         free(c);
-        return ED_ERR_CAPACITY;
+        return ED_ERR_CUDA;
     }
     c->ws = (char *)workspace;
     c->ws_bytes = workspace_bytes;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
         cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess) {
-        free(c->row_ptr_host);
+        cudaFreeHost(c->row_ptr_host);
+        cudaFreeHost(c->pinned);
         free(c);
         return ED_ERR_CUDA;
     }
@@ -158,7 +162,8 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
 extern "C" ed_status ed_destroy(ed_context *ctx)
 {
     if (!ctx) return ED_ERR_ARG;
-    free(ctx->row_ptr_host);
+    cudaFreeHost(ctx->row_ptr_host);
+    cudaFreeHost(ctx->pinned);
     free(ctx);
     return ED_OK;
 }

@@ -19,6 +19,7 @@
 #define ED_PCG_PART 8          // doubles per PCG CTA partial
 #define ED_MAX_BATCH_LAUNCH 32 // problems in one batched PCG launch
 #define ED_MAX_PCG_GRID 1184   // 8 x 148
+#define ED_PINNED_INTS (ED_MAX_PCG_GRID + 1 + 16)
 
 // indices of the misc int words in the workspace
 enum {
@@ -33,8 +34,10 @@ enum {
     MI_NCHUNK = 15,
     MI_BBOX = 16,        // 16..21 ordered-int bbox (min xyz, max xyz)
     MI_PHASE_BASE = 24,  // running node count during sampling
-    MI_BAR = 32,         // grid barrier arrival count (33 unused)
+    MI_BAR = 32,         // grid barrier arrival count of the PCG
+    MI_BAR_GRAPH = 33,   // grid barrier arrival count of the Poisson sampler
     MI_FUSE = 40,        // 40 kept, 41 lifted
+    MI_READ = 48,        // 48..51 values gathered for one host read (chunk totals, upper blocks)
     MI_PHASES = 64,      // 64..90 phase counts, 96..123 starts, 128..154 fill counters
     MI_COUNT = 192
 };
@@ -148,7 +151,8 @@ struct ed_context {
     ed_pcg_plan_t pcg;       // single-problem PCG launch (one 512-thread CTA per SM)
     int *pcg_rows;           // [ED_MAX_PCG_GRID + 1] first node row of every CTA (device)
     int *pcg_rows_b;         // [ED_MAX_PCG_GRID + 1] the same for a batched launch (device)
-    int *row_ptr_host;       // [max_nodes + 1] host copy of the block row pointer
+    int *row_ptr_host;       // [max_nodes + 1] host copy of the block row pointer (pinned)
+    int *pinned;             // [ED_PINNED_INTS] pinned host staging of small host-to-device copies
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
@@ -313,6 +317,77 @@ struct ed_warped {
     float3 v;     // R s + T
     float3 n;     // normalize(R sum_j w_j A_j n)
 };
+
+// ---------------------------------------------------------------------------
+// grid barrier of a cooperative (co-resident) launch, with a bounded wait
+// ---------------------------------------------------------------------------
+
+#define ED_BAR_TIMEOUT_NS 2000000000ull
+
+__device__ __forceinline__ unsigned long long ed_gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ed_ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ed_atom_add_release(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void ed_st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void ed_red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// grid barrier on a monotonic arrival counter that every CTA polls: the CTA's
+// writes are ordered before thread 0's arrival by the CTA barrier and a fence,
+// other CTAs' writes are visible after its acquire load of the count (later
+// reads of shared data bypass L1); returns false when the context status is
+// set (an error elsewhere, or this wait timed out)
+__device__ __forceinline__ bool ed_grid_sync(unsigned *count, int *status, unsigned nblocks, unsigned &target, int *s_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        target += 1;
+        __threadfence();   // the whole CTA's writes (ordered by the CTA barrier) before the arrival
+        ed_red_add_release(count, 1u);
+        const unsigned goal = nblocks * target;
+        const unsigned long long t0 = ed_gtimer();
+        unsigned spins = 0;
+        while (ed_ld_acquire(count) < goal) {
+            if ((++spins & 63u) == 0) {
+                if (*(volatile int *)status != ED_OK) { ok = 0; break; }
+                if (ed_gtimer() - t0 > ED_BAR_TIMEOUT_NS) {
+                    atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (*(volatile int *)status != ED_OK) ok = 0;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 
 // Float-float accumulation (value = hi + lo): Knuth's error-free two-sum of
 // the high parts, the low parts added to its error, then a fast two-sum

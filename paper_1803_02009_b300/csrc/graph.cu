@@ -149,7 +149,7 @@ __global__ void k_phase_scan(const int *__restrict__ cnt, int *__restrict__ star
 }
 
 __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
-                                const int *__restrict__ start, int *__restrict__ fill, int *__restrict__ bucket)
+                                const int *__restrict__ start, int *__restrict__ fill, int2 *__restrict__ bucket)
 {
     __shared__ int h[27], base[27];
     const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1];
@@ -157,15 +157,16 @@ __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const in
         if (threadIdx.x < 27) h[threadIdx.x] = 0;
         __syncthreads();
         const int i = i0 + threadIdx.x;
-        int ph = -1, loc = 0;
+        int ph = -1, loc = 0, ci = 0;
         if (i < n) {
-            ph = cell_phase(cell_of[i], nx, ny);
+            ci = cell_of[i];
+            ph = cell_phase(ci, nx, ny);
             loc = atomicAdd(&h[ph], 1);
         }
         __syncthreads();
         if (threadIdx.x < 27) base[threadIdx.x] = h[threadIdx.x] ? atomicAdd(&fill[threadIdx.x], h[threadIdx.x]) : 0;
         __syncthreads();
-        if (i < n) bucket[start[ph] + base[ph] + loc] = i;
+        if (i < n) bucket[start[ph] + base[ph] + loc] = make_int2(i, ci);
         __syncthreads();
     }
 }
@@ -173,15 +174,13 @@ __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const in
 // phase ph: a point bids for its cell when its FP32 key to every node chosen
 // in earlier phases (cells within +-2) is >= r*r; the lowest index wins.
 // Five lanes per point (lanes 5g .. 5g+4 of a warp, six points per warp) each
-// check one z layer of the 5x5x5 neighbourhood; the group votes.
-__global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__restrict__ bucket,
-                               const int *__restrict__ start, int phase, const int *__restrict__ misc,
-                               const float *__restrict__ fmisc, const int *__restrict__ cell_of,
-                               int *__restrict__ cell_pick)
+// check one z layer of the 5x5x5 neighbourhood; the group votes.  All 27
+// phases run in one persistent cooperative launch with a grid barrier between
+// phases; the winning bids of earlier phases are read from L2 (they were
+// written by atomics of other CTAs during this launch).
+__device__ __forceinline__ void poisson_phase(const float4 *__restrict__ pos, const int2 *__restrict__ bucket, int e0,
+                                              int e1, int nx, int ny, int nz, float r2, int *cell_pick)
 {
-    const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1], nz = misc[MI_DIMS + 2];
-    const float r2 = fmisc[MF_R2];
-    const int e0 = start[phase], e1 = start[phase + 1];
     const int lane = threadIdx.x & 31, grp = lane / 5, sub = lane % 5;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int wbase = e0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 6; wbase < e1; wbase += warps * 6) {
@@ -190,8 +189,9 @@ __global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__rest
         bool ok = true;
         int i = -1, c = 0;
         if (act) {
-            i = bucket[e];
-            c = cell_of[i];
+            const int2 bc = bucket[e];
+            i = bc.x;
+            c = bc.y;
             const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
             const int dz = sub - 2, az = cz + dz;
             if (az >= 0 && az < nz) {
@@ -201,7 +201,7 @@ __global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__rest
                 for (int k = 0; k < 25; ++k) {
                     const int ay = cy + k / 5 - 2, ax = cx + k % 5 - 2;
                     const bool in = ay >= 0 && ay < ny && ax >= 0 && ax < nx && !(dz == 0 && k == 12);
-                    q[k] = in ? cell_pick[ax + nx * (ay + ny * az)] : NO_BID;   // earlier phases: final
+                    q[k] = in ? __ldcg(cell_pick + ax + nx * (ay + ny * az)) : NO_BID;   // earlier phases: final
                 }
 #pragma unroll
                 for (int k = 0; k < 25; ++k) {
@@ -215,6 +215,22 @@ __global__ void k_poisson_pick(const float4 *__restrict__ pos, const int *__rest
         const unsigned bad = __ballot_sync(0xffffffffu, act && !ok);
         const unsigned gmask = 0x1fu << (5 * grp);
         if (act && sub == 0 && !(bad & gmask)) atomicMin(&cell_pick[c], i);
+    }
+}
+
+#define POISSON_T 512
+__global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restrict__ pos, const int2 *__restrict__ bucket,
+                                                           const int *__restrict__ start, const int *__restrict__ misc_in,
+                                                           const float *__restrict__ fmisc, int *cell_pick, unsigned *bar,
+                                                           int *status)
+{
+    __shared__ int s_flag;
+    const int nx = misc_in[MI_DIMS], ny = misc_in[MI_DIMS + 1], nz = misc_in[MI_DIMS + 2];
+    const float r2 = fmisc[MF_R2];
+    unsigned target = 0;
+    for (int ph = 0; ph < 27; ++ph) {
+        poisson_phase(pos, bucket, start[ph], start[ph + 1], nx, ny, nz, r2, cell_pick);
+        if (ph < 26 && !ed_grid_sync(bar, status, gridDim.x, target, &s_flag)) return;
     }
 }
 
@@ -668,7 +684,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         const int cells = hm[MI_DIMS + 3];
         ED_CUDA_TRY(cudaMemsetAsync(ctx->cell_pick, 0x7f, sizeof(int) * cells, st));
         int *pcnt = ctx->misc + MI_PHASES, *pstart = ctx->misc + MI_PHASES + 32, *pfill = ctx->misc + MI_PHASES + 64;
-        int *bucket = ctx->flag_a;                  // N ints
+        int2 *bucket = reinterpret_cast<int2 *>(ctx->ent_key);  // N (point, cell) pairs; the entry keys come later
         ED_CUDA_TRY(cudaMemsetAsync(pcnt, 0, sizeof(int) * 27, st));
         const int pg = min(ed_div_up(N, 256), 4 * ctx->num_sms);
         k_cell_of<<<ed_div_up(N, 256), 256, 0, st>>>(P4, N, ctx->misc, ctx->fmisc, ctx->cell_of); ed_note_launch();
@@ -676,12 +692,25 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_phase_scan<<<1, 32, 0, st>>>(pcnt, pstart, pfill); ed_note_launch();
         k_phase_scatter<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pstart, pfill, bucket); ed_note_launch();
         ED_LAUNCH_CHECK();
-        const int pick_grid = min(ed_div_up((N / 27 + 1) * 32 / 6 + 32, 128), 8 * ctx->num_sms);
-        for (int ph = 0; ph < 27; ++ph) {
-            k_poisson_pick<<<pick_grid, 128, 0, st>>>(P4, bucket, pstart, ph, ctx->misc, ctx->fmisc, ctx->cell_of,
-                                                      ctx->cell_pick); ed_note_launch();
+        // one cooperative launch for the 27 phases: one CTA per SM (fewer
+        // barrier arrivals), sized down for small inputs
+        int per_sm = 0;
+        ED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson_all, POISSON_T, 0));
+        int pick_grid = min(ed_div_up((N / 27 + 1) * 32 / 6 + 32, POISSON_T), min(per_sm, 1) * ctx->num_sms);
+        if (pick_grid < 1) pick_grid = 1;
+        ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_BAR_GRAPH, 0, sizeof(int), st));
+        {
+            const int *misc_c = ctx->misc, *pstart_c = pstart;
+            const float *fmisc_c = ctx->fmisc;
+            const int2 *bucket_c = bucket;
+            int *cell_pick = ctx->cell_pick;
+            unsigned *bar = (unsigned *)(ctx->misc + MI_BAR_GRAPH);
+            int *status = ctx->misc + MI_STATUS;
+            void *args[] = {(void *)&P4, (void *)&bucket_c, (void *)&pstart_c, (void *)&misc_c, (void *)&fmisc_c,
+                            (void *)&cell_pick, (void *)&bar, (void *)&status};
+            ed_note_launch();
+            ED_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_poisson_all, pick_grid, POISSON_T, args, 0, st));
         }
-        ED_LAUNCH_CHECK();
         // node numbers in (phase, cell) order
         PhaseTable T;
         const int dx = hm[MI_DIMS], dy = hm[MI_DIMS + 1], dz = hm[MI_DIMS + 2];
@@ -703,14 +732,19 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH_CHECK();
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_PHASE_BASE, pre + tot, sizeof(int), cudaMemcpyDeviceToDevice, st));
         if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
+        if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
         const int mt = hm[MI_PHASE_BASE];
         m = mt < max_nodes ? mt : max_nodes;
-        int cnt[2] = {m, mt};
-        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
+        ctx->pinned[ED_MAX_PCG_GRID + 3] = m;
+        ctx->pinned[ED_MAX_PCG_GRID + 4] = mt;
+        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts, ctx->pinned + ED_MAX_PCG_GRID + 3, 2 * sizeof(int),
+                                    cudaMemcpyHostToDevice, st));
     } else {
         m = m_in;
-        int cnt[2] = {m, m};
-        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
+        ctx->pinned[ED_MAX_PCG_GRID + 3] = m;
+        ctx->pinned[ED_MAX_PCG_GRID + 4] = m;
+        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts, ctx->pinned + ED_MAX_PCG_GRID + 3, 2 * sizeof(int),
+                                    cudaMemcpyHostToDevice, st));
     }
     if (m < ED_K || (prm->weight_mode == ED_WEIGHT_EQ2 && m < ED_K + 1) || m <= prm->k_graph) return ED_ERR_ARG;
 
@@ -773,10 +807,16 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt, ctx->chunk_start, nnzb, st)) != ED_OK) return s;
         if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt1, ctx->chunk_start1, nnzb, st)) != ED_OK) return s;
-        int nc01[2];
-        ED_CUDA_TRY(cudaMemcpyAsync(&nc01[0], ctx->chunk_start + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
-        ED_CUDA_TRY(cudaMemcpyAsync(&nc01[1], ctx->chunk_start1 + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
+        // one host read for what the rest of the build needs: chunk totals,
+        // upper-block count (gathered into misc) and the row pointer (pinned)
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ, ctx->chunk_start + nnzb, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 1, ctx->chunk_start1 + nnzb, sizeof(int),
+                                    cudaMemcpyDeviceToDevice, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 2, ctx->flag_b + nnzb, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->row_ptr_host, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
         if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
+        const int nc01[2] = {hm[MI_READ], hm[MI_READ + 1]};
+        n_upper = hm[MI_READ + 2];
         if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
         const int base1 = (nc01[0] + 31) & ~31;
         nchunks = base1 + nc01[1];
@@ -790,24 +830,16 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, P4, graph->weights,
                                                          G4, ctx->ent_geo); ed_note_launch();
         ED_LAUNCH_CHECK();
-        int cnt3[2] = {nnzb, 0};
-        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, cnt3, sizeof(cnt3), cudaMemcpyHostToDevice, st));
-        ED_CUDA_TRY(cudaMemcpyAsync(&n_upper, ctx->flag_b + nnzb, sizeof(int), cudaMemcpyDeviceToHost, st));
-        ED_CUDA_TRY(cudaStreamSynchronize(st));
+        ctx->pinned[ED_MAX_PCG_GRID + 1] = nnzb;
+        ctx->pinned[ED_MAX_PCG_GRID + 2] = 0;
+        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, ctx->pinned + ED_MAX_PCG_GRID + 1, 2 * sizeof(int),
+                                    cudaMemcpyHostToDevice, st));
         n_upper += m;   // strictly upper blocks + the diagonal
         if (2 * n_upper != nnzb + m) return ED_ERR_STATE;   // the pattern must be symmetric with a full diagonal
     }
     // row partition and shared-memory plan of the PCG solve
-    {
-        int *rp = (int *)malloc(sizeof(int) * (m + 1));
-        if (!rp) return ED_ERR_ARG;
-        cudaError_t e = cudaMemcpyAsync(rp, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        ctx->m = m;
-        ed_status ps = e == cudaSuccess ? ed_pcg_plan(ctx, rp, st) : ED_ERR_CUDA;
-        free(rp);
-        if (ps != ED_OK) return ps;
-    }
+    ctx->m = m;
+    if ((s = ed_pcg_plan(ctx, ctx->row_ptr_host, st)) != ED_OK) return s;
 
     ctx->pos = pos;
     ctx->nrm = nrm;

@@ -21,76 +21,13 @@
 
 #include "ed_internal.cuh"
 
-#define BAR_TIMEOUT_NS 2000000000ull
 #define PCG_SMEM_MAX (200 * 1024)      // one 512-thread CTA per SM
 #define PCG_SMEM_MAX_256 (100 * 1024)  // two 256-thread CTAs per SM
 
+#define PCG_RI 2                       // staged column items per thread held in registers
+
 // 12 threads per node row (one per output row of a 12x12 block)
 template <int NT> struct RowsPerPass { static constexpr int v = NT / 12; };
-
-__device__ __forceinline__ unsigned long long gtimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned atom_add_release(unsigned *p, unsigned v)
-{
-    unsigned old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// grid barrier on a monotonic arrival counter that every CTA polls: the CTA's
-// writes are ordered before thread 0's arrival by the CTA barrier and a fence,
-// other CTAs' writes are visible after its acquire load of the count (later
-// reads of shared data bypass L1); returns false when the context status is
-// set (an error elsewhere, or this wait timed out)
-__device__ bool grid_sync(unsigned *count, int *status, unsigned nblocks, unsigned &target, int *s_flag)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        target += 1;
-        __threadfence();   // the whole CTA's writes (ordered by the CTA barrier) before the arrival
-        red_add_release(count, 1u);
-        const unsigned goal = nblocks * target;
-        const unsigned long long t0 = gtimer();
-        unsigned spins = 0;
-        while (ld_acquire(count) < goal) {
-            if ((++spins & 63u) == 0) {
-                if (*(volatile int *)status != ED_OK) { ok = 0; break; }
-                if (gtimer() - t0 > BAR_TIMEOUT_NS) {
-                    atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        if (*(volatile int *)status != ED_OK) ok = 0;
-        *s_flag = ok;
-    }
-    __syncthreads();
-    return *s_flag != 0;
-}
 
 struct PcgArgs {
     int m, n_iter;
@@ -278,10 +215,24 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         }
     };
 
-    // the block columns' z (and previous p) from their owners, issued together
-    // with the loads of the reduction that follows each barrier
-    auto stage_columns = [&](const float *pprev) {
-        for (int i = t; i < nblk * 3; i += NT) {
+    // The block columns' z and previous p from their owners, loaded in the same
+    // round as the reduction that follows each barrier: the first PCG_RI
+    // float4 items of every thread stay in registers until beta is known, the
+    // rest (large CTA shares) go through shared memory.
+    float4 zr[PCG_RI], pr[PCG_RI];
+    const int n_items = nblk * 3;
+    auto stage_issue = [&](const float *pprev) {
+#pragma unroll
+        for (int u = 0; u < PCG_RI; ++u) {
+            const int i = t + u * NT;
+            if (i < n_items) {
+                const int lb = i / 3, q4 = i - 3 * lb;
+                const int l = lc[lb];
+                zr[u] = __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l) + q4);
+                pr[u] = pprev ? __ldcg(reinterpret_cast<const float4 *>(pprev + 12 * l) + q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        for (int i = t + PCG_RI * NT; i < n_items; i += NT) {
             const int lb = i / 3, q4 = i - 3 * lb;
             const int l = lc[lb];
             reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] =
@@ -291,6 +242,30 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                     __ldcg(reinterpret_cast<const float4 *>(pprev + 12 * l) + q4);
         }
         if (t < 6) s_zp[t] = __ldcg(a.z + P + t);
+    };
+    // p_l = z_l + beta p_l(prev) for every staged item (beta unused at the first iteration)
+    auto stage_finish = [&](float beta, bool first) {
+#pragma unroll
+        for (int u = 0; u < PCG_RI; ++u) {
+            const int i = t + u * NT;
+            if (i < n_items) {
+                const int lb = i / 3, q4 = i - 3 * lb;
+                const float4 z4 = zr[u], p4 = pr[u];
+                reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] =
+                    first ? z4
+                          : make_float4(__fmaf_rn(beta, p4.x, z4.x), __fmaf_rn(beta, p4.y, z4.y),
+                                        __fmaf_rn(beta, p4.z, z4.z), __fmaf_rn(beta, p4.w, z4.w));
+            }
+        }
+        if (!first) {
+            for (int i = t + PCG_RI * NT; i < n_items; i += NT) {
+                const int lb = i / 3, q4 = i - 3 * lb;
+                float4 *b4 = reinterpret_cast<float4 *>(pb + (size_t)lb * 12) + q4;
+                const float4 z4 = *b4, p4 = reinterpret_cast<const float4 *>(po + (size_t)lb * 12)[q4];
+                *b4 = make_float4(__fmaf_rn(beta, p4.x, z4.x), __fmaf_rn(beta, p4.y, z4.y), __fmaf_rn(beta, p4.z, z4.z),
+                                  __fmaf_rn(beta, p4.w, z4.w));
+            }
+        }
     };
 
     // ---- set-up: r = b, d = 0, z = M^-1 r ----
@@ -312,8 +287,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         *part_at(part0, 0, cta) = (double)v1;
         *part_at(part0, 1, cta) = (double)v2;
     }
-    if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
-    stage_columns(nullptr);
+    if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+    stage_issue(nullptr);
     sum_partials<DT, NT, 2>(part0, nb, s_red, s_sum);
     if (t == 0) {
         s_rho = s_sum[0];
@@ -331,8 +306,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         const float beta = (float)s_beta;
         float *pnew = (it & 1) ? a.p1 : a.p0;
         // ---- p = z + beta p(prev): block columns (staged), own rows (published), pose ----
-        if (it > 0)
-            for (int i = t; i < nblk * 12; i += NT) pb[i] = __fmaf_rn(beta, po[i], pb[i]);
+        stage_finish(beta, it == 0);
         for (int i = t; i < rows * 12; i += NT) {
             const float pv = it > 0 ? __fmaf_rn(beta, ps[i], zs[i]) : zs[i];
             ps[i] = pv;
@@ -384,7 +358,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             block_sum_n<DT, NT, 7>(vv, s_red, s_blk);
             if (t < 7) *part_at(part1, t, cta) = (double)s_blk[t];
         }
-        if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         // ---- phase B: alpha, d += alpha p, r -= alpha q, z = M^-1 r ----
         sum_partials<DT, NT, 7>(part1, nb, s_red, s_sum);
         if (t < 6) {
@@ -426,8 +400,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             *part_at(part0, 0, cta) = (double)w1;
             *part_at(part0, 1, cta) = (double)w2;
         }
-        if (!grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
-        stage_columns(pnew);
+        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+        stage_issue(pnew);
         sum_partials<DT, NT, 2>(part0, nb, s_red, s_sum);
         if (t == 0) {
             s_beta = s_sum[0] / rho;
@@ -539,13 +513,12 @@ ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st)
     int grid = ctx->num_sms;
     if (grid > ED_MAX_PCG_GRID) grid = ED_MAX_PCG_GRID;
     if (grid > m) grid = m;
-    int rows_start[ED_MAX_PCG_GRID + 1];
+    int *rows_start = ctx->pinned;   // pinned: the copy below needs no synchronisation
     ed_pcg_plan_t pl;
     if ((s = ed_pcg_make_plan(row_ptr_host, m, grid, 512, &pl, rows_start)) != ED_OK) return s;
     ctx->pcg = pl;
-    memcpy(ctx->row_ptr_host, row_ptr_host, sizeof(int) * (m + 1));
+    if (row_ptr_host != ctx->row_ptr_host) memcpy(ctx->row_ptr_host, row_ptr_host, sizeof(int) * (m + 1));
     ED_CUDA_TRY(cudaMemcpyAsync(ctx->pcg_rows, rows_start, sizeof(int) * (grid + 1), cudaMemcpyHostToDevice, st));
-    ED_CUDA_TRY(cudaStreamSynchronize(st));   // rows_start lives on this stack frame
     return ED_OK;
 }
 
