@@ -197,56 +197,152 @@ __device__ __forceinline__ void warp_halving2(float2 (&v)[NV])
     }
 }
 
-// role 0: one warp per chunk of <= 128 entries of one upper block (j, l); lane
-// k takes entries k, k + 32, k + 64, k + 96 and forms the 60 moments
-// c (nb nb^T) (x) (d^ d^T) of its entries (paired FP32 FMA), the warp then sums
-// them by recursive halving: lane k owns moments 2k and 2k + 1
+// Recursive halving of 16 float2 values per lane down to one per lane pair,
+// then the pair: afterwards lanes 2k and 2k + 1 both hold the full sum of
+// slot k (fixed order: deterministic).
+__device__ __forceinline__ void warp_halving2_16(float2 (&v)[16])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16, n = 16; o > 1; o >>= 1, n >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) {
+            const float2 keep = hi ? v[k + n / 2] : v[k];
+            const float2 give = hi ? v[k] : v[k + n / 2];
+            float2 recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, give.x, o);
+            recv.y = __shfl_xor_sync(0xffffffffu, give.y, o);
+            v[k] = __fadd2_rn(keep, recv);
+        }
+    }
+    float2 recv;
+    recv.x = __shfl_xor_sync(0xffffffffu, v[0].x, 1);
+    recv.y = __shfl_xor_sync(0xffffffffu, v[0].y, 1);
+    v[0] = __fadd2_rn(v[0], recv);
+}
+
+// role 0: two warps per chunk of <= 128 entries of one upper block (j, l).
+// Lane k takes entries k, k + 32, k + 64, k + 96; warp half h forms the 30
+// moments c nn_a (d^ d^T)_q of a = 3h .. 3h + 2 (nn = the 6 products of
+// n~ = sqrt(w) R^T n, d^ = [v - g_j; 1], paired FP32 FMA), the warp then sums
+// them by recursive halving; half h writes moment pairs 15h .. 15h + 14.
 __global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
                                                    const float4 *__restrict__ geo, const uint32_t *__restrict__ ent,
                                                    const float4 *__restrict__ rec0, float *__restrict__ part)
 {
     const int lane = threadIdx.x & 31;
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int c = wg >> 1, h = wg & 1;
     if (c >= nchunks) return;
     const int4 ch = chunks[c];
     float4 gd[4], b[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int e = lane + 32 * h;
-        gd[h] = e < ch.z ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);   // w = 0: no contribution
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        gd[q] = e < ch.z ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);   // w = 0: no contribution
     }
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int e = lane + 32 * h;
-        b[h] = e < ch.z ? __ldg(rec0 + (__ldg(ent + ch.y + e) >> 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        b[q] = e < ch.z ? __ldg(rec0 + (__ldg(ent + ch.y + e) >> 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float2 v[32];
+    float2 v[16];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
+    for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const float cf = gd[h].w;
-        const float d0 = gd[h].x, d1 = gd[h].y, d2 = gd[h].z;
-        const float bx = cf * b[h].x, by = cf * b[h].y, bz = cf * b[h].z;
-        const float nn[6] = {bx * b[h].x, bx * b[h].y, bx * b[h].z, by * b[h].y, by * b[h].z, bz * b[h].z};
+    for (int q = 0; q < 4; ++q) {
+        const float cf = gd[q].w;
+        const float d0 = gd[q].x, d1 = gd[q].y, d2 = gd[q].z;
+        // this half's three products: (x x, x y, x z) or (y y, y z, z z), times c
+        const float s0 = cf * (h ? b[q].y : b[q].x);
+        const float s2 = cf * (h ? b[q].z : b[q].x);
+        const float nn[3] = {s0 * (h ? b[q].y : b[q].x), s0 * (h ? b[q].z : b[q].y), s2 * b[q].z};
         // d^ d^T upper triangle in pairs: (d0 d0, d0 d1) (d0 d2, d0) (d1 d1, d1 d2) (d1, d2 d2) (d2, 1)
         const float2 dd[5] = {make_float2(d0 * d0, d0 * d1), make_float2(d0 * d2, d0), make_float2(d1 * d1, d1 * d2),
                               make_float2(d1, d2 * d2), make_float2(d2, 1.0f)};
 #pragma unroll
-        for (int a = 0; a < 6; ++a) {
+        for (int a = 0; a < 3; ++a) {
             const float2 na = make_float2(nn[a], nn[a]);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) v[5 * a + q] = __ffma2_rn(na, dd[q], v[5 * a + q]);
+            for (int k = 0; k < 5; ++k) v[5 * a + k] = __ffma2_rn(na, dd[k], v[5 * a + k]);
+        }
+    }
+    warp_halving2_16(v);
+    if (!(lane & 1) && (lane >> 1) < 15)   // chunk-major partials: moment pairs 15 h + lane / 2
+        reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[15 * h + (lane >> 1)] = v[0];
+}
+
+// role 1 (diagonal blocks): two warps per chunk; per entry J^T r (12 floats)
+// and the pose-node block (6 x 12) of node j.  Moment pairs (float2 slots):
+// 0..5 J^T r, 6 + 6 t + 2 r (+1) pose-node row t, node row r.  Half 0 forms
+// slots 0..23 (J^T r, rows t = 0..2), half 1 slots 24..41 (t = 3..5); the
+// loads of two entries are issued together.
+template <int H>
+__device__ __forceinline__ void assemble1_half(const int4 ch, int c, const float *R, const float4 *__restrict__ geo,
+                                               const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
+                                               const float4 *__restrict__ rec1, float *__restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    constexpr int BASE = H == 0 ? 6 : 0;   // slot of row t = 3H within this half
+    float2 v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q0 = 0; q0 < 4; q0 += 2) {
+        float4 gd[2], b[2], jq[2];
+        int pi[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = lane + 32 * (q0 + u);
+            const bool in = e < ch.z;
+            gd[u] = in ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            pi[u] = in ? (int)(__ldg(ent + ch.y + e) >> 4) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            b[u] = pi[u] >= 0 ? __ldg(rec0 + pi[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (H == 0) jq[u] = pi[u] >= 0 ? __ldg(rec1 + pi[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float ws = sqrtf(gd[u].w);   // diagonal entries store w_s * w_s (0 for absent entries)
+            const float2 dlo = make_float2(gd[u].x, gd[u].y), dhi = make_float2(gd[u].z, 1.0f);
+            const float nb[3] = {ws * b[u].x, ws * b[u].y, ws * b[u].z};
+            // d r / d pose: angles (t = 0..2) from the point record, translation
+            // (t = 3..5) = R nb_s with nb_s = sqrt(w) R^T n
+            float jp[3];
+            if (H == 0) {
+                jp[0] = jq[u].x;
+                jp[1] = jq[u].y;
+                jp[2] = jq[u].z;
+            } else {
+                jp[0] = R[0] * b[u].x + R[1] * b[u].y + R[2] * b[u].z;
+                jp[1] = R[3] * b[u].x + R[4] * b[u].y + R[5] * b[u].z;
+                jp[2] = R[6] * b[u].x + R[7] * b[u].y + R[8] * b[u].z;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                if (H == 0) {
+                    const float2 g2 = make_float2(b[u].w * nb[r], b[u].w * nb[r]);
+                    v[2 * r] = __ffma2_rn(g2, dlo, v[2 * r]);
+                    v[2 * r + 1] = __ffma2_rn(g2, dhi, v[2 * r + 1]);
+                }
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const float s2 = jp[t] * nb[r];
+                    const float2 c2 = make_float2(s2, s2);
+                    v[BASE + 6 * t + 2 * r] = __ffma2_rn(c2, dlo, v[BASE + 6 * t + 2 * r]);
+                    v[BASE + 6 * t + 2 * r + 1] = __ffma2_rn(c2, dhi, v[BASE + 6 * t + 2 * r + 1]);
+                }
+            }
         }
     }
     warp_halving2<32>(v);
-    if (2 * lane < 60)   // chunk-major partials: 2 consecutive floats per lane, coalesced
-        reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[lane] = v[0];
+    constexpr int NSLOT = H == 0 ? 24 : 18;
+    if (lane < NSLOT) reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[24 * H + lane] = v[0];
 }
 
-// role 1 (diagonal blocks): one warp per chunk; per entry J^T r (12) and the
-// pose-node block (6 x 12) of node j, summed by recursive halving (128 slots,
-// 84 used: 0..11 J^T r, 12 + 12 t + p pose-node (t, p)); lane k owns 4k..4k+3
 __global__ void __launch_bounds__(128) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
                                                    int max_chunks, const float4 *__restrict__ geo,
                                                    const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
@@ -256,46 +352,12 @@ __global__ void __launch_bounds__(128) k_assemble1(const int4 *__restrict__ chun
     __shared__ ed_pose_f P;
     if (threadIdx.x == 0) ed_pose_eval(pose, P);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int c = c_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int c = c_begin + (wg >> 1), h = wg & 1;
     if (c >= c_begin + nchunks) return;
     const int4 ch = chunks[c];
-    const float *R = P.R;
-    float2 v[64];
-#pragma unroll
-    for (int k = 0; k < 64; ++k) v[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int e = lane + 32 * h;
-        if (e < ch.z) {
-            const float4 gd = __ldg(geo + ch.y + e);
-            const int i = (int)(__ldg(ent + ch.y + e) >> 4);
-            const float4 b = __ldg(rec0 + i);
-            const float4 jq = __ldg(rec1 + i);
-            const float ws = sqrtf(gd.w);   // diagonal entries store w_s * w_s
-            const float2 dlo = make_float2(gd.x, gd.y), dhi = make_float2(gd.z, 1.0f);
-            const float nb[3] = {ws * b.x, ws * b.y, ws * b.z};
-            // d r / d pose: (angles, R nb_s) with nb_s = sqrt(w) R^T n
-            const float jp[6] = {jq.x, jq.y, jq.z, R[0] * b.x + R[1] * b.y + R[2] * b.z,
-                                 R[3] * b.x + R[4] * b.y + R[5] * b.z, R[6] * b.x + R[7] * b.y + R[8] * b.z};
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const float2 g2 = make_float2(b.w * nb[r], b.w * nb[r]);
-                v[2 * r] = __ffma2_rn(g2, dlo, v[2 * r]);
-                v[2 * r + 1] = __ffma2_rn(g2, dhi, v[2 * r + 1]);
-#pragma unroll
-                for (int t = 0; t < 6; ++t) {
-                    const float s2 = jp[t] * nb[r];
-                    const float2 c2 = make_float2(s2, s2);
-                    v[6 + 6 * t + 2 * r] = __ffma2_rn(c2, dlo, v[6 + 6 * t + 2 * r]);
-                    v[6 + 6 * t + 2 * r + 1] = __ffma2_rn(c2, dhi, v[6 + 6 * t + 2 * r + 1]);
-                }
-            }
-        }
-    }
-    warp_halving2<64>(v);
-    if (4 * lane < 84)
-        reinterpret_cast<float4 *>(part + (long)c * ED_PART_STRIDE)[lane] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    if (h == 0) assemble1_half<0>(ch, c, P.R, geo, ent, rec0, rec1, part);
+    else assemble1_half<1>(ch, c, P.R, geo, ent, rec0, rec1, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -780,11 +842,11 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
         const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
         if (n0 > 0) {
-            k_assemble0<<<ed_div_up(n0, 4), 128, 0, st>>>(ctx->chunks, n0, ctx->max_chunks, ctx->ent_geo, ctx->ent_val,
+            k_assemble0<<<ed_div_up(2 * n0, 4), 128, 0, st>>>(ctx->chunks, n0, ctx->max_chunks, ctx->ent_geo, ctx->ent_val,
                                                            ctx->rec0, ctx->partials); ed_note_launch();
         }
         if (n1 > 0) {
-            k_assemble1<<<ed_div_up(n1, 4), 128, 0, st>>>(ctx->chunks, base1, n1, ctx->max_chunks, ctx->ent_geo,
+            k_assemble1<<<ed_div_up(2 * n1, 4), 128, 0, st>>>(ctx->chunks, base1, n1, ctx->max_chunks, ctx->ent_geo,
                                                            ctx->ent_val, ctx->rec0, ctx->rec1, pose, ctx->partials); ed_note_launch();
         }
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
