@@ -39,7 +39,7 @@ size_t carve(ed_context *c, char *base)
     const size_t nnzb = M * (size_t)L.max_pairs_per_node;
     const size_t nent = 10 * N;
     const size_t tiles = (nent + 1023) / 1024 + 1;
-    const size_t chunks = (16 * N) / ED_CHUNK + nnzb + M + 64;
+    const size_t chunks = (10 * N) / ED_CHUNK + (4 * N) / ED_CHUNK1 + nnzb + M + 64;
     const size_t P = 12 * M + 6;
     const size_t big = (N > WH ? N : WH);
     size_t scan_len = big > 256 * tiles ? big : 256 * tiles;

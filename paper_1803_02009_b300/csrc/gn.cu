@@ -197,6 +197,8 @@ __device__ __forceinline__ void warp_halving2(float2 (&v)[NV])
     }
 }
 
+static_assert(ED_CHUNK == 128 && ED_CHUNK1 == 128, "the assembly kernels take 4 entries per lane");
+
 // Recursive halving of 16 float2 values per lane down to one per lane pair,
 // then the pair: afterwards lanes 2k and 2k + 1 both hold the full sum of
 // slot k (fixed order: deterministic).
@@ -433,6 +435,20 @@ __device__ __forceinline__ float rot_res(const float *X, int q)
 
 #define FIN_WARPS 4
 
+// E_rot Gauss-Newton block between columns c and cp of A (3-vectors x_c over
+// node rows r, rp): sum over the 6 residuals x_a.x_b - delta_ab of products of
+// their derivatives; c != cp: x_cp[r] x_c[rp]; c == cp: 4 x_c[r] x_c[rp] +
+// sum_{d != c} x_d[r] x_d[rp]
+__device__ __forceinline__ float rot_jtj(const float *X, int r, int c, int rp, int cp)
+{
+    if (c != cp) return X[4 * r + cp] * X[4 * rp + c];
+    float v = 4.0f * X[4 * r + c] * X[4 * rp + c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d != c) v += X[4 * r + d] * X[4 * rp + d];
+    return v;
+}
+
 __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
 {
     __shared__ float sM[FIN_WARPS][84];
@@ -440,6 +456,17 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __shared__ float sX[FIN_WARPS][12];
     __shared__ float sS[FIN_WARPS][16];
     __shared__ float sL[FIN_WARPS][144];
+    __shared__ float sRinv[FIN_WARPS][12];
+    // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
+    // shift), R, C (the same for every block; computed once per CTA)
+    __shared__ int s_tab[144];
+    for (int e = threadIdx.x; e < 144; e += blockDim.x) {
+        const int R = e / 12, Cc = e % 12;
+        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+        const int mi = 10 * sym3(r, rp) + sym4(c, cp), m3 = 10 * sym3(r, rp) + sym4(c, 3);
+        s_tab[e] = mi | (m3 << 8) | (R << 16) | (Cc << 24);
+    }
+    __syncthreads();
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int u = blockIdx.x * FIN_WARPS + wid;
     if (u >= a.n_upper) return;
@@ -468,11 +495,11 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
             return;
         }
         for (int e = lane; e < 144; e += 32) {
-            const int R = e / 12, Cc = e % 12;
+            const int T = s_tab[e];
+            const int R = (T >> 16) & 255, Cc = T >> 24;
             const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
-            const float *Mr = M + 10 * sym3(r, rp);
-            float h = Mr[sym4(c, cp)];
-            if (cp < 3) h += dl[cp] * Mr[sym4(c, 3)];
+            float h = M[T & 255];
+            if (cp < 3) h += dl[cp] * M[(T >> 8) & 255];
             if (r == rp) {   // E_reg, edges j -> l (d e / d t_l = -I) and l -> j (d e / d t_j = -I)
                 if (e_jl && cp == 3) h -= wr * hjl[c];
                 if (e_lj && c == 3) h -= wr * (cp < 3 ? -hjl[cp] : 1.0f);
@@ -487,7 +514,7 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     const int c1 = a.n_chunks0 + a.chunk_start1[b];
     float *Gx = M + 60;
     for (int k = lane; k < 84; k += 32) {
-        const float v = sum_parts(a.part, k, a.max_chunks, c1, nch, a.mixed);
+        const float v = sum_parts(a.part, k, a.max_chunks, c1, (a.ent_cnt[b] + ED_CHUNK1 - 1) / ED_CHUNK1, a.mixed);
         if (k < 12) Gx[k] = v;
         else a.pnode[(long)j * 72 + (k - 12)] = v;
     }
@@ -528,15 +555,11 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __syncwarp();
     // the 144 entries: data moments + E_rot + E_reg (out-edges S, in-edges on t)
     for (int e = lane; e < 144; e += 32) {
-        const int R = e / 12, Cc = e % 12;
+        const int T = s_tab[e];
+        const int R = (T >> 16) & 255, Cc = T >> 24;
         const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
-        float h = M[10 * sym3(r, rp) + sym4(c, cp)];
-        if (c < 3 && cp < 3) {
-            float v = 0.f;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v += rot_jac(X, q, r, c) * rot_jac(X, q, rp, cp);
-            h += a.w_rot * v;
-        }
+        float h = M[T & 255];
+        if (c < 3 && cp < 3) h += a.w_rot * rot_jtj(X, r, c, rp, cp);
         if (r == rp) {
             h += wr * S[4 * c + cp];
             if (c == 3 && cp == 3) h += wr * nin;
@@ -588,24 +611,42 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __syncwarp();
     for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
     __syncwarp();
-    // block-Jacobi inverse: Cholesky of H + jitter tr/12 I, then L^-T L^-1
+    // block-Jacobi inverse: Cholesky of H + jitter tr/12 I (lower triangle, 78
+    // entries, at most three per lane), then L^-T L^-1
     float tr = 0.f;
     for (int k = 0; k < 12; ++k) tr += H[k * 13];
     __syncwarp();
     if (lane < 12) H[lane * 13] += a.jitter * tr / 12.0f;
+    int tri_r[3], tri_c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        int t = lane + 32 * q, r = 0;
+        while (t > r) {   // t -> (r, c) with t = r (r + 1) / 2 + c, c <= r
+            t -= r + 1;
+            ++r;
+        }
+        tri_r[q] = lane + 32 * q < 78 ? r : -1;
+        tri_c[q] = t;
+    }
     __syncwarp();
+    float *rinv = sRinv[wid];
     bool ok = true;
     for (int k = 0; k < 12; ++k) {
         const float piv = H[k * 13];
         if (!(piv > 0.f)) ok = false;
         const float sq = ok ? sqrtf(piv) : 1.0f;
+        const float inv = 1.0f / sq;
         __syncwarp();
-        if (lane == 0) H[k * 13] = sq;
-        if (lane > k && lane < 12) H[lane * 12 + k] /= sq;
+        if (lane == 0) {
+            H[k * 13] = sq;
+            rinv[k] = inv;
+        }
+        if (lane > k && lane < 12) H[lane * 12 + k] *= inv;
         __syncwarp();
-        for (int e = lane; e < 144; e += 32) {
-            const int r = e / 12, c = e % 12;
-            if (r > k && c > k && c <= r) H[e] -= H[r * 12 + k] * H[c * 12 + k];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int r = tri_r[q], c = tri_c[q];
+            if (r > k && c > k) H[r * 12 + c] -= H[r * 12 + k] * H[c * 12 + k];
         }
         __syncwarp();
     }
@@ -619,15 +660,16 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
         for (int r = 0; r < 12; ++r) {
             float v = (r == lane) ? 1.0f : 0.0f;
             for (int k = lane; k < r; ++k) v -= H[r * 12 + k] * sL[wid][k * 12 + lane];
-            sL[wid][r * 12 + lane] = r < lane ? 0.f : v / H[r * 13];
+            sL[wid][r * 12 + lane] = r < lane ? 0.f : v * rinv[r];
         }
     }
     __syncwarp();
+    // M^-1 = L^-T L^-1: entry (p, q) sums rows k >= max(p, q) of the lower-triangular L^-1
     for (int e = lane; e < 144; e += 32) {
-        const int p = e / 12, q = e % 12;
+        const int T = s_tab[e];
+        const int p = (T >> 16) & 255, q = T >> 24;
         float s2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) s2 += sL[wid][k * 12 + p] * sL[wid][k * 12 + q];
+        for (int k = p > q ? p : q; k < 12; ++k) s2 += sL[wid][k * 12 + p] * sL[wid][k * 12 + q];
         a.minv[(long)j * 144 + e] = s2;
     }
 }

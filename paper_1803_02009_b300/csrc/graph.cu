@@ -585,16 +585,16 @@ __global__ void k_ent_count(const uint32_t *__restrict__ key, int ne, int nnzb, 
     cnt[b] = lo2 - lo;
 }
 
-// chunks of <= ED_CHUNK entries: role 0 (moments) for every upper block, role 1
-// (J^T r and the pose-node block) for diagonal blocks; role-0 chunks first
+// chunks of <= ED_CHUNK entries, role 0 (moments), for every upper block and of
+// <= ED_CHUNK1 entries, role 1 (J^T r and the pose-node block), for diagonal
+// blocks; role-0 chunks first
 __global__ void k_chunk_count(int nnzb, const int *__restrict__ cnt, const int *__restrict__ brow,
                               const int *__restrict__ col, int *__restrict__ ccnt0, int *__restrict__ ccnt1)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnzb) return;
-    const int c = (cnt[b] + ED_CHUNK - 1) / ED_CHUNK;
-    ccnt0[b] = col[b] >= brow[b] ? c : 0;
-    ccnt1[b] = col[b] == brow[b] ? c : 0;
+    ccnt0[b] = col[b] >= brow[b] ? (cnt[b] + ED_CHUNK - 1) / ED_CHUNK : 0;
+    ccnt1[b] = col[b] == brow[b] ? (cnt[b] + ED_CHUNK1 - 1) / ED_CHUNK1 : 0;
 }
 
 __global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *__restrict__ ent_start,
@@ -605,13 +605,14 @@ __global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *_
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnzb || col[b] < brow[b]) return;
     const int n = cnt[b];
-    const int per = (n + ED_CHUNK - 1) / ED_CHUNK;
     const int base1 = (cstart0[nnzb] + 31) & ~31;   // role-1 chunks start warp-aligned
     for (int r = 0; r < (brow[b] == col[b] ? 2 : 1); ++r) {
+        const int size = r == 0 ? ED_CHUNK : ED_CHUNK1;
+        const int per = (n + size - 1) / size;
         int q = r == 0 ? cstart0[b] : base1 + cstart1[b];
         for (int k = 0; k < per; ++k) {
-            const int beg = ent_start[b] + k * ED_CHUNK;
-            const int c = min(ED_CHUNK, n - k * ED_CHUNK);
+            const int beg = ent_start[b] + k * size;
+            const int c = min(size, n - k * size);
             chunks[q++] = make_int4(b, beg, c, r);
         }
     }
