@@ -390,6 +390,55 @@ __device__ __forceinline__ bool ed_grid_sync(unsigned *count, int *status, unsig
 }
 
 
+// ---------------------------------------------------------------------------
+// bulk asynchronous global -> shared copies completing on an mbarrier
+// (addresses and sizes 16-byte aligned)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ed_smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ed_mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ed_smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// the calling thread arrives and announces `bytes` of copies to come
+__device__ __forceinline__ void ed_mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ed_smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ed_bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     ed_smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(ed_smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool ed_mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(ed_smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bounded wait for phase `parity` of an mbarrier (all threads may call it);
+// false when ED_BAR_TIMEOUT_NS passed (the caller records the error and then
+// waits once more for its copies before leaving)
+__device__ __forceinline__ bool ed_mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const unsigned long long t0 = ed_gtimer();
+    while (!ed_mbar_test(bar, parity))
+        if (ed_gtimer() - t0 > ED_BAR_TIMEOUT_NS) return false;
+    return true;
+}
+
 // Float-float accumulation (value = hi + lo): Knuth's error-free two-sum of
 // the high parts, the low parts added to its error, then a fast two-sum
 // renormalisation.  About 44 significant bits on the FP32 pipe (B300's FP64

@@ -161,26 +161,47 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
 
     if (*(volatile int *)a.status != ED_OK) return;
 
-    // ---- the CTA's share of H, M^-1, C, block columns and b into shared memory ----
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(a.bsr + (size_t)b0 * 144);
-        float4 *dst = reinterpret_cast<float4 *>(Hs);
-        for (int i = t; i < ncache * 36; i += NT) dst[i] = __ldg(src + i);
-        const float4 *ms = reinterpret_cast<const float4 *>(a.minv + (size_t)r0 * 144);
-        float4 *md = reinterpret_cast<float4 *>(Ms);
-        for (int i = t; i < rows * 36; i += NT) md[i] = __ldg(ms + i);
-        for (int i = t; i < rows * 72; i += NT) Cs[i] = __ldg(a.pnode + (size_t)r0 * 72 + i);
-        for (int i = t; i < nblk; i += NT) lc[i] = __ldg(a.col + b0 + i);
-        for (int i = t; i < rows * 12; i += NT) {
-            rs[i] = -__ldg(a.grad + 12 * r0 + i);
-            ds[i] = 0.f;
-        }
-        if (t < 36) {
-            s_Hpp[t] = a.pose_blk[t];
-            s_Mp[t] = a.pose_blk[36 + t];
-        }
+    // ---- the CTA's share of H, M^-1 and C into shared memory by bulk
+    // asynchronous copies (inverses and pose-node blocks on mbarrier 0, needed
+    // first; blocks on mbarrier 1, needed by the first q = H p); block columns
+    // and b by plain loads meanwhile ----
+    __shared__ __align__(8) unsigned long long s_mbar[2];
+    if (t == 0) {
+        ed_mbar_init(&s_mbar[0], 1);
+        ed_mbar_init(&s_mbar[1], 1);
     }
     __syncthreads();
+    if (t == 0) {
+        const unsigned mbytes = (unsigned)rows * 576u, cbytes = (unsigned)rows * 288u;
+        ed_mbar_expect_tx(&s_mbar[0], mbytes + cbytes);
+        if (mbytes) ed_bulk_g2s(Ms, a.minv + (size_t)r0 * 144, mbytes, &s_mbar[0]);
+        if (cbytes) ed_bulk_g2s(Cs, a.pnode + (size_t)r0 * 72, cbytes, &s_mbar[0]);
+        const size_t hbytes = (size_t)ncache * 576;
+        ed_mbar_expect_tx(&s_mbar[1], (unsigned)hbytes);
+        const char *hsrc = reinterpret_cast<const char *>(a.bsr + (size_t)b0 * 144);
+        char *hdst = reinterpret_cast<char *>(Hs);
+        for (size_t o = 0; o < hbytes; o += 32768) {
+            const unsigned n = (unsigned)(hbytes - o < 32768 ? hbytes - o : 32768);
+            ed_bulk_g2s(hdst + o, hsrc + o, n, &s_mbar[1]);
+        }
+    }
+    for (int i = t; i < nblk; i += NT) lc[i] = __ldg(a.col + b0 + i);
+    for (int i = t; i < rows * 12; i += NT) {
+        rs[i] = -__ldg(a.grad + 12 * r0 + i);
+        ds[i] = 0.f;
+    }
+    if (t < 36) {
+        s_Hpp[t] = a.pose_blk[t];
+        s_Mp[t] = a.pose_blk[36 + t];
+    }
+    if (!ed_mbar_wait(&s_mbar[0], 0)) {
+        atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
+        ed_mbar_wait(&s_mbar[0], 0);
+        ed_mbar_wait(&s_mbar[1], 0);
+        return;
+    }
+    __syncthreads();
+    bool h_ready = false;
 
     // z_j = Minv_j r_j for the own rows (thread = one output row); partials r.z, r.r
     auto precond = [&](DT &rz, DT &rrs) {
@@ -314,6 +335,14 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         }
         if (t < 6) s_pp[t] = it > 0 ? __fmaf_rn(beta, s_pp[t], s_zp[t]) : s_zp[t];
         __syncthreads();
+        if (!h_ready) {   // the blocks, copied during the set-up
+            if (!ed_mbar_wait(&s_mbar[1], 0)) {
+                atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
+                ed_mbar_wait(&s_mbar[1], 0);
+                return;
+            }
+            h_ready = true;
+        }
         // ---- phase A: q = H p for the own rows (thread = one output row of one
         // of the S splits of a row's blocks), partials p.q and C p ----
         DT pq = 0;
