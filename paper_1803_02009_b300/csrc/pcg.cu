@@ -49,10 +49,12 @@ __device__ __forceinline__ double *part_at(double *part, int w, int c) { return 
 
 // sums the NC components of all CTA partials: NT / NCP threads per
 // component stride over the CTAs (one round of loads for up to 4x that many
-// CTAs), then a fixed shuffle tree and a fixed-order sum of the warp results,
-// so every CTA gets the same result.  Called by all threads; result in out_sh.
+// CTAs), then a fixed shuffle tree and a fixed-order sum of the warp results
+// that every thread forms itself (one CTA barrier), so every CTA and every
+// thread gets the same values.  `sh` must not be in use by other code
+// between two calls.
 template <typename DT, int NT, int NC>
-__device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh)[8], DT *out_sh)
+__device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh)[8], DT (&out)[NC])
 {
     constexpr int NCP = NC <= 1 ? 1 : NC <= 2 ? 2 : NC <= 4 ? 4 : 8;
     constexpr int TPC = NT / NCP;       // threads per component
@@ -68,18 +70,19 @@ __device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) sh[threadIdx.x >> 5][0] = s;
     __syncthreads();
-    if (threadIdx.x < NC) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
         DT r = 0;
 #pragma unroll
-        for (int k = 0; k < WPC; ++k) r += sh[threadIdx.x * WPC + k][0];
-        out_sh[threadIdx.x] = r;
+        for (int k = 0; k < WPC; ++k) r += sh[c * WPC + k][0];
+        out[c] = r;
     }
-    __syncthreads();
 }
 
-// block reduction of NV values per thread; result in sh_out[0..NV) (all threads)
+// block reduction of NV values per thread: after one CTA barrier,
+// block_sum_get(c) gives component c (fixed order) to any thread that asks
 template <typename DT, int NT, int NV>
-__device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8], DT *sh_out)
+__device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8])
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -90,12 +93,14 @@ __device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8], DT *sh_out
         if (lane == 0) sh[wid][k] = x;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        DT s = 0;
-        for (int w = 0; w < NT / 32; ++w) s += sh[w][threadIdx.x];
-        sh_out[threadIdx.x] = s;
-    }
-    __syncthreads();
+}
+
+template <typename DT, int NT>
+__device__ __forceinline__ DT block_sum_get(const DT (*sh)[8], int c)
+{
+    DT s = 0;
+    for (int w = 0; w < NT / 32; ++w) s += sh[w][c];
+    return s;
 }
 
 // shared-memory carve of one CTA (in floats; every region a multiple of 4)
@@ -131,13 +136,11 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_flag;
-    __shared__ DT s_red[NT / 32][8];
-    __shared__ DT s_sum[8];
-    __shared__ DT s_blk[8];
-    __shared__ float s_pp[6], s_zp[6], s_qp[6], s_rpose[6], s_dpose[6];
+    __shared__ DT s_red[NT / 32][8];    // block reductions
+    __shared__ DT s_red2[NT / 32][8];   // sums of the CTA partials
+    __shared__ float s_pp[6], s_zp[6], s_rpose[6], s_dpose[6];
     __shared__ float s_Hpp[36], s_Mp[36];
-    __shared__ DT s_rho, s_beta, s_rr, s_res0, s_alpha;
-    __shared__ int s_break;
+
     unsigned target = 0;
     const int m = a.m;
     const int r0 = a.cta_rows[cta], r1 = a.cta_rows[cta + 1];
@@ -294,10 +297,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         DT rz = 0, rrs = 0;
         precond(rz, rrs);
         DT vv[2] = {rz, rrs};
-        block_sum_n<DT, NT, 2>(vv, s_red, s_blk);
+        block_sum_n<DT, NT, 2>(vv, s_red);
     }
     if (t == 0) {
-        DT v1 = s_blk[0], v2 = s_blk[1];
+        DT v1 = block_sum_get<DT, NT>(s_red, 0), v2 = block_sum_get<DT, NT>(s_red, 1);
         if (cta == 0) {
             for (int i = 0; i < 6; ++i) {
                 s_rpose[i] = -a.grad[P + i];
@@ -310,21 +313,22 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     }
     if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
     stage_issue(nullptr);
-    sum_partials<DT, NT, 2>(part0, nb, s_red, s_sum);
-    if (t == 0) {
-        s_rho = s_sum[0];
-        s_rr = s_sum[1];
-        s_res0 = sqrt((double)s_sum[1]);
-        s_beta = 0;
+    // the scalars of the iteration live in every thread's registers (identical values)
+    DT rho, rr2s, res0;
+    float beta = 0.f;
+    {
+        DT sums[2];
+        sum_partials<DT, NT, 2>(part0, nb, s_red2, sums);
+        rho = sums[0];
+        rr2s = sums[1];
+        res0 = (DT)sqrt((double)sums[1]);
     }
-    __syncthreads();
+    float qp[6];   // the pose rows of q = H p (CTA 0 thread 0 uses them for the pose update)
 
     int it = 0;
     for (; it < a.n_iter; ++it) {
-        const DT rho = s_rho;
         if (!(rho > (DT)0)) break;
-        if (a.tol > 0.f && sqrt((double)s_rr) <= (double)a.tol * (double)s_res0) break;
-        const float beta = (float)s_beta;
+        if (a.tol > 0.f && sqrt((double)rr2s) <= (double)a.tol * (double)res0) break;
         float *pnew = (it & 1) ? a.p1 : a.p0;
         // ---- p = z + beta p(prev): block columns (staged), own rows (published), pose ----
         stage_finish(beta, it == 0);
@@ -380,32 +384,35 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
 #pragma unroll
                 for (int s = 0; s < 6; ++s) cp[s] += (DT)C[12 * s + rr] * (DT)pv;
             }
-            __syncthreads();
+            if (j0 + rpp < rows) __syncthreads();   // qsplit is reused by the next pass
         }
         {
             DT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
-            block_sum_n<DT, NT, 7>(vv, s_red, s_blk);
-            if (t < 7) *part_at(part1, t, cta) = (double)s_blk[t];
+            block_sum_n<DT, NT, 7>(vv, s_red);
+            if (t < 7) *part_at(part1, t, cta) = (double)block_sum_get<DT, NT>(s_red, t);
         }
         if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
-        // ---- phase B: alpha, d += alpha p, r -= alpha q, z = M^-1 r ----
-        sum_partials<DT, NT, 7>(part1, nb, s_red, s_sum);
-        if (t < 6) {
-            float qi = (float)s_sum[1 + t];
-            for (int k = 0; k < 6; ++k) qi += Hpp[6 * t + k] * s_pp[k];
-            s_qp[t] = qi;
+        // ---- phase B: alpha (every thread), d += alpha p, r -= alpha q, z = M^-1 r ----
+        DT alpha_d;
+        {
+            DT sums[7];
+            sum_partials<DT, NT, 7>(part1, nb, s_red2, sums);
+            DT pqt = sums[0];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                float qi = (float)sums[1 + i];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
+                qp[i] = qi;
+                pqt += (DT)s_pp[i] * (DT)qi;
+            }
+            if (!(pqt > (DT)0)) {
+                if (cta == 0 && t == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
+                break;
+            }
+            alpha_d = rho / pqt;
         }
-        __syncthreads();
-        if (t == 0) {
-            DT pqt = s_sum[0];
-            for (int i = 0; i < 6; ++i) pqt += (DT)s_pp[i] * (DT)s_qp[i];
-            s_break = !(pqt > (DT)0);
-            s_alpha = rho / pqt;
-            if (s_break && cta == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
-        }
-        __syncthreads();
-        if (s_break) break;
-        const float alpha = (float)s_alpha;
+        const float alpha = (float)alpha_d;
         for (int i = t; i < rows * 12; i += NT) {
             ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
             rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
@@ -415,14 +422,14 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             DT rz2 = 0, rr2 = 0;
             precond(rz2, rr2);
             DT vv[2] = {rz2, rr2};
-            block_sum_n<DT, NT, 2>(vv, s_red, s_blk);
+            block_sum_n<DT, NT, 2>(vv, s_red);
         }
         if (t == 0) {
-            DT w1 = s_blk[0], w2 = s_blk[1];
+            DT w1 = block_sum_get<DT, NT>(s_red, 0), w2 = block_sum_get<DT, NT>(s_red, 1);
             if (cta == 0) {
                 for (int i = 0; i < 6; ++i) {
                     s_dpose[i] = __fmaf_rn(alpha, s_pp[i], s_dpose[i]);
-                    s_rpose[i] = __fmaf_rn(-alpha, s_qp[i], s_rpose[i]);
+                    s_rpose[i] = __fmaf_rn(-alpha, qp[i], s_rpose[i]);
                 }
                 pose_precond(w1, w2);
             }
@@ -431,21 +438,21 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         }
         if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         stage_issue(pnew);
-        sum_partials<DT, NT, 2>(part0, nb, s_red, s_sum);
-        if (t == 0) {
-            s_beta = s_sum[0] / rho;
-            s_rho = s_sum[0];
-            s_rr = s_sum[1];
+        {
+            DT sums[2];
+            sum_partials<DT, NT, 2>(part0, nb, s_red2, sums);
+            beta = (float)(sums[0] / rho);
+            rho = sums[0];
+            rr2s = sums[1];
         }
-        __syncthreads();
     }
     // solution of the CTA's rows (and of the pose: CTA 0)
     for (int i = t; i < rows * 12; i += NT) a.d[12 * r0 + i] = ds[i];
     if (cta == 0 && t < 6) a.d[P + t] = s_dpose[t];
     if (cta == 0 && t == 0 && a.stats) {
         a.stats->pcg_iters = it;
-        a.stats->pcg_res0 = (double)s_res0;
-        a.stats->pcg_res = sqrt((double)s_rr);
+        a.stats->pcg_res0 = (double)res0;
+        a.stats->pcg_res = sqrt((double)rr2s);
     }
 }
 
