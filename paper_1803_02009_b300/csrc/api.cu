@@ -44,6 +44,7 @@ size_t carve(ed_context *c, char *base)
     const size_t big = (N > WH ? N : WH);
     size_t scan_len = big > 256 * tiles ? big : 256 * tiles;
     if (nnzb > scan_len) scan_len = nnzb;
+    if (cells + 1 > scan_len) scan_len = cells + 1;   // node flags over the sampling grid
     Carver k{base};
     c->misc = k.take<int>(MI_COUNT);
     c->fmisc = k.take<float>(MF_COUNT);
@@ -100,7 +101,9 @@ size_t carve(ed_context *c, char *base)
     c->fused_pix = k.take<int>(N);
     c->flag_a = k.take<int>(big + 1);
     c->flag_b = k.take<int>(big + 1);
-    c->scan_tmp = k.take<int>(scan_len / 1024 + 2048);
+    c->scan_state_len = (int)((scan_len + 4095) / 4096 + 2);
+    c->scan_state = k.take<unsigned long long>(c->scan_state_len);
+    c->scan_ticket = k.take<unsigned>(64);
     c->gpts = k.take<float4>(2 * N);
     return k.off + 256;
 }
@@ -149,7 +152,9 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
     c->ws_bytes = workspace_bytes;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess) {
+        cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess ||
+        cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_state_len) != cudaSuccess ||
+        cudaMemset(c->scan_ticket, 0, sizeof(unsigned)) != cudaSuccess) {
         cudaFreeHost(c->row_ptr_host);
         cudaFreeHost(c->pinned);
         free(c);
@@ -227,89 +232,116 @@ extern "C" ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of int arrays (out[n] = total), three-phase, recursive
+// exclusive scan of int arrays (out[n] = total) in one pass: decoupled
+// look-back over tiles of 4096.  Tiles take increasing ticket numbers in the
+// order CTAs start, so a tile only waits for tiles that are already running.
+// Every tile publishes its aggregate, then its inclusive prefix, as one 64-bit
+// word tagged with the scan's epoch (words of older scans never match); the
+// wait for a predecessor gives up after ED_BAR_TIMEOUT_NS (ED_ERR_TIMEOUT).
 // ---------------------------------------------------------------------------
 
-#define SCAN_T 256
-#define SCAN_PER 4
-#define SCAN_TILE (SCAN_T * SCAN_PER)
+#define DS_T 256
+#define DS_PER 16
+#define DS_TILE (DS_T * DS_PER)
+#define DS_AGG 1u
+#define DS_INC 2u
 
-__device__ __forceinline__ int block_excl_scan(int v, int *sh, int &total)
+__device__ __forceinline__ unsigned long long ds_load(const unsigned long long *p)
 {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void ds_store(unsigned long long *p, unsigned epoch, unsigned flag, int v)
+{
+    const unsigned long long w = ((unsigned long long)((epoch << 2) | flag) << 32) | (unsigned)v;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int n, unsigned long long *state,
+                                                   unsigned *ticket, unsigned ticket_base, unsigned epoch,
+                                                   int *status)
+{
+    __shared__ int s_tile, s_excl, s_warp[DS_T / 32];
+    if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ticket, 1u) - ticket_base);
+    __syncthreads();
+    const int tile = s_tile;
+    const long base = (long)tile * DS_TILE + (long)threadIdx.x * DS_PER;
+    int v[DS_PER], sum = 0;
+    if (base + DS_PER <= n && !((uintptr_t)(in + base) & 15)) {
+        const int4 *p4 = reinterpret_cast<const int4 *>(in + base);
+#pragma unroll
+        for (int q = 0; q < DS_PER / 4; ++q) {
+            const int4 w = p4[q];
+            v[4 * q] = w.x;
+            v[4 * q + 1] = w.y;
+            v[4 * q + 2] = w.z;
+            v[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < DS_PER; ++e) v[e] = base + e < n ? in[base + e] : 0;
+    }
+#pragma unroll
+    for (int e = 0; e < DS_PER; ++e) sum += v[e];
+    // exclusive prefix of the thread sums within the tile
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
+    int x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) sh[wid] = x;
+    if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        int s = lane < (SCAN_T / 32) ? sh[lane] : 0;
+        int w = lane < DS_T / 32 ? s_warp[lane] : 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+        for (int o = 1; o < DS_T / 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
         }
-        if (lane < (SCAN_T / 32)) sh[lane] = s;
+        if (lane < DS_T / 32) s_warp[lane] = w;
     }
     __syncthreads();
-    total = sh[SCAN_T / 32 - 1];
-    int r = x - v + (wid > 0 ? sh[wid - 1] : 0);
+    const int aggregate = s_warp[DS_T / 32 - 1];
+    int run = (wid > 0 ? s_warp[wid - 1] : 0) + x - sum;
+    // the tile's exclusive prefix from its predecessors
+    if (threadIdx.x == 0) {
+        int excl = 0;
+        if (tile == 0) {
+            ds_store(state, epoch, DS_INC, aggregate);
+        } else {
+            ds_store(state + tile, epoch, DS_AGG, aggregate);
+            const unsigned long long t0 = ed_gtimer();
+            unsigned spins = 0;
+            for (int p = tile - 1; p >= 0;) {
+                const unsigned long long w = ds_load(state + p);
+                const unsigned hi = (unsigned)(w >> 32), fl = hi & 3u;
+                if ((hi >> 2) != epoch || fl == 0u) {
+                    if ((++spins & 63u) == 0 && ed_gtimer() - t0 > ED_BAR_TIMEOUT_NS) {
+                        atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                excl += (int)(unsigned)w;
+                if (fl == DS_INC) break;
+                --p;
+            }
+            ds_store(state + tile, epoch, DS_INC, excl + aggregate);
+        }
+        s_excl = excl;
+    }
     __syncthreads();
-    return r;
-}
-
-__global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int n, int *__restrict__ sums)
-{
-    __shared__ int sh[32];
-    const long base = (long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
-    int v[SCAN_PER], loc = 0;
+    run += s_excl;
 #pragma unroll
-    for (int e = 0; e < SCAN_PER; ++e) {
-        v[e] = (base + e < n) ? in[base + e] : 0;
-        loc += v[e];
+    for (int e = 0; e < DS_PER; ++e) {
+        if (base + e < n) out[base + e] = run;
+        run += v[e];
+        if (base + e == n - 1) out[n] = run;
     }
-    int total;
-    int pre = block_excl_scan(loc, sh, total);
-#pragma unroll
-    for (int e = 0; e < SCAN_PER; ++e) {
-        if (base + e < n) out[base + e] = pre;
-        pre += v[e];
-    }
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
-}
-
-__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ offs, int *__restrict__ total_out,
-                           const int *__restrict__ total_src)
-{
-    const long base = (long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
-    const int o = offs[blockIdx.x];
-#pragma unroll
-    for (int e = 0; e < SCAN_PER; ++e)
-        if (base + e < n) out[base + e] += o;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *total_out = *total_src;
-}
-
-static ed_status scan_rec(const int *in, int *out, int n, int *tmp, cudaStream_t st)
-{
-    const int nb = ed_div_up(n, SCAN_TILE);
-    int *sums = tmp;              // nb + 1 entries (exclusive scan, last = total)
-    int *next = tmp + nb + 1;
-    k_scan_tiles<<<nb, SCAN_T, 0, st>>>(in, out, n, sums); ed_note_launch();
-    ED_LAUNCH_CHECK();
-    if (nb == 1) {
-        // sums[0] = total; make out[n] = total and sums exclusive
-        k_scan_add<<<1, SCAN_T, 0, st>>>(out, 0, next /*unused*/, out + n, sums); ed_note_launch();
-        ED_LAUNCH_CHECK();
-        return ED_OK;
-    }
-    ed_status s = scan_rec(sums, sums, nb, next, st);
-    if (s != ED_OK) return s;
-    k_scan_add<<<nb, SCAN_T, 0, st>>>(out, n, sums, out + n, sums + nb); ed_note_launch();
-    ED_LAUNCH_CHECK();
-    return ED_OK;
 }
 
 __global__ void k_set_zero_at(int *p) { *p = 0; }
@@ -321,8 +353,18 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
         ED_LAUNCH_CHECK();
         return ED_OK;
     }
-    // the nb == 1 path of scan_rec reads offs[0] of `next`; keep it zero
-    return scan_rec(in, out, n, ctx->scan_tmp, st);
+    const int tiles = ed_div_up(n, DS_TILE);
+    if (tiles > ctx->scan_state_len) return ED_ERR_CAPACITY;
+    unsigned epoch = ++ctx->scan_epoch;
+    if (epoch >= (1u << 30)) {   // epochs wrap: clear the words of old scans
+        ED_CUDA_TRY(cudaMemsetAsync(ctx->scan_state, 0, sizeof(unsigned long long) * ctx->scan_state_len, st));
+        ctx->scan_epoch = epoch = 1;
+    }
+    k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
+                                       ctx->misc + MI_STATUS); ed_note_launch();
+    ctx->scan_ticket_base += (unsigned)tiles;
+    ED_LAUNCH_CHECK();
+    return ED_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -130,7 +130,10 @@ struct ed_context {
     int *fused_pix;          // [N]
     int *flag_a;             // [max(N, W H) + 1]
     int *flag_b;             // [max(N, W H) + 1]
-    int *scan_tmp;           // block sums
+    unsigned long long *scan_state;   // [scan_state_len] tile words of the one-pass scan
+    int scan_state_len;
+    unsigned *scan_ticket;   // tile ticket counter (never reset; host mirror below)
+    unsigned scan_ticket_base, scan_epoch;
     float4 *gpts;            // [N] gradient per-point records (x2)
 
     // ---- graph state (host) ----
