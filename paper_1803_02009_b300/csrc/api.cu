@@ -385,35 +385,43 @@ __global__ void k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift
     cnt[(long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// one warp per tile; elements visited in order, 32 at a time; equal digits keep order
-__global__ void k_radix_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int n, int shift,
-                                int ntiles, const int *__restrict__ offs, uint32_t *__restrict__ ko,
-                                uint32_t *__restrict__ vo)
+// one warp per tile; the tile's keys and values are loaded up front (32 per
+// lane, one round of loads), then visited in order, 32 at a time; equal digits
+// keep their order
+__global__ void __launch_bounds__(32) k_radix_scatter(const uint32_t *__restrict__ keys,
+                                                      const uint32_t *__restrict__ vals, int n, int shift, int ntiles,
+                                                      const int *__restrict__ offs, uint32_t *__restrict__ ko,
+                                                      uint32_t *__restrict__ vo)
 {
     __shared__ int c[256];
     const int tile = blockIdx.x;
     const int lane = threadIdx.x;
+    const long base = (long)tile * RX_TILE;
+    uint32_t kk[RX_TILE / 32], vv[RX_TILE / 32];
+#pragma unroll
+    for (int r = 0; r < RX_TILE / 32; ++r) {
+        const long e = base + 32 * r + lane;
+        kk[r] = e < n ? keys[e] : 0u;
+        vv[r] = e < n ? vals[e] : 0u;
+    }
     for (int d = lane; d < 256; d += 32) c[d] = offs[(long)d * ntiles + tile];
     __syncwarp();
-    const long base = (long)tile * RX_TILE;
     const unsigned lt = (1u << lane) - 1u;
-    for (int s = 0; s < RX_TILE; s += 32) {
-        const long e = base + s + lane;
+#pragma unroll
+    for (int r = 0; r < RX_TILE / 32; ++r) {
+        const long e = base + 32 * r + lane;
         const bool ok = e < n;
-        const unsigned active = __ballot_sync(0xffffffffu, ok);
-        if (!active) break;
-        uint32_t k = ok ? keys[e] : 0u;
-        uint32_t v = ok ? vals[e] : 0u;
-        int d = ok ? (int)((k >> shift) & 255u) : 256 + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int rank = __popc(peers & lt);
-        int pos = ok ? c[d] + rank : 0;
+        const uint32_t k = kk[r];
+        const int d = ok ? (int)((k >> shift) & 255u) : 256 + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        const int pos = ok ? c[d] + rank : 0;
         __syncwarp();
         if (ok && rank == 0) c[d] += __popc(peers);
         __syncwarp();
         if (ok) {
             ko[pos] = k;
-            vo[pos] = v;
+            vo[pos] = vv[r];
         }
     }
 }
