@@ -22,8 +22,9 @@ __global__ void k_bbox_init(int *misc)
     }
 }
 
-__global__ void k_bbox(const float4 *__restrict__ pos, int n, int *misc)
+__global__ void __launch_bounds__(256) k_bbox(const float4 *__restrict__ pos, int n, int *misc)
 {
+    __shared__ float smn[3][8], smx[3][8];
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float4 p = pos[i];
@@ -36,11 +37,24 @@ __global__ void k_bbox(const float4 *__restrict__ pos, int n, int *misc)
             mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
             mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
         }
-    if ((threadIdx.x & 31) == 0)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
         for (int d = 0; d < 3; ++d) {
-            atomicMin(&misc[MI_BBOX + d], f2o(mn[d]));
-            atomicMax(&misc[MI_BBOX + 3 + d], f2o(mx[d]));
+            smn[d][w] = mn[d];
+            smx[d][w] = mx[d];
         }
+    __syncthreads();
+    // one atomic per CTA and bound (min/max are exact in any order)
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        float a = smn[d][0], b = smx[d][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            a = fminf(a, smn[d][k]);
+            b = fmaxf(b, smx[d][k]);
+        }
+        atomicMin(&misc[MI_BBOX + d], f2o(a));
+        atomicMax(&misc[MI_BBOX + 3 + d], f2o(b));
+    }
 }
 
 // cell size, inverse and dims of the sampling grid (edge r / sqrt 3) and of the
@@ -565,34 +579,28 @@ __global__ void k_entries_gen(const ushort4 *__restrict__ idx, int n, const int 
         }
 }
 
-// entries of block b = [lower_bound(b), lower_bound(b + 1)) in the sorted keys
-__global__ void k_ent_count(const uint32_t *__restrict__ key, int ne, int nnzb, int *__restrict__ cnt)
+// first entry of every block in the sorted keys: the entry at each key change
+// starts the blocks (previous key, its key]; one extra thread closes the range
+// up to nnzb (start[nnzb] = ne); blocks without entries get empty ranges
+__global__ void k_ent_bounds(const uint32_t *__restrict__ key, int ne, int nnzb, int *__restrict__ start)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnzb) return;
-    int lo = 0, hi = ne;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (key[mid] < (uint32_t)b) lo = mid + 1;
-        else hi = mid;
-    }
-    int lo2 = lo, hi2 = ne;
-    while (lo2 < hi2) {
-        const int mid = (lo2 + hi2) >> 1;
-        if (key[mid] < (uint32_t)b + 1u) lo2 = mid + 1;
-        else hi2 = mid;
-    }
-    cnt[b] = lo2 - lo;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > ne) return;
+    const int cur = e < ne ? (int)key[e] : nnzb;
+    const int prev = e > 0 ? (int)key[e - 1] : -1;
+    for (int b = prev + 1; b <= cur; ++b) start[b] = e;
 }
 
 // chunks of <= ED_CHUNK entries, role 0 (moments), for every upper block and of
 // <= ED_CHUNK1 entries, role 1 (J^T r and the pose-node block), for diagonal
 // blocks; role-0 chunks first
-__global__ void k_chunk_count(int nnzb, const int *__restrict__ cnt, const int *__restrict__ brow,
-                              const int *__restrict__ col, int *__restrict__ ccnt0, int *__restrict__ ccnt1)
+__global__ void k_chunk_count(int nnzb, const int *__restrict__ ent_start, int *__restrict__ cnt,
+                              const int *__restrict__ brow, const int *__restrict__ col, int *__restrict__ ccnt0,
+                              int *__restrict__ ccnt1)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnzb) return;
+    cnt[b] = ent_start[b + 1] - ent_start[b];
     ccnt0[b] = col[b] >= brow[b] ? (cnt[b] + ED_CHUNK - 1) / ED_CHUNK : 0;
     ccnt1[b] = col[b] == brow[b] ? (cnt[b] + ED_CHUNK1 - 1) / ED_CHUNK1 : 0;
 }
@@ -800,11 +808,9 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         int bits = 1;
         while ((1 << bits) < nnzb) ++bits;
         if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, ne, bits, st)) != ED_OK) return s;
-        k_ent_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(ctx->ent_key, ne, nnzb, ctx->ent_cnt); ed_note_launch();
-        ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->ent_cnt, ctx->ent_start, nnzb, st)) != ED_OK) return s;
-        k_chunk_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->brow, ctx->col, ctx->chunk_cnt,
-                                                            ctx->chunk_cnt1); ed_note_launch();
+        k_ent_bounds<<<ed_div_up(ne + 1, 256), 256, 0, st>>>(ctx->ent_key, ne, nnzb, ctx->ent_start); ed_note_launch();
+        k_chunk_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_start, ctx->ent_cnt, ctx->brow, ctx->col,
+                                                            ctx->chunk_cnt, ctx->chunk_cnt1); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt, ctx->chunk_start, nnzb, st)) != ED_OK) return s;
         if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt1, ctx->chunk_start1, nnzb, st)) != ED_OK) return s;
