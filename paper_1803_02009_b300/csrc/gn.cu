@@ -32,7 +32,7 @@ struct PointArgs {
 // Per point: Eq. (1) warp, visible-point gate, data residual r = n(u).(v~ - Gamma)
 // and its derivative factors; per-CTA sums of E_data, the count, the 6x6 pose
 // block and the pose gradient (fixed grid-stride order: deterministic).
-__global__ void __launch_bounds__(ED_K1_THREADS) k_points(PointArgs a)
+__global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
 {
     __shared__ ed_pose_f P;
     __shared__ float red[ED_K1_THREADS / 32][30];

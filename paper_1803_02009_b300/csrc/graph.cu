@@ -551,32 +551,44 @@ __global__ void k_compact_upper(int nnzb, int m, const int *__restrict__ flag, c
 
 // one entry per (point, unordered slot pair s <= t): key = upper block, value =
 // point << 4 | row slot << 2 | column slot, generated in point order
-__global__ void k_entries_gen(const ushort4 *__restrict__ idx, int n, const int *__restrict__ row_ptr,
-                              const int *__restrict__ col, uint32_t *__restrict__ key, uint32_t *__restrict__ val,
-                              int *__restrict__ status)
+#define EG_T 128
+// the 10 entries (s <= t) of every point, written through shared memory so
+// that a CTA's 10 x 128 keys and values go out as contiguous stores
+__global__ void __launch_bounds__(EG_T) k_entries_gen(const ushort4 *__restrict__ idx, int n,
+                                                      const int *__restrict__ row_ptr, const int *__restrict__ col,
+                                                      uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                      int *__restrict__ status)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const ushort4 q = idx[i];
-    const int id[4] = {q.x, q.y, q.z, q.w};
-    int e = 0;
+    __shared__ uint32_t sk[10 * EG_T], sv[10 * EG_T];
+    const int i0 = blockIdx.x * EG_T, i = i0 + threadIdx.x;
+    if (i < n) {
+        const ushort4 q = idx[i];
+        const int id[4] = {q.x, q.y, q.z, q.w};
+        int e = 0;
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+        for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int t = s; t < 4; ++t) {
-            int j = id[s], l = id[t], sr = s, sc = t;
-            if (j > l) {
-                j = id[t];
-                l = id[s];
-                sr = t;
-                sc = s;
+            for (int t = s; t < 4; ++t) {
+                int j = id[s], l = id[t], sr = s, sc = t;
+                if (j > l) {
+                    j = id[t];
+                    l = id[s];
+                    sr = t;
+                    sc = s;
+                }
+                const int b = find_block(row_ptr, col, j, l);
+                if (b < 0) atomicExch(status, ED_ERR_STATE);
+                sk[10 * threadIdx.x + e] = (uint32_t)(b < 0 ? 0 : b);
+                sv[10 * threadIdx.x + e] = ((uint32_t)i << 4) | ((uint32_t)sr << 2) | (uint32_t)sc;
+                ++e;
             }
-            const int b = find_block(row_ptr, col, j, l);
-            if (b < 0) atomicExch(status, ED_ERR_STATE);
-            key[10L * i + e] = (uint32_t)(b < 0 ? 0 : b);
-            val[10L * i + e] = ((uint32_t)i << 4) | ((uint32_t)sr << 2) | (uint32_t)sc;
-            ++e;
-        }
+    }
+    __syncthreads();
+    const int cnt = 10 * min(EG_T, n - i0);
+    for (int k = threadIdx.x; k < cnt; k += EG_T) {
+        key[10L * i0 + k] = sk[k];
+        val[10L * i0 + k] = sv[k];
+    }
 }
 
 // first entry of every block in the sorted keys: the entry at each key change
@@ -802,7 +814,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     const int ne = 10 * N;
     int nchunks, n_upper = 0;
     {
-        k_entries_gen<<<ed_div_up(N, 128), 128, 0, st>>>((const ushort4 *)graph->idx, N, ctx->row_ptr, ctx->col,
+        k_entries_gen<<<ed_div_up(N, EG_T), EG_T, 0, st>>>((const ushort4 *)graph->idx, N, ctx->row_ptr, ctx->col,
                                                           ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         int bits = 1;
