@@ -345,7 +345,7 @@ __device__ __forceinline__ void assemble1_half(const int4 ch, int c, const float
     if (lane < NSLOT) reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[24 * H + lane] = v[0];
 }
 
-__global__ void __launch_bounds__(128) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
+__global__ void __launch_bounds__(128, 6) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
                                                    int max_chunks, const float4 *__restrict__ geo,
                                                    const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
                                                    const float4 *__restrict__ rec1, const double *__restrict__ pose,
