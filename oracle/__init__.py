@@ -45,7 +45,9 @@ class _Problem(C.Structure):
                 ("W", C.c_int), ("H", C.c_int),
                 ("w_data", C.c_double), ("w_rot", C.c_double), ("w_reg", C.c_double),
                 ("w_r", C.c_double), ("w_p", C.c_double),
-                ("eps_d", C.c_float), ("cos_eps_n", C.c_float), ("prior", C.c_double * 6)]
+                ("eps_d", C.c_float), ("cos_eps_n", C.c_float), ("prior", C.c_double * 6),
+                ("NK", C.c_int), ("kp_pos", _dp), ("kp_idx", _ip), ("kp_w", _dp), ("kp_tgt", _dp),
+                ("w_corr", C.c_double)]
 
 
 class _Solver(C.Structure):
@@ -249,11 +251,36 @@ def calibrate_radius(pos, count, lo=None, hi=None, iters=40):
     return float(np.float32(lo))
 
 
+W_CORR = 10.0   # weight of the sparse correspondence term (Sec. III.B, reading R18)
+
+
+@dataclasses.dataclass
+class Keypoints:
+    """Sparse key correspondences (E_corr, Sec. II.E): model key points
+    pos [NK][4] (mm, model frame), their K nearest nodes and normalised
+    weights (the same rule as the model points), and 3D targets [NK][3] in the
+    camera frame of the new frame."""
+    pos: np.ndarray
+    idx: np.ndarray
+    w: np.ndarray
+    target: np.ndarray
+    w_corr: float = W_CORR
+
+
+def keypoints(pos, target, g, K=4, mode=0, sigma=1.0, w_corr=W_CORR) -> Keypoints:
+    """Key points skinned by the oracle's own nearest-node rule and weights."""
+    pos = _f(pos)
+    idx_k1, _ = knn(pos, g, K + 1)
+    w = skin_weights(pos, g, idx_k1, K, mode, sigma)
+    return Keypoints(pos=pos, idx=np.ascontiguousarray(idx_k1[:, :K]), w=w, target=_d(target), w_corr=w_corr)
+
+
 class Problem:
     """Holds the arrays of one registration problem (double geometry)."""
 
     def __init__(self, pos, nrm, graph: Graph, depth, nmap, intr, prior,
-                 weights=(W_DATA, W_ROT, W_REG, W_R, W_P), eps_d=EPS_D_MM, eps_n_deg=EPS_N_DEG, cos_eps_n=None):
+                 weights=(W_DATA, W_ROT, W_REG, W_R, W_P), eps_d=EPS_D_MM, eps_n_deg=EPS_N_DEG, cos_eps_n=None,
+                 keypoints: Optional["Keypoints"] = None):
         self.pos = _d(pos)
         self.nrm = _d(nrm)
         self.idx = _i(graph.idx)
@@ -279,6 +306,16 @@ class Problem:
         s.cos_eps_n = float(cos_eps_n if cos_eps_n is not None else cos_deg_f32(eps_n_deg))
         for t in range(6):
             s.prior[t] = float(prior[t])
+        self.kp = keypoints
+        if keypoints is not None and keypoints.pos.shape[0] > 0:
+            self.kp_pos = _d(keypoints.pos)
+            self.kp_idx = _i(keypoints.idx)
+            self.kp_w = _d(keypoints.w)
+            self.kp_tgt = _d(keypoints.target)
+            s.NK = self.kp_pos.shape[0]
+            s.kp_pos, s.kp_idx = _p(self.kp_pos, _dp), _p(self.kp_idx, _ip)
+            s.kp_w, s.kp_tgt = _p(self.kp_w, _dp), _p(self.kp_tgt, _dp)
+            s.w_corr = float(keypoints.w_corr)
         self.s = s
 
     @property
@@ -318,7 +355,7 @@ class NormalEq:
         self.C = np.zeros((m, 6, 12))
         self.Hpp = np.zeros((6, 6))
         self.g = np.zeros(12 * m + 6)
-        self.E = np.zeros(5)
+        self.E = np.zeros(6)   # data, rot, reg, rot prior, pos prior, correspondence
         nv = C.c_int(0)
         lib().or_normal_eq_export(self.h, _p(self.row_ptr, _ip), _p(self.col, _ip), _p(self.blk, _dp),
                                   _p(self.C, _dp), _p(self.Hpp, _dp), _p(self.g, _dp), _p(self.E, _dp),
@@ -377,7 +414,7 @@ class NormalEq:
 
 def energy(P: Problem, x, pose, pix_in=None):
     x, pose = _d(x), _d(pose)
-    terms = np.zeros(5)
+    terms = np.zeros(6)   # data, rot, reg, rot prior, pos prior, correspondence
     nv = C.c_int(0)
     pin = None if pix_in is None else _i(pix_in)
     E = lib().or_energy(C.byref(P.s), _p(x, _dp), _p(pose, _dp), _p(pin, _ip), _p(terms, _dp), C.byref(nv))

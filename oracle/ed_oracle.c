@@ -470,6 +470,14 @@ typedef struct {
     double w_data, w_rot, w_reg, w_r, w_p;
     float eps_d, cos_eps_n;
     double prior[6];
+    /* sparse key correspondences (E_corr): NK model key points with their own
+       skinning and 3D targets in the camera frame; weight w_corr */
+    int NK;
+    const double *kp_pos;  /* NK x 4 */
+    const int *kp_idx;     /* NK x K */
+    const double *kp_w;    /* NK x K */
+    const double *kp_tgt;  /* NK x 3 */
+    double w_corr;
 } or_problem;
 
 /*
@@ -506,6 +514,26 @@ void or_warp(const or_problem *P, const double *x, const double *pose, double *w
             if (spre) spre[3 * (size_t)i + r] = s[r];
         }
     }
+}
+
+/* Eq. (1) for key point k: warped position and the pre-pose sum s */
+static void warp_keypoint(const or_problem *P, const double *x, const double *R, const double *pose, int k,
+                          double *out, double *s)
+{
+    const double *v = P->kp_pos + 4 * (size_t)k;
+    s[0] = s[1] = s[2] = 0.0;
+    for (int q = 0; q < P->K; ++q) {
+        int j = P->kp_idx[(size_t)k * P->K + q];
+        double wj = P->kp_w[(size_t)k * P->K + q];
+        const double *gj = P->g + 4 * (size_t)j, *xj = x + 12 * (size_t)j;
+        double d[3] = {v[0] - gj[0], v[1] - gj[1], v[2] - gj[2]};
+        for (int r = 0; r < 3; ++r) {
+            const double *row = xj + 4 * r;
+            s[r] += wj * (row[0] * d[0] + row[1] * d[1] + row[2] * d[2] + gj[r] + row[3]);
+        }
+    }
+    mat3_vec(R, s, out);
+    for (int r = 0; r < 3; ++r) out[r] += pose[3 + r];
 }
 
 /* association of the FP64 warp: the FP32 rule applied to the rounded warp */
@@ -586,7 +614,7 @@ typedef struct {
     double *C;       /* m x 72: pose-node blocks d(pose) x d(x_j), row-major 6 x 12 */
     double Hpp[36];  /* pose block */
     double *g;       /* 12 m + 6: J^T r */
-    double E[5];     /* data, rot, reg, rot-prior, pos-prior energies */
+    double E[6];     /* data, rot, reg, rot-prior, pos-prior, correspondence energies */
     int n_valid;
 } or_normal_eq;
 
@@ -600,13 +628,17 @@ static int cmp_pair(const void *a, const void *b)
 static void pattern_build(const or_problem *P, or_normal_eq *Q)
 {
     int m = P->m, K = P->K;
-    size_t cap = (size_t)P->N * K * K + (size_t)m * (2 * P->KG + 1);
+    size_t cap = (size_t)(P->N + P->NK) * K * K + (size_t)m * (2 * P->KG + 1);
     int64_t *pr = (int64_t *)malloc(sizeof(int64_t) * (cap > 0 ? cap : 1));
     size_t n = 0;
     for (int i = 0; i < P->N; ++i)
         for (int a = 0; a < K; ++a)
             for (int b = 0; b < K; ++b)
                 pr[n++] = (int64_t)P->idx[(size_t)i * K + a] * m + P->idx[(size_t)i * K + b];
+    for (int i = 0; i < P->NK; ++i)
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b)
+                pr[n++] = (int64_t)P->kp_idx[(size_t)i * K + a] * m + P->kp_idx[(size_t)i * K + b];
     for (int j = 0; j < m; ++j) {
         pr[n++] = (int64_t)j * m + j;
         for (int s = 0; s < P->KG; ++s) {
@@ -669,6 +701,53 @@ static void outer12(double *blk, const double *a, const double *b, double s)
 }
 
 /*
+ * One point-to-plane residual r = sw n^T (v~ - target) of a point v with
+ * skinning (idx, w) and pre-pose sum s: its rows of J (w.r.t. [A_j | t_j] of
+ * its nodes and the pose) added to H = J^T J, g = J^T r, C and the pose block.
+ */
+static void add_plane_residual(or_normal_eq *Q, const or_problem *P, const double *R, const double *dR, double r,
+                               double sw, const double *nt, const double *v, const int *idx, const double *w,
+                               const double *s)
+{
+    const int K = P->K, m = P->m;
+    double a[8][12];
+    double nb[3] = {R[0] * nt[0] + R[3] * nt[1] + R[6] * nt[2], R[1] * nt[0] + R[4] * nt[1] + R[7] * nt[2],
+                    R[2] * nt[0] + R[5] * nt[1] + R[8] * nt[2]}; /* R^T n */
+    for (int k = 0; k < K; ++k) {
+        int j = idx[k];
+        double wj = w[k];
+        const double *gj = P->g + 4 * (size_t)j;
+        double dh[4] = {v[0] - gj[0], v[1] - gj[1], v[2] - gj[2], 1.0};
+        for (int rr = 0; rr < 3; ++rr)
+            for (int c = 0; c < 4; ++c)
+                a[k][4 * rr + c] = sw * wj * nb[rr] * dh[c];
+    }
+    double jp[6];
+    for (int t = 0; t < 3; ++t) {
+        double ds[3];
+        mat3_vec(dR + 9 * t, s, ds);
+        jp[t] = sw * (nt[0] * ds[0] + nt[1] * ds[1] + nt[2] * ds[2]);
+        jp[3 + t] = sw * nt[t];
+    }
+    double *gpose = Q->g + 12 * (size_t)m;
+    for (int k = 0; k < K; ++k) {
+        int j = idx[k];
+        for (int l = 0; l < K; ++l)
+            outer12(block_at(Q, j, idx[l]), a[k], a[l], 1.0);
+        for (int p = 0; p < 12; ++p)
+            Q->g[12 * (size_t)j + p] += r * a[k][p];
+        for (int t = 0; t < 6; ++t)
+            for (int p = 0; p < 12; ++p)
+                Q->C[72 * (size_t)j + 12 * t + p] += jp[t] * a[k][p];
+    }
+    for (int t = 0; t < 6; ++t) {
+        gpose[t] += r * jp[t];
+        for (int u = 0; u < 6; ++u)
+            Q->Hpp[6 * t + u] += jp[t] * jp[u];
+    }
+}
+
+/*
  * Linearise Eq. (3) at (x, pose): association (or the frozen pix[] when
  * pix_in != NULL), residuals, energy terms, H = J^T J and g = J^T r with every
  * residual carrying sqrt(w) of its term.  pix_out (optional) receives the
@@ -695,48 +774,30 @@ int or_linearize(const or_problem *P, const double *x, const double *pose, const
     double *gpose = Q->g + 12 * (size_t)m;
 
     /* data term */
-    double a[8][12];
     for (int i = 0; i < N; ++i) {
         if (pix[i] < 0) continue;
         double nt[3];
-        double r = data_residual(P, pix[i], wpos + 3 * (size_t)i, nt);
         double sw = sqrt(P->w_data);
-        r *= sw;
+        double r = sw * data_residual(P, pix[i], wpos + 3 * (size_t)i, nt);
         Q->E[0] += r * r;
         Q->n_valid++;
-        double nb[3] = {R[0] * nt[0] + R[3] * nt[1] + R[6] * nt[2], R[1] * nt[0] + R[4] * nt[1] + R[7] * nt[2],
-                        R[2] * nt[0] + R[5] * nt[1] + R[8] * nt[2]}; /* R^T n */
-        const double *v = P->pos + 4 * (size_t)i;
-        for (int k = 0; k < K; ++k) {
-            int j = P->idx[(size_t)i * K + k];
-            double wj = P->w[(size_t)i * K + k];
-            const double *gj = P->g + 4 * (size_t)j;
-            double dh[4] = {v[0] - gj[0], v[1] - gj[1], v[2] - gj[2], 1.0};
-            for (int rr = 0; rr < 3; ++rr)
-                for (int c = 0; c < 4; ++c)
-                    a[k][4 * rr + c] = sw * wj * nb[rr] * dh[c];
-        }
-        double jp[6];
-        for (int t = 0; t < 3; ++t) {
-            double ds[3];
-            mat3_vec(dR + 9 * t, spre + 3 * (size_t)i, ds);
-            jp[t] = sw * (nt[0] * ds[0] + nt[1] * ds[1] + nt[2] * ds[2]);
-            jp[3 + t] = sw * nt[t];
-        }
-        for (int k = 0; k < K; ++k) {
-            int j = P->idx[(size_t)i * K + k];
-            for (int l = 0; l < K; ++l)
-                outer12(block_at(Q, j, P->idx[(size_t)i * K + l]), a[k], a[l], 1.0);
-            for (int p = 0; p < 12; ++p)
-                Q->g[12 * (size_t)j + p] += r * a[k][p];
-            for (int t = 0; t < 6; ++t)
-                for (int p = 0; p < 12; ++p)
-                    Q->C[72 * (size_t)j + 12 * t + p] += jp[t] * a[k][p];
-        }
-        for (int t = 0; t < 6; ++t) {
-            gpose[t] += r * jp[t];
-            for (int u = 0; u < 6; ++u)
-                Q->Hpp[6 * t + u] += jp[t] * jp[u];
+        add_plane_residual(Q, P, R, dR, r, sw, nt, P->pos + 4 * (size_t)i, P->idx + (size_t)i * K,
+                           P->w + (size_t)i * K, spre + 3 * (size_t)i);
+    }
+
+    /* E_corr: the three components of sqrt(w_corr) (v~_k - V_k) of every key
+       point, each the residual of the plane through V_k normal to a camera axis */
+    for (int k = 0; k < P->NK; ++k) {
+        double vt[3], sk[3];
+        warp_keypoint(P, x, R, pose, k, vt, sk);
+        double sw = sqrt(P->w_corr);
+        for (int c = 0; c < 3; ++c) {
+            double nt[3] = {0.0, 0.0, 0.0};
+            nt[c] = 1.0;
+            double r = sw * (vt[c] - P->kp_tgt[3 * (size_t)k + c]);
+            Q->E[5] += r * r;
+            add_plane_residual(Q, P, R, dR, r, sw, nt, P->kp_pos + 4 * (size_t)k, P->kp_idx + (size_t)k * K,
+                               P->kp_w + (size_t)k * K, sk);
         }
     }
 
@@ -799,7 +860,7 @@ double or_energy(const or_problem *P, const double *x, const double *pose, const
 {
     or_normal_eq Q;
     or_linearize(P, x, pose, pix_in, NULL, &Q);
-    double E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4];
+    double E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4] + Q.E[5];
     if (terms) memcpy(terms, Q.E, sizeof(Q.E));
     if (n_valid) *n_valid = Q.n_valid;
     or_normal_eq_free(&Q);
@@ -817,7 +878,7 @@ int or_residual_count(const or_problem *P, const int *pix)
     for (int i = 0; i < P->N; ++i) n += pix[i] >= 0;
     int ne = 0;
     for (int j = 0; j < P->m * P->KG; ++j) ne += P->nbr[j] >= 0;
-    return n + 6 * P->m + 3 * ne + 6;
+    return n + 3 * P->NK + 6 * P->m + 3 * ne + 6;
 }
 
 /*
@@ -865,6 +926,37 @@ void or_residuals(const or_problem *P, const double *x, const double *pose, cons
             }
         }
         row++;
+    }
+    /* E_corr rows: sqrt(w_corr) (v~_k - V_k), component c */
+    double swc = sqrt(P->w_corr);
+    for (int k = 0; k < P->NK; ++k) {
+        double vt[3], sk[3];
+        warp_keypoint(P, x, R, pose, k, vt, sk);
+        const double *v = P->kp_pos + 4 * (size_t)k;
+        for (int c = 0; c < 3; ++c) {
+            res[row] = swc * (vt[c] - P->kp_tgt[3 * (size_t)k + c]);
+            if (J) {
+                double *Jr = J + (size_t)row * ncol;
+                memset(Jr, 0, sizeof(double) * ncol);
+                /* d v~_c / d A_j[r][c'] = w_j R[c][r] (v - g_j)_c' ; d v~_c / d t_j[r] = w_j R[c][r] */
+                for (int q = 0; q < K; ++q) {
+                    int j = P->kp_idx[(size_t)k * K + q];
+                    double wj = P->kp_w[(size_t)k * K + q];
+                    const double *gj = P->g + 4 * (size_t)j;
+                    double dh[4] = {v[0] - gj[0], v[1] - gj[1], v[2] - gj[2], 1.0};
+                    for (int r = 0; r < 3; ++r)
+                        for (int cc = 0; cc < 4; ++cc)
+                            Jr[12 * j + 4 * r + cc] += swc * wj * R[3 * c + r] * dh[cc];
+                }
+                for (int t = 0; t < 3; ++t) {
+                    double ds[3];
+                    mat3_vec(dR + 9 * t, sk, ds);
+                    Jr[12 * m + t] = swc * ds[c];
+                }
+                Jr[12 * m + 3 + c] = swc;
+            }
+            row++;
+        }
     }
     double swr = sqrt(P->w_rot);
     for (int j = 0; j < m; ++j) {
@@ -1126,7 +1218,7 @@ int or_gn_solve(const or_problem *P, const or_solver *S, double *x, double *pose
     for (int it = 0; it < S->n_gn; ++it) {
         or_normal_eq Q;
         or_linearize(P, x, pose, NULL, NULL, &Q);
-        double E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4];
+        double E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4] + Q.E[5];
         if (S->lm_accept && it > 0 && E > Eprev) {
             /* reject the last step */
             or_normal_eq_free(&Q);
@@ -1303,7 +1395,7 @@ void or_normal_eq_export(const or_normal_eq *Q, int *row_ptr, int *col, double *
     if (C) memcpy(C, Q->C, sizeof(double) * 72 * (size_t)m);
     if (Hpp) memcpy(Hpp, Q->Hpp, sizeof(double) * 36);
     if (g) memcpy(g, Q->g, sizeof(double) * (12 * (size_t)m + 6));
-    if (E) memcpy(E, Q->E, sizeof(double) * 5);
+    if (E) memcpy(E, Q->E, sizeof(double) * 6);
     if (n_valid) *n_valid = Q->n_valid;
 }
 int or_pcg_eq(const or_normal_eq *Q, const double *b, int n_iter, double tol, double jitter, double *d, int *iters,

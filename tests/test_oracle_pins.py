@@ -496,3 +496,97 @@ def test_fuse_zbuffer_lift_delete_conservation():
     kept = [i for i in range(n) if i not in deleted]
     assert np.array_equal(to[:len(kept)], np.where(np.isin(kept, list(registered)), 25, t[kept]))
     assert np.all(po[len(kept):, 3] == 1.0) and np.all(to[len(kept):] == 25)
+
+
+# ----------------------------------------------------------------------------
+# sparse key correspondences, E_corr (Sec. II.E "Correspondence", w_corr = 10)
+# ----------------------------------------------------------------------------
+
+def _keypoint_problem(seed=0, nk=40, shift=None):
+    """The small problem plus nk key points drawn from the model, their targets
+    the key points themselves moved by `shift` (or by seeded noise)."""
+    s, G, P0 = _small_problem()
+    rng = np.random.default_rng(100 + seed)
+    sel = rng.choice(s.N, nk, replace=False)
+    kp = s.model_pos[sel].astype(np.float32)
+    d = rng.normal(0, 0.5, (nk, 3)) if shift is None else np.broadcast_to(np.asarray(shift, float), (nk, 3))
+    tgt = kp[:, :3].astype(np.float64) + d
+    K = oracle.keypoints(kp, tgt, G.g, K=4, mode=0, sigma=s.sigma)
+    nm = oracle.normals(s.tgt_depth, s.intr, s.cfg.normal_half_width)
+    P = oracle.Problem(s.model_pos, s.model_nrm, G, s.tgt_depth, nm, s.intr, s.pose_prior, keypoints=K)
+    return s, G, P, d
+
+
+def test_corr_energy_closed_form_at_identity():
+    s, G, P, d = _keypoint_problem(shift=None)
+    zero_pose = np.zeros(6)
+    # identity warp and pose: the warped key point is the key point, so
+    # E_corr = w_corr sum_k |target_k - p_k|^2
+    _, terms, _ = oracle.energy(P, P.identity_x(), zero_pose)
+    assert terms[5] == pytest.approx(oracle.W_CORR * float((d ** 2).sum()), rel=1e-12)
+    # the key points at their targets: E_corr vanishes
+    s2, G2, P2, d2 = _keypoint_problem(shift=(0.0, 0.0, 0.0))
+    _, terms2, _ = oracle.energy(P2, P2.identity_x(), zero_pose)
+    assert terms2[5] < 1e-20     # the identity warp up to the rounding of the normalised weights
+    # a pure translation T of the pose moves every key point by T
+    T = np.array([0.0, 0.0, 0.0, 0.7, -0.4, 1.1])
+    _, terms3, _ = oracle.energy(P2, P2.identity_x(), T)
+    assert terms3[5] == pytest.approx(oracle.W_CORR * 40 * float((T[3:] ** 2).sum()), rel=1e-12)
+
+
+def test_corr_jacobian_and_normal_equations():
+    s, G, P, d = _keypoint_problem(seed=1)
+    x, pose = _perturbed(P, 4)
+    Q = oracle.NormalEq(P, x, pose)
+    r, J = oracle.residuals(P, x, pose, Q.pix, jacobian=True)
+    nv = int((Q.pix >= 0).sum())
+    kr = slice(nv, nv + 3 * 40)                      # the key-point rows
+    assert float(r[kr] @ r[kr]) == pytest.approx(Q.E[5], rel=1e-12)
+    # explicit Jacobian rows of the key points against central differences
+    rng = np.random.default_rng(6)
+    nodes = np.unique(P.kp_idx)
+    cols = [12 * j + c for j in rng.choice(nodes, 6, replace=False) for c in range(12)]
+    cols += list(range(12 * P.m, 12 * P.m + 6))
+    flat = np.concatenate([x.ravel(), pose])
+    for c in cols:
+        h = 1e-6 * max(1.0, abs(flat[c]))
+        fp, fm = flat.copy(), flat.copy()
+        fp[c] += h
+        fm[c] -= h
+        rp = oracle.residuals(P, fp[:-6].reshape(P.m, 12), fp[-6:], Q.pix)[kr]
+        rm = oracle.residuals(P, fm[:-6].reshape(P.m, 12), fm[-6:], Q.pix)[kr]
+        fd = (rp - rm) / (2 * h)
+        assert np.abs(fd - J[kr, c]).max() <= 1e-6 * max(1.0, np.abs(J[kr, c]).max()), c
+    # the assembled normal equations still equal J^T J and J^T r
+    H = Q.dense()
+    assert np.abs(H - J.T @ J).max() <= 1e-10 * np.abs(J.T @ J).max()
+    assert np.abs(Q.g - J.T @ r).max() <= 1e-10 * np.abs(J.T @ r).max()
+    # and E_corr shows in the gradient: 2 J^T r against the energy's differences
+    grad = 2.0 * Q.g
+    for c in cols[:20] + cols[-6:]:
+        h = 1e-5 * max(1.0, abs(flat[c]))
+        fp, fm = flat.copy(), flat.copy()
+        fp[c] += h
+        fm[c] -= h
+        Ep = oracle.energy(P, fp[:-6].reshape(P.m, 12), fp[-6:], Q.pix)[0]
+        Em = oracle.energy(P, fm[:-6].reshape(P.m, 12), fm[-6:], Q.pix)[0]
+        assert abs((Ep - Em) / (2 * h) - grad[c]) <= 1e-5 * max(1.0, abs(grad[c])), c
+
+
+def test_rigid_motion_recovered_with_consistent_keypoints():
+    pr = X.rigid_problem()
+    pos = pr["pos"]
+    g, sp = X.grid_nodes(pos[:, :3], 4, 3)
+    G = oracle.build_graph(pos.astype(np.float32), nodes=g, K=4, KG=4, mode=0, sigma=sp)
+    R, _ = oracle.rotation(pr["pose"])
+    rng = np.random.default_rng(3)
+    sel = rng.choice(pos.shape[0], 30, replace=False)
+    kp = pos[sel].astype(np.float32)
+    tgt = kp[:, :3].astype(np.float64) @ R.T + pr["pose"][3:]     # the true rigid motion of the key points
+    K = oracle.keypoints(kp, tgt, G.g, K=4, mode=0, sigma=sp)
+    P = oracle.Problem(pos, pr["nrm"], G, pr["depth"], pr["nmap"], pr["intr"], pr["pose"], keypoints=K)
+    pose0 = pr["pose"] + np.array([0.004, -0.003, 0.005, 0.3, -0.2, 0.25])
+    x, pose, hist, st = oracle.gn_solve(P, P.identity_x(), pose0, 12, 0, dense=True)
+    assert st == 0
+    assert np.abs(pose - pr["pose"]).max() < 1e-9
+    assert np.abs(x - P.identity_x()).max() < 1e-9
