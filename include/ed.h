@@ -139,6 +139,23 @@ typedef struct ed_graph {
 ed_status ed_build_graph(ed_context *ctx, const float *pos, const float *nrm, int n_points, int m_in,
                          const ed_graph_params *params, const ed_graph *graph, cudaStream_t stream);
 
+/*
+ * Sparse key correspondences (Sec. II.E "Correspondence"): the term
+ * w_corr sum_k |v~_k - V_k|^2 over n_keypoints model key points kp_pos
+ * (device [n][4], model frame, within the model's bounding box) warped by
+ * Eq. (1) with the global pose, and their 3D targets kp_target (device
+ * [n][4], camera frame of the new frame; w = 0 disables a key point).  The
+ * paper's weight is w_corr = 10.  Call before ed_build_graph: the build then
+ * skins the key points like model points (three rows per key point, after
+ * the model points, so the graph's idx and weights must hold n_points +
+ * 3 n_keypoints rows and max_points must cover them), and every later
+ * ed_gn_step / ed_energy / ed_energy_grad includes the term (its energy in
+ * ed_stats.e_corr and energy_out[6]).  The pointers are retained until the
+ * next call; n_keypoints = 0 removes the term.
+ */
+ed_status ed_set_keypoints(ed_context *ctx, const float *kp_pos, const float *kp_target, int n_keypoints,
+                           float w_corr);
+
 /* Host-side sizes of the graph built last (host out; NULL entries skipped). */
 ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_chunks);
 
@@ -171,6 +188,7 @@ typedef struct ed_stats {
     int pcg_iters;
     int status;            /* ed_status of the device-side checks */
     int reserved;
+    double e_corr;         /* sparse key-correspondence energy (0 without key points) */
 } ed_stats;
 
 /*
@@ -264,7 +282,8 @@ ed_status ed_fuse(ed_context *ctx, const float *pos, const float *nrm, const flo
 /*
  * Energy of Eq. (3) at (x, pose) with the graph built last (forward of the
  * differentiable warp + energy).  Association is recomputed and stored in
- * the context for ed_energy_grad.  With Gaussian weights (the graph's
+ * the context for ed_energy_grad.  energy_out has 7 entries when key points
+ * are set (E_corr last) and 6 otherwise.  With Gaussian weights (the graph's
  * weight_mode) the skinning weights of Eq. (1) are recomputed from the node
  * indices instead of read from the graph (the same values, bit for bit), here
  * and in ed_energy_grad.  energy_out: device double[6] = (total,

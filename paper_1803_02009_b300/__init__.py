@@ -72,7 +72,7 @@ class Stats(C.Structure):
     _fields_ = [("energy", C.c_double), ("e_data", C.c_double), ("e_rot", C.c_double), ("e_reg", C.c_double),
                 ("e_rot_prior", C.c_double), ("e_pos_prior", C.c_double), ("pcg_res0", C.c_double),
                 ("pcg_res", C.c_double), ("n_valid", C.c_int), ("pcg_iters", C.c_int), ("status", C.c_int),
-                ("reserved", C.c_int)]
+                ("reserved", C.c_int), ("e_corr", C.c_double)]
 
 
 STATS_BYTES = C.sizeof(Stats)
@@ -109,6 +109,7 @@ _SIGS = {
     "ed_energy_grad": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, C.c_float, _vp, _vp, _vp],
     "ed_set_timing": [_vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)],
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
+    "ed_set_keypoints": [_vp, _vp, _vp, C.c_int, C.c_float],
     "ed_batch_query_workspace": [_vp, C.c_int, C.POINTER(C.c_size_t)],
     "ed_batch_create": [_vp, C.c_int, _vp, C.c_size_t, C.POINTER(_vp)],
     "ed_batch_destroy": [_vp],
@@ -245,6 +246,8 @@ class Context:
         self.h = h
         self.graph: Optional[Graph] = None
         self._keep = []
+        self.n_keypoints = 0
+        self._kp = None
 
     def __del__(self):
         try:
@@ -262,14 +265,27 @@ class Context:
                                                               _ptr(nmap), _stream(stream)))
         return nmap
 
+    def set_keypoints(self, kp_pos=None, kp_target=None, w_corr=10.0):
+        """Sparse key correspondences (E_corr): model key points kp_pos [n][4]
+        and their camera-frame targets kp_target [n][4] (w = 0 disables one);
+        takes effect at the next build_graph.  None removes the term."""
+        if kp_pos is None or kp_pos.shape[0] == 0:
+            _check("ed_set_keypoints", lib().ed_set_keypoints(self.h, None, None, 0, 0.0))
+            self.n_keypoints, self._kp = 0, None
+            return
+        _check("ed_set_keypoints", lib().ed_set_keypoints(self.h, _ptr(kp_pos), _ptr(kp_target),
+                                                          int(kp_pos.shape[0]), float(w_corr)))
+        self.n_keypoints, self._kp = int(kp_pos.shape[0]), (kp_pos, kp_target)
+
     def build_graph(self, pos, nrm, nodes=None, node_radius=0.0, max_nodes=0, k_graph=4,
                     weight_mode=ED_WEIGHT_GAUSSIAN, sigma=1.0, search_cell=0.0, stream=None) -> Graph:
         dev = pos.device
         N = pos.shape[0]
+        rows = N + 3 * self.n_keypoints      # the key points' rows follow the model points
         cap = int(self.limits.max_nodes)
         g = Graph(nodes=torch.zeros((cap, 4), dtype=torch.float32, device=dev),
-                  idx=torch.empty((N, 4), dtype=torch.int16, device=dev),
-                  weights=torch.empty((N, 4), dtype=torch.float32, device=dev),
+                  idx=torch.empty((rows, 4), dtype=torch.int16, device=dev),
+                  weights=torch.empty((rows, 4), dtype=torch.float32, device=dev),
                   nbr=torch.empty((cap, k_graph), dtype=torch.int32, device=dev),
                   counts=torch.zeros(4, dtype=torch.int32, device=dev))
         m_in = 0
@@ -360,7 +376,8 @@ class Context:
         return self._tm_rec.value
 
     def energy(self, frame: Frame, params: SolverParams, x, pose, out=None, stream=None):
-        e = out if out is not None else torch.empty(6, dtype=torch.float64, device="cuda")
+        e = out if out is not None else torch.empty(7 if self.n_keypoints else 6, dtype=torch.float64,
+                                                    device="cuda")
         p = params.c()
         _check("ed_energy", lib().ed_energy(self.h, C.byref(frame), C.byref(p), _ptr(x), _ptr(pose), _ptr(e),
                                             _stream(stream)))

@@ -105,6 +105,8 @@ size_t carve(ed_context *c, char *base)
     c->scan_state = k.take<unsigned long long>(c->scan_state_len);
     c->scan_ticket = k.take<unsigned>(64);
     c->gpts = k.take<float4>(2 * N);
+    c->comb_pos = k.take<float4>(N);
+    c->comb_nrm = k.take<float4>(N);
     return k.off + 256;
 }
 
@@ -200,6 +202,21 @@ extern "C" ed_status ed_set_debug(ed_context *ctx, float *warped_pos, float *war
 static unsigned long long g_launches = 0;
 void ed_note_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
 void ed_note_launches(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+
+extern "C" ed_status ed_set_keypoints(ed_context *ctx, const float *kp_pos, const float *kp_target, int n_keypoints,
+                                      float w_corr)
+{
+    if (!ctx || n_keypoints < 0) return ED_ERR_ARG;
+    if (n_keypoints > 0 && (!kp_pos || !kp_target || ((uintptr_t)kp_pos & 15) || ((uintptr_t)kp_target & 15) ||
+                            !(w_corr >= 0.f)))
+        return ED_ERR_ARG;
+    ctx->kp_pos = n_keypoints > 0 ? (const float4 *)kp_pos : nullptr;
+    ctx->kp_tgt = n_keypoints > 0 ? (const float4 *)kp_target : nullptr;
+    ctx->n_kp = n_keypoints;
+    ctx->w_corr = w_corr;
+    ctx->have_graph = 0;   // the point set changes: build the graph again
+    return ED_OK;
+}
 
 extern "C" ed_status ed_launch_count(unsigned long long *count)
 {

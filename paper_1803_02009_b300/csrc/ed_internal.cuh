@@ -135,9 +135,17 @@ struct ed_context {
     unsigned *scan_ticket;   // tile ticket counter (never reset; host mirror below)
     unsigned scan_ticket_base, scan_epoch;
     float4 *gpts;            // [N] gradient per-point records (x2)
+    float4 *comb_pos;        // [N] model points followed by the key-point rows (when key points are set)
+    float4 *comb_nrm;
 
     // ---- graph state (host) ----
     int have_graph;
+    // sparse key correspondences (ed_set_keypoints); rows n_model .. N of the
+    // point set are the key points, three rows each
+    const float4 *kp_pos, *kp_tgt;
+    int n_kp;
+    float w_corr;
+    int n_model;
     const float *pos;
     const float *nrm;
     int N;

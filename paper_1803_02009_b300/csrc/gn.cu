@@ -21,6 +21,9 @@ struct PointArgs {
     int recompute_w;   // Gaussian weights recomputed from the node indices (energy / gradient path)
     int m;
     float sigma;
+    int n_model;       // rows >= n_model: key points, three rows each (E_corr)
+    const float4 *kp_tgt;
+    float sw_corr;
     int *pix;          // association (written in STEP / ENERGY, read in GRAD)
     float4 *rec0, *rec1;
     float2 *part;      // [ED_K1_PART][pstride] float-float partials, component-major
@@ -35,40 +38,65 @@ struct PointArgs {
 __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
 {
     __shared__ ed_pose_f P;
-    __shared__ float red[ED_K1_THREADS / 32][30];
+    __shared__ float red[ED_K1_THREADS / 32][31];
     if (threadIdx.x == 0) ed_pose_eval(a.pose, P);
     __syncthreads();
-    float acc[30];
+    // 0 E_data, 1 count, 2..22 pose block, 23..28 pose gradient, 29 non-finite, 30 E_corr
+    float acc[31];
 #pragma unroll
-    for (int k = 0; k < 30; ++k) acc[k] = 0.f;
+    for (int k = 0; k < 31; ++k) acc[k] = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const float4 p = a.pos[i], nr = a.nrm[i];
         const ushort4 id = a.idx[i];
         const float4 wi = a.recompute_w ? ed_gauss_weights(p, id, a.g, a.m, a.sigma) : a.w[i];
         const ed_warped W = ed_warp_point(p, nr, id, wi, a.g, a.x4, P.R, P.T);
-        int q;
-        if (a.mode == PASS_GRAD) q = a.pix[i];
-        else {
-            q = ed_associate(W, a.depth, a.nmap, a.K, a.eps2, a.cos_eps_n);
-            a.pix[i] = q;
-            if (a.dbg_pix) {
-                a.dbg_pix[i] = q;
-                reinterpret_cast<float4 *>(a.dbg_wpos)[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
-                reinterpret_cast<float4 *>(a.dbg_wnrm)[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
+        const bool kp = i >= a.n_model;
+        // the plane of the residual: target point G and normal tn (the pixel's
+        // back-projection and normal, or a key point's target and a camera axis)
+        bool valid;
+        float G[3];
+        float4 tn;
+        float sw;
+        if (!kp) {
+            int q;
+            if (a.mode == PASS_GRAD) q = a.pix[i];
+            else {
+                q = ed_associate(W, a.depth, a.nmap, a.K, a.eps2, a.cos_eps_n);
+                a.pix[i] = q;
+                if (a.dbg_pix) {
+                    a.dbg_pix[i] = q;
+                    reinterpret_cast<float4 *>(a.dbg_wpos)[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
+                    reinterpret_cast<float4 *>(a.dbg_wnrm)[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
+                }
             }
+            valid = q >= 0;
+            if (valid) {
+                const int u = q % a.K.width, v = q / a.K.width;
+                const float D = __ldg(a.depth + q);
+                tn = __ldg(a.nmap + q);
+                G[0] = ((float)u - a.K.cx) * D / a.K.fx;
+                G[1] = ((float)v - a.K.cy) * D / a.K.fy;
+                G[2] = D;
+            }
+            sw = a.sw;
+        } else {
+            const int t = i - a.n_model, c = t % 3;
+            const float4 T = __ldg(a.kp_tgt + t / 3);
+            valid = T.w != 0.f;
+            G[0] = T.x;
+            G[1] = T.y;
+            G[2] = T.z;
+            tn = make_float4(c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f, 1.f);
+            sw = a.sw_corr;
         }
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        if (q >= 0) {
-            const int u = q % a.K.width, v = q / a.K.width;
-            const float D = __ldg(a.depth + q);
-            const float4 tn = __ldg(a.nmap + q);
-            const float Gx = ((float)u - a.K.cx) * D / a.K.fx, Gy = ((float)v - a.K.cy) * D / a.K.fy;
-            const float r = a.sw * (tn.x * (W.v.x - Gx) + tn.y * (W.v.y - Gy) + tn.z * (W.v.z - D));
+        if (valid) {
+            const float r = sw * (tn.x * (W.v.x - G[0]) + tn.y * (W.v.y - G[1]) + tn.z * (W.v.z - G[2]));
             const float *R = P.R;
-            // R^T n(u), scaled by sqrt(w_data)
-            const float b0 = a.sw * (R[0] * tn.x + R[3] * tn.y + R[6] * tn.z);
-            const float b1 = a.sw * (R[1] * tn.x + R[4] * tn.y + R[7] * tn.z);
-            const float b2 = a.sw * (R[2] * tn.x + R[5] * tn.y + R[8] * tn.z);
+            // R^T n(u), scaled by the residual's sqrt(w)
+            const float b0 = sw * (R[0] * tn.x + R[3] * tn.y + R[6] * tn.z);
+            const float b1 = sw * (R[1] * tn.x + R[4] * tn.y + R[7] * tn.z);
+            const float b2 = sw * (R[2] * tn.x + R[5] * tn.y + R[8] * tn.z);
             float jp[6];
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
@@ -76,15 +104,19 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
                 const float e0 = d[0] * W.s.x + d[1] * W.s.y + d[2] * W.s.z;
                 const float e1 = d[3] * W.s.x + d[4] * W.s.y + d[5] * W.s.z;
                 const float e2 = d[6] * W.s.x + d[7] * W.s.y + d[8] * W.s.z;
-                jp[t] = a.sw * (tn.x * e0 + tn.y * e1 + tn.z * e2);
+                jp[t] = sw * (tn.x * e0 + tn.y * e1 + tn.z * e2);
             }
-            jp[3] = a.sw * tn.x;
-            jp[4] = a.sw * tn.y;
-            jp[5] = a.sw * tn.z;
+            jp[3] = sw * tn.x;
+            jp[4] = sw * tn.y;
+            jp[5] = sw * tn.z;
             r0 = make_float4(b0, b1, b2, r);
             r1 = make_float4(jp[0], jp[1], jp[2], 1.0f);
-            acc[0] += r * r;
-            acc[1] += 1.0f;
+            if (kp) {
+                acc[30] += r * r;
+            } else {
+                acc[0] += r * r;
+                acc[1] += 1.0f;
+            }
             int k = 2;
 #pragma unroll
             for (int t = 0; t < 6; ++t)
@@ -102,14 +134,14 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
     // block reduction: warp shuffles (float), then the warps in order (float-float)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 30; ++k) {
+    for (int k = 0; k < 31; ++k) {
         float v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[wid][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 30) {
+    if (threadIdx.x < 31) {
         float2 s = make_float2(0.f, 0.f);
         for (int w = 0; w < ED_K1_THREADS / 32; ++w) s = ed_ff_add1(s, red[w][threadIdx.x]);
         a.part[(size_t)threadIdx.x * a.pstride + blockIdx.x] = s;
@@ -149,6 +181,9 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.recompute_w = mode != PASS_STEP && ctx->weight_mode == ED_WEIGHT_GAUSSIAN;
     a.m = ctx->m;
     a.sigma = ctx->sigma;
+    a.n_model = ctx->n_kp > 0 ? ctx->n_model : ctx->N;
+    a.kp_tgt = ctx->kp_tgt;
+    a.sw_corr = sqrtf(ctx->w_corr);
     a.pix = ctx->pix;
     a.rec0 = mode == PASS_GRAD ? ctx->gpts : ctx->rec0;
     a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : ctx->rec1;
@@ -683,15 +718,15 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
 
 #define PF_BATCH 20   // loads in flight per lane (>= 4 * 148 / 32 partials: one round at 640x480)
 
-// sums of the point-pass partials (component k by warp k < 30, lanes striding
+// sums of the point-pass partials (component k by warp k < 31, lanes striding
 // the CTAs, PF_BATCH loads in flight) and of the node energies (all threads,
-// then one warp over the warps); s[0..29], ne[0..1]
+// then one warp over the warps); s[0..30], ne[0..1]
 __device__ __forceinline__ void pf_sums(const float2 *__restrict__ part, int nparts, int pstride,
                                         const float2 *__restrict__ node_energy, int m, double *s, double *ne,
                                         float2 (*wsum)[2])
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (w < 30) {
+    if (w < 31) {
         const float2 *src = part + (size_t)w * pstride;
         float2 v = make_float2(0.f, 0.f);
         for (int c0 = 0; c0 < nparts; c0 += 32 * PF_BATCH) {
@@ -811,7 +846,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restr
         }
     } else if (t == 32) {
         const double Er = pri[0] + pri[1] + pri[2], Ep = pri[3] + pri[4] + pri[5];
-        const double E = s[0] + ne[0] + ne[1] + Er + Ep;
+        const double E = s[0] + ne[0] + ne[1] + Er + Ep + s[30];
         if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
         dmisc[0] = E;
         dmisc[1] = s[0];
@@ -820,7 +855,9 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restr
         dmisc[4] = Er;
         dmisc[5] = Ep;
         dmisc[6] = s[1];
+        dmisc[7] = s[30];
         if (stats) {
+            stats->e_corr = s[30];
             stats->energy = E;
             stats->e_data = s[0];
             stats->e_rot = ne[0];
@@ -1009,7 +1046,7 @@ __global__ void k_node_energy(int m, int kg, const int *__restrict__ nbr, const 
 __global__ void __launch_bounds__(PF_THREADS) k_energy_final(const float2 *__restrict__ part, int nparts, int pstride,
                                                               const float2 *__restrict__ node_energy, int m,
                                                               const double *__restrict__ pose, ed_solver_params prm,
-                                                              double *__restrict__ out)
+                                                              int has_corr, double *__restrict__ out)
 {
     __shared__ double s[32];
     __shared__ double ne[2];
@@ -1022,12 +1059,13 @@ __global__ void __launch_bounds__(PF_THREADS) k_energy_final(const float2 *__res
             if (q < 3) Er += prm.w_r * d * d;
             else Ep += prm.w_p * d * d;
         }
-        out[0] = s[0] + ne[0] + ne[1] + Er + Ep;
+        out[0] = s[0] + ne[0] + ne[1] + Er + Ep + s[30];
         out[1] = s[0];
         out[2] = ne[0];
         out[3] = ne[1];
         out[4] = Er;
         out[5] = Ep;
+        if (has_corr) out[6] = s[30];
     }
 }
 
@@ -1043,7 +1081,7 @@ extern "C" ed_status ed_energy(ed_context *ctx, const ed_frame *fr, const ed_sol
                                                           (const float4 *)ctx->graph.nodes, (const float4 *)x,
                                                           prm->w_rot, prm->w_reg, ctx->node_energy); ed_note_launch();
     k_energy_final<<<1, PF_THREADS, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, ctx->node_energy, ctx->m,
-                                              pose, *prm, energy_out); ed_note_launch();
+                                              pose, *prm, ctx->n_kp > 0, energy_out); ed_note_launch();
     ED_LAUNCH_CHECK();
     ctx->have_energy = 1;
     return ED_OK;

@@ -655,6 +655,17 @@ __global__ void k_entry_geo(int ne, const uint32_t *__restrict__ key, const uint
 
 // ---------------------------------------------------------------------------
 
+// the three rows of every key point after the model points
+__global__ void k_kp_expand(const float4 *__restrict__ kp, int nk, int n_model, float4 *__restrict__ pos,
+                            float4 *__restrict__ nrm)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nk) return;
+    const float4 p = kp[t / 3];
+    pos[n_model + t] = make_float4(p.x, p.y, p.z, 0.f);
+    nrm[n_model + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 static ed_status read_misc(ed_context *ctx, int *host, cudaStream_t st)
 {
     ED_CUDA_TRY(cudaMemcpyAsync(host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
@@ -681,8 +692,18 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     ctx->have_graph = 0;
     ctx->have_system = 0;
     ctx->have_energy = 0;
-    const int N = n_points;
+    const int N = n_points;                     // model points: the bounding box and the nodes
+    const int NT = n_points + 3 * ctx->n_kp;    // model points and key-point rows: skinning, pattern, entries
+    if (NT > ctx->lim.max_points) return ED_ERR_CAPACITY;
     const float4 *P4 = (const float4 *)pos;
+    const float4 *PT = P4;                      // the extended point set
+    if (ctx->n_kp > 0) {
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->comb_pos, pos, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->comb_nrm, nrm, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+        k_kp_expand<<<ed_div_up(3 * ctx->n_kp, 256), 256, 0, st>>>(ctx->kp_pos, ctx->n_kp, N, ctx->comb_pos,
+                                                                   ctx->comb_nrm); ed_note_launch();
+        PT = ctx->comb_pos;
+    }
     float4 *G4 = (float4 *)graph->nodes;
     int hm[MI_COUNT];
     ed_status s;
@@ -780,7 +801,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
         k_kcell_fill<<<ed_div_up(m, 256), 256, 0, st>>>(m, ctx->kcell_start, ctx->kcell_cnt, cell_of_node,
                                                          ctx->kcell_nodes); ed_note_launch();
-        k_knn<<<ed_div_up(N, 128), 128, 0, st>>>(P4, N, G4, m, ctx->misc, ctx->fmisc, ctx->kcell_start,
+        k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m, ctx->misc, ctx->fmisc, ctx->kcell_start,
                                                   ctx->kcell_nodes, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
         k_node_graph<<<ed_div_up(m, 4), 128, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
@@ -792,7 +813,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     int nnzb;
     {
         ED_CUDA_TRY(cudaMemsetAsync(ctx->bitmap, 0, sizeof(uint32_t) * (size_t)m * words, st));
-        k_pairs_points<<<ed_div_up(N, 256), 256, 0, st>>>((const ushort4 *)graph->idx, N, ctx->bitmap, words); ed_note_launch();
+        k_pairs_points<<<ed_div_up(NT, 256), 256, 0, st>>>((const ushort4 *)graph->idx, NT, ctx->bitmap, words); ed_note_launch();
         k_pairs_graph<<<ed_div_up(m, 256), 256, 0, st>>>(graph->nbr, m, prm->k_graph, ctx->bitmap, words); ed_note_launch();
         k_row_count<<<ed_div_up(m, 128), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
@@ -811,10 +832,10 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     }
 
     // ---- per-block point lists (stable: point order inside each block) ----
-    const int ne = 10 * N;
+    const int ne = 10 * NT;
     int nchunks, n_upper = 0;
     {
-        k_entries_gen<<<ed_div_up(N, EG_T), EG_T, 0, st>>>((const ushort4 *)graph->idx, N, ctx->row_ptr, ctx->col,
+        k_entries_gen<<<ed_div_up(NT, EG_T), EG_T, 0, st>>>((const ushort4 *)graph->idx, NT, ctx->row_ptr, ctx->col,
                                                           ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         int bits = 1;
@@ -846,7 +867,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             ED_CUDA_TRY(cudaMemsetAsync(ctx->chunks + nc01[0], 0, sizeof(int4) * (base1 - nc01[0]), st));
         k_chunk_fill<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->ent_start, ctx->brow, ctx->col,
                                                            ctx->chunk_start, ctx->chunk_start1, ctx->chunks); ed_note_launch();
-        k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, P4, graph->weights,
+        k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, PT, graph->weights,
                                                          G4, ctx->ent_geo); ed_note_launch();
         ED_LAUNCH_CHECK();
         ctx->pinned[ED_MAX_PCG_GRID + 1] = nnzb;
@@ -860,9 +881,10 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     ctx->m = m;
     if ((s = ed_pcg_plan(ctx, ctx->row_ptr_host, st)) != ED_OK) return s;
 
-    ctx->pos = pos;
-    ctx->nrm = nrm;
-    ctx->N = N;
+    ctx->pos = ctx->n_kp > 0 ? (const float *)ctx->comb_pos : pos;
+    ctx->nrm = ctx->n_kp > 0 ? (const float *)ctx->comb_nrm : nrm;
+    ctx->N = NT;
+    ctx->n_model = N;
     ctx->graph = *graph;
     ctx->k_graph = prm->k_graph;
     ctx->weight_mode = prm->weight_mode;

@@ -318,3 +318,18 @@ def batch_scenes(count: int = 16, seed0: int = 1) -> List[Tuple[Scene, int]]:
                                   node_count=m, n_gn=5, n_pcg=10)
         out.append((make_scene(cfg, seed=seed0 + i), m))
     return out
+
+
+def make_keypoints(scene: Scene, count: int = 500, seed: int = 1, noise_mm: float = 0.2):
+    """Synthetic sparse key correspondences standing in for matched ORB
+    features: `count` seeded model points (float4, model frame) and their
+    ground-truth positions in the new frame plus N(0, noise_mm) localisation
+    noise (float4, w = 1).  Returns (kp_pos [count][4], kp_target [count][4],
+    indices into the model)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7, count]))
+    sel = np.sort(rng.choice(scene.N, size=min(count, scene.N), replace=False))
+    kp = scene.model_pos[sel].astype(np.float32).copy()
+    kp[:, 3] = 0.0
+    tgt = scene.gt_positions()[sel] + rng.normal(0.0, noise_mm, (len(sel), 3))
+    tgt4 = np.concatenate([tgt, np.ones((len(sel), 1))], axis=1).astype(np.float32)
+    return kp, tgt4, sel
