@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--keypoints", type=int, default=0,
+                    help="sparse key correspondences (E_corr, w_corr = 10): this many seeded key points")
+    ap.add_argument("--weights", default="gaussian", choices=["gaussian", "eq2"],
+                    help="skinning weights: Gaussian (the workload's) or the paper's Eq. (2)")
     ap.add_argument("--radius", type=float, default=0.0,
                     help="Poisson radius (mm); 0 = calibrate to the workload's node count")
     return ap.parse_args()
@@ -228,8 +232,8 @@ def run_ours(args, rank, world, local):
     fx, fy, cx, cy, W, H = s.intr
     dev = "cuda"
     cap_pts = s.N + W * H
-    ctx = E.Context(max_points=cap_pts, max_nodes=max(cfg.node_count, 64), max_width=W, max_height=H,
-                    max_cells=1 << 24)
+    ctx = E.Context(max_points=cap_pts + 3 * args.keypoints, max_nodes=max(cfg.node_count, 64), max_width=W,
+                    max_height=H, max_cells=1 << 24)
     pos = torch.from_numpy(s.model_pos).to(dev)
     nrm = torch.from_numpy(s.model_nrm).to(dev)
     col = torch.from_numpy(s.model_col).to(dev)
@@ -239,6 +243,12 @@ def run_ours(args, rank, world, local):
     nmap = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     frame = E.make_frame(depth, nmap, s.intr, color)
     radius = args.radius if args.radius > 0 else E.calibrate_radius(ctx, pos, nrm, cfg.node_count)
+    wmode = E.ED_WEIGHT_EQ2 if args.weights == "eq2" else E.ED_WEIGHT_GAUSSIAN
+    kp_keep = None
+    if args.keypoints > 0:
+        kp, kp_tgt, _ = synth.make_keypoints(s, args.keypoints, seed=rank_seed(rank))
+        kp_keep = (torch.from_numpy(kp).to(dev), torch.from_numpy(kp_tgt).to(dev))
+        ctx.set_keypoints(kp_keep[0], kp_keep[1], 10.0)
     prm = E.SolverParams(n_pcg=cfg.n_pcg, prior=tuple(float(v) for v in s.pose_prior),
                          precision=E.ED_PRECISION_MIXED if args.precision == "mixed" else E.ED_PRECISION_FP32)
     F = E.FuseParams(frame=1)
@@ -260,7 +270,7 @@ def run_ours(args, rank, world, local):
 
     def step(record_gn=False):
         ctx.compute_normals(depth, s.intr, cfg.normal_half_width, out=nmap)
-        g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius)
+        g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius, weight_mode=wmode)
         m = g.m
         x[:m].zero_()
         x[:m, 0] = 1.0
@@ -372,7 +382,8 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded stereo-scope tissue scene, no dataset)",
         "config": {"workload": args.config, "width": W, "height": H, "model_points": s.N, "nodes": g.m,
                    "nnz_blocks": g.nnzb, "gn_iters_per_step": cfg.n_gn, "pcg_iters": cfg.n_pcg,
-                   "node_radius_mm": radius, "precision": args.precision,
+                   "node_radius_mm": radius, "precision": args.precision, "keypoints": args.keypoints,
+                   "weights": args.weights,
                    "l2": "flushed between steps (512 MB write)",
                    "step": "normals + build_graph + 10 x gn_step + warp + fuse"},
         "gn_only_iters_per_s": gn_rate,
@@ -545,14 +556,20 @@ def run_batch(args, rank, world, local):
 # oracle (CPU) leg
 # ----------------------------------------------------------------------------
 
-def oracle_frame(s, radius):
+def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1):
     """One frame of the whole path in the FP64 oracle; returns seconds."""
     import oracle
+    import synth
     cfg = s.cfg
+    mode = 1 if weights == "eq2" else 0
     t0 = time.perf_counter()
     nm = oracle.normals(s.tgt_depth, s.intr, cfg.normal_half_width)
-    G = oracle.build_graph(s.model_pos, radius=radius, max_nodes=cfg.node_count, K=4, KG=4, mode=0, sigma=radius)
-    P = oracle.Problem(s.model_pos, s.model_nrm, G, s.tgt_depth, nm, s.intr, s.pose_prior)
+    G = oracle.build_graph(s.model_pos, radius=radius, max_nodes=cfg.node_count, K=4, KG=4, mode=mode, sigma=radius)
+    K = None
+    if keypoints > 0:
+        kp, kp_tgt, _ = synth.make_keypoints(s, keypoints, seed=seed)
+        K = oracle.keypoints(kp, kp_tgt[:, :3].astype(np.float64), G.g, K=4, mode=mode, sigma=radius)
+    P = oracle.Problem(s.model_pos, s.model_nrm, G, s.tgt_depth, nm, s.intr, s.pose_prior, keypoints=K)
     x, pose, hist, st = oracle.gn_solve(P, P.identity_x(), s.pose_prior, cfg.n_gn, cfg.n_pcg)
     wp, wn, _ = oracle.warp(P, x, pose)
     wp4 = np.concatenate([wp, s.model_pos[:, 3:4]], 1).astype(np.float32)
@@ -562,13 +579,13 @@ def oracle_frame(s, radius):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(s, budget_s):
+def cpu_baseline(s, budget_s, keypoints=0, weights="gaussian"):
     import oracle
     radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     times = []
     t_start = time.perf_counter()
     while not times or (time.perf_counter() - t_start < budget_s and len(times) < 3):
-        times.append(oracle_frame(s, radius))
+        times.append(oracle_frame(s, radius, keypoints, weights))
     tot = sum(times)
     return {"value": len(times) * s.cfg.n_gn / tot, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} whole frame(s) of the same workload (normals, graph, {s.cfg.n_gn} GN x "
@@ -583,8 +600,9 @@ def run_reference(args, rank, world):
     s = synth.make_scene(args.config, seed=1)
     radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     for _ in range(args.warmup):
-        oracle_frame(s, radius)
-    times = [oracle_frame(s, radius) for _ in range(args.steps)]
+        oracle_frame(s, radius, getattr(args, "keypoints", 0), getattr(args, "weights", "gaussian"))
+    times = [oracle_frame(s, radius, getattr(args, "keypoints", 0), getattr(args, "weights", "gaussian"))
+             for _ in range(args.steps)]
     tot = sum(times)
     value = args.steps * s.cfg.n_gn / tot
     return {"metric": METRIC, "value": value, "unit": "GN iters/s", "n_gpus": world, "steps": args.steps,
@@ -592,7 +610,8 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": args.config, "width": s.cfg.W, "height": s.cfg.H, "model_points": s.N,
-                       "nodes": s.cfg.node_count},
+                       "nodes": s.cfg.node_count, "keypoints": getattr(args, "keypoints", 0),
+                       "weights": getattr(args, "weights", "gaussian")},
             "cpu_baseline": {"value": value, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} whole frames, single-threaded FP64 oracle"},
             "e2e": {"value": value, "unit": "GN iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -614,7 +633,7 @@ def main():
     out, s = run_ours(args, rank, world, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(s, args.cpu_budget_s)
+            out["cpu_baseline"] = cpu_baseline(s, args.cpu_budget_s, args.keypoints, args.weights)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out))

@@ -44,6 +44,47 @@ struct PcgArgs {
     ed_stats *stats;
 };
 
+// Accumulation of the PCG dot products and norms.  FP32 mode: float.  Mixed
+// mode: float-float (hi + lo, about 44 significant bits) on the FP32 pipe --
+// each product is formed exactly (a b = p + e with e = fma(a, b, -p)) and
+// summed by error-free two-sums; on B300 the FP64 rate is a small fraction of
+// the FP32 rate, so the extended precision is kept off the FP64 units.  The
+// per-CTA partials between CTAs are stored as double.
+template <typename DT> struct PcgAcc;
+
+template <> struct PcgAcc<float> {
+    typedef float T;
+    static __device__ __forceinline__ T zero() { return 0.f; }
+    static __device__ __forceinline__ T madd(T acc, float a, float b) { return acc + a * b; }
+    static __device__ __forceinline__ T add(T x, T y) { return x + y; }
+    static __device__ __forceinline__ T shfl(T x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+    static __device__ __forceinline__ T from_double(double d) { return (float)d; }
+    static __device__ __forceinline__ double to_double(T x) { return (double)x; }
+    static __device__ __forceinline__ float to_float(T x) { return x; }
+};
+
+template <> struct PcgAcc<double> {
+    typedef float2 T;
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ T madd(T acc, float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        return ed_ff_add(acc, make_float2(p, __fmaf_rn(a, b, -p)));
+    }
+    static __device__ __forceinline__ T add(T x, T y) { return ed_ff_add(x, y); }
+    static __device__ __forceinline__ T shfl(T x, int o)
+    {
+        return make_float2(__shfl_xor_sync(0xffffffffu, x.x, o), __shfl_xor_sync(0xffffffffu, x.y, o));
+    }
+    static __device__ __forceinline__ T from_double(double d)
+    {
+        const float hi = (float)d;
+        return make_float2(hi, (float)(d - (double)hi));
+    }
+    static __device__ __forceinline__ double to_double(T x) { return (double)x.x + (double)x.y; }
+    static __device__ __forceinline__ float to_float(T x) { return x.x + x.y; }
+};
+
 // component w of the partials of CTA c
 __device__ __forceinline__ double *part_at(double *part, int w, int c) { return part + (size_t)w * ED_MAX_PCG_GRID + c; }
 
@@ -54,27 +95,29 @@ __device__ __forceinline__ double *part_at(double *part, int w, int c) { return 
 // thread gets the same values.  `sh` must not be in use by other code
 // between two calls.
 template <typename DT, int NT, int NC>
-__device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh)[8], DT (&out)[NC])
+__device__ __forceinline__ void sum_partials(const double *part, int nb, typename PcgAcc<DT>::T (*sh)[8],
+                                             typename PcgAcc<DT>::T (&out)[NC])
 {
+    typedef PcgAcc<DT> A;
     constexpr int NCP = NC <= 1 ? 1 : NC <= 2 ? 2 : NC <= 4 ? 4 : 8;
     constexpr int TPC = NT / NCP;       // threads per component
     constexpr int WPC = TPC / 32;       // warps per component
     const int lane = threadIdx.x & 31, w = threadIdx.x / TPC, sub = threadIdx.x % TPC;
-    DT s = 0;
+    typename A::T s = A::zero();
     if (w < NC) {
         const double *src = part + (size_t)w * ED_MAX_PCG_GRID;
 #pragma unroll 4
-        for (int c = sub; c < nb; c += TPC) s += (DT)__ldcg(src + c);
+        for (int c = sub; c < nb; c += TPC) s = A::add(s, A::from_double(__ldcg(src + c)));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
     if (lane == 0) sh[threadIdx.x >> 5][0] = s;
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        DT r = 0;
+        typename A::T r = A::zero();
 #pragma unroll
-        for (int k = 0; k < WPC; ++k) r += sh[c * WPC + k][0];
+        for (int k = 0; k < WPC; ++k) r = A::add(r, sh[c * WPC + k][0]);
         out[c] = r;
     }
 }
@@ -82,24 +125,26 @@ __device__ __forceinline__ void sum_partials(const double *part, int nb, DT (*sh
 // block reduction of NV values per thread: after one CTA barrier,
 // block_sum_get(c) gives component c (fixed order) to any thread that asks
 template <typename DT, int NT, int NV>
-__device__ __forceinline__ void block_sum_n(DT (&v)[NV], DT (*sh)[8])
+__device__ __forceinline__ void block_sum_n(typename PcgAcc<DT>::T (&v)[NV], typename PcgAcc<DT>::T (*sh)[8])
 {
+    typedef PcgAcc<DT> A;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        DT x = v[k];
+        typename A::T x = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl(x, o));
         if (lane == 0) sh[wid][k] = x;
     }
     __syncthreads();
 }
 
 template <typename DT, int NT>
-__device__ __forceinline__ DT block_sum_get(const DT (*sh)[8], int c)
+__device__ __forceinline__ typename PcgAcc<DT>::T block_sum_get(const typename PcgAcc<DT>::T (*sh)[8], int c)
 {
-    DT s = 0;
-    for (int w = 0; w < NT / 32; ++w) s += sh[w][c];
+    typedef PcgAcc<DT> A;
+    typename A::T s = A::zero();
+    for (int w = 0; w < NT / 32; ++w) s = A::add(s, sh[w][c]);
     return s;
 }
 
@@ -133,11 +178,13 @@ template <typename DT, int NT>
 __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const unsigned nb)
 {
     constexpr int ROWS_PER_PASS = RowsPerPass<NT>::v;
+    typedef PcgAcc<DT> A;
+    typedef typename A::T AT;   // accumulator of the dot products and norms
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_flag;
-    __shared__ DT s_red[NT / 32][8];    // block reductions
-    __shared__ DT s_red2[NT / 32][8];   // sums of the CTA partials
+    __shared__ AT s_red[NT / 32][8];    // block reductions
+    __shared__ AT s_red2[NT / 32][8];   // sums of the CTA partials
     __shared__ float s_pp[6], s_zp[6], s_rpose[6], s_dpose[6];
     __shared__ float s_Hpp[36], s_Mp[36];
 
@@ -207,7 +254,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     bool h_ready = false;
 
     // z_j = Minv_j r_j for the own rows (thread = one output row); partials r.z, r.r
-    auto precond = [&](DT &rz, DT &rrs) {
+    auto precond = [&](AT &rz, AT &rrs) {
         for (int j0 = 0; j0 < rows; j0 += ROWS_PER_PASS) {
             const int jl = j0 + grp;
             if (in_grp && jl < rows) {
@@ -222,20 +269,20 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                 const float rv1 = rs[jl * 12 + rr];
                 zs[jl * 12 + rr] = zz;
                 a.z[12 * (r0 + jl) + rr] = zz;
-                rz += (DT)rv1 * (DT)zz;
-                rrs += (DT)rv1 * (DT)rv1;
+                rz = A::madd(rz, rv1, zz);
+                rrs = A::madd(rrs, rv1, rv1);
             }
         }
     };
 
     // pose rows (CTA 0, thread 0): z_p = Mp r_p; adds the pose terms of r.z and r.r
-    auto pose_precond = [&](DT &v1, DT &v2) {
+    auto pose_precond = [&](AT &v1, AT &v2) {
         for (int i = 0; i < 6; ++i) {
             float zi = 0.f;
             for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
             a.z[P + i] = zi;
-            v1 += (DT)s_rpose[i] * (DT)zi;
-            v2 += (DT)s_rpose[i] * (DT)s_rpose[i];
+            v1 = A::madd(v1, s_rpose[i], zi);
+            v2 = A::madd(v2, s_rpose[i], s_rpose[i]);
         }
     };
 
@@ -294,13 +341,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
 
     // ---- set-up: r = b, d = 0, z = M^-1 r ----
     {
-        DT rz = 0, rrs = 0;
+        AT rz = A::zero(), rrs = A::zero();
         precond(rz, rrs);
-        DT vv[2] = {rz, rrs};
+        AT vv[2] = {rz, rrs};
         block_sum_n<DT, NT, 2>(vv, s_red);
     }
     if (t == 0) {
-        DT v1 = block_sum_get<DT, NT>(s_red, 0), v2 = block_sum_get<DT, NT>(s_red, 1);
+        AT v1 = block_sum_get<DT, NT>(s_red, 0), v2 = block_sum_get<DT, NT>(s_red, 1);
         if (cta == 0) {
             for (int i = 0; i < 6; ++i) {
                 s_rpose[i] = -a.grad[P + i];
@@ -308,27 +355,27 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             }
             pose_precond(v1, v2);
         }
-        *part_at(part0, 0, cta) = (double)v1;
-        *part_at(part0, 1, cta) = (double)v2;
+        *part_at(part0, 0, cta) = A::to_double(v1);
+        *part_at(part0, 1, cta) = A::to_double(v2);
     }
     if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
     stage_issue(nullptr);
     // the scalars of the iteration live in every thread's registers (identical values)
-    DT rho, rr2s, res0;
-    float beta = 0.f;
+    AT rho, rr2s;
+    float res0, beta = 0.f;
     {
-        DT sums[2];
+        AT sums[2];
         sum_partials<DT, NT, 2>(part0, nb, s_red2, sums);
         rho = sums[0];
         rr2s = sums[1];
-        res0 = (DT)sqrt((double)sums[1]);
+        res0 = sqrtf(A::to_float(sums[1]));
     }
     float qp[6];   // the pose rows of q = H p (CTA 0 thread 0 uses them for the pose update)
 
     int it = 0;
     for (; it < a.n_iter; ++it) {
-        if (!(rho > (DT)0)) break;
-        if (a.tol > 0.f && sqrt((double)rr2s) <= (double)a.tol * (double)res0) break;
+        if (!(A::to_float(rho) > 0.f)) break;
+        if (a.tol > 0.f && sqrtf(A::to_float(rr2s)) <= a.tol * res0) break;
         float *pnew = (it & 1) ? a.p1 : a.p0;
         // ---- p = z + beta p(prev): block columns (staged), own rows (published), pose ----
         stage_finish(beta, it == 0);
@@ -349,8 +396,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         }
         // ---- phase A: q = H p for the own rows (thread = one output row of one
         // of the S splits of a row's blocks), partials p.q and C p ----
-        DT pq = 0;
-        DT cp[6] = {0, 0, 0, 0, 0, 0};
+        AT pq = A::zero();
+        AT cp[6] = {A::zero(), A::zero(), A::zero(), A::zero(), A::zero(), A::zero()};
         for (int j0 = 0; j0 < rows; j0 += rpp) {
             const int jl = j0 + grp / S, sp = grp - (grp / S) * S;
             if (in_grp && grp < rpp * S && jl < rows) {
@@ -380,52 +427,52 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                 for (int s = 0; s < 6; ++s) qv += C[12 * s + rr] * s_pp[s];
                 qs[jr * 12 + rr] = qv;
                 const float pv = ps[jr * 12 + rr];
-                pq += (DT)pv * (DT)qv;
+                pq = A::madd(pq, pv, qv);
 #pragma unroll
-                for (int s = 0; s < 6; ++s) cp[s] += (DT)C[12 * s + rr] * (DT)pv;
+                for (int s = 0; s < 6; ++s) cp[s] = A::madd(cp[s], C[12 * s + rr], pv);
             }
             if (j0 + rpp < rows) __syncthreads();   // qsplit is reused by the next pass
         }
         {
-            DT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
+            AT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
             block_sum_n<DT, NT, 7>(vv, s_red);
-            if (t < 7) *part_at(part1, t, cta) = (double)block_sum_get<DT, NT>(s_red, t);
+            if (t < 7) *part_at(part1, t, cta) = A::to_double(block_sum_get<DT, NT>(s_red, t));
         }
         if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         // ---- phase B: alpha (every thread), d += alpha p, r -= alpha q, z = M^-1 r ----
-        DT alpha_d;
+        float alpha;
         {
-            DT sums[7];
+            AT sums[7];
             sum_partials<DT, NT, 7>(part1, nb, s_red2, sums);
-            DT pqt = sums[0];
+            AT pqt = sums[0];
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                float qi = (float)sums[1 + i];
+                float qi = A::to_float(sums[1 + i]);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
                 qp[i] = qi;
-                pqt += (DT)s_pp[i] * (DT)qi;
+                pqt = A::madd(pqt, s_pp[i], qi);
             }
-            if (!(pqt > (DT)0)) {
+            const float pqt_f = A::to_float(pqt);
+            if (!(pqt_f > 0.f)) {
                 if (cta == 0 && t == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
                 break;
             }
-            alpha_d = rho / pqt;
+            alpha = A::to_float(rho) / pqt_f;
         }
-        const float alpha = (float)alpha_d;
         for (int i = t; i < rows * 12; i += NT) {
             ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
             rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
         }
         __syncthreads();
         {
-            DT rz2 = 0, rr2 = 0;
+            AT rz2 = A::zero(), rr2 = A::zero();
             precond(rz2, rr2);
-            DT vv[2] = {rz2, rr2};
+            AT vv[2] = {rz2, rr2};
             block_sum_n<DT, NT, 2>(vv, s_red);
         }
         if (t == 0) {
-            DT w1 = block_sum_get<DT, NT>(s_red, 0), w2 = block_sum_get<DT, NT>(s_red, 1);
+            AT w1 = block_sum_get<DT, NT>(s_red, 0), w2 = block_sum_get<DT, NT>(s_red, 1);
             if (cta == 0) {
                 for (int i = 0; i < 6; ++i) {
                     s_dpose[i] = __fmaf_rn(alpha, s_pp[i], s_dpose[i]);
@@ -433,15 +480,15 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                 }
                 pose_precond(w1, w2);
             }
-            *part_at(part0, 0, cta) = (double)w1;
-            *part_at(part0, 1, cta) = (double)w2;
+            *part_at(part0, 0, cta) = A::to_double(w1);
+            *part_at(part0, 1, cta) = A::to_double(w2);
         }
         if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
         stage_issue(pnew);
         {
-            DT sums[2];
+            AT sums[2];
             sum_partials<DT, NT, 2>(part0, nb, s_red2, sums);
-            beta = (float)(sums[0] / rho);
+            beta = A::to_float(sums[0]) / A::to_float(rho);
             rho = sums[0];
             rr2s = sums[1];
         }
@@ -452,7 +499,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     if (cta == 0 && t == 0 && a.stats) {
         a.stats->pcg_iters = it;
         a.stats->pcg_res0 = (double)res0;
-        a.stats->pcg_res = sqrt((double)rr2s);
+        a.stats->pcg_res = sqrt(A::to_double(rr2s));
     }
 }
 
