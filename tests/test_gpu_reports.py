@@ -7,8 +7,8 @@ pose coordinates, and against the J^T r that the Gauss-Newton step assembles
 with its own kernels.
 
 Precision (160x120 over the whole 5-iteration trajectory, 1280x720 / 4096
-nodes for one iteration): plain FP32 and the mixed form (FP64 PCG dot
-products and node-parameter master copy, compensated block reductions), each
+nodes for one iteration): plain FP32 and the mixed form (float-float PCG
+dot products, FP64 node-parameter master copy, compensated block reductions), each
 result's error against the oracle stated: energy, node parameters, warped
 points in mm.
 
