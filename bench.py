@@ -51,6 +51,9 @@ def parse():
                     help="sparse key correspondences (E_corr, w_corr = 10): this many seeded key points")
     ap.add_argument("--weights", default="gaussian", choices=["gaussian", "eq2"],
                     help="skinning weights: Gaussian (the workload's) or the paper's Eq. (2)")
+    ap.add_argument("--lm", type=float, default=None, metavar="LAMBDA0",
+                    help="Levenberg-Marquardt acceptance on the device from this damping (Sec. II.F); "
+                         "default: plain Gauss-Newton (lambda = 0)")
     ap.add_argument("--radius", type=float, default=0.0,
                     help="Poisson radius (mm); 0 = calibrate to the workload's node count")
     return ap.parse_args()
@@ -250,7 +253,8 @@ def run_ours(args, rank, world, local):
         kp_keep = (torch.from_numpy(kp).to(dev), torch.from_numpy(kp_tgt).to(dev))
         ctx.set_keypoints(kp_keep[0], kp_keep[1], 10.0)
     prm = E.SolverParams(n_pcg=cfg.n_pcg, prior=tuple(float(v) for v in s.pose_prior),
-                         precision=E.ED_PRECISION_MIXED if args.precision == "mixed" else E.ED_PRECISION_FP32)
+                         precision=E.ED_PRECISION_MIXED if args.precision == "mixed" else E.ED_PRECISION_FP32,
+                         lm_accept=args.lm is not None)
     F = E.FuseParams(frame=1)
     x = torch.empty((cfg.node_count, 12), dtype=torch.float32, device=dev)
     xm = torch.empty((cfg.node_count, 12), dtype=torch.float64, device=dev)
@@ -278,6 +282,8 @@ def run_ours(args, rank, world, local):
         x[:m, 10] = 1.0
         xm[:m].copy_(x[:m])
         pose.copy_(prior)
+        if args.lm is not None:
+            ctx.lm_reset(args.lm)
         if record_gn:
             e0 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -384,6 +390,7 @@ def run_ours(args, rank, world, local):
                    "nnz_blocks": g.nnzb, "gn_iters_per_step": cfg.n_gn, "pcg_iters": cfg.n_pcg,
                    "node_radius_mm": radius, "precision": args.precision, "keypoints": args.keypoints,
                    "weights": args.weights,
+                   "solver": "gauss-newton" if args.lm is None else f"levenberg-marquardt, lambda0 = {args.lm:g}",
                    "l2": "flushed between steps (512 MB write)",
                    "step": "normals + build_graph + 10 x gn_step + warp + fuse"},
         "gn_only_iters_per_s": gn_rate,
@@ -556,7 +563,7 @@ def run_batch(args, rank, world, local):
 # oracle (CPU) leg
 # ----------------------------------------------------------------------------
 
-def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1):
+def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1, lm=None):
     """One frame of the whole path in the FP64 oracle; returns seconds."""
     import oracle
     import synth
@@ -570,7 +577,8 @@ def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1):
         kp, kp_tgt, _ = synth.make_keypoints(s, keypoints, seed=seed)
         K = oracle.keypoints(kp, kp_tgt[:, :3].astype(np.float64), G.g, K=4, mode=mode, sigma=radius)
     P = oracle.Problem(s.model_pos, s.model_nrm, G, s.tgt_depth, nm, s.intr, s.pose_prior, keypoints=K)
-    x, pose, hist, st = oracle.gn_solve(P, P.identity_x(), s.pose_prior, cfg.n_gn, cfg.n_pcg)
+    x, pose, hist, st = oracle.gn_solve(P, P.identity_x(), s.pose_prior, cfg.n_gn, cfg.n_pcg,
+                                        lam=0.0 if lm is None else lm, lm_accept=lm is not None)
     wp, wn, _ = oracle.warp(P, x, pose)
     wp4 = np.concatenate([wp, s.model_pos[:, 3:4]], 1).astype(np.float32)
     wn4 = np.concatenate([wn, s.model_nrm[:, 3:4]], 1).astype(np.float32)
@@ -579,13 +587,13 @@ def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(s, budget_s, keypoints=0, weights="gaussian"):
+def cpu_baseline(s, budget_s, keypoints=0, weights="gaussian", lm=None):
     import oracle
     radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     times = []
     t_start = time.perf_counter()
     while not times or (time.perf_counter() - t_start < budget_s and len(times) < 3):
-        times.append(oracle_frame(s, radius, keypoints, weights))
+        times.append(oracle_frame(s, radius, keypoints, weights, lm=lm))
     tot = sum(times)
     return {"value": len(times) * s.cfg.n_gn / tot, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} whole frame(s) of the same workload (normals, graph, {s.cfg.n_gn} GN x "
@@ -600,8 +608,8 @@ def run_reference(args, rank, world):
     s = synth.make_scene(args.config, seed=1)
     radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     for _ in range(args.warmup):
-        oracle_frame(s, radius, getattr(args, "keypoints", 0), getattr(args, "weights", "gaussian"))
-    times = [oracle_frame(s, radius, getattr(args, "keypoints", 0), getattr(args, "weights", "gaussian"))
+        oracle_frame(s, radius, args.keypoints, args.weights, lm=args.lm)
+    times = [oracle_frame(s, radius, args.keypoints, args.weights, lm=args.lm)
              for _ in range(args.steps)]
     tot = sum(times)
     value = args.steps * s.cfg.n_gn / tot
@@ -611,7 +619,8 @@ def run_reference(args, rank, world):
             "impl": "reference",
             "config": {"workload": args.config, "width": s.cfg.W, "height": s.cfg.H, "model_points": s.N,
                        "nodes": s.cfg.node_count, "keypoints": getattr(args, "keypoints", 0),
-                       "weights": getattr(args, "weights", "gaussian")},
+                       "weights": getattr(args, "weights", "gaussian"),
+                       "solver": "gauss-newton" if args.lm is None else f"levenberg-marquardt, lambda0 = {args.lm:g}"},
             "cpu_baseline": {"value": value, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} whole frames, single-threaded FP64 oracle"},
             "e2e": {"value": value, "unit": "GN iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -633,7 +642,7 @@ def main():
     out, s = run_ours(args, rank, world, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(s, args.cpu_budget_s, args.keypoints, args.weights)
+            out["cpu_baseline"] = cpu_baseline(s, args.cpu_budget_s, args.keypoints, args.weights, args.lm)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out))

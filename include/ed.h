@@ -176,6 +176,8 @@ typedef struct ed_solver_params {
     float jitter;          /* preconditioner block shift, relative to trace/size */
     int precision;         /* ED_PRECISION_FP32 or ED_PRECISION_MIXED */
     double prior[6];       /* pose prior for E_r, E_p (Sec. II.E "Global Pose") */
+    int lm_accept;         /* 1: Levenberg-Marquardt acceptance on the device (ed_lm_reset);
+                              lambda then comes from the context's damping state */
 } ed_solver_params;
 
 /* Device-side statistics of one Gauss-Newton step, at its input (x, pose). */
@@ -187,8 +189,9 @@ typedef struct ed_stats {
     int n_valid;           /* points that passed the visible-point gate */
     int pcg_iters;
     int status;            /* ed_status of the device-side checks */
-    int reserved;
+    int lm_rejected;       /* lm_accept: 1 when this step undid the previous one */
     double e_corr;         /* sparse key-correspondence energy (0 without key points) */
+    double lambda;         /* damping of the system this step solved */
 } ed_stats;
 
 /*
@@ -202,10 +205,29 @@ typedef struct ed_stats {
  * ED_PRECISION_MIXED (the master copy that accumulates the updates; x is
  * rewritten from it), ignored otherwise.  pose: double[6], updated in place.
  * stats: device ed_stats (may be NULL).  When a device check fails the
- * update is skipped and stats->status says why.
+ * update is skipped and stats->status says why.  With params->lm_accept the
+ * Levenberg-Marquardt decision of ed_lm_reset comes between the assembly and
+ * the solve, and params->lambda is not used.
  */
 ed_status ed_gn_step(ed_context *ctx, const ed_frame *frame, const ed_solver_params *params, float *x,
                      double *x_master, double *pose, ed_stats *stats, cudaStream_t stream);
+
+/*
+ * Levenberg-Marquardt damping schedule (Sec. II.F solves Eq. 3 with LM), kept
+ * on the device so that a sequence of ed_gn_step calls needs no host
+ * synchronisation and can be captured in a CUDA graph.  Steps with
+ * params->lm_accept = 1 compare the energy at their input point with the
+ * energy of the last accepted point: if it rose, the previous update is
+ * undone (x, x_master, pose restored and the normal equations of the
+ * accepted point reused, unchanged) and lambda <- 10 lambda (1e-4 when it
+ * was 0); otherwise the point is accepted and lambda <- lambda / 10 (not on
+ * the first step after a reset).  The system solved is H + lambda diag(H),
+ * the block-Jacobi inverses taken from the damped diagonal blocks.  The
+ * energy reported for a rejected step is that of the restored point.
+ * ed_lm_reset starts a new solve: lambda = lambda0, no accepted point yet.
+ * Enqueued on the stream; a context starts with lambda = 0 and no point.
+ */
+ed_status ed_lm_reset(ed_context *ctx, float lambda0, cudaStream_t stream);
 
 /*
  * Optional debug outputs of the next ed_gn_step calls (device buffers or

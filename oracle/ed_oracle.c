@@ -1219,14 +1219,14 @@ int or_gn_solve(const or_problem *P, const or_solver *S, double *x, double *pose
         or_normal_eq Q;
         or_linearize(P, x, pose, NULL, NULL, &Q);
         double E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4] + Q.E[5];
-        if (S->lm_accept && it > 0 && E > Eprev) {
+        if (S->lm_accept && it > 0 && !(E <= Eprev)) {   /* a non-finite energy is not a decrease */
             /* reject the last step */
             or_normal_eq_free(&Q);
             memcpy(x, xprev, sizeof(double) * 12 * (size_t)m);
             memcpy(pose, xprev + 12 * (size_t)m, sizeof(double) * 6);
             lambda = lambda > 0 ? lambda * 10.0 : 1e-4;
             or_linearize(P, x, pose, NULL, NULL, &Q);
-            E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4];
+            E = Q.E[0] + Q.E[1] + Q.E[2] + Q.E[3] + Q.E[4] + Q.E[5];
         } else if (S->lm_accept && it > 0) {
             lambda *= 0.1;
         }

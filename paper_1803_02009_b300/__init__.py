@@ -65,14 +65,14 @@ class SolverParamsC(C.Structure):
     _fields_ = [("w_data", C.c_float), ("w_rot", C.c_float), ("w_reg", C.c_float), ("w_r", C.c_float),
                 ("w_p", C.c_float), ("eps_d", C.c_float), ("cos_eps_n", C.c_float), ("n_pcg", C.c_int),
                 ("pcg_tol", C.c_float), ("lam", C.c_float), ("jitter", C.c_float), ("precision", C.c_int),
-                ("prior", C.c_double * 6)]
+                ("prior", C.c_double * 6), ("lm_accept", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("energy", C.c_double), ("e_data", C.c_double), ("e_rot", C.c_double), ("e_reg", C.c_double),
                 ("e_rot_prior", C.c_double), ("e_pos_prior", C.c_double), ("pcg_res0", C.c_double),
                 ("pcg_res", C.c_double), ("n_valid", C.c_int), ("pcg_iters", C.c_int), ("status", C.c_int),
-                ("reserved", C.c_int), ("e_corr", C.c_double)]
+                ("lm_rejected", C.c_int), ("e_corr", C.c_double), ("lam", C.c_double)]
 
 
 STATS_BYTES = C.sizeof(Stats)
@@ -110,6 +110,7 @@ _SIGS = {
     "ed_set_timing": [_vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)],
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
     "ed_set_keypoints": [_vp, _vp, _vp, C.c_int, C.c_float],
+    "ed_lm_reset": [_vp, C.c_float, _vp],
     "ed_batch_query_workspace": [_vp, C.c_int, C.POINTER(C.c_size_t)],
     "ed_batch_create": [_vp, C.c_int, _vp, C.c_size_t, C.POINTER(_vp)],
     "ed_batch_destroy": [_vp],
@@ -189,6 +190,7 @@ class SolverParams:
     jitter: float = 1e-6
     precision: int = ED_PRECISION_FP32
     prior: tuple = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    lm_accept: bool = False   # device-side Levenberg-Marquardt acceptance (Context.lm_reset)
 
     def c(self) -> SolverParamsC:
         p = SolverParamsC()
@@ -198,6 +200,7 @@ class SolverParams:
         p.n_pcg, p.pcg_tol, p.lam, p.jitter, p.precision = self.n_pcg, self.pcg_tol, self.lam, self.jitter, self.precision
         for i in range(6):
             p.prior[i] = float(self.prior[i])
+        p.lm_accept = int(bool(self.lm_accept))
         return p
 
 
@@ -316,6 +319,11 @@ class Context:
         p = params.c()
         _check("ed_gn_step", lib().ed_gn_step(self.h, C.byref(frame), C.byref(p), _ptr(x), _ptr(x_master),
                                               _ptr(pose), _ptr(stats), _stream(stream)))
+
+    def lm_reset(self, lambda0=0.0, stream=None):
+        """Starts a Levenberg-Marquardt solve: damping lambda0, no accepted
+        point (steps with SolverParams.lm_accept use this device state)."""
+        _check("ed_lm_reset", lib().ed_lm_reset(self.h, float(lambda0), _stream(stream)))
 
     def set_debug(self, wpos=None, wnrm=None, pix=None):
         _check("ed_set_debug", lib().ed_set_debug(self.h, _ptr(wpos), _ptr(wnrm), _ptr(pix)))

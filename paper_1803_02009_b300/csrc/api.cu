@@ -85,6 +85,13 @@ size_t carve(ed_context *c, char *base)
     c->pnode = k.take<float>(M * 72);
     c->minv = k.take<float>(M * 144);
     c->pose_blk = k.take<float>(72);
+    c->bsr_s = k.take<float>(nnzb * 144);
+    c->grad_s = k.take<float>(P);
+    c->pnode_s = k.take<float>(M * 72);
+    c->pblk_s = k.take<float>(36);
+    c->x_prev = k.take<float>(M * 12);
+    c->xm_prev = k.take<double>(M * 12);
+    c->pose_prev = k.take<double>(6);
     c->node_energy = k.take<float2>(M);
     c->rec0 = k.take<float4>(N);
     c->rec1 = k.take<float4>(N);
@@ -155,6 +162,7 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
         cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess ||
+        cudaMemset(c->dmisc, 0, sizeof(double) * 64) != cudaSuccess ||
         cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_state_len) != cudaSuccess ||
         cudaMemset(c->scan_ticket, 0, sizeof(unsigned)) != cudaSuccess) {
         cudaFreeHost(c->row_ptr_host);

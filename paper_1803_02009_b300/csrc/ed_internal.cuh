@@ -22,6 +22,14 @@
 #define ED_MAX_PCG_GRID 1184   // 8 x 148
 #define ED_PINNED_INTS (ED_MAX_PCG_GRID + 1 + 16)
 
+// indices of the dmisc doubles: 0..7 energy terms of the current step
+// (total, data, rot, reg, rot prior, pos prior, valid points, corr)
+enum {
+    DM_LAM = 16,         // Levenberg-Marquardt damping lambda
+    DM_EPREV = 17,       // energy of the last accepted point
+    DM_SAVED = 24,       // 24..31 energy terms of the last accepted point
+};
+
 // indices of the misc int words in the workspace
 enum {
     MI_STATUS = 0,       // device status word (ed_status)
@@ -37,6 +45,8 @@ enum {
     MI_PHASE_BASE = 24,  // running node count during sampling
     MI_BAR = 32,         // grid barrier arrival count of the PCG
     MI_BAR_GRAPH = 33,   // grid barrier arrival count of the Poisson sampler
+    MI_LM_HAVE = 36,     // Levenberg-Marquardt: an accepted point is stored
+    MI_LM_REJECT = 37,   // Levenberg-Marquardt: the current step undid the previous one
     MI_FUSE = 40,        // 40 kept, 41 lifted
     MI_READ = 48,        // 48..51 values gathered for one host read (chunk totals, upper blocks)
     MI_PHASES = 64,      // 64..90 phase counts, 96..123 starts, 128..154 fill counters
@@ -114,6 +124,15 @@ struct ed_context {
     float *pnode;            // [m][72] pose-node blocks
     float *minv;             // [m][144] block-Jacobi inverses
     float *pose_blk;         // [36] pose block, [36..72) its inverse
+    // Levenberg-Marquardt: the undamped system and the parameters of the last
+    // accepted point (restored when a step raises the energy)
+    float *bsr_s;            // [max_nnzb][144]
+    float *grad_s;           // [12 m + 6]
+    float *pnode_s;          // [m][72]
+    float *pblk_s;           // [36]
+    float *x_prev;           // [m][12]
+    double *xm_prev;         // [m][12]
+    double *pose_prev;       // [6]
     float2 *node_energy;     // [m] (rot, reg) of every node
     float4 *rec0;            // [N] (R^T n(u), r)
     float4 *rec1;            // [N] (d r / d angles, 0)

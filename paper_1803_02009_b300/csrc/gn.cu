@@ -484,6 +484,87 @@ __device__ __forceinline__ float rot_jtj(const float *X, int r, int c, int rp, i
     return v;
 }
 
+// block-Jacobi inverse of one 12x12 block H (shared memory, one warp):
+// Cholesky of H + jitter tr/12 I in place (lower triangle, 78 entries, at most
+// three per lane), then M^-1 = L^-T L^-1 into out (row-major); false, with out
+// untouched, on a non-positive pivot.  L, rinv: per-warp shared scratch;
+// s_tab: the entry table of k_finalize (row in bits 16..23, column in 24..31).
+__device__ __forceinline__ bool block_inverse12(float *H, float *L, float *rinv, const int *s_tab, float jitter,
+                                                float *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    float tr = 0.f;
+    for (int k = 0; k < 12; ++k) tr += H[k * 13];
+    __syncwarp();
+    if (lane < 12) H[lane * 13] += jitter * tr / 12.0f;
+    int tri_r[3], tri_c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        int t = lane + 32 * q, r = 0;
+        while (t > r) {   // t -> (r, c) with t = r (r + 1) / 2 + c, c <= r
+            t -= r + 1;
+            ++r;
+        }
+        tri_r[q] = lane + 32 * q < 78 ? r : -1;
+        tri_c[q] = t;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < 12; ++k) {
+        const float piv = H[k * 13];
+        if (!(piv > 0.f)) ok = false;
+        const float sq = ok ? sqrtf(piv) : 1.0f;
+        const float inv = 1.0f / sq;
+        __syncwarp();
+        if (lane == 0) {
+            H[k * 13] = sq;
+            rinv[k] = inv;
+        }
+        if (lane > k && lane < 12) H[lane * 12 + k] *= inv;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int r = tri_r[q], c = tri_c[q];
+            if (r > k && c > k) H[r * 12 + c] -= H[r * 12 + k] * H[c * 12 + k];
+        }
+        __syncwarp();
+    }
+    if (!ok) return false;
+    // L^-1 by forward substitution, one column per lane (lanes 0..11)
+    if (lane < 12) {
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            float v = (r == lane) ? 1.0f : 0.0f;
+            for (int k = lane; k < r; ++k) v -= H[r * 12 + k] * L[k * 12 + lane];
+            L[r * 12 + lane] = r < lane ? 0.f : v * rinv[r];
+        }
+    }
+    __syncwarp();
+    // M^-1 = L^-T L^-1: entry (p, q) sums rows k >= max(p, q) of the lower-triangular L^-1
+    for (int e = lane; e < 144; e += 32) {
+        const int T = s_tab[e];
+        const int p = (T >> 16) & 255, q = T >> 24;
+        float s2 = 0.f;
+        for (int k = p > q ? p : q; k < 12; ++k) s2 += L[k * 12 + p] * L[k * 12 + q];
+        out[e] = s2;
+    }
+    return true;
+}
+
+// the entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
+// shift), R, C
+__device__ __forceinline__ void fill_block_table(int *s_tab)
+{
+    for (int e = threadIdx.x; e < 144; e += blockDim.x) {
+        const int R = e / 12, Cc = e % 12;
+        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+        const int mi = 10 * sym3(r, rp) + sym4(c, cp), m3 = 10 * sym3(r, rp) + sym4(c, 3);
+        s_tab[e] = mi | (m3 << 8) | (R << 16) | (Cc << 24);
+    }
+}
+
+// INV = false: the block inverses are taken later (Levenberg-Marquardt stage)
+template <bool INV>
 __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
 {
     __shared__ float sM[FIN_WARPS][84];
@@ -495,12 +576,7 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
     // shift), R, C (the same for every block; computed once per CTA)
     __shared__ int s_tab[144];
-    for (int e = threadIdx.x; e < 144; e += blockDim.x) {
-        const int R = e / 12, Cc = e % 12;
-        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
-        const int mi = 10 * sym3(r, rp) + sym4(c, cp), m3 = 10 * sym3(r, rp) + sym4(c, 3);
-        s_tab[e] = mi | (m3 << 8) | (R << 16) | (Cc << 24);
-    }
+    fill_block_table(s_tab);
     __syncthreads();
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int u = blockIdx.x * FIN_WARPS + wid;
@@ -646,67 +722,9 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __syncwarp();
     for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
     __syncwarp();
-    // block-Jacobi inverse: Cholesky of H + jitter tr/12 I (lower triangle, 78
-    // entries, at most three per lane), then L^-T L^-1
-    float tr = 0.f;
-    for (int k = 0; k < 12; ++k) tr += H[k * 13];
-    __syncwarp();
-    if (lane < 12) H[lane * 13] += a.jitter * tr / 12.0f;
-    int tri_r[3], tri_c[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        int t = lane + 32 * q, r = 0;
-        while (t > r) {   // t -> (r, c) with t = r (r + 1) / 2 + c, c <= r
-            t -= r + 1;
-            ++r;
-        }
-        tri_r[q] = lane + 32 * q < 78 ? r : -1;
-        tri_c[q] = t;
-    }
-    __syncwarp();
-    float *rinv = sRinv[wid];
-    bool ok = true;
-    for (int k = 0; k < 12; ++k) {
-        const float piv = H[k * 13];
-        if (!(piv > 0.f)) ok = false;
-        const float sq = ok ? sqrtf(piv) : 1.0f;
-        const float inv = 1.0f / sq;
-        __syncwarp();
-        if (lane == 0) {
-            H[k * 13] = sq;
-            rinv[k] = inv;
-        }
-        if (lane > k && lane < 12) H[lane * 12 + k] *= inv;
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int r = tri_r[q], c = tri_c[q];
-            if (r > k && c > k) H[r * 12 + c] -= H[r * 12 + k] * H[c * 12 + k];
-        }
-        __syncwarp();
-    }
-    if (!ok) {
-        if (lane == 0) atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
-        return;
-    }
-    // L^-1 by forward substitution, one column per lane (lanes 0..11)
-    if (lane < 12) {
-#pragma unroll
-        for (int r = 0; r < 12; ++r) {
-            float v = (r == lane) ? 1.0f : 0.0f;
-            for (int k = lane; k < r; ++k) v -= H[r * 12 + k] * sL[wid][k * 12 + lane];
-            sL[wid][r * 12 + lane] = r < lane ? 0.f : v * rinv[r];
-        }
-    }
-    __syncwarp();
-    // M^-1 = L^-T L^-1: entry (p, q) sums rows k >= max(p, q) of the lower-triangular L^-1
-    for (int e = lane; e < 144; e += 32) {
-        const int T = s_tab[e];
-        const int p = (T >> 16) & 255, q = T >> 24;
-        float s2 = 0.f;
-        for (int k = p > q ? p : q; k < 12; ++k) s2 += sL[wid][k * 12 + p] * sL[wid][k * 12 + q];
-        a.minv[(long)j * 144 + e] = s2;
-    }
+    if (!INV) return;
+    if (!block_inverse12(H, sL[wid], sRinv[wid], s_tab, a.jitter, a.minv + (long)j * 144) && lane == 0)
+        atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
 }
 
 // ---------------------------------------------------------------------------
@@ -766,6 +784,58 @@ __device__ __forceinline__ void pf_sums(const float2 *__restrict__ part, int npa
     __syncthreads();
 }
 
+// inverse of the 6x6 pose block Ls (+ jitter tr/6 I; shared memory, one warp,
+// one row per lane): Cholesky in place, then forward and back substitution,
+// one column per lane, into out[36] (row-major); false on a non-positive pivot
+__device__ __forceinline__ bool pose_inverse6(float *Ls, float *rinv, float jitter, float *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const float tr = Ls[0] + Ls[7] + Ls[14] + Ls[21] + Ls[28] + Ls[35];
+    __syncwarp();
+    if (lane < 6) Ls[7 * lane] += jitter * tr / 6.0f;
+    __syncwarp();
+    bool ok = true;
+    for (int c = 0; c < 6; ++c) {
+        if (lane == c) {
+            float d = Ls[7 * c];
+            for (int p = 0; p < c; ++p) d -= Ls[6 * c + p] * Ls[6 * c + p];
+            ok = d > 0.f;
+            d = sqrtf(fmaxf(d, 1e-30f));
+            Ls[7 * c] = d;
+            rinv[c] = 1.0f / d;
+        }
+        __syncwarp();
+        if (lane > c && lane < 6) {
+            float v = Ls[6 * lane + c];
+            for (int p = 0; p < c; ++p) v -= Ls[6 * lane + p] * Ls[6 * c + p];
+            Ls[6 * lane + c] = v * rinv[c];
+        }
+        __syncwarp();
+    }
+    const bool all_ok = __all_sync(0xffffffffu, ok);
+    if (lane < 6) {
+        const int col = lane;
+        float y[6], xv[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            float v = r == col ? 1.0f : 0.0f;
+#pragma unroll
+            for (int p = 0; p < r; ++p) v -= Ls[6 * r + p] * y[p];
+            y[r] = v * rinv[r];
+        }
+#pragma unroll
+        for (int r = 5; r >= 0; --r) {
+            float v = y[r];
+#pragma unroll
+            for (int p = r + 1; p < 6; ++p) v -= Ls[6 * p + r] * xv[p];
+            xv[r] = v * rinv[r];
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) out[6 * r + col] = xv[r];
+    }
+    return all_ok;
+}
+
 __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restrict__ part, int nparts, int pstride,
                                                            const float2 *__restrict__ node_energy, int m,
                                                            const double *__restrict__ pose, ed_solver_params prm,
@@ -798,52 +868,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restr
         grad[a] = (float)(s[23 + a] + wt * d);
     }
     __syncthreads();
-    // Cholesky factor of the pose block + jitter tr/6 I: warp 0, one row per lane
     if (t < 32) {
-        const float tr = Ls[0] + Ls[7] + Ls[14] + Ls[21] + Ls[28] + Ls[35];
-        if (lane < 6) Ls[7 * lane] += prm.jitter * tr / 6.0f;
-        __syncwarp();
-        bool ok = true;
-        for (int c = 0; c < 6; ++c) {
-            if (lane == c) {
-                float d = Ls[7 * c];
-                for (int p = 0; p < c; ++p) d -= Ls[6 * c + p] * Ls[6 * c + p];
-                ok = d > 0.f;
-                d = sqrtf(fmaxf(d, 1e-30f));
-                Ls[7 * c] = d;
-                rinv[c] = 1.0f / d;
-            }
-            __syncwarp();
-            if (lane > c && lane < 6) {
-                float v = Ls[6 * lane + c];
-                for (int p = 0; p < c; ++p) v -= Ls[6 * lane + p] * Ls[6 * c + p];
-                Ls[6 * lane + c] = v * rinv[c];
-            }
-            __syncwarp();
-        }
-        if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
-        __syncwarp();
-        // the inverse, one column per lane: forward then back substitution
-        if (lane < 6) {
-            const int col = lane;
-            float y[6], xv[6];
-#pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                float v = r == col ? 1.0f : 0.0f;
-#pragma unroll
-                for (int p = 0; p < r; ++p) v -= Ls[6 * r + p] * y[p];
-                y[r] = v * rinv[r];
-            }
-#pragma unroll
-            for (int r = 5; r >= 0; --r) {
-                float v = y[r];
-#pragma unroll
-                for (int p = r + 1; p < 6; ++p) v -= Ls[6 * p + r] * xv[p];
-                xv[r] = v * rinv[r];
-            }
-#pragma unroll
-            for (int r = 0; r < 6; ++r) pose_blk[36 + 6 * r + col] = xv[r];
-        }
+        if (!pose_inverse6(Ls, rinv, prm.jitter, pose_blk + 36) && lane == 0) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
     } else if (t == 32) {
         const double Er = pri[0] + pri[1] + pri[2], Ep = pri[3] + pri[4] + pri[5];
         const double E = s[0] + ne[0] + ne[1] + Er + Ep + s[30];
@@ -865,8 +891,194 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restr
             stats->e_rot_prior = Er;
             stats->e_pos_prior = Ep;
             stats->n_valid = (int)s[1];
+            stats->lm_rejected = 0;
+            stats->lambda = prm.lambda;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Levenberg-Marquardt acceptance on the device (Sec. II.F solves Eq. 3 with
+// LM): the energy at the step's input against that of the last accepted point
+// ---------------------------------------------------------------------------
+
+__global__ void k_lm_reset(double *__restrict__ dmisc, int *__restrict__ misc, float lambda0)
+{
+    dmisc[DM_LAM] = lambda0;
+    misc[MI_LM_HAVE] = 0;
+    misc[MI_LM_REJECT] = 0;
+}
+
+// one thread: reject (restore the accepted point, lambda x 10, 1e-4 from 0) or
+// accept (store this point, lambda / 10 after the first); a step whose energy
+// is not finite is rejected too when an accepted point exists
+__global__ void k_lm_decide(double *__restrict__ dmisc, int *__restrict__ misc, ed_stats *stats)
+{
+    int rej = 0;
+    double lam = dmisc[DM_LAM];
+    const int st = misc[MI_STATUS];
+    if (st == ED_OK || st == ED_ERR_NONFINITE) {
+        const double E = dmisc[0];
+        const int have = misc[MI_LM_HAVE];
+        if (have && !(E <= dmisc[DM_EPREV])) {
+            rej = 1;
+            lam = lam > 0.0 ? 10.0 * lam : 1e-4;
+            for (int k = 0; k < 8; ++k) dmisc[k] = dmisc[DM_SAVED + k];
+            misc[MI_STATUS] = ED_OK;
+        } else if (st == ED_OK) {
+            if (have) lam *= 0.1;
+            dmisc[DM_EPREV] = E;
+            for (int k = 0; k < 8; ++k) dmisc[DM_SAVED + k] = dmisc[k];
+            misc[MI_LM_HAVE] = 1;
+        }
+        dmisc[DM_LAM] = lam;
+    }
+    misc[MI_LM_REJECT] = rej;
+    if (stats) {
+        if (rej) {
+            stats->energy = dmisc[0];
+            stats->e_data = dmisc[1];
+            stats->e_rot = dmisc[2];
+            stats->e_reg = dmisc[3];
+            stats->e_rot_prior = dmisc[4];
+            stats->e_pos_prior = dmisc[5];
+            stats->n_valid = (int)dmisc[6];
+            stats->e_corr = dmisc[7];
+        }
+        stats->lm_rejected = rej;
+        stats->lambda = lam;
+    }
+}
+
+struct LmSwapArgs {
+    float4 *bsr, *bsr_s;
+    long n_bsr4;
+    float4 *pnode, *pnode_s;
+    int n_pnode4;
+    float4 *x, *x_p;
+    int n_x4;
+    float *grad, *grad_s;
+    int n_grad;
+    float *pblk, *pblk_s;   // 36 floats
+    double *xm, *xm_p;      // n_xm doubles (0 without the FP64 master)
+    int n_xm;
+    double *pose, *pose_p;  // 6 doubles
+    const int *misc;
+};
+
+template <typename T>
+__device__ __forceinline__ void lm_move(T *live, T *saved, long n, bool rej, long i0, long stride)
+{
+    if (rej) {
+        for (long k = i0; k < n; k += stride) live[k] = saved[k];
+    } else {
+        for (long k = i0; k < n; k += stride) saved[k] = live[k];
+    }
+}
+
+// the undamped system and the parameters: stored on accept, restored on reject
+__global__ void __launch_bounds__(512) k_lm_swap(LmSwapArgs a)
+{
+    if (a.misc[MI_STATUS] != ED_OK) return;
+    const bool rej = a.misc[MI_LM_REJECT] != 0;
+    const long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x, st = (long)gridDim.x * blockDim.x;
+    lm_move(a.bsr, a.bsr_s, a.n_bsr4, rej, i0, st);
+    lm_move(a.pnode, a.pnode_s, a.n_pnode4, rej, i0, st);
+    lm_move(a.x, a.x_p, a.n_x4, rej, i0, st);
+    lm_move(a.grad, a.grad_s, a.n_grad, rej, i0, st);
+    lm_move(a.pblk, a.pblk_s, 36, rej, i0, st);
+    lm_move(a.xm, a.xm_p, a.n_xm, rej, i0, st);
+    lm_move(a.pose, a.pose_p, 6, rej, i0, st);
+}
+
+// damping of the diagonal blocks and of the pose block by (1 + lambda) on their
+// diagonals, and their block-Jacobi inverses (one warp per node, then the pose)
+__global__ void __launch_bounds__(32 * FIN_WARPS) k_lm_precond(const int *__restrict__ diag_pos, int m,
+                                                                float *__restrict__ bsr, float *__restrict__ minv,
+                                                                float *__restrict__ pose_blk,
+                                                                const double *__restrict__ dmisc, float jitter,
+                                                                int *__restrict__ misc)
+{
+    __shared__ float sH[FIN_WARPS][144];
+    __shared__ float sL[FIN_WARPS][144];
+    __shared__ float sRinv[FIN_WARPS][12];
+    __shared__ int s_tab[144];
+    fill_block_table(s_tab);
+    __syncthreads();
+    if (misc[MI_STATUS] != ED_OK) return;
+    const float f = 1.0f + (float)dmisc[DM_LAM];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * FIN_WARPS + wid;
+    float *H = sH[wid];
+    if (j < m) {
+        float *Hb = bsr + (long)diag_pos[j] * 144;
+        for (int e = lane; e < 144; e += 32) {
+            float h = Hb[e];
+            if (e % 13 == 0) {
+                h *= f;
+                Hb[e] = h;
+            }
+            H[e] = h;
+        }
+        __syncwarp();
+        if (!block_inverse12(H, sL[wid], sRinv[wid], s_tab, jitter, minv + (long)j * 144) && lane == 0)
+            atomicCAS(misc + MI_STATUS, 0, ED_ERR_BREAKDOWN);
+    } else if (j == m) {
+        for (int e = lane; e < 36; e += 32) {
+            float h = pose_blk[e];
+            if (e % 7 == 0) {
+                h *= f;
+                pose_blk[e] = h;
+            }
+            H[e] = h;
+        }
+        __syncwarp();
+        if (!pose_inverse6(H, sRinv[wid], jitter, pose_blk + 36) && lane == 0)
+            atomicCAS(misc + MI_STATUS, 0, ED_ERR_BREAKDOWN);
+    }
+}
+
+static ed_status lm_stage(ed_context *ctx, const ed_solver_params *prm, float *x, double *x_master, double *pose,
+                          ed_stats *stats, cudaStream_t st)
+{
+    const int m = ctx->m;
+    k_lm_decide<<<1, 1, 0, st>>>(ctx->dmisc, ctx->misc, stats); ed_note_launch();
+    LmSwapArgs la;
+    la.bsr = (float4 *)ctx->bsr;
+    la.bsr_s = (float4 *)ctx->bsr_s;
+    la.n_bsr4 = (long)ctx->nnzb * 36;
+    la.pnode = (float4 *)ctx->pnode;
+    la.pnode_s = (float4 *)ctx->pnode_s;
+    la.n_pnode4 = m * 18;
+    la.x = (float4 *)x;
+    la.x_p = (float4 *)ctx->x_prev;
+    la.n_x4 = m * 3;
+    la.grad = ctx->grad;
+    la.grad_s = ctx->grad_s;
+    la.n_grad = 12 * m + 6;
+    la.pblk = ctx->pose_blk;
+    la.pblk_s = ctx->pblk_s;
+    const bool mixed = prm->precision == ED_PRECISION_MIXED;
+    la.xm = mixed ? x_master : nullptr;
+    la.xm_p = ctx->xm_prev;
+    la.n_xm = mixed ? 12 * m : 0;
+    la.pose = pose;
+    la.pose_p = ctx->pose_prev;
+    la.misc = ctx->misc;
+    k_lm_swap<<<2 * ctx->num_sms, 512, 0, st>>>(la); ed_note_launch();
+    k_lm_precond<<<ed_div_up(m + 1, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(ctx->diag_pos, m, ctx->bsr, ctx->minv,
+                                                                       ctx->pose_blk, ctx->dmisc, prm->jitter,
+                                                                       ctx->misc); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}
+
+extern "C" ed_status ed_lm_reset(ed_context *ctx, float lambda0, cudaStream_t st)
+{
+    if (!ctx || !(lambda0 >= 0.f) || !isfinite(lambda0)) return ED_ERR_ARG;
+    k_lm_reset<<<1, 1, 0, st>>>(ctx->dmisc, ctx->misc, lambda0); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -912,7 +1124,8 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     ed_status s = check_frame(ctx, fr);
     if (s != ED_OK) return s;
     if (prm->n_pcg < 0 || (prm->precision == ED_PRECISION_MIXED && !x_master) ||
-        (prm->precision != ED_PRECISION_FP32 && prm->precision != ED_PRECISION_MIXED))
+        (prm->precision != ED_PRECISION_FP32 && prm->precision != ED_PRECISION_MIXED) ||
+        (prm->lm_accept != 0 && prm->lm_accept != 1))
         return ED_ERR_ARG;
     const int m = ctx->m;
     ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_STATUS, 0, sizeof(int), st));
@@ -951,7 +1164,8 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     fa.x4 = (const float4 *)x;
     fa.w_rot = prm->w_rot;
     fa.w_reg = prm->w_reg;
-    fa.lambda = prm->lambda;
+    const bool lm = prm->lm_accept != 0;
+    fa.lambda = lm ? 0.f : prm->lambda;
     fa.jitter = prm->jitter;
     fa.bsr = ctx->bsr;
     fa.grad = ctx->grad;
@@ -960,13 +1174,16 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     fa.node_energy = ctx->node_energy;
     fa.status = ctx->misc + MI_STATUS;
     ed_tm_begin(ctx, ED_KERNEL_FINALIZE, st);
-    k_finalize<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
+    (lm ? k_finalize<false> : k_finalize<true>)<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
     ED_LAUNCH_CHECK();
+    ed_solver_params pf = *prm;
+    if (lm) pf.lambda = 0.f;
     k_pose_final<<<1, PF_THREADS, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, ctx->node_energy, m, pose,
-                                           *prm, ctx->pose_blk,
+                                           pf, ctx->pose_blk,
                                     ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS, stats); ed_note_launch();
     ED_LAUNCH_CHECK();
+    if (lm) return lm_stage(ctx, prm, x, x_master, pose, stats, st);
     return ED_OK;
 }
 
