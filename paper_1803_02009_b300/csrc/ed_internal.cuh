@@ -17,7 +17,7 @@
 #define ED_PART_STRIDE 96      // floats per chunk partial (60 moments, or 12 + 72), chunk-major
 #define ED_K1_THREADS 256
 #define ED_K1_PART 32          // components of a point-kernel CTA partial (30 used)
-#define ED_PCG_PART 8          // doubles per PCG CTA partial
+#define ED_PCG_PART 16         // doubles per PCG CTA partial (at most)
 #define ED_MAX_BATCH_LAUNCH 32 // problems in one batched PCG launch
 #define ED_MAX_PCG_GRID 1184   // 8 x 148
 #define ED_PINNED_INTS (ED_MAX_PCG_GRID + 1 + 16)

@@ -6,17 +6,22 @@
 // triangles stored, row-major blocks) bordered by the 6 pose unknowns:
 // pose-node blocks C_j (6x12) and a 6x6 pose block.  Each CTA (one per SM)
 // owns a contiguous range of node rows, balanced by block count at graph
-// build; CTA 0 also owns the pose rows.  For the whole solve a CTA keeps in
-// shared memory its rows' blocks (as many as fit; the rest stream from L2),
-// block inverses, pose-node blocks and its slices of d, r, z, p, q.  Per PCG
-// iteration it forms the search direction of every block column it touches,
-// p_l = z_l + beta p_l(prev), from the owners' z and previous p (double
-// buffer), which it loads in the same round of loads as the reduction that
-// follows the second barrier; multiplies from shared memory (several thread
-// groups per row when a CTA has few rows) and meets the other CTAs at two
-// bounded grid barriers (after q = H p for p.q and the pose row, after
-// z = M^-1 r for r.z).  Reductions are per-CTA partials summed in a fixed
-// order by every CTA: deterministic.
+// build.  For the whole solve a CTA keeps in shared memory its rows' blocks
+// (as many as fit; the rest stream from L2), block inverses, pose-node
+// blocks, its slices of d, r, z, p, q, s and the z and p of every block
+// column its rows touch; the pose parts of the vectors are kept, identical,
+// in every CTA.
+//
+// One grid barrier per iteration.  After q = H p a CTA forms s = M^-1 q for
+// its rows and publishes it, together with its partials of p.q, q.z, q.s,
+// r.z, r.r, r.q, q.q and C p; after the barrier every CTA has the sums,
+// alpha = r.z / p.q, and beta from r'.z' = r.z - 2 alpha q.z + alpha^2 q.s
+// (z' = z - alpha s), and updates its block columns' z and p from the
+// owners' s exactly as the owners do (same fused multiply-adds, so every
+// copy agrees bit for bit).  r.z itself is summed afresh at every barrier,
+// so alpha never rests on the recurrence.  In exact arithmetic this is the
+// standard preconditioned CG.  Reductions are per-CTA partials summed in a
+// fixed order by every CTA: deterministic.
 #include <mutex>
 
 #include "ed_internal.cuh"
@@ -25,6 +30,7 @@
 #define PCG_SMEM_MAX_256 (100 * 1024)  // two 256-thread CTAs per SM
 
 #define PCG_RI 2                       // staged column items per thread held in registers
+#define PCG_NC 13                      // partials per CTA and iteration: p.q, q.z, q.s, r.z, r.r, r.q, q.q, C p
 
 // 12 threads per node row (one per output row of a 12x12 block)
 template <int NT> struct RowsPerPass { static constexpr int v = NT / 12; };
@@ -37,8 +43,9 @@ struct PcgArgs {
     int n_cache;             // blocks of each CTA cached in shared memory
     int max_rows, max_blk;   // shared-memory plan
     const float *bsr, *pnode, *minv, *pose_blk, *grad;
-    float *d, *z, *p0, *p1;  // global vectors (z and p are read by other CTAs)
-    double *part;            // [2][ED_PCG_PART][ED_MAX_PCG_GRID], component-major
+    float *d;                // the solution
+    float *z0, *s0, *s1;     // published z of the set-up, s = M^-1 q of even / odd iterations
+    double *part;            // [2][PCG_NC][ED_MAX_PCG_GRID] partials of even / odd iterations, component-major
     unsigned *bar;           // arrival count
     int *status;
     ed_stats *stats;
@@ -88,46 +95,55 @@ template <> struct PcgAcc<double> {
 // component w of the partials of CTA c
 __device__ __forceinline__ double *part_at(double *part, int w, int c) { return part + (size_t)w * ED_MAX_PCG_GRID + c; }
 
-// sums the NC components of all CTA partials: NT / NCP threads per
-// component stride over the CTAs (one round of loads for up to 4x that many
-// CTAs), then a fixed shuffle tree and a fixed-order sum of the warp results
-// that every thread forms itself (one CTA barrier), so every CTA and every
-// thread gets the same values.  `sh` must not be in use by other code
-// between two calls.
+// sums the NC components of all CTA partials: WPC warps per component (all
+// warps when NC is small) stride over the CTAs, components in rounds of
+// GROUPS when there are more components than warps; then a fixed shuffle
+// tree and a fixed-order sum of the warp results that every thread forms
+// itself (one CTA barrier), so every CTA and every thread gets the same
+// values.  `sh` must not be in use by other code between two calls.
 template <typename DT, int NT, int NC>
 __device__ __forceinline__ void sum_partials(const double *part, int nb, typename PcgAcc<DT>::T (*sh)[8],
                                              typename PcgAcc<DT>::T (&out)[NC])
 {
     typedef PcgAcc<DT> A;
-    constexpr int NCP = NC <= 1 ? 1 : NC <= 2 ? 2 : NC <= 4 ? 4 : 8;
-    constexpr int TPC = NT / NCP;       // threads per component
-    constexpr int WPC = TPC / 32;       // warps per component
-    const int lane = threadIdx.x & 31, w = threadIdx.x / TPC, sub = threadIdx.x % TPC;
-    typename A::T s = A::zero();
-    if (w < NC) {
-        const double *src = part + (size_t)w * ED_MAX_PCG_GRID;
-#pragma unroll 4
-        for (int c = sub; c < nb; c += TPC) s = A::add(s, A::from_double(__ldcg(src + c)));
-    }
+    constexpr int NWARP = NT / 32;
+    constexpr int WPC = NWARP >= NC ? NWARP / NC : 1;   // warps per component
+    constexpr int GROUPS = NWARP / WPC;                 // components per round
+    constexpr int ROUNDS = (NC + GROUPS - 1) / GROUPS;
+    static_assert(ROUNDS <= 8, "warp results of one component round per sh column");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int g = wid / WPC, wsub = wid - g * WPC;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
-    if (lane == 0) sh[threadIdx.x >> 5][0] = s;
+    for (int rd = 0; rd < ROUNDS; ++rd) {
+        const int c = rd * GROUPS + g;
+        typename A::T s = A::zero();
+        if (g < GROUPS && c < NC) {
+            const double *src = part + (size_t)c * ED_MAX_PCG_GRID;
+#pragma unroll 4
+            for (int k = wsub * 32 + lane; k < nb; k += WPC * 32) s = A::add(s, A::from_double(__ldcg(src + k)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
+        if (lane == 0) sh[wid][rd] = s;
+    }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
+        const int rd = c / GROUPS, gg = c - rd * GROUPS;
         typename A::T r = A::zero();
 #pragma unroll
-        for (int k = 0; k < WPC; ++k) r = A::add(r, sh[c * WPC + k][0]);
+        for (int k = 0; k < WPC; ++k) r = A::add(r, sh[gg * WPC + k][rd]);
         out[c] = r;
     }
 }
 
 // block reduction of NV values per thread: after one CTA barrier,
 // block_sum_get(c) gives component c (fixed order) to any thread that asks
-template <typename DT, int NT, int NV>
-__device__ __forceinline__ void block_sum_n(typename PcgAcc<DT>::T (&v)[NV], typename PcgAcc<DT>::T (*sh)[8])
+template <typename DT, int NT, int NV, int SW>
+__device__ __forceinline__ void block_sum_n(typename PcgAcc<DT>::T (&v)[NV], typename PcgAcc<DT>::T (*sh)[SW])
 {
     typedef PcgAcc<DT> A;
+    static_assert(NV <= SW, "one shared column per value");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -139,8 +155,8 @@ __device__ __forceinline__ void block_sum_n(typename PcgAcc<DT>::T (&v)[NV], typ
     __syncthreads();
 }
 
-template <typename DT, int NT>
-__device__ __forceinline__ typename PcgAcc<DT>::T block_sum_get(const typename PcgAcc<DT>::T (*sh)[8], int c)
+template <typename DT, int NT, int SW>
+__device__ __forceinline__ typename PcgAcc<DT>::T block_sum_get(const typename PcgAcc<DT>::T (*sh)[SW], int c)
 {
     typedef PcgAcc<DT> A;
     typename A::T s = A::zero();
@@ -150,7 +166,7 @@ __device__ __forceinline__ typename PcgAcc<DT>::T block_sum_get(const typename P
 
 // shared-memory carve of one CTA (in floats; every region a multiple of 4)
 struct PcgSmem {
-    size_t o_H, o_pb, o_po, o_lc, o_M, o_C, o_r, o_d, o_z, o_p, o_q, o_qs, total;
+    size_t o_H, o_pb, o_po, o_lc, o_M, o_C, o_r, o_d, o_z, o_p, o_q, o_s, o_qs, total;
 };
 
 __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncache, int nt)
@@ -158,8 +174,8 @@ __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncach
     PcgSmem L;
     size_t o = 0;
     L.o_H = o; o += (size_t)ncache * 144;
-    L.o_pb = o; o += (size_t)nblk * 12;            // z of the block columns, then p
-    L.o_po = o; o += (size_t)nblk * 12;            // previous p of the block columns
+    L.o_pb = o; o += (size_t)nblk * 12;            // p of the block columns
+    L.o_po = o; o += (size_t)nblk * 12;            // z of the block columns
     L.o_lc = o; o += ((size_t)nblk + 3) / 4 * 4;   // block column indices (int)
     L.o_M = o; o += (size_t)rows * 144;
     L.o_C = o; o += (size_t)rows * 72;
@@ -168,6 +184,7 @@ __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncach
     L.o_z = o; o += (size_t)rows * 12;
     L.o_p = o; o += (size_t)rows * 12;
     L.o_q = o; o += (size_t)rows * 12;
+    L.o_s = o; o += (size_t)rows * 12;
     L.o_qs = o; o += (size_t)(nt / 12) * 12;       // split partial products of q
     L.total = o;
     return L;
@@ -183,9 +200,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_flag;
-    __shared__ AT s_red[NT / 32][8];    // block reductions
-    __shared__ AT s_red2[NT / 32][8];   // sums of the CTA partials
-    __shared__ float s_pp[6], s_zp[6], s_rpose[6], s_dpose[6];
+    __shared__ AT s_red[NT / 32][PCG_NC];   // block reductions
+    __shared__ AT s_red2[NT / 32][8];       // sums of the CTA partials
+    // the pose parts of r, z, p, d: the same values in every CTA
+    __shared__ float s_rp[6], s_zp[6], s_pp[6], s_dp[6];
     __shared__ float s_Hpp[36], s_Mp[36];
 
     unsigned target = 0;
@@ -195,9 +213,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     const int b0 = a.row_ptr[r0], nblk = a.row_ptr[r1] - b0;
     const int ncache = min(nblk, a.n_cache);
     const PcgSmem L = pcg_smem_layout(a.max_rows, a.max_blk, a.n_cache, NT);
-    float *Hs = sm + L.o_H, *pb = sm + L.o_pb, *po = sm + L.o_po, *Ms = sm + L.o_M, *Cs = sm + L.o_C;
+    float *Hs = sm + L.o_H, *pb = sm + L.o_pb, *zb = sm + L.o_po, *Ms = sm + L.o_M, *Cs = sm + L.o_C;
     float *rs = sm + L.o_r, *ds = sm + L.o_d, *zs = sm + L.o_z, *ps = sm + L.o_p, *qs = sm + L.o_q;
-    float *qsplit = sm + L.o_qs;
+    float *ss = sm + L.o_s, *qsplit = sm + L.o_qs;
     int *lc = reinterpret_cast<int *>(sm + L.o_lc);
     const int t = threadIdx.x;
     const int grp = t / 12, rr = t % 12;
@@ -207,7 +225,6 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     const int rpp = ROWS_PER_PASS / S;   // rows per pass
     const int P = 12 * m;
     const float *Hpp = s_Hpp, *Mp = s_Mp;
-    double *part0 = a.part, *part1 = a.part + (size_t)ED_MAX_PCG_GRID * ED_PCG_PART;
 
     if (*(volatile int *)a.status != ED_OK) return;
 
@@ -244,6 +261,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         s_Hpp[t] = a.pose_blk[t];
         s_Mp[t] = a.pose_blk[36 + t];
     }
+    if (t < 6) {
+        s_rp[t] = -__ldg(a.grad + P + t);
+        s_dp[t] = 0.f;
+    }
     if (!ed_mbar_wait(&s_mbar[0], 0)) {
         atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
         ed_mbar_wait(&s_mbar[0], 0);
@@ -253,138 +274,120 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     __syncthreads();
     bool h_ready = false;
 
-    // z_j = Minv_j r_j for the own rows (thread = one output row); partials r.z, r.r
-    auto precond = [&](AT &rz, AT &rrs) {
+    // dst = M^-1 src for the own rows (thread = one output row of a node),
+    // also into gdst; f(element index, value) sees every result
+    auto apply_minv = [&](const float *src, float *dst, float *gdst, auto &&f) {
         for (int j0 = 0; j0 < rows; j0 += ROWS_PER_PASS) {
             const int jl = j0 + grp;
             if (in_grp && jl < rows) {
                 const float4 *mv = reinterpret_cast<const float4 *>(Ms + jl * 144 + rr * 12);
-                const float4 *rv = reinterpret_cast<const float4 *>(rs + jl * 12);
-                float zz = 0.f;
+                const float4 *sv = reinterpret_cast<const float4 *>(src + jl * 12);
+                float v = 0.f;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    const float4 m4 = mv[q], r4 = rv[q];
-                    zz += m4.x * r4.x + m4.y * r4.y + m4.z * r4.z + m4.w * r4.w;
+                    const float4 m4 = mv[q], s4 = sv[q];
+                    v += m4.x * s4.x + m4.y * s4.y + m4.z * s4.z + m4.w * s4.w;
                 }
-                const float rv1 = rs[jl * 12 + rr];
-                zs[jl * 12 + rr] = zz;
-                a.z[12 * (r0 + jl) + rr] = zz;
-                rz = A::madd(rz, rv1, zz);
-                rrs = A::madd(rrs, rv1, rv1);
+                const int e = jl * 12 + rr;
+                dst[e] = v;
+                gdst[12 * r0 + e] = v;
+                f(e, v);
             }
         }
     };
 
-    // pose rows (CTA 0, thread 0): z_p = Mp r_p; adds the pose terms of r.z and r.r
-    auto pose_precond = [&](AT &v1, AT &v2) {
-        for (int i = 0; i < 6; ++i) {
-            float zi = 0.f;
-            for (int k = 0; k < 6; ++k) zi += Mp[6 * i + k] * s_rpose[k];
-            a.z[P + i] = zi;
-            v1 = A::madd(v1, s_rpose[i], zi);
-            v2 = A::madd(v2, s_rpose[i], s_rpose[i]);
-        }
-    };
-
-    // The block columns' z and previous p from their owners, loaded in the same
-    // round as the reduction that follows each barrier: the first PCG_RI
-    // float4 items of every thread stay in registers until beta is known, the
-    // rest (large CTA shares) go through shared memory.
-    float4 zr[PCG_RI], pr[PCG_RI];
+    // ---- set-up: r = b, d = 0, z = M^-1 r (published for the CTAs whose
+    // block columns reach these rows), p = z; partial r.r for ||b|| ----
+    {
+        AT rr0 = A::zero();
+        apply_minv(rs, zs, a.z0, [&](int e, float) { rr0 = A::madd(rr0, rs[e], rs[e]); });
+        AT vv[1] = {rr0};
+        block_sum_n<DT, NT, 1>(vv, s_red);
+    }
+    if (t < 6) {
+        float zi = 0.f;
+        for (int k = 0; k < 6; ++k) zi += Mp[6 * t + k] * s_rp[k];
+        s_zp[t] = zi;
+        s_pp[t] = zi;
+    }
+    // (the partials of odd iterations hold the set-up's: iteration 0 writes the even ones
+    // while slower CTAs may still read these)
+    double *part_setup = a.part + (size_t)ED_MAX_PCG_GRID * PCG_NC;
+    if (t == 0) *part_at(part_setup, 0, cta) = A::to_double(block_sum_get<DT, NT>(s_red, 0));
+    if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+    // z of every block column from its owner; p = z
     const int n_items = nblk * 3;
-    auto stage_issue = [&](const float *pprev) {
+    for (int i = t; i < n_items; i += NT) {
+        const int lb = i / 3, q4 = i - 3 * lb;
+        const float4 z4 = __ldcg(reinterpret_cast<const float4 *>(a.z0 + 12 * lc[lb]) + q4);
+        reinterpret_cast<float4 *>(zb + (size_t)lb * 12)[q4] = z4;
+        reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] = z4;
+    }
+    for (int i = t; i < rows * 12; i += NT) ps[i] = zs[i];
+    float res0;
+    {
+        AT sums[1];
+        sum_partials<DT, NT, 1>(part_setup, nb, s_red2, sums);
+        AT v = sums[0];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v = A::madd(v, s_rp[i], s_rp[i]);
+        res0 = sqrtf(A::to_float(v));
+    }
+
+    // The search direction of every block column is kept here, in step with
+    // its owner: z_l <- z_l - alpha s_l, p_l <- z_l + beta p_l with the
+    // owner's published s = M^-1 q, so one grid barrier per iteration
+    // suffices.  The first PCG_RI float4 items of s per thread stay in
+    // registers from the load after the barrier to the update.
+    float4 sr[PCG_RI];
+    auto stage_issue = [&](const float *sg) {
 #pragma unroll
         for (int u = 0; u < PCG_RI; ++u) {
             const int i = t + u * NT;
             if (i < n_items) {
                 const int lb = i / 3, q4 = i - 3 * lb;
-                const int l = lc[lb];
-                zr[u] = __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l) + q4);
-                pr[u] = pprev ? __ldcg(reinterpret_cast<const float4 *>(pprev + 12 * l) + q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                sr[u] = __ldcg(reinterpret_cast<const float4 *>(sg + 12 * lc[lb]) + q4);
             }
         }
+    };
+    auto col_update = [&](float4 &z4, float4 &p4, const float4 s4, float alpha, float beta) {
+        z4 = make_float4(__fmaf_rn(-alpha, s4.x, z4.x), __fmaf_rn(-alpha, s4.y, z4.y), __fmaf_rn(-alpha, s4.z, z4.z),
+                         __fmaf_rn(-alpha, s4.w, z4.w));
+        p4 = make_float4(__fmaf_rn(beta, p4.x, z4.x), __fmaf_rn(beta, p4.y, z4.y), __fmaf_rn(beta, p4.z, z4.z),
+                         __fmaf_rn(beta, p4.w, z4.w));
+    };
+    auto stage_finish = [&](const float *sg, float alpha, float beta) {
+#pragma unroll
+        for (int u = 0; u < PCG_RI; ++u) {
+            const int i = t + u * NT;
+            if (i < n_items) {
+                const int lb = i / 3, q4 = i - 3 * lb;
+                float4 *zp4 = reinterpret_cast<float4 *>(zb + (size_t)lb * 12) + q4;
+                float4 *pp4 = reinterpret_cast<float4 *>(pb + (size_t)lb * 12) + q4;
+                float4 z4 = *zp4, p4 = *pp4;
+                col_update(z4, p4, sr[u], alpha, beta);
+                *zp4 = z4;
+                *pp4 = p4;
+            }
+        }
+        // large CTA shares: the remaining items load s now
         for (int i = t + PCG_RI * NT; i < n_items; i += NT) {
             const int lb = i / 3, q4 = i - 3 * lb;
-            const int l = lc[lb];
-            reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] =
-                __ldcg(reinterpret_cast<const float4 *>(a.z + 12 * l) + q4);
-            if (pprev)
-                reinterpret_cast<float4 *>(po + (size_t)lb * 12)[q4] =
-                    __ldcg(reinterpret_cast<const float4 *>(pprev + 12 * l) + q4);
-        }
-        if (t < 6) s_zp[t] = __ldcg(a.z + P + t);
-    };
-    // p_l = z_l + beta p_l(prev) for every staged item (beta unused at the first iteration)
-    auto stage_finish = [&](float beta, bool first) {
-#pragma unroll
-        for (int u = 0; u < PCG_RI; ++u) {
-            const int i = t + u * NT;
-            if (i < n_items) {
-                const int lb = i / 3, q4 = i - 3 * lb;
-                const float4 z4 = zr[u], p4 = pr[u];
-                reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] =
-                    first ? z4
-                          : make_float4(__fmaf_rn(beta, p4.x, z4.x), __fmaf_rn(beta, p4.y, z4.y),
-                                        __fmaf_rn(beta, p4.z, z4.z), __fmaf_rn(beta, p4.w, z4.w));
-            }
-        }
-        if (!first) {
-            for (int i = t + PCG_RI * NT; i < n_items; i += NT) {
-                const int lb = i / 3, q4 = i - 3 * lb;
-                float4 *b4 = reinterpret_cast<float4 *>(pb + (size_t)lb * 12) + q4;
-                const float4 z4 = *b4, p4 = reinterpret_cast<const float4 *>(po + (size_t)lb * 12)[q4];
-                *b4 = make_float4(__fmaf_rn(beta, p4.x, z4.x), __fmaf_rn(beta, p4.y, z4.y), __fmaf_rn(beta, p4.z, z4.z),
-                                  __fmaf_rn(beta, p4.w, z4.w));
-            }
+            const float4 s4 = __ldcg(reinterpret_cast<const float4 *>(sg + 12 * lc[lb]) + q4);
+            float4 *zp4 = reinterpret_cast<float4 *>(zb + (size_t)lb * 12) + q4;
+            float4 *pp4 = reinterpret_cast<float4 *>(pb + (size_t)lb * 12) + q4;
+            float4 z4 = *zp4, p4 = *pp4;
+            col_update(z4, p4, s4, alpha, beta);
+            *zp4 = z4;
+            *pp4 = p4;
         }
     };
 
-    // ---- set-up: r = b, d = 0, z = M^-1 r ----
-    {
-        AT rz = A::zero(), rrs = A::zero();
-        precond(rz, rrs);
-        AT vv[2] = {rz, rrs};
-        block_sum_n<DT, NT, 2>(vv, s_red);
-    }
-    if (t == 0) {
-        AT v1 = block_sum_get<DT, NT>(s_red, 0), v2 = block_sum_get<DT, NT>(s_red, 1);
-        if (cta == 0) {
-            for (int i = 0; i < 6; ++i) {
-                s_rpose[i] = -a.grad[P + i];
-                s_dpose[i] = 0.f;
-            }
-            pose_precond(v1, v2);
-        }
-        *part_at(part0, 0, cta) = A::to_double(v1);
-        *part_at(part0, 1, cta) = A::to_double(v2);
-    }
-    if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
-    stage_issue(nullptr);
-    // the scalars of the iteration live in every thread's registers (identical values)
-    AT rho, rr2s;
-    float res0, beta = 0.f;
-    {
-        AT sums[2];
-        sum_partials<DT, NT, 2>(part0, nb, s_red2, sums);
-        rho = sums[0];
-        rr2s = sums[1];
-        res0 = sqrtf(A::to_float(sums[1]));
-    }
-    float qp[6];   // the pose rows of q = H p (CTA 0 thread 0 uses them for the pose update)
-
+    float rr_last = res0 * res0;   // ||r||^2 of the last residual
     int it = 0;
     for (; it < a.n_iter; ++it) {
-        if (!(A::to_float(rho) > 0.f)) break;
-        if (a.tol > 0.f && sqrtf(A::to_float(rr2s)) <= a.tol * res0) break;
-        float *pnew = (it & 1) ? a.p1 : a.p0;
-        // ---- p = z + beta p(prev): block columns (staged), own rows (published), pose ----
-        stage_finish(beta, it == 0);
-        for (int i = t; i < rows * 12; i += NT) {
-            const float pv = it > 0 ? __fmaf_rn(beta, ps[i], zs[i]) : zs[i];
-            ps[i] = pv;
-            pnew[12 * r0 + i] = pv;
-        }
-        if (t < 6) s_pp[t] = it > 0 ? __fmaf_rn(beta, s_pp[t], s_zp[t]) : s_zp[t];
+        float *sg = (it & 1) ? a.s1 : a.s0;                       // published s = M^-1 q (double buffer)
+        double *part = a.part + (size_t)(it & 1) * ED_MAX_PCG_GRID * PCG_NC;   // partials (double buffer)
         __syncthreads();
         if (!h_ready) {   // the blocks, copied during the set-up
             if (!ed_mbar_wait(&s_mbar[1], 0)) {
@@ -394,9 +397,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             }
             h_ready = true;
         }
-        // ---- phase A: q = H p for the own rows (thread = one output row of one
-        // of the S splits of a row's blocks), partials p.q and C p ----
-        AT pq = A::zero();
+        // ---- q = H p for the own rows (thread = one output row of one of
+        // the S splits of a row's blocks), partials C p of the pose rows ----
         AT cp[6] = {A::zero(), A::zero(), A::zero(), A::zero(), A::zero(), A::zero()};
         for (int j0 = 0; j0 < rows; j0 += rpp) {
             const int jl = j0 + grp / S, sp = grp - (grp / S) * S;
@@ -427,79 +429,116 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                 for (int s = 0; s < 6; ++s) qv += C[12 * s + rr] * s_pp[s];
                 qs[jr * 12 + rr] = qv;
                 const float pv = ps[jr * 12 + rr];
-                pq = A::madd(pq, pv, qv);
 #pragma unroll
                 for (int s = 0; s < 6; ++s) cp[s] = A::madd(cp[s], C[12 * s + rr], pv);
             }
-            if (j0 + rpp < rows) __syncthreads();   // qsplit is reused by the next pass
+            __syncthreads();   // qsplit is reused by the next pass; q complete after the last
         }
+        // ---- s = M^-1 q for the own rows (published); partials of p.q, q.z,
+        // q.s, r.z, r.r, r.q, q.q over the own rows ----
         {
-            AT vv[7] = {pq, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
-            block_sum_n<DT, NT, 7>(vv, s_red);
-            if (t < 7) *part_at(part1, t, cta) = A::to_double(block_sum_get<DT, NT>(s_red, t));
+            AT pq = A::zero(), qz = A::zero(), qq2 = A::zero(), rz = A::zero(), r2 = A::zero(), rq = A::zero(),
+               q2 = A::zero();
+            apply_minv(qs, ss, sg, [&](int e, float sv) {
+                const float qv = qs[e], rv = rs[e], zv = zs[e];
+                pq = A::madd(pq, ps[e], qv);
+                qz = A::madd(qz, qv, zv);
+                qq2 = A::madd(qq2, qv, sv);
+                rz = A::madd(rz, rv, zv);
+                r2 = A::madd(r2, rv, rv);
+                rq = A::madd(rq, rv, qv);
+                q2 = A::madd(q2, qv, qv);
+            });
+            AT vv[PCG_NC] = {pq, qz, qq2, rz, r2, rq, q2, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
+            block_sum_n<DT, NT, PCG_NC>(vv, s_red);
+            if (t < PCG_NC) *part_at(part, t, cta) = A::to_double(block_sum_get<DT, NT>(s_red, t));
         }
         if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
-        // ---- phase B: alpha (every thread), d += alpha p, r -= alpha q, z = M^-1 r ----
-        float alpha;
+        stage_issue(sg);
+        // ---- every thread: the sums, the pose rows (q_p = sum C p + H_pp p_p,
+        // s_p = M_p q_p) and their terms, alpha, beta ----
+        float alpha, beta, qp[6], sp[6];
+        AT rq_t, q2_t;
         {
-            AT sums[7];
-            sum_partials<DT, NT, 7>(part1, nb, s_red2, sums);
-            AT pqt = sums[0];
+            AT sums[PCG_NC];
+            sum_partials<DT, NT, PCG_NC>(part, nb, s_red2, sums);
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                float qi = A::to_float(sums[1 + i]);
+                float qi = A::to_float(sums[7 + i]);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
                 qp[i] = qi;
-                pqt = A::madd(pqt, s_pp[i], qi);
             }
-            const float pqt_f = A::to_float(pqt);
-            if (!(pqt_f > 0.f)) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                float si = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) si += Mp[6 * i + k] * qp[k];
+                sp[i] = si;
+            }
+            AT pq = sums[0], qz = sums[1], qq2 = sums[2], rz = sums[3], r2 = sums[4];
+            rq_t = sums[5];
+            q2_t = sums[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                pq = A::madd(pq, s_pp[i], qp[i]);
+                qz = A::madd(qz, qp[i], s_zp[i]);
+                qq2 = A::madd(qq2, qp[i], sp[i]);
+                rz = A::madd(rz, s_rp[i], s_zp[i]);
+                r2 = A::madd(r2, s_rp[i], s_rp[i]);
+                rq_t = A::madd(rq_t, s_rp[i], qp[i]);
+                q2_t = A::madd(q2_t, qp[i], qp[i]);
+            }
+            // r.z and r.r of the current residual: the tests of the loop head
+            const float rho = A::to_float(rz);
+            rr_last = A::to_float(r2);
+            if (!(rho > 0.f)) break;
+            if (a.tol > 0.f && sqrtf(rr_last) <= a.tol * res0) break;
+            const float pqt = A::to_float(pq);
+            if (!(pqt > 0.f)) {
                 if (cta == 0 && t == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
                 break;
             }
-            alpha = A::to_float(rho) / pqt_f;
+            alpha = rho / pqt;
+            // r'.z' = r.z - 2 alpha q.z + alpha^2 q.s (z' = z - alpha s, M^-1 symmetric)
+            const float rho_next = rho - 2.f * alpha * A::to_float(qz) + alpha * alpha * A::to_float(qq2);
+            beta = rho_next / rho;
         }
+        // ---- updates: own rows, block columns, pose ----
         for (int i = t; i < rows * 12; i += NT) {
             ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
             rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
+            const float zn = __fmaf_rn(-alpha, ss[i], zs[i]);
+            zs[i] = zn;
+            ps[i] = __fmaf_rn(beta, ps[i], zn);
         }
-        __syncthreads();
-        {
-            AT rz2 = A::zero(), rr2 = A::zero();
-            precond(rz2, rr2);
-            AT vv[2] = {rz2, rr2};
-            block_sum_n<DT, NT, 2>(vv, s_red);
-        }
-        if (t == 0) {
-            AT w1 = block_sum_get<DT, NT>(s_red, 0), w2 = block_sum_get<DT, NT>(s_red, 1);
-            if (cta == 0) {
-                for (int i = 0; i < 6; ++i) {
-                    s_dpose[i] = __fmaf_rn(alpha, s_pp[i], s_dpose[i]);
-                    s_rpose[i] = __fmaf_rn(-alpha, qp[i], s_rpose[i]);
+        stage_finish(sg, alpha, beta);
+        __syncthreads();   // every thread has read s_pp, s_zp, s_rp above
+        if (t < 6) {
+            float qt = 0.f, st = 0.f;   // qp[t], sp[t] without a dynamic register index
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (i == t) {
+                    qt = qp[i];
+                    st = sp[i];
                 }
-                pose_precond(w1, w2);
-            }
-            *part_at(part0, 0, cta) = A::to_double(w1);
-            *part_at(part0, 1, cta) = A::to_double(w2);
+            s_dp[t] = __fmaf_rn(alpha, s_pp[t], s_dp[t]);
+            s_rp[t] = __fmaf_rn(-alpha, qt, s_rp[t]);
+            const float zn = __fmaf_rn(-alpha, st, s_zp[t]);
+            s_zp[t] = zn;
+            s_pp[t] = __fmaf_rn(beta, s_pp[t], zn);
         }
-        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
-        stage_issue(pnew);
-        {
-            AT sums[2];
-            sum_partials<DT, NT, 2>(part0, nb, s_red2, sums);
-            beta = A::to_float(sums[0]) / A::to_float(rho);
-            rho = sums[0];
-            rr2s = sums[1];
-        }
+        // ||r'||^2 = r.r - 2 alpha r.q + alpha^2 q.q (reported after the last iteration)
+        rr_last = rr_last - 2.f * alpha * A::to_float(rq_t) + alpha * alpha * A::to_float(q2_t);
     }
+    __syncthreads();
     // solution of the CTA's rows (and of the pose: CTA 0)
     for (int i = t; i < rows * 12; i += NT) a.d[12 * r0 + i] = ds[i];
-    if (cta == 0 && t < 6) a.d[P + t] = s_dpose[t];
+    if (cta == 0 && t < 6) a.d[P + t] = s_dp[t];
     if (cta == 0 && t == 0 && a.stats) {
         a.stats->pcg_iters = it;
         a.stats->pcg_res0 = (double)res0;
-        a.stats->pcg_res = sqrt(A::to_double(rr2s));
+        a.stats->pcg_res = sqrt((double)fmaxf(rr_last, 0.f));
     }
 }
 
@@ -624,15 +663,15 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     a.pose_blk = ctx->pose_blk;
     a.grad = ctx->grad;
     a.d = ctx->vec;
-    a.z = ctx->vec + 2 * P;
-    a.p0 = ctx->vec + 3 * P;
-    a.p1 = ctx->vec + 4 * P;
+    a.z0 = ctx->vec + 2 * P;
+    a.s0 = ctx->vec + 3 * P;
+    a.s1 = ctx->vec + 4 * P;
     a.part = ctx->pcg_part;
     a.bar = (unsigned *)(ctx->misc + MI_BAR);
     a.status = ctx->misc + MI_STATUS;
     a.stats = stats;
     // every vector is read as float4 rows: 16-byte alignment is required
-    const float *vv[4] = {a.d, a.z, a.p0, a.p1};
+    const float *vv[4] = {a.d, a.z0, a.s0, a.s1};
     for (int i = 0; i < 4; ++i)
         if ((uintptr_t)vv[i] & 15) return ED_ERR_STATE;
     if (((uintptr_t)a.bsr & 15) || ((uintptr_t)a.minv & 15)) return ED_ERR_STATE;
