@@ -129,20 +129,21 @@ static ed_status batch_enqueue(ed_batch *b, const ed_frame *frames, const ed_sol
         ed_context *gc[ED_MAX_BATCH_LAUNCH];
         const ed_solver_params *gp[ED_MAX_BATCH_LAUNCH];
         ed_stats *gs[ED_MAX_BATCH_LAUNCH];
+        float *gx[ED_MAX_BATCH_LAUNCH];
+        double *gxm[ED_MAX_BATCH_LAUNCH], *gpose[ED_MAX_BATCH_LAUNCH];
         for (int i = 0; i < n; ++i) {
             const int p = b->member[k0 + i];
             gc[i] = b->ctx[p];
             gp[i] = &params[p];
             gs[i] = stat_at(stats, p, it);
+            gx[i] = x[p];
+            gxm[i] = xm ? xm[p] : nullptr;
+            gpose[i] = pose[p];
         }
-        if ((s = ed_pcg_solve_batch(gc, &b->plan[g], gp, gs, st)) != ED_OK) return s;
+        if ((s = ed_pcg_solve_batch(gc, &b->plan[g], gp, gx, gxm, gpose, gs, st)) != ED_OK) return s;
     }
-    if ((s = fork()) != ED_OK) return s;
-    for (int p = 0; p < count && first == ED_OK; ++p)
-        first = ed_gn_post(b->ctx[p], &params[p], x[p], xm ? xm[p] : nullptr, pose[p], stat_at(stats, p, it),
-                           b->side[p % W]);
-    s = join();
-    return first != ED_OK ? first : s;
+    for (int p = 0; p < count; ++p) ed_gn_post(b->ctx[p]);
+    return ED_OK;
 }
 
 static ed_status check_args(const ed_batch *b, const ed_frame *frames, const ed_solver_params *params,

@@ -412,7 +412,6 @@ __device__ __forceinline__ bool ed_grid_sync(unsigned *count, int *status, unsig
                 }
             }
         }
-        if (*(volatile int *)status != ED_OK) ok = 0;
         *s_flag = ok;
     }
     __syncthreads();
@@ -605,15 +604,16 @@ __device__ __forceinline__ int ed_associate(const ed_warped &W, const float *__r
 
 ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st);
 ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
-ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st);
+ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,
+                       ed_stats *stats, cudaStream_t st);
 ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st);
 ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x, double *x_master,
                     double *pose, ed_stats *stats, cudaStream_t st);
-ed_status ed_gn_post(ed_context *ctx, const ed_solver_params *prm, float *x, double *x_master, double *pose,
-                     ed_stats *stats, cudaStream_t st);
+ed_status ed_gn_post(ed_context *ctx);
 ed_status ed_pcg_make_plan(const int *row_ptr_host, int m, int grid, int nt, ed_pcg_plan_t *pl, int *rows_start);
 ed_status ed_pcg_batch_plan(ed_context *const *ctxs, int count, int nt, int grid_total, ed_pcg_batch_plan_t *bp);
 ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t *bp, const ed_solver_params *const *prm,
-                             ed_stats *const *stats, cudaStream_t st);
+                             float *const *x, double *const *xm, double *const *pose, ed_stats *const *stats,
+                             cudaStream_t st);
 ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, const float *x,
                         const double *pose, int write_records, cudaStream_t st);

@@ -1081,30 +1081,6 @@ extern "C" ed_status ed_lm_reset(ed_context *ctx, float lambda0, cudaStream_t st
     return ED_OK;
 }
 
-// ---------------------------------------------------------------------------
-// update x += d (and the FP64 master in mixed precision), pose += d_pose
-// ---------------------------------------------------------------------------
-
-__global__ void k_update(int n, const float *__restrict__ d, float *__restrict__ x, double *__restrict__ xm,
-                         double *__restrict__ pose, const int *__restrict__ status, ed_stats *stats)
-{
-    const int st = *status;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && stats) stats->status = st;
-    if (st != ED_OK) return;
-    if (i < n) {
-        if (xm) {
-            const double v = xm[i] + (double)d[i];
-            xm[i] = v;
-            x[i] = (float)v;
-        } else {
-            x[i] += d[i];
-        }
-    } else if (i < n + 6) {
-        pose[i - n] += (double)d[i];
-    }
-}
-
 static ed_status check_frame(const ed_context *ctx, const ed_frame *fr)
 {
     if (!fr || !fr->depth || !fr->nmap || fr->intr.width <= 0 || fr->intr.height <= 0 ||
@@ -1187,14 +1163,10 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     return ED_OK;
 }
 
-// the update x += delta (and the pose) after the PCG solve
-ed_status ed_gn_post(ed_context *ctx, const ed_solver_params *prm, float *x, double *x_master, double *pose,
-                     ed_stats *stats, cudaStream_t st)
+// after the PCG solve (which also applied x += d, pose += d_pose): the
+// system of this step can be exported
+ed_status ed_gn_post(ed_context *ctx)
 {
-    const int n = 12 * ctx->m;
-    k_update<<<ed_div_up(n + 6, 256), 256, 0, st>>>(n, ctx->vec, x, prm->precision == ED_PRECISION_MIXED ? x_master : nullptr,
-                                                   pose, ctx->misc + MI_STATUS, stats); ed_note_launch();
-    ED_LAUNCH_CHECK();
     ctx->have_system = 1;
     return ED_OK;
 }
@@ -1204,8 +1176,8 @@ extern "C" ed_status ed_gn_step(ed_context *ctx, const ed_frame *fr, const ed_so
 {
     ed_status s = ed_gn_pre(ctx, fr, prm, x, x_master, pose, stats, st);
     if (s != ED_OK) return s;
-    if ((s = ed_pcg_solve(ctx, prm, stats, st)) != ED_OK) return s;
-    return ed_gn_post(ctx, prm, x, x_master, pose, stats, st);
+    if ((s = ed_pcg_solve(ctx, prm, x, x_master, pose, stats, st)) != ED_OK) return s;
+    return ed_gn_post(ctx);
 }
 
 // blocks (row-major BSR), pose-node blocks, pose block, J^T r, solution

@@ -46,6 +46,9 @@ struct PcgArgs {
     float *d;                // the solution
     float *z0, *s0, *s1;     // published z of the set-up, s = M^-1 q of even / odd iterations
     double *part;            // [2][PCG_NC][ED_MAX_PCG_GRID] partials of even / odd iterations, component-major
+    float *x;                // node parameters, x += d at the end (all CTAs passed every barrier)
+    double *xm;              // FP64 master copy (mixed precision) or NULL
+    double *pose;            // pose += d_pose (CTA 0)
     unsigned *bar;           // arrival count
     int *status;
     ed_stats *stats;
@@ -119,8 +122,17 @@ __device__ __forceinline__ void sum_partials(const double *part, int nb, typenam
         typename A::T s = A::zero();
         if (g < GROUPS && c < NC) {
             const double *src = part + (size_t)c * ED_MAX_PCG_GRID;
-#pragma unroll 4
-            for (int k = wsub * 32 + lane; k < nb; k += WPC * 32) s = A::add(s, A::from_double(__ldcg(src + k)));
+            // every load of the lane in flight before the first add (up to 8 per lane)
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = wsub * 32 + lane + u * WPC * 32;
+                v[u] = k < nb ? __ldcg(src + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (wsub * 32 + lane + u * WPC * 32 < nb) s = A::add(s, A::from_double(v[u]));
+            for (int k = wsub * 32 + lane + 8 * WPC * 32; k < nb; k += WPC * 32) s = A::add(s, A::from_double(__ldcg(src + k)));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
@@ -226,7 +238,14 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     const int P = 12 * m;
     const float *Hpp = s_Hpp, *Mp = s_Mp;
 
-    if (*(volatile int *)a.status != ED_OK) return;
+    // a failed solve leaves x and the pose untouched; CTA 0 reports the status
+    auto fail = [&]() {
+        if (cta == 0 && t == 0 && a.stats) a.stats->status = *(volatile int *)a.status;
+    };
+    if (*(volatile int *)a.status != ED_OK) {
+        fail();
+        return;
+    }
 
     // ---- the CTA's share of H, M^-1 and C into shared memory by bulk
     // asynchronous copies (inverses and pose-node blocks on mbarrier 0, needed
@@ -269,6 +288,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
         ed_mbar_wait(&s_mbar[0], 0);
         ed_mbar_wait(&s_mbar[1], 0);
+        fail();
         return;
     }
     __syncthreads();
@@ -314,7 +334,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     // while slower CTAs may still read these)
     double *part_setup = a.part + (size_t)ED_MAX_PCG_GRID * PCG_NC;
     if (t == 0) *part_at(part_setup, 0, cta) = A::to_double(block_sum_get<DT, NT>(s_red, 0));
-    if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+    if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
+        fail();
+        return;
+    }
     // z of every block column from its owner; p = z
     const int n_items = nblk * 3;
     for (int i = t; i < n_items; i += NT) {
@@ -384,6 +407,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     };
 
     float rr_last = res0 * res0;   // ||r||^2 of the last residual
+    bool breakdown = false;        // the same in every CTA: it follows from the summed p.q
     int it = 0;
     for (; it < a.n_iter; ++it) {
         float *sg = (it & 1) ? a.s1 : a.s0;                       // published s = M^-1 q (double buffer)
@@ -393,6 +417,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             if (!ed_mbar_wait(&s_mbar[1], 0)) {
                 atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
                 ed_mbar_wait(&s_mbar[1], 0);
+                fail();
                 return;
             }
             h_ready = true;
@@ -453,7 +478,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             block_sum_n<DT, NT, PCG_NC>(vv, s_red);
             if (t < PCG_NC) *part_at(part, t, cta) = A::to_double(block_sum_get<DT, NT>(s_red, t));
         }
-        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) return;
+        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
+            fail();
+            return;
+        }
         stage_issue(sg);
         // ---- every thread: the sums, the pose rows (q_p = sum C p + H_pp p_p,
         // s_p = M_p q_p) and their terms, alpha, beta ----
@@ -497,6 +525,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             const float pqt = A::to_float(pq);
             if (!(pqt > 0.f)) {
                 if (cta == 0 && t == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
+                breakdown = true;
                 break;
             }
             alpha = rho / pqt;
@@ -532,13 +561,33 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         rr_last = rr_last - 2.f * alpha * A::to_float(rq_t) + alpha * alpha * A::to_float(q2_t);
     }
     __syncthreads();
-    // solution of the CTA's rows (and of the pose: CTA 0)
-    for (int i = t; i < rows * 12; i += NT) a.d[12 * r0 + i] = ds[i];
-    if (cta == 0 && t < 6) a.d[P + t] = s_dp[t];
+    // solution of the CTA's rows (and of the pose: CTA 0), and the update
+    // x += d, pose += d_pose unless the solve broke down.  No wait follows the
+    // last barrier, so either every CTA gets here or none does: the update is
+    // never partial.
+    for (int i = t; i < rows * 12; i += NT) {
+        const size_t gi = 12 * (size_t)r0 + i;
+        const float dv = ds[i];
+        a.d[gi] = dv;
+        if (!breakdown) {
+            if (a.xm) {
+                const double v = a.xm[gi] + (double)dv;
+                a.xm[gi] = v;
+                a.x[gi] = (float)v;
+            } else {
+                a.x[gi] += dv;
+            }
+        }
+    }
+    if (cta == 0 && t < 6) {
+        a.d[P + t] = s_dp[t];
+        if (!breakdown) a.pose[t] += (double)s_dp[t];
+    }
     if (cta == 0 && t == 0 && a.stats) {
         a.stats->pcg_iters = it;
         a.stats->pcg_res0 = (double)res0;
         a.stats->pcg_res = sqrt((double)fmaxf(rr_last, 0.f));
+        a.stats->status = *(volatile int *)a.status;
     }
 }
 
@@ -645,8 +694,13 @@ ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st)
 }
 
 static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const int *cta_rows,
-                               const ed_solver_params *prm, ed_stats *stats, PcgArgs &a)
+                               const ed_solver_params *prm, float *x, double *xm, double *pose, ed_stats *stats,
+                               PcgArgs &a)
 {
+    if (!x || !pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
+    a.x = x;
+    a.xm = prm->precision == ED_PRECISION_MIXED ? xm : nullptr;
+    a.pose = pose;
     const size_t P = ctx->vec_stride;
     a.m = ctx->m;
     a.n_iter = prm->n_pcg;
@@ -693,12 +747,13 @@ static cudaError_t launch_coop(const void *fn, int grid, int nt, void **args, si
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, ed_stats *stats, cudaStream_t st)
+ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,
+                       ed_stats *stats, cudaStream_t st)
 {
     const bool mixed = prm->precision == ED_PRECISION_MIXED;
     if (ctx->pcg.grid <= 0) return ED_ERR_STATE;
     PcgArgs a;
-    ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, stats, a);
+    ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, x, xm, pose, stats, a);
     if (s != ED_OK) return s;
     ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_BAR, 0, 2 * sizeof(int), st));
     void *args[] = {&a};
@@ -774,7 +829,8 @@ ed_status ed_pcg_batch_plan(ed_context *const *ctxs, int count, int nt, int grid
 
 // one persistent launch for the PCG solves of a planned group of problems
 ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t *bp, const ed_solver_params *const *prm,
-                             ed_stats *const *stats, cudaStream_t st)
+                             float *const *x, double *const *xm, double *const *pose, ed_stats *const *stats,
+                             cudaStream_t st)
 {
     const int count = bp->count;
     const bool mixed = prm[0]->precision == ED_PRECISION_MIXED;
@@ -784,7 +840,8 @@ ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t 
     for (int p = 0; p <= count; ++p) b.cta_first[p] = bp->cta_first[p];
     for (int p = 0; p < count; ++p) {
         if ((prm[p]->precision == ED_PRECISION_MIXED) != mixed) return ED_ERR_ARG;
-        ed_status s = pcg_fill_args(ctxs[p], bp->plan[p], ctxs[p]->pcg_rows_b, prm[p], stats[p], b.probs[p]);
+        ed_status s = pcg_fill_args(ctxs[p], bp->plan[p], ctxs[p]->pcg_rows_b, prm[p], x[p], xm[p], pose[p], stats[p],
+                                    b.probs[p]);
         if (s != ED_OK) return s;
         ED_CUDA_TRY(cudaMemsetAsync(ctxs[p]->misc + MI_BAR, 0, 2 * sizeof(int), st));
     }
