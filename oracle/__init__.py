@@ -94,6 +94,11 @@ def _declare(L):
     L.or_fuse.argtypes = [_fp, _fp, _fp, _ip, C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_float, C.c_float, C.c_float,
                           C.c_float, C.c_int, C.c_int, C.POINTER(_FuseParams), C.c_int, _fp, _fp, _fp, _ip, _ip]
     L.or_fuse.restype = C.c_int
+    L.or_downsample.argtypes = [_fp, _fp, _fp, _ip, C.c_int, C.c_float, C.c_double, C.c_double, C.c_int, _fp, _fp,
+                                _fp, _ip, C.POINTER(C.c_uint32)]
+    L.or_downsample.restype = C.c_int
+    L.or_depth_error.argtypes = [_fp, C.c_int, _fp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, C.c_int, _dp]
+    L.or_depth_error.restype = None
 
 
 def _f(a):
@@ -474,3 +479,63 @@ def fuse(pos, nrm, col, tstamp, wpos, wnrm, depth, nmap, color, intr, F: FusePar
     if n < 0:
         raise RuntimeError("fuse capacity exceeded")
     return po[:n], no[:n], co[:n], to[:n], reg
+
+
+def downsample(pos, nrm, col, tstamp, box, omega_max=20.0, tau_weight=3.0, capacity=None):
+    """Box downsampling of the model (Sec. III.A, Alg. 3): returns (pos, nrm,
+    col, t, box keys) of the merged points in increasing key order."""
+    pos, nrm, col, tstamp = _f(pos), _f(nrm), _f(col), _i(tstamp)
+    n = pos.shape[0]
+    cap = n if capacity is None else int(capacity)
+    po = np.zeros((max(cap, 1), 4), np.float32)
+    no = np.zeros_like(po)
+    co = np.zeros_like(po)
+    to = np.zeros(max(cap, 1), np.int32)
+    ko = np.zeros(max(cap, 1), np.uint32)
+    k = lib().or_downsample(_p(pos, _fp), _p(nrm, _fp), _p(col, _fp), _p(tstamp, _ip), n, float(np.float32(box)),
+                            float(omega_max), float(tau_weight), cap, _p(po, _fp), _p(no, _fp), _p(co, _fp),
+                            _p(to, _ip), ko.ctypes.data_as(C.POINTER(C.c_uint32)))
+    if k == -1:
+        raise RuntimeError("downsample capacity exceeded")
+    if k == -2:
+        raise RuntimeError("downsample box grid too large")
+    return po[:k], no[:k], co[:k], to[:k], ko[:k]
+
+
+def depth_error(wpos, depth, intr):
+    """Back-projection error of warped model points against a depth image
+    (Sec. III): (mean |z - D|, count, max |z - D|, rms) over the pixels that
+    keep a point (nearest z, then lowest index) and have D > 0."""
+    fx, fy, cx, cy, W, H = intr
+    wpos, depth = _f(wpos), _f(depth)
+    out = np.zeros(4)
+    lib().or_depth_error(_p(wpos, _fp), wpos.shape[0], _p(depth, _fp), fx, fy, cx, cy, W, H, _p(out, _dp))
+    cnt = out[1]
+    return (out[0] / cnt if cnt else 0.0), int(cnt), out[2], (math.sqrt(out[3] / cnt) if cnt else 0.0)
+
+
+def track_frame(model, depth, color, intr, radius, max_nodes, box, n_gn, n_pcg, frame_index, normal_half_width,
+                truth_depth=None, prior=(0.0, 0.0, 0.0, 0.0, 0.0, 0.0), fuse_params=None, capacity=None):
+    """One frame of Algorithm 2 with Algorithm 3: the target normals, nodes
+    sampled afresh on the current model (Alg. 2 step 5) with identity
+    parameters, n_gn Gauss-Newton steps (block-Jacobi PCG, n_pcg iterations),
+    the final warp, the back-projection error against `truth_depth` (default
+    the observation), fusion (Alg. 1-2, Eqs. fusion1-4) and box downsampling
+    (Sec. III.A).  `model` = (pos, nrm, col, t); returns (new model, info)."""
+    pos, nrm, col, t = model
+    fx, fy, cx, cy, W, H = intr
+    nm = normals(depth, intr, normal_half_width)
+    G = build_graph(pos, radius=radius, max_nodes=max_nodes, K=4, KG=4, mode=0, sigma=radius)
+    P = Problem(pos, nrm, G, depth, nm, intr, np.asarray(prior, float))
+    x, pose, hist, st = gn_solve(P, P.identity_x(), np.asarray(prior, float), n_gn, n_pcg)
+    wp, wn, _ = warp(P, x, pose)
+    wp4 = np.concatenate([wp, pos[:, 3:4]], 1).astype(np.float32)
+    wn4 = np.concatenate([wn, nrm[:, 3:4]], 1).astype(np.float32)
+    err = depth_error(wp4, truth_depth if truth_depth is not None else depth, intr)
+    F = dataclasses.replace(fuse_params or FuseParams(), frame=int(frame_index))
+    cap = capacity if capacity is not None else pos.shape[0] + W * H
+    fpos, fnrm, fcol, ft, _ = fuse(pos, nrm, col, t, wp4, wn4, depth, nm, color, intr, F, cap)
+    dpos, dnrm, dcol, dt, _ = downsample(fpos, fnrm, fcol, ft, box, F.omega_max, F.tau_weight)
+    info = dict(nodes=G.g.shape[0], fused=fpos.shape[0], model=dpos.shape[0], status=st, energy=hist,
+                error_mean_mm=err[0], error_pixels=err[1], error_max_mm=err[2], error_rms_mm=err[3], x=x, pose=pose)
+    return (dpos, dnrm, dcol, dt), info

@@ -10,10 +10,12 @@
  * double precision, with no blocking or fusion:
  *   Sec. II.D  Eq. (1) warp, Eq. (2) skinning weight, node sampling
  *   Sec. II.E  Eq. (3) energy: E_rot, E_reg, E_data (+ visibility gate),
- *              E_r / E_p pose priors (E_corr is not part of this path)
+ *              E_r / E_p pose priors, E_corr key correspondences
  *   Sec. II.F  Levenberg-Marquardt / Gauss-Newton step
  *   Sec. II.G  Algorithm 1 (point-to-depth registration), Algorithm 2
- *              (deform, register, fuse, lift, delete), fusion Eqs. (fusion1-4)
+ *              (deform, register, fuse, lift, delete), fusion Eqs. (fusion1-4),
+ *              Algorithm 3 (box downsampling, Sec. III.A)
+ *   Sec. III   back-projection error (projected model image - depth image)
  *
  * Integer decisions (projection to a pixel, nearest-node keys, the
  * visibility / registration gates, the z-buffer) are taken in FP32 by the
@@ -1376,6 +1378,159 @@ int or_fuse(const float *pos, const float *nrm, const float *col, const int *tst
     }
     free(zb); free(reg); free(fused); free(pix_of);
     return n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Point-cloud downsampling (Sec. III.A "a fixed box ... average points fill  */
+/* inside each 3D box"; Alg. 3, first line)                                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    uint32_t key;
+    int idx;
+} or_key_idx;
+
+static int cmp_key_idx(const void *a, const void *b)
+{
+    const or_key_idx *x = (const or_key_idx *)a, *y = (const or_key_idx *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+/*
+ * Boxes of edge `box` anchored at the minimum of the points' bounding box.
+ * Box index per axis in FP32: floor((x - min) / box) (one subtraction, one
+ * division); boxes per axis floor((max - min) / box) + 1; key = ix + nx (iy +
+ * ny iz).  The points of one box become one point (reading: the paper
+ * averages the points in a box and says nothing of the other fields; here
+ * the average is weighted by the fusion weight omega as in Eqs. fusion1-4,
+ * the normal is the normalised weighted sum, the merged weight the capped sum
+ * min(sum omega, omega_max), the time stamp the latest, the stability flag
+ * omega >= tau_weight).  Output in increasing key order; returns the count,
+ * -1 past capacity, -2 when the box grid has 2^32 boxes or more.
+ */
+int or_downsample(const float *pos, const float *nrm, const float *col, const int *tstamp, int n, float box,
+                  double omega_max, double tau_weight, int capacity, float *pos_out, float *nrm_out, float *col_out,
+                  int *t_out, uint32_t *key_out)
+{
+    if (n <= 0) return 0;
+    float mn[3], mx[3];
+    for (int d = 0; d < 3; ++d) { mn[d] = pos[d]; mx[d] = pos[d]; }
+    for (int i = 1; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            float v = pos[4 * (size_t)i + d];
+            if (v < mn[d]) mn[d] = v;
+            if (v > mx[d]) mx[d] = v;
+        }
+    long dims[3];
+    for (int d = 0; d < 3; ++d) {
+        float ext = mx[d] - mn[d];
+        float q = ext / box;
+        dims[d] = (long)floorf(q) + 1;
+    }
+    if ((double)dims[0] * (double)dims[1] * (double)dims[2] >= 4294967296.0) return -2;
+    or_key_idx *ki = (or_key_idx *)malloc(sizeof(or_key_idx) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        long c[3];
+        for (int d = 0; d < 3; ++d) {
+            float rel = pos[4 * (size_t)i + d] - mn[d];
+            float q = rel / box;
+            c[d] = (long)floorf(q);
+            if (c[d] > dims[d] - 1) c[d] = dims[d] - 1;
+        }
+        ki[i].key = (uint32_t)(c[0] + dims[0] * (c[1] + dims[1] * c[2]));
+        ki[i].idx = i;
+    }
+    qsort(ki, (size_t)n, sizeof(or_key_idx), cmp_key_idx);
+    int out = 0;
+    for (int a = 0; a < n;) {
+        int b = a;
+        while (b < n && ki[b].key == ki[a].key) ++b;
+        double sw = 0, sp[3] = {0, 0, 0}, sn[3] = {0, 0, 0}, sc[4] = {0, 0, 0, 0};
+        int tmax = tstamp[ki[a].idx];
+        for (int k = a; k < b; ++k) {
+            int i = ki[k].idx;
+            double w = pos[4 * (size_t)i + 3];
+            sw += w;
+            for (int d = 0; d < 3; ++d) {
+                sp[d] += w * pos[4 * (size_t)i + d];
+                sn[d] += w * nrm[4 * (size_t)i + d];
+            }
+            for (int d = 0; d < 4; ++d) sc[d] += w * col[4 * (size_t)i + d];
+            if (tstamp[i] > tmax) tmax = tstamp[i];
+        }
+        if (!(sw > 0)) {   /* no weight in the box: a plain average */
+            sw = 0;
+            for (int d = 0; d < 3; ++d) sp[d] = sn[d] = 0;
+            for (int d = 0; d < 4; ++d) sc[d] = 0;
+            for (int k = a; k < b; ++k) {
+                int i = ki[k].idx;
+                sw += 1.0;
+                for (int d = 0; d < 3; ++d) { sp[d] += pos[4 * (size_t)i + d]; sn[d] += nrm[4 * (size_t)i + d]; }
+                for (int d = 0; d < 4; ++d) sc[d] += col[4 * (size_t)i + d];
+            }
+        }
+        if (out >= capacity) { free(ki); return -1; }
+        double wsum = 0;
+        for (int k = a; k < b; ++k) wsum += pos[4 * (size_t)ki[k].idx + 3];
+        double w_out = wsum < omega_max ? wsum : omega_max;
+        double len = sqrt(sn[0] * sn[0] + sn[1] * sn[1] + sn[2] * sn[2]);
+        for (int d = 0; d < 3; ++d) {
+            pos_out[4 * (size_t)out + d] = (float)(sp[d] / sw);
+            nrm_out[4 * (size_t)out + d] = (float)(len > 0 ? sn[d] / len : 0.0);
+        }
+        pos_out[4 * (size_t)out + 3] = (float)w_out;
+        nrm_out[4 * (size_t)out + 3] = w_out >= tau_weight ? 1.0f : 0.0f;
+        for (int d = 0; d < 4; ++d) col_out[4 * (size_t)out + d] = (float)(sc[d] / sw);
+        t_out[out] = tmax;
+        if (key_out) key_out[out] = ki[a].key;
+        ++out;
+        a = b;
+    }
+    free(ki);
+    return out;
+}
+
+/*
+ * Back-projection error (Sec. III: the projected model image minus the
+ * observed depth image).  The model points (warped into the frame) are
+ * projected by the FP32 rule P; a pixel keeps the point of smallest z, then
+ * of lowest index; over the pixels that keep a point and have D > 0:
+ * out = (sum |z - D|, count, max |z - D|, sum (z - D)^2).
+ */
+void or_depth_error(const float *wpos, int n, const float *depth, float fx, float fy, float cx, float cy, int W,
+                    int H, double *out)
+{
+    size_t npx = (size_t)W * H;
+    uint64_t *zb = (uint64_t *)malloc(sizeof(uint64_t) * npx);
+    for (size_t q = 0; q < npx; ++q) zb[q] = UINT64_MAX;
+    for (int i = 0; i < n; ++i) {
+        const float *p = wpos + 4 * (size_t)i;
+        int u, v;
+        if (!project_f32(p[0], p[1], p[2], fx, fy, cx, cy, W, H, &u, &v)) continue;
+        uint32_t zbits;
+        memcpy(&zbits, &p[2], 4);
+        uint64_t key = ((uint64_t)zbits << 32) | (uint32_t)i;
+        size_t q = (size_t)v * W + u;
+        if (key < zb[q]) zb[q] = key;
+    }
+    double sa = 0, cnt = 0, mx = 0, s2 = 0;
+    for (size_t q = 0; q < npx; ++q) {
+        if (zb[q] == UINT64_MAX) continue;
+        double D = depth[q];
+        if (!(D > 0)) continue;
+        double z = wpos[4 * (size_t)(zb[q] & 0xffffffffu) + 2];
+        double e = fabs(z - D);
+        sa += e;
+        cnt += 1;
+        if (e > mx) mx = e;
+        s2 += (z - D) * (z - D);
+    }
+    out[0] = sa;
+    out[1] = cnt;
+    out[2] = mx;
+    out[3] = s2;
+    free(zb);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -83,6 +83,16 @@ CONFIGS = {
         name="tissue_1280x720_n4096", W=1280, H=720, fx=1050.0, fy=1050.0, cx=640.0, cy=360.0,
         n_bumps=8, bump_amp=(1.0, 3.0), bump_width=(5.0, 15.0), node_mode="poisson",
         node_count=4096, n_gn=10, n_pcg=20, normal_half_width=32),
+    # push sequences (static camera, one 2-3 mm push per frame): 160x120 for the
+    # oracle's lock-step tests, 640x480 / 2048 nodes for the benchmark
+    "push_160x120": SceneConfig(
+        name="push_160x120", W=160, H=120, fx=131.25, fy=131.25, cx=80.0, cy=60.0,
+        n_bumps=0, bump_amp=(0.0, 0.0), bump_width=(10.0, 10.0), rot_deg=0.0, trans_mm=0.0,
+        node_mode="poisson", node_count=128, n_gn=5, n_pcg=10, normal_half_width=4),
+    "push_640x480_n2048": SceneConfig(
+        name="push_640x480_n2048", W=640, H=480, fx=525.0, fy=525.0, cx=320.0, cy=240.0,
+        n_bumps=0, bump_amp=(0.0, 0.0), bump_width=(10.0, 10.0), rot_deg=0.0, trans_mm=0.0,
+        node_mode="poisson", node_count=2048, n_gn=10, n_pcg=20, normal_half_width=16),
     # 320x240 member size of the batched workload
     "tissue_320x240": SceneConfig(
         name="tissue_320x240", W=320, H=240, fx=262.5, fy=262.5, cx=160.0, cy=120.0,
@@ -333,3 +343,83 @@ def make_keypoints(scene: Scene, count: int = 500, seed: int = 1, noise_mm: floa
     tgt = scene.gt_positions()[sel] + rng.normal(0.0, noise_mm, (len(sel), 3))
     tgt4 = np.concatenate([tgt, np.ones((len(sel), 1))], axis=1).astype(np.float32)
     return kp, tgt4, sel
+
+
+# ----------------------------------------------------------------------------
+# push sequence (a synthetic analogue of the simulation experiment, Sec. III.D)
+# ----------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class PushFrame:
+    index: int                 # frame number (1, 2, ...)
+    depth: np.ndarray          # float32 [H, W] noisy observation, 0 = hole
+    depth_clean: np.ndarray    # float32 [H, W] noise-free ray cast (ground truth)
+    color: np.ndarray          # float32 [H, W, 4]
+    bumps: Bumps               # cumulative deformation of the rest surface up to this frame
+
+
+@dataclasses.dataclass
+class PushSequence:
+    cfg: SceneConfig
+    seed: int
+    intr: Tuple[float, float, float, float, int, int]
+    model_pos: np.ndarray      # float32 [N, 4] frame-0 model, w = fusion weight
+    model_nrm: np.ndarray      # float32 [N, 4] w = stability flag
+    model_col: np.ndarray      # float32 [N, 4]
+    model_t: np.ndarray        # int32 [N] time stamps (0)
+    frames: List[PushFrame]
+
+
+def make_push_sequence(cfg: SceneConfig | str, n_frames: int, seed: int = 1, push_amp=(2.0, 3.0),
+                       push_width=(5.0, 15.0)) -> PushSequence:
+    """A tissue surface seen by a static camera and pushed once per frame.
+
+    Frame 0 is the rest surface h (its valid pixels, at their noisy depth,
+    make the initial model, as in make_scene).  Frame k adds one push to the
+    deformation of frame k-1: a Gaussian dent or bulge of amplitude
+    U(push_amp) mm with a random sign, width U(push_width) mm, centred in the
+    central 60% of the field of view.  Every frame is ray cast in FP64 (noise
+    N(0, noise_mm) and Bernoulli(p_hole) holes on the observation; the clean
+    depth is kept as ground truth)."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    ss = np.random.SeedSequence([seed, cfg.W, cfg.H, 77])
+    rng_push, rng_noise, rng_hole = [np.random.default_rng(s) for s in ss.spawn(3)]
+    ext_x = (0.0 - cfg.cx) / cfg.fx * Z0, (cfg.W - cfg.cx) / cfg.fx * Z0
+    ext_y = (0.0 - cfg.cy) / cfg.fy * Z0, (cfg.H - cfg.cy) / cfg.fy * Z0
+    I3, t0 = np.eye(3), np.zeros(3)
+
+    z0, qx0, qy0 = raycast(cfg, None, I3, t0)
+    src = z0 + rng_noise.normal(0.0, cfg.noise_mm, z0.shape)
+    src[rng_hole.random(src.shape) < cfg.p_hole] = 0.0
+    src32 = src.astype(np.float32)
+    a, b = _rays(cfg)
+    pix = np.nonzero(src32.reshape(-1) > 0)[0]
+    dval = src32.reshape(-1)[pix].astype(np.float64)
+    ar, br = a.reshape(-1)[pix], b.reshape(-1)[pix]
+    pos = np.stack([ar * dval, br * dval, dval, np.full_like(dval, cfg.model_weight)], axis=1)
+    qx, qy = qx0.reshape(-1)[pix], qy0.reshape(-1)[pix]
+    gx, gy = h_base_grad(qx, qy)
+    nrm = np.stack([gx, gy, -np.ones_like(gx)], axis=1)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    nrm4 = np.concatenate([nrm, np.ones((nrm.shape[0], 1))], axis=1)
+    col = texture(qx, qy)
+
+    amp, xc, yc, wid = [], [], [], []
+    frames = []
+    for k in range(1, n_frames + 1):
+        sgn = 1.0 if rng_push.random() < 0.5 else -1.0
+        amp.append(sgn * rng_push.uniform(push_amp[0], push_amp[1]))
+        wid.append(rng_push.uniform(push_width[0], push_width[1]))
+        xc.append(rng_push.uniform(0.2, 0.8) * (ext_x[1] - ext_x[0]) + ext_x[0])
+        yc.append(rng_push.uniform(0.2, 0.8) * (ext_y[1] - ext_y[0]) + ext_y[0])
+        bumps = Bumps(np.array(amp), np.array(xc), np.array(yc), np.array(wid))
+        zk, qxk, qyk = raycast(cfg, bumps, I3, t0)
+        obs = zk + rng_noise.normal(0.0, cfg.noise_mm, zk.shape)
+        obs[rng_hole.random(obs.shape) < cfg.p_hole] = 0.0
+        frames.append(PushFrame(index=k, depth=obs.astype(np.float32), depth_clean=zk.astype(np.float32),
+                                color=texture(qxk, qyk).astype(np.float32), bumps=bumps))
+    return PushSequence(cfg=cfg, seed=seed, intr=(cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.W, cfg.H),
+                        model_pos=pos.astype(np.float32), model_nrm=nrm4.astype(np.float32),
+                        model_col=col.astype(np.float32), model_t=np.zeros(pix.shape[0], np.int32), frames=frames)

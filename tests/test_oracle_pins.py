@@ -590,3 +590,119 @@ def test_rigid_motion_recovered_with_consistent_keypoints():
     assert st == 0
     assert np.abs(pose - pr["pose"]).max() < 1e-9
     assert np.abs(x - P.identity_x()).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# model maintenance: box downsampling (Sec. III.A, Alg. 3), back-projection
+# error (Sec. III)
+# ----------------------------------------------------------------------------
+
+def _lattice(nx, ny, nz, box, rng, jitter=0.3):
+    """One point inside each box of an nx x ny x nz grid of edge `box` whose
+    origin is a corner point, so the bounding box starts at the origin."""
+    ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    c = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1).astype(np.float64)
+    off = 0.5 + rng.uniform(-jitter, jitter, c.shape)
+    off[0] = 0.0          # the first point sits on the origin (the bbox minimum)
+    p = (c + off) * box
+    return c, p
+
+
+def test_downsample_one_point_per_box_keeps_every_point():
+    rng = np.random.default_rng(3)
+    box = 0.5
+    c, p = _lattice(5, 4, 3, box, rng)
+    n = p.shape[0]
+    perm = rng.permutation(n)
+    pos = np.concatenate([p[perm], rng.uniform(1, 4, (n, 1))], 1).astype(np.float32)
+    nrm = np.concatenate([rng.normal(size=(n, 3)), np.ones((n, 1))], 1)
+    nrm[:, :3] /= np.linalg.norm(nrm[:, :3], axis=1, keepdims=True)
+    nrm = nrm.astype(np.float32)
+    col = rng.random((n, 4)).astype(np.float32)
+    t = rng.integers(0, 9, n).astype(np.int32)
+    po, no, co, to, ko = oracle.downsample(pos, nrm, col, t, box, omega_max=20.0, tau_weight=3.0)
+    assert po.shape[0] == n
+    # output in box order: x fastest, then y, then z; the key of box (i, j, k) is i + 5 (j + 4 k)
+    cp = c[perm]
+    key = (cp[:, 0] + 5 * (cp[:, 1] + 4 * cp[:, 2])).astype(np.uint32)
+    order = np.argsort(key)
+    assert np.array_equal(ko, key[order])
+    assert np.array_equal(po, pos[order])               # a single point is its own mean
+    assert np.allclose(no[:, :3], nrm[order, :3], atol=1e-7)
+    assert np.array_equal(no[:, 3], (pos[order, 3] >= 3.0).astype(np.float32))
+    assert np.array_equal(co, col[order]) and np.array_equal(to, t[order])
+
+
+def test_downsample_merges_a_box_to_its_weighted_mean():
+    rng = np.random.default_rng(4)
+    box = 1.0
+    anchor = np.array([[0.0, 0.0, 0.0, 1.0]], np.float32)   # fixes the bounding-box minimum
+    pts = np.array([[2.2, 3.1, 4.4], [2.7, 3.9, 4.05], [2.05, 3.5, 4.95]], np.float64)
+    w = np.array([1.0, 2.0, 3.0])
+    pos = np.concatenate([anchor, np.concatenate([pts, w[:, None]], 1).astype(np.float32)])
+    nrm = np.array([[0, 0, -1, 1], [0.6, 0, -0.8, 1], [0, 0.6, -0.8, 1], [0, 0, -1, 1]], np.float32)
+    col = np.array([[0, 0, 0, 1], [1, 0, 0, 1], [0, 1, 0, 1], [0, 0, 1, 1]], np.float32)
+    t = np.array([0, 4, 9, 2], np.int32)
+    po, no, co, to, ko = oracle.downsample(pos, nrm, col, t, box, omega_max=5.0, tau_weight=3.0)
+    assert po.shape[0] == 2
+    assert np.array_equal(po[0], anchor[0]) and ko[0] == 0
+    p32 = pos[1:, :3].astype(np.float64)
+    assert np.allclose(po[1, :3], (w[:, None] * p32).sum(0) / 6.0, rtol=0, atol=1e-6)
+    assert po[1, 3] == 5.0                                   # min(1 + 2 + 3, omega_max)
+    nsum = (w[:, None] * nrm[1:, :3]).sum(0)
+    assert np.allclose(no[1, :3], nsum / np.linalg.norm(nsum), atol=1e-7) and no[1, 3] == 1.0
+    assert np.allclose(co[1], (w[:, None] * col[1:]).sum(0) / 6.0, atol=1e-7)
+    assert to[1] == 9
+    # box (2, 3, 4) of the 3 x 4 x 5 grid: floor(max / box) + 1 boxes per axis
+    dims = np.floor(np.max(pos[:, :3], 0) / np.float32(box)).astype(int) + 1
+    assert ko[1] == 2 + dims[0] * (3 + dims[1] * 4)
+
+
+def test_downsample_keeps_the_weighted_sum_and_ignores_input_order():
+    rng = np.random.default_rng(5)
+    n = 4000
+    pos = np.concatenate([rng.uniform(0, 6, (n, 3)), rng.integers(1, 4, (n, 1))], 1).astype(np.float32)
+    nrm = np.tile(np.array([0, 0, -1, 1], np.float32), (n, 1))
+    col = rng.random((n, 4)).astype(np.float32)
+    t = rng.integers(0, 5, n).astype(np.int32)
+    po, no, co, to, ko = oracle.downsample(pos, nrm, col, t, 0.8, omega_max=1e9, tau_weight=3.0)
+    w = pos[:, 3].astype(np.float64)
+    assert np.isclose(po[:, 3].astype(np.float64).sum(), w.sum())
+    assert np.allclose((po[:, 3:4] * po[:, :3]).sum(0), (w[:, None] * pos[:, :3]).sum(0), rtol=1e-6)
+    assert np.all(np.diff(ko.astype(np.int64)) > 0)
+    perm = rng.permutation(n)
+    qo, qn, qc, qt, qk = oracle.downsample(pos[perm], nrm[perm], col[perm], t[perm], 0.8, omega_max=1e9)
+    assert np.array_equal(qk, ko) and np.array_equal(qt, to) and np.array_equal(qo[:, 3], po[:, 3])
+    assert np.allclose(qo, po, atol=1e-6) and np.allclose(qc, co, atol=1e-6)
+
+
+def test_downsample_box_without_weight_is_a_plain_mean():
+    pos = np.array([[0, 0, 0, 0], [0.2, 0.4, 0.1, 0]], np.float32)
+    nrm = np.array([[0, 0, -1, 0], [0, 0, -1, 0]], np.float32)
+    col = np.array([[1, 0, 0, 1], [0, 1, 0, 1]], np.float32)
+    po, no, co, to, ko = oracle.downsample(pos, nrm, col, np.zeros(2, np.int32), 1.0)
+    assert po.shape[0] == 1
+    assert np.allclose(po[0, :3], [0.1, 0.2, 0.05], atol=1e-7) and po[0, 3] == 0.0 and no[0, 3] == 0.0
+    assert np.allclose(co[0], [0.5, 0.5, 0, 1])
+
+
+def test_depth_error_zero_for_the_depth_itself_and_equal_to_a_shift_along_rays():
+    depth, intr, nm, pos, nrm, pix = _exact_selfreg()
+    mean, cnt, mx, rms = oracle.depth_error(pos, depth, intr)
+    assert cnt == pos.shape[0] and mean == 0.0 and mx == 0.0
+    # every point moved along its ray by 0.5 mm: the same pixel, z + 0.5
+    d = 0.5
+    s = (pos[:, 2].astype(np.float64) + d) / pos[:, 2]
+    moved = pos.copy()
+    moved[:, :3] = (pos[:, :3] * s[:, None]).astype(np.float32)
+    got = oracle.associate_f32(moved, nrm, depth, nm, intr, eps_d=1e6, cos_eps_n=np.float32(-2.0))
+    keep = got == pix                                     # points that stayed on their pixel
+    assert keep.mean() > 0.9
+    mean, cnt, mx, rms = oracle.depth_error(moved[keep], depth, intr)
+    zerr = np.abs(moved[keep, 2].astype(np.float64) - depth.reshape(-1)[pix[keep]])
+    assert cnt == keep.sum() and np.isclose(mean, zerr.mean()) and abs(mean - d) < 1e-5
+    # a second copy of the surface 5 mm behind it is hidden by the z-buffer
+    behind = pos.copy()
+    behind[:, :3] = (pos[:, :3] * ((pos[:, 2:3] + 5.0) / pos[:, 2:3])).astype(np.float32)
+    mean, cnt, mx, rms = oracle.depth_error(np.concatenate([pos, behind]), depth, intr)
+    assert mx == 0.0 and cnt == pos.shape[0]
