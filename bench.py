@@ -41,9 +41,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=WORKLOAD)
-    ap.add_argument("--workload", default="single", choices=["single", "batch16"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch16", "push_sequence"],
                     help="batch16: 16 independent problems (320x240 / 640x480 / 1280x720, 200-4096 nodes) "
-                         "as one batched, graph-captured GN iteration vs 16 sequential solves")
+                         "as one batched, graph-captured GN iteration vs 16 sequential solves; push_sequence: "
+                         "the frame loop (registration, fusion, downsampling, node regeneration) over a "
+                         "synthetic 640x480 push sequence, one frame per step")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -560,6 +562,139 @@ def run_batch(args, rank, world, local):
 
 
 # ----------------------------------------------------------------------------
+# push sequence: the frame loop of Algorithm 2 with Algorithm 3
+# ----------------------------------------------------------------------------
+
+SEQ_WORKLOAD = "push_640x480_n2048"
+SEQ_BOX_MM = 0.2        # point-cloud density of Sec. III.A (dataset 6)
+
+
+def run_sequence(args, rank, world, local):
+    import torch
+    import paper_1803_02009_b300 as E
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = "cuda"
+    W0, K = args.warmup, args.steps
+    S = synth.make_push_sequence(SEQ_WORKLOAD, W0 + K, seed=rank_seed(rank))
+    cfg = S.cfg
+    fx, fy, cx, cy, W, H = S.intr
+    cap = S.model_pos.shape[0] + 2 * W * H
+    ctx = E.Context(max_points=cap, max_nodes=cfg.node_count, max_width=W, max_height=H, max_cells=1 << 24)
+    pos0 = torch.from_numpy(S.model_pos).to(dev)
+    nrm0 = torch.from_numpy(S.model_nrm).to(dev)
+    radius = E.calibrate_radius(ctx, pos0, nrm0, cfg.node_count)
+    tc = E.TrackerConfig(node_radius=radius, max_nodes=cfg.node_count, box=SEQ_BOX_MM, n_gn=cfg.n_gn,
+                         normal_half_width=cfg.normal_half_width, solver=E.SolverParams(n_pcg=cfg.n_pcg),
+                         fuse=E.FuseParams())
+    T = E.Tracker(pos0, nrm0, torch.from_numpy(S.model_col).to(dev), torch.from_numpy(S.model_t).to(dev), S.intr,
+                  tc, cap, ctx=ctx)
+    # observations in pinned host memory; each step copies its frame in (e2e)
+    h_depth = [torch.from_numpy(f.depth).pin_memory() for f in S.frames]
+    h_color = [torch.from_numpy(np.ascontiguousarray(f.color)).pin_memory() for f in S.frames]
+    truth = [torch.from_numpy(f.depth_clean).to(dev) for f in S.frames]
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    color = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    infos = []
+    for k in range(W0):
+        depth.copy_(h_depth[k])
+        color.copy_(h_color[k])
+        infos.append(T.process(depth, color, k + 1, truth_depth=truth[k]))
+    n_events = K * cfg.n_gn
+    tm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_events)]
+    ctx.set_timing(E.ED_KERNEL_PCG, tm_ev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = E.launch_count()
+    step_ms = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(W0, W0 + K):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        depth.copy_(h_depth[k], non_blocking=True)
+        color.copy_(h_color[k], non_blocking=True)
+        infos.append(T.process(depth, color, k + 1, truth_depth=truth[k]))
+        ev1.record()
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    wall_s = time.perf_counter() - t_wall
+    if dist is not None:
+        dist.barrier()
+    launches = E.launch_count() - l0
+    clk = clocks.stop()
+    n_rec = ctx.timing_count()
+    ctx.set_timing(E.ED_KERNEL_PCG, [])
+    pcg_ms = [tm_ev[2 * i].elapsed_time(tm_ev[2 * i + 1]) for i in range(n_rec)]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = whole_job_rate(world, K, cfg.n_gn, total_s)
+    e2e_value = whole_job_rate(world, K, cfg.n_gn, max_over_ranks(wall_s, dist, dev))
+    timed = infos[W0:]
+    g = ctx.graph
+    n_upper = (g.nnzb + g.m) // 2
+    byt = pcg_bytes_per_launch(g.m, n_upper, cfg.n_pcg)
+    avg_pcg_s = (sum(pcg_ms) / len(pcg_ms)) / 1e3 if pcg_ms else float("nan")
+    peak, peak_kind = measured_peaks()
+    achieved = byt / avg_pcg_s / 1e9
+    h2d = h_depth[0].numel() * 4 + h_color[0].numel() * 4
+    d2h = 4 * 8 + 4 + 2 * 4 + E.STATS_BYTES        # error sums, fused count, model count + status, the last step's statistics
+    return {
+        "metric": METRIC, "value": value, "unit": "GN iters/s", "n_gpus": world, "steps": K, "warmup": W0,
+        "ms_per_step": total_s * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded push sequence: static camera, one 2-3 mm push per frame)",
+        "config": {"workload": SEQ_WORKLOAD, "width": W, "height": H, "frames_timed": K, "nodes": cfg.node_count,
+                   "node_radius_mm": radius, "box_mm": SEQ_BOX_MM, "gn_iters_per_step": cfg.n_gn,
+                   "pcg_iters": cfg.n_pcg,
+                   "step": "normals + node regeneration + 10 x gn_step + warp + error + fuse + downsample (one frame)",
+                   "l2": "inputs of every step differ (a new frame); model 0.3-0.6 M points"},
+        "frames_per_s": K / total_s,
+        "accuracy": {"metric": "back-projection error vs the noise-free depth (Sec. III)", "unit": "mm",
+                     "mean": float(np.mean([i["error_mean_mm"] for i in timed])),
+                     "rms": float(np.sqrt(np.mean([i["error_rms_mm"] ** 2 for i in timed]))),
+                     "max": float(max(i["error_max_mm"] for i in timed)),
+                     "per_frame_mean": [round(i["error_mean_mm"], 4) for i in infos]},
+        "model_points": [i["model"] for i in infos],
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "wall clock of the timed loop: pinned host frames copied in, results read back"},
+        "roofline": {"kernel": "k_pcg (persistent block-Jacobi PCG)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": byt, "avg_launch_us": avg_pcg_s * 1e6,
+                     "launches_timed": len(pcg_ms)},
+    }, S, radius
+
+
+def sequence_cpu_baseline(S, radius, budget_s):
+    import oracle
+    cfg = S.cfg
+    model = (S.model_pos, S.model_nrm, S.model_col, S.model_t)
+    times = []
+    t_start = time.perf_counter()
+    for f in S.frames:
+        if times and (time.perf_counter() - t_start > budget_s or len(times) >= 3):
+            break
+        t0 = time.perf_counter()
+        model, _ = oracle.track_frame(model, f.depth, f.color, S.intr, radius, cfg.node_count, SEQ_BOX_MM, cfg.n_gn,
+                                      cfg.n_pcg, f.index, cfg.normal_half_width, truth_depth=f.depth_clean)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    return {"value": len(times) * cfg.n_gn / tot, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {len(times)} frame(s) of the same push sequence (normals, nodes, {cfg.n_gn} GN x "
+                      f"{cfg.n_pcg} PCG, warp, error, fuse, downsample) in the single-threaded FP64 oracle, "
+                      f"{tot:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
 # oracle (CPU) leg
 # ----------------------------------------------------------------------------
 
@@ -600,11 +735,42 @@ def cpu_baseline(s, budget_s, keypoints=0, weights="gaussian", lm=None):
                       f"{s.cfg.n_pcg} PCG, warp, fuse) in the single-threaded FP64 oracle, {tot:.1f} s"}
 
 
+def run_reference_sequence(args, world):
+    import synth
+    import oracle
+    S = synth.make_push_sequence(SEQ_WORKLOAD, args.warmup + args.steps, seed=1)
+    cfg = S.cfg
+    radius = oracle.calibrate_radius(S.model_pos, cfg.node_count)
+    model = (S.model_pos, S.model_nrm, S.model_col, S.model_t)
+    times, errs = [], []
+    for k, f in enumerate(S.frames):
+        t0 = time.perf_counter()
+        model, info = oracle.track_frame(model, f.depth, f.color, S.intr, radius, cfg.node_count, SEQ_BOX_MM, cfg.n_gn,
+                                         cfg.n_pcg, f.index, cfg.normal_half_width, truth_depth=f.depth_clean)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            errs.append(info["error_mean_mm"])
+    tot = sum(times)
+    value = args.steps * cfg.n_gn / tot
+    return {"metric": METRIC, "value": value, "unit": "GN iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": SEQ_WORKLOAD, "width": cfg.W, "height": cfg.H, "frames_timed": args.steps,
+                       "nodes": cfg.node_count, "box_mm": SEQ_BOX_MM},
+            "accuracy": {"metric": "back-projection error vs the noise-free depth (Sec. III)", "unit": "mm",
+                         "mean": float(np.mean(errs))},
+            "cpu_baseline": {"value": value, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} frames of the push sequence, single-threaded FP64 oracle"},
+            "e2e": {"value": value, "unit": "GN iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, rank, world):
     import synth
     import oracle
     if rank != 0:
         return None
+    if args.workload == "push_sequence":
+        return run_reference_sequence(args, world)
     s = synth.make_scene(args.config, seed=1)
     radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     for _ in range(args.warmup):
@@ -637,6 +803,13 @@ def main():
     if args.workload == "batch16":
         out = run_batch(args, rank, world, local)
         if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.workload == "push_sequence":
+        out, S, radius = run_sequence(args, rank, world, local)
+        if rank == 0:
+            out["cpu_baseline"] = (sequence_cpu_baseline(S, radius, args.cpu_budget_s)
+                                   if world == 1 and not args.no_cpu_baseline else None)
             print(json.dumps(out))
         return
     out, s = run_ours(args, rank, world, local)

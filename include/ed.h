@@ -13,6 +13,8 @@
  *   ed_warp             final warp of every model point     (Sec. II.D Eq. 1; Sec. II.G)
  *   ed_fuse             registration map, Alg. 1 gate, fusion
  *                       Eqs. fusion1-4, lifting, deletion   (Sec. II.G, Alg. 1-3)
+ *   ed_downsample       box averaging of the fused model    (Sec. III.A, Alg. 3)
+ * and, for measurement, ed_depth_error (projected model minus depth, Sec. III).
  *
  * Conventions
  *   Units are millimetres.  Camera frame: x right, y down, z forward.
@@ -225,7 +227,8 @@ ed_status ed_gn_step(ed_context *ctx, const ed_frame *frame, const ed_solver_par
  * the block-Jacobi inverses taken from the damped diagonal blocks.  The
  * energy reported for a rejected step is that of the restored point.
  * ed_lm_reset starts a new solve: lambda = lambda0, no accepted point yet.
- * Enqueued on the stream; a context starts with lambda = 0 and no point.
+ * Enqueued on the stream; a context starts with lambda = 0 and no point, and
+ * ed_build_graph forgets the accepted point (lambda is kept).
  */
 ed_status ed_lm_reset(ed_context *ctx, float lambda0, cudaStream_t stream);
 
@@ -300,6 +303,45 @@ ed_status ed_fuse(ed_context *ctx, const float *pos, const float *nrm, const flo
                   int n_in, const float *wpos, const float *wnrm, const ed_frame *frame,
                   const ed_fuse_params *params, int capacity, float *pos_out, float *nrm_out, float *col_out,
                   int *t_out, int *counts_out, int *reg_out, cudaStream_t stream);
+
+typedef struct ed_downsample_params {
+    float box;             /* box edge (mm): the point-cloud density (Sec. III.A: 0.2 or 1 mm) */
+    float omega_max;       /* cap of a merged point's fusion weight (Eq. fusion4) */
+    float tau_weight;      /* stability flag of the merged point: omega >= tau_weight */
+} ed_downsample_params;
+
+/*
+ * Box downsampling of a model (Sec. III.A: a fixed 3D box grid, the points in
+ * each box averaged into one; Algorithm 3, first line), out of place.  The
+ * boxes have edge params->box and are anchored at the minimum of the points'
+ * bounding box; a point's box per axis is floor((x - min) / box) in FP32
+ * (one subtraction, one IEEE division), boxes per axis floor((max - min) /
+ * box) + 1, box key ix + nx (iy + ny iz).  The points of one box, taken in
+ * increasing index order, become one point: omega-weighted means of position
+ * and colour, the normalised omega-weighted sum of normals, weight
+ * min(sum omega, omega_max), the latest time stamp, stability flag (nrm.w)
+ * omega >= tau_weight; with no weight in a box, plain means.  Output in
+ * increasing box key order.  Inputs as for ed_fuse; the outputs must not
+ * alias the inputs.  counts_out: device int[2] = (output count, status); the
+ * output is truncated at capacity with status ED_ERR_CAPACITY.  Returns
+ * ED_ERR_CAPACITY when the grid has 2^32 boxes or more.  Synchronises the
+ * stream once (it reads back the grid size to choose the sort's key width).
+ */
+ed_status ed_downsample(ed_context *ctx, const float *pos, const float *nrm, const float *col, const int *tstamp,
+                        int n_in, const ed_downsample_params *params, int capacity, float *pos_out, float *nrm_out,
+                        float *col_out, int *t_out, int *counts_out, cudaStream_t stream);
+
+/*
+ * Back-projection error (Sec. III measures the projected model image minus
+ * the observed depth image).  The points wpos (device [n][4], in the frame's
+ * camera frame, e.g. from ed_warp) are projected by the rule P of the
+ * association; a pixel keeps the point of smallest z, then of lowest index.
+ * Over the pixels that keep a point and have depth D > 0:
+ * out (device double[4]) = (sum |z - D|, count, max |z - D|, sum (z - D)^2),
+ * summed in a fixed order (deterministic).
+ */
+ed_status ed_depth_error(ed_context *ctx, const float *wpos, int n_points, const float *depth, ed_intrinsics intr,
+                         double *out, cudaStream_t stream);
 
 /*
  * Energy of Eq. (3) at (x, pose) with the graph built last (forward of the

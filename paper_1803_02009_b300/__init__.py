@@ -83,6 +83,10 @@ class FuseParamsC(C.Structure):
                 ("tau_weight", C.c_float), ("frame", C.c_int)]
 
 
+class DownsampleParamsC(C.Structure):
+    _fields_ = [("box", C.c_float), ("omega_max", C.c_float), ("tau_weight", C.c_float)]
+
+
 class BatchSchedule(C.Structure):
     _fields_ = [("pcg_threads", C.c_int), ("problems_per_launch", C.c_int), ("streams", C.c_int)]
 
@@ -111,6 +115,9 @@ _SIGS = {
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
     "ed_set_keypoints": [_vp, _vp, _vp, C.c_int, C.c_float],
     "ed_lm_reset": [_vp, C.c_float, _vp],
+    "ed_downsample": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.POINTER(DownsampleParamsC), C.c_int, _vp, _vp, _vp, _vp,
+                      _vp, _vp],
+    "ed_depth_error": [_vp, _vp, C.c_int, _vp, Intrinsics, _vp, _vp],
     "ed_batch_query_workspace": [_vp, C.c_int, C.POINTER(C.c_size_t)],
     "ed_batch_create": [_vp, C.c_int, _vp, C.c_size_t, C.POINTER(_vp)],
     "ed_batch_destroy": [_vp],
@@ -352,6 +359,35 @@ class Context:
                                         _stream(stream)))
         return po, no
 
+    def downsample(self, pos, nrm, col, tstamp, box, omega_max=20.0, tau_weight=3.0, capacity=None, out=None,
+                   stream=None):
+        """Box downsampling (Sec. III.A, Alg. 3) of the first pos.shape[0]
+        model points into `out` (pos, nrm, col, t, counts = (count, status))."""
+        dev = pos.device
+        n = int(pos.shape[0])
+        cap = n if capacity is None else int(capacity)
+        if out is None:
+            out = dict(pos=torch.empty((cap, 4), dtype=torch.float32, device=dev),
+                       nrm=torch.empty((cap, 4), dtype=torch.float32, device=dev),
+                       col=torch.empty((cap, 4), dtype=torch.float32, device=dev),
+                       t=torch.empty(cap, dtype=torch.int32, device=dev),
+                       counts=torch.zeros(2, dtype=torch.int32, device=dev))
+        prm = DownsampleParamsC(float(box), float(omega_max), float(tau_weight))
+        _check("ed_downsample", lib().ed_downsample(self.h, _ptr(pos), _ptr(nrm), _ptr(col), _ptr(tstamp), n,
+                                                    C.byref(prm), cap, _ptr(out["pos"]), _ptr(out["nrm"]),
+                                                    _ptr(out["col"]), _ptr(out["t"]), _ptr(out["counts"]),
+                                                    _stream(stream)))
+        return out
+
+    def depth_error(self, wpos, depth, intr, out=None, stream=None):
+        """Back-projection error of warped points against a depth image
+        (Sec. III): device double[4] = (sum |z - D|, count, max |z - D|,
+        sum (z - D)^2) over the pixels that keep a point."""
+        o = out if out is not None else torch.empty(4, dtype=torch.float64, device=wpos.device)
+        _check("ed_depth_error", lib().ed_depth_error(self.h, _ptr(wpos), int(wpos.shape[0]), _ptr(depth),
+                                                      intrinsics(intr), _ptr(o), _stream(stream)))
+        return o
+
     def fuse(self, pos, nrm, col, tstamp, wpos, wnrm, frame: Frame, params: FuseParams, capacity, out=None,
              reg=None, stream=None):
         dev = pos.device
@@ -569,3 +605,6 @@ class Batch:
     def set_schedule(self, pcg_threads, problems_per_launch, streams):
         sch = BatchSchedule(int(pcg_threads), int(problems_per_launch), int(streams))
         _check("ed_batch_set_schedule", lib().ed_batch_set_schedule(self.h, C.byref(sch)))
+
+
+from .tracker import Tracker, TrackerConfig  # noqa: E402,F401

@@ -101,6 +101,7 @@ size_t carve(ed_context *c, char *base)
     c->vec_stride = (P + 63) / 64 * 64;
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
+    c->red_part = k.take<double>(4 * (size_t)ED_MAX_PCG_GRID);
     c->pcg_rows = k.take<int>(ED_MAX_PCG_GRID + 1);
     c->pcg_rows_b = k.take<int>(ED_MAX_PCG_GRID + 1);
     c->zbuf = k.take<unsigned long long>(WH);

@@ -49,10 +49,20 @@ enum {
     MI_LM_REJECT = 37,   // Levenberg-Marquardt: the current step undid the previous one
     MI_FUSE = 40,        // 40 kept, 41 lifted
     MI_READ = 48,        // 48..51 values gathered for one host read (chunk totals, upper blocks)
+    MI_VOX = 52,         // 52..54 box-grid dims of ed_downsample, 55 its status
     MI_PHASES = 64,      // 64..90 phase counts, 96..123 starts, 128..154 fill counters
     MI_COUNT = 192
 };
-enum { MF_CELL = 0, MF_INV = 1, MF_KCELL = 2, MF_KINV = 3, MF_R2 = 4, MF_BBOX = 8, MF_COUNT = 16 };
+enum { MF_CELL = 0, MF_INV = 1, MF_KCELL = 2, MF_KINV = 3, MF_R2 = 4, MF_VOX = 5, MF_BBOX = 8, MF_COUNT = 16 };
+// (MF_VOX .. MF_VOX + 2: the origin of the ed_downsample box grid)
+
+// ordered-int image of a float (monotone for signed comparison)
+__device__ __forceinline__ int f2o(float f)
+{
+    int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7fffffff); }
 
 // launch plan of the PCG of one problem
 struct ed_pcg_plan_t {
@@ -143,6 +153,7 @@ struct ed_context {
     float *vec;              // 6 vectors of 12 max_nodes + 6: d, r, z, p0, p1, q
     size_t vec_stride;       // floats between vectors (multiple of 64: 16-byte aligned float4 rows)
     double *pcg_part;        // [2][ED_PCG_PART][ED_MAX_PCG_GRID] (component-major)
+    double *red_part;        // [4][ED_MAX_PCG_GRID] per-CTA partials of ed_depth_error
     // fusion / scans
     unsigned long long *zbuf;  // [W H]
     int *regpix;             // [W H]
@@ -604,6 +615,7 @@ __device__ __forceinline__ int ed_associate(const ed_warped &W, const float *__r
 
 ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st);
 ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
+ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_t st);
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,
                        ed_stats *stats, cudaStream_t st);
 ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st);

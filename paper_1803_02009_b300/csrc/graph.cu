@@ -6,14 +6,6 @@
 
 #include "ed_internal.cuh"
 
-// ordered-int image of a float (monotone for signed comparison)
-__device__ __forceinline__ int f2o(float f)
-{
-    int b = __float_as_int(f);
-    return b >= 0 ? b : b ^ 0x7fffffff;
-}
-__device__ __forceinline__ float o2f(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7fffffff); }
-
 __global__ void k_bbox_init(int *misc)
 {
     if (threadIdx.x < 3) {
@@ -664,6 +656,17 @@ __global__ void k_kp_expand(const float4 *__restrict__ kp, int nk, int n_model, 
     const float4 p = kp[t / 3];
     pos[n_model + t] = make_float4(p.x, p.y, p.z, 0.f);
     nrm[n_model + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// bounding box of n points into misc[MI_BBOX .. MI_BBOX + 5] (ordered ints)
+ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_t st)
+{
+    k_bbox_init<<<1, 32, 0, st>>>(ctx->misc); ed_note_launch();
+    if (n > 0) {
+        k_bbox<<<min(ed_div_up(n, 256), 4 * ctx->num_sms), 256, 0, st>>>(pos, n, ctx->misc); ed_note_launch();
+    }
+    ED_LAUNCH_CHECK();
+    return ED_OK;
 }
 
 static ed_status read_misc(ed_context *ctx, int *host, cudaStream_t st)
