@@ -274,7 +274,7 @@ def run_ours(args, rank, world, local):
 
     gn_ev = []
 
-    def step(record_gn=False):
+    def step(record_gn=False, depth=depth, color=color, frame=frame):
         ctx.compute_normals(depth, s.intr, cfg.normal_half_width, out=nmap)
         g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius, weight_mode=wmode)
         m = g.m
@@ -340,30 +340,51 @@ def run_ours(args, rank, world, local):
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
     value = whole_job_rate(world, K, cfg.n_gn, total_s)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies
+    # its frame (depth, colour) in from pinned host memory and reads its result
+    # (node parameters, statistics) back; the next frame's copy runs on a copy
+    # stream into the other of two input buffers while this frame computes
     h_depth = torch.from_numpy(s.tgt_depth).pin_memory()
     h_color = torch.from_numpy(np.ascontiguousarray(s.tgt_color)).pin_memory()
     h_x = torch.empty((cfg.node_count, 12), dtype=torch.float32).pin_memory()
     h_stats = torch.empty(stats.shape, dtype=torch.uint8).pin_memory()
     h2d = h_depth.numel() * 4 + h_color.numel() * 4
     d2h = h_x.numel() * 4 + h_stats.numel()
-    e2e_ms = []
+    d_in = [torch.empty_like(depth) for _ in range(2)]
+    c_in = [torch.empty_like(color) for _ in range(2)]
+    f_in = [E.make_frame(d_in[i], nmap, s.intr, c_in[i]) for i in range(2)]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    released = [torch.cuda.Event() for _ in range(2)]
+    compute = torch.cuda.current_stream()
     barrier()
     torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+
+    def fetch(k):
+        b = k & 1
+        copy_stream.wait_stream(compute) if k == 0 else copy_stream.wait_event(released[b])
+        with torch.cuda.stream(copy_stream):
+            d_in[b].copy_(h_depth, non_blocking=True)
+            c_in[b].copy_(h_color, non_blocking=True)
+            copied[b].record()
+
+    fetch(0)
     for k in range(K):
-        flush.fill_(k & 0xff)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        depth.copy_(h_depth, non_blocking=True)
-        color.copy_(h_color, non_blocking=True)
-        gg = step()
+        b = k & 1
+        if k + 1 < K:
+            fetch(k + 1)
+        flush.fill_(k & 0xff)            # L2 flushed before every step, inside the timed region here
+        compute.wait_event(copied[b])
+        gg = step(depth=d_in[b], color=c_in[b], frame=f_in[b])
+        released[b].record()
         h_x[:gg.m].copy_(x[:gg.m], non_blocking=True)
         h_stats.copy_(stats, non_blocking=True)
-        ev1.record()
-        ev1.synchronize()
-        e2e_ms.append(ev0.elapsed_time(ev1))
-    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
+    ev1.record()
+    ev1.synchronize()
+    e2e_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
     e2e_value = whole_job_rate(world, K, cfg.n_gn, e2e_s)
 
     peak, peak_kind = measured_peaks()
@@ -398,7 +419,10 @@ def run_ours(args, rank, world, local):
         "gn_only_iters_per_s": gn_rate,
         "gpu_launches": launches,
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "K steps end to end: each frame copied in from pinned host memory (the next frame's copy "
+                        "overlapping this frame's compute on a copy stream), results read back, L2 flush "
+                        "inside the timed region"},
         "roofline": {"kernel": "k_pcg (persistent block-Jacobi PCG)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": byt,
