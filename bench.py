@@ -257,11 +257,11 @@ def run_ours(args, rank, world, local):
     prm = E.SolverParams(n_pcg=cfg.n_pcg, prior=tuple(float(v) for v in s.pose_prior),
                          precision=E.ED_PRECISION_MIXED if args.precision == "mixed" else E.ED_PRECISION_FP32,
                          lm_accept=args.lm is not None)
+    prm_c = prm.c()
     F = E.FuseParams(frame=1)
     x = torch.empty((cfg.node_count, 12), dtype=torch.float32, device=dev)
     xm = torch.empty((cfg.node_count, 12), dtype=torch.float64, device=dev)
     pose = torch.empty(6, dtype=torch.float64, device=dev)
-    prior = torch.tensor(s.pose_prior, dtype=torch.float64, device=dev)
     stats = E.new_stats(cfg.n_gn)
     wpos = torch.empty_like(pos)
     wnrm = torch.empty_like(nrm)
@@ -276,21 +276,17 @@ def run_ours(args, rank, world, local):
 
     def step(record_gn=False, depth=depth, color=color, frame=frame):
         ctx.compute_normals(depth, s.intr, cfg.normal_half_width, out=nmap)
-        g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius, weight_mode=wmode)
+        g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius, weight_mode=wmode,
+                            reuse=True)
         m = g.m
-        x[:m].zero_()
-        x[:m, 0] = 1.0
-        x[:m, 5] = 1.0
-        x[:m, 10] = 1.0
-        xm[:m].copy_(x[:m])
-        pose.copy_(prior)
+        ctx.reset_params(x[:m], pose, x_master=xm[:m], prior=s.pose_prior)
         if args.lm is not None:
             ctx.lm_reset(args.lm)
         if record_gn:
             e0 = torch.cuda.Event(enable_timing=True)
             e0.record()
         for it in range(cfg.n_gn):
-            ctx.gn_step(frame, prm, x[:m], pose, x_master=xm[:m], stats=stats[it:it + 1])
+            ctx.gn_step(frame, prm_c, x[:m], pose, x_master=xm[:m], stats=stats[it:it + 1])
         if record_gn:
             e1 = torch.cuda.Event(enable_timing=True)
             e1.record()
@@ -357,12 +353,6 @@ def run_ours(args, rank, world, local):
     copied = [torch.cuda.Event() for _ in range(2)]
     released = [torch.cuda.Event() for _ in range(2)]
     compute = torch.cuda.current_stream()
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record()
-
     def fetch(k):
         b = k & 1
         copy_stream.wait_stream(compute) if k == 0 else copy_stream.wait_event(released[b])
@@ -371,17 +361,26 @@ def run_ours(args, rank, world, local):
             c_in[b].copy_(h_color, non_blocking=True)
             copied[b].record()
 
-    fetch(0)
-    for k in range(K):
-        b = k & 1
-        if k + 1 < K:
-            fetch(k + 1)
-        flush.fill_(k & 0xff)            # L2 flushed before every step, inside the timed region here
-        compute.wait_event(copied[b])
-        gg = step(depth=d_in[b], color=c_in[b], frame=f_in[b])
-        released[b].record()
-        h_x[:gg.m].copy_(x[:gg.m], non_blocking=True)
-        h_stats.copy_(stats, non_blocking=True)
+    def e2e_run(n):
+        fetch(0)
+        for k in range(n):
+            b = k & 1
+            if k + 1 < n:
+                fetch(k + 1)
+            flush.fill_(k & 0xff)            # L2 flushed before every step, inside the timed region here
+            compute.wait_event(copied[b])
+            gg = step(depth=d_in[b], color=c_in[b], frame=f_in[b])
+            released[b].record()
+            h_x[:gg.m].copy_(x[:gg.m], non_blocking=True)
+            h_stats.copy_(stats, non_blocking=True)
+
+    e2e_run(args.warmup)                     # untimed: first use of the copy stream and buffers
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    e2e_run(K)
     ev1.record()
     ev1.synchronize()
     e2e_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)

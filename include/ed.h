@@ -215,6 +215,15 @@ ed_status ed_gn_step(ed_context *ctx, const ed_frame *frame, const ed_solver_par
                      double *x_master, double *pose, ed_stats *stats, cudaStream_t stream);
 
 /*
+ * Start of a solve: x [m][12] = the identity warp (A_j = I, t_j = 0) for the
+ * m nodes of the graph built last, x_master (may be NULL) the same in FP64,
+ * pose double[6] = prior_host (host double[6]; NULL = zeros), in one launch
+ * on the stream.
+ */
+ed_status ed_reset_params(ed_context *ctx, float *x, double *x_master, double *pose, const double *prior_host,
+                          cudaStream_t stream);
+
+/*
  * Levenberg-Marquardt damping schedule (Sec. II.F solves Eq. 3 with LM), kept
  * on the device so that a sequence of ed_gn_step calls needs no host
  * synchronisation and can be captured in a CUDA graph.  Steps with

@@ -115,6 +115,7 @@ _SIGS = {
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
     "ed_set_keypoints": [_vp, _vp, _vp, C.c_int, C.c_float],
     "ed_lm_reset": [_vp, C.c_float, _vp],
+    "ed_reset_params": [_vp, _vp, _vp, _vp, C.POINTER(C.c_double * 6), _vp],
     "ed_downsample": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.POINTER(DownsampleParamsC), C.c_int, _vp, _vp, _vp, _vp,
                       _vp, _vp],
     "ed_depth_error": [_vp, _vp, C.c_int, _vp, Intrinsics, _vp, _vp],
@@ -288,16 +289,27 @@ class Context:
         self.n_keypoints, self._kp = int(kp_pos.shape[0]), (kp_pos, kp_target)
 
     def build_graph(self, pos, nrm, nodes=None, node_radius=0.0, max_nodes=0, k_graph=4,
-                    weight_mode=ED_WEIGHT_GAUSSIAN, sigma=1.0, search_cell=0.0, stream=None) -> Graph:
+                    weight_mode=ED_WEIGHT_GAUSSIAN, sigma=1.0, search_cell=0.0, stream=None, reuse=False) -> Graph:
+        """Builds the graph of a model (ed_build_graph).  reuse=True writes into
+        the buffers of the previous build when they are large enough (the
+        previous Graph's contents are then replaced), saving the allocations
+        of a per-frame rebuild."""
         dev = pos.device
         N = pos.shape[0]
         rows = N + 3 * self.n_keypoints      # the key points' rows follow the model points
         cap = int(self.limits.max_nodes)
-        g = Graph(nodes=torch.zeros((cap, 4), dtype=torch.float32, device=dev),
-                  idx=torch.empty((rows, 4), dtype=torch.int16, device=dev),
-                  weights=torch.empty((rows, 4), dtype=torch.float32, device=dev),
-                  nbr=torch.empty((cap, k_graph), dtype=torch.int32, device=dev),
-                  counts=torch.zeros(4, dtype=torch.int32, device=dev))
+        old = self.graph if reuse else None
+        if old is not None and old.idx.shape[0] >= rows and old.nbr.shape[1] == k_graph:
+            g = Graph(nodes=old.nodes, idx=old.idx[:rows], weights=old.weights[:rows], nbr=old.nbr, counts=old.counts)
+            g._full = getattr(old, "_full", (old.idx, old.weights))
+        else:
+            rows_alloc = int(self.limits.max_points) if reuse else rows
+            idx = torch.empty((rows_alloc, 4), dtype=torch.int16, device=dev)
+            w = torch.empty((rows_alloc, 4), dtype=torch.float32, device=dev)
+            g = Graph(nodes=torch.zeros((cap, 4), dtype=torch.float32, device=dev), idx=idx[:rows], weights=w[:rows],
+                      nbr=torch.empty((cap, k_graph), dtype=torch.int32, device=dev),
+                      counts=torch.zeros(4, dtype=torch.int32, device=dev))
+            g._full = (idx, w)
         m_in = 0
         if nodes is not None:
             m_in = nodes.shape[0]
@@ -322,10 +334,21 @@ class Context:
         x[:, 0] = x[:, 5] = x[:, 10] = 1.0
         return x
 
-    def gn_step(self, frame: Frame, params: SolverParams, x, pose, x_master=None, stats=None, stream=None):
-        p = params.c()
+    def gn_step(self, frame: Frame, params, x, pose, x_master=None, stats=None, stream=None):
+        """One Gauss-Newton step; params: SolverParams or its prepared C form
+        (SolverParams.c(), saves the conversion in a loop)."""
+        p = params if isinstance(params, SolverParamsC) else params.c()
         _check("ed_gn_step", lib().ed_gn_step(self.h, C.byref(frame), C.byref(p), _ptr(x), _ptr(x_master),
                                               _ptr(pose), _ptr(stats), _stream(stream)))
+
+    def reset_params(self, x, pose, x_master=None, prior=None, stream=None):
+        """x = identity warp for the nodes of the last graph (and x_master),
+        pose = prior (host sequence of 6; None = zeros), one launch."""
+        pr = None
+        if prior is not None:
+            pr = (C.c_double * 6)(*[float(v) for v in prior])
+        _check("ed_reset_params", lib().ed_reset_params(self.h, _ptr(x), _ptr(x_master), _ptr(pose),
+                                                        C.byref(pr) if pr is not None else None, _stream(stream)))
 
     def lm_reset(self, lambda0=0.0, stream=None):
         """Starts a Levenberg-Marquardt solve: damping lambda0, no accepted

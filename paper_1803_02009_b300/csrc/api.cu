@@ -542,6 +542,39 @@ __global__ void k_warp(const float4 *__restrict__ pos, const float4 *__restrict_
     nrm_out[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
 }
 
+struct ResetPose {
+    double v[6];
+};
+
+// identity warp (A_j = I, t_j = 0) for the first m nodes, the FP64 master copy
+// likewise, the pose from its prior
+__global__ void k_reset_params(int m, float *__restrict__ x, double *__restrict__ xm, double *__restrict__ pose,
+                               ResetPose prior)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 12 * m) {
+        const int e = i % 12;
+        const float v = (e == 0 || e == 5 || e == 10) ? 1.0f : 0.0f;
+        x[i] = v;
+        if (xm) xm[i] = (double)v;
+    } else if (i < 12 * m + 6) {
+        pose[i - 12 * m] = prior.v[i - 12 * m];
+    }
+}
+
+extern "C" ed_status ed_reset_params(ed_context *ctx, float *x, double *x_master, double *pose,
+                                     const double *prior_host, cudaStream_t st)
+{
+    if (!ctx || !x || !pose) return ED_ERR_ARG;
+    if (!ctx->have_graph) return ED_ERR_STATE;
+    ResetPose pr;
+    for (int k = 0; k < 6; ++k) pr.v[k] = prior_host ? prior_host[k] : 0.0;
+    const int m = ctx->m;
+    k_reset_params<<<ed_div_up(12 * m + 6, 256), 256, 0, st>>>(m, x, x_master, pose, pr); ed_note_launch();
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+}
+
 extern "C" ed_status ed_warp(ed_context *ctx, const float *x, const double *pose, const float *pos_in,
                              const float *nrm_in, int n_points, float *pos_out, float *nrm_out, cudaStream_t stream)
 {

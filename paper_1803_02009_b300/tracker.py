@@ -67,7 +67,6 @@ class Tracker:
         self.x = torch.empty((cfg.max_nodes, 12), dtype=torch.float32, device=dev)
         self.xm = torch.empty((cfg.max_nodes, 12), dtype=torch.float64, device=dev)
         self.pose = torch.zeros(6, dtype=torch.float64, device=dev)
-        self.prior = torch.tensor(cfg.solver.prior, dtype=torch.float64, device=dev)
         self.stats = new_stats(cfg.n_gn)
         self.err = torch.zeros(4, dtype=torch.float64, device=dev)
 
@@ -82,17 +81,15 @@ class Tracker:
         pos, nrm = self.A["pos"][:n], self.A["nrm"][:n]
         sigma = c.sigma if c.sigma is not None else c.node_radius
         g = ctx.build_graph(pos, nrm, node_radius=c.node_radius, max_nodes=c.max_nodes, sigma=sigma,
-                            weight_mode=ED_WEIGHT_GAUSSIAN)
+                            weight_mode=ED_WEIGHT_GAUSSIAN, reuse=True)
         m = g.m
         x, xm = self.x[:m], self.xm[:m]
-        x.zero_()
-        x[:, 0] = x[:, 5] = x[:, 10] = 1.0
-        xm.copy_(x)
-        self.pose.copy_(self.prior)
+        ctx.reset_params(x, self.pose, x_master=xm, prior=c.solver.prior)
         if c.solver.lm_accept:
             ctx.lm_reset(c.solver.lam)
+        prm = c.solver.c()
         for it in range(c.n_gn):
-            ctx.gn_step(frame, c.solver, x, self.pose, x_master=xm, stats=self.stats[it:it + 1])
+            ctx.gn_step(frame, prm, x, self.pose, x_master=xm, stats=self.stats[it:it + 1])
         wpos, wnrm = self.wpos[:n], self.wnrm[:n]
         ctx.warp(x, self.pose, pos, nrm, wpos, wnrm)
         ctx.depth_error(wpos, truth_depth if truth_depth is not None else depth, self.intr, out=self.err)
