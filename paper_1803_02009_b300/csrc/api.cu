@@ -171,6 +171,16 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         free(c);
         return ED_ERR_CUDA;
     }
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->aux) cudaStreamDestroy(c->aux);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        cudaFreeHost(c->row_ptr_host);
+        cudaFreeHost(c->pinned);
+        free(c);
+        return ED_ERR_CUDA;
+    }
     *out = c;
     return ED_OK;
 }
@@ -178,6 +188,10 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
 extern "C" ed_status ed_destroy(ed_context *ctx)
 {
     if (!ctx) return ED_ERR_ARG;
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
     cudaFreeHost(ctx->row_ptr_host);
     cudaFreeHost(ctx->pinned);
     free(ctx);

@@ -28,6 +28,7 @@ enum {
     DM_LAM = 16,         // Levenberg-Marquardt damping lambda
     DM_EPREV = 17,       // energy of the last accepted point
     DM_SAVED = 24,       // 24..31 energy terms of the last accepted point
+    DM_POSE = 40,        // 40..45 from the pose pass: E_data, valid points, non-finite flag, E_corr, E_r, E_p
 };
 
 // indices of the misc int words in the workspace
@@ -47,6 +48,7 @@ enum {
     MI_BAR_GRAPH = 33,   // grid barrier arrival count of the Poisson sampler
     MI_LM_HAVE = 36,     // Levenberg-Marquardt: an accepted point is stored
     MI_LM_REJECT = 37,   // Levenberg-Marquardt: the current step undid the previous one
+    MI_FIN_DONE = 38,    // CTAs of k_finalize done (the last one forms the energy totals)
     MI_FUSE = 40,        // 40 kept, 41 lifted
     MI_READ = 48,        // 48..51 values gathered for one host read (chunk totals, upper blocks)
     MI_VOX = 52,         // 52..54 box-grid dims of ed_downsample, 55 its status
@@ -195,6 +197,10 @@ struct ed_context {
     int *pcg_rows_b;         // [ED_MAX_PCG_GRID + 1] the same for a batched launch (device)
     int *row_ptr_host;       // [max_nodes + 1] host copy of the block row pointer (pinned)
     int *pinned;             // [ED_PINNED_INTS] pinned host staging of small host-to-device copies
+
+    // the pose pass of a Gauss-Newton step runs beside the assembly
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_join;
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;

@@ -412,6 +412,13 @@ struct FinArgs {
     float *bsr, *grad, *pnode, *minv;
     float2 *node_energy;
     int *status;
+    // the last CTA forms the energy totals of the step from the node energies
+    // and the pose pass's sums
+    int m;
+    int *misc;
+    double *dmisc;
+    ed_stats *stats;
+    float lambda_report;     // damping reported in the statistics
 };
 
 __device__ __forceinline__ int sym3(int a, int b)
@@ -563,30 +570,18 @@ __device__ __forceinline__ void fill_block_table(int *s_tab)
     }
 }
 
-// INV = false: the block inverses are taken later (Levenberg-Marquardt stage)
+// one warp per upper block u (INV = false: the block inverses are taken
+// later, in the Levenberg-Marquardt stage)
 template <bool INV>
-__global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
+__device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M, float *H, float *X, float *S,
+                                               float *Lw, float *rinv_w, const int *s_tab)
 {
-    __shared__ float sM[FIN_WARPS][84];
-    __shared__ float sH[FIN_WARPS][144];
-    __shared__ float sX[FIN_WARPS][12];
-    __shared__ float sS[FIN_WARPS][16];
-    __shared__ float sL[FIN_WARPS][144];
-    __shared__ float sRinv[FIN_WARPS][12];
-    // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
-    // shift), R, C (the same for every block; computed once per CTA)
-    __shared__ int s_tab[144];
-    fill_block_table(s_tab);
-    __syncthreads();
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = blockIdx.x * FIN_WARPS + wid;
-    if (u >= a.n_upper) return;
+    const int lane = threadIdx.x & 31;
     const int b = a.up_list[u];
     const int j = a.brow[b], l = a.col[b];
     const bool diag = j == l;
     const int nch = (a.ent_cnt[b] + ED_CHUNK - 1) / ED_CHUNK;
     const int c0 = a.chunk_start[b];
-    float *M = sM[wid], *H = sH[wid], *X = sX[wid], *S = sS[wid];
     for (int k = lane; k < 60; k += 32) M[k] = sum_parts(a.part, k, a.max_chunks, c0, nch, a.mixed);
     if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
     __syncwarp();
@@ -723,13 +718,97 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
     __syncwarp();
     if (!INV) return;
-    if (!block_inverse12(H, sL[wid], sRinv[wid], s_tab, a.jitter, a.minv + (long)j * 144) && lane == 0)
+    if (!block_inverse12(H, Lw, rinv_w, s_tab, a.jitter, a.minv + (long)j * 144) && lane == 0)
         atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
 }
 
+// the CTA that finishes last: the node energies summed in a fixed order
+// (float-float), the energy of Eq. (3) from them and the pose pass's sums,
+// the non-finite check, the step's statistics
+__device__ __forceinline__ void finalize_totals(const FinArgs &a)
+{
+    __shared__ int s_last;
+    __shared__ float2 s_w[32 * FIN_WARPS / 32][2];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(reinterpret_cast<unsigned *>(a.misc + MI_FIN_DONE), 1u);
+        s_last = t == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float2 er = make_float2(0.f, 0.f), eg = er;
+    for (int j = threadIdx.x; j < a.m; j += 32 * FIN_WARPS) {
+        const float2 e = __ldcg(a.node_energy + j);
+        er = ed_ff_add1(er, e.x);
+        eg = ed_ff_add1(eg, e.y);
+    }
+    er = ed_ff_warp_sum(er);
+    eg = ed_ff_warp_sum(eg);
+    if (lane == 0) {
+        s_w[w][0] = er;
+        s_w[w][1] = eg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 a0 = s_w[0][0], a1 = s_w[0][1];
+        for (int k = 1; k < FIN_WARPS; ++k) {
+            a0 = ed_ff_add(a0, s_w[k][0]);
+            a1 = ed_ff_add(a1, s_w[k][1]);
+        }
+        const double ne0 = ed_ff_value(a0), ne1 = ed_ff_value(a1);
+        const double *ps = a.dmisc + DM_POSE;   // E_data, valid, non-finite flag, E_corr, E_r, E_p
+        const double E = ps[0] + ne0 + ne1 + ps[4] + ps[5] + ps[3];
+        if (!isfinite(E) || ps[2] > 0.0) atomicCAS(a.status, ED_OK, ED_ERR_NONFINITE);
+        a.dmisc[0] = E;
+        a.dmisc[1] = ps[0];
+        a.dmisc[2] = ne0;
+        a.dmisc[3] = ne1;
+        a.dmisc[4] = ps[4];
+        a.dmisc[5] = ps[5];
+        a.dmisc[6] = ps[1];
+        a.dmisc[7] = ps[3];
+        if (a.stats) {
+            a.stats->e_corr = ps[3];
+            a.stats->energy = E;
+            a.stats->e_data = ps[0];
+            a.stats->e_rot = ne0;
+            a.stats->e_reg = ne1;
+            a.stats->e_rot_prior = ps[4];
+            a.stats->e_pos_prior = ps[5];
+            a.stats->n_valid = (int)ps[1];
+            a.stats->lm_rejected = 0;
+            a.stats->lambda = a.lambda_report;
+        }
+        a.misc[MI_FIN_DONE] = 0;   // ready for the next launch
+    }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
+{
+    __shared__ float sM[FIN_WARPS][84];
+    __shared__ float sH[FIN_WARPS][144];
+    __shared__ float sX[FIN_WARPS][12];
+    __shared__ float sS[FIN_WARPS][16];
+    __shared__ float sL[FIN_WARPS][144];
+    __shared__ float sRinv[FIN_WARPS][12];
+    // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
+    // shift), R, C (the same for every block; computed once per CTA)
+    __shared__ int s_tab[144];
+    fill_block_table(s_tab);
+    __syncthreads();
+    const int wid = threadIdx.x >> 5;
+    const int u = blockIdx.x * FIN_WARPS + wid;
+    if (u < a.n_upper) finalize_block<INV>(a, u, sM[wid], sH[wid], sX[wid], sS[wid], sL[wid], sRinv[wid], s_tab);
+    finalize_totals(a);
+}
+
 // ---------------------------------------------------------------------------
-// pose finalisation (one CTA): pose block and gradient, priors E_r / E_p,
-// energy totals, pose preconditioner
+// pose pass (one CTA): pose block and gradient, priors E_r / E_p, the sums
+// of the point pass, pose preconditioner
 // ---------------------------------------------------------------------------
 
 #define PF_THREADS 1024
@@ -836,12 +915,10 @@ __device__ __forceinline__ bool pose_inverse6(float *Ls, float *rinv, float jitt
     return all_ok;
 }
 
-__global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restrict__ part, int nparts, int pstride,
-                                                           const float2 *__restrict__ node_energy, int m,
-                                                           const double *__restrict__ pose, ed_solver_params prm,
-                                                           float *__restrict__ pose_blk, float *__restrict__ grad,
-                                                           double *__restrict__ dmisc, int *__restrict__ status,
-                                                           ed_stats *stats)
+__global__ void __launch_bounds__(PF_THREADS) k_pose_part(const float2 *__restrict__ part, int nparts, int pstride,
+                                                          const double *__restrict__ pose, ed_solver_params prm,
+                                                          float *__restrict__ pose_blk, float *__restrict__ grad,
+                                                          double *__restrict__ dmisc, int *__restrict__ status)
 {
     __shared__ double s[32];
     __shared__ double ne[2];
@@ -851,7 +928,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restr
     __shared__ float rinv[6];
     const int t = threadIdx.x, lane = t & 31;
     static_assert(PF_BATCH * 32 * 1 >= 4 * 148, "one round of loads on a 148-SM part");
-    pf_sums(part, nparts, pstride, node_energy, m, s, ne, wsum);
+    pf_sums(part, nparts, pstride, nullptr, 0, s, ne, wsum);
     // pose block (+ prior weights on the diagonal, LM damping), one entry per thread;
     // priors and the pose gradient, one coordinate per thread
     if (t < 36) {
@@ -871,29 +948,15 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_final(const float2 *__restr
     if (t < 32) {
         if (!pose_inverse6(Ls, rinv, prm.jitter, pose_blk + 36) && lane == 0) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
     } else if (t == 32) {
-        const double Er = pri[0] + pri[1] + pri[2], Ep = pri[3] + pri[4] + pri[5];
-        const double E = s[0] + ne[0] + ne[1] + Er + Ep + s[30];
-        if (!isfinite(E) || s[29] > 0.0) atomicCAS(status, 0, ED_ERR_NONFINITE);
-        dmisc[0] = E;
-        dmisc[1] = s[0];
-        dmisc[2] = ne[0];
-        dmisc[3] = ne[1];
-        dmisc[4] = Er;
-        dmisc[5] = Ep;
-        dmisc[6] = s[1];
-        dmisc[7] = s[30];
-        if (stats) {
-            stats->e_corr = s[30];
-            stats->energy = E;
-            stats->e_data = s[0];
-            stats->e_rot = ne[0];
-            stats->e_reg = ne[1];
-            stats->e_rot_prior = Er;
-            stats->e_pos_prior = Ep;
-            stats->n_valid = (int)s[1];
-            stats->lm_rejected = 0;
-            stats->lambda = prm.lambda;
-        }
+        // for the energy totals the last CTA of k_finalize forms (the node
+        // energies are not known yet: this pass runs beside the assembly)
+        double *ps = dmisc + DM_POSE;
+        ps[0] = s[0];
+        ps[1] = s[1];
+        ps[2] = s[29];
+        ps[3] = s[30];
+        ps[4] = pri[0] + pri[1] + pri[2];
+        ps[5] = pri[3] + pri[4] + pri[5];
     }
 }
 
@@ -1106,6 +1169,21 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     const int m = ctx->m;
     ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_STATUS, 0, sizeof(int), st));
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_STEP, st)) != ED_OK) return s;
+    const bool lm = prm->lm_accept != 0;
+    // the pose pass (pose block, its inverse, pose gradient, prior energies,
+    // the point-pass sums) needs only the point pass: it runs on the context's
+    // second stream beside the assembly, joined before the finalisation
+    {
+        ed_solver_params pf = *prm;
+        if (lm) pf.lambda = 0.f;
+        ED_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+        ED_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        k_pose_part<<<1, PF_THREADS, 0, ctx->aux>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, pose, pf,
+                                                    ctx->pose_blk, ctx->grad + 12 * m, ctx->dmisc,
+                                                    ctx->misc + MI_STATUS); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        ED_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
+    }
     if (ctx->n_chunks > 0) {
         const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
@@ -1140,7 +1218,6 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     fa.x4 = (const float4 *)x;
     fa.w_rot = prm->w_rot;
     fa.w_reg = prm->w_reg;
-    const bool lm = prm->lm_accept != 0;
     fa.lambda = lm ? 0.f : prm->lambda;
     fa.jitter = prm->jitter;
     fa.bsr = ctx->bsr;
@@ -1149,15 +1226,15 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     fa.minv = ctx->minv;
     fa.node_energy = ctx->node_energy;
     fa.status = ctx->misc + MI_STATUS;
+    fa.m = m;
+    fa.misc = ctx->misc;
+    fa.dmisc = ctx->dmisc;
+    fa.stats = stats;
+    fa.lambda_report = fa.lambda;
+    ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ed_tm_begin(ctx, ED_KERNEL_FINALIZE, st);
     (lm ? k_finalize<false> : k_finalize<true>)<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
-    ED_LAUNCH_CHECK();
-    ed_solver_params pf = *prm;
-    if (lm) pf.lambda = 0.f;
-    k_pose_final<<<1, PF_THREADS, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, ctx->node_energy, m, pose,
-                                           pf, ctx->pose_blk,
-                                    ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS, stats); ed_note_launch();
     ED_LAUNCH_CHECK();
     if (lm) return lm_stage(ctx, prm, x, x_master, pose, stats, st);
     return ED_OK;
