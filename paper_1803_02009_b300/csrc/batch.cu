@@ -120,7 +120,7 @@ static ed_status batch_enqueue(ed_batch *b, const ed_frame *frames, const ed_sol
     if (s != ED_OK) return s;
     for (int p = 0; p < count && first == ED_OK; ++p)
         first = ed_gn_pre(b->ctx[p], &frames[p], &params[p], x[p], xm ? xm[p] : nullptr, pose[p],
-                          stat_at(stats, p, it), b->side[p % W]);
+                          stat_at(stats, p, it), b->side[p % W], false);
     s = join();   // always rejoin, also after an error (a capture must not end forked)
     if (first != ED_OK) return first;
     if (s != ED_OK) return s;

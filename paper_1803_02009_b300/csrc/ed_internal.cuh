@@ -48,7 +48,6 @@ enum {
     MI_BAR_GRAPH = 33,   // grid barrier arrival count of the Poisson sampler
     MI_LM_HAVE = 36,     // Levenberg-Marquardt: an accepted point is stored
     MI_LM_REJECT = 37,   // Levenberg-Marquardt: the current step undid the previous one
-    MI_FIN_DONE = 38,    // CTAs of k_finalize done (the last one forms the energy totals)
     MI_FUSE = 40,        // 40 kept, 41 lifted
     MI_READ = 48,        // 48..51 values gathered for one host read (chunk totals, upper blocks)
     MI_VOX = 52,         // 52..54 box-grid dims of ed_downsample, 55 its status
@@ -156,6 +155,7 @@ struct ed_context {
     size_t vec_stride;       // floats between vectors (multiple of 64: 16-byte aligned float4 rows)
     double *pcg_part;        // [2][ED_PCG_PART][ED_MAX_PCG_GRID] (component-major)
     double *red_part;        // [4][ED_MAX_PCG_GRID] per-CTA partials of ed_depth_error
+    unsigned *fin_tickets;   // [33][32] two-level done counters of k_finalize (one per 128-byte line)
     // fusion / scans
     unsigned long long *zbuf;  // [W H]
     int *regpix;             // [W H]
@@ -626,7 +626,7 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, d
                        ed_stats *stats, cudaStream_t st);
 ed_status ed_pcg_plan(ed_context *ctx, const int *row_ptr_host, cudaStream_t st);
 ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x, double *x_master,
-                    double *pose, ed_stats *stats, cudaStream_t st);
+                    double *pose, ed_stats *stats, cudaStream_t st, bool fork_pose = true);
 ed_status ed_gn_post(ed_context *ctx);
 ed_status ed_pcg_make_plan(const int *row_ptr_host, int m, int grid, int nt, ed_pcg_plan_t *pl, int *rows_start);
 ed_status ed_pcg_batch_plan(ed_context *const *ctxs, int count, int nt, int grid_total, ed_pcg_batch_plan_t *bp);

@@ -416,6 +416,7 @@ struct FinArgs {
     // and the pose pass's sums
     int m;
     int *misc;
+    unsigned *tickets;       // [33][32]: 32 group counters, then the counter of the groups
     double *dmisc;
     ed_stats *stats;
     float lambda_report;     // damping reported in the statistics
@@ -731,9 +732,18 @@ __device__ __forceinline__ void finalize_totals(const FinArgs &a)
     __shared__ float2 s_w[32 * FIN_WARPS / 32][2];
     __syncthreads();
     if (threadIdx.x == 0) {
+        // two-level ticket (32 group counters on their own lines, then one
+        // counter of the groups): no single address sees every CTA
         __threadfence();
-        const unsigned t = atomicAdd(reinterpret_cast<unsigned *>(a.misc + MI_FIN_DONE), 1u);
-        s_last = t == gridDim.x - 1;
+        const unsigned g = blockIdx.x & 31u, n = gridDim.x;
+        const unsigned in_group = (n - g + 31u) / 32u;
+        int last = 0;
+        if (atomicAdd(a.tickets + 32 * g, 1u) == in_group - 1) {
+            __threadfence();
+            const unsigned groups = n < 32u ? n : 32u;
+            last = atomicAdd(a.tickets + 32 * 32, 1u) == groups - 1;
+        }
+        s_last = last;
     }
     __syncthreads();
     if (!s_last) return;
@@ -782,8 +792,8 @@ __device__ __forceinline__ void finalize_totals(const FinArgs &a)
             a.stats->lm_rejected = 0;
             a.stats->lambda = a.lambda_report;
         }
-        a.misc[MI_FIN_DONE] = 0;   // ready for the next launch
     }
+    if (threadIdx.x < 33) a.tickets[32 * threadIdx.x] = 0;   // ready for the next launch
 }
 
 template <bool INV>
@@ -1156,7 +1166,7 @@ static ed_status check_frame(const ed_context *ctx, const ed_frame *fr)
 // one Gauss-Newton iteration up to the normal equations: association,
 // residuals, assembly, block inverses, pose rows
 ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params *prm, float *x, double *x_master,
-                    double *pose, ed_stats *stats, cudaStream_t st)
+                    double *pose, ed_stats *stats, cudaStream_t st, bool fork_pose)
 {
     if (!ctx || !prm || !x || !pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
     if (!ctx->have_graph) return ED_ERR_STATE;
@@ -1172,17 +1182,20 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     const bool lm = prm->lm_accept != 0;
     // the pose pass (pose block, its inverse, pose gradient, prior energies,
     // the point-pass sums) needs only the point pass: it runs on the context's
-    // second stream beside the assembly, joined before the finalisation
+    // second stream beside the assembly, joined before the finalisation (in a
+    // batch, where other problems fill the GPU, it stays on the step's stream)
     {
         ed_solver_params pf = *prm;
         if (lm) pf.lambda = 0.f;
-        ED_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
-        ED_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-        k_pose_part<<<1, PF_THREADS, 0, ctx->aux>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, pose, pf,
-                                                    ctx->pose_blk, ctx->grad + 12 * m, ctx->dmisc,
-                                                    ctx->misc + MI_STATUS); ed_note_launch();
+        cudaStream_t ps = fork_pose ? ctx->aux : st;
+        if (fork_pose) {
+            ED_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+            ED_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        }
+        k_pose_part<<<1, PF_THREADS, 0, ps>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, pose, pf, ctx->pose_blk,
+                                              ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
-        ED_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
+        if (fork_pose) ED_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
     }
     if (ctx->n_chunks > 0) {
         const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
@@ -1228,10 +1241,11 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     fa.status = ctx->misc + MI_STATUS;
     fa.m = m;
     fa.misc = ctx->misc;
+    fa.tickets = ctx->fin_tickets;
     fa.dmisc = ctx->dmisc;
     fa.stats = stats;
     fa.lambda_report = fa.lambda;
-    ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    if (fork_pose) ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ed_tm_begin(ctx, ED_KERNEL_FINALIZE, st);
     (lm ? k_finalize<false> : k_finalize<true>)<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
