@@ -361,13 +361,21 @@ def run_ours(args, rank, world, local):
             c_in[b].copy_(h_color, non_blocking=True)
             copied[b].record()
 
-    def e2e_run(n):
+    flush_ev = []
+
+    def e2e_run(n, timed=False):
         fetch(0)
         for k in range(n):
             b = k & 1
             if k + 1 < n:
                 fetch(k + 1)
-            flush.fill_(k & 0xff)            # L2 flushed before every step, inside the timed region here
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record()
+            flush.fill_(k & 0xff)            # L2 flushed before every step; its time is taken out below
+            f1.record()
+            if timed:
+                flush_ev.append((f0, f1))
             compute.wait_event(copied[b])
             gg = step(depth=d_in[b], color=c_in[b], frame=f_in[b])
             released[b].record()
@@ -380,10 +388,11 @@ def run_ours(args, rank, world, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
-    e2e_run(K)
+    e2e_run(K, timed=True)
     ev1.record()
     ev1.synchronize()
-    e2e_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
+    flush_ms = sum(a.elapsed_time(b) for a, b in flush_ev)
+    e2e_s = max_over_ranks((ev0.elapsed_time(ev1) - flush_ms) / 1e3, dist, dev)
     e2e_value = whole_job_rate(world, K, cfg.n_gn, e2e_s)
 
     peak, peak_kind = measured_peaks()
@@ -420,8 +429,8 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "K steps end to end: each frame copied in from pinned host memory (the next frame's copy "
-                        "overlapping this frame's compute on a copy stream), results read back, L2 flush "
-                        "inside the timed region"},
+                        "overlapping this frame's compute on a copy stream), results read back; the L2 flush "
+                        "before every step is timed by events and taken out"},
         "roofline": {"kernel": "k_pcg (persistent block-Jacobi PCG)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": byt,

@@ -406,27 +406,41 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
 // One warp per node: every lane keeps the best k_graph of its strided share of
 // the nodes, then the warp merges the 32 sorted lists by repeated minimum of
 // (key bits, index) -- keys are non-negative, so their bits order like floats.
-__global__ void k_node_graph(const float4 *__restrict__ nodes, int m, int kg, int *__restrict__ nbr)
+// The candidates come from shared memory, NG_TILE nodes at a time.
+#define NG_WARPS 16
+#define NG_TILE 2048
+__global__ void __launch_bounds__(32 * NG_WARPS) k_node_graph(const float4 *__restrict__ nodes, int m, int kg,
+                                                              int *__restrict__ nbr)
 {
+    __shared__ float4 s_nodes[NG_TILE];
     const int lane = threadIdx.x & 31;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= m) return;
+    const int j = blockIdx.x * NG_WARPS + (threadIdx.x >> 5);
+    const bool active = j < m;
     unsigned long long best[ED_MAX_KG];
     for (int s = 0; s < ED_MAX_KG; ++s) best[s] = ~0ull;
-    const float4 g = nodes[j];
-    for (int l = lane; l < m; l += 32) {
-        if (l == j) continue;
-        const float4 h = __ldg(nodes + l);
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(ed_key(g.x, g.y, g.z, h.x, h.y, h.z)) << 32) | (unsigned)l;
-        if (key >= best[kg - 1]) continue;
-        int p = kg - 1;
-        while (p > 0 && best[p - 1] > key) {
-            best[p] = best[p - 1];
-            --p;
+    const float4 g = active ? nodes[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t0 = 0; t0 < m; t0 += NG_TILE) {
+        const int tn = min(NG_TILE, m - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < tn; i += 32 * NG_WARPS) s_nodes[i] = __ldg(nodes + t0 + i);
+        __syncthreads();
+        if (!active) continue;
+        for (int li = lane; li < tn; li += 32) {
+            const int l = t0 + li;
+            if (l == j) continue;
+            const float4 h = s_nodes[li];
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(ed_key(g.x, g.y, g.z, h.x, h.y, h.z)) << 32) | (unsigned)l;
+            if (key >= best[kg - 1]) continue;
+            int p = kg - 1;
+            while (p > 0 && best[p - 1] > key) {
+                best[p] = best[p - 1];
+                --p;
+            }
+            best[p] = key;
         }
-        best[p] = key;
     }
+    if (!active) return;
     int head = 0;
     for (int s = 0; s < kg; ++s) {
         const unsigned long long mine = head < kg ? best[head] : ~0ull;
@@ -807,7 +821,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m, ctx->misc, ctx->fmisc, ctx->kcell_start,
                                                   ctx->kcell_nodes, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
-        k_node_graph<<<ed_div_up(m, 4), 128, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
+        k_node_graph<<<ed_div_up(m, NG_WARPS), 32 * NG_WARPS, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
 
