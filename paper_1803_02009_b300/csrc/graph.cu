@@ -185,23 +185,26 @@ __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const in
 // phases; the winning bids of earlier phases are read from L2 (they were
 // written by atomics of other CTAs during this launch).
 __device__ __forceinline__ void poisson_phase(const float4 *__restrict__ pos, const int2 *__restrict__ bucket, int e0,
-                                              int e1, int nx, int ny, int nz, float r2, int *cell_pick)
+                                              int e1, int nx, int ny, int nz, float r2, int *cell_pick,
+                                              int2 first_bc, float4 first_p)
 {
     const int lane = threadIdx.x & 31, grp = lane / 5, sub = lane % 5;
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    bool first = true;
     for (int wbase = e0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 6; wbase < e1; wbase += warps * 6) {
         const int e = wbase + grp;
         const bool act = grp < 6 && e < e1;
         bool ok = true;
         int i = -1, c = 0;
         if (act) {
-            const int2 bc = bucket[e];
+            // the first round's bucket entry and point were loaded before the barrier
+            const int2 bc = first ? first_bc : bucket[e];
             i = bc.x;
             c = bc.y;
             const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
             const int dz = sub - 2, az = cz + dz;
             if (az >= 0 && az < nz) {
-                const float4 p = pos[i];
+                const float4 p = first ? first_p : pos[i];
                 int q[25];
 #pragma unroll
                 for (int k = 0; k < 25; ++k) {
@@ -217,10 +220,26 @@ __device__ __forceinline__ void poisson_phase(const float4 *__restrict__ pos, co
                 }
             }
         }
+        first = false;
         // the group's verdict: every one of its five lanes found no close node
         const unsigned bad = __ballot_sync(0xffffffffu, act && !ok);
         const unsigned gmask = 0x1fu << (5 * grp);
         if (act && sub == 0 && !(bad & gmask)) atomicMin(&cell_pick[c], i);
+    }
+}
+
+// the bucket entry and point of this lane's group in the first round of a
+// phase (independent of the picks, so loaded before the barrier that opens it)
+__device__ __forceinline__ void poisson_prefetch(const float4 *__restrict__ pos, const int2 *__restrict__ bucket,
+                                                 int e0, int e1, int2 &bc, float4 &p)
+{
+    const int lane = threadIdx.x & 31, grp = lane / 5;
+    const int e = e0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 6 + grp;
+    bc = make_int2(0, 0);
+    p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (grp < 6 && e < e1) {
+        bc = bucket[e];
+        p = pos[bc.x];
     }
 }
 
@@ -234,9 +253,15 @@ __global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restr
     const int nx = misc_in[MI_DIMS], ny = misc_in[MI_DIMS + 1], nz = misc_in[MI_DIMS + 2];
     const float r2 = fmisc[MF_R2];
     unsigned target = 0;
+    int2 bc;
+    float4 p;
+    poisson_prefetch(pos, bucket, start[0], start[1], bc, p);
     for (int ph = 0; ph < 27; ++ph) {
-        poisson_phase(pos, bucket, start[ph], start[ph + 1], nx, ny, nz, r2, cell_pick);
-        if (ph < 26 && !ed_grid_sync(bar, status, gridDim.x, target, &s_flag)) return;
+        poisson_phase(pos, bucket, start[ph], start[ph + 1], nx, ny, nz, r2, cell_pick, bc, p);
+        if (ph < 26) {
+            poisson_prefetch(pos, bucket, start[ph + 1], start[ph + 2], bc, p);
+            if (!ed_grid_sync(bar, status, gridDim.x, target, &s_flag)) return;
+        }
     }
 }
 
