@@ -175,9 +175,13 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
     }
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_misc, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void **)&c->misc_host, sizeof(int) * MI_COUNT) != cudaSuccess) {
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
+        if (c->ev_misc) cudaEventDestroy(c->ev_misc);
         cudaFreeHost(c->row_ptr_host);
         cudaFreeHost(c->pinned);
         free(c);
@@ -194,6 +198,8 @@ extern "C" ed_status ed_destroy(ed_context *ctx)
     cudaStreamDestroy(ctx->aux);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
+    cudaEventDestroy(ctx->ev_misc);
+    cudaFreeHost(ctx->misc_host);
     cudaFreeHost(ctx->row_ptr_host);
     cudaFreeHost(ctx->pinned);
     free(ctx);

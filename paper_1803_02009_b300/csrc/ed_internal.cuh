@@ -201,6 +201,9 @@ struct ed_context {
     // the pose pass of a Gauss-Newton step runs beside the assembly
     cudaStream_t aux;
     cudaEvent_t ev_fork, ev_join;
+    // the misc words copied to the host without draining the stream
+    int *misc_host;          // [MI_COUNT] pinned
+    cudaEvent_t ev_misc;
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;

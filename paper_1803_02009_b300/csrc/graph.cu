@@ -101,11 +101,21 @@ __device__ __forceinline__ int3 cell3(float x, float y, float z, const float *fm
     return make_int3(c[0], c[1], c[2]);
 }
 
+#define NO_BID 0x7f7f7f7f
+
+// every cell of the sampling grid without a bid (the cell count from the set-up)
+__global__ void k_fill_cells(int *__restrict__ cell_pick, const int *__restrict__ misc)
+{
+    if (misc[MI_STATUS] != ED_OK) return;
+    const int cells = misc[MI_DIMS + 3];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += gridDim.x * blockDim.x) cell_pick[c] = NO_BID;
+}
+
 __global__ void k_cell_of(const float4 *__restrict__ pos, int n, const int *__restrict__ misc,
                           const float *__restrict__ fmisc, int *__restrict__ cell_of)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || misc[MI_STATUS] != ED_OK) return;   // no grid when the set-up failed
     const int dims[3] = {misc[MI_DIMS], misc[MI_DIMS + 1], misc[MI_DIMS + 2]};
     const float4 p = pos[i];
     int3 c = cell3(p.x, p.y, p.z, fmisc, fmisc[MF_INV], dims);
@@ -120,7 +130,6 @@ __global__ void k_cell_of(const float4 *__restrict__ pos, int n, const int *__re
 // of each other), so no per-phase commit is needed.  Node numbers follow the
 // (phase, linear cell index) order and are assigned by one scan at the end.
 
-#define NO_BID 0x7f7f7f7f
 
 __device__ __forceinline__ int cell_phase(int c, int nx, int ny)
 {
@@ -131,6 +140,7 @@ __device__ __forceinline__ int cell_phase(int c, int nx, int ny)
 __global__ void k_phase_count(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
                               int *__restrict__ cnt)
 {
+    if (misc[MI_STATUS] != ED_OK) return;
     __shared__ int h[27];
     if (threadIdx.x < 27) h[threadIdx.x] = 0;
     __syncthreads();
@@ -157,6 +167,7 @@ __global__ void k_phase_scan(const int *__restrict__ cnt, int *__restrict__ star
 __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
                                 const int *__restrict__ start, int *__restrict__ fill, int2 *__restrict__ bucket)
 {
+    if (misc[MI_STATUS] != ED_OK) return;
     __shared__ int h[27], base[27];
     const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1];
     for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
@@ -250,6 +261,7 @@ __global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restr
                                                            int *status)
 {
     __shared__ int s_flag;
+    if (*(volatile int *)status != ED_OK) return;   // every CTA: no grid when the set-up failed
     const int nx = misc_in[MI_DIMS], ny = misc_in[MI_DIMS + 1], nz = misc_in[MI_DIMS + 2];
     const float r2 = fmisc[MF_R2];
     unsigned target = 0;
@@ -759,17 +771,18 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     k_grid_setup<<<1, 1, 0, st>>>(ctx->misc, ctx->fmisc, m_in > 0 ? 1.0f : prm->node_radius, kc, ctx->lim.max_cells,
                                   m_in == 0); ed_note_launch();
     ED_LAUNCH_CHECK();
-    if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
-    if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
+    // the grid dims go to the host without draining the stream
+    ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
+    ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
 
-    // ---- nodes ----
+    // ---- nodes: the sampling launches need no host value, so they are queued
+    // before the grid dims are waited for (the sampler runs meanwhile); every
+    // one of them returns at once when the set-up failed ----
     int m;
+    int *pcnt = ctx->misc + MI_PHASES, *pstart = ctx->misc + MI_PHASES + 32, *pfill = ctx->misc + MI_PHASES + 64;
     if (m_in == 0) {
-        const int cells = hm[MI_DIMS + 3];
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->cell_pick, 0x7f, sizeof(int) * cells, st));
-        int *pcnt = ctx->misc + MI_PHASES, *pstart = ctx->misc + MI_PHASES + 32, *pfill = ctx->misc + MI_PHASES + 64;
         int2 *bucket = reinterpret_cast<int2 *>(ctx->ent_key);  // N (point, cell) pairs; the entry keys come later
-        ED_CUDA_TRY(cudaMemsetAsync(pcnt, 0, sizeof(int) * 27, st));
+        k_fill_cells<<<4 * ctx->num_sms, 256, 0, st>>>(ctx->cell_pick, ctx->misc); ed_note_launch();
         const int pg = min(ed_div_up(N, 256), 4 * ctx->num_sms);
         k_cell_of<<<ed_div_up(N, 256), 256, 0, st>>>(P4, N, ctx->misc, ctx->fmisc, ctx->cell_of); ed_note_launch();
         k_phase_count<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pcnt); ed_note_launch();
@@ -778,12 +791,11 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH_CHECK();
         // one cooperative launch for the 27 phases: one CTA per SM (fewer
         // barrier arrivals), sized down for small inputs
-        int per_sm = 0;
-        ED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson_all, POISSON_T, 0));
+        static int per_sm = -1;   // resident sampler CTAs per SM (the same for every call)
+        if (per_sm < 0) ED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson_all, POISSON_T, 0));
         int pick_grid = min(ed_div_up((N / 27 + 1) * 32 / 6 + 32, POISSON_T), min(per_sm, 1) * ctx->num_sms);
         if (pick_grid < 1) pick_grid = 1;
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_BAR_GRAPH, 0, sizeof(int), st));
-        {
+        {   // the arrival counter was cleared with the misc words above
             const int *misc_c = ctx->misc, *pstart_c = pstart;
             const float *fmisc_c = ctx->fmisc;
             const int2 *bucket_c = bucket;
@@ -795,6 +807,11 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             ed_note_launch();
             ED_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_poisson_all, pick_grid, POISSON_T, args, 0, st));
         }
+    }
+    ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
+    memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
+    if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
+    if (m_in == 0) {
         // node numbers in (phase, cell) order
         PhaseTable T;
         const int dx = hm[MI_DIMS], dy = hm[MI_DIMS + 1], dz = hm[MI_DIMS + 2];
@@ -832,7 +849,9 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     }
     if (m < ED_K || (prm->weight_mode == ED_WEIGHT_EQ2 && m < ED_K + 1) || m <= prm->k_graph) return ED_ERR_ARG;
 
-    // ---- nearest nodes and weights ----
+    // ---- node graph first (it needs only the nodes: the GPU runs it while the
+    // search-grid launches are queued), then nearest nodes and weights ----
+    k_node_graph<<<ed_div_up(m, NG_WARPS), 32 * NG_WARPS, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
     {
         const int kcells = hm[MI_KDIMS + 3];
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
@@ -846,7 +865,6 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m, ctx->misc, ctx->fmisc, ctx->kcell_start,
                                                   ctx->kcell_nodes, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
-        k_node_graph<<<ed_div_up(m, NG_WARPS), 32 * NG_WARPS, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
 
