@@ -320,11 +320,14 @@ __global__ void k_node_write(PhaseTable T, int total, const int *__restrict__ mi
 // nearest-node search grid
 // ---------------------------------------------------------------------------
 
-__global__ void k_kcell_count(const float4 *__restrict__ nodes, int m, const int *__restrict__ misc,
-                              const float *__restrict__ fmisc, int *__restrict__ cnt, int *__restrict__ cell_of_node)
+// (m, the node count, is read from the graph's counts: the launches are queued
+// before the host knows it)
+__global__ void k_kcell_count(const float4 *__restrict__ nodes, const int *__restrict__ m_dev,
+                              const int *__restrict__ misc, const float *__restrict__ fmisc, int *__restrict__ cnt,
+                              int *__restrict__ cell_of_node)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+    if (j >= *m_dev) return;
     const int dims[3] = {misc[MI_KDIMS], misc[MI_KDIMS + 1], misc[MI_KDIMS + 2]};
     const float4 g = nodes[j];
     int3 c = cell3(g.x, g.y, g.z, fmisc, fmisc[MF_KINV], dims);
@@ -333,11 +336,11 @@ __global__ void k_kcell_count(const float4 *__restrict__ nodes, int m, const int
     atomicAdd(&cnt[L], 1);
 }
 
-__global__ void k_kcell_fill(int m, const int *__restrict__ start, int *__restrict__ fill,
+__global__ void k_kcell_fill(const int *__restrict__ m_dev, const int *__restrict__ start, int *__restrict__ fill,
                              const int *__restrict__ cell_of_node, int *__restrict__ kn)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+    if (j >= *m_dev) return;
     const int L = cell_of_node[j];
     kn[start[L] + atomicAdd(&fill[L], 1)] = j;
 }
@@ -360,13 +363,14 @@ __device__ __forceinline__ void topk_ins(float *kk, int *ii, float key, int id)
 // K+1 nearest nodes by rings of search cells; a ring R is the last one needed
 // once the (K+1)-th key is below (R * cell)^2 (with a round-off margin): every
 // node outside rings 0..R is at least R cells away.  Then the weights.
-__global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__restrict__ nodes, int m,
-                      const int *__restrict__ misc, const float *__restrict__ fmisc, const int *__restrict__ start,
-                      const int *__restrict__ kn, int mode, float sigma, ushort4 *__restrict__ idx_out,
-                      float4 *__restrict__ w_out)
+__global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__restrict__ nodes,
+                      const int *__restrict__ m_dev, const int *__restrict__ misc, const float *__restrict__ fmisc,
+                      const int *__restrict__ start, const int *__restrict__ kn, int mode, float sigma,
+                      ushort4 *__restrict__ idx_out, float4 *__restrict__ w_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int m = *m_dev;
     const int dims[3] = {misc[MI_KDIMS], misc[MI_KDIMS + 1], misc[MI_KDIMS + 2]};
     const float kc = fmisc[MF_KCELL];
     const float4 p = pos[i];
@@ -446,10 +450,12 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
 // The candidates come from shared memory, NG_TILE nodes at a time.
 #define NG_WARPS 16
 #define NG_TILE 2048
-__global__ void __launch_bounds__(32 * NG_WARPS) k_node_graph(const float4 *__restrict__ nodes, int m, int kg,
+__global__ void __launch_bounds__(32 * NG_WARPS) k_node_graph(const float4 *__restrict__ nodes,
+                                                              const int *__restrict__ m_dev, int kg,
                                                               int *__restrict__ nbr)
 {
     __shared__ float4 s_nodes[NG_TILE];
+    const int m = *m_dev;
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * NG_WARPS + (threadIdx.x >> 5);
     const bool active = j < m;
@@ -709,6 +715,14 @@ __global__ void k_kp_expand(const float4 *__restrict__ kp, int nk, int n_model, 
     nrm[n_model + t] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// node counts of the sampled graph: counts[0] = min(sampled, max_nodes), counts[1] = sampled
+__global__ void k_set_counts(const int *__restrict__ misc, int max_nodes, int *__restrict__ counts)
+{
+    const int mt = misc[MI_PHASE_BASE];
+    counts[0] = mt < max_nodes ? mt : max_nodes;
+    counts[1] = mt;
+}
+
 // bounding box of n points into misc[MI_BBOX .. MI_BBOX + 5] (ordered ints)
 ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_t st)
 {
@@ -832,41 +846,45 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_node_write<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, pre, P4, G4, max_nodes); ed_note_launch();
         ED_LAUNCH_CHECK();
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_PHASE_BASE, pre + tot, sizeof(int), cudaMemcpyDeviceToDevice, st));
-        if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
-        if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
-        const int mt = hm[MI_PHASE_BASE];
-        m = mt < max_nodes ? mt : max_nodes;
-        ctx->pinned[ED_MAX_PCG_GRID + 3] = m;
-        ctx->pinned[ED_MAX_PCG_GRID + 4] = mt;
-        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts, ctx->pinned + ED_MAX_PCG_GRID + 3, 2 * sizeof(int),
-                                    cudaMemcpyHostToDevice, st));
+        k_set_counts<<<1, 1, 0, st>>>(ctx->misc, max_nodes, graph->counts); ed_note_launch();
     } else {
-        m = m_in;
-        ctx->pinned[ED_MAX_PCG_GRID + 3] = m;
-        ctx->pinned[ED_MAX_PCG_GRID + 4] = m;
+        ctx->pinned[ED_MAX_PCG_GRID + 3] = m_in;
+        ctx->pinned[ED_MAX_PCG_GRID + 4] = m_in;
         ED_CUDA_TRY(cudaMemcpyAsync(graph->counts, ctx->pinned + ED_MAX_PCG_GRID + 3, 2 * sizeof(int),
                                     cudaMemcpyHostToDevice, st));
     }
-    if (m < ED_K || (prm->weight_mode == ED_WEIGHT_EQ2 && m < ED_K + 1) || m <= prm->k_graph) return ED_ERR_ARG;
+    // the node count goes to the host while the next kernels run: they read it
+    // from graph->counts and are sized for max_nodes
+    ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
+    ED_CUDA_TRY(cudaMemcpyAsync(ctx->pinned + ED_MAX_PCG_GRID + 5, graph->counts, 2 * sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
+    ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
 
     // ---- node graph first (it needs only the nodes: the GPU runs it while the
     // search-grid launches are queued), then nearest nodes and weights ----
-    k_node_graph<<<ed_div_up(m, NG_WARPS), 32 * NG_WARPS, 0, st>>>(G4, m, prm->k_graph, graph->nbr); ed_note_launch();
+    const int *m_dev = graph->counts;
+    k_node_graph<<<ed_div_up(max_nodes, NG_WARPS), 32 * NG_WARPS, 0, st>>>(G4, m_dev, prm->k_graph, graph->nbr); ed_note_launch();
     {
         const int kcells = hm[MI_KDIMS + 3];
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
         int *cell_of_node = ctx->row_cnt;   // scratch (m + 1 ints)
-        k_kcell_count<<<ed_div_up(m, 256), 256, 0, st>>>(G4, m, ctx->misc, ctx->fmisc, ctx->kcell_cnt, cell_of_node); ed_note_launch();
+        k_kcell_count<<<ed_div_up(max_nodes, 256), 256, 0, st>>>(G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_cnt,
+                                                                 cell_of_node); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->kcell_cnt, ctx->kcell_start, kcells, st)) != ED_OK) return s;
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
-        k_kcell_fill<<<ed_div_up(m, 256), 256, 0, st>>>(m, ctx->kcell_start, ctx->kcell_cnt, cell_of_node,
-                                                         ctx->kcell_nodes); ed_note_launch();
-        k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m, ctx->misc, ctx->fmisc, ctx->kcell_start,
+        k_kcell_fill<<<ed_div_up(max_nodes, 256), 256, 0, st>>>(m_dev, ctx->kcell_start, ctx->kcell_cnt, cell_of_node,
+                                                                ctx->kcell_nodes); ed_note_launch();
+        k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_start,
                                                   ctx->kcell_nodes, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
+    ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
+    memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
+    if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
+    m = ctx->pinned[ED_MAX_PCG_GRID + 5];
+    if (m < ED_K || (prm->weight_mode == ED_WEIGHT_EQ2 && m < ED_K + 1) || m <= prm->k_graph) return ED_ERR_ARG;
 
     // ---- block pattern ----
     const int words = ed_div_up(m, 32);
