@@ -126,9 +126,10 @@ extern "C" ed_status ed_fuse(ed_context *ctx, const float *pos, const float *nrm
                              int *t_out, int *counts_out, int *reg_out, cudaStream_t st)
 {
     (void)nrm;
-    if (!ctx || !pos || !col || !tstamp || !wpos || !wnrm || !fr || !F || !pos_out || !nrm_out || !col_out || !t_out ||
-        !counts_out || n_in < 0 || capacity < 0 || n_in > ctx->lim.max_points)
+    if (!ctx || !fr || !F || !pos_out || !nrm_out || !col_out || !t_out || !counts_out || n_in < 0 || capacity < 0 ||
+        n_in > ctx->lim.max_points)
         return ED_ERR_ARG;
+    if (n_in > 0 && (!pos || !col || !tstamp || !wpos || !wnrm)) return ED_ERR_ARG;   // (NULL allowed for no model)
     if (!fr->depth || !fr->nmap || !fr->color || fr->intr.width <= 0 || fr->intr.height <= 0 ||
         fr->intr.width > ctx->lim.max_width || fr->intr.height > ctx->lim.max_height)
         return ED_ERR_ARG;

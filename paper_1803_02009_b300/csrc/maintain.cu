@@ -112,18 +112,19 @@ extern "C" ed_status ed_downsample(ed_context *ctx, const float *pos, const floa
                                    float *pos_out, float *nrm_out, float *col_out, int *t_out, int *counts_out,
                                    cudaStream_t st)
 {
-    if (!ctx || !P || !pos || !nrm || !col || !tstamp || !pos_out || !nrm_out || !col_out || !t_out || !counts_out ||
-        n_in < 0 || n_in > ctx->lim.max_points || capacity < 0 || !(P->box > 0.f) || !isfinite(P->box))
+    if (!ctx || !P || !counts_out || n_in < 0 || n_in > ctx->lim.max_points || capacity < 0 || !(P->box > 0.f) ||
+        !isfinite(P->box))
         return ED_ERR_ARG;
+    if (n_in == 0) {   // nothing to merge (the arrays may be NULL)
+        ED_CUDA_TRY(cudaMemsetAsync(counts_out, 0, 2 * sizeof(int), st));
+        return ED_OK;
+    }
+    if (!pos || !nrm || !col || !tstamp || !pos_out || !nrm_out || !col_out || !t_out) return ED_ERR_ARG;
     if (((uintptr_t)pos & 15) || ((uintptr_t)nrm & 15) || ((uintptr_t)col & 15) || ((uintptr_t)pos_out & 15) ||
         ((uintptr_t)nrm_out & 15) || ((uintptr_t)col_out & 15))
         return ED_ERR_ARG;
     if (pos == pos_out || nrm == nrm_out || col == col_out || (const float *)tstamp == (const float *)t_out)
         return ED_ERR_ARG;
-    if (n_in == 0) {
-        ED_CUDA_TRY(cudaMemsetAsync(counts_out, 0, 2 * sizeof(int), st));
-        return ED_OK;
-    }
     const float4 *P4 = (const float4 *)pos;
     ed_status s;
     if ((s = ed_bbox_enqueue(ctx, P4, n_in, st)) != ED_OK) return s;
@@ -224,7 +225,7 @@ __global__ void k_de_final(const double *__restrict__ part, int nb, double *__re
 extern "C" ed_status ed_depth_error(ed_context *ctx, const float *wpos, int n_points, const float *depth,
                                     ed_intrinsics intr, double *out, cudaStream_t st)
 {
-    if (!ctx || !wpos || !depth || !out || n_points < 0 || n_points > ctx->lim.max_points || intr.width <= 0 ||
+    if (!ctx || (!wpos && n_points > 0) || !depth || !out || n_points < 0 || n_points > ctx->lim.max_points || intr.width <= 0 ||
         intr.height <= 0 || intr.width > ctx->lim.max_width || intr.height > ctx->lim.max_height ||
         !(intr.fx > 0.f) || !(intr.fy > 0.f) || ((uintptr_t)wpos & 15))
         return ED_ERR_ARG;
