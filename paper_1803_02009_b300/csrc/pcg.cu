@@ -46,6 +46,7 @@ struct PcgArgs {
     float *d;                // the solution
     float *z0, *s0, *s1;     // published z of the set-up, s = M^-1 q of even / odd iterations
     double *part;            // [2][PCG_NC][ED_MAX_PCG_GRID] partials of even / odd iterations, component-major
+                             // (stored in the accumulator's type: float in FP32 mode, float2 in mixed mode)
     float *x;                // node parameters, x += d at the end (all CTAs passed every barrier)
     double *xm;              // FP64 master copy (mixed precision) or NULL
     double *pose;            // pose += d_pose (CTA 0)
@@ -58,8 +59,9 @@ struct PcgArgs {
 // mode: float-float (hi + lo, about 44 significant bits) on the FP32 pipe --
 // each product is formed exactly (a b = p + e with e = fma(a, b, -p)) and
 // summed by error-free two-sums; on B300 the FP64 rate is a small fraction of
-// the FP32 rate, so the extended precision is kept off the FP64 units.  The
-// per-CTA partials between CTAs are stored as double.
+// the FP32 rate, so the extended precision is kept off the FP64 units (the
+// per-CTA partials between CTAs are stored in the accumulator's own type:
+// a conversion to and from double would run on those units).
 template <typename DT> struct PcgAcc;
 
 template <> struct PcgAcc<float> {
@@ -68,8 +70,7 @@ template <> struct PcgAcc<float> {
     static __device__ __forceinline__ T madd(T acc, float a, float b) { return acc + a * b; }
     static __device__ __forceinline__ T add(T x, T y) { return x + y; }
     static __device__ __forceinline__ T shfl(T x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
-    static __device__ __forceinline__ T from_double(double d) { return (float)d; }
-    static __device__ __forceinline__ double to_double(T x) { return (double)x; }
+    static __device__ __forceinline__ T shfl_down(T x, int o) { return __shfl_down_sync(0xffffffffu, x, o); }
     static __device__ __forceinline__ float to_float(T x) { return x; }
 };
 
@@ -86,67 +87,80 @@ template <> struct PcgAcc<double> {
     {
         return make_float2(__shfl_xor_sync(0xffffffffu, x.x, o), __shfl_xor_sync(0xffffffffu, x.y, o));
     }
-    static __device__ __forceinline__ T from_double(double d)
+    static __device__ __forceinline__ T shfl_down(T x, int o)
     {
-        const float hi = (float)d;
-        return make_float2(hi, (float)(d - (double)hi));
+        return make_float2(__shfl_down_sync(0xffffffffu, x.x, o), __shfl_down_sync(0xffffffffu, x.y, o));
     }
-    static __device__ __forceinline__ double to_double(T x) { return (double)x.x + (double)x.y; }
     static __device__ __forceinline__ float to_float(T x) { return x.x + x.y; }
 };
 
 // component w of the partials of CTA c
-__device__ __forceinline__ double *part_at(double *part, int w, int c) { return part + (size_t)w * ED_MAX_PCG_GRID + c; }
+template <typename DT>
+__device__ __forceinline__ typename PcgAcc<DT>::T *part_at(double *part, int w, int c)
+{
+    return reinterpret_cast<typename PcgAcc<DT>::T *>(part) + (size_t)w * ED_MAX_PCG_GRID + c;
+}
 
-// sums the NC components of all CTA partials: WPC warps per component (all
-// warps when NC is small) stride over the CTAs, components in rounds of
-// GROUPS when there are more components than warps; then a fixed shuffle
-// tree and a fixed-order sum of the warp results that every thread forms
-// itself (one CTA barrier), so every CTA and every thread gets the same
-// values.  `sh` must not be in use by other code between two calls.
+// work split of the sum of NC partial components over the warps of a CTA:
+// WPC warps per component (all warps when NC is small) stride over the CTAs,
+// components in rounds of GROUPS when there are more components than warps
+template <int NT, int NC> struct PartSplit {
+    static constexpr int NWARP = NT / 32;
+    static constexpr int WPC = NWARP >= NC ? NWARP / NC : 1;
+    static constexpr int GROUPS = NWARP / WPC;
+    static constexpr int ROUNDS = (NC + GROUPS - 1) / GROUPS;
+    static_assert(ROUNDS <= 8, "warp results of one component round per sh column");
+};
+
+// first stage of the sum of the NC components of all CTA partials: every
+// warp's share through a fixed shuffle tree into `sh`, then one CTA barrier.
+// Components whose bit is set in `skip` are not loaded (their totals read 0).
+// sum_partials_get gives the totals (a fixed-order sum of the warp results,
+// the same in every CTA and thread).  `sh` must not be in use by other code
+// between the two.
 template <typename DT, int NT, int NC>
-__device__ __forceinline__ void sum_partials(const double *part, int nb, typename PcgAcc<DT>::T (*sh)[8],
-                                             typename PcgAcc<DT>::T (&out)[NC])
+__device__ __forceinline__ void sum_partials(double *part, int nb, typename PcgAcc<DT>::T (*sh)[8], unsigned skip = 0u)
 {
     typedef PcgAcc<DT> A;
-    constexpr int NWARP = NT / 32;
-    constexpr int WPC = NWARP >= NC ? NWARP / NC : 1;   // warps per component
-    constexpr int GROUPS = NWARP / WPC;                 // components per round
-    constexpr int ROUNDS = (NC + GROUPS - 1) / GROUPS;
-    static_assert(ROUNDS <= 8, "warp results of one component round per sh column");
+    typedef PartSplit<NT, NC> S;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int g = wid / WPC, wsub = wid - g * WPC;
+    const int g = wid / S::WPC, wsub = wid - g * S::WPC;
 #pragma unroll
-    for (int rd = 0; rd < ROUNDS; ++rd) {
-        const int c = rd * GROUPS + g;
+    for (int rd = 0; rd < S::ROUNDS; ++rd) {
+        const int c = rd * S::GROUPS + g;
         typename A::T s = A::zero();
-        if (g < GROUPS && c < NC) {
-            const double *src = part + (size_t)c * ED_MAX_PCG_GRID;
+        if (g < S::GROUPS && c < NC && !((skip >> c) & 1u)) {
+            const typename A::T *src = part_at<DT>(part, c, 0);
             // every load of the lane in flight before the first add (up to 8 per lane)
-            double v[8];
+            typename A::T v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int k = wsub * 32 + lane + u * WPC * 32;
-                v[u] = k < nb ? __ldcg(src + k) : 0.0;
+                const int k = wsub * 32 + lane + u * S::WPC * 32;
+                v[u] = k < nb ? __ldcg(src + k) : A::zero();
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (wsub * 32 + lane + u * WPC * 32 < nb) s = A::add(s, A::from_double(v[u]));
-            for (int k = wsub * 32 + lane + 8 * WPC * 32; k < nb; k += WPC * 32) s = A::add(s, A::from_double(__ldcg(src + k)));
+                if (wsub * 32 + lane + u * S::WPC * 32 < nb) s = A::add(s, v[u]);
+            for (int k = wsub * 32 + lane + 8 * S::WPC * 32; k < nb; k += S::WPC * 32)
+                s = A::add(s, __ldcg(src + k));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
         if (lane == 0) sh[wid][rd] = s;
     }
     __syncthreads();
+}
+
+template <typename DT, int NT, int NC>
+__device__ __forceinline__ typename PcgAcc<DT>::T sum_partials_get(const typename PcgAcc<DT>::T (*sh)[8], int c)
+{
+    typedef PcgAcc<DT> A;
+    typedef PartSplit<NT, NC> S;
+    const int rd = c / S::GROUPS, gg = c - rd * S::GROUPS;
+    typename A::T r = A::zero();
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const int rd = c / GROUPS, gg = c - rd * GROUPS;
-        typename A::T r = A::zero();
-#pragma unroll
-        for (int k = 0; k < WPC; ++k) r = A::add(r, sh[gg * WPC + k][rd]);
-        out[c] = r;
-    }
+    for (int k = 0; k < S::WPC; ++k) r = A::add(r, sh[gg * S::WPC + k][rd]);
+    return r;
 }
 
 // block reduction of NV values per thread: after one CTA barrier,
@@ -164,6 +178,37 @@ __device__ __forceinline__ void block_sum_n(typename PcgAcc<DT>::T (&v)[NV], typ
         for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl(x, o));
         if (lane == 0) sh[wid][k] = x;
     }
+    __syncthreads();
+}
+
+// the same for several values: a butterfly over the warp that halves the
+// values a lane carries at every step (lane bit o keeps the upper or the lower
+// half and receives that half from its partner), so lanes 2c and 2c + 1 end
+// with value c's warp total -- about 2 NV shuffles instead of 5 NV
+template <typename DT, int NT, int NV, int SW>
+__device__ __forceinline__ void block_sum_bfly(const typename PcgAcc<DT>::T (&v)[NV], typename PcgAcc<DT>::T (*sh)[SW])
+{
+    typedef PcgAcc<DT> A;
+    typedef typename A::T T;
+    static_assert(NV > 1 && NV <= 16 && NV <= SW, "up to 16 values, one shared column each");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = k < NV ? v[k] : A::zero();
+#pragma unroll
+    for (int lvl = 0; lvl < 4; ++lvl) {
+        const int o = 16 >> lvl, half = 8 >> lvl;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const T send = up ? x[j] : x[j + half];
+            const T keep = up ? x[j + half] : x[j];
+            x[j] = A::add(keep, A::shfl(send, o));
+        }
+    }
+    const T r = A::add(x[0], A::shfl(x[0], 1));
+    const int c = lane >> 1;
+    if (!(lane & 1) && c < NV) sh[wid][c] = r;
     __syncthreads();
 }
 
@@ -217,6 +262,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     // the pose parts of r, z, p, d: the same values in every CTA
     __shared__ float s_rp[6], s_zp[6], s_pp[6], s_dp[6];
     __shared__ float s_Hpp[36], s_Mp[36];
+    __shared__ float s_ab[2];               // alpha, beta of the iteration
+    __shared__ int s_ctl;                   // 0 go on, 1 converged or stalled, 2 breakdown
 
     unsigned target = 0;
     const int m = a.m;
@@ -232,9 +279,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     const int t = threadIdx.x;
     const int grp = t / 12, rr = t % 12;
     const bool in_grp = grp < ROWS_PER_PASS;
-    // q = H p: with few rows, S groups of 12 threads share the blocks of a row
-    const int S = rows <= ROWS_PER_PASS ? ROWS_PER_PASS / rows : 1;
-    const int rpp = ROWS_PER_PASS / S;   // rows per pass
+    // q = H p.  Up to ROWS_PER_PASS rows: every row gets groups of 12 threads
+    // in proportion to its blocks (at most T blocks per thread, T as small as
+    // the groups allow), mapped here; more rows: one group per row, in passes.
+    constexpr int NG = ROWS_PER_PASS;
+    const bool split_rows = rows <= NG;
+    __shared__ short s_grow[NG], s_gsp[NG];     // group -> row, split index (row -1: idle)
+    __shared__ short s_rfirst[NG], s_rcnt[NG];  // row -> first group, groups
     const int P = 12 * m;
     const float *Hpp = s_Hpp, *Mp = s_Mp;
 
@@ -293,6 +344,49 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     }
     __syncthreads();
     bool h_ready = false;
+    if (split_rows && t < 32) {   // (read after the grid barrier of the set-up)
+        auto blocks = [&](int j) { return j < rows ? a.row_ptr[r0 + j + 1] - a.row_ptr[r0 + j] : 0; };
+        const int bA = blocks(t), bB = blocks(t + 32);
+        int T = max(1, (nblk + NG - 1) / NG);
+        for (;;) {   // ends: at T = the longest row every row takes one group
+            int c = (bA + T - 1) / T + (bB + T - 1) / T;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (c <= NG) break;
+            ++T;
+        }
+        const int gA = (bA + T - 1) / T, gB = (bB + T - 1) / T;
+        int xA = gA, xB = gB;   // inclusive scans over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yA = __shfl_up_sync(0xffffffffu, xA, o), yB = __shfl_up_sync(0xffffffffu, xB, o);
+            if (t >= o) {
+                xA += yA;
+                xB += yB;
+            }
+        }
+        const int totA = __shfl_sync(0xffffffffu, xA, 31), tot = totA + __shfl_sync(0xffffffffu, xB, 31);
+        if (t < rows) {
+            const int f = xA - gA;
+            s_rfirst[t] = (short)f;
+            s_rcnt[t] = (short)gA;
+            for (int q = 0; q < gA; ++q) {
+                s_grow[f + q] = (short)t;
+                s_gsp[f + q] = (short)q;
+            }
+        }
+        if (t + 32 < rows) {
+            const int f = totA + xB - gB;
+            s_rfirst[t + 32] = (short)f;
+            s_rcnt[t + 32] = (short)gB;
+            for (int q = 0; q < gB; ++q) {
+                s_grow[f + q] = (short)(t + 32);
+                s_gsp[f + q] = (short)q;
+            }
+        }
+        for (int g = tot + t; g < NG; g += 32) s_grow[g] = -1;
+    }
+
 
     // dst = M^-1 src for the own rows (thread = one output row of a node),
     // also into gdst; f(element index, value) sees every result
@@ -333,7 +427,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     // (the partials of odd iterations hold the set-up's: iteration 0 writes the even ones
     // while slower CTAs may still read these)
     double *part_setup = a.part + (size_t)ED_MAX_PCG_GRID * PCG_NC;
-    if (t == 0) *part_at(part_setup, 0, cta) = A::to_double(block_sum_get<DT, NT>(s_red, 0));
+    if (t == 0) *part_at<DT>(part_setup, 0, cta) = block_sum_get<DT, NT>(s_red, 0);
     if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
         fail();
         return;
@@ -349,9 +443,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     for (int i = t; i < rows * 12; i += NT) ps[i] = zs[i];
     float res0;
     {
-        AT sums[1];
-        sum_partials<DT, NT, 1>(part_setup, nb, s_red2, sums);
-        AT v = sums[0];
+        sum_partials<DT, NT, 1>(part_setup, nb, s_red2);
+        AT v = sum_partials_get<DT, NT, 1>(s_red2, 0);
 #pragma unroll
         for (int i = 0; i < 6; ++i) v = A::madd(v, s_rp[i], s_rp[i]);
         res0 = sqrtf(A::to_float(v));
@@ -406,7 +499,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         }
     };
 
-    float rr_last = res0 * res0;   // ||r||^2 of the last residual
+    float rr_last = res0 * res0;   // ||r||^2 of the last residual (thread 0)
     bool breakdown = false;        // the same in every CTA: it follows from the summed p.q
     int it = 0;
     for (; it < a.n_iter; ++it) {
@@ -425,30 +518,56 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         // ---- q = H p for the own rows (thread = one output row of one of
         // the S splits of a row's blocks), partials C p of the pose rows ----
         AT cp[6] = {A::zero(), A::zero(), A::zero(), A::zero(), A::zero(), A::zero()};
-        for (int j0 = 0; j0 < rows; j0 += rpp) {
-            const int jl = j0 + grp / S, sp = grp - (grp / S) * S;
-            if (in_grp && grp < rpp * S && jl < rows) {
+        for (int j0 = 0; j0 < rows; j0 += NG) {
+            int jl = j0 + grp, sp = 0, S = 1;
+            if (split_rows && in_grp) {
+                jl = s_grow[grp];
+                sp = s_gsp[grp];
+                S = jl >= 0 ? s_rcnt[jl] : 1;
+            }
+            if (in_grp && jl >= 0 && jl < rows) {
                 const int j = r0 + jl;
                 const int bb0 = a.row_ptr[j] - b0, bb1 = a.row_ptr[j + 1] - b0;
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-                for (int lb = bb0 + sp; lb < bb1; lb += S) {
-                    const float4 *hrow = lb < ncache ? reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12)
-                                                     : reinterpret_cast<const float4 *>(a.bsr + (size_t)(b0 + lb) * 144 + rr * 12);
-                    const float4 *pl = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
-                    const float4 h0 = hrow[0], h1 = hrow[1], h2 = hrow[2];
-                    const float4 p0 = pl[0], p1 = pl[1], p2 = pl[2];
-                    acc0 += h0.x * p0.x + h0.y * p0.y + h0.z * p0.z + h0.w * p0.w;
-                    acc1 += h1.x * p1.x + h1.y * p1.y + h1.z * p1.z + h1.w * p1.w;
-                    acc2 += h2.x * p2.x + h2.y * p2.y + h2.z * p2.z + h2.w * p2.w;
+                auto hrow_of = [&](int lb) {
+                    return lb < ncache ? reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12)
+                                       : reinterpret_cast<const float4 *>(a.bsr + (size_t)(b0 + lb) * 144 + rr * 12);
+                };
+                auto madd4 = [](float acc, float4 h, float4 p) {
+                    return fmaf(h.w, p.w, fmaf(h.z, p.z, fmaf(h.y, p.y, fmaf(h.x, p.x, acc))));
+                };
+                int lb = bb0 + sp;
+                // two blocks per step, every load of both before the first product
+                for (; lb + S < bb1; lb += 2 * S) {
+                    const float4 *ha = hrow_of(lb), *hb = hrow_of(lb + S);
+                    const float4 *pa = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
+                    const float4 *pbb = reinterpret_cast<const float4 *>(pb + (size_t)(lb + S) * 12);
+                    const float4 ha0 = ha[0], ha1 = ha[1], ha2 = ha[2], hb0 = hb[0], hb1 = hb[1], hb2 = hb[2];
+                    const float4 pa0 = pa[0], pa1 = pa[1], pa2 = pa[2], pb0 = pbb[0], pb1 = pbb[1], pb2 = pbb[2];
+                    acc0 = madd4(madd4(acc0, ha0, pa0), hb0, pb0);
+                    acc1 = madd4(madd4(acc1, ha1, pa1), hb1, pb1);
+                    acc2 = madd4(madd4(acc2, ha2, pa2), hb2, pb2);
+                }
+                if (lb < bb1) {
+                    const float4 *ha = hrow_of(lb);
+                    const float4 *pa = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
+                    acc0 = madd4(acc0, ha[0], pa[0]);
+                    acc1 = madd4(acc1, ha[1], pa[1]);
+                    acc2 = madd4(acc2, ha[2], pa[2]);
                 }
                 qsplit[grp * 12 + rr] = acc0 + acc1 + acc2;
             }
             __syncthreads();
-            // the S splits of a row in a fixed order, plus the pose coupling C_j^T p_pose
+            // the splits of a row in a fixed order, plus the pose coupling C_j^T p_pose
             const int jr = j0 + grp;
-            if (in_grp && grp < rpp && jr < rows) {
+            if (in_grp && jr < rows) {
                 float qv = 0.f;
-                for (int q = 0; q < S; ++q) qv += qsplit[(grp * S + q) * 12 + rr];
+                if (split_rows) {
+                    const int f = s_rfirst[jr], n = s_rcnt[jr];
+                    for (int q = 0; q < n; ++q) qv += qsplit[(f + q) * 12 + rr];
+                } else {
+                    qv = qsplit[grp * 12 + rr];
+                }
                 const float *C = Cs + jr * 72;
 #pragma unroll
                 for (int s = 0; s < 6; ++s) qv += C[12 * s + rr] * s_pp[s];
@@ -475,65 +594,88 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                 q2 = A::madd(q2, qv, qv);
             });
             AT vv[PCG_NC] = {pq, qz, qq2, rz, r2, rq, q2, cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
-            block_sum_n<DT, NT, PCG_NC>(vv, s_red);
-            if (t < PCG_NC) *part_at(part, t, cta) = A::to_double(block_sum_get<DT, NT>(s_red, t));
+            block_sum_bfly<DT, NT, PCG_NC>(vv, s_red);
+            if (t < PCG_NC) *part_at<DT>(part, t, cta) = block_sum_get<DT, NT>(s_red, t);
         }
         if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
             fail();
             return;
         }
         stage_issue(sg);
-        // ---- every thread: the sums, the pose rows (q_p = sum C p + H_pp p_p,
-        // s_p = M_p q_p) and their terms, alpha, beta ----
-        float alpha, beta, qp[6], sp[6];
-        AT rq_t, q2_t;
+        // ---- the sums of the partials; warp 0 adds the pose rows (q_p =
+        // sum C p + H_pp p_p, s_p = M_p q_p; lane i < 6 holds entry i) and
+        // their terms, takes the loop tests, forms alpha and beta and hands
+        // them to the CTA ----
+        // r.q and q.q serve only ||r'||^2 after the last iteration: not loaded before
+        sum_partials<DT, NT, PCG_NC>(part, nb, s_red2, it + 1 < a.n_iter ? (1u << 5) | (1u << 6) : 0u);
+        float qpi = 0.f, spi = 0.f;   // lanes i < 6 of warp 0: q_p[i], s_p[i]
+        AT rq_t = A::zero(), q2_t = A::zero();   // thread 0: r.q and q.q
+        if (t < 32) {
+            const int i = t < 6 ? t : 0;
+            float qi = A::to_float(sum_partials_get<DT, NT, PCG_NC>(s_red2, 7 + i));
+#pragma unroll
+            for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
+            float si = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) si += Mp[6 * i + k] * __shfl_sync(0xffffffffu, qi, k);
+            const float ppi = s_pp[i], zpi = s_zp[i], rpi = s_rp[i];
+            AT tm[7];
+            tm[0] = A::madd(A::zero(), ppi, qi);
+            tm[1] = A::madd(A::zero(), qi, zpi);
+            tm[2] = A::madd(A::zero(), qi, si);
+            tm[3] = A::madd(A::zero(), rpi, zpi);
+            tm[4] = A::madd(A::zero(), rpi, rpi);
+            tm[5] = A::madd(A::zero(), rpi, qi);
+            tm[6] = A::madd(A::zero(), qi, qi);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                if (t >= 6) tm[k] = A::zero();
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) tm[k] = A::add(tm[k], A::shfl_down(tm[k], o));
+            }
+            qpi = qi;
+            spi = si;
+            if (t == 0) {
+                AT tot[7];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) tot[k] = A::add(sum_partials_get<DT, NT, PCG_NC>(s_red2, k), tm[k]);
+                rq_t = tot[5];
+                q2_t = tot[6];
+                // r.z and r.r of the current residual: the tests of the loop head
+                const float rho = A::to_float(tot[3]);
+                rr_last = A::to_float(tot[4]);
+                int ctl = 0;
+                float al = 0.f, be = 0.f;
+                if (!(rho > 0.f) || (a.tol > 0.f && sqrtf(rr_last) <= a.tol * res0)) {
+                    ctl = 1;
+                } else {
+                    const float pqt = A::to_float(tot[0]);
+                    if (!(pqt > 0.f)) {
+                        if (cta == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
+                        ctl = 2;
+                    } else {
+                        al = rho / pqt;
+                        // r'.z' = r.z - 2 alpha q.z + alpha^2 q.s (z' = z - alpha s, M^-1 symmetric)
+                        const float rho_next = rho - 2.f * al * A::to_float(tot[1]) + al * al * A::to_float(tot[2]);
+                        be = rho_next / rho;
+                    }
+                }
+                s_ab[0] = al;
+                s_ab[1] = be;
+                s_ctl = ctl;
+            }
+        }
+        __syncthreads();
         {
-            AT sums[PCG_NC];
-            sum_partials<DT, NT, PCG_NC>(part, nb, s_red2, sums);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                float qi = A::to_float(sums[7 + i]);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
-                qp[i] = qi;
-            }
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                float si = 0.f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) si += Mp[6 * i + k] * qp[k];
-                sp[i] = si;
-            }
-            AT pq = sums[0], qz = sums[1], qq2 = sums[2], rz = sums[3], r2 = sums[4];
-            rq_t = sums[5];
-            q2_t = sums[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                pq = A::madd(pq, s_pp[i], qp[i]);
-                qz = A::madd(qz, qp[i], s_zp[i]);
-                qq2 = A::madd(qq2, qp[i], sp[i]);
-                rz = A::madd(rz, s_rp[i], s_zp[i]);
-                r2 = A::madd(r2, s_rp[i], s_rp[i]);
-                rq_t = A::madd(rq_t, s_rp[i], qp[i]);
-                q2_t = A::madd(q2_t, qp[i], qp[i]);
-            }
-            // r.z and r.r of the current residual: the tests of the loop head
-            const float rho = A::to_float(rz);
-            rr_last = A::to_float(r2);
-            if (!(rho > 0.f)) break;
-            if (a.tol > 0.f && sqrtf(rr_last) <= a.tol * res0) break;
-            const float pqt = A::to_float(pq);
-            if (!(pqt > 0.f)) {
-                if (cta == 0 && t == 0) atomicCAS(a.status, ED_OK, ED_ERR_BREAKDOWN);
-                breakdown = true;
+            const int ctl = s_ctl;
+            if (ctl != 0) {   // the same decision in every CTA: it follows from the summed partials
+                breakdown = ctl == 2;
                 break;
             }
-            alpha = rho / pqt;
-            // r'.z' = r.z - 2 alpha q.z + alpha^2 q.s (z' = z - alpha s, M^-1 symmetric)
-            const float rho_next = rho - 2.f * alpha * A::to_float(qz) + alpha * alpha * A::to_float(qq2);
-            beta = rho_next / rho;
         }
-        // ---- updates: own rows, block columns, pose ----
+        const float alpha = s_ab[0], beta = s_ab[1];
+        // ---- updates: own rows, block columns, pose (warp 0; every reader of
+        // the pose parts has passed the barrier above) ----
         for (int i = t; i < rows * 12; i += NT) {
             ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
             rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
@@ -542,23 +684,15 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             ps[i] = __fmaf_rn(beta, ps[i], zn);
         }
         stage_finish(sg, alpha, beta);
-        __syncthreads();   // every thread has read s_pp, s_zp, s_rp above
         if (t < 6) {
-            float qt = 0.f, st = 0.f;   // qp[t], sp[t] without a dynamic register index
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-                if (i == t) {
-                    qt = qp[i];
-                    st = sp[i];
-                }
             s_dp[t] = __fmaf_rn(alpha, s_pp[t], s_dp[t]);
-            s_rp[t] = __fmaf_rn(-alpha, qt, s_rp[t]);
-            const float zn = __fmaf_rn(-alpha, st, s_zp[t]);
+            s_rp[t] = __fmaf_rn(-alpha, qpi, s_rp[t]);
+            const float zn = __fmaf_rn(-alpha, spi, s_zp[t]);
             s_zp[t] = zn;
             s_pp[t] = __fmaf_rn(beta, s_pp[t], zn);
         }
         // ||r'||^2 = r.r - 2 alpha r.q + alpha^2 q.q (reported after the last iteration)
-        rr_last = rr_last - 2.f * alpha * A::to_float(rq_t) + alpha * alpha * A::to_float(q2_t);
+        if (t == 0) rr_last = rr_last - 2.f * alpha * A::to_float(rq_t) + alpha * alpha * A::to_float(q2_t);
     }
     __syncthreads();
     // solution of the CTA's rows (and of the pose: CTA 0), and the update
