@@ -433,28 +433,58 @@ __device__ __forceinline__ int sym4(int a, int b)
     return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
 }
 
-// sum of the chunk partials of one component (two-sum compensated when mixed);
-// partials are chunk-major, ED_PART_STRIDE floats per chunk
-__device__ __forceinline__ float sum_parts(const float *part, int comp, int max_chunks, int c0, int n, int mixed)
+// sum of the chunk partials of one component (partials are chunk-major,
+// ED_PART_STRIDE floats per chunk): p = the component in the first chunk
+// (NULL: none), n chunks, summed in chunk order, two-sum compensated when
+// mixed.  A lane keeps several of them and loads four chunks of each before
+// adding, so the loads of all its components are in flight together.
+struct PartSum {
+    const float *p;
+    int n;
+    float s, err;
+};
+
+__device__ __forceinline__ PartSum part_sum(const float *part, int comp, int c0, int n)
 {
-    (void)max_chunks;
-    const float *p = part + (long)c0 * ED_PART_STRIDE + comp;
-    float s = 0.f;
-    if (!mixed) {
-#pragma unroll 4
-        for (int k = 0; k < n; ++k) s += p[(long)k * ED_PART_STRIDE];
-        return s;
-    }
-    float err = 0.f;
-    for (int k = 0; k < n; ++k) {
-        const float a = p[(long)k * ED_PART_STRIDE];
-        const float t = s + a;
-        const float bp = t - s;
-        err += (s - (t - bp)) + (a - bp);
-        s = t;
-    }
-    return s + err;
+    PartSum r;
+    r.p = comp >= 0 ? part + (long)c0 * ED_PART_STRIDE + comp : nullptr;
+    r.n = comp >= 0 ? n : 0;
+    r.s = 0.f;
+    r.err = 0.f;
+    return r;
 }
+
+__device__ __forceinline__ void part_load4(const PartSum &c, int k0, float4 &v)
+{
+    const float *p = c.p + (long)k0 * ED_PART_STRIDE;
+    v.x = k0 < c.n ? p[0] : 0.f;
+    v.y = k0 + 1 < c.n ? p[ED_PART_STRIDE] : 0.f;
+    v.z = k0 + 2 < c.n ? p[2 * ED_PART_STRIDE] : 0.f;
+    v.w = k0 + 3 < c.n ? p[3 * ED_PART_STRIDE] : 0.f;
+}
+
+__device__ __forceinline__ void part_add1(PartSum &c, float x, bool in, int mixed)
+{
+    if (!in) return;
+    if (!mixed) {
+        c.s += x;
+        return;
+    }
+    const float t = c.s + x;
+    const float bp = t - c.s;
+    c.err += (c.s - (t - bp)) + (x - bp);
+    c.s = t;
+}
+
+__device__ __forceinline__ void part_add4(PartSum &c, int k0, const float4 v, int mixed)
+{
+    part_add1(c, v.x, k0 < c.n, mixed);
+    part_add1(c, v.y, k0 + 1 < c.n, mixed);
+    part_add1(c, v.z, k0 + 2 < c.n, mixed);
+    part_add1(c, v.w, k0 + 3 < c.n, mixed);
+}
+
+__device__ __forceinline__ float part_value(const PartSum &c, int mixed) { return mixed ? c.s + c.err : c.s; }
 
 // derivative of the Rot(A) residual q (column pair ca, cb) with respect to
 // the parameter 4 r + c of [A | t]
@@ -492,70 +522,51 @@ __device__ __forceinline__ float rot_jtj(const float *X, int r, int c, int rp, i
     return v;
 }
 
-// block-Jacobi inverse of one 12x12 block H (shared memory, one warp):
-// Cholesky of H + jitter tr/12 I in place (lower triangle, 78 entries, at most
-// three per lane), then M^-1 = L^-T L^-1 into out (row-major); false, with out
-// untouched, on a non-positive pivot.  L, rinv: per-warp shared scratch;
-// s_tab: the entry table of k_finalize (row in bits 16..23, column in 24..31).
-__device__ __forceinline__ bool block_inverse12(float *H, float *L, float *rinv, const int *s_tab, float jitter,
-                                                float *__restrict__ out)
+// block-Jacobi inverse of one 12x12 block H (shared memory, row-major; one
+// warp): Gauss-Jordan elimination without pivoting on [H + jitter tr/12 I | I].
+// H is symmetric positive definite, so every pivot is positive (the pivots
+// are the squares of the Cholesky pivots).  Lane r < 24 keeps row r % 12 of
+// the left (r < 12) or the right half in registers; the pivot row and the
+// elimination factors travel by shuffles, so the 12 steps have no shared
+// memory traffic.  The right half, symmetrised through `scratch` (144
+// floats), goes to out (row-major); false, with out untouched, on a
+// non-positive pivot.
+__device__ __forceinline__ bool block_inverse12(const float *H, float *scratch, float jitter, float *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
+    const int r = lane < 24 ? lane % 12 : 0, half = lane >= 12 && lane < 24 ? 1 : 0;
     float tr = 0.f;
+#pragma unroll
     for (int k = 0; k < 12; ++k) tr += H[k * 13];
-    __syncwarp();
-    if (lane < 12) H[lane * 13] += jitter * tr / 12.0f;
-    int tri_r[3], tri_c[3];
+    const float jd = jitter * tr / 12.0f;
+    float v[12];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        int t = lane + 32 * q, r = 0;
-        while (t > r) {   // t -> (r, c) with t = r (r + 1) / 2 + c, c <= r
-            t -= r + 1;
-            ++r;
-        }
-        tri_r[q] = lane + 32 * q < 78 ? r : -1;
-        tri_c[q] = t;
-    }
-    __syncwarp();
+    for (int c = 0; c < 12; ++c) v[c] = half ? (c == r ? 1.0f : 0.0f) : H[r * 12 + c] + (c == r ? jd : 0.0f);
     bool ok = true;
-    for (int k = 0; k < 12; ++k) {
-        const float piv = H[k * 13];
-        if (!(piv > 0.f)) ok = false;
-        const float sq = ok ? sqrtf(piv) : 1.0f;
-        const float inv = 1.0f / sq;
-        __syncwarp();
-        if (lane == 0) {
-            H[k * 13] = sq;
-            rinv[k] = inv;
-        }
-        if (lane > k && lane < 12) H[lane * 12 + k] *= inv;
-        __syncwarp();
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int r = tri_r[q], c = tri_c[q];
-            if (r > k && c > k) H[r * 12 + c] -= H[r * 12 + k] * H[c * 12 + k];
+    for (int k = 0; k < 12; ++k) {
+        const float piv = __shfl_sync(0xffffffffu, v[k], k);   // row k, column k (left half)
+        const float fr = __shfl_sync(0xffffffffu, v[k], r);    // row r, column k (left half)
+        ok = ok && piv > 0.0f;
+        const float ip = 1.0f / piv, f = -fr * ip;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const float pc = __shfl_sync(0xffffffffu, v[c], k + 12 * half);   // pivot row, this lane's half
+            v[c] = r == k ? pc * ip : fmaf(f, pc, v[c]);
         }
-        __syncwarp();
     }
     if (!ok) return false;
-    // L^-1 by forward substitution, one column per lane (lanes 0..11)
-    if (lane < 12) {
+    __syncwarp();
+    if (half) {
 #pragma unroll
-        for (int r = 0; r < 12; ++r) {
-            float v = (r == lane) ? 1.0f : 0.0f;
-            for (int k = lane; k < r; ++k) v -= H[r * 12 + k] * L[k * 12 + lane];
-            L[r * 12 + lane] = r < lane ? 0.f : v * rinv[r];
-        }
+        for (int c = 0; c < 12; ++c) scratch[r * 12 + c] = v[c];
     }
     __syncwarp();
-    // M^-1 = L^-T L^-1: entry (p, q) sums rows k >= max(p, q) of the lower-triangular L^-1
     for (int e = lane; e < 144; e += 32) {
-        const int T = s_tab[e];
-        const int p = (T >> 16) & 255, q = T >> 24;
-        float s2 = 0.f;
-        for (int k = p > q ? p : q; k < 12; ++k) s2 += L[k * 12 + p] * L[k * 12 + q];
-        out[e] = s2;
+        const int p = e / 12, q = e - 12 * p;
+        out[e] = 0.5f * (scratch[e] + scratch[q * 12 + p]);
     }
+    __syncwarp();
     return true;
 }
 
@@ -571,108 +582,180 @@ __device__ __forceinline__ void fill_block_table(int *s_tab)
     }
 }
 
+// component i of (v0, v1, v2, v3) without a local array
+__device__ __forceinline__ float pick4(float v0, float v1, float v2, float v3, int i)
+{
+    return i == 0 ? v0 : (i == 1 ? v1 : (i == 2 ? v2 : v3));
+}
+
+// the partial sums of components (c_a, c_b) over n chunks from c0 (c_b < 0: one)
+__device__ __forceinline__ void part_sums2(const FinArgs &a, int ca, int cb, int c0, int n, float &va, float &vb)
+{
+    PartSum pa = part_sum(a.part, ca, c0, n), pb = part_sum(a.part, cb, c0, n);
+    for (int k0 = 0; k0 < pa.n; k0 += 4) {
+        float4 x, y;
+        part_load4(pa, k0, x);
+        part_load4(pb, k0, y);
+        part_add4(pa, k0, x, a.mixed);
+        part_add4(pb, k0, y, a.mixed);
+    }
+    va = part_value(pa, a.mixed);
+    vb = part_value(pb, a.mixed);
+}
+
 // one warp per upper block u (INV = false: the block inverses are taken
-// later, in the Levenberg-Marquardt stage)
+// later, in the Levenberg-Marquardt stage).  The 144 entries of a block go to
+// lanes 0..23: lane L takes column C = L % 12 of the rows R = L / 12 + 2 k,
+// k < 6, so a lane's column quantities are formed once.
 template <bool INV>
 __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M, float *H, float *X, float *S,
-                                               float *Lw, float *rinv_w, const int *s_tab)
+                                               float *Lw, int *Nk, float4 *Ng, float *Nx, const int *s_tab)
 {
     const int lane = threadIdx.x & 31;
     const int b = a.up_list[u];
     const int j = a.brow[b], l = a.col[b];
+    const int cnt = a.ent_cnt[b], c0 = a.chunk_start[b];
     const bool diag = j == l;
-    const int nch = (a.ent_cnt[b] + ED_CHUNK - 1) / ED_CHUNK;
-    const int c0 = a.chunk_start[b];
-    for (int k = lane; k < 60; k += 32) M[k] = sum_parts(a.part, k, a.max_chunks, c0, nch, a.mixed);
-    if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
-    __syncwarp();
-    const float4 gj = a.g[j], gl = a.g[l];
-    const float dl[3] = {gj.x - gl.x, gj.y - gl.y, gj.z - gl.z};   // d^_l = d^_j + [g_j - g_l; 0]
+    const int nch = (cnt + ED_CHUNK - 1) / ED_CHUNK;
+    const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
+    const bool ent_lane = lane < 24;
     const float wr = a.w_reg;
     if (!diag) {
+        const int tb = a.tpos[b];
         bool e_jl = false, e_lj = false;
         for (int s = 0; s < a.kg; ++s) {
             e_jl |= a.nbr[j * a.kg + s] == l;
             e_lj |= a.nbr[l * a.kg + s] == j;
         }
-        const float hjl[4] = {gl.x - gj.x, gl.y - gj.y, gl.z - gj.z, 1.0f};
-        const int tb = a.tpos[b];
+        const float4 gj = a.g[j], gl = a.g[l];
+        {
+            float v0, v1;
+            part_sums2(a, lane, lane + 32 < 60 ? lane + 32 : -1, c0, nch, v0, v1);
+            M[lane] = v0;
+            if (lane + 32 < 60) M[lane + 32] = v1;
+        }
+        __syncwarp();
         if (tb < 0) {
             if (lane == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
             return;
         }
-        for (int e = lane; e < 144; e += 32) {
-            const int T = s_tab[e];
-            const int R = (T >> 16) & 255, Cc = T >> 24;
-            const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+        if (!ent_lane) return;
+        // d^_l = d^_j + [g_j - g_l; 0]; h_jl = [g_l - g_j; 1]
+        const float dlc = pick4(gj.x - gl.x, gj.y - gl.y, gj.z - gl.z, 0.f, cp);
+        const float hx = gl.x - gj.x, hy = gl.y - gj.y, hz = gl.z - gj.z;
+        // E_reg, edge l -> j (d e / d t_j = -I): column quantity of the rows c = 3
+        const float reg_lj = e_lj ? -wr * (cp < 3 ? -pick4(hx, hy, hz, 1.f, cp) : 1.0f) : 0.f;
+        float *dst = a.bsr + (long)b * 144 + Cc;
+        float *dstT = a.bsr + (long)tb * 144 + Cc * 12;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int R = h0 + 2 * k, r = R >> 2, c = R & 3;
+            const int T = s_tab[R * 12 + Cc];
             float h = M[T & 255];
-            if (cp < 3) h += dl[cp] * M[(T >> 8) & 255];
-            if (r == rp) {   // E_reg, edges j -> l (d e / d t_l = -I) and l -> j (d e / d t_j = -I)
-                if (e_jl && cp == 3) h -= wr * hjl[c];
-                if (e_lj && c == 3) h -= wr * (cp < 3 ? -hjl[cp] : 1.0f);
+            if (cp < 3) h += dlc * M[(T >> 8) & 255];
+            if (r == rp) {   // E_reg, edge j -> l (d e / d t_l = -I) on the t column
+                if (e_jl && cp == 3) h -= wr * pick4(hx, hy, hz, 1.f, c);
+                if (c == 3) h += reg_lj;
             }
-            a.bsr[(long)b * 144 + e] = h;
-            a.bsr[(long)tb * 144 + Cc * 12 + R] = h;
+            dst[R * 12] = h;
+            dstT[R] = h;
         }
         return;
     }
     // ---- diagonal block ----
-    // data gradient and pose-node block from the role-1 chunks
-    const int c1 = a.n_chunks0 + a.chunk_start1[b];
-    float *Gx = M + 60;
-    for (int k = lane; k < 84; k += 32) {
-        const float v = sum_parts(a.part, k, a.max_chunks, c1, (a.ent_cnt[b] + ED_CHUNK1 - 1) / ED_CHUNK1, a.mixed);
-        if (k < 12) Gx[k] = v;
-        else a.pnode[(long)j * 72 + (k - 12)] = v;
+    const int cs1 = a.chunk_start1[b];
+    const int rp0 = a.row_ptr[j], rp1 = a.row_ptr[j + 1];
+    if (lane < a.kg) {   // out-edges j -> k: index, position and parameters of k, loaded once
+        const int k = a.nbr[j * a.kg + lane];
+        Nk[lane] = k;
+        if (k >= 0) {
+            Ng[lane] = a.g[k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) reinterpret_cast<float4 *>(Nx + 12 * lane)[q] = a.x4[3 * k + q];
+        }
     }
+    if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
+    const float4 gj = a.g[j];
+    // the 60 moments (role-0 chunks), then J^T r and the pose-node block (84
+    // components of the role-1 chunks)
+    float *Gx = M + 60;
+    {
+        float v0, v1;
+        part_sums2(a, lane, lane + 32 < 60 ? lane + 32 : -1, c0, nch, v0, v1);
+        M[lane] = v0;
+        if (lane + 32 < 60) M[lane + 32] = v1;
+        const int c1 = a.n_chunks0 + cs1, nch1 = (cnt + ED_CHUNK1 - 1) / ED_CHUNK1;
+        float w0, w1, w2, w3;
+        part_sums2(a, lane, lane + 32, c1, nch1, w0, w1);
+        part_sums2(a, lane + 64 < 84 ? lane + 64 : -1, -1, c1, nch1, w2, w3);
+        auto put = [&](int k, float v) {
+            if (k < 12) Gx[k] = v;
+            else a.pnode[(long)j * 72 + (k - 12)] = v;
+        };
+        put(lane, w0);
+        put(lane + 32, w1);
+        if (lane + 64 < 84) put(lane + 64, w2);
+    }
+    __syncwarp();
     // S = sum over out-edges j -> k of h h^T, h = [g_k - g_j; 1]
     if (lane < 16) {
-        const int c = lane >> 2, cp = lane & 3;
+        const int c = lane >> 2, cq = lane & 3;
         float v = 0.f;
         for (int s = 0; s < a.kg; ++s) {
-            const int k = a.nbr[j * a.kg + s];
-            if (k < 0) continue;
-            const float4 gk = a.g[k];
-            const float h[4] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z, 1.0f};
-            v += h[c] * h[cp];
+            if (Nk[s] < 0) continue;
+            const float4 gk = Ng[s];
+            const float hx = gk.x - gj.x, hy = gk.y - gj.y, hz = gk.z - gj.z;
+            v += pick4(hx, hy, hz, 1.f, c) * pick4(hx, hy, hz, 1.f, cq);
         }
         S[lane] = v;
     }
     // in-edges k -> j (they lie in row j): count and summed residuals
-    float nin = 0.f, ein[3] = {0.f, 0.f, 0.f};
-    for (int t = a.row_ptr[j] + lane; t < a.row_ptr[j + 1]; t += 32) {
+    float nin = 0.f, ein0 = 0.f, ein1 = 0.f, ein2 = 0.f;
+    for (int t = rp0 + lane; t < rp1; t += 32) {
         const int k = a.col[t];
-        if (k == j) continue;
-        bool in = false;
-        for (int s = 0; s < a.kg; ++s) in |= a.nbr[k * a.kg + s] == j;
-        if (!in) continue;
+        // the neighbours of k, its position and parameters: every load issued together
+        int nb[ED_MAX_KG];
+#pragma unroll
+        for (int s = 0; s < ED_MAX_KG; ++s) nb[s] = s < a.kg ? a.nbr[k * a.kg + s] : -1;
         const float4 gk = a.g[k];
+        const float4 xk0 = a.x4[3 * k], xk1 = a.x4[3 * k + 1], xk2 = a.x4[3 * k + 2];
+        bool in = false;
+#pragma unroll
+        for (int s = 0; s < ED_MAX_KG; ++s) in |= nb[s] == j;
+        if (k == j || !in) continue;
         const float hh[3] = {gj.x - gk.x, gj.y - gk.y, gj.z - gk.z};
-        const float *xk = &a.x4[3 * k].x;
+        const float x0[4] = {xk0.x, xk0.y, xk0.z, xk0.w}, x1[4] = {xk1.x, xk1.y, xk1.z, xk1.w};
+        const float x2[4] = {xk2.x, xk2.y, xk2.z, xk2.w};
         nin += 1.f;
-        for (int r = 0; r < 3; ++r) ein[r] += ed_reg_residual(xk + 4 * r, r, hh, X[4 * r + 3]);
+        ein0 += ed_reg_residual(x0, 0, hh, X[3]);
+        ein1 += ed_reg_residual(x1, 1, hh, X[7]);
+        ein2 += ed_reg_residual(x2, 2, hh, X[11]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         nin += __shfl_xor_sync(0xffffffffu, nin, o);
-        ein[0] += __shfl_xor_sync(0xffffffffu, ein[0], o);
-        ein[1] += __shfl_xor_sync(0xffffffffu, ein[1], o);
-        ein[2] += __shfl_xor_sync(0xffffffffu, ein[2], o);
+        ein0 += __shfl_xor_sync(0xffffffffu, ein0, o);
+        ein1 += __shfl_xor_sync(0xffffffffu, ein1, o);
+        ein2 += __shfl_xor_sync(0xffffffffu, ein2, o);
     }
     __syncwarp();
     // the 144 entries: data moments + E_rot + E_reg (out-edges S, in-edges on t)
-    for (int e = lane; e < 144; e += 32) {
-        const int T = s_tab[e];
-        const int R = (T >> 16) & 255, Cc = T >> 24;
-        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
-        float h = M[T & 255];
-        if (c < 3 && cp < 3) h += a.w_rot * rot_jtj(X, r, c, rp, cp);
-        if (r == rp) {
-            h += wr * S[4 * c + cp];
-            if (c == 3 && cp == 3) h += wr * nin;
+    if (ent_lane) {
+        float *dst = a.bsr + (long)b * 144 + Cc;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int R = h0 + 2 * k, r = R >> 2, c = R & 3;
+            const int T = s_tab[R * 12 + Cc];
+            float h = M[T & 255];
+            if (c < 3 && cp < 3) h += a.w_rot * rot_jtj(X, r, c, rp, cp);
+            if (r == rp) {
+                h += wr * S[4 * c + cp];
+                if (c == 3 && cp == 3) h += wr * nin;
+            }
+            if (R == Cc) h *= 1.0f + a.lambda;   // LM damping
+            H[R * 12 + Cc] = h;
+            dst[R * 12] = h;
         }
-        if (R == Cc) h *= 1.0f + a.lambda;   // LM damping
-        H[e] = h;
     }
     // gradient: data + E_rot + E_reg (out-edges, in-edges)
     if (lane < 12) {
@@ -685,14 +768,13 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
             g += a.w_rot * v;
         }
         for (int s = 0; s < a.kg; ++s) {
-            const int k = a.nbr[j * a.kg + s];
-            if (k < 0) continue;
-            const float4 gk = a.g[k];
-            const float hh[4] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z, 1.0f};
-            const float er = ed_reg_residual(X + 4 * r, r, hh, (&a.x4[3 * k].x)[4 * r + 3]);
-            g += wr * er * hh[c];
+            if (Nk[s] < 0) continue;
+            const float4 gk = Ng[s];
+            const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
+            const float er = ed_reg_residual(X + 4 * r, r, hh, Nx[12 * s + 4 * r + 3]);
+            g += wr * er * pick4(hh[0], hh[1], hh[2], 1.f, c);
         }
-        if (c == 3) g -= wr * ein[r];
+        if (c == 3) g -= wr * (r == 0 ? ein0 : (r == 1 ? ein1 : ein2));
         a.grad[12 * j + lane] = g;
     }
     // energies of node j: Rot(A_j), and its out-edges
@@ -703,23 +785,19 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
             erot += a.w_rot * rho * rho;
         }
         for (int s = 0; s < a.kg; ++s) {
-            const int k = a.nbr[j * a.kg + s];
-            if (k < 0) continue;
-            const float4 gk = a.g[k];
+            if (Nk[s] < 0) continue;
+            const float4 gk = Ng[s];
             const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
-            const float *xk = &a.x4[3 * k].x;
             for (int r = 0; r < 3; ++r) {
-                const float e = ed_reg_residual(X + 4 * r, r, hh, xk[4 * r + 3]);
+                const float e = ed_reg_residual(X + 4 * r, r, hh, Nx[12 * s + 4 * r + 3]);
                 ereg += wr * e * e;
             }
         }
         a.node_energy[j] = make_float2(erot, ereg);
     }
     __syncwarp();
-    for (int e = lane; e < 144; e += 32) a.bsr[(long)b * 144 + e] = H[e];
-    __syncwarp();
     if (!INV) return;
-    if (!block_inverse12(H, Lw, rinv_w, s_tab, a.jitter, a.minv + (long)j * 144) && lane == 0)
+    if (!block_inverse12(H, Lw, a.jitter, a.minv + (long)j * 144) && lane == 0)
         atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
 }
 
@@ -804,7 +882,9 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __shared__ float sX[FIN_WARPS][12];
     __shared__ float sS[FIN_WARPS][16];
     __shared__ float sL[FIN_WARPS][144];
-    __shared__ float sRinv[FIN_WARPS][12];
+    __shared__ int sNk[FIN_WARPS][ED_MAX_KG];
+    __shared__ float4 sNg[FIN_WARPS][ED_MAX_KG];
+    __shared__ __align__(16) float sNx[FIN_WARPS][12 * ED_MAX_KG];
     // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
     // shift), R, C (the same for every block; computed once per CTA)
     __shared__ int s_tab[144];
@@ -812,7 +892,8 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     __syncthreads();
     const int wid = threadIdx.x >> 5;
     const int u = blockIdx.x * FIN_WARPS + wid;
-    if (u < a.n_upper) finalize_block<INV>(a, u, sM[wid], sH[wid], sX[wid], sS[wid], sL[wid], sRinv[wid], s_tab);
+    if (u < a.n_upper)
+        finalize_block<INV>(a, u, sM[wid], sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid], s_tab);
     finalize_totals(a);
 }
 
@@ -1075,9 +1156,6 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_lm_precond(const int *__rest
     __shared__ float sH[FIN_WARPS][144];
     __shared__ float sL[FIN_WARPS][144];
     __shared__ float sRinv[FIN_WARPS][12];
-    __shared__ int s_tab[144];
-    fill_block_table(s_tab);
-    __syncthreads();
     if (misc[MI_STATUS] != ED_OK) return;
     const float f = 1.0f + (float)dmisc[DM_LAM];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1094,7 +1172,7 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_lm_precond(const int *__rest
             H[e] = h;
         }
         __syncwarp();
-        if (!block_inverse12(H, sL[wid], sRinv[wid], s_tab, jitter, minv + (long)j * 144) && lane == 0)
+        if (!block_inverse12(H, sL[wid], jitter, minv + (long)j * 144) && lane == 0)
             atomicCAS(misc + MI_STATUS, 0, ED_ERR_BREAKDOWN);
     } else if (j == m) {
         for (int e = lane; e < 36; e += 32) {
