@@ -3,6 +3,7 @@
 // Everything here is private to the library; the public ABI is include/ed.h.
 #pragma once
 
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -368,6 +369,34 @@ struct ed_warped {
     float3 v;     // R s + T
     float3 n;     // normalize(R sum_j w_j A_j n)
 };
+
+// ---------------------------------------------------------------------------
+// programmatic dependent launch: a kernel launched by ed_launch_pdl may be
+// dispatched while the kernel before it on the stream is still finishing; it
+// calls ed_pdl_wait() before it reads or writes anything that kernel touches
+// (launched without the attribute, the wait returns at once).  Only for a
+// kernel whose stream predecessor is a kernel: not after a wait on another
+// stream's event.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void ed_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t ed_launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                        Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // grid barrier of a cooperative (co-resident) launch, with a bounded wait

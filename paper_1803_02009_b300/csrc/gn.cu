@@ -25,6 +25,7 @@ struct PointArgs {
     const float4 *kp_tgt;
     float sw_corr;
     int *pix;          // association (written in STEP / ENERGY, read in GRAD)
+    int *status_reset; // the step's device status word, cleared by the first thread (STEP), or NULL
     float4 *rec0, *rec1;
     float2 *part;      // [ED_K1_PART][pstride] float-float partials, component-major
     int pstride;
@@ -37,6 +38,10 @@ struct PointArgs {
 // block and the pose gradient (fixed grid-stride order: deterministic).
 __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
 {
+    ed_pdl_wait();
+    // a Gauss-Newton step starts with a clear status word: nothing before this
+    // kernel's end reads it, and no thread of this kernel writes it otherwise
+    if (a.status_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.status_reset = ED_OK;
     __shared__ ed_pose_f P;
     __shared__ float red[ED_K1_THREADS / 32][31];
     if (threadIdx.x == 0) ed_pose_eval(a.pose, P);
@@ -185,6 +190,7 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.kp_tgt = ctx->kp_tgt;
     a.sw_corr = sqrtf(ctx->w_corr);
     a.pix = ctx->pix;
+    a.status_reset = mode == PASS_STEP ? ctx->misc + MI_STATUS : nullptr;
     a.rec0 = mode == PASS_GRAD ? ctx->gpts : ctx->rec0;
     a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : ctx->rec1;
     a.part = ctx->k1_part;
@@ -193,7 +199,7 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.dbg_wnrm = ctx->dbg_wnrm;
     a.dbg_pix = (mode == PASS_STEP && ctx->dbg_wpos && ctx->dbg_wnrm) ? ctx->dbg_pix : nullptr;
     if (mode == PASS_STEP) ed_tm_begin(ctx, ED_KERNEL_POINTS, st);
-    k_points<<<k1_grid(ctx), ED_K1_THREADS, 0, st>>>(a); ed_note_launch();
+    ED_CUDA_TRY(ed_launch_pdl(k_points, dim3(k1_grid(ctx)), dim3(ED_K1_THREADS), 0, st, a)); ed_note_launch();
     if (mode == PASS_STEP) ed_tm_end(ctx, ED_KERNEL_POINTS, st);
     ED_LAUNCH_CHECK();
     return ED_OK;
@@ -268,6 +274,7 @@ __global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chun
                                                    const float4 *__restrict__ geo, const uint32_t *__restrict__ ent,
                                                    const float4 *__restrict__ rec0, float *__restrict__ part)
 {
+    ed_pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int c = wg >> 1, h = wg & 1;
@@ -386,6 +393,7 @@ __global__ void __launch_bounds__(128, 6) k_assemble1(const int4 *__restrict__ c
                                                    const float4 *__restrict__ rec1, const double *__restrict__ pose,
                                                    float *__restrict__ part)
 {
+    ed_pdl_wait();
     __shared__ ed_pose_f P;
     if (threadIdx.x == 0) ed_pose_eval(pose, P);
     __syncthreads();
@@ -872,6 +880,7 @@ __device__ __forceinline__ void finalize_totals(const FinArgs &a)
         }
     }
     if (threadIdx.x < 33) a.tickets[32 * threadIdx.x] = 0;   // ready for the next launch
+    if (threadIdx.x < 2) a.misc[MI_BAR + threadIdx.x] = 0;   // the arrival count of the step's PCG
 }
 
 template <bool INV>
@@ -1255,7 +1264,7 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
         (prm->lm_accept != 0 && prm->lm_accept != 1))
         return ED_ERR_ARG;
     const int m = ctx->m;
-    ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_STATUS, 0, sizeof(int), st));
+    // (the point pass clears the device status word)
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_STEP, st)) != ED_OK) return s;
     const bool lm = prm->lm_accept != 0;
     // the pose pass (pose block, its inverse, pose gradient, prior energies,
@@ -1279,12 +1288,15 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
         const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
         if (n0 > 0) {
-            k_assemble0<<<ed_div_up(2 * n0, 4), 128, 0, st>>>(ctx->chunks, n0, ctx->max_chunks, ctx->ent_geo, ctx->ent_val,
-                                                           ctx->rec0, ctx->partials); ed_note_launch();
+            ED_CUDA_TRY(ed_launch_pdl(k_assemble0, dim3(ed_div_up(2 * n0, 4)), dim3(128), 0, st, (const int4 *)ctx->chunks, n0,
+                                      ctx->max_chunks, (const float4 *)ctx->ent_geo, (const uint32_t *)ctx->ent_val,
+                                      (const float4 *)ctx->rec0, ctx->partials)); ed_note_launch();
         }
         if (n1 > 0) {
-            k_assemble1<<<ed_div_up(2 * n1, 4), 128, 0, st>>>(ctx->chunks, base1, n1, ctx->max_chunks, ctx->ent_geo,
-                                                           ctx->ent_val, ctx->rec0, ctx->rec1, pose, ctx->partials); ed_note_launch();
+            ED_CUDA_TRY(ed_launch_pdl(k_assemble1, dim3(ed_div_up(2 * n1, 4)), dim3(128), 0, st, (const int4 *)ctx->chunks,
+                                      base1, n1, ctx->max_chunks, (const float4 *)ctx->ent_geo,
+                                      (const uint32_t *)ctx->ent_val, (const float4 *)ctx->rec0,
+                                      (const float4 *)ctx->rec1, (const double *)pose, ctx->partials)); ed_note_launch();
         }
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();

@@ -728,6 +728,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
 template <typename DT, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_pcg(PcgArgs a)
 {
+    ed_pdl_wait();
     pcg_body<DT, NT>(a, blockIdx.x, gridDim.x);
 }
 
@@ -866,18 +867,22 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     return ED_OK;
 }
 
-static cudaError_t launch_coop(const void *fn, int grid, int nt, void **args, size_t smem, cudaStream_t st)
+// cooperative launch; pdl: also programmatic dependent launch (the kernel
+// waits for its stream predecessor before anything else)
+static cudaError_t launch_coop(const void *fn, int grid, int nt, void **args, size_t smem, cudaStream_t st, bool pdl)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
@@ -889,12 +894,12 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, d
     PcgArgs a;
     ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, x, xm, pose, stats, a);
     if (s != ED_OK) return s;
-    ED_CUDA_TRY(cudaMemsetAsync(ctx->misc + MI_BAR, 0, 2 * sizeof(int), st));
+    // (the arrival count was cleared by the last CTA of the finalisation)
     void *args[] = {&a};
     ed_tm_begin(ctx, ED_KERNEL_PCG, st);
     ed_note_launch();
     const void *fn = mixed ? (const void *)k_pcg<double, 512> : (const void *)k_pcg<float, 512>;
-    cudaError_t e = launch_coop(fn, ctx->pcg.grid, 512, args, ctx->pcg.smem, st);
+    cudaError_t e = launch_coop(fn, ctx->pcg.grid, 512, args, ctx->pcg.smem, st, true);
     ed_tm_end(ctx, ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: PCG launch failed: %s\n", cudaGetErrorString(e));
@@ -984,7 +989,7 @@ ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t 
     if (bp->nt == 512) fn = mixed ? (const void *)k_pcg_batch<double, 512> : (const void *)k_pcg_batch<float, 512>;
     else fn = mixed ? (const void *)k_pcg_batch<double, 256> : (const void *)k_pcg_batch<float, 256>;
     ed_note_launch();
-    cudaError_t e = launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st);
+    cudaError_t e = launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st, false);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: batched PCG launch failed: %s\n", cudaGetErrorString(e));
         return ED_ERR_CUDA;
