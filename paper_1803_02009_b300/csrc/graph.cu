@@ -544,10 +544,17 @@ __global__ void k_row_count(const uint32_t *__restrict__ bm, int m, int words, i
     cnt[j] = c;
 }
 
+// (queued before the host has the block count: a count above the capacity
+// writes nothing and sets the status)
 __global__ void k_row_fill(const uint32_t *__restrict__ bm, int m, int words, const int *__restrict__ row_ptr,
-                           int *__restrict__ col, int *__restrict__ brow, int *__restrict__ diag_pos)
+                           int *__restrict__ col, int *__restrict__ brow, int *__restrict__ diag_pos, int max_nnzb,
+                           int *__restrict__ status)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row_ptr[m] > max_nnzb) {
+        if (j == 0) atomicCAS(status, ED_OK, ED_ERR_CAPACITY);
+        return;
+    }
     if (j >= m) return;
     int p = row_ptr[j];
     for (int w = 0; w < words; ++w) {
@@ -603,12 +610,15 @@ __global__ void k_compact_upper(int nnzb, int m, const int *__restrict__ flag, c
 #define EG_T 128
 // the 10 entries (s <= t) of every point, written through shared memory so
 // that a CTA's 10 x 128 keys and values go out as contiguous stores
+// (queued before the host has the block count: nothing when it is above the
+// capacity, where k_row_fill has set the status)
 __global__ void __launch_bounds__(EG_T) k_entries_gen(const ushort4 *__restrict__ idx, int n,
                                                       const int *__restrict__ row_ptr, const int *__restrict__ col,
                                                       uint32_t *__restrict__ key, uint32_t *__restrict__ val,
-                                                      int *__restrict__ status)
+                                                      int *__restrict__ status, int m, int max_nnzb)
 {
     __shared__ uint32_t sk[10 * EG_T], sv[10 * EG_T];
+    if (row_ptr[m] > max_nnzb) return;   // the same for every thread
     const int i0 = blockIdx.x * EG_T, i = i0 + threadIdx.x;
     if (i < n) {
         const ushort4 q = idx[i];
@@ -666,23 +676,29 @@ __global__ void k_chunk_count(int nnzb, const int *__restrict__ ent_start, int *
     ccnt1[b] = col[b] == brow[b] ? (cnt[b] + ED_CHUNK1 - 1) / ED_CHUNK1 : 0;
 }
 
+// (queued before the host has the chunk totals: chunks beyond max_chunks are
+// not written and set the status; the padding chunks between the roles are
+// written empty here)
 __global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *__restrict__ ent_start,
                              const int *__restrict__ brow, const int *__restrict__ col,
                              const int *__restrict__ cstart0, const int *__restrict__ cstart1,
-                             int4 *__restrict__ chunks)
+                             int4 *__restrict__ chunks, int max_chunks, int *__restrict__ status)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n0 = cstart0[nnzb];
+    const int base1 = (n0 + 31) & ~31;   // role-1 chunks start warp-aligned
+    if (b < 32 && n0 + b < base1 && n0 + b < max_chunks) chunks[n0 + b] = make_int4(0, 0, 0, 0);
     if (b >= nnzb || col[b] < brow[b]) return;
     const int n = cnt[b];
-    const int base1 = (cstart0[nnzb] + 31) & ~31;   // role-1 chunks start warp-aligned
     for (int r = 0; r < (brow[b] == col[b] ? 2 : 1); ++r) {
         const int size = r == 0 ? ED_CHUNK : ED_CHUNK1;
         const int per = (n + size - 1) / size;
         int q = r == 0 ? cstart0[b] : base1 + cstart1[b];
-        for (int k = 0; k < per; ++k) {
+        for (int k = 0; k < per; ++k, ++q) {
             const int beg = ent_start[b] + k * size;
             const int c = min(size, n - k * size);
-            chunks[q++] = make_int4(b, beg, c, r);
+            if (q < max_chunks) chunks[q] = make_int4(b, beg, c, r);
+            else atomicCAS(status, ED_OK, ED_ERR_CAPACITY);
         }
     }
 }
@@ -731,13 +747,6 @@ ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_
         k_bbox<<<min(ed_div_up(n, 256), 4 * ctx->num_sms), 256, 0, st>>>(pos, n, ctx->misc); ed_note_launch();
     }
     ED_LAUNCH_CHECK();
-    return ED_OK;
-}
-
-static ed_status read_misc(ed_context *ctx, int *host, cudaStream_t st)
-{
-    ED_CUDA_TRY(cudaMemcpyAsync(host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
-    ED_CUDA_TRY(cudaStreamSynchronize(st));
     return ED_OK;
 }
 
@@ -896,11 +905,21 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_row_count<<<ed_div_up(m, 128), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->row_cnt, ctx->row_ptr, m, st)) != ED_OK) return s;
-        ED_CUDA_TRY(cudaMemcpyAsync(&nnzb, ctx->row_ptr + m, sizeof(int), cudaMemcpyDeviceToHost, st));
-        ED_CUDA_TRY(cudaStreamSynchronize(st));
-        if (nnzb > ctx->max_nnzb) return ED_ERR_CAPACITY;
+        // the block count goes to the host (pinned copy + event) while the
+        // kernels that need only the row pointer run: the block lists and the
+        // (point, block) entries, both checking the count against the capacity
+        int *nz_host = ctx->pinned + ED_MAX_PCG_GRID + 6;
+        ED_CUDA_TRY(cudaMemcpyAsync(nz_host, ctx->row_ptr + m, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
         k_row_fill<<<ed_div_up(m, 128), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
-                                                      ctx->diag_pos); ed_note_launch();
+                                                      ctx->diag_pos, ctx->max_nnzb, ctx->misc + MI_STATUS); ed_note_launch();
+        k_entries_gen<<<ed_div_up(NT, EG_T), EG_T, 0, st>>>((const ushort4 *)graph->idx, NT, ctx->row_ptr, ctx->col,
+                                                          ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS, m,
+                                                          ctx->max_nnzb); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
+        nnzb = *nz_host;
+        if (nnzb > ctx->max_nnzb) return ED_ERR_CAPACITY;
         k_tpos<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, nnzb, st)) != ED_OK) return s;
@@ -913,9 +932,6 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     const int ne = 10 * NT;
     int nchunks, n_upper = 0;
     {
-        k_entries_gen<<<ed_div_up(NT, EG_T), EG_T, 0, st>>>((const ushort4 *)graph->idx, NT, ctx->row_ptr, ctx->col,
-                                                          ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
-        ED_LAUNCH_CHECK();
         int bits = 1;
         while ((1 << bits) < nnzb) ++bits;
         if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, ne, bits, st)) != ED_OK) return s;
@@ -932,7 +948,18 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                     cudaMemcpyDeviceToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 2, ctx->flag_b + nnzb, sizeof(int), cudaMemcpyDeviceToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->row_ptr_host, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
-        if ((s = read_misc(ctx, hm, st)) != ED_OK) return s;
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
+        ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
+        // the chunk table and the entry geometry need no host value: queued
+        // before the wait (the chunk table checks its capacity itself)
+        k_chunk_fill<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->ent_start, ctx->brow, ctx->col,
+                                                           ctx->chunk_start, ctx->chunk_start1, ctx->chunks,
+                                                           ctx->max_chunks, ctx->misc + MI_STATUS); ed_note_launch();
+        k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, PT, graph->weights,
+                                                         G4, ctx->ent_geo); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
+        memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
         const int nc01[2] = {hm[MI_READ], hm[MI_READ + 1]};
         n_upper = hm[MI_READ + 2];
         if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
@@ -941,13 +968,6 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ctx->n_chunks0 = nc01[0];
         ctx->chunk_base1 = base1;
         if (nchunks > ctx->max_chunks) return ED_ERR_CAPACITY;
-        if (base1 > nc01[0])   // padding chunks between the roles: empty
-            ED_CUDA_TRY(cudaMemsetAsync(ctx->chunks + nc01[0], 0, sizeof(int4) * (base1 - nc01[0]), st));
-        k_chunk_fill<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->ent_start, ctx->brow, ctx->col,
-                                                           ctx->chunk_start, ctx->chunk_start1, ctx->chunks); ed_note_launch();
-        k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, PT, graph->weights,
-                                                         G4, ctx->ent_geo); ed_note_launch();
-        ED_LAUNCH_CHECK();
         ctx->pinned[ED_MAX_PCG_GRID + 1] = nnzb;
         ctx->pinned[ED_MAX_PCG_GRID + 2] = 0;
         ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, ctx->pinned + ED_MAX_PCG_GRID + 1, 2 * sizeof(int),
