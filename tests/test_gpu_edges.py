@@ -139,3 +139,32 @@ def test_graph_node_cap_truncates_in_selection_order():
     counts = g.counts.cpu().numpy()
     assert g.m == cap and counts[0] == cap and counts[1] == len(full_pt)
     assert np.array_equal(g.nodes[:cap, :3].cpu().numpy(), s.model_pos[full_pt[:cap], :3])
+
+
+def test_block_capacity_is_an_error_not_a_fault():
+    # a context whose block budget (max_pairs_per_node) is below the graph's
+    # row lengths: the pattern kernels queued before the host sees the block
+    # count check it themselves; the build reports ED_ERR_CAPACITY and the
+    # context stays usable (no graph: a GN step is refused)
+    torch, E = _torch(), _E()
+    s = C.scene(SMALL)
+    fx, fy, cx, cy, W, H = s.intr
+    ctx = E.Context(max_points=s.N, max_nodes=64, max_width=W, max_height=H, max_pairs_per_node=4)
+    pos = torch.from_numpy(s.model_pos).cuda()
+    nrm = torch.from_numpy(s.model_nrm).cuda()
+    r = C.radius_for(SMALL)
+    with pytest.raises(E.EDError) as ei:
+        ctx.build_graph(pos, nrm, node_radius=r, max_nodes=64, sigma=r)
+    assert ei.value.status == 3
+    depth = torch.from_numpy(s.tgt_depth).cuda()
+    nmap = ctx.compute_normals(depth, s.intr, s.cfg.normal_half_width)
+    frame = E.make_frame(depth, nmap, s.intr)
+    x = torch.zeros((64, 12), dtype=torch.float32, device="cuda")
+    pose = torch.zeros(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(E.EDError) as ei:
+        ctx.gn_step(frame, E.SolverParams(), x, pose)
+    assert ei.value.status == 7
+    torch.cuda.synchronize()
+    # the same build with the default budget succeeds
+    G = C.gpu_setup(s, radius=r, max_nodes=64)
+    assert G["graph"].m > 0
