@@ -136,14 +136,31 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
             a.rec1[i] = r1;
         }
     }
-    // block reduction: warp shuffles (float), then the warps in order (float-float)
+    // block reduction: for each half of the 31 sums a butterfly over the warp
+    // that halves the values a lane carries at every shuffle step (lane bit o
+    // keeps the upper or the lower half and receives that half from its
+    // partner), so lanes 2k and 2k + 1 end with the half's value k (float);
+    // then the warps in order (float-float)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 31; ++k) {
-        float v = acc[k];
+    for (int hf = 0; hf < 2; ++hf) {
+        float x[16];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][k] = v;
+        for (int k = 0; k < 16; ++k) x[k] = 16 * hf + k < 31 ? acc[16 * hf + k] : 0.f;
+#pragma unroll
+        for (int lvl = 0; lvl < 4; ++lvl) {
+            const int o = 16 >> lvl, n = 8 >> lvl;
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < n; ++j) {
+                const float send = up ? x[j] : x[j + n];
+                const float keep = up ? x[j + n] : x[j];
+                x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        const float v = x[0] + __shfl_xor_sync(0xffffffffu, x[0], 1);
+        const int k = 16 * hf + (lane >> 1);
+        if (!(lane & 1) && k < 31) red[wid][k] = v;
     }
     __syncthreads();
     if (threadIdx.x < 31) {
