@@ -102,7 +102,6 @@ size_t carve(ed_context *c, char *base)
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
     c->red_part = k.take<double>(4 * (size_t)ED_MAX_PCG_GRID);
-    c->fin_tickets = k.take<unsigned>(33 * 32);
     c->pcg_rows = k.take<int>(ED_MAX_PCG_GRID + 1);
     c->pcg_rows_b = k.take<int>(ED_MAX_PCG_GRID + 1);
     c->zbuf = k.take<unsigned long long>(WH);
@@ -165,7 +164,6 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
         cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess ||
         cudaMemset(c->dmisc, 0, sizeof(double) * 64) != cudaSuccess ||
-        cudaMemset(c->fin_tickets, 0, sizeof(unsigned) * 33 * 32) != cudaSuccess ||
         cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_state_len) != cudaSuccess ||
         cudaMemset(c->scan_ticket, 0, sizeof(unsigned)) != cudaSuccess) {
         cudaFreeHost(c->row_ptr_host);

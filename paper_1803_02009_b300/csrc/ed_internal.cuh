@@ -156,7 +156,6 @@ struct ed_context {
     size_t vec_stride;       // floats between vectors (multiple of 64: 16-byte aligned float4 rows)
     double *pcg_part;        // [2][ED_PCG_PART][ED_MAX_PCG_GRID] (component-major)
     double *red_part;        // [4][ED_MAX_PCG_GRID] per-CTA partials of ed_depth_error
-    unsigned *fin_tickets;   // [33][32] two-level done counters of k_finalize (one per 128-byte line)
     // fusion / scans
     unsigned long long *zbuf;  // [W H]
     int *regpix;             // [W H]

@@ -437,11 +437,10 @@ struct FinArgs {
     float *bsr, *grad, *pnode, *minv;
     float2 *node_energy;
     int *status;
-    // the last CTA forms the energy totals of the step from the node energies
+    // for k_fin_totals: the energy totals of the step from the node energies
     // and the pose pass's sums
     int m;
     int *misc;
-    unsigned *tickets;       // [33][32]: 32 group counters, then the counter of the groups
     double *dmisc;
     ed_stats *stats;
     float lambda_report;     // damping reported in the statistics
@@ -826,31 +825,14 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
         atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
 }
 
-// the CTA that finishes last: the node energies summed in a fixed order
+// after the finalisation, one CTA: the node energies summed in a fixed order
 // (float-float), the energy of Eq. (3) from them and the pose pass's sums,
-// the non-finite check, the step's statistics
-__device__ __forceinline__ void finalize_totals(const FinArgs &a)
+// the non-finite check, the step's statistics; it also clears the arrival
+// count of the step's PCG
+__global__ void __launch_bounds__(32 * FIN_WARPS) k_fin_totals(FinArgs a)
 {
-    __shared__ int s_last;
-    __shared__ float2 s_w[32 * FIN_WARPS / 32][2];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // two-level ticket (32 group counters on their own lines, then one
-        // counter of the groups): no single address sees every CTA
-        __threadfence();
-        const unsigned g = blockIdx.x & 31u, n = gridDim.x;
-        const unsigned in_group = (n - g + 31u) / 32u;
-        int last = 0;
-        if (atomicAdd(a.tickets + 32 * g, 1u) == in_group - 1) {
-            __threadfence();
-            const unsigned groups = n < 32u ? n : 32u;
-            last = atomicAdd(a.tickets + 32 * 32, 1u) == groups - 1;
-        }
-        s_last = last;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    ed_pdl_wait();
+    __shared__ float2 s_w[FIN_WARPS][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float2 er = make_float2(0.f, 0.f), eg = er;
     for (int j = threadIdx.x; j < a.m; j += 32 * FIN_WARPS) {
@@ -896,7 +878,6 @@ __device__ __forceinline__ void finalize_totals(const FinArgs &a)
             a.stats->lambda = a.lambda_report;
         }
     }
-    if (threadIdx.x < 33) a.tickets[32 * threadIdx.x] = 0;   // ready for the next launch
     if (threadIdx.x < 2) a.misc[MI_BAR + threadIdx.x] = 0;   // the arrival count of the step's PCG
 }
 
@@ -920,7 +901,6 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     const int u = blockIdx.x * FIN_WARPS + wid;
     if (u < a.n_upper)
         finalize_block<INV>(a, u, sM[wid], sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid], s_tab);
-    finalize_totals(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1348,13 +1328,13 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     fa.status = ctx->misc + MI_STATUS;
     fa.m = m;
     fa.misc = ctx->misc;
-    fa.tickets = ctx->fin_tickets;
     fa.dmisc = ctx->dmisc;
     fa.stats = stats;
     fa.lambda_report = fa.lambda;
     if (fork_pose) ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ed_tm_begin(ctx, ED_KERNEL_FINALIZE, st);
     (lm ? k_finalize<false> : k_finalize<true>)<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
+    ED_CUDA_TRY(ed_launch_pdl(k_fin_totals, dim3(1), dim3(32 * FIN_WARPS), 0, st, fa)); ed_note_launch();
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
     ED_LAUNCH_CHECK();
     if (lm) return lm_stage(ctx, prm, x, x_master, pose, stats, st);

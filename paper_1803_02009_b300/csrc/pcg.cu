@@ -894,7 +894,7 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, d
     PcgArgs a;
     ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, x, xm, pose, stats, a);
     if (s != ED_OK) return s;
-    // (the arrival count was cleared by the last CTA of the finalisation)
+    // (the arrival count was cleared by k_fin_totals, after the finalisation)
     void *args[] = {&a};
     ed_tm_begin(ctx, ED_KERNEL_PCG, st);
     ed_note_launch();
