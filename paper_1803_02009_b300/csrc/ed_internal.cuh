@@ -14,7 +14,7 @@
 #define ED_MAX_KG 8            // node-graph neighbours
 #define ED_HARD_MAX_NODES 16384
 #define ED_CHUNK 128           // role-0 assembly entries per chunk (4 per lane of a warp)
-#define ED_CHUNK1 128          // role-1 (J^T r, pose-node) assembly entries per chunk
+#define ED_CHUNK1 1024         // role-1 (J^T r, pose-node) assembly entries per chunk (rounds of 128)
 #define ED_PART_STRIDE 96      // floats per chunk partial (60 moments, or 12 + 72), chunk-major
 #define ED_K1_THREADS 256
 #define ED_K1_PART 32          // components of a point-kernel CTA partial (30 used)

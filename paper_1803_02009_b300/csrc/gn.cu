@@ -255,7 +255,7 @@ __device__ __forceinline__ void warp_halving2(float2 (&v)[NV])
     }
 }
 
-static_assert(ED_CHUNK == 128 && ED_CHUNK1 == 128, "the assembly kernels take 4 entries per lane");
+static_assert(ED_CHUNK == 128 && ED_CHUNK1 % 128 == 0, "the assembly kernels take 4 entries per lane (and round)");
 
 // Recursive halving of 16 float2 values per lane down to one per lane pair,
 // then the pair: afterwards lanes 2k and 2k + 1 both hold the full sum of
@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chun
         reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[15 * h + (lane >> 1)] = v[0];
 }
 
-// role 1 (diagonal blocks): two warps per chunk; per entry J^T r (12 floats)
+// role 1 (diagonal blocks): two warps per chunk of <= ED_CHUNK1 entries (most
+// nodes have one chunk), in rounds of 128 entries; per entry J^T r (12 floats)
 // and the pose-node block (6 x 12) of node j.  Moment pairs (float2 slots):
 // 0..5 J^T r, 6 + 6 t + 2 r (+1) pose-node row t, node row r.  Half 0 forms
 // slots 0..23 (J^T r, rows t = 0..2), half 1 slots 24..41 (t = 3..5); the
@@ -349,13 +350,15 @@ __device__ __forceinline__ void assemble1_half(const int4 ch, int c, const float
     float2 v[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int e0 = 0; e0 < ch.z; e0 += 128) {
 #pragma unroll
     for (int q0 = 0; q0 < 4; q0 += 2) {
         float4 gd[2], b[2], jq[2];
         int pi[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int e = lane + 32 * (q0 + u);
+            const int e = e0 + lane + 32 * (q0 + u);
             const bool in = e < ch.z;
             gd[u] = in ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);
             pi[u] = in ? (int)(__ldg(ent + ch.y + e) >> 4) : -1;
@@ -399,12 +402,13 @@ __device__ __forceinline__ void assemble1_half(const int4 ch, int c, const float
             }
         }
     }
+    }
     warp_halving2<32>(v);
     constexpr int NSLOT = H == 0 ? 24 : 18;
     if (lane < NSLOT) reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[24 * H + lane] = v[0];
 }
 
-__global__ void __launch_bounds__(128, 6) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
+__global__ void __launch_bounds__(128, 4) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
                                                    int max_chunks, const float4 *__restrict__ geo,
                                                    const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
                                                    const float4 *__restrict__ rec1, const double *__restrict__ pose,
