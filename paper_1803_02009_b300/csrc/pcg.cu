@@ -44,7 +44,7 @@ struct PcgArgs {
     int max_rows, max_blk;   // shared-memory plan
     const float *bsr, *pnode, *minv, *pose_blk, *grad;
     float *d;                // the solution
-    float *z0, *s0, *s1;     // published z of the set-up, s = M^-1 q of even / odd iterations
+    float *s0, *s1;          // published s = M^-1 q of even / odd iterations
     double *part;            // [2][PCG_NC][ED_MAX_PCG_GRID] partials of even / odd iterations, component-major
                              // (stored in the accumulator's type: float in FP32 mode, float2 in mixed mode)
     float *x;                // node parameters, x += d at the end (all CTAs passed every barrier)
@@ -247,6 +247,23 @@ __host__ __device__ inline PcgSmem pcg_smem_layout(int rows, int nblk, int ncach
     return L;
 }
 
+// a row of a 12x12 block times a 12-vector, rounded in a fixed order: a CTA
+// forms z = M^-1 r for its own rows and, from the owners' data, for the copies
+// of its block columns, and the copies must agree with the owners bit for bit
+__device__ __forceinline__ float dot12(const float4 (&m)[3], const float4 (&v)[3])
+{
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float d = __fmul_rn(m[q].x, v[q].x);
+        d = __fmaf_rn(m[q].y, v[q].y, d);
+        d = __fmaf_rn(m[q].z, v[q].z, d);
+        d = __fmaf_rn(m[q].w, v[q].w, d);
+        acc = __fadd_rn(acc, d);
+    }
+    return acc;
+}
+
 // the solve of one problem by CTA `cta` of the `nb` CTAs given to it
 template <typename DT, int NT>
 __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const unsigned nb)
@@ -293,15 +310,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     auto fail = [&]() {
         if (cta == 0 && t == 0 && a.stats) a.stats->status = *(volatile int *)a.status;
     };
-    if (*(volatile int *)a.status != ED_OK) {
-        fail();
-        return;
-    }
 
     // ---- the CTA's share of H, M^-1 and C into shared memory by bulk
     // asynchronous copies (inverses and pose-node blocks on mbarrier 0, needed
-    // first; blocks on mbarrier 1, needed by the first q = H p); block columns
-    // and b by plain loads meanwhile ----
+    // first; blocks on mbarrier 1, needed by the first q = H p); block columns,
+    // b and z = M^-1 b of the block columns by plain loads meanwhile.  All of it
+    // is in bounds whatever the status word says; the status is checked once
+    // the copies have landed ----
     __shared__ __align__(8) unsigned long long s_mbar[2];
     if (t == 0) {
         ed_mbar_init(&s_mbar[0], 1);
@@ -335,6 +350,39 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         s_rp[t] = -__ldg(a.grad + P + t);
         s_dp[t] = 0.f;
     }
+    // z = M^-1 r (r = b) and p = z of every block column, formed here from its
+    // owner's inverse and gradient with the owner's arithmetic (dot12 on the
+    // same values), so no exchange is needed before the first iteration
+    for (int i0 = t; i0 < nblk * 12; i0 += 2 * NT) {   // two items per step, their loads together
+        float4 m4[2][3], r4[2][3];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = i0 + u * NT;
+            if (i < nblk * 12) {
+                const int lb = i / 12, rw = i - 12 * lb;
+                const size_t l = (size_t)__ldg(a.col + b0 + lb);
+                const float4 *mv = reinterpret_cast<const float4 *>(a.minv + l * 144 + rw * 12);
+                const float4 *gv = reinterpret_cast<const float4 *>(a.grad + 12 * l);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    m4[u][q] = __ldg(mv + q);
+                    r4[u][q] = __ldg(gv + q);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = i0 + u * NT;
+            if (i < nblk * 12) {
+                const int lb = i / 12, rw = i - 12 * lb;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) r4[u][q] = make_float4(-r4[u][q].x, -r4[u][q].y, -r4[u][q].z, -r4[u][q].w);
+                const float z = dot12(m4[u], r4[u]);
+                zb[(size_t)lb * 12 + rw] = z;
+                pb[(size_t)lb * 12 + rw] = z;
+            }
+        }
+    }
     if (!ed_mbar_wait(&s_mbar[0], 0)) {
         atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
         ed_mbar_wait(&s_mbar[0], 0);
@@ -342,9 +390,15 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         fail();
         return;
     }
+    if (t == 0) s_flag = *(volatile int *)a.status == ED_OK;   // one reading for the whole CTA
     __syncthreads();
+    if (!s_flag) {
+        ed_mbar_wait(&s_mbar[1], 0);
+        fail();
+        return;
+    }
     bool h_ready = false;
-    if (split_rows && t < 32) {   // (read after the grid barrier of the set-up)
+    if (split_rows && t < 32) {   // (read after the CTA barrier at the loop head)
         auto blocks = [&](int j) { return j < rows ? a.row_ptr[r0 + j + 1] - a.row_ptr[r0 + j] : 0; };
         const int bA = blocks(t), bB = blocks(t + 32);
         int T = max(1, (nblk + NG - 1) / NG);
@@ -389,61 +443,52 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
 
 
     // dst = M^-1 src for the own rows (thread = one output row of a node),
-    // also into gdst; f(element index, value) sees every result
+    // also into gdst unless NULL; f(element index, value) sees every result
     auto apply_minv = [&](const float *src, float *dst, float *gdst, auto &&f) {
         for (int j0 = 0; j0 < rows; j0 += ROWS_PER_PASS) {
             const int jl = j0 + grp;
             if (in_grp && jl < rows) {
                 const float4 *mv = reinterpret_cast<const float4 *>(Ms + jl * 144 + rr * 12);
                 const float4 *sv = reinterpret_cast<const float4 *>(src + jl * 12);
-                float v = 0.f;
+                float4 m4[3], s4[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    const float4 m4 = mv[q], s4 = sv[q];
-                    v += m4.x * s4.x + m4.y * s4.y + m4.z * s4.z + m4.w * s4.w;
+                    m4[q] = mv[q];
+                    s4[q] = sv[q];
                 }
+                const float v = dot12(m4, s4);
                 const int e = jl * 12 + rr;
                 dst[e] = v;
-                gdst[12 * r0 + e] = v;
+                if (gdst) gdst[12 * r0 + e] = v;
                 f(e, v);
             }
         }
     };
 
-    // ---- set-up: r = b, d = 0, z = M^-1 r (published for the CTAs whose
-    // block columns reach these rows), p = z; partial r.r for ||b|| ----
-    {
-        AT rr0 = A::zero();
-        apply_minv(rs, zs, a.z0, [&](int e, float) { rr0 = A::madd(rr0, rs[e], rs[e]); });
-        AT vv[1] = {rr0};
-        block_sum_n<DT, NT, 1>(vv, s_red);
-    }
+    // ---- set-up: r = b, d = 0, z = M^-1 r, p = z (the block columns' copies
+    // were formed above); ||b|| comes with the r.r of the first iteration ----
+    apply_minv(rs, zs, nullptr, [&](int, float) {});
     if (t < 6) {
         float zi = 0.f;
         for (int k = 0; k < 6; ++k) zi += Mp[6 * t + k] * s_rp[k];
         s_zp[t] = zi;
         s_pp[t] = zi;
     }
-    // (the partials of odd iterations hold the set-up's: iteration 0 writes the even ones
-    // while slower CTAs may still read these)
-    double *part_setup = a.part + (size_t)ED_MAX_PCG_GRID * PCG_NC;
-    if (t == 0) *part_at<DT>(part_setup, 0, cta) = block_sum_get<DT, NT>(s_red, 0);
-    if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
-        fail();
-        return;
-    }
-    // z of every block column from its owner; p = z
-    const int n_items = nblk * 3;
-    for (int i = t; i < n_items; i += NT) {
-        const int lb = i / 3, q4 = i - 3 * lb;
-        const float4 z4 = __ldcg(reinterpret_cast<const float4 *>(a.z0 + 12 * lc[lb]) + q4);
-        reinterpret_cast<float4 *>(zb + (size_t)lb * 12)[q4] = z4;
-        reinterpret_cast<float4 *>(pb + (size_t)lb * 12)[q4] = z4;
-    }
+    __syncthreads();
     for (int i = t; i < rows * 12; i += NT) ps[i] = zs[i];
-    float res0;
-    {
-        sum_partials<DT, NT, 1>(part_setup, nb, s_red2);
+    const int n_items = nblk * 3;
+    float res0 = 0.f;   // ||b|| (thread 0)
+    if (a.n_iter == 0) {   // no iteration: ||b|| for the statistics by one reduction
+        AT rr0 = A::zero();
+        for (int i = t; i < rows * 12; i += NT) rr0 = A::madd(rr0, rs[i], rs[i]);
+        AT vv[1] = {rr0};
+        block_sum_n<DT, NT, 1>(vv, s_red);
+        if (t == 0) *part_at<DT>(a.part, 0, cta) = block_sum_get<DT, NT>(s_red, 0);
+        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
+            fail();
+            return;
+        }
+        sum_partials<DT, NT, 1>(a.part, nb, s_red2);
         AT v = sum_partials_get<DT, NT, 1>(s_red2, 0);
 #pragma unroll
         for (int i = 0; i < 6; ++i) v = A::madd(v, s_rp[i], s_rp[i]);
@@ -644,6 +689,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
                 // r.z and r.r of the current residual: the tests of the loop head
                 const float rho = A::to_float(tot[3]);
                 rr_last = A::to_float(tot[4]);
+                if (it == 0) res0 = sqrtf(fmaxf(rr_last, 0.f));   // r = b at the start
                 int ctl = 0;
                 float al = 0.f, be = 0.f;
                 if (!(rho > 0.f) || (a.tol > 0.f && sqrtf(rr_last) <= a.tol * res0)) {
@@ -852,7 +898,6 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     a.pose_blk = ctx->pose_blk;
     a.grad = ctx->grad;
     a.d = ctx->vec;
-    a.z0 = ctx->vec + 2 * P;
     a.s0 = ctx->vec + 3 * P;
     a.s1 = ctx->vec + 4 * P;
     a.part = ctx->pcg_part;
@@ -860,8 +905,8 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     a.status = ctx->misc + MI_STATUS;
     a.stats = stats;
     // every vector is read as float4 rows: 16-byte alignment is required
-    const float *vv[4] = {a.d, a.z0, a.s0, a.s1};
-    for (int i = 0; i < 4; ++i)
+    const float *vv[3] = {a.d, a.s0, a.s1};
+    for (int i = 0; i < 3; ++i)
         if ((uintptr_t)vv[i] & 15) return ED_ERR_STATE;
     if (((uintptr_t)a.bsr & 15) || ((uintptr_t)a.minv & 15)) return ED_ERR_STATE;
     return ED_OK;
