@@ -722,7 +722,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         const float alpha = s_ab[0], beta = s_ab[1];
         // ---- updates: own rows, block columns, pose (warp 0; every reader of
         // the pose parts has passed the barrier above) ----
-        for (int i = t; i < rows * 12; i += NT) {
+        // (own rows from the last thread down: the first threads also take the
+        // block-column items beyond the first NT)
+        for (int i = NT - 1 - t; i < rows * 12; i += NT) {
             ds[i] = __fmaf_rn(alpha, ps[i], ds[i]);
             rs[i] = __fmaf_rn(-alpha, qs[i], rs[i]);
             const float zn = __fmaf_rn(-alpha, ss[i], zs[i]);
