@@ -279,6 +279,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     // the pose parts of r, z, p, d: the same values in every CTA
     __shared__ float s_rp[6], s_zp[6], s_pp[6], s_dp[6];
     __shared__ float s_Hpp[36], s_Mp[36];
+    __shared__ float s_hp[6];               // H_pp p_pose of the iteration (formed at its start)
     __shared__ float s_ab[2];               // alpha, beta of the iteration
     __shared__ int s_ctl;                   // 0 go on, 1 converged or stalled, 2 breakdown
 
@@ -560,6 +561,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             }
             h_ready = true;
         }
+        if (t >= NT - 6) {   // the last warp: H_pp p_pose, needed after the barrier
+            const int i = t - (NT - 6);
+            float h = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h += Hpp[6 * i + k] * s_pp[k];
+            s_hp[i] = h;
+        }
         // ---- q = H p for the own rows (thread = one output row of one of
         // the S splits of a row's blocks), partials C p of the pose rows ----
         AT cp[6] = {A::zero(), A::zero(), A::zero(), A::zero(), A::zero(), A::zero()};
@@ -657,9 +665,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         AT rq_t = A::zero(), q2_t = A::zero();   // thread 0: r.q and q.q
         if (t < 32) {
             const int i = t < 6 ? t : 0;
-            float qi = A::to_float(sum_partials_get<DT, NT, PCG_NC>(s_red2, 7 + i));
-#pragma unroll
-            for (int k = 0; k < 6; ++k) qi += Hpp[6 * i + k] * s_pp[k];
+            const float qi = A::to_float(sum_partials_get<DT, NT, PCG_NC>(s_red2, 7 + i)) + s_hp[i];
             float si = 0.f;
 #pragma unroll
             for (int k = 0; k < 6; ++k) si += Mp[6 * i + k] * __shfl_sync(0xffffffffu, qi, k);
