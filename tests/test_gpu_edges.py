@@ -168,3 +168,33 @@ def test_block_capacity_is_an_error_not_a_fault():
     # the same build with the default budget succeeds
     G = C.gpu_setup(s, radius=r, max_nodes=64)
     assert G["graph"].m > 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_zero_pcg_iterations_keep_the_parameters_and_report_b(precision):
+    # n_pcg = 0: no PCG iteration, x and the pose unchanged, d = 0; ||b||
+    # (the norm of the assembled gradient) is still reported, the same as a
+    # solve with iterations reports for the same system
+    torch, E = _torch(), _E()
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s)
+    ctx, m = G["ctx"], G["graph"].m
+    prec = E.ED_PRECISION_MIXED if precision == "mixed" else E.ED_PRECISION_FP32
+    x = ctx.identity_x()
+    xm = x.double().clone()
+    pose = torch.zeros(6, dtype=torch.float64, device="cuda")
+    st = E.new_stats(1)
+    ctx.gn_step(G["frame"], E.SolverParams(n_pcg=0, precision=prec), x, pose, x_master=xm, stats=st)
+    r0 = E.read_stats(st)[0]
+    assert r0["status"] == 0 and r0["pcg_iters"] == 0
+    assert torch.equal(x, ctx.identity_x()) and torch.equal(pose, torch.zeros_like(pose))
+    sysm = ctx.export_system()
+    assert float(sysm["delta"].abs().max()) == 0.0
+    gnorm = float(sysm["grad"].double().norm())
+    assert r0["pcg_res0"] == pytest.approx(gnorm, rel=1e-5) and r0["pcg_res"] == pytest.approx(gnorm, rel=1e-5)
+    # the same system solved with iterations reports the same ||b||
+    ctx.gn_step(G["frame"], E.SolverParams(n_pcg=10, precision=prec), x, pose, x_master=xm, stats=st)
+    r1 = E.read_stats(st)[0]
+    assert r1["status"] == 0 and r1["pcg_iters"] == 10
+    assert r1["pcg_res0"] == pytest.approx(gnorm, rel=1e-5)
+    assert r1["pcg_res"] < r1["pcg_res0"]
