@@ -64,6 +64,7 @@ size_t carve(ed_context *c, char *base)
     c->tpos = k.take<int>(nnzb);
     c->diag_pos = k.take<int>(M);
     c->up_list = k.take<int>(nnzb);
+    c->fin_info = k.take<int4>(2 * ((nnzb + M) / 2 + 1));
     c->max_nnzb = (int)nnzb;
     c->ent_key = k.take<uint32_t>(nent);
     c->ent_val = k.take<uint32_t>(nent);

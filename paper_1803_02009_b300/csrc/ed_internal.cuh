@@ -111,6 +111,7 @@ struct ed_context {
     int *tpos;               // [max_nnzb] position of the transposed block
     int *diag_pos;           // [max_nodes]
     int *up_list;            // [max_nnzb] upper block positions
+    int4 *fin_info;          // [n_upper][2] packed finalisation records (per frame, k_fin_pack)
     int max_nnzb;
     // assembly lists
     uint32_t *ent_key;       // [10 N] block id, then sorted

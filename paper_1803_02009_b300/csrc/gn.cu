@@ -431,9 +431,10 @@ __global__ void __launch_bounds__(128, 4) k_assemble1(const int4 *__restrict__ c
 // ---------------------------------------------------------------------------
 
 struct FinArgs {
-    const int *up_list, *brow, *col, *tpos, *row_ptr, *chunk_start, *chunk_start1, *ent_cnt, *nbr;
+    const int4 *info;        // [n_upper][2] records of the upper blocks (k_fin_pack)
+    const int *col, *nbr;
     const float *part;
-    int max_chunks, n_chunks0;
+    int max_chunks;
     int n_upper, kg, mixed;
     const float4 *g;
     const float4 *x4;
@@ -631,6 +632,25 @@ __device__ __forceinline__ void part_sums2(const FinArgs &a, int ca, int cb, int
     vb = part_value(pb, a.mixed);
 }
 
+// the same for three components (cc < 0: none)
+__device__ __forceinline__ void part_sums3(const FinArgs &a, int ca, int cb, int cc, int c0, int n, float &va, float &vb,
+                                           float &vc)
+{
+    PartSum pa = part_sum(a.part, ca, c0, n), pb = part_sum(a.part, cb, c0, n), pc = part_sum(a.part, cc, c0, n);
+    for (int k0 = 0; k0 < pa.n; k0 += 4) {
+        float4 x, y, z;
+        part_load4(pa, k0, x);
+        part_load4(pb, k0, y);
+        part_load4(pc, k0, z);
+        part_add4(pa, k0, x, a.mixed);
+        part_add4(pb, k0, y, a.mixed);
+        part_add4(pc, k0, z, a.mixed);
+    }
+    va = part_value(pa, a.mixed);
+    vb = part_value(pb, a.mixed);
+    vc = part_value(pc, a.mixed);
+}
+
 // one warp per upper block u (INV = false: the block inverses are taken
 // later, in the Levenberg-Marquardt stage).  The 144 entries of a block go to
 // lanes 0..23: lane L takes column C = L % 12 of the rows R = L / 12 + 2 k,
@@ -640,21 +660,16 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
                                                float *Lw, int *Nk, float4 *Ng, float *Nx, const int *s_tab)
 {
     const int lane = threadIdx.x & 31;
-    const int b = a.up_list[u];
-    const int j = a.brow[b], l = a.col[b];
-    const int cnt = a.ent_cnt[b], c0 = a.chunk_start[b];
+    const int4 i0 = a.info[2 * u], i1 = a.info[2 * u + 1];
+    const int b = i0.x, j = i0.y, l = i0.z;
     const bool diag = j == l;
-    const int nch = (cnt + ED_CHUNK - 1) / ED_CHUNK;
+    const int c0 = i1.x, nch = i1.y;
     const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
     const bool ent_lane = lane < 24;
     const float wr = a.w_reg;
     if (!diag) {
-        const int tb = a.tpos[b];
-        bool e_jl = false, e_lj = false;
-        for (int s = 0; s < a.kg; ++s) {
-            e_jl |= a.nbr[j * a.kg + s] == l;
-            e_lj |= a.nbr[l * a.kg + s] == j;
-        }
+        const int tb = i0.w;
+        const bool e_jl = (i1.z & 1) != 0, e_lj = (i1.z & 2) != 0;   // graph edges j -> l, l -> j
         const float4 gj = a.g[j], gl = a.g[l];
         {
             float v0, v1;
@@ -691,8 +706,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
         return;
     }
     // ---- diagonal block ----
-    const int cs1 = a.chunk_start1[b];
-    const int rp0 = a.row_ptr[j], rp1 = a.row_ptr[j + 1];
+    const int rp0 = i0.w, rp1 = rp0 + (i1.w >> 16);   // row j of the block pattern
     if (lane < a.kg) {   // out-edges j -> k: index, position and parameters of k, loaded once
         const int k = a.nbr[j * a.kg + lane];
         Nk[lane] = k;
@@ -712,10 +726,9 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
         part_sums2(a, lane, lane + 32 < 60 ? lane + 32 : -1, c0, nch, v0, v1);
         M[lane] = v0;
         if (lane + 32 < 60) M[lane + 32] = v1;
-        const int c1 = a.n_chunks0 + cs1, nch1 = (cnt + ED_CHUNK1 - 1) / ED_CHUNK1;
-        float w0, w1, w2, w3;
-        part_sums2(a, lane, lane + 32, c1, nch1, w0, w1);
-        part_sums2(a, lane + 64 < 84 ? lane + 64 : -1, -1, c1, nch1, w2, w3);
+        const int c1 = i1.z, nch1 = i1.w & 0xffff;
+        float w0, w1, w2;
+        part_sums3(a, lane, lane + 32, lane + 64 < 84 ? lane + 64 : -1, c1, nch1, w0, w1, w2);
         auto put = [&](int k, float v) {
             if (k < 12) Gx[k] = v;
             else a.pnode[(long)j * 72 + (k - 12)] = v;
@@ -1303,18 +1316,11 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
         ED_LAUNCH_CHECK();
     }
     FinArgs fa;
-    fa.up_list = ctx->up_list;
-    fa.brow = ctx->brow;
+    fa.info = ctx->fin_info;
     fa.col = ctx->col;
-    fa.tpos = ctx->tpos;
-    fa.row_ptr = ctx->row_ptr;
-    fa.chunk_start = ctx->chunk_start;
-    fa.chunk_start1 = ctx->chunk_start1;
-    fa.ent_cnt = ctx->ent_cnt;
     fa.nbr = ctx->graph.nbr;
     fa.part = ctx->partials;
     fa.max_chunks = ctx->max_chunks;
-    fa.n_chunks0 = ctx->chunk_base1;
     fa.n_upper = ctx->n_upper;
     fa.kg = ctx->k_graph;
     fa.mixed = prm->precision == ED_PRECISION_MIXED;

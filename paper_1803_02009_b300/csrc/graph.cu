@@ -703,6 +703,39 @@ __global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *_
     }
 }
 
+// the finalisation's record of every upper block u, fixed for the frame (one
+// load for what the finalisation's warps would otherwise fetch in dependent
+// steps): {b, j, l, transpose position} and {first role-0 chunk, role-0
+// chunks, graph-edge flags (j -> l: 1, l -> j: 2), 0}; for a diagonal block
+// {b, j, j, row start} and {first role-0 chunk, role-0 chunks, first role-1
+// chunk, role-1 chunks | row length << 16}
+__global__ void k_fin_pack(int nnzb, int m, int kg, const int *__restrict__ up_list, const int *__restrict__ flag_b,
+                           const int *__restrict__ brow, const int *__restrict__ col, const int *__restrict__ tpos,
+                           const int *__restrict__ row_ptr, const int *__restrict__ cnt,
+                           const int *__restrict__ cstart0, const int *__restrict__ cstart1,
+                           const int *__restrict__ nbr, int4 *__restrict__ info)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= m + flag_b[nnzb]) return;   // the upper-block count
+    const int b = up_list[u];
+    const int j = brow[b], l = col[b], n = cnt[b];
+    const int c0 = cstart0[b], nch = (n + ED_CHUNK - 1) / ED_CHUNK;
+    if (j == l) {
+        const int base1 = (cstart0[nnzb] + 31) & ~31;   // role-1 chunks start warp-aligned
+        const int rp0 = row_ptr[j], len = row_ptr[j + 1] - rp0;
+        info[2 * u] = make_int4(b, j, l, rp0);
+        info[2 * u + 1] = make_int4(c0, nch, base1 + cstart1[b], ((n + ED_CHUNK1 - 1) / ED_CHUNK1) | (len << 16));
+    } else {
+        int flags = 0;
+        for (int s = 0; s < kg; ++s) {
+            if (nbr[j * kg + s] == l) flags |= 1;
+            if (nbr[l * kg + s] == j) flags |= 2;
+        }
+        info[2 * u] = make_int4(b, j, l, tpos[b]);
+        info[2 * u + 1] = make_int4(c0, nch, flags, 0);
+    }
+}
+
 // per-entry geometry, fixed for the frame: geo[e] = (v_i - g_j, w_s w_t) for the
 // entry e (point i, slots s, t) of upper block (j, l)
 __global__ void k_entry_geo(int ne, const uint32_t *__restrict__ key, const uint32_t *__restrict__ ent,
@@ -957,6 +990,10 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                                            ctx->max_chunks, ctx->misc + MI_STATUS); ed_note_launch();
         k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, PT, graph->weights,
                                                          G4, ctx->ent_geo); ed_note_launch();
+        k_fin_pack<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow,
+                                                         ctx->col, ctx->tpos, ctx->row_ptr, ctx->ent_cnt,
+                                                         ctx->chunk_start, ctx->chunk_start1, graph->nbr,
+                                                         ctx->fin_info); ed_note_launch();
         ED_LAUNCH_CHECK();
         ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
         memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
