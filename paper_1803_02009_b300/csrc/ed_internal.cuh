@@ -376,10 +376,16 @@ struct ed_warped {
 // calls ed_pdl_wait() before it reads or writes anything that kernel touches
 // (launched without the attribute, the wait returns at once).  Only for a
 // kernel whose stream predecessor is a kernel: not after a wait on another
-// stream's event.
+// stream's event.  Reads before the wait are limited to data written two or
+// more kernels back by kernels that call ed_pdl_trigger after their own wait.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void ed_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// lets the next programmatic dependent launch start (its CTAs fill the slots
+// this kernel frees); called after ed_pdl_wait, so that a dependent may read,
+// before its own wait, anything written two or more kernels back
+__device__ __forceinline__ void ed_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 static inline cudaError_t ed_launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -39,6 +39,7 @@ struct PointArgs {
 __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
 {
     ed_pdl_wait();
+    ed_pdl_trigger();
     // a Gauss-Newton step starts with a clear status word: nothing before this
     // kernel's end reads it, and no thread of this kernel writes it otherwise
     if (a.status_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.status_reset = ED_OK;
@@ -291,23 +292,27 @@ __global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chun
                                                    const float4 *__restrict__ geo, const uint32_t *__restrict__ ent,
                                                    const float4 *__restrict__ rec0, float *__restrict__ part)
 {
-    ed_pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int c = wg >> 1, h = wg & 1;
     if (c >= nchunks) return;
+    // the chunk, its geometry and its entries are fixed for the frame: loaded
+    // before the wait for the point pass (whose residual records come after)
     const int4 ch = chunks[c];
     float4 gd[4], b[4];
+    int pt[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int e = lane + 32 * q;
         gd[q] = e < ch.z ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);   // w = 0: no contribution
+        pt[q] = e < ch.z ? (int)(__ldg(ent + ch.y + e) >> 4) : -1;
     }
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    // (the point pass may still have been writing the records while this kernel
+    // was alive: coherent loads, not the read-only path)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int e = lane + 32 * q;
-        b[q] = e < ch.z ? __ldg(rec0 + (__ldg(ent + ch.y + e) >> 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    for (int q = 0; q < 4; ++q) b[q] = pt[q] >= 0 ? __ldcg(rec0 + pt[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
     float2 v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
@@ -414,14 +419,14 @@ __global__ void __launch_bounds__(128, 4) k_assemble1(const int4 *__restrict__ c
                                                    const float4 *__restrict__ rec1, const double *__restrict__ pose,
                                                    float *__restrict__ part)
 {
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int c = c_begin + (wg >> 1), h = wg & 1;
+    const int4 ch = c < c_begin + nchunks ? chunks[c] : make_int4(0, 0, 0, 0);   // fixed for the frame
     ed_pdl_wait();
     __shared__ ed_pose_f P;
     if (threadIdx.x == 0) ed_pose_eval(pose, P);
     __syncthreads();
-    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int c = c_begin + (wg >> 1), h = wg & 1;
     if (c >= c_begin + nchunks) return;
-    const int4 ch = chunks[c];
     if (h == 0) assemble1_half<0>(ch, c, P.R, geo, ent, rec0, rec1, part);
     else assemble1_half<1>(ch, c, P.R, geo, ent, rec0, rec1, part);
 }
@@ -849,6 +854,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
 __global__ void __launch_bounds__(32 * FIN_WARPS) k_fin_totals(FinArgs a)
 {
     ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ float2 s_w[FIN_WARPS][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float2 er = make_float2(0.f, 0.f), eg = er;
@@ -912,6 +918,7 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
     // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
     // shift), R, C (the same for every block; computed once per CTA)
     __shared__ int s_tab[144];
+    ed_pdl_trigger();   // (launched after the join with the pose stream: everything before is complete)
     fill_block_table(s_tab);
     __syncthreads();
     const int wid = threadIdx.x >> 5;

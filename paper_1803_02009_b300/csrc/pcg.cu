@@ -50,6 +50,8 @@ struct PcgArgs {
     float *x;                // node parameters, x += d at the end (all CTAs passed every barrier)
     double *xm;              // FP64 master copy (mixed precision) or NULL
     double *pose;            // pose += d_pose (CTA 0)
+    int load_before_wait;    // 1: the set-up's loads come before the wait for the stream predecessor (which
+                             // then must be k_fin_totals: everything these loads read is two kernels back)
     unsigned *bar;           // arrival count
     int *status;
     ed_stats *stats;
@@ -391,6 +393,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         fail();
         return;
     }
+    ed_pdl_wait();   // (no-op when it came first or without the launch attribute)
     if (t == 0) s_flag = *(volatile int *)a.status == ED_OK;   // one reading for the whole CTA
     __syncthreads();
     if (!s_flag) {
@@ -782,7 +785,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
 template <typename DT, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_pcg(PcgArgs a)
 {
-    ed_pdl_wait();
+    // (no early trigger: the next point pass reads x and the pose through the
+    // read-only path, so it must not be alive while this kernel writes them)
+    if (!a.load_before_wait) ed_pdl_wait();
     pcg_body<DT, NT>(a, blockIdx.x, gridDim.x);
 }
 
@@ -912,6 +917,7 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     a.bar = (unsigned *)(ctx->misc + MI_BAR);
     a.status = ctx->misc + MI_STATUS;
     a.stats = stats;
+    a.load_before_wait = 0;
     // every vector is read as float4 rows: 16-byte alignment is required
     const float *vv[3] = {a.d, a.s0, a.s1};
     for (int i = 0; i < 3; ++i)
@@ -947,6 +953,9 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, d
     PcgArgs a;
     ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, x, xm, pose, stats, a);
     if (s != ED_OK) return s;
+    // the stream predecessor is k_fin_totals unless the Levenberg-Marquardt
+    // stage comes between (its kernels are launched without triggers)
+    a.load_before_wait = prm->lm_accept ? 0 : 1;
     // (the arrival count was cleared by k_fin_totals, after the finalisation)
     void *args[] = {&a};
     ed_tm_begin(ctx, ED_KERNEL_PCG, st);
