@@ -1069,8 +1069,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_pose_part(const float2 *__restri
     if (t < 32) {
         if (!pose_inverse6(Ls, rinv, prm.jitter, pose_blk + 36) && lane == 0) atomicCAS(status, 0, ED_ERR_BREAKDOWN);
     } else if (t == 32) {
-        // for the energy totals the last CTA of k_finalize forms (the node
-        // energies are not known yet: this pass runs beside the assembly)
+        // for the energy totals k_fin_totals forms after the finalisation (the
+        // node energies are not known yet: this pass runs beside the assembly)
         double *ps = dmisc + DM_POSE;
         ps[0] = s[0];
         ps[1] = s[1];
