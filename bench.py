@@ -274,7 +274,7 @@ def run_ours(args, rank, world, local):
 
     gn_ev = []
 
-    def step(record_gn=False, depth=depth, color=color, frame=frame):
+    def step(record_gn=False, depth=depth, color=color, frame=frame, while_solving=None):
         ctx.compute_normals(depth, s.intr, cfg.normal_half_width, out=nmap)
         g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius, weight_mode=wmode,
                             reuse=True)
@@ -287,6 +287,8 @@ def run_ours(args, rank, world, local):
             e0.record()
         for it in range(cfg.n_gn):
             ctx.gn_step(frame, prm_c, x[:m], pose, x_master=xm[:m], stats=stats[it:it + 1])
+            if it == 0 and while_solving is not None:
+                while_solving()              # (host work while the GPU has the solve queued)
         if record_gn:
             e1 = torch.cuda.Event(enable_timing=True)
             e1.record()
@@ -339,7 +341,9 @@ def run_ours(args, rank, world, local):
     # end to end through the public API with host buffers: every step copies
     # its frame (depth, colour) in from pinned host memory and reads its result
     # (node parameters, statistics) back; the next frame's copy runs on a copy
-    # stream into the other of two input buffers while this frame computes
+    # stream into the other of two input buffers while this frame's solve runs
+    # (issued after the first Gauss-Newton step: during the graph build, whose
+    # host reads wait for the GPU, the copy held the build back)
     h_depth = torch.from_numpy(s.tgt_depth).pin_memory()
     h_color = torch.from_numpy(np.ascontiguousarray(s.tgt_color)).pin_memory()
     h_x = torch.empty((cfg.node_count, 12), dtype=torch.float32).pin_memory()
@@ -367,8 +371,7 @@ def run_ours(args, rank, world, local):
         fetch(0)
         for k in range(n):
             b = k & 1
-            if k + 1 < n:
-                fetch(k + 1)
+            nxt = (lambda kk=k + 1: fetch(kk)) if k + 1 < n else None
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
             f0.record()
@@ -377,7 +380,7 @@ def run_ours(args, rank, world, local):
             if timed:
                 flush_ev.append((f0, f1))
             compute.wait_event(copied[b])
-            gg = step(depth=d_in[b], color=c_in[b], frame=f_in[b])
+            gg = step(depth=d_in[b], color=c_in[b], frame=f_in[b], while_solving=nxt)
             released[b].record()
             h_x[:gg.m].copy_(x[:gg.m], non_blocking=True)
             h_stats.copy_(stats, non_blocking=True)
