@@ -17,6 +17,8 @@ Multi-GPU: every rank solves its own frame (independent problems, weak
 scaling, no collective on the data path).
 """
 import argparse
+import contextlib
+import gc
 import json
 import os
 import statistics
@@ -33,6 +35,20 @@ sys.path.insert(0, ROOT)
 METRIC = "ED Gauss-Newton iters/s @640x480, 2048 nodes; fraction of HBM roofline"
 WORKLOAD = "tissue_640x480_n2048"
 
+
+
+@contextlib.contextmanager
+def gc_paused():
+    """A timed region runs with Python's garbage collector off (collected just
+    before), as timeit does: the host loop issues work between its waits for
+    the GPU, and a collection pass of a few milliseconds there would show up as
+    GPU idle time in a region of some tens of milliseconds."""
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -318,15 +334,16 @@ def run_ours(args, rank, world, local):
     step_ms = []
     barrier()
     torch.cuda.synchronize()
-    for k in range(K):
-        flush.fill_(k & 0xff)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        step(record_gn=True)
-        ev1.record()
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
+    with gc_paused():
+        for k in range(K):
+            flush.fill_(k & 0xff)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            step(record_gn=True)
+            ev1.record()
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
     torch.cuda.synchronize()
     barrier()
     launches = E.launch_count() - l0
@@ -392,12 +409,13 @@ def run_ours(args, rank, world, local):
     ev1 = torch.cuda.Event(enable_timing=True)
     e2e_clocks = ClockSampler(local)
     e2e_clocks.start()
-    t_host = time.perf_counter()
-    ev0.record()
-    e2e_run(K, timed=True)
-    ev1.record()
-    ev1.synchronize()
-    e2e_wall_ms = (time.perf_counter() - t_host) * 1e3
+    with gc_paused():
+        t_host = time.perf_counter()
+        ev0.record()
+        e2e_run(K, timed=True)
+        ev1.record()
+        ev1.synchronize()
+        e2e_wall_ms = (time.perf_counter() - t_host) * 1e3
     e2e_clk = e2e_clocks.stop()
     flush_ms = sum(a.elapsed_time(b) for a, b in flush_ev)
     e2e_s = max_over_ranks((ev0.elapsed_time(ev1) - flush_ms) / 1e3, dist, dev)
@@ -520,15 +538,16 @@ def run_batch(args, rank, world, local):
         sequential()
     torch.cuda.synchronize()
     seq_ms = []
-    for k in range(K):
-        reset()
-        flush.fill_(k & 0xff)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        sequential()
-        e1.record()
-        e1.synchronize()
-        seq_ms.append(e0.elapsed_time(e1))
+    with gc_paused():
+        for k in range(K):
+            reset()
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sequential()
+            e1.record()
+            e1.synchronize()
+            seq_ms.append(e0.elapsed_time(e1))
     seq_x = [x.cpu().numpy() for x in xs]
     reset()
     for p, x, q in zip(probs, xs, poses):
@@ -554,16 +573,17 @@ def run_batch(args, rank, world, local):
     clocks.start()
     l0 = E.launch_count()
     bat_ms = []
-    for k in range(K):
-        reset()
-        flush.fill_(k & 0xff)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        B.stream.wait_stream(torch.cuda.current_stream())   # reset and flush done before the clock starts
-        e0.record(B.stream)
-        B.launch(stream=B.stream)
-        e1.record(B.stream)
-        e1.synchronize()
-        bat_ms.append(e0.elapsed_time(e1))
+    with gc_paused():
+        for k in range(K):
+            reset()
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            B.stream.wait_stream(torch.cuda.current_stream())   # reset and flush done before the clock starts
+            e0.record(B.stream)
+            B.launch(stream=B.stream)
+            e1.record(B.stream)
+            e1.synchronize()
+            bat_ms.append(e0.elapsed_time(e1))
     launches = E.launch_count() - l0
     clk = clocks.stop()
     torch.cuda.synchronize()
@@ -656,19 +676,20 @@ def run_sequence(args, rank, world, local):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    for k in range(W0, W0 + K):
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        depth.copy_(h_depth[k], non_blocking=True)
-        color.copy_(h_color[k], non_blocking=True)
-        infos.append(T.process(depth, color, k + 1, truth_depth=truth[k]))
-        ev1.record()
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-    torch.cuda.synchronize()
-    wall_s = time.perf_counter() - t_wall
+    with gc_paused():
+        t_wall = time.perf_counter()
+        for k in range(W0, W0 + K):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            depth.copy_(h_depth[k], non_blocking=True)
+            color.copy_(h_color[k], non_blocking=True)
+            infos.append(T.process(depth, color, k + 1, truth_depth=truth[k]))
+            ev1.record()
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t_wall
     if dist is not None:
         dist.barrier()
     launches = E.launch_count() - l0
