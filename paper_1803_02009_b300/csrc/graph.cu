@@ -232,7 +232,7 @@ __device__ __forceinline__ void poisson_phase(const float4 *__restrict__ pos, co
             }
         }
         first = false;
-        // the group's verdict: every one of its five lanes found no close node
+        // the group's vote: every one of its five lanes found no close node
         const unsigned bad = __ballot_sync(0xffffffffu, act && !ok);
         const unsigned gmask = 0x1fu << (5 * grp);
         if (act && sub == 0 && !(bad & gmask)) atomicMin(&cell_pick[c], i);
