@@ -846,10 +846,13 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_phase_scatter<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pstart, pfill, bucket); ed_note_launch();
         ED_LAUNCH_CHECK();
         // one cooperative launch for the 27 phases: one CTA per SM (fewer
-        // barrier arrivals), sized down for small inputs
+        // barrier arrivals), sized down for small inputs.  A phase's points are
+        // spread over all warps (six per warp and round); the grid is sized for
+        // 1.5x the mean points per phase, since phases hold up to ~10% more than
+        // the mean and one sized for the mean takes two rounds on those phases
         static int per_sm = -1;   // resident sampler CTAs per SM (the same for every call)
         if (per_sm < 0) ED_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_poisson_all, POISSON_T, 0));
-        int pick_grid = min(ed_div_up((N / 27 + 1) * 32 / 6 + 32, POISSON_T), min(per_sm, 1) * ctx->num_sms);
+        int pick_grid = min(ed_div_up((N / 18 + 1) * 32 / 6 + 32, POISSON_T), min(per_sm, 1) * ctx->num_sms);
         if (pick_grid < 1) pick_grid = 1;
         {   // the arrival counter was cleared with the misc words above
             const int *misc_c = ctx->misc, *pstart_c = pstart;
