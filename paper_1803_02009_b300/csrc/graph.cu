@@ -196,11 +196,20 @@ __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const in
 // phases; the winning bids of earlier phases are read from L2 (they were
 // written by atomics of other CTAs during this launch).
 __device__ __forceinline__ void poisson_phase(const float4 *__restrict__ pos, const int2 *__restrict__ bucket, int e0,
-                                              int e1, int nx, int ny, int nz, float r2, int *cell_pick,
+                                              int e1, int ph, int nx, int ny, int nz, float r2, int *cell_pick,
                                               int2 first_bc, float4 first_p)
 {
     const int lane = threadIdx.x & 31, grp = lane / 5, sub = lane % 5;
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    // phase residues of the neighbours at offsets -2..2 (this phase's cells
+    // have residues px, py, pz): only cells of earlier phases can hold a node
+    const int px = ph % 3, py = (ph / 3) % 3, pz = ph / 9;
+    int rx[5], ry[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        rx[d] = (px + d + 1) % 3;
+        ry[d] = 3 * ((py + d + 1) % 3);
+    }
     bool first = true;
     for (int wbase = e0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 6; wbase < e1; wbase += warps * 6) {
         const int e = wbase + grp;
@@ -214,13 +223,16 @@ __device__ __forceinline__ void poisson_phase(const float4 *__restrict__ pos, co
             c = bc.y;
             const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
             const int dz = sub - 2, az = cz + dz;
+            const int rz = 9 * ((pz + sub + 1) % 3);
             if (az >= 0 && az < nz) {
                 const float4 p = first ? first_p : pos[i];
                 int q[25];
 #pragma unroll
                 for (int k = 0; k < 25; ++k) {
                     const int ay = cy + k / 5 - 2, ax = cx + k % 5 - 2;
-                    const bool in = ay >= 0 && ay < ny && ax >= 0 && ax < nx && !(dz == 0 && k == 12);
+                    // (a cell of this phase or a later one holds no node yet: not read)
+                    const bool in = ay >= 0 && ay < ny && ax >= 0 && ax < nx && !(dz == 0 && k == 12) &&
+                                    rx[k % 5] + ry[k / 5] + rz < ph;
                     q[k] = in ? __ldcg(cell_pick + ax + nx * (ay + ny * az)) : NO_BID;   // earlier phases: final
                 }
 #pragma unroll
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restr
     float4 p;
     poisson_prefetch(pos, bucket, start[0], start[1], bc, p);
     for (int ph = 0; ph < 27; ++ph) {
-        poisson_phase(pos, bucket, start[ph], start[ph + 1], nx, ny, nz, r2, cell_pick, bc, p);
+        poisson_phase(pos, bucket, start[ph], start[ph + 1], ph, nx, ny, nz, r2, cell_pick, bc, p);
         if (ph < 26) {
             poisson_prefetch(pos, bucket, start[ph + 1], start[ph + 2], bc, p);
             if (!ed_grid_sync(bar, status, gridDim.x, target, &s_flag)) return;
