@@ -917,10 +917,13 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                 cudaMemcpyDeviceToHost, st));
     ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
 
-    // ---- node graph first (it needs only the nodes: the GPU runs it while the
-    // search-grid launches are queued), then nearest nodes and weights ----
+    // ---- node graph on the context's second stream (it needs only the nodes;
+    // only the block pattern reads it), beside the nearest nodes and weights ----
     const int *m_dev = graph->counts;
-    k_node_graph<<<ed_div_up(max_nodes, NG_WARPS), 32 * NG_WARPS, 0, st>>>(G4, m_dev, prm->k_graph, graph->nbr); ed_note_launch();
+    ED_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+    ED_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    k_node_graph<<<ed_div_up(max_nodes, NG_WARPS), 32 * NG_WARPS, 0, ctx->aux>>>(G4, m_dev, prm->k_graph, graph->nbr); ed_note_launch();
+    ED_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
     {
         const int kcells = hm[MI_KDIMS + 3];
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
@@ -937,6 +940,8 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
+    // every later launch on the caller's stream (and every return) follows the node graph
+    ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
     memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
     if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
