@@ -453,6 +453,8 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between steps (512 MB write)",
                    "step": "normals + build_graph + 10 x gn_step + warp + fuse"},
         "gn_only_iters_per_s": gn_rate,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms),
+                    "note": "this rank's timed steps one by one (CUDA events)"},
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "GN iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
