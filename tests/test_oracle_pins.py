@@ -457,6 +457,70 @@ def test_fuse_identity_same_frame():
     assert np.allclose(no[:, :3], nrm[:, :3], atol=1e-7)
 
 
+def _fuse_unequal_case():
+    """Four model points registered to a fronto-parallel depth map D = 60 mm
+    (16x12 pixels, f = 16, principal point (8, 6), every target normal
+    (0, 0, -1)) with warped depths different from D, unequal weights and one
+    tilted normal.  The values below were worked out by hand from Eqs.
+    fusion1-4 (Sec. II.G) with observation weight 1, the registered point
+    moved along its own ray, omega_max = 20 (Sec. III.B)."""
+    W, H, f = 16, 12, 16.0
+    intr = (f, f, 8.0, 6.0, W, H)
+    depth = np.full((H, W), 60.0, np.float32)
+    nm = np.zeros((H, W, 4), np.float32)
+    nm[..., 2] = -1.0
+    nm[..., 3] = 1.0
+    color = np.zeros((H, W, 4), np.float32)
+    color[..., :] = (1.0, 0.0, 0.2, 1.0)
+    # warped positions (x, y, z~) and weights omega; pixels by P:
+    # A (0, 0, 62) -> (8, 6); B (7, 0, 56) -> (10, 6); C (-16, -12, 64) -> (4, 3);
+    # D (14.5, 10.875, 58) -> (12, 9)
+    wpos = np.array([[0.0, 0.0, 62.0, 3.0], [7.0, 0.0, 56.0, 1.0], [-16.0, -12.0, 64.0, 19.5],
+                     [14.5, 10.875, 58.0, 20.0]], np.float32)
+    wnrm = np.array([[0.6, 0.0, -0.8, 0.0], [0.0, 0.0, -1.0, 0.0], [0.0, 0.0, -1.0, 0.0],
+                     [0.0, 0.0, -1.0, 0.0]], np.float32)
+    col = np.tile(np.array([0.2, 0.4, 0.6, 1.0], np.float32), (4, 1))
+    t = np.zeros(4, np.int32)
+    # the tilted normal of A is 36.87 degrees off the target normal: a 60 degree gate lets it through
+    F = oracle.FuseParams(frame=7, delta_deg=60.0)
+    return dict(intr=intr, depth=depth, nm=nm, color=color, wpos=wpos, wnrm=wnrm, col=col, t=t, F=F)
+
+
+def test_fuse_unequal_depths_weights_and_normals():
+    c = _fuse_unequal_case()
+    po, no, co, to, reg = oracle.fuse(c["wpos"], c["wnrm"], c["col"], c["t"], c["wpos"], c["wnrm"], c["depth"],
+                                      c["nm"], c["color"], c["intr"], c["F"], 400)
+    W = 16
+    assert reg[6 * W + 8] == 0 and reg[6 * W + 10] == 1 and reg[3 * W + 4] == 2 and reg[9 * W + 12] == 3
+    assert po.shape[0] == 16 * 12                    # 4 fused + 188 lifted pixels
+    # Eq. fusion1: D' = (z~ omega + D) / (omega + 1), along the point's ray
+    #   A: (62*3 + 60)/4 = 61.5
+    #   B: (56*1 + 60)/2 = 58;  x' = 7 * 58/56 = 7.25
+    #   C: (64*19.5 + 60)/20.5 = 2616/41;  x' = -16 (2616/41)/64 = -654/41, y' = -12 (2616/41)/64 = -1962/164
+    #   D: (58*20 + 60)/21 = 1220/21;  x' = 14.5 (1220/21)/58 = 14.5 * 1220/1218, y' = 10.875 * 1220/1218
+    exp_pos = np.array([[0.0, 0.0, 61.5], [7.25, 0.0, 58.0],
+                        [-654.0 / 41.0, -1962.0 / 164.0, 2616.0 / 41.0],
+                        [14.5 * 1220.0 / 1218.0, 10.875 * 1220.0 / 1218.0, 1220.0 / 21.0]])
+    assert np.abs(po[:4, :3] - exp_pos).max() < 1e-5
+    # Eq. fusion4: omega' = min(omega + 1, 20): 3 -> 4, 1 -> 2, 19.5 -> 20, 20 -> 20
+    assert np.array_equal(po[:4, 3], np.array([4.0, 2.0, 20.0, 20.0], np.float32))
+    # Eq. fusion3: A's normal (3 (0.6, 0, -0.8) + (0, 0, -1)) / 4 = (0.45, 0, -0.85), renormalised:
+    # (1.8, 0, -3.4) / sqrt(14.8)
+    s148 = 14.8 ** 0.5
+    assert np.abs(no[0, :3] - np.array([1.8 / s148, 0.0, -3.4 / s148])).max() < 1e-6
+    assert np.abs(no[1:4, :3] - np.array([0.0, 0.0, -1.0])).max() < 1e-7
+    # stability flags omega' >= tau_weight = 3: all but B (omega' = 2)
+    assert np.array_equal(no[:4, 3], np.array([1.0, 0.0, 1.0, 1.0], np.float32))
+    # Eq. fusion2 (colour), A: ((0.2, 0.4, 0.6, 1) 3 + (1, 0, 0.2, 1)) / 4 = (0.4, 0.3, 0.5, 1)
+    assert np.abs(co[0] - np.array([0.4, 0.3, 0.5, 1.0])).max() < 1e-6
+    # C: (c 19.5 + (1, 0, 0.2, 1)) / 20.5: red (3.9 + 1) / 20.5 = 4.9 / 20.5
+    assert abs(co[2, 0] - 4.9 / 20.5) < 1e-6
+    assert np.array_equal(to[:4], np.full(4, 7))
+    # the first lifted pixel (0, 0): Pi(u, 60) = ((0 - 8) 60 / 16, (0 - 6) 60 / 16, 60), omega 1, frame 7
+    assert np.abs(po[4] - np.array([-30.0, -22.5, 60.0, 1.0])).max() < 1e-6
+    assert to[4] == 7 and np.array_equal(no[4], np.array([0.0, 0.0, -1.0, 0.0], np.float32))
+
+
 def test_fuse_zbuffer_lift_delete_conservation():
     rng = np.random.default_rng(0)
     depth, intr = X.exact_plane(16, 12, 16.0)
