@@ -62,7 +62,9 @@ def parse():
                          "as one batched, graph-captured GN iteration vs 16 sequential solves; push_sequence: "
                          "the frame loop (registration, fusion, downsampling, node regeneration) over a "
                          "synthetic 640x480 push sequence, one frame per step")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "mixed_fp64"],
+                    help="mixed: float-float PCG dot products; mixed_fp64: FP64 PCG dot products (both with "
+                         "compensated block reductions and FP64 master parameters)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--keypoints", type=int, default=0,
@@ -74,6 +76,7 @@ def parse():
                          "default: plain Gauss-Newton (lambda = 0)")
     ap.add_argument("--radius", type=float, default=0.0,
                     help="Poisson radius (mm); 0 = calibrate to the workload's node count")
+    ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)   # child process of the OpenMP CPU leg
     return ap.parse_args()
 
 
@@ -265,7 +268,11 @@ def run_ours(args, rank, world, local):
     color = torch.from_numpy(np.ascontiguousarray(s.tgt_color)).to(dev)
     nmap = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     frame = E.make_frame(depth, nmap, s.intr, color)
-    radius = args.radius if args.radius > 0 else E.calibrate_radius(ctx, pos, nrm, cfg.node_count)
+    # the grid-node workload (160x120, an 8x8 node grid) keeps its given nodes;
+    # the others sample Poisson nodes at the radius that yields the node count
+    nodes_t = torch.from_numpy(s.nodes).to(dev) if s.nodes is not None else None
+    radius = (0.0 if nodes_t is not None else
+              args.radius if args.radius > 0 else E.calibrate_radius(ctx, pos, nrm, cfg.node_count))
     wmode = E.ED_WEIGHT_EQ2 if args.weights == "eq2" else E.ED_WEIGHT_GAUSSIAN
     kp_keep = None
     if args.keypoints > 0:
@@ -273,7 +280,8 @@ def run_ours(args, rank, world, local):
         kp_keep = (torch.from_numpy(kp).to(dev), torch.from_numpy(kp_tgt).to(dev))
         ctx.set_keypoints(kp_keep[0], kp_keep[1], 10.0)
     prm = E.SolverParams(n_pcg=cfg.n_pcg, prior=tuple(float(v) for v in s.pose_prior),
-                         precision=E.ED_PRECISION_MIXED if args.precision == "mixed" else E.ED_PRECISION_FP32,
+                         precision={"fp32": E.ED_PRECISION_FP32, "mixed": E.ED_PRECISION_MIXED,
+                                    "mixed_fp64": E.ED_PRECISION_MIXED_FP64}[args.precision],
                          lm_accept=args.lm is not None)
     prm_c = prm.c()
     F = E.FuseParams(frame=1)
@@ -294,8 +302,11 @@ def run_ours(args, rank, world, local):
 
     def step(record_gn=False, depth=depth, color=color, frame=frame, while_solving=None):
         ctx.compute_normals(depth, s.intr, cfg.normal_half_width, out=nmap)
-        g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius, weight_mode=wmode,
-                            reuse=True)
+        if nodes_t is not None:
+            g = ctx.build_graph(pos, nrm, nodes=nodes_t, sigma=s.sigma, weight_mode=wmode, reuse=True)
+        else:
+            g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius,
+                                weight_mode=wmode, reuse=True)
         m = g.m
         ctx.reset_params(x[:m], pose, x_master=xm[:m], prior=s.pose_prior)
         if args.lm is not None:
@@ -423,6 +434,23 @@ def run_ours(args, rank, world, local):
     e2e_s = max_over_ranks((ev0.elapsed_time(ev1) - flush_ms) / 1e3, dist, dev)
     e2e_value = whole_job_rate(world, K, cfg.n_gn, e2e_s)
 
+    # per-kernel device time of a Gauss-Newton iteration (events recorded by
+    # the library around each launch of one kernel; two extra steps per
+    # kernel, outside the timed region)
+    kern_us = {}
+    for kid, name in ((E.ED_KERNEL_POINTS, "k_points"), (E.ED_KERNEL_ASSEMBLE, "k_assemble"),
+                      (E.ED_KERNEL_FINALIZE, "k_fin_totals"), (E.ED_KERNEL_PCG, "k_pcg")):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * cfg.n_gn)]
+        ctx.set_timing(kid, ev)
+        for k in range(2):
+            flush.fill_(k & 0xff)
+            step()
+        torch.cuda.synchronize()
+        n_r = ctx.timing_count()
+        ctx.set_timing(kid, [])
+        t = [ev[2 * i].elapsed_time(ev[2 * i + 1]) * 1e3 for i in range(n_r)]
+        kern_us[name] = statistics.median(t) if t else None
+
     peak, peak_kind = measured_peaks()
     n_upper = (g.nnzb + g.m) // 2          # symmetric pattern, every diagonal block present
     byt = pcg_bytes_per_launch(g.m, n_upper, cfg.n_pcg)
@@ -466,6 +494,8 @@ def run_ours(args, rank, world, local):
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": byt,
                      "avg_launch_us": avg_pcg_s * 1e6, "launches_timed": len(pcg_ms)},
+        "gn_kernels_us": dict(kern_us, note="median device time per launch (library events on the launching "
+                                             "stream, 2 extra steps outside the timed region)"),
         "gn_iteration_roofline": {"bound": "hbm", "algorithmic_bytes": gn_byt,
                                   "achieved": gn_byt * gn_rate / world / 1e9 if gn_rate else None,
                                   "peak": peak, "unit": "GB/s",
@@ -772,7 +802,11 @@ def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1, lm=None):
     mode = 1 if weights == "eq2" else 0
     t0 = time.perf_counter()
     nm = oracle.normals(s.tgt_depth, s.intr, cfg.normal_half_width)
-    G = oracle.build_graph(s.model_pos, radius=radius, max_nodes=cfg.node_count, K=4, KG=4, mode=mode, sigma=radius)
+    if s.nodes is not None:   # the grid-node workload
+        G = oracle.build_graph(s.model_pos, nodes=s.nodes, K=4, KG=4, mode=mode, sigma=s.sigma)
+    else:
+        G = oracle.build_graph(s.model_pos, radius=radius, max_nodes=cfg.node_count, K=4, KG=4, mode=mode,
+                               sigma=radius)
     K = None
     if keypoints > 0:
         kp, kp_tgt, _ = synth.make_keypoints(s, keypoints, seed=seed)
@@ -788,17 +822,65 @@ def oracle_frame(s, radius, keypoints=0, weights="gaussian", seed=1, lm=None):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(s, budget_s, keypoints=0, weights="gaussian", lm=None):
+def oracle_frames(s, budget_s, max_frames, keypoints=0, weights="gaussian", lm=None):
+    """Whole frames of the workload in the oracle (as many as fit the budget,
+    at least one, at most max_frames); GN iters/s from the median frame."""
     import oracle
-    radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
+    radius = None if s.nodes is not None else oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     times = []
     t_start = time.perf_counter()
-    while not times or (time.perf_counter() - t_start < budget_s and len(times) < 3):
+    while not times or (time.perf_counter() - t_start < budget_s and len(times) < max_frames):
         times.append(oracle_frame(s, radius, keypoints, weights, lm=lm))
-    tot = sum(times)
-    return {"value": len(times) * s.cfg.n_gn / tot, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} whole frame(s) of the same workload (normals, graph, {s.cfg.n_gn} GN x "
-                      f"{s.cfg.n_pcg} PCG, warp, fuse) in the single-threaded FP64 oracle, {tot:.1f} s"}
+    return times
+
+
+def cpu_baseline(s, budget_s, keypoints=0, weights="gaussian", lm=None, config=WORKLOAD):
+    """The oracle as it stands (single-threaded), and beside it the OpenMP
+    build of the same source over every host core (os.cpu_count()), each on
+    whole frames of the same workload, the figure from the median frame."""
+    times = oracle_frames(s, budget_s, 3, keypoints, weights, lm)
+    med = statistics.median(times)
+    out = {"value": s.cfg.n_gn / med, "unit": "GN iters/s", "cores": 1, "kind": "oracle",
+           "sample": f"{len(times)} whole frame(s) of the same workload (normals, graph, {s.cfg.n_gn} GN x "
+                     f"{s.cfg.n_pcg} PCG, warp, fuse) in the single-threaded FP64 oracle, median of "
+                     f"{len(times)} frames ({sum(times):.1f} s)"}
+    out["openmp"] = cpu_baseline_openmp(config, budget_s, keypoints, weights, lm)
+    return out
+
+
+def cpu_baseline_openmp(config, budget_s, keypoints, weights, lm):
+    """The OpenMP build of the oracle (liboracle_omp.so, chosen by the
+    library loader of a fresh process: a child that never touches CUDA) on
+    os.cpu_count() threads, median of up to 5 whole frames."""
+    cores = os.cpu_count() or 1
+    spec = json.dumps({"config": config, "budget_s": budget_s, "keypoints": keypoints, "weights": weights, "lm": lm})
+    env = dict(os.environ, ED_ORACLE_OPENMP="1", OMP_NUM_THREADS=str(cores), OMP_PROC_BIND="false",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", spec], env=env,
+                           capture_output=True, text=True, timeout=max(120.0, 6 * budget_s))
+        times = json.loads(r.stdout.strip().splitlines()[-1])["times"]
+    except Exception as e:   # reported, not fatal: the GPU figures stand without it
+        return {"value": None, "cores": cores, "kind": "oracle (OpenMP build)", "error": str(e)[:200]}
+    med = statistics.median(times)
+    s_cfg = _scene_cfg(config)
+    return {"value": s_cfg.n_gn / med, "unit": "GN iters/s", "cores": cores, "kind": "oracle (OpenMP build)",
+            "sample": f"{len(times)} whole frame(s) of the same workload in the OpenMP build of the FP64 oracle on "
+                      f"{cores} threads, median of {len(times)} frames ({sum(times):.1f} s)"}
+
+
+def _scene_cfg(config):
+    import synth
+    return synth.CONFIGS[config] if config in synth.CONFIGS else synth.make_scene(config, seed=1).cfg
+
+
+def oracle_leg_main(spec):
+    """--oracle-leg: whole oracle frames only (no GPU), times as JSON."""
+    import synth
+    d = json.loads(spec)
+    s = synth.make_scene(d["config"], seed=1)
+    times = oracle_frames(s, d["budget_s"], 5, d["keypoints"], d["weights"], d["lm"])
+    print(json.dumps({"times": times}))
 
 
 def run_reference_sequence(args, world):
@@ -838,7 +920,7 @@ def run_reference(args, rank, world):
     if args.workload == "push_sequence":
         return run_reference_sequence(args, world)
     s = synth.make_scene(args.config, seed=1)
-    radius = oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
+    radius = None if s.nodes is not None else oracle.calibrate_radius(s.model_pos, s.cfg.node_count)
     for _ in range(args.warmup):
         oracle_frame(s, radius, args.keypoints, args.weights, lm=args.lm)
     times = [oracle_frame(s, radius, args.keypoints, args.weights, lm=args.lm)
@@ -860,6 +942,9 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.oracle_leg is not None:
+        oracle_leg_main(args.oracle_leg)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
@@ -881,7 +966,8 @@ def main():
     out, s = run_ours(args, rank, world, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(s, args.cpu_budget_s, args.keypoints, args.weights, args.lm)
+            out["cpu_baseline"] = cpu_baseline(s, args.cpu_budget_s, args.keypoints, args.weights, args.lm,
+                                               config=args.config)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out))

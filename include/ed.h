@@ -62,7 +62,13 @@ typedef enum ed_status {
     ED_ERR_STATE = 7       /* call order: e.g. ed_gn_step before ed_build_graph */
 } ed_status;
 
-enum { ED_PRECISION_FP32 = 0, ED_PRECISION_MIXED = 1 };
+/* Arithmetic of a Gauss-Newton step.  FP32: residuals, assembly and PCG in
+ * FP32.  MIXED: FP32 residuals and assembly with two-sum compensated block
+ * reductions, PCG dot products and norms accumulated as float-float
+ * (about 44 significant bits, on the FP32 pipe), an FP64 master copy of the
+ * node parameters that accumulates the updates.  MIXED_FP64: the same with
+ * the PCG dot products and norms accumulated in FP64. */
+enum { ED_PRECISION_FP32 = 0, ED_PRECISION_MIXED = 1, ED_PRECISION_MIXED_FP64 = 2 };
 enum { ED_WEIGHT_GAUSSIAN = 0, ED_WEIGHT_EQ2 = 1 };
 
 /* Capacities a context is created for; they size the workspace. */
@@ -131,8 +137,9 @@ typedef struct ed_graph {
  *   skinning: the k nearest nodes of every point by the FP32 squared
  *   distance (ties to the lower node index), normalised weights (Eq. 1-2);
  *   node graph: the k_graph nearest other nodes of every node (alpha_jk = 1);
- *   and, internally, the block-sparsity pattern of J^T J and the per-block
- *   point lists used by ed_gn_step.
+ *   and, internally, the block-sparsity pattern of J^T J, the points sorted
+ *   by their set of four nodes and, per block, the runs of points that
+ *   contribute to it, used by ed_gn_step.
  * pos/nrm [N][4] are the model (they must stay valid until the next
  * ed_build_graph); the graph buffers are retained by the context likewise.
  * Synchronises the stream four times (it reads back the grid, node, block and
@@ -158,8 +165,11 @@ ed_status ed_build_graph(ed_context *ctx, const float *pos, const float *nrm, in
 ed_status ed_set_keypoints(ed_context *ctx, const float *kp_pos, const float *kp_target, int n_keypoints,
                            float w_corr);
 
-/* Host-side sizes of the graph built last (host out; NULL entries skipped). */
-ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_chunks);
+/* Host-side sizes of the graph built last (host out; NULL entries skipped):
+ * nodes m, stored 12x12 blocks nnzb (both triangles), the (block, point)
+ * pairs the assembly visits per step (10 per point) and the runs of points
+ * that share their four nearest nodes. */
+ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs);
 
 typedef struct ed_frame {
     const float *depth;    /* [H][W] target depth D (mm), 0 = hole */
@@ -176,7 +186,7 @@ typedef struct ed_solver_params {
     float pcg_tol;         /* early PCG stop when ||r|| <= tol ||b|| (0 = fixed count) */
     float lambda;          /* Levenberg-Marquardt damping: H + lambda diag(H) */
     float jitter;          /* preconditioner block shift, relative to trace/size */
-    int precision;         /* ED_PRECISION_FP32 or ED_PRECISION_MIXED */
+    int precision;         /* ED_PRECISION_FP32, ED_PRECISION_MIXED or ED_PRECISION_MIXED_FP64 */
     double prior[6];       /* pose prior for E_r, E_p (Sec. II.E "Global Pose") */
     int lm_accept;         /* 1: Levenberg-Marquardt acceptance on the device (ed_lm_reset);
                               lambda then comes from the context's damping state */
@@ -204,7 +214,7 @@ typedef struct ed_stats {
  * block-Jacobi preconditioned CG on (H + lambda diag H) d = -J^T r from d = 0,
  * and x += d, pose += d_pose.
  * x: [m][12] float, updated in place.  x_master: [m][12] double, required for
- * ED_PRECISION_MIXED (the master copy that accumulates the updates; x is
+ * the mixed precisions (the master copy that accumulates the updates; x is
  * rewritten from it), ignored otherwise.  pose: double[6], updated in place.
  * stats: device ed_stats (may be NULL).  When a device check fails the
  * update is skipped and stats->status says why.  With params->lm_accept the
@@ -258,6 +268,28 @@ ed_status ed_export_system(ed_context *ctx, int *row_ptr, int *col, float *block
                            float *pose_block, float *grad, float *delta, cudaStream_t stream);
 
 /*
+ * Limit of every bounded device-side wait in this context's launches (the
+ * grid barriers of the PCG solve and of the node sampler, the look-back of
+ * the library's scans, the waits for bulk copies into shared memory), in
+ * nanoseconds of the GPU's global timer; 0 restores the default of 2 s.
+ * Limits under 100 us are rejected (ED_ERR_ARG).  A wait that runs out sets
+ * ED_ERR_TIMEOUT in the device status word (ed_stats.status of the step) and
+ * the kernel returns; the PCG then leaves x and the pose unchanged.  Takes
+ * effect for launches enqueued after the call.  The paper has no counterpart:
+ * this is the bound that keeps a stalled launch from holding the GPU.
+ */
+ed_status ed_set_wait_limit(ed_context *ctx, unsigned long long limit_ns);
+
+/*
+ * Test hook for the bounded wait of the PCG grid barrier: the barrier of the
+ * following ed_gn_step calls expects extra_arrivals (0..1024) more arrivals
+ * than the launch has CTAs, so it can never complete and gives up after the
+ * wait limit, reporting ED_ERR_TIMEOUT; 0 (the default) restores normal
+ * operation.  The context stays usable.  The paper has no counterpart.
+ */
+ed_status ed_set_barrier_test(ed_context *ctx, int extra_arrivals);
+
+/*
  * Measurement hook: from now on, record events[2k] / events[2k+1] (caller-
  * created cudaEvent_t, host array) on the launching stream immediately before
  * and after the k-th launch of the selected kernel, for k < n_pairs; the count
@@ -267,12 +299,12 @@ ed_status ed_export_system(ed_context *ctx, int *row_ptr, int *col, float *block
  * n_pairs = 0 switches the hook off.  The paper has no counterpart: this is
  * instrumentation for roofline measurements.
  */
+enum { ED_KERNEL_PCG = 0, ED_KERNEL_POINTS = 1, ED_KERNEL_ASSEMBLE = 2, ED_KERNEL_FINALIZE = 3 };
+ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded);
+
 /* Kernel launches the library has issued in this process so far (host out).
  * Instrumentation; the paper has no counterpart. */
 ed_status ed_launch_count(unsigned long long *count);
-
-enum { ED_KERNEL_PCG = 0, ED_KERNEL_POINTS = 1, ED_KERNEL_ASSEMBLE = 2, ED_KERNEL_FINALIZE = 3 };
-ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded);
 
 /*
  * Eq. (1) warp of n points with the graph built last:
@@ -379,22 +411,26 @@ ed_status ed_energy_grad(ed_context *ctx, const ed_frame *frame, const ed_solver
 /*
  * The energy of ed_energy for callers that cannot allocate device memory
  * (host frameworks that own every device allocation and hand a plugin only
- * its buffers, code running during CUDA stream capture, real-time loops that
- * forbid allocation after start-up).  The paper has no counterpart: this is a
- * deployment variant of ed_energy's reduction.
+ * its buffers, real-time loops that forbid allocation after start-up).  The
+ * paper has no counterpart: this is a deployment variant of ed_energy's
+ * reduction.
  * It needs no context and no workspace: the caller passes the model (pos,
  * nrm [n][4]), its skinning (idx [n][4], weights [n][4]), the nodes [m][4],
  * the node graph nbr [m][k_graph], the frame, the parameters, x [m][12] and
  * the pose, and receives energy_out (device double[6]: total, data, rot, reg,
- * rot prior, pos prior), as from ed_energy.  The only scratch, the partial
+ * rot prior, pos prior).  The total is Eq. (3) without the key-correspondence
+ * term E_corr (this entry point takes no key points): it equals ed_energy's
+ * for a context with no key correspondences set.  The only scratch, the partial
  * sums of the reduction (133,120 bytes), is a fixed array in device global
  * memory inside the library, held by every GPU that loads it until the
  * process exits; no allocation routine is called.
  * Limits: n_points <= 2,097,152 and m <= 32,768; larger sizes return
  * ED_ERR_CAPACITY (with a message on stderr) before any launch.
  * The first call on a device looks up the device address of that array
- * (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture.  Every call writes every scratch slot it reads,
+ * (cudaGetSymbolAddress, with the device current) and keeps it for the rest
+ * of the process; make that first call before any stream capture.  A device
+ * reset (cudaDeviceReset) invalidates the kept address: do not call this
+ * entry point again in a process after resetting the device.  Every call writes every scratch slot it reads,
  * so stale contents never matter, but all calls share the one array: calls
  * that overlap on the GPU (different streams, or different host threads on
  * one device) race and must be serialised by the caller.

@@ -15,6 +15,7 @@ from __future__ import annotations
 import ctypes as C
 import dataclasses
 import math
+import os
 from typing import Optional
 
 import numpy as np
@@ -25,11 +26,21 @@ _lib = None
 
 
 def lib():
+    """The oracle library.  With ED_ORACLE_OPENMP=1 in the environment of the
+    process (set before the first call), the OpenMP build of the same source
+    is loaded instead: the multi-core timing baseline of the benchmark, not
+    the oracle of the tests."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        omp = os.environ.get("ED_ORACLE_OPENMP", "0") == "1"
+        _lib = C.CDLL(_build.build_openmp() if omp else _build.build())
         _declare(_lib)
     return _lib
+
+
+def variant():
+    """'openmp' or 'serial': which build lib() loads in this process."""
+    return "openmp" if os.environ.get("ED_ORACLE_OPENMP", "0") == "1" else "serial"
 
 
 _dp = C.POINTER(C.c_double)

@@ -35,16 +35,30 @@
  *   the pose is (alpha, beta, gamma, T), R = Rz(gamma) Ry(beta) Rx(alpha);
  *   the observation weight in the fusion equations is 1, the TSDW formula
  *   only acts as the |z - D| < tau gate; omega_max is a parameter (20).
+ *
+ * The oracle is this file compiled without OpenMP.  The same source compiled
+ * with -fopenmp (liboracle_omp.so) is only timed, as the multi-core CPU
+ * baseline: its per-point and per-node loops run in parallel (each iteration
+ * writes its own outputs), the sort of the block pattern runs as per-thread
+ * sorts and a merge (the same result), and the data term of the normal
+ * equations is summed per thread over contiguous point ranges, the thread
+ * sums then added in thread order (a fixed order, so the result is
+ * deterministic for a given thread count, and equal to the oracle's up to
+ * rounding).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_ERR_ARG 1
 #define OR_ERR_CAPACITY 3
 #define OR_ERR_BREAKDOWN 5
+#define OR_MAXK 64   /* largest K of the nearest-node searches */
 
 /* ------------------------------------------------------------------------- */
 /* FP32 decision rules (bit-exact)                                            */
@@ -122,6 +136,7 @@ void or_associate_f32(const float *wpos, const float *wnrm, int N, const float *
                       float eps_d, float cos_eps_n, int *pix)
 {
     float eps2 = eps_d * eps_d;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; ++i) {
         const float *p = wpos + 4 * (size_t)i;
         const float *n = wnrm + 4 * (size_t)i;
@@ -162,6 +177,7 @@ void or_associate_f32(const float *wpos, const float *wnrm, int N, const float *
 void or_normals(const float *depth, int W, int H, double fx, double fy, double cx, double cy,
                 int h, float *nmap)
 {
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < H; ++v)
         for (int u = 0; u < W; ++u) {
             float *o = nmap + 4 * ((size_t)v * W + u);
@@ -335,9 +351,12 @@ void or_knn(const float *pos, int N, const int *sel, int nsel, const float *g, i
             float *key)
 {
     int cnt = sel ? nsel : N;
-    float *kk = (float *)malloc(sizeof(float) * (size_t)K);
-    int *ii = (int *)malloc(sizeof(int) * (size_t)K);
+    if (K < 1 || K > OR_MAXK)
+        return;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int t = 0; t < cnt; ++t) {
+        float kk[OR_MAXK];
+        int ii[OR_MAXK];
         int i = sel ? sel[t] : t;
         const float *p = pos + 4 * (size_t)i;
         int len = 0;
@@ -348,16 +367,17 @@ void or_knn(const float *pos, int N, const int *sel, int nsel, const float *g, i
             key[(size_t)t * K + s] = s < len ? kk[s] : INFINITY;
         }
     }
-    free(kk);
-    free(ii);
 }
 
 /* N(j): the KG nearest other nodes (FP32 key, ties to the lower index) */
 void or_node_graph(const float *g, int m, int KG, int *nbr)
 {
-    float *kk = (float *)malloc(sizeof(float) * (size_t)KG);
-    int *ii = (int *)malloc(sizeof(int) * (size_t)KG);
+    if (KG < 1 || KG > OR_MAXK)
+        return;
+#pragma omp parallel for schedule(dynamic, 16)
     for (int j = 0; j < m; ++j) {
+        float kk[OR_MAXK];
+        int ii[OR_MAXK];
         int len = 0;
         for (int l = 0; l < m; ++l) {
             if (l == j)
@@ -368,8 +388,6 @@ void or_node_graph(const float *g, int m, int KG, int *nbr)
         for (int s = 0; s < KG; ++s)
             nbr[(size_t)j * KG + s] = s < len ? ii[s] : -1;
     }
-    free(kk);
-    free(ii);
 }
 
 /*
@@ -382,6 +400,7 @@ void or_skin_weights(const float *pos, int N, const float *g, const int *idx, in
                      double sigma, double *w)
 {
     int stride = K + 1;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; ++i) {
         const float *p = pos + 4 * (size_t)i;
         double d[64];
@@ -492,6 +511,7 @@ void or_warp(const or_problem *P, const double *x, const double *pose, double *w
 {
     double R[9];
     or_rotation(pose, R, NULL);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < P->N; ++i) {
         const double *v = P->pos + 4 * (size_t)i, *n = P->nrm + 4 * (size_t)i;
         double s[3] = {0, 0, 0}, sn[3] = {0, 0, 0};
@@ -543,6 +563,7 @@ static void associate_from_f64(const or_problem *P, const double *wpos, const do
 {
     float *fp = (float *)malloc(sizeof(float) * 4 * (size_t)(P->N > 0 ? P->N : 1));
     float *fn = (float *)malloc(sizeof(float) * 4 * (size_t)(P->N > 0 ? P->N : 1));
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < P->N; ++i)
         for (int r = 0; r < 4; ++r) {
             fp[4 * (size_t)i + r] = r < 3 ? (float)wpos[3 * (size_t)i + r] : 0.0f;
@@ -626,17 +647,53 @@ static int cmp_pair(const void *a, const void *b)
     return x < y ? -1 : x > y;
 }
 
+#ifdef _OPENMP
+/* the same ascending order as qsort: per-thread sorts of contiguous chunks,
+   then rounds of pairwise merges (OpenMP build only) */
+static void sort_pairs_parallel(int64_t *a, size_t n)
+{
+    int T = omp_get_max_threads();
+    if (T < 2 || n < 65536) {
+        qsort(a, n, sizeof(int64_t), cmp_pair);
+        return;
+    }
+    size_t *cut = (size_t *)malloc(sizeof(size_t) * (size_t)(T + 1));
+    for (int t = 0; t <= T; ++t) cut[t] = n * (size_t)t / (size_t)T;
+#pragma omp parallel for schedule(static, 1)
+    for (int t = 0; t < T; ++t) qsort(a + cut[t], cut[t + 1] - cut[t], sizeof(int64_t), cmp_pair);
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * n);
+    int64_t *src = a, *dst = tmp;
+    for (int w = 1; w < T; w *= 2) {
+#pragma omp parallel for schedule(static, 1)
+        for (int t = 0; t < T; t += 2 * w) {
+            size_t lo = cut[t], mid = cut[t + w < T ? t + w : T], hi = cut[t + 2 * w < T ? t + 2 * w : T];
+            size_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) dst[k++] = src[j] < src[i] ? src[j++] : src[i++];
+            while (i < mid) dst[k++] = src[i++];
+            while (j < hi) dst[k++] = src[j++];
+        }
+        int64_t *x = src; src = dst; dst = x;
+    }
+    if (src != a) memcpy(a, src, sizeof(int64_t) * n);
+    free(tmp);
+    free(cut);
+}
+#endif
+
 /* sparsity pattern: node pairs sharing a point, node-graph edges, diagonal */
 static void pattern_build(const or_problem *P, or_normal_eq *Q)
 {
     int m = P->m, K = P->K;
     size_t cap = (size_t)(P->N + P->NK) * K * K + (size_t)m * (2 * P->KG + 1);
     int64_t *pr = (int64_t *)malloc(sizeof(int64_t) * (cap > 0 ? cap : 1));
-    size_t n = 0;
+    const size_t KK = (size_t)K * K;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < P->N; ++i)
         for (int a = 0; a < K; ++a)
             for (int b = 0; b < K; ++b)
-                pr[n++] = (int64_t)P->idx[(size_t)i * K + a] * m + P->idx[(size_t)i * K + b];
+                pr[(size_t)i * KK + (size_t)a * K + b] =
+                    (int64_t)P->idx[(size_t)i * K + a] * m + P->idx[(size_t)i * K + b];
+    size_t n = (size_t)P->N * KK;
     for (int i = 0; i < P->NK; ++i)
         for (int a = 0; a < K; ++a)
             for (int b = 0; b < K; ++b)
@@ -650,7 +707,11 @@ static void pattern_build(const or_problem *P, or_normal_eq *Q)
             pr[n++] = (int64_t)k * m + j;
         }
     }
+#ifdef _OPENMP
+    sort_pairs_parallel(pr, n);
+#else
     qsort(pr, n, sizeof(int64_t), cmp_pair);
+#endif
     size_t u = 0;
     for (size_t t = 0; t < n; ++t)
         if (u == 0 || pr[t] != pr[u - 1])
@@ -749,6 +810,63 @@ static void add_plane_residual(or_normal_eq *Q, const or_problem *P, const doubl
     }
 }
 
+#ifdef _OPENMP
+/* the data term of the OpenMP build: thread t sums the points of its
+   contiguous range into its own normal equations (same pattern), then the
+   thread sums are added to Q in thread order */
+static void data_term_parallel(or_normal_eq *Q, const or_problem *P, const double *R, const double *dR,
+                               const int *pix, const double *wpos, const double *spre)
+{
+    const int T = omp_get_max_threads(), N = P->N, K = P->K, m = Q->m;
+    const size_t nblk = (size_t)Q->nnzb * 144, nC = (size_t)m * 72, ng = (size_t)12 * m + 6;
+    or_normal_eq *S = (or_normal_eq *)calloc((size_t)T, sizeof(or_normal_eq));
+    for (int t = 0; t < T; ++t) {
+        S[t].m = m;
+        S[t].nnzb = Q->nnzb;
+        S[t].row_ptr = Q->row_ptr;
+        S[t].col = Q->col;
+        S[t].blk = (double *)calloc(nblk + 1, sizeof(double));
+        S[t].C = (double *)calloc(nC + 1, sizeof(double));
+        S[t].g = (double *)calloc(ng, sizeof(double));
+    }
+#pragma omp parallel num_threads(T)
+    {
+        const int t = omp_get_thread_num();
+        const int i0 = (int)((long)N * t / T), i1 = (int)((long)N * (t + 1) / T);
+        or_normal_eq *St = S + t;
+        for (int i = i0; i < i1; ++i) {
+            if (pix[i] < 0) continue;
+            double nt[3];
+            double sw = sqrt(P->w_data);
+            double r = sw * data_residual(P, pix[i], wpos + 3 * (size_t)i, nt);
+            St->E[0] += r * r;
+            St->n_valid++;
+            add_plane_residual(St, P, R, dR, r, sw, nt, P->pos + 4 * (size_t)i, P->idx + (size_t)i * K,
+                               P->w + (size_t)i * K, spre + 3 * (size_t)i);
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < (long)nblk; ++e) {
+        double v = Q->blk[e];
+        for (int t = 0; t < T; ++t) v += S[t].blk[e];
+        Q->blk[e] = v;
+    }
+    for (size_t e = 0; e < nC; ++e)
+        for (int t = 0; t < T; ++t) Q->C[e] += S[t].C[e];
+    for (size_t e = 0; e < ng; ++e)
+        for (int t = 0; t < T; ++t) Q->g[e] += S[t].g[e];
+    for (int t = 0; t < T; ++t) {
+        for (int e = 0; e < 36; ++e) Q->Hpp[e] += S[t].Hpp[e];
+        Q->E[0] += S[t].E[0];
+        Q->n_valid += S[t].n_valid;
+        free(S[t].blk);
+        free(S[t].C);
+        free(S[t].g);
+    }
+    free(S);
+}
+#endif
+
 /*
  * Linearise Eq. (3) at (x, pose): association (or the frozen pix[] when
  * pix_in != NULL), residuals, energy terms, H = J^T J and g = J^T r with every
@@ -776,6 +894,9 @@ int or_linearize(const or_problem *P, const double *x, const double *pose, const
     double *gpose = Q->g + 12 * (size_t)m;
 
     /* data term */
+#ifdef _OPENMP
+    data_term_parallel(Q, P, R, dR, pix, wpos, spre);
+#else
     for (int i = 0; i < N; ++i) {
         if (pix[i] < 0) continue;
         double nt[3];
@@ -786,6 +907,7 @@ int or_linearize(const or_problem *P, const double *x, const double *pose, const
         add_plane_residual(Q, P, R, dR, r, sw, nt, P->pos + 4 * (size_t)i, P->idx + (size_t)i * K,
                            P->w + (size_t)i * K, spre + 3 * (size_t)i);
     }
+#endif
 
     /* E_corr: the three components of sqrt(w_corr) (v~_k - V_k) of every key
        point, each the residual of the plane through V_k normal to a camera axis */
@@ -1086,6 +1208,7 @@ static void spmv(const or_normal_eq *Q, const double *p, double *q)
     const double *pp = p + 12 * (size_t)m;
     double *qp = q + 12 * (size_t)m;
     for (int t = 0; t < 6; ++t) qp[t] = 0.0;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < m; ++j) {
         double *qj = q + 12 * (size_t)j;
         for (int r = 0; r < 12; ++r) qj[r] = 0.0;
@@ -1098,6 +1221,9 @@ static void spmv(const or_normal_eq *Q, const double *p, double *q)
         const double *C = Q->C + 72 * (size_t)j;
         for (int r = 0; r < 12; ++r)
             for (int t = 0; t < 6; ++t) qj[r] += C[12 * t + r] * pp[t];
+    }
+    for (int j = 0; j < m; ++j) {   /* the pose rows: sum over the nodes in order */
+        const double *C = Q->C + 72 * (size_t)j;
         for (int t = 0; t < 6; ++t)
             for (int r = 0; r < 12; ++r) qp[t] += C[12 * t + r] * p[12 * (size_t)j + r];
     }

@@ -19,7 +19,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libed.so")
 
-ED_PRECISION_FP32, ED_PRECISION_MIXED = 0, 1
+ED_PRECISION_FP32, ED_PRECISION_MIXED, ED_PRECISION_MIXED_FP64 = 0, 1, 2
 ED_WEIGHT_GAUSSIAN, ED_WEIGHT_EQ2 = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "capacity exceeded", 4: "non-finite value",
           5: "PCG breakdown", 6: "device wait timed out", 7: "invalid call order"}
@@ -113,6 +113,8 @@ _SIGS = {
     "ed_energy_grad": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, C.c_float, _vp, _vp, _vp],
     "ed_set_timing": [_vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)],
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
+    "ed_set_wait_limit": [_vp, C.c_ulonglong],
+    "ed_set_barrier_test": [_vp, C.c_int],
     "ed_set_keypoints": [_vp, _vp, _vp, C.c_int, C.c_float],
     "ed_lm_reset": [_vp, C.c_float, _vp],
     "ed_reset_params": [_vp, _vp, _vp, _vp, C.POINTER(C.c_double * 6), _vp],
@@ -323,7 +325,7 @@ class Context:
         m, nnzb, ne, nc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check("ed_graph_info", lib().ed_graph_info(self.h, C.byref(m), C.byref(nnzb), C.byref(ne), C.byref(nc)))
         g.m, g.nnzb = m.value, nnzb.value
-        self.n_entries, self.n_chunks = ne.value, nc.value
+        self.n_entries, self.n_runs = ne.value, nc.value
         self.graph = g
         self._keep = [pos, nrm]          # the context reads them until the next build
         return g
@@ -354,6 +356,16 @@ class Context:
         """Starts a Levenberg-Marquardt solve: damping lambda0, no accepted
         point (steps with SolverParams.lm_accept use this device state)."""
         _check("ed_lm_reset", lib().ed_lm_reset(self.h, float(lambda0), _stream(stream)))
+
+    def set_wait_limit(self, limit_ns=0):
+        """Limit of every bounded device wait of this context's launches (ns;
+        0 = the default 2 s)."""
+        _check("ed_set_wait_limit", lib().ed_set_wait_limit(self.h, int(limit_ns)))
+
+    def set_barrier_test(self, extra_arrivals=0):
+        """Test hook: the PCG grid barrier expects this many arrivals more than
+        it has CTAs (it then gives up after the wait limit); 0 = normal."""
+        _check("ed_set_barrier_test", lib().ed_set_barrier_test(self.h, int(extra_arrivals)))
 
     def set_debug(self, wpos=None, wnrm=None, pix=None):
         _check("ed_set_debug", lib().ed_set_debug(self.h, _ptr(wpos), _ptr(wnrm), _ptr(pix)))

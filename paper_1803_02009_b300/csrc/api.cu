@@ -39,7 +39,6 @@ size_t carve(ed_context *c, char *base)
     const size_t nnzb = M * (size_t)L.max_pairs_per_node;
     const size_t nent = 10 * N;
     const size_t tiles = (nent + 1023) / 1024 + 1;
-    const size_t chunks = (10 * N) / ED_CHUNK + (4 * N) / ED_CHUNK1 + nnzb + M + 64;
     const size_t P = 12 * M + 6;
     const size_t big = (N > WH ? N : WH);
     size_t scan_len = big > 256 * tiles ? big : 256 * tiles;
@@ -71,21 +70,32 @@ size_t carve(ed_context *c, char *base)
     c->ent_key2 = k.take<uint32_t>(nent);
     c->ent_val2 = k.take<uint32_t>(nent);
     c->radix_cnt = k.take<int>(256 * tiles + 1);
-    c->ent_cnt = k.take<int>(nnzb);
+    c->inc = k.take<uint32_t>(nent);
     c->ent_start = k.take<int>(nnzb + 1);
-    c->chunk_cnt = k.take<int>(nnzb);
-    c->chunk_start = k.take<int>(nnzb + 1);
-    c->chunks = k.take<int4>(chunks);
-    c->chunk_cnt1 = k.take<int>(nnzb);
-    c->chunk_start1 = k.take<int>(nnzb + 1);
-    c->max_chunks = (int)chunks;
-    c->ent_geo = k.take<float4>(nent);
-    c->partials = k.take<float>((size_t)ED_PART_STRIDE * chunks);
+    c->perm = k.take<int>(N);
+    c->spos = k.take<float4>(N);
+    c->snrm = k.take<float4>(N);
+    c->sidx = k.take<ushort4>(N);
+    c->sw = k.take<float4>(N);
+    c->sidx_d = k.take<ushort4>(N);
+    c->sw_d = k.take<float4>(N);
+    c->run_start = k.take<int>(N + 1);
+    c->run_of_start = k.take<int>(N);
+    c->bcnt = k.take<int>(2 * (M + 1));
+    c->bstart = k.take<int>(M + 1);
+    c->icnt = k.take<int>(2 * (nnzb + 1));
+    c->crec0 = k.take<float4>(N);
+    c->crec1 = k.take<float4>(N);
+    c->cpos = k.take<float4>(N);
+    c->csw = k.take<float4>(N);
+    c->vrun_start = k.take<int>(N + 1);
+    c->pose_R = k.take<float>(16);
     c->bsr = k.take<float>(nnzb * 144);
     c->grad = k.take<float>(P);
     c->pnode = k.take<float>(M * 72);
     c->minv = k.take<float>(M * 144);
     c->pose_blk = k.take<float>(72);
+    c->dmom = k.take<float>(M * 72);
     c->bsr_s = k.take<float>(nnzb * 144);
     c->grad_s = k.take<float>(P);
     c->pnode_s = k.take<float>(M * 72);
@@ -99,6 +109,7 @@ size_t carve(ed_context *c, char *base)
     c->pix = k.take<int>(N);
     c->max_k1_ctas = (int)((N + ED_K1_THREADS - 1) / ED_K1_THREADS) + 1;
     c->k1_part = k.take<float2>((size_t)c->max_k1_ctas * ED_K1_PART);
+    c->vcount = k.take<int>((size_t)c->max_k1_ctas);
     c->vec_stride = (P + 63) / 64 * 64;
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
@@ -161,10 +172,13 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
     }
     c->ws = (char *)workspace;
     c->ws_bytes = workspace_bytes;
+    c->wait_ns = ED_BAR_TIMEOUT_NS;
+    c->bar_extra = 0;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
         cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess ||
         cudaMemset(c->dmisc, 0, sizeof(double) * 64) != cudaSuccess ||
+        cudaMemset(c->pcg_part, 0, sizeof(double) * 2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART) != cudaSuccess ||
         cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_state_len) != cudaSuccess ||
         cudaMemset(c->scan_ticket, 0, sizeof(unsigned)) != cudaSuccess) {
         cudaFreeHost(c->row_ptr_host);
@@ -248,6 +262,22 @@ extern "C" ed_status ed_set_keypoints(ed_context *ctx, const float *kp_pos, cons
     return ED_OK;
 }
 
+extern "C" ed_status ed_set_wait_limit(ed_context *ctx, unsigned long long limit_ns)
+{
+    if (!ctx) return ED_ERR_ARG;
+    if (limit_ns == 0) limit_ns = ED_BAR_TIMEOUT_NS;
+    if (limit_ns < ED_MIN_WAIT_NS) return ED_ERR_ARG;
+    ctx->wait_ns = limit_ns;
+    return ED_OK;
+}
+
+extern "C" ed_status ed_set_barrier_test(ed_context *ctx, int extra_arrivals)
+{
+    if (!ctx || extra_arrivals < 0 || extra_arrivals > 1024) return ED_ERR_ARG;
+    ctx->bar_extra = extra_arrivals;
+    return ED_OK;
+}
+
 extern "C" ed_status ed_launch_count(unsigned long long *count)
 {
     if (!count) return ED_ERR_ARG;
@@ -267,14 +297,14 @@ extern "C" ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *
     return ED_OK;
 }
 
-extern "C" ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_chunks)
+extern "C" ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs)
 {
     if (!ctx) return ED_ERR_ARG;
     if (!ctx->have_graph) return ED_ERR_STATE;
     if (m) *m = ctx->m;
     if (nnzb) *nnzb = ctx->nnzb;
     if (n_entries) *n_entries = ctx->n_entries;
-    if (n_chunks) *n_chunks = ctx->n_chunks;
+    if (n_runs) *n_runs = ctx->n_runs;
     return ED_OK;
 }
 
@@ -284,7 +314,7 @@ extern "C" ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int
 // order CTAs start, so a tile only waits for tiles that are already running.
 // Every tile publishes its aggregate, then its inclusive prefix, as one 64-bit
 // word tagged with the scan's epoch (words of older scans never match); the
-// wait for a predecessor gives up after ED_BAR_TIMEOUT_NS (ED_ERR_TIMEOUT).
+// wait for a predecessor gives up after the context's wait limit (ED_ERR_TIMEOUT).
 // ---------------------------------------------------------------------------
 
 #define DS_T 256
@@ -308,7 +338,7 @@ __device__ __forceinline__ void ds_store(unsigned long long *p, unsigned epoch, 
 
 __global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int n, unsigned long long *state,
                                                    unsigned *ticket, unsigned ticket_base, unsigned epoch,
-                                                   int *status)
+                                                   int *status, unsigned long long wait_ns)
 {
     __shared__ int s_tile, s_excl, s_warp[DS_T / 32];
     if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ticket, 1u) - ticket_base);
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int 
                 const unsigned long long w = ds_load(state + p);
                 const unsigned hi = (unsigned)(w >> 32), fl = hi & 3u;
                 if ((hi >> 2) != epoch || fl == 0u) {
-                    if ((++spins & 63u) == 0 && ed_gtimer() - t0 > ED_BAR_TIMEOUT_NS) {
+                    if ((++spins & 63u) == 0 && ed_gtimer() - t0 > wait_ns) {
                         atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
                         break;
                     }
@@ -408,7 +438,7 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
         ctx->scan_epoch = epoch = 1;
     }
     k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
-                                       ctx->misc + MI_STATUS); ed_note_launch();
+                                       ctx->misc + MI_STATUS, ctx->wait_ns); ed_note_launch();
     ctx->scan_ticket_base += (unsigned)tiles;
     ED_LAUNCH_CHECK();
     return ED_OK;

@@ -98,9 +98,8 @@ static ed_status batch_enqueue(ed_batch *b, const ed_frame *frames, const ed_sol
                                double *const *xm, double *const *pose, ed_stats *const *stats, int it, cudaStream_t st)
 {
     const int count = b->count, W = b->sched.streams;
-    const int mixed = params[0].precision == ED_PRECISION_MIXED;
     for (int p = 0; p < count; ++p)
-        if ((params[p].precision == ED_PRECISION_MIXED) != mixed) return ED_ERR_ARG;
+        if (params[p].precision != params[0].precision) return ED_ERR_ARG;
     ed_status first = ED_OK;
     auto fork = [&]() -> ed_status {
         ED_CUDA_TRY(cudaEventRecord(b->ev_fork, st));

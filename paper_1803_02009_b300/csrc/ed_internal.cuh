@@ -13,9 +13,6 @@
 #define ED_K 4                 // nearest nodes per point (Eq. 1)
 #define ED_MAX_KG 8            // node-graph neighbours
 #define ED_HARD_MAX_NODES 16384
-#define ED_CHUNK 128           // role-0 assembly entries per chunk (4 per lane of a warp)
-#define ED_CHUNK1 1024         // role-1 (J^T r, pose-node) assembly entries per chunk (rounds of 128)
-#define ED_PART_STRIDE 96      // floats per chunk partial (60 moments, or 12 + 72), chunk-major
 #define ED_K1_THREADS 256
 #define ED_K1_PART 32          // components of a point-kernel CTA partial (30 used)
 #define ED_PCG_PART 16         // doubles per PCG CTA partial (at most)
@@ -57,6 +54,12 @@ enum {
 };
 enum { MF_CELL = 0, MF_INV = 1, MF_KCELL = 2, MF_KINV = 3, MF_R2 = 4, MF_VOX = 5, MF_BBOX = 8, MF_COUNT = 16 };
 // (MF_VOX .. MF_VOX + 2: the origin of the ed_downsample box grid)
+
+// the mixed precisions (compensated reductions, FP64 master parameters)
+static inline bool ed_is_mixed(int precision)
+{
+    return precision == ED_PRECISION_MIXED || precision == ED_PRECISION_MIXED_FP64;
+}
 
 // ordered-int image of a float (monotone for signed comparison)
 __device__ __forceinline__ int f2o(float f)
@@ -111,32 +114,39 @@ struct ed_context {
     int *tpos;               // [max_nnzb] position of the transposed block
     int *diag_pos;           // [max_nodes]
     int *up_list;            // [max_nnzb] upper block positions
-    int4 *fin_info;          // [n_upper][2] packed finalisation records (per frame, k_fin_pack)
+    int4 *fin_info;          // [n_upper][2] packed assembly records (per frame, k_fin_pack)
     int max_nnzb;
-    // assembly lists
-    uint32_t *ent_key;       // [10 N] block id, then sorted
-    uint32_t *ent_val;       // [10 N] point << 4 | s << 2 | t, then sorted
+    // the points in node-tuple order and the (block, run) incidences
+    uint32_t *ent_key;       // [10 N] sort keys: tuple keys of the points, then the block of every incidence
+    uint32_t *ent_val;       // [10 N] values: point indices of the tuple sort (and scratch of other sorts)
     uint32_t *ent_key2;      // radix temp
     uint32_t *ent_val2;
     int *radix_cnt;          // [256 * tiles + 1]
-    int *ent_cnt;            // [max_nnzb]
-    int *ent_start;          // [max_nnzb + 1]
-    int *chunk_cnt;          // [max_nnzb]
-    int *chunk_start;        // [max_nnzb + 1]
-    int4 *chunks;            // [max_chunks] (block, begin, count, role); role-0 chunks first
-    int *chunk_cnt1;         // [max_nnzb] role-1 chunks of every diagonal block
-    int *chunk_start1;       // [max_nnzb + 1]
-    int max_chunks;
-    int n_chunks0;           // role-0 chunks
-    int chunk_base1;         // first role-1 chunk (n_chunks0 rounded up to 32: warp-aligned slots)
-    float4 *ent_geo;         // [10 N] per sorted entry: (v_i - g_j, w_s w_t)
-    float *partials;         // [ED_PART_STRIDE][max_chunks]
+    uint32_t *inc;           // [10 N] incidences run << 4 | s << 2 | t sorted by block (kept for the frame)
+    int *ent_start;          // [max_nnzb + 1] first incidence of every block
+    int *perm;               // [N] point at each sorted position
+    float4 *spos, *snrm;     // [N] positions and normals in sorted order
+    ushort4 *sidx;           // [N] the tuple (nodes in increasing index order) at each sorted position
+    float4 *sw;              // [N] skinning weights in tuple order
+    ushort4 *sidx_d;         // [N] the nearest nodes in the graph's order (nearest first) at each sorted position
+    float4 *sw_d;            // [N] their weights: the warp of a step sums in the order ed_warp and ed_energy do
+    int *run_start;          // [N + 1] first sorted position of every run
+    int *run_of_start;       // [N] r where sorted position k starts run r, else -1
+    int *bcnt;               // [2 (max_nodes + 1)] bucket counts and fill counters of the tuple grouping
+    int *bstart;             // [max_nodes + 1] bucket starts
+    int *icnt;               // [2 (max_nnzb + 1)] incidence counts and fill counters per block
+    // a step's valid rows, compacted in sorted order (k_compact)
+    float4 *crec0, *crec1, *cpos, *csw;   // [N] records, position, tuple weights
+    int *vrun_start;         // [N + 1] first compacted row of every run
+    int *vcount;             // [max_k1_ctas] valid rows of every point-pass chunk
+    float *pose_R;           // [16] R of the step's pose (from the point pass)
     // normal equations
     float *bsr;              // [max_nnzb][144]
     float *grad;             // [12 m + 6] J^T r
     float *pnode;            // [m][72] pose-node blocks
     float *minv;             // [m][144] block-Jacobi inverses
     float *pose_blk;         // [36] pose block, [36..72) its inverse
+    float *dmom;             // [m][72] moments (60) and J^T r (12) of the diagonal blocks, per step
     // Levenberg-Marquardt: the undamped system and the parameters of the last
     // accepted point (restored when a step raises the energy)
     float *bsr_s;            // [max_nnzb][144]
@@ -147,8 +157,8 @@ struct ed_context {
     double *xm_prev;         // [m][12]
     double *pose_prev;       // [6]
     float2 *node_energy;     // [m] (rot, reg) of every node
-    float4 *rec0;            // [N] (R^T n(u), r)
-    float4 *rec1;            // [N] (d r / d angles, 0)
+    float4 *rec0;            // [N] (sqrt(w) R^T n(u), r), sorted order in a Gauss-Newton step
+    float4 *rec1;            // [N] (d r / d angles, 0), likewise
     int *pix;                // [N] association of the last evaluation
     float2 *k1_part;         // [ED_K1_PART][max_k1_ctas] float-float partials, component-major
     int max_k1_ctas;
@@ -189,8 +199,8 @@ struct ed_context {
     int m;
     int nnzb;
     int n_upper;
-    int n_entries;
-    int n_chunks;
+    int n_entries;           // (block, point) pairs the assembly visits: 10 per point
+    int n_runs;              // runs of equal node tuples
     int have_system;
     int have_energy;
     ed_pcg_plan_t pcg;       // single-problem PCG launch (one 512-thread CTA per SM)
@@ -208,6 +218,11 @@ struct ed_context {
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
+
+    // bounded device waits: limit (ed_set_wait_limit) and the extra arrivals
+    // the PCG grid barrier expects (ed_set_barrier_test; 0 outside tests)
+    unsigned long long wait_ns;
+    int bar_extra;
 
     // measurement hook (ed_set_timing)
     int tm_kernel;
@@ -408,7 +423,8 @@ static inline cudaError_t ed_launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 
 // grid barrier of a cooperative (co-resident) launch, with a bounded wait
 // ---------------------------------------------------------------------------
 
-#define ED_BAR_TIMEOUT_NS 2000000000ull
+#define ED_BAR_TIMEOUT_NS 2000000000ull   // default limit of a device wait (ed_set_wait_limit)
+#define ED_MIN_WAIT_NS 100000ull          // shortest limit ed_set_wait_limit accepts (100 us)
 
 __device__ __forceinline__ unsigned long long ed_gtimer()
 {
@@ -446,7 +462,8 @@ __device__ __forceinline__ void ed_red_add_release(unsigned *p, unsigned v)
 // other CTAs' writes are visible after its acquire load of the count (later
 // reads of shared data bypass L1); returns false when the context status is
 // set (an error elsewhere, or this wait timed out)
-__device__ __forceinline__ bool ed_grid_sync(unsigned *count, int *status, unsigned nblocks, unsigned &target, int *s_flag)
+__device__ __forceinline__ bool ed_grid_sync(unsigned *count, int *status, unsigned nblocks, unsigned &target, int *s_flag,
+                                             unsigned long long limit_ns = ED_BAR_TIMEOUT_NS)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -460,7 +477,7 @@ __device__ __forceinline__ bool ed_grid_sync(unsigned *count, int *status, unsig
         while (ed_ld_acquire(count) < goal) {
             if ((++spins & 63u) == 0) {
                 if (*(volatile int *)status != ED_OK) { ok = 0; break; }
-                if (ed_gtimer() - t0 > ED_BAR_TIMEOUT_NS) {
+                if (ed_gtimer() - t0 > limit_ns) {
                     atomicCAS(status, ED_OK, ED_ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -513,13 +530,14 @@ __device__ __forceinline__ bool ed_mbar_test(unsigned long long *bar, unsigned p
 }
 
 // bounded wait for phase `parity` of an mbarrier (all threads may call it);
-// false when ED_BAR_TIMEOUT_NS passed (the caller records the error and then
-// waits once more for its copies before leaving)
-__device__ __forceinline__ bool ed_mbar_wait(unsigned long long *bar, unsigned parity)
+// false when limit_ns passed (the caller records the error and then waits
+// once more for its copies before leaving)
+__device__ __forceinline__ bool ed_mbar_wait(unsigned long long *bar, unsigned parity,
+                                             unsigned long long limit_ns = ED_BAR_TIMEOUT_NS)
 {
     const unsigned long long t0 = ed_gtimer();
     while (!ed_mbar_test(bar, parity))
-        if (ed_gtimer() - t0 > ED_BAR_TIMEOUT_NS) return false;
+        if (ed_gtimer() - t0 > limit_ns) return false;
     return true;
 }
 

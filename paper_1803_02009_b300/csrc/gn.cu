@@ -24,11 +24,17 @@ struct PointArgs {
     int n_model;       // rows >= n_model: key points, three rows each (E_corr)
     const float4 *kp_tgt;
     float sw_corr;
-    int *pix;          // association (written in STEP / ENERGY, read in GRAD)
+    const int *perm;   // STEP: the arrays above are in node-tuple order, position k holds point perm[k]
+                       // (records at k; association, debug outputs and key-point rows by point index)
+    int *pix;          // association (written in ENERGY, read in GRAD)
     int *status_reset; // the step's device status word, cleared by the first thread (STEP), or NULL
     float4 *rec0, *rec1;
     float2 *part;      // [ED_K1_PART][pstride] float-float partials, component-major
     int pstride;
+    int chunk;         // > 0: CTA c takes the contiguous positions [c chunk, (c + 1) chunk) (STEP);
+                       // 0: a grid-stride loop
+    int *vcount;       // STEP: valid rows of every CTA's chunk (for the compaction), or NULL
+    float *pose_R;     // STEP: R of the step's pose (9 floats, written by CTA 0), or NULL
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
 };
@@ -44,17 +50,26 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
     // kernel's end reads it, and no thread of this kernel writes it otherwise
     if (a.status_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.status_reset = ED_OK;
     __shared__ ed_pose_f P;
-    __shared__ float red[ED_K1_THREADS / 32][31];
-    if (threadIdx.x == 0) ed_pose_eval(a.pose, P);
+    __shared__ float red[ED_K1_THREADS / 32][32];
+    if (threadIdx.x == 0) {
+        ed_pose_eval(a.pose, P);
+        if (a.pose_R && blockIdx.x == 0)
+            for (int q = 0; q < 9; ++q) a.pose_R[q] = P.R[q];
+    }
     __syncthreads();
-    // 0 E_data, 1 count, 2..22 pose block, 23..28 pose gradient, 29 non-finite, 30 E_corr
-    float acc[31];
+    // 0 E_data, 1 count, 2..22 pose block, 23..28 pose gradient, 29 non-finite, 30 E_corr,
+    // 31 valid rows (model and key-point rows: the compaction's count)
+    float acc[32];
 #pragma unroll
-    for (int k = 0; k < 31; ++k) acc[k] = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const float4 p = a.pos[i], nr = a.nrm[i];
-        const ushort4 id = a.idx[i];
-        const float4 wi = a.recompute_w ? ed_gauss_weights(p, id, a.g, a.m, a.sigma) : a.w[i];
+    for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+    const int k_first = a.chunk ? blockIdx.x * a.chunk + threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
+    const int k_end = a.chunk ? min(a.n, (int)(blockIdx.x + 1) * a.chunk) : a.n;
+    const int k_step = a.chunk ? blockDim.x : gridDim.x * blockDim.x;
+    for (int k = k_first; k < k_end; k += k_step) {
+        const int i = a.perm ? __ldg(a.perm + k) : k;
+        const float4 p = a.pos[k], nr = a.nrm[k];
+        const ushort4 id = a.idx[k];
+        const float4 wi = a.recompute_w ? ed_gauss_weights(p, id, a.g, a.m, a.sigma) : a.w[k];
         const ed_warped W = ed_warp_point(p, nr, id, wi, a.g, a.x4, P.R, P.T);
         const bool kp = i >= a.n_model;
         // the plane of the residual: target point G and normal tn (the pixel's
@@ -68,7 +83,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
             if (a.mode == PASS_GRAD) q = a.pix[i];
             else {
                 q = ed_associate(W, a.depth, a.nmap, a.K, a.eps2, a.cos_eps_n);
-                a.pix[i] = q;
+                if (a.mode == PASS_ENERGY) a.pix[i] = q;
                 if (a.dbg_pix) {
                     a.dbg_pix[i] = q;
                     reinterpret_cast<float4 *>(a.dbg_wpos)[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
@@ -123,21 +138,22 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
                 acc[0] += r * r;
                 acc[1] += 1.0f;
             }
-            int k = 2;
+            acc[31] += 1.0f;
+            int ka = 2;
 #pragma unroll
             for (int t = 0; t < 6; ++t)
 #pragma unroll
-                for (int s = t; s < 6; ++s) acc[k++] += jp[t] * jp[s];
+                for (int s = t; s < 6; ++s) acc[ka++] += jp[t] * jp[s];
 #pragma unroll
             for (int t = 0; t < 6; ++t) acc[23 + t] += r * jp[t];
             if (!isfinite(r)) acc[29] += 1.0f;
         }
         if (a.mode != PASS_ENERGY) {
-            a.rec0[i] = r0;
-            a.rec1[i] = r1;
+            a.rec0[k] = r0;
+            a.rec1[k] = r1;
         }
     }
-    // block reduction: for each half of the 31 sums a butterfly over the warp
+    // block reduction: for each half of the 32 sums a butterfly over the warp
     // that halves the values a lane carries at every shuffle step (lane bit o
     // keeps the upper or the lower half and receives that half from its
     // partner), so lanes 2k and 2k + 1 end with the half's value k (float);
@@ -147,7 +163,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
     for (int hf = 0; hf < 2; ++hf) {
         float x[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) x[k] = 16 * hf + k < 31 ? acc[16 * hf + k] : 0.f;
+        for (int k = 0; k < 16; ++k) x[k] = acc[16 * hf + k];
 #pragma unroll
         for (int lvl = 0; lvl < 4; ++lvl) {
             const int o = 16 >> lvl, n = 8 >> lvl;
@@ -161,15 +177,91 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
         }
         const float v = x[0] + __shfl_xor_sync(0xffffffffu, x[0], 1);
         const int k = 16 * hf + (lane >> 1);
-        if (!(lane & 1) && k < 31) red[wid][k] = v;
+        if (!(lane & 1)) red[wid][k] = v;
     }
     __syncthreads();
     if (threadIdx.x < 31) {
         float2 s = make_float2(0.f, 0.f);
         for (int w = 0; w < ED_K1_THREADS / 32; ++w) s = ed_ff_add1(s, red[w][threadIdx.x]);
         a.part[(size_t)threadIdx.x * a.pstride + blockIdx.x] = s;
+    } else if (threadIdx.x == 31 && a.vcount) {
+        float c = 0.f;   // (integers below 2^24: exact)
+        for (int w = 0; w < ED_K1_THREADS / 32; ++w) c += red[w][31];
+        a.vcount[blockIdx.x] = (int)c;
     }
 }
+
+// stable compaction of the valid rows of a step's point records (sorted
+// order kept): CTA c takes the chunk the point pass's CTA c took, its first
+// output position the valid rows of the chunks before it (from the point
+// pass's counts, summed by warp 0: no look-back); also the first compacted
+// position of every run (vrun_start) and, from the last CTA, the total
+#define CP_CHUNK 512
+__global__ void __launch_bounds__(256) k_compact(const int *__restrict__ vcount, int nchunks, int n,
+                                                 const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                 const float4 *__restrict__ spos, const float4 *__restrict__ sw,
+                                                 const int *__restrict__ run_of_start, int n_runs,
+                                                 float4 *__restrict__ crec0, float4 *__restrict__ crec1,
+                                                 float4 *__restrict__ cpos, float4 *__restrict__ csw,
+                                                 int *__restrict__ vrun_start)
+{
+    __shared__ int s_base, s_total, s_warp[8];
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    const int c = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        int pre = 0, tot = 0;
+        for (int i = lane; i < nchunks; i += 32) {
+            const int v = __ldcg(vcount + i);
+            tot += v;
+            if (i < c) pre += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pre += __shfl_xor_sync(0xffffffffu, pre, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (lane == 0) {
+            s_base = pre;
+            s_total = tot;
+        }
+    }
+    __syncthreads();
+    int base = s_base;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int e = 0; e < CP_CHUNK / 256; ++e) {
+        const int k = c * CP_CHUNK + e * 256 + threadIdx.x;
+        const bool in = k < n;
+        const bool v = in && __ldcg(rec1 + k).w != 0.f;   // (w = 1 on valid rows, 0 otherwise)
+        const unsigned bal = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) s_warp[wid] = __popc(bal);
+        __syncthreads();
+        int wpre = 0, btot = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int t = s_warp[q];
+            if (q < wid) wpre += t;
+            btot += t;
+        }
+        const int excl = base + wpre + __popc(bal & lt);
+        if (in) {
+            if (v) {
+                crec0[excl] = __ldcg(rec0 + k);
+                crec1[excl] = __ldcg(rec1 + k);
+                cpos[excl] = __ldg(spos + k);
+                csw[excl] = __ldg(sw + k);
+            }
+            const int r = __ldg(run_of_start + k);
+            if (r >= 0) vrun_start[r] = excl;
+        }
+        base += btot;
+        __syncthreads();   // (s_warp is rewritten by the next round)
+    }
+    if (c == nchunks - 1 && threadIdx.x == 0) vrun_start[n_runs] = s_total;
+}
+
+// CTAs of a step's point pass: one per contiguous chunk of CP_CHUNK positions
+static int k1_grid_step(const ed_context *ctx) { return ed_div_up(ctx->N > 0 ? ctx->N : 1, CP_CHUNK); }
 
 static int k1_grid(const ed_context *ctx)
 {
@@ -184,12 +276,16 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
                         const double *pose, int mode, cudaStream_t st)
 {
     PointArgs a;
-    a.pos = (const float4 *)ctx->pos;
-    a.nrm = (const float4 *)ctx->nrm;
-    a.w = (const float4 *)ctx->graph.weights;
+    const bool step = mode == PASS_STEP;
+    // a Gauss-Newton step runs over the points in node-tuple order (its
+    // records feed the assembly); the energy and gradient over the model order
+    a.pos = step ? ctx->spos : (const float4 *)ctx->pos;
+    a.nrm = step ? ctx->snrm : (const float4 *)ctx->nrm;
+    a.w = step ? ctx->sw_d : (const float4 *)ctx->graph.weights;
+    a.perm = step ? ctx->perm : nullptr;
     a.g = (const float4 *)ctx->graph.nodes;
     a.x4 = (const float4 *)x;
-    a.idx = (const ushort4 *)ctx->graph.idx;
+    a.idx = step ? ctx->sidx_d : (const ushort4 *)ctx->graph.idx;
     a.pose = pose;
     a.depth = fr->depth;
     a.nmap = (const float4 *)fr->nmap;
@@ -216,20 +312,40 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.dbg_wpos = ctx->dbg_wpos;
     a.dbg_wnrm = ctx->dbg_wnrm;
     a.dbg_pix = (mode == PASS_STEP && ctx->dbg_wpos && ctx->dbg_wnrm) ? ctx->dbg_pix : nullptr;
+    a.chunk = step ? CP_CHUNK : 0;
+    a.vcount = step ? ctx->vcount : nullptr;
+    a.pose_R = step ? ctx->pose_R : nullptr;
+    const int grid = step ? k1_grid_step(ctx) : k1_grid(ctx);
     if (mode == PASS_STEP) ed_tm_begin(ctx, ED_KERNEL_POINTS, st);
-    ED_CUDA_TRY(ed_launch_pdl(k_points, dim3(k1_grid(ctx)), dim3(ED_K1_THREADS), 0, st, a)); ed_note_launch();
+    ED_CUDA_TRY(ed_launch_pdl(k_points, dim3(grid), dim3(ED_K1_THREADS), 0, st, a)); ed_note_launch();
+    if (step) {   // the valid rows compacted for the assembly
+        ED_CUDA_TRY(ed_launch_pdl(k_compact, dim3(grid), dim3(256), 0, st, (const int *)ctx->vcount, grid, ctx->N,
+                                  (const float4 *)ctx->rec0, (const float4 *)ctx->rec1, (const float4 *)ctx->spos,
+                                  (const float4 *)ctx->sw, (const int *)ctx->run_of_start, ctx->n_runs, ctx->crec0,
+                                  ctx->crec1, ctx->cpos, ctx->csw, ctx->vrun_start)); ed_note_launch();
+    }
     if (mode == PASS_STEP) ed_tm_end(ctx, ED_KERNEL_POINTS, st);
     ED_LAUNCH_CHECK();
     return ED_OK;
 }
 
 // ---------------------------------------------------------------------------
-// assembly: one warp per chunk of <= ED_CHUNK entries of one upper block (j, l)
-// role 0: the 60 independent entries of sum c (nb nb^T) (x) (d^ d^T),
-//         d^ = [v - g_j; 1], c = w_s w_t  (every data-term block of J^T J)
-// role 1 (diagonal blocks): J^T r (12) and the pose-node block (6 x 12)
-// The per-entry geometry (d, c) was written at graph build; the residual
-// record of the point is gathered (entries of a chunk are in point order).
+// assembly of the normal equations, one upper block (j, l), j <= l, at a time
+// (Sec. II.E-F): the data term's Jacobian row of a point i with respect to
+// node j is w_ij n~_i^T (x) d^_ij^T, n~ = sqrt(w) R^T n(u), d^ = [v_i - g_j; 1]
+// (Eq. 1 with the nodes' 3x4 parameters [A_j | t_j]), so
+//   block (j, l) of J^T J = sum_i w_ij w_il (n~ n~^T) (x) (d^_ij d^_il^T),
+// 60 independent moments sum c (n~ n~^T)_a (d^_ij d^_ij^T)_q (d^_il is a shift
+// of d^_ij); the diagonal blocks add J^T r (12) and the pose-node block
+// (6 x 12).  The points are sorted by their set of four nodes; a block's
+// points are the runs of the tuples that hold both of its nodes (its
+// incidences).  A warp streams them, one point per lane and round, the lanes
+// of a round taking consecutive points of the concatenated runs, accumulates
+// in registers, sums over the warp by recursive halving (fixed order:
+// deterministic; two-sum compensated in mixed precision) and finalises the
+// block in the same kernel: E_rot and E_reg terms, the transposed copy, and
+// for a diagonal block the gradient, the node energies and the block-Jacobi
+// inverse.
 // ---------------------------------------------------------------------------
 
 // Recursive halving of NV float2 values per lane across the warp (fixed order,
@@ -256,205 +372,236 @@ __device__ __forceinline__ void warp_halving2(float2 (&v)[NV])
     }
 }
 
-static_assert(ED_CHUNK == 128 && ED_CHUNK1 % 128 == 0, "the assembly kernels take 4 entries per lane (and round)");
+// error-free sum a + b = s + e (Knuth's two-sum)
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
 
-// Recursive halving of 16 float2 values per lane down to one per lane pair,
-// then the pair: afterwards lanes 2k and 2k + 1 both hold the full sum of
-// slot k (fixed order: deterministic).
-__device__ __forceinline__ void warp_halving2_16(float2 (&v)[16])
+// the same halving with every addition error-free (two-sum) and the errors
+// carried along: the compensated block reduction of the mixed-precision form.
+// Lane k ends with value + error of slot k (NV = 32).
+template <int NV>
+__device__ __forceinline__ void warp_halving2_ff(float2 (&v)[NV])
 {
     const int lane = threadIdx.x & 31;
+    float2 err[NV];
 #pragma unroll
-    for (int o = 16, n = 16; o > 1; o >>= 1, n >>= 1) {
+    for (int k = 0; k < NV; ++k) err[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int o = 16, n = NV; o > 0; o >>= 1, n >>= 1) {
         const bool hi = (lane & o) != 0;
 #pragma unroll
         for (int k = 0; k < n / 2; ++k) {
-            const float2 keep = hi ? v[k + n / 2] : v[k];
-            const float2 give = hi ? v[k] : v[k + n / 2];
-            float2 recv;
+            const float2 keep = hi ? v[k + n / 2] : v[k], keep_e = hi ? err[k + n / 2] : err[k];
+            const float2 give = hi ? v[k] : v[k + n / 2], give_e = hi ? err[k] : err[k + n / 2];
+            float2 recv, recv_e;
             recv.x = __shfl_xor_sync(0xffffffffu, give.x, o);
             recv.y = __shfl_xor_sync(0xffffffffu, give.y, o);
-            v[k] = __fadd2_rn(keep, recv);
+            recv_e.x = __shfl_xor_sync(0xffffffffu, give_e.x, o);
+            recv_e.y = __shfl_xor_sync(0xffffffffu, give_e.y, o);
+            float ex, ey;
+            v[k].x = two_sum(keep.x, recv.x, ex);
+            v[k].y = two_sum(keep.y, recv.y, ey);
+            err[k].x = __fadd_rn(__fadd_rn(keep_e.x, recv_e.x), ex);
+            err[k].y = __fadd_rn(__fadd_rn(keep_e.y, recv_e.y), ey);
         }
     }
-    float2 recv;
-    recv.x = __shfl_xor_sync(0xffffffffu, v[0].x, 1);
-    recv.y = __shfl_xor_sync(0xffffffffu, v[0].y, 1);
-    v[0] = __fadd2_rn(v[0], recv);
+    v[0].x = __fadd_rn(v[0].x, err[0].x);
+    v[0].y = __fadd_rn(v[0].y, err[0].y);
 }
 
-// role 0: two warps per chunk of <= 128 entries of one upper block (j, l).
-// Lane k takes entries k, k + 32, k + 64, k + 96; warp half h forms the 30
-// moments c nn_a (d^ d^T)_q of a = 3h .. 3h + 2 (nn = the 6 products of
-// n~ = sqrt(w) R^T n, d^ = [v - g_j; 1], paired FP32 FMA), the warp then sums
-// them by recursive halving; half h writes moment pairs 15h .. 15h + 14.
-__global__ void __launch_bounds__(128) k_assemble0(const int4 *__restrict__ chunks, int nchunks, int max_chunks,
-                                                   const float4 *__restrict__ geo, const uint32_t *__restrict__ ent,
-                                                   const float4 *__restrict__ rec0, float *__restrict__ part)
+__device__ __forceinline__ float pick4(float v0, float v1, float v2, float v3, int i)
+{
+    return i == 0 ? v0 : (i == 1 ? v1 : (i == 2 ? v2 : v3));
+}
+__device__ __forceinline__ float pick4(float4 v, int i) { return pick4(v.x, v.y, v.z, v.w, i); }
+
+// The points of the incidences [i0, i0 + n) of one block, two consecutive
+// points per lane and round (64 per round): lane L of round R takes points
+// 64 R + 2 L and 64 R + 2 L + 1 of the concatenated runs (run r covers
+// [run_start[r], run_start[r + 1]); runs may be empty).  Rounds R with
+// R % stride != phase are left to other warps.  f(k0, s0, k1, s1) gets the
+// two positions (-1 past the end) and their slot codes s << 2 | t of the
+// block's row and column nodes in the tuple (the two points may lie in two
+// runs).  Warp-uniform control flow.
+template <typename F>
+__device__ __forceinline__ void block_points(const uint32_t *__restrict__ inc, const int *__restrict__ run_start,
+                                             int i0, int n, int phase, int stride, F &&f)
 {
     const int lane = threadIdx.x & 31;
-    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int c = wg >> 1, h = wg & 1;
-    if (c >= nchunks) return;
-    // the chunk, its geometry and its entries are fixed for the frame: loaded
-    // before the wait for the point pass (whose residual records come after)
-    const int4 ch = chunks[c];
-    float4 gd[4], b[4];
-    int pt[4];
+    int round = 0;
+    for (int ib = 0; ib < n; ib += 32) {
+        int st = 0, len = 0, sl = 0;
+        if (ib + lane < n) {
+            const uint32_t v = __ldg(inc + i0 + ib + lane);   // fixed for the frame
+            const int r = (int)(v >> 4);
+            st = __ldcg(run_start + r);   // (the compacted starts change every step)
+            len = __ldcg(run_start + r + 1) - st;
+            sl = (int)(v & 15u);
+        }
+        int incl = len;   // inclusive scan of the run lengths over the lanes
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int e = lane + 32 * q;
-        gd[q] = e < ch.z ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);   // w = 0: no contribution
-        pt[q] = e < ch.z ? (int)(__ldg(ent + ch.y + e) >> 4) : -1;
-    }
-    ed_pdl_wait();
-    ed_pdl_trigger();
-    // (the point pass may still have been writing the records while this kernel
-    // was alive: coherent loads, not the read-only path)
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int v0 = 0; v0 < total; v0 += 64, ++round) {
+            if (round % stride != phase) continue;
+            const int vv = v0 + 2 * lane;
+            // owner of vv: the lowest lane whose inclusive end exceeds vv
+            int lo = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) b[q] = pt[q] >= 0 ? __ldcg(rec0 + pt[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 v[16];
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                if (e <= vv) lo += step;
+            }
+            // and of vv + 1 (a later run may follow empty ones)
+            int lo1 = 0;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float cf = gd[q].w;
-        const float d0 = gd[q].x, d1 = gd[q].y, d2 = gd[q].z;
-        // this half's three products: (x x, x y, x z) or (y y, y z, z z), times c
-        const float s0 = cf * (h ? b[q].y : b[q].x);
-        const float s2 = cf * (h ? b[q].z : b[q].x);
-        const float nn[3] = {s0 * (h ? b[q].y : b[q].x), s0 * (h ? b[q].z : b[q].y), s2 * b[q].z};
-        // d^ d^T upper triangle in pairs: (d0 d0, d0 d1) (d0 d2, d0) (d1 d1, d1 d2) (d1, d2 d2) (d2, 1)
-        const float2 dd[5] = {make_float2(d0 * d0, d0 * d1), make_float2(d0 * d2, d0), make_float2(d1 * d1, d1 * d2),
-                              make_float2(d1, d2 * d2), make_float2(d2, 1.0f)};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float2 na = make_float2(nn[a], nn[a]);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) v[5 * a + k] = __ffma2_rn(na, dd[k], v[5 * a + k]);
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, incl, lo1 + step - 1);
+                if (e <= vv + 1) lo1 += step;
+            }
+            const int o_st = __shfl_sync(0xffffffffu, st, lo), o_in = __shfl_sync(0xffffffffu, incl, lo);
+            const int o_len = __shfl_sync(0xffffffffu, len, lo), o_sl = __shfl_sync(0xffffffffu, sl, lo);
+            const int n_st = __shfl_sync(0xffffffffu, st, lo1), n_in = __shfl_sync(0xffffffffu, incl, lo1);
+            const int n_len = __shfl_sync(0xffffffffu, len, lo1), n_sl = __shfl_sync(0xffffffffu, sl, lo1);
+            const int k0 = vv < total ? o_st + vv - (o_in - o_len) : -1;
+            const int k1 = vv + 1 < total ? n_st + vv + 1 - (n_in - n_len) : -1;
+            f(k0, o_sl, k1, n_sl);
         }
     }
-    warp_halving2_16(v);
-    if (!(lane & 1) && (lane >> 1) < 15)   // chunk-major partials: moment pairs 15 h + lane / 2
-        reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[15 * h + (lane >> 1)] = v[0];
 }
 
-// role 1 (diagonal blocks): two warps per chunk of <= ED_CHUNK1 entries (most
-// nodes have one chunk), in rounds of 128 entries; per entry J^T r (12 floats)
-// and the pose-node block (6 x 12) of node j.  Moment pairs (float2 slots):
-// 0..5 J^T r, 6 + 6 t + 2 r (+1) pose-node row t, node row r.  Half 0 forms
-// slots 0..23 (J^T r, rows t = 0..2), half 1 slots 24..41 (t = 3..5); the
-// loads of two entries are issued together.
-template <int H>
-__device__ __forceinline__ void assemble1_half(const int4 ch, int c, const float *R, const float4 *__restrict__ geo,
-                                               const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
-                                               const float4 *__restrict__ rec1, float *__restrict__ part)
+struct AsmArgs {
+    const int4 *info;        // [n_upper][2] records of the upper blocks (k_fin_pack)
+    const uint32_t *inc;     // incidences run << 4 | s << 2 | t, sorted by block
+    const int *run_start;    // [n_runs + 1] runs in the compacted records (the step's valid rows)
+    const float4 *spos, *sw, *rec0, *rec1;   // compacted valid rows: position, tuple weights, records
+    const float *pose_R;     // R of the step's pose (9 floats, from the point pass)
+    const int *col, *nbr;
+    const float4 *g;
+    const float4 *x4;
+    const double *pose;
+    int m, n_off, kg, mixed;
+    float w_rot, w_reg, lambda, jitter;
+    float *bsr, *grad, *pnode, *minv;
+    float *dmom;             // [m][72]: moments of the diagonal blocks (60) and their J^T r (12)
+    float2 *node_energy;
+    int *status;
+};
+
+// role 0: the 60 moments of block (j, l) (row node j at g), in float2 pairs
+// v[5 a + k] = moments (10 a + 2 k, 10 a + 2 k + 1), a = the product of n~
+// components (xx, xy, xz, yy, yz, zz), 2 k, 2 k + 1 = the pairs of d^ d^T
+// (d0 d0, d0 d1) (d0 d2, d0) (d1 d1, d1 d2) (d1, d2 d2) (d2, 1)
+__device__ __forceinline__ void moments_add(float2 (&v)[32], float4 P, float4 W, float4 B, int sl, float4 gj)
 {
-    const int lane = threadIdx.x & 31;
-    constexpr int BASE = H == 0 ? 6 : 0;   // slot of row t = 3H within this half
+    const float c = pick4(W, sl >> 2) * pick4(W, sl & 3);
+    const float d0 = P.x - gj.x, d1 = P.y - gj.y, d2 = P.z - gj.z;
+    const float cx = c * B.x, cy = c * B.y, cz = c * B.z;
+    const float nn[6] = {cx * B.x, cx * B.y, cx * B.z, cy * B.y, cy * B.z, cz * B.z};
+    const float2 dd[5] = {make_float2(d0 * d0, d0 * d1), make_float2(d0 * d2, d0), make_float2(d1 * d1, d1 * d2),
+                          make_float2(d1, d2 * d2), make_float2(d2, 1.0f)};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float2 na = make_float2(nn[q], nn[q]);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[5 * q + k] = __ffma2_rn(na, dd[k], v[5 * q + k]);
+    }
+}
+
+__device__ __forceinline__ void role0(const AsmArgs &a, int i0, int n, int phase, int stride, float4 gj, float *M)
+{
     float2 v[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
-#pragma unroll 1
-    for (int e0 = 0; e0 < ch.z; e0 += 128) {
-#pragma unroll
-    for (int q0 = 0; q0 < 4; q0 += 2) {
-        float4 gd[2], b[2], jq[2];
-        int pi[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int e = e0 + lane + 32 * (q0 + u);
-            const bool in = e < ch.z;
-            gd[u] = in ? __ldg(geo + ch.y + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-            pi[u] = in ? (int)(__ldg(ent + ch.y + e) >> 4) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            b[u] = pi[u] >= 0 ? __ldg(rec0 + pi[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (H == 0) jq[u] = pi[u] >= 0 ? __ldg(rec1 + pi[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float ws = sqrtf(gd[u].w);   // diagonal entries store w_s * w_s (0 for absent entries)
-            const float2 dlo = make_float2(gd[u].x, gd[u].y), dhi = make_float2(gd[u].z, 1.0f);
-            const float nb[3] = {ws * b[u].x, ws * b[u].y, ws * b[u].z};
-            // d r / d pose: angles (t = 0..2) from the point record, translation
-            // (t = 3..5) = R nb_s with nb_s = sqrt(w) R^T n
-            float jp[3];
-            if (H == 0) {
-                jp[0] = jq[u].x;
-                jp[1] = jq[u].y;
-                jp[2] = jq[u].z;
-            } else {
-                jp[0] = R[0] * b[u].x + R[1] * b[u].y + R[2] * b[u].z;
-                jp[1] = R[3] * b[u].x + R[4] * b[u].y + R[5] * b[u].z;
-                jp[2] = R[6] * b[u].x + R[7] * b[u].y + R[8] * b[u].z;
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                if (H == 0) {
-                    const float2 g2 = make_float2(b[u].w * nb[r], b[u].w * nb[r]);
-                    v[2 * r] = __ffma2_rn(g2, dlo, v[2 * r]);
-                    v[2 * r + 1] = __ffma2_rn(g2, dhi, v[2 * r + 1]);
-                }
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    const float s2 = jp[t] * nb[r];
-                    const float2 c2 = make_float2(s2, s2);
-                    v[BASE + 6 * t + 2 * r] = __ffma2_rn(c2, dlo, v[BASE + 6 * t + 2 * r]);
-                    v[BASE + 6 * t + 2 * r + 1] = __ffma2_rn(c2, dhi, v[BASE + 6 * t + 2 * r + 1]);
-                }
-            }
-        }
-    }
-    }
-    warp_halving2<32>(v);
-    constexpr int NSLOT = H == 0 ? 24 : 18;
-    if (lane < NSLOT) reinterpret_cast<float2 *>(part + (long)c * ED_PART_STRIDE)[24 * H + lane] = v[0];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    block_points(a.inc, a.run_start, i0, n, phase, stride, [&](int k0, int s0, int k1, int s1) {
+        // every load of both points before the first product; records of the
+        // point pass through the coherent path (written by the kernel before)
+        const float4 B0 = k0 >= 0 ? __ldcg(a.rec0 + k0) : z4, B1 = k1 >= 0 ? __ldcg(a.rec0 + k1) : z4;
+        const float4 P0 = k0 >= 0 ? __ldcg(a.spos + k0) : z4, P1 = k1 >= 0 ? __ldcg(a.spos + k1) : z4;
+        const float4 W0 = k0 >= 0 ? __ldcg(a.sw + k0) : z4, W1 = k1 >= 0 ? __ldcg(a.sw + k1) : z4;
+        moments_add(v, P0, W0, B0, s0, gj);
+        moments_add(v, P1, W1, B1, s1, gj);
+    });
+    if (a.mixed) warp_halving2_ff<32>(v);
+    else warp_halving2<32>(v);
+    const int lane = threadIdx.x & 31;
+    if (lane < 30) reinterpret_cast<float2 *>(M)[lane] = v[0];
 }
 
-__global__ void __launch_bounds__(128, 4) k_assemble1(const int4 *__restrict__ chunks, int c_begin, int nchunks,
-                                                   int max_chunks, const float4 *__restrict__ geo,
-                                                   const uint32_t *__restrict__ ent, const float4 *__restrict__ rec0,
-                                                   const float4 *__restrict__ rec1, const double *__restrict__ pose,
-                                                   float *__restrict__ part)
+// role 1 (diagonal block of node j): J^T r (12) and the pose-node block (6 x
+// 12) in float2 slots: 0..5 J^T r, 6 + 6 t + 2 r (+1) pose row t, node row r.
+// Half 0 forms slots 0..23 (J^T r, pose rows t = 0..2: the angle derivatives
+// of the point record), half 1 slots 24..41 (t = 3..5: translation, R n~);
+// lane k < 24 / 18 then holds the half's slot k, stored at G[2 k], G[2 k + 1].
+template <int H>
+__device__ __forceinline__ void role1_add(float2 (&v)[32], float4 P, float4 W, float4 B, float4 J, int s, float4 gj,
+                                          const float *R)
 {
-    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int c = c_begin + (wg >> 1), h = wg & 1;
-    const int4 ch = c < c_begin + nchunks ? chunks[c] : make_int4(0, 0, 0, 0);   // fixed for the frame
-    ed_pdl_wait();
-    __shared__ ed_pose_f P;
-    if (threadIdx.x == 0) ed_pose_eval(pose, P);
-    __syncthreads();
-    if (c >= c_begin + nchunks) return;
-    if (h == 0) assemble1_half<0>(ch, c, P.R, geo, ent, rec0, rec1, part);
-    else assemble1_half<1>(ch, c, P.R, geo, ent, rec0, rec1, part);
+    constexpr int BASE = H == 0 ? 6 : 0;
+    const float ws = pick4(W, s);
+    const float2 dlo = make_float2(P.x - gj.x, P.y - gj.y), dhi = make_float2(P.z - gj.z, 1.0f);
+    const float nb[3] = {ws * B.x, ws * B.y, ws * B.z};
+    float jp[3];
+    if (H == 0) {
+        jp[0] = J.x;
+        jp[1] = J.y;
+        jp[2] = J.z;
+    } else {
+        jp[0] = R[0] * B.x + R[1] * B.y + R[2] * B.z;
+        jp[1] = R[3] * B.x + R[4] * B.y + R[5] * B.z;
+        jp[2] = R[6] * B.x + R[7] * B.y + R[8] * B.z;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (H == 0) {
+            const float2 g2 = make_float2(B.w * nb[r], B.w * nb[r]);
+            v[2 * r] = __ffma2_rn(g2, dlo, v[2 * r]);
+            v[2 * r + 1] = __ffma2_rn(g2, dhi, v[2 * r + 1]);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const float s2 = jp[t] * nb[r];
+            const float2 c2 = make_float2(s2, s2);
+            v[BASE + 6 * t + 2 * r] = __ffma2_rn(c2, dlo, v[BASE + 6 * t + 2 * r]);
+            v[BASE + 6 * t + 2 * r + 1] = __ffma2_rn(c2, dhi, v[BASE + 6 * t + 2 * r + 1]);
+        }
+    }
 }
 
-// ---------------------------------------------------------------------------
-// finalisation: one warp per upper block (j, l), j <= l
-// ---------------------------------------------------------------------------
-
-struct FinArgs {
-    const int4 *info;        // [n_upper][2] records of the upper blocks (k_fin_pack)
-    const int *col, *nbr;
-    const float *part;
-    int max_chunks;
-    int n_upper, kg, mixed;
-    const float4 *g;
-    const float4 *x4;
-    float w_rot, w_reg, lambda, jitter;
-    float *bsr, *grad, *pnode, *minv;
-    float2 *node_energy;
-    int *status;
-    // for k_fin_totals: the energy totals of the step from the node energies
-    // and the pose pass's sums
-    int m;
-    int *misc;
-    double *dmisc;
-    ed_stats *stats;
-    float lambda_report;     // damping reported in the statistics
-};
+template <int H>
+__device__ __forceinline__ void role1(const AsmArgs &a, int i0, int n, float4 gj, const float *R, float *G)
+{
+    float2 v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    block_points(a.inc, a.run_start, i0, n, 0, 1, [&](int k0, int s0, int k1, int s1) {
+        const float4 B0 = k0 >= 0 ? __ldcg(a.rec0 + k0) : z4, B1 = k1 >= 0 ? __ldcg(a.rec0 + k1) : z4;
+        float4 J0 = z4, J1 = z4;
+        if (H == 0) {
+            J0 = k0 >= 0 ? __ldcg(a.rec1 + k0) : z4;
+            J1 = k1 >= 0 ? __ldcg(a.rec1 + k1) : z4;
+        }
+        const float4 P0 = k0 >= 0 ? __ldcg(a.spos + k0) : z4, P1 = k1 >= 0 ? __ldcg(a.spos + k1) : z4;
+        const float4 W0 = k0 >= 0 ? __ldcg(a.sw + k0) : z4, W1 = k1 >= 0 ? __ldcg(a.sw + k1) : z4;
+        role1_add<H>(v, P0, W0, B0, J0, s0 >> 2, gj, R);
+        role1_add<H>(v, P1, W1, B1, J1, s1 >> 2, gj, R);
+    });
+    if (a.mixed) warp_halving2_ff<32>(v);
+    else warp_halving2<32>(v);
+    const int lane = threadIdx.x & 31;
+    constexpr int NSLOT = H == 0 ? 24 : 18;
+    if (lane < NSLOT) reinterpret_cast<float2 *>(G)[lane] = v[0];   // G: this half's slots
+}
 
 __device__ __forceinline__ int sym3(int a, int b)
 {
@@ -466,59 +613,6 @@ __device__ __forceinline__ int sym4(int a, int b)
     if (a > b) { int t = a; a = b; b = t; }
     return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
 }
-
-// sum of the chunk partials of one component (partials are chunk-major,
-// ED_PART_STRIDE floats per chunk): p = the component in the first chunk
-// (NULL: none), n chunks, summed in chunk order, two-sum compensated when
-// mixed.  A lane keeps several of them and loads four chunks of each before
-// adding, so the loads of all its components are in flight together.
-struct PartSum {
-    const float *p;
-    int n;
-    float s, err;
-};
-
-__device__ __forceinline__ PartSum part_sum(const float *part, int comp, int c0, int n)
-{
-    PartSum r;
-    r.p = comp >= 0 ? part + (long)c0 * ED_PART_STRIDE + comp : nullptr;
-    r.n = comp >= 0 ? n : 0;
-    r.s = 0.f;
-    r.err = 0.f;
-    return r;
-}
-
-__device__ __forceinline__ void part_load4(const PartSum &c, int k0, float4 &v)
-{
-    const float *p = c.p + (long)k0 * ED_PART_STRIDE;
-    v.x = k0 < c.n ? p[0] : 0.f;
-    v.y = k0 + 1 < c.n ? p[ED_PART_STRIDE] : 0.f;
-    v.z = k0 + 2 < c.n ? p[2 * ED_PART_STRIDE] : 0.f;
-    v.w = k0 + 3 < c.n ? p[3 * ED_PART_STRIDE] : 0.f;
-}
-
-__device__ __forceinline__ void part_add1(PartSum &c, float x, bool in, int mixed)
-{
-    if (!in) return;
-    if (!mixed) {
-        c.s += x;
-        return;
-    }
-    const float t = c.s + x;
-    const float bp = t - c.s;
-    c.err += (c.s - (t - bp)) + (x - bp);
-    c.s = t;
-}
-
-__device__ __forceinline__ void part_add4(PartSum &c, int k0, const float4 v, int mixed)
-{
-    part_add1(c, v.x, k0 < c.n, mixed);
-    part_add1(c, v.y, k0 + 1 < c.n, mixed);
-    part_add1(c, v.z, k0 + 2 < c.n, mixed);
-    part_add1(c, v.w, k0 + 3 < c.n, mixed);
-}
-
-__device__ __forceinline__ float part_value(const PartSum &c, int mixed) { return mixed ? c.s + c.err : c.s; }
 
 // derivative of the Rot(A) residual q (column pair ca, cb) with respect to
 // the parameter 4 r + c of [A | t]
@@ -539,8 +633,6 @@ __device__ __forceinline__ float rot_res(const float *X, int q)
     float d = X[ca] * X[cb] + X[4 + ca] * X[4 + cb] + X[8 + ca] * X[8 + cb];
     return ca == cb ? d - 1.0f : d;
 }
-
-#define FIN_WARPS 4
 
 // E_rot Gauss-Newton block between columns c and cp of A (3-vectors x_c over
 // node rows r, rp): sum over the 6 residuals x_a.x_b - delta_ab of products of
@@ -604,114 +696,70 @@ __device__ __forceinline__ bool block_inverse12(const float *H, float *scratch, 
     return true;
 }
 
-// the entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
-// shift), R, C
-__device__ __forceinline__ void fill_block_table(int *s_tab)
+// moment indices of entry (R, C) of a 12x12 block: of (R, C) itself and of
+// (R, the column's t component), for the shift d^_l = d^_j + [g_j - g_l; 0]
+__device__ __forceinline__ void block_entry_moments(int R, int Cc, int &mi, int &m3)
 {
-    for (int e = threadIdx.x; e < 144; e += blockDim.x) {
-        const int R = e / 12, Cc = e % 12;
-        const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
-        const int mi = 10 * sym3(r, rp) + sym4(c, cp), m3 = 10 * sym3(r, rp) + sym4(c, 3);
-        s_tab[e] = mi | (m3 << 8) | (R << 16) | (Cc << 24);
-    }
+    const int r = R >> 2, c = R & 3, rp = Cc >> 2, cp = Cc & 3;
+    const int a = 10 * sym3(r, rp);
+    mi = a + sym4(c, cp);
+    m3 = a + sym4(c, 3);
 }
 
-// component i of (v0, v1, v2, v3) without a local array
-__device__ __forceinline__ float pick4(float v0, float v1, float v2, float v3, int i)
-{
-    return i == 0 ? v0 : (i == 1 ? v1 : (i == 2 ? v2 : v3));
-}
-
-// the partial sums of components (c_a, c_b) over n chunks from c0 (c_b < 0: one)
-__device__ __forceinline__ void part_sums2(const FinArgs &a, int ca, int cb, int c0, int n, float &va, float &vb)
-{
-    PartSum pa = part_sum(a.part, ca, c0, n), pb = part_sum(a.part, cb, c0, n);
-    for (int k0 = 0; k0 < pa.n; k0 += 4) {
-        float4 x, y;
-        part_load4(pa, k0, x);
-        part_load4(pb, k0, y);
-        part_add4(pa, k0, x, a.mixed);
-        part_add4(pb, k0, y, a.mixed);
-    }
-    va = part_value(pa, a.mixed);
-    vb = part_value(pb, a.mixed);
-}
-
-// the same for three components (cc < 0: none)
-__device__ __forceinline__ void part_sums3(const FinArgs &a, int ca, int cb, int cc, int c0, int n, float &va, float &vb,
-                                           float &vc)
-{
-    PartSum pa = part_sum(a.part, ca, c0, n), pb = part_sum(a.part, cb, c0, n), pc = part_sum(a.part, cc, c0, n);
-    for (int k0 = 0; k0 < pa.n; k0 += 4) {
-        float4 x, y, z;
-        part_load4(pa, k0, x);
-        part_load4(pb, k0, y);
-        part_load4(pc, k0, z);
-        part_add4(pa, k0, x, a.mixed);
-        part_add4(pb, k0, y, a.mixed);
-        part_add4(pc, k0, z, a.mixed);
-    }
-    va = part_value(pa, a.mixed);
-    vb = part_value(pb, a.mixed);
-    vc = part_value(pc, a.mixed);
-}
-
-// one warp per upper block u (INV = false: the block inverses are taken
-// later, in the Levenberg-Marquardt stage).  The 144 entries of a block go to
-// lanes 0..23: lane L takes column C = L % 12 of the rows R = L / 12 + 2 k,
-// k < 6, so a lane's column quantities are formed once.
-template <bool INV>
-__device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M, float *H, float *X, float *S,
-                                               float *Lw, int *Nk, float4 *Ng, float *Nx, const int *s_tab)
+// an off-diagonal upper block (j, l) from its moments M: the 144 entries
+// (lane L < 24 takes column C = L % 12 of the rows R = L / 12 + 2 k, k < 6)
+// with d^_l = d^_j + [g_j - g_l; 0], plus the E_reg terms of the graph edges
+// j -> l and l -> j; the block and its transpose are written
+__device__ __forceinline__ void fin_offdiag(const AsmArgs &a, int4 i0, int4 i1, const float *M)
 {
     const int lane = threadIdx.x & 31;
-    const int4 i0 = a.info[2 * u], i1 = a.info[2 * u + 1];
-    const int b = i0.x, j = i0.y, l = i0.z;
-    const bool diag = j == l;
-    const int c0 = i1.x, nch = i1.y;
+    const int b = i0.x, j = i0.y, l = i0.z, tb = i0.w;
+    if (tb < 0) {
+        if (lane == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
+        return;
+    }
+    if (lane >= 24) return;
+    const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
+    const float wr = a.w_reg;
+    const bool e_jl = (i1.z & 1) != 0, e_lj = (i1.z & 2) != 0;   // graph edges j -> l, l -> j
+    const float4 gj = a.g[j], gl = a.g[l];
+    const float dlc = pick4(gj.x - gl.x, gj.y - gl.y, gj.z - gl.z, 0.f, cp);
+    const float hx = gl.x - gj.x, hy = gl.y - gj.y, hz = gl.z - gj.z;
+    // E_reg, edge l -> j (d e / d t_j = -I): column quantity of the rows c = 3
+    const float reg_lj = e_lj ? -wr * (cp < 3 ? -pick4(hx, hy, hz, 1.f, cp) : 1.0f) : 0.f;
+    float *dst = a.bsr + (long)b * 144 + Cc;
+    float *dstT = a.bsr + (long)tb * 144 + Cc * 12;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int R = h0 + 2 * k, r = R >> 2, c = R & 3;
+        int mi, m3;
+        block_entry_moments(R, Cc, mi, m3);
+        float h = M[mi];
+        if (cp < 3) h += dlc * M[m3];
+        if (r == rp) {   // E_reg, edge j -> l (d e / d t_l = -I) on the t column
+            if (e_jl && cp == 3) h -= wr * pick4(hx, hy, hz, 1.f, c);
+            if (c == 3) h += reg_lj;
+        }
+        dst[R * 12] = h;
+        dstT[R] = h;
+    }
+}
+
+// a diagonal block (j, j) from its moments M and J^T r G (12 floats; the
+// pose-node block was written by the role-1 warps): one warp adds E_rot and
+// E_reg (out-edges j -> k: S = sum h h^T, h = [g_k - g_j; 1]; in-edges k -> j
+// on the t rows), writes the block, the gradient and the node's energies, and
+// (INV) the inverse of the jittered block
+template <bool INV>
+__device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, const float *M, const float *G, float *H,
+                                         float *X, float *S, float *Lw, int *Nk, float4 *Ng, float *Nx)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = i0.x, j = i0.y;
+    const int rp0 = i0.w, rp1 = rp0 + i1.z;   // row j of the block pattern
     const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
     const bool ent_lane = lane < 24;
     const float wr = a.w_reg;
-    if (!diag) {
-        const int tb = i0.w;
-        const bool e_jl = (i1.z & 1) != 0, e_lj = (i1.z & 2) != 0;   // graph edges j -> l, l -> j
-        const float4 gj = a.g[j], gl = a.g[l];
-        {
-            float v0, v1;
-            part_sums2(a, lane, lane + 32 < 60 ? lane + 32 : -1, c0, nch, v0, v1);
-            M[lane] = v0;
-            if (lane + 32 < 60) M[lane + 32] = v1;
-        }
-        __syncwarp();
-        if (tb < 0) {
-            if (lane == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
-            return;
-        }
-        if (!ent_lane) return;
-        // d^_l = d^_j + [g_j - g_l; 0]; h_jl = [g_l - g_j; 1]
-        const float dlc = pick4(gj.x - gl.x, gj.y - gl.y, gj.z - gl.z, 0.f, cp);
-        const float hx = gl.x - gj.x, hy = gl.y - gj.y, hz = gl.z - gj.z;
-        // E_reg, edge l -> j (d e / d t_j = -I): column quantity of the rows c = 3
-        const float reg_lj = e_lj ? -wr * (cp < 3 ? -pick4(hx, hy, hz, 1.f, cp) : 1.0f) : 0.f;
-        float *dst = a.bsr + (long)b * 144 + Cc;
-        float *dstT = a.bsr + (long)tb * 144 + Cc * 12;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int R = h0 + 2 * k, r = R >> 2, c = R & 3;
-            const int T = s_tab[R * 12 + Cc];
-            float h = M[T & 255];
-            if (cp < 3) h += dlc * M[(T >> 8) & 255];
-            if (r == rp) {   // E_reg, edge j -> l (d e / d t_l = -I) on the t column
-                if (e_jl && cp == 3) h -= wr * pick4(hx, hy, hz, 1.f, c);
-                if (c == 3) h += reg_lj;
-            }
-            dst[R * 12] = h;
-            dstT[R] = h;
-        }
-        return;
-    }
-    // ---- diagonal block ----
-    const int rp0 = i0.w, rp1 = rp0 + (i1.w >> 16);   // row j of the block pattern
     if (lane < a.kg) {   // out-edges j -> k: index, position and parameters of k, loaded once
         const int k = a.nbr[j * a.kg + lane];
         Nk[lane] = k;
@@ -723,27 +771,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
     }
     if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
     const float4 gj = a.g[j];
-    // the 60 moments (role-0 chunks), then J^T r and the pose-node block (84
-    // components of the role-1 chunks)
-    float *Gx = M + 60;
-    {
-        float v0, v1;
-        part_sums2(a, lane, lane + 32 < 60 ? lane + 32 : -1, c0, nch, v0, v1);
-        M[lane] = v0;
-        if (lane + 32 < 60) M[lane + 32] = v1;
-        const int c1 = i1.z, nch1 = i1.w & 0xffff;
-        float w0, w1, w2;
-        part_sums3(a, lane, lane + 32, lane + 64 < 84 ? lane + 64 : -1, c1, nch1, w0, w1, w2);
-        auto put = [&](int k, float v) {
-            if (k < 12) Gx[k] = v;
-            else a.pnode[(long)j * 72 + (k - 12)] = v;
-        };
-        put(lane, w0);
-        put(lane + 32, w1);
-        if (lane + 64 < 84) put(lane + 64, w2);
-    }
     __syncwarp();
-    // S = sum over out-edges j -> k of h h^T, h = [g_k - g_j; 1]
     if (lane < 16) {
         const int c = lane >> 2, cq = lane & 3;
         float v = 0.f;
@@ -759,7 +787,6 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
     float nin = 0.f, ein0 = 0.f, ein1 = 0.f, ein2 = 0.f;
     for (int t = rp0 + lane; t < rp1; t += 32) {
         const int k = a.col[t];
-        // the neighbours of k, its position and parameters: every load issued together
         int nb[ED_MAX_KG];
 #pragma unroll
         for (int s = 0; s < ED_MAX_KG; ++s) nb[s] = s < a.kg ? a.nbr[k * a.kg + s] : -1;
@@ -791,8 +818,9 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int R = h0 + 2 * k, r = R >> 2, c = R & 3;
-            const int T = s_tab[R * 12 + Cc];
-            float h = M[T & 255];
+            int mi, m3;
+            block_entry_moments(R, Cc, mi, m3);
+            float h = M[mi];
             if (c < 3 && cp < 3) h += a.w_rot * rot_jtj(X, r, c, rp, cp);
             if (r == rp) {
                 h += wr * S[4 * c + cp];
@@ -806,7 +834,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
     // gradient: data + E_rot + E_reg (out-edges, in-edges)
     if (lane < 12) {
         const int r = lane >> 2, c = lane & 3;
-        float g = Gx[lane];
+        float g = G[lane];
         if (c < 3) {
             float v = 0.f;
 #pragma unroll
@@ -846,6 +874,91 @@ __device__ __forceinline__ void finalize_block(const FinArgs &a, int u, float *M
     if (!block_inverse12(H, Lw, a.jitter, a.minv + (long)j * 144) && lane == 0)
         atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
 }
+
+#define ASM_WARPS 4
+
+// One warp per work item, four per CTA, in this order: the moments of the m
+// diagonal blocks (to dmom[j][0..60), finalised by k_fin_diag), the two
+// halves of J^T r and the pose-node block of every node (J^T r to
+// dmom[j][60..72), the pose-node block to pnode), then the off-diagonal upper
+// blocks, each finalised by its warp.
+template <bool INV>
+__global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
+{
+    __shared__ __align__(16) float sM[ASM_WARPS][84];
+    __shared__ float s_R[ASM_WARPS][9];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = (int)blockIdx.x * ASM_WARPS + wid;
+    const int m = a.m;
+    const int kind = w < m ? 0 : (w < 3 * m ? 1 : 2);   // diagonal moments, node rows, off-diagonal block
+    const int u = kind == 0 ? w : (kind == 1 ? (w - m) >> 1 : m + (w - 3 * m));
+    const bool has = kind < 2 || u < m + a.n_off;
+    // the block's records and node position are fixed for the frame: loaded
+    // before the wait for the point pass (whose records come after)
+    const int4 i0 = has ? a.info[2 * u] : make_int4(0, 0, 0, 0), i1 = has ? a.info[2 * u + 1] : make_int4(0, 0, 0, 0);
+    const float4 gj = has ? a.g[i0.y] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    if (!has) return;
+    float *M = sM[wid];   // (every warp works alone from here: warp-level synchronisation only)
+    if (kind == 0) {
+        role0(a, i1.x, i1.y, 0, 1, gj, M);
+        __syncwarp();
+        for (int q = lane; q < 60; q += 32) a.dmom[(long)u * 72 + q] = M[q];
+    } else if (kind == 1) {
+        const int h = (w - m) & 1;
+        if (lane < 9) s_R[wid][lane] = __ldcg(a.pose_R + lane);
+        __syncwarp();
+        if (h == 0) role1<0>(a, i1.x, i1.y, gj, s_R[wid], M);   // J^T r (12), pose rows 0..2 (36)
+        else role1<1>(a, i1.x, i1.y, gj, s_R[wid], M);          // pose rows 3..5 (36)
+        __syncwarp();
+        float *pn = a.pnode + (long)i0.y * 72;
+        if (h == 0) {
+            if (lane < 12) a.dmom[(long)u * 72 + 60 + lane] = M[lane];
+            for (int q = lane; q < 36; q += 32) pn[q] = M[12 + q];
+        } else {
+            for (int q = lane; q < 36; q += 32) pn[36 + q] = M[q];
+        }
+    } else {
+        role0(a, i1.x, i1.y, 0, 1, gj, M);
+        __syncwarp();
+        fin_offdiag(a, i0, i1, M);
+    }
+}
+
+// the diagonal blocks from their moments and J^T r (dmom), one warp per node
+template <bool INV>
+__global__ void __launch_bounds__(32 * ASM_WARPS) k_fin_diag(AsmArgs a)
+{
+    __shared__ __align__(16) float sM[ASM_WARPS][72];
+    __shared__ float sH[ASM_WARPS][144], sL[ASM_WARPS][144], sX[ASM_WARPS][12], sS[ASM_WARPS][16];
+    __shared__ int sNk[ASM_WARPS][ED_MAX_KG];
+    __shared__ float4 sNg[ASM_WARPS][ED_MAX_KG];
+    __shared__ __align__(16) float sNx[ASM_WARPS][12 * ED_MAX_KG];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = (int)blockIdx.x * ASM_WARPS + wid;
+    const int4 i0 = j < a.m ? a.info[2 * j] : make_int4(0, 0, 0, 0), i1 = j < a.m ? a.info[2 * j + 1] : make_int4(0, 0, 0, 0);
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    if (j >= a.m) return;
+    for (int q = lane; q < 72; q += 32) sM[wid][q] = __ldcg(a.dmom + (long)j * 72 + q);
+    __syncwarp();
+    fin_diag<INV>(a, i0, i1, sM[wid], sM[wid] + 60, sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid]);
+}
+
+#define FIN_WARPS 4
+
+// arguments of k_fin_totals: the energy totals of the step from the node
+// energies and the pose pass's sums
+struct FinArgs {
+    float2 *node_energy;
+    int *status;
+    int m;
+    int *misc;
+    double *dmisc;
+    ed_stats *stats;
+    float lambda_report;     // damping reported in the statistics
+};
 
 // after the finalisation, one CTA: the node energies summed in a fixed order
 // (float-float), the energy of Eq. (3) from them and the pose pass's sums,
@@ -902,29 +1015,6 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_fin_totals(FinArgs a)
         }
     }
     if (threadIdx.x < 2) a.misc[MI_BAR + threadIdx.x] = 0;   // the arrival count of the step's PCG
-}
-
-template <bool INV>
-__global__ void __launch_bounds__(32 * FIN_WARPS) k_finalize(FinArgs a)
-{
-    __shared__ float sM[FIN_WARPS][84];
-    __shared__ float sH[FIN_WARPS][144];
-    __shared__ float sX[FIN_WARPS][12];
-    __shared__ float sS[FIN_WARPS][16];
-    __shared__ float sL[FIN_WARPS][144];
-    __shared__ int sNk[FIN_WARPS][ED_MAX_KG];
-    __shared__ float4 sNg[FIN_WARPS][ED_MAX_KG];
-    __shared__ __align__(16) float sNx[FIN_WARPS][12 * ED_MAX_KG];
-    // entry table of a 12x12 block: moment index of (R, C) and of (R, 3-column
-    // shift), R, C (the same for every block; computed once per CTA)
-    __shared__ int s_tab[144];
-    ed_pdl_trigger();   // (launched after the join with the pose stream: everything before is complete)
-    fill_block_table(s_tab);
-    __syncthreads();
-    const int wid = threadIdx.x >> 5;
-    const int u = blockIdx.x * FIN_WARPS + wid;
-    if (u < a.n_upper)
-        finalize_block<INV>(a, u, sM[wid], sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid], s_tab);
 }
 
 // ---------------------------------------------------------------------------
@@ -1239,7 +1329,7 @@ static ed_status lm_stage(ed_context *ctx, const ed_solver_params *prm, float *x
     la.n_grad = 12 * m + 6;
     la.pblk = ctx->pose_blk;
     la.pblk_s = ctx->pblk_s;
-    const bool mixed = prm->precision == ED_PRECISION_MIXED;
+    const bool mixed = ed_is_mixed(prm->precision);
     la.xm = mixed ? x_master : nullptr;
     la.xm_p = ctx->xm_prev;
     la.n_xm = mixed ? 12 * m : 0;
@@ -1280,8 +1370,8 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     if (!ctx->have_graph) return ED_ERR_STATE;
     ed_status s = check_frame(ctx, fr);
     if (s != ED_OK) return s;
-    if (prm->n_pcg < 0 || (prm->precision == ED_PRECISION_MIXED && !x_master) ||
-        (prm->precision != ED_PRECISION_FP32 && prm->precision != ED_PRECISION_MIXED) ||
+    if (prm->n_pcg < 0 || prm->n_pcg > 4000 || (ed_is_mixed(prm->precision) && !x_master) ||
+        (prm->precision != ED_PRECISION_FP32 && !ed_is_mixed(prm->precision)) ||
         (prm->lm_accept != 0 && prm->lm_accept != 1))
         return ED_ERR_ARG;
     const int m = ctx->m;
@@ -1300,58 +1390,67 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
             ED_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
             ED_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
         }
-        k_pose_part<<<1, PF_THREADS, 0, ps>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, pose, pf, ctx->pose_blk,
+        k_pose_part<<<1, PF_THREADS, 0, ps>>>(ctx->k1_part, k1_grid_step(ctx), ctx->max_k1_ctas, pose, pf, ctx->pose_blk,
                                               ctx->grad + 12 * m, ctx->dmisc, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         if (fork_pose) ED_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
     }
-    if (ctx->n_chunks > 0) {
-        const int n0 = ctx->n_chunks0, base1 = ctx->chunk_base1, n1 = ctx->n_chunks - base1;
+    AsmArgs aa;
+    aa.info = ctx->fin_info;
+    aa.inc = ctx->inc;
+    aa.run_start = ctx->vrun_start;
+    aa.spos = ctx->cpos;
+    aa.sw = ctx->csw;
+    aa.rec0 = ctx->crec0;
+    aa.rec1 = ctx->crec1;
+    aa.pose_R = ctx->pose_R;
+    aa.col = ctx->col;
+    aa.nbr = ctx->graph.nbr;
+    aa.g = (const float4 *)ctx->graph.nodes;
+    aa.x4 = (const float4 *)x;
+    aa.pose = pose;
+    aa.m = m;
+    aa.n_off = ctx->n_upper - m;
+    aa.kg = ctx->k_graph;
+    aa.mixed = ed_is_mixed(prm->precision);
+    aa.w_rot = prm->w_rot;
+    aa.w_reg = prm->w_reg;
+    aa.lambda = lm ? 0.f : prm->lambda;
+    aa.jitter = prm->jitter;
+    aa.bsr = ctx->bsr;
+    aa.grad = ctx->grad;
+    aa.pnode = ctx->pnode;
+    aa.minv = ctx->minv;
+    aa.node_energy = ctx->node_energy;
+    aa.status = ctx->misc + MI_STATUS;
+    aa.dmom = ctx->dmom;
+    {
+        // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks
+        const int grid = ed_div_up(3 * m + aa.n_off, ASM_WARPS);
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
-        if (n0 > 0) {
-            ED_CUDA_TRY(ed_launch_pdl(k_assemble0, dim3(ed_div_up(2 * n0, 4)), dim3(128), 0, st, (const int4 *)ctx->chunks, n0,
-                                      ctx->max_chunks, (const float4 *)ctx->ent_geo, (const uint32_t *)ctx->ent_val,
-                                      (const float4 *)ctx->rec0, ctx->partials)); ed_note_launch();
-        }
-        if (n1 > 0) {
-            ED_CUDA_TRY(ed_launch_pdl(k_assemble1, dim3(ed_div_up(2 * n1, 4)), dim3(128), 0, st, (const int4 *)ctx->chunks,
-                                      base1, n1, ctx->max_chunks, (const float4 *)ctx->ent_geo,
-                                      (const uint32_t *)ctx->ent_val, (const float4 *)ctx->rec0,
-                                      (const float4 *)ctx->rec1, (const double *)pose, ctx->partials)); ed_note_launch();
-        }
+        ED_CUDA_TRY(ed_launch_pdl(lm ? k_assemble<false> : k_assemble<true>, dim3(grid), dim3(32 * ASM_WARPS), 0, st,
+                                  aa)); ed_note_launch();
+        ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS)),
+                                  dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();
     }
     FinArgs fa;
-    fa.info = ctx->fin_info;
-    fa.col = ctx->col;
-    fa.nbr = ctx->graph.nbr;
-    fa.part = ctx->partials;
-    fa.max_chunks = ctx->max_chunks;
-    fa.n_upper = ctx->n_upper;
-    fa.kg = ctx->k_graph;
-    fa.mixed = prm->precision == ED_PRECISION_MIXED;
-    fa.g = (const float4 *)ctx->graph.nodes;
-    fa.x4 = (const float4 *)x;
-    fa.w_rot = prm->w_rot;
-    fa.w_reg = prm->w_reg;
-    fa.lambda = lm ? 0.f : prm->lambda;
-    fa.jitter = prm->jitter;
-    fa.bsr = ctx->bsr;
-    fa.grad = ctx->grad;
-    fa.pnode = ctx->pnode;
-    fa.minv = ctx->minv;
     fa.node_energy = ctx->node_energy;
     fa.status = ctx->misc + MI_STATUS;
     fa.m = m;
     fa.misc = ctx->misc;
     fa.dmisc = ctx->dmisc;
     fa.stats = stats;
-    fa.lambda_report = fa.lambda;
-    if (fork_pose) ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    fa.lambda_report = aa.lambda;
     ed_tm_begin(ctx, ED_KERNEL_FINALIZE, st);
-    (lm ? k_finalize<false> : k_finalize<true>)<<<ed_div_up(ctx->n_upper, FIN_WARPS), 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
-    ED_CUDA_TRY(ed_launch_pdl(k_fin_totals, dim3(1), dim3(32 * FIN_WARPS), 0, st, fa)); ed_note_launch();
+    if (fork_pose) {
+        // (after the join with the pose stream: a normal launch)
+        ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+        k_fin_totals<<<1, 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
+    } else {
+        ED_CUDA_TRY(ed_launch_pdl(k_fin_totals, dim3(1), dim3(32 * FIN_WARPS), 0, st, fa)); ed_note_launch();
+    }
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
     ED_LAUNCH_CHECK();
     if (lm) return lm_stage(ctx, prm, x, x_master, pose, stats, st);
@@ -1473,34 +1572,37 @@ extern "C" ed_status ed_energy(ed_context *ctx, const ed_frame *fr, const ed_sol
 
 // dE/dx_j = 2 [ sum_i r_i w_ij sqrt(w) (R^T n) (x) d^_ij  +  rot and reg terms ]
 // (Gaussian w_ij recomputed from the node indices, not read from the graph),
-// gathered per node over the points of its diagonal block (fixed order)
+// gathered per node over the points of the runs of its diagonal block (fixed
+// order: deterministic); the point records are in model order
 __global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__restrict__ nbr,
                                                     const int *__restrict__ row_ptr, const int *__restrict__ col,
-                                                    const int *__restrict__ diag_pos, const int *__restrict__ ent_start,
-                                                    const int *__restrict__ ent_cnt, const uint32_t *__restrict__ ent,
-                                                    const float4 *__restrict__ g, const float4 *__restrict__ x4,
-                                                    const float4 *__restrict__ pos, const float *__restrict__ wts,
-                                                    const ushort4 *__restrict__ idx, int recompute_w, float sigma,
-                                                    const float4 *__restrict__ gp0, float w_rot, float w_reg,
-                                                    float scale, float *__restrict__ grad)
+                                                    const int *__restrict__ diag_pos, const int *__restrict__ inc_start,
+                                                    const uint32_t *__restrict__ inc, const int *__restrict__ run_start,
+                                                    const int *__restrict__ perm, const float4 *__restrict__ g,
+                                                    const float4 *__restrict__ x4, const float4 *__restrict__ pos,
+                                                    const float *__restrict__ wts, const ushort4 *__restrict__ idx,
+                                                    int recompute_w, float sigma, const float4 *__restrict__ gp0,
+                                                    float w_rot, float w_reg, float scale, float *__restrict__ grad)
 {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.x * 4 + wid;
     if (j >= m) return;
     const int b = diag_pos[j];
-    const int e0 = ent_start[b], ne = ent_cnt[b];
+    const int e0 = inc_start[b], ne = inc_start[b + 1] - e0;
     const float4 gj = g[j];
     float acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = 0.f;
-    for (int e = e0 + lane; e < e0 + ne; e += 32) {
-        const uint32_t v = ent[e];
-        const int i = (int)(v >> 4), s = (v >> 2) & 3;
+    auto add = [&](int k) {
+        if (k < 0) return;
+        const int i = perm[k];
         const float4 r0 = gp0[i];
         const float4 p = pos[i];
+        const ushort4 id = idx[i];
+        const int s = id.x == j ? 0 : (id.y == j ? 1 : (id.z == j ? 2 : 3));   // node j's slot
         float ws;
         if (recompute_w) {
-            const float4 w4 = ed_gauss_weights(p, idx[i], g, m, sigma);
+            const float4 w4 = ed_gauss_weights(p, id, g, m, sigma);
             ws = s == 0 ? w4.x : s == 1 ? w4.y : s == 2 ? w4.z : w4.w;
         } else {
             ws = wts[4 * i + s];
@@ -1511,8 +1613,12 @@ __global__ void __launch_bounds__(128) k_grad_nodes(int m, int kg, const int *__
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[4 * r + k] += c * nb[r] * dh[k];
-    }
+            for (int q = 0; q < 4; ++q) acc[4 * r + q] += c * nb[r] * dh[q];
+    };
+    block_points(inc, run_start, e0, ne, 0, 1, [&](int k0, int, int k1, int) {
+        add(k0);
+        add(k1);
+    });
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -1583,8 +1689,8 @@ extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const e
     if (s != ED_OK) return s;
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_GRAD, st)) != ED_OK) return s;
     k_grad_nodes<<<ed_div_up(ctx->m, 4), 128, 0, st>>>(ctx->m, ctx->k_graph, ctx->graph.nbr, ctx->row_ptr, ctx->col,
-                                                       ctx->diag_pos,
-                                                       ctx->ent_start, ctx->ent_cnt, ctx->ent_val,
+                                                       ctx->diag_pos, ctx->ent_start, ctx->inc, ctx->run_start,
+                                                       ctx->perm,
                                                        (const float4 *)ctx->graph.nodes, (const float4 *)x,
                                                        (const float4 *)ctx->pos, ctx->graph.weights,
                                                        (const ushort4 *)ctx->graph.idx,

@@ -270,7 +270,7 @@ __device__ __forceinline__ void poisson_prefetch(const float4 *__restrict__ pos,
 __global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restrict__ pos, const int2 *__restrict__ bucket,
                                                            const int *__restrict__ start, const int *__restrict__ misc_in,
                                                            const float *__restrict__ fmisc, int *cell_pick, unsigned *bar,
-                                                           int *status)
+                                                           int *status, unsigned long long wait_ns)
 {
     __shared__ int s_flag;
     if (*(volatile int *)status != ED_OK) return;   // every CTA: no grid when the set-up failed
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restr
         poisson_phase(pos, bucket, start[ph], start[ph + 1], ph, nx, ny, nz, r2, cell_pick, bc, p);
         if (ph < 26) {
             poisson_prefetch(pos, bucket, start[ph + 1], start[ph + 2], bc, p);
-            if (!ed_grid_sync(bar, status, gridDim.x, target, &s_flag)) return;
+            if (!ed_grid_sync(bar, status, gridDim.x, target, &s_flag, wait_ns)) return;
         }
     }
 }
@@ -521,11 +521,13 @@ __device__ __forceinline__ void set_bit(uint32_t *bm, int words, int a, int b)
     if (!(*w & bit)) atomicOr(w, bit);
 }
 
-__global__ void k_pairs_points(const ushort4 *__restrict__ idx, int n, uint32_t *bm, int words)
+// the same with the run count read from the device (queued before the host has it)
+__global__ void k_pairs_runs_dev(const int *__restrict__ n_runs_dev, const int *__restrict__ run_start,
+                                 const ushort4 *__restrict__ sidx, uint32_t *bm, int words)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const ushort4 q = idx[i];
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= *n_runs_dev) return;
+    const ushort4 q = sidx[run_start[r]];
     const int id[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -547,13 +549,17 @@ __global__ void k_pairs_graph(const int *__restrict__ nbr, int m, int kg, uint32
     }
 }
 
+// one warp per node row: the set bits of its bitmap words
 __global__ void k_row_count(const uint32_t *__restrict__ bm, int m, int words, int *__restrict__ cnt)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= m) return;
     int c = 0;
-    for (int w = 0; w < words; ++w) c += __popc(bm[(long)j * words + w]);
-    cnt[j] = c;
+    for (int w = lane; w < words; w += 32) c += __popc(bm[(long)j * words + w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[j] = c;
 }
 
 // (queued before the host has the block count: a count above the capacity
@@ -562,24 +568,37 @@ __global__ void k_row_fill(const uint32_t *__restrict__ bm, int m, int words, co
                            int *__restrict__ col, int *__restrict__ brow, int *__restrict__ diag_pos, int max_nnzb,
                            int *__restrict__ status)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per node row: the words in rounds of 32, a lane's bits placed
+    // after the bits of the lanes (and rounds) before it: ascending columns
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row_ptr[m] > max_nnzb) {
-        if (j == 0) atomicCAS(status, ED_OK, ED_ERR_CAPACITY);
+        if (j == 0 && lane == 0) atomicCAS(status, ED_OK, ED_ERR_CAPACITY);
         return;
     }
     if (j >= m) return;
     int p = row_ptr[j];
-    for (int w = 0; w < words; ++w) {
-        uint32_t v = bm[(long)j * words + w];
+    for (int w0 = 0; w0 < words; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t v = w < words ? bm[(long)j * words + w] : 0u;
+        const int c = __popc(v);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int q = p + incl - c;
         while (v) {
             const int b = __ffs(v) - 1;
             v &= v - 1;
             const int l = (w << 5) + b;
-            if (l == j) diag_pos[j] = p;
-            col[p] = l;
-            brow[p] = j;
-            ++p;
+            if (l == j) diag_pos[j] = q;
+            col[q] = l;
+            brow[q] = j;
+            ++q;
         }
+        p += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
@@ -617,126 +636,344 @@ __global__ void k_compact_upper(int nnzb, int m, const int *__restrict__ flag, c
     if (flag[b]) up_list[m + pre[b]] = b;
 }
 
-// one entry per (point, unordered slot pair s <= t): key = upper block, value =
-// point << 4 | row slot << 2 | column slot, generated in point order
-#define EG_T 128
-// the 10 entries (s <= t) of every point, written through shared memory so
-// that a CTA's 10 x 128 keys and values go out as contiguous stores
-// (queued before the host has the block count: nothing when it is above the
-// capacity, where k_row_fill has set the status)
-__global__ void __launch_bounds__(EG_T) k_entries_gen(const ushort4 *__restrict__ idx, int n,
-                                                      const int *__restrict__ row_ptr, const int *__restrict__ col,
-                                                      uint32_t *__restrict__ key, uint32_t *__restrict__ val,
-                                                      int *__restrict__ status, int m, int max_nnzb)
+// ---------------------------------------------------------------------------
+// points grouped by their node tuple.  Every point carries its k = 4 nearest
+// nodes; the points whose four nodes are the same set form a run of the
+// points sorted by that set (the tuple, nodes in increasing index order).  A
+// run contributes to the 10 blocks (tuple[s], tuple[t]), s <= t, of J^T J;
+// each such (block, run) pair is an incidence, and the assembly streams, for
+// one block, the points of its runs.
+// ---------------------------------------------------------------------------
+
+// the four nodes of a point in increasing index order, with the slot (position
+// in the point's nearest-node list) each came from: a sorting network
+__device__ __forceinline__ void tuple_of(ushort4 q, int (&n)[4], int (&slot)[4])
 {
-    __shared__ uint32_t sk[10 * EG_T], sv[10 * EG_T];
-    if (row_ptr[m] > max_nnzb) return;   // the same for every thread
-    const int i0 = blockIdx.x * EG_T, i = i0 + threadIdx.x;
-    if (i < n) {
-        const ushort4 q = idx[i];
-        const int id[4] = {q.x, q.y, q.z, q.w};
-        int e = 0;
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-#pragma unroll
-            for (int t = s; t < 4; ++t) {
-                int j = id[s], l = id[t], sr = s, sc = t;
-                if (j > l) {
-                    j = id[t];
-                    l = id[s];
-                    sr = t;
-                    sc = s;
-                }
-                const int b = find_block(row_ptr, col, j, l);
-                if (b < 0) atomicExch(status, ED_ERR_STATE);
-                sk[10 * threadIdx.x + e] = (uint32_t)(b < 0 ? 0 : b);
-                sv[10 * threadIdx.x + e] = ((uint32_t)i << 4) | ((uint32_t)sr << 2) | (uint32_t)sc;
-                ++e;
-            }
+    n[0] = q.x; n[1] = q.y; n[2] = q.z; n[3] = q.w;
+    slot[0] = 0; slot[1] = 1; slot[2] = 2; slot[3] = 3;
+    auto cx = [&](int a, int b) {
+        if (n[a] > n[b]) {
+            const int t = n[a]; n[a] = n[b]; n[b] = t;
+            const int u = slot[a]; slot[a] = slot[b]; slot[b] = u;
+        }
+    };
+    cx(0, 1); cx(2, 3); cx(0, 2); cx(1, 3); cx(1, 2);
+}
+
+// sort key of a tuple: the four indices in fields of `fb` bits, the smallest
+// node most significant
+__device__ __forceinline__ unsigned long long tuple_key(const int (&n)[4], int fb)
+{
+    return ((unsigned long long)n[0] << (3 * fb)) | ((unsigned long long)n[1] << (2 * fb)) |
+           ((unsigned long long)n[2] << fb) | (unsigned long long)n[3];
+}
+
+// ---- grouping by bucket sort: the points are counted into buckets by their
+// tuple's smallest node, placed (in any order) into their bucket's range,
+// and each bucket is then ordered by the rest of the tuple and the point
+// index.  The order equals that of a stable sort by the full tuple key. ----
+
+// the lanes of a warp with the same bucket add their count with one atomic:
+// returns each lane's position among the warp's lanes of its bucket, and the
+// bucket's base from the atomic (fill pass) or nothing (count pass)
+__device__ __forceinline__ int warp_bucket_add(int *ctr, int bucket, bool active)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, active ? bucket : -1);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (active && lane == leader) base = atomicAdd(ctr + bucket, __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void k_tb_count(const ushort4 *__restrict__ idx, int n, int *__restrict__ cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int t[4] = {0, 0, 0, 0}, sl[4];
+    if (i < n) tuple_of(idx[i], t, sl);
+    warp_bucket_add(cnt, t[0], i < n);
+}
+
+__global__ void k_tb_place(const ushort4 *__restrict__ idx, int n, const int *__restrict__ start,
+                           int *__restrict__ fill, uint32_t *__restrict__ order)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int t[4] = {0, 0, 0, 0}, sl[4];
+    if (i < n) tuple_of(idx[i], t, sl);
+    const int pos = warp_bucket_add(fill, t[0], i < n);
+    if (i < n) order[start[t[0]] + pos] = (uint32_t)i;
+}
+
+// one CTA per bucket: its points ordered by (the other three nodes, point
+// index) -- unique keys -- by a bitonic sort in shared memory over the
+// bucket padded to a power of two (TB_MAX at most); a larger bucket by ranks
+// against shared-memory tiles instead
+#define TB_T 256
+#define TB_MAX 2048
+__global__ void __launch_bounds__(TB_T) k_tb_sort(const ushort4 *__restrict__ idx, const int *__restrict__ start,
+                                                  int nb, int fb, const uint32_t *__restrict__ order,
+                                                  uint32_t *__restrict__ out)
+{
+    __shared__ unsigned long long s_key[TB_MAX];
+    __shared__ uint32_t s_pt[TB_MAX];
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int b0 = start[b], n = start[b + 1] - b0;
+    if (n == 0) return;
+    auto key3 = [&](uint32_t i) {
+        int t[4], sl[4];
+        tuple_of(idx[i], t, sl);
+        return ((unsigned long long)t[1] << (2 * fb)) | ((unsigned long long)t[2] << fb) | (unsigned long long)t[3];
+    };
+    // (key, point) before (key', point')
+    auto less = [](unsigned long long ka, uint32_t pa, unsigned long long kb, uint32_t pb) {
+        return ka < kb || (ka == kb && pa < pb);
+    };
+    if (n == 1) {
+        if (threadIdx.x == 0) out[b0] = order[b0];
+        return;
     }
-    __syncthreads();
-    const int cnt = 10 * min(EG_T, n - i0);
-    for (int k = threadIdx.x; k < cnt; k += EG_T) {
-        key[10L * i0 + k] = sk[k];
-        val[10L * i0 + k] = sv[k];
+    if (n <= TB_MAX) {
+        int P = 2;
+        while (P < n) P <<= 1;
+        for (int q = threadIdx.x; q < P; q += TB_T) {
+            if (q < n) {
+                const uint32_t pq = order[b0 + q];
+                s_pt[q] = pq;
+                s_key[q] = key3(pq);
+            } else {   // padding sorts last
+                s_pt[q] = 0xffffffffu;
+                s_key[q] = ~0ull;
+            }
+        }
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int q = threadIdx.x; q < P; q += TB_T) {
+                    const int o = q ^ j;
+                    if (o > q) {
+                        const bool up = (q & k) == 0;
+                        const unsigned long long kq = s_key[q], ko = s_key[o];
+                        const uint32_t pq = s_pt[q], po = s_pt[o];
+                        if (less(ko, po, kq, pq) == up) {
+                            s_key[q] = ko;
+                            s_key[o] = kq;
+                            s_pt[q] = po;
+                            s_pt[o] = pq;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int q = threadIdx.x; q < n; q += TB_T) out[b0 + q] = s_pt[q];
+        return;
+    }
+    for (int e0 = 0; e0 < n; e0 += TB_T) {
+        const int e = e0 + threadIdx.x;
+        uint32_t pi = 0;
+        unsigned long long ki = 0;
+        if (e < n) {
+            pi = order[b0 + e];
+            ki = key3(pi);
+        }
+        int rank = 0;
+        for (int t0 = 0; t0 < n; t0 += TB_MAX) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < TB_MAX && t0 + q < n; q += TB_T) {
+                const uint32_t pq = order[b0 + t0 + q];
+                s_pt[q] = pq;
+                s_key[q] = key3(pq);
+            }
+            __syncthreads();
+            if (e < n) {
+                const int lim = min(TB_MAX, n - t0);
+                for (int q = 0; q < lim; ++q) rank += less(s_key[q], s_pt[q], ki, pi);
+            }
+        }
+        if (e < n) out[b0 + rank] = pi;
     }
 }
 
-// first entry of every block in the sorted keys: the entry at each key change
-// starts the blocks (previous key, its key]; one extra thread closes the range
-// up to nnzb (start[nnzb] = ne); blocks without entries get empty ranges
-__global__ void k_ent_bounds(const uint32_t *__restrict__ key, int ne, int nnzb, int *__restrict__ start)
+// the incidences of every block in run order: counted by block, placed (in
+// any order), then each block's short list ordered by run (a run meets a
+// block at most once)
+__global__ void k_ic_count(int ne, const uint32_t *__restrict__ key, int *__restrict__ cnt)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e > ne) return;
-    const int cur = e < ne ? (int)key[e] : nnzb;
-    const int prev = e > 0 ? (int)key[e - 1] : -1;
-    for (int b = prev + 1; b <= cur; ++b) start[b] = e;
+    warp_bucket_add(cnt, e < ne ? (int)key[e] : 0, e < ne);
 }
 
-// chunks of <= ED_CHUNK entries, role 0 (moments), for every upper block and of
-// <= ED_CHUNK1 entries, role 1 (J^T r and the pose-node block), for diagonal
-// blocks; role-0 chunks first
-__global__ void k_chunk_count(int nnzb, const int *__restrict__ ent_start, int *__restrict__ cnt,
-                              const int *__restrict__ brow, const int *__restrict__ col, int *__restrict__ ccnt0,
-                              int *__restrict__ ccnt1)
+__global__ void k_ic_place(int ne, const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+                           const int *__restrict__ start, int *__restrict__ fill, uint32_t *__restrict__ out)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = e < ne ? (int)key[e] : 0;
+    const int pos = warp_bucket_add(fill, b, e < ne);
+    if (e < ne) out[start[b] + pos] = val[e];
+}
+
+// one warp per block: up to 64 incidences (two per lane) by a bitonic sort
+// over the warp on the run field; longer lists (rare) by insertion in place
+__global__ void __launch_bounds__(128) k_ic_sort(int nnzb, const int *__restrict__ start, uint32_t *__restrict__ list)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nnzb) return;
-    cnt[b] = ent_start[b + 1] - ent_start[b];
-    ccnt0[b] = col[b] >= brow[b] ? (cnt[b] + ED_CHUNK - 1) / ED_CHUNK : 0;
-    ccnt1[b] = col[b] == brow[b] ? (cnt[b] + ED_CHUNK1 - 1) / ED_CHUNK1 : 0;
-}
-
-// (queued before the host has the chunk totals: chunks beyond max_chunks are
-// not written and set the status; the padding chunks between the roles are
-// written empty here)
-__global__ void k_chunk_fill(int nnzb, const int *__restrict__ cnt, const int *__restrict__ ent_start,
-                             const int *__restrict__ brow, const int *__restrict__ col,
-                             const int *__restrict__ cstart0, const int *__restrict__ cstart1,
-                             int4 *__restrict__ chunks, int max_chunks, int *__restrict__ status)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n0 = cstart0[nnzb];
-    const int base1 = (n0 + 31) & ~31;   // role-1 chunks start warp-aligned
-    if (b < 32 && n0 + b < base1 && n0 + b < max_chunks) chunks[n0 + b] = make_int4(0, 0, 0, 0);
-    if (b >= nnzb || col[b] < brow[b]) return;
-    const int n = cnt[b];
-    for (int r = 0; r < (brow[b] == col[b] ? 2 : 1); ++r) {
-        const int size = r == 0 ? ED_CHUNK : ED_CHUNK1;
-        const int per = (n + size - 1) / size;
-        int q = r == 0 ? cstart0[b] : base1 + cstart1[b];
-        for (int k = 0; k < per; ++k, ++q) {
-            const int beg = ent_start[b] + k * size;
-            const int c = min(size, n - k * size);
-            if (q < max_chunks) chunks[q] = make_int4(b, beg, c, r);
-            else atomicCAS(status, ED_OK, ED_ERR_CAPACITY);
-        }
+    const int b0 = start[b], n = start[b + 1] - b0;
+    if (n <= 1) return;
+    if (n > 64) {
+        if (lane == 0)
+            for (int i = 1; i < n; ++i) {
+                const uint32_t v = list[b0 + i];
+                int j = i - 1;
+                while (j >= 0 && (list[b0 + j] >> 4) > (v >> 4)) {
+                    list[b0 + j + 1] = list[b0 + j];
+                    --j;
+                }
+                list[b0 + j + 1] = v;
+            }
+        return;
     }
+    // element q of 64 is held by lane q >> 1, slot q & 1; padding sorts last
+    uint32_t v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) v[u] = 2 * lane + u < n ? list[b0 + 2 * lane + u] : 0xffffffffu;
+    for (int k = 2; k <= 64; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            // the partners' values, all read before any slot changes: for j = 1
+            // the other slot of this lane, else lane ^ (j / 2), same slot
+            uint32_t w[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) w[u] = j == 1 ? v[u ^ 1] : __shfl_xor_sync(0xffffffffu, v[u], j >> 1);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int q = 2 * lane + u, o = q ^ j;
+                const bool up = (q & k) == 0, lower = q < o;
+                // lower element of an ascending pair keeps the smaller run, and so on
+                // (padding 0xffffffff has the largest run field)
+                const bool take = lower ? ((w[u] >> 4) < (v[u] >> 4)) == up : ((v[u] >> 4) < (w[u] >> 4)) == up;
+                if (take) v[u] = w[u];
+            }
+        }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (2 * lane + u < n) list[b0 + 2 * lane + u] = v[u];
 }
 
-// the finalisation's record of every upper block u, fixed for the frame (one
-// load for what the finalisation's warps would otherwise fetch in dependent
-// steps): {b, j, l, transpose position} and {first role-0 chunk, role-0
-// chunks, graph-edge flags (j -> l: 1, l -> j: 2), 0}; for a diagonal block
-// {b, j, j, row start} and {first role-0 chunk, role-0 chunks, first role-1
-// chunk, role-1 chunks | row length << 16}
+// low 32 bits of every point's key, value = point index (the first pass of a
+// two-pass stable sort by the full key)
+__global__ void k_tuple_lo(const ushort4 *__restrict__ idx, int n, int fb, uint32_t *__restrict__ key,
+                           uint32_t *__restrict__ val)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int t[4], sl[4];
+    tuple_of(idx[i], t, sl);
+    key[i] = (uint32_t)tuple_key(t, fb);
+    val[i] = (uint32_t)i;
+}
+
+// high bits of the key of the point at each position of the first pass
+__global__ void k_tuple_hi(const ushort4 *__restrict__ idx, int n, int fb, const uint32_t *__restrict__ val,
+                           uint32_t *__restrict__ key)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int t[4], sl[4];
+    tuple_of(idx[val[e]], t, sl);
+    key[e] = (uint32_t)(tuple_key(t, fb) >> 32);
+}
+
+// the points in tuple order (sorted position k holds point perm[k]): position,
+// normal, the tuple and the skinning weights in tuple order; flag[k] = 1 where
+// a run starts
+__global__ void k_tuple_gather(const uint32_t *__restrict__ val, int n, const ushort4 *__restrict__ idx,
+                               const float4 *__restrict__ w, const float4 *__restrict__ pos,
+                               const float4 *__restrict__ nrm, int *__restrict__ perm, float4 *__restrict__ spos,
+                               float4 *__restrict__ snrm, ushort4 *__restrict__ sidx, float4 *__restrict__ sw,
+                               ushort4 *__restrict__ sidx_d, float4 *__restrict__ sw_d, int *__restrict__ flag)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)val[k];
+    const ushort4 id = idx[i];
+    int t[4], sl[4];
+    tuple_of(id, t, sl);
+    const float4 wi = w[i];
+    const float wv[4] = {wi.x, wi.y, wi.z, wi.w};
+    perm[k] = i;
+    spos[k] = pos[i];
+    snrm[k] = nrm[i];
+    sidx[k] = make_ushort4((unsigned short)t[0], (unsigned short)t[1], (unsigned short)t[2], (unsigned short)t[3]);
+    sw[k] = make_float4(wv[sl[0]], wv[sl[1]], wv[sl[2]], wv[sl[3]]);
+    sidx_d[k] = id;   // (nearest first, as the graph holds them: the warp's summation order)
+    sw_d[k] = wi;
+    int start = 1;
+    if (k > 0) {
+        int tp[4], sp[4];
+        tuple_of(idx[val[k - 1]], tp, sp);
+        start = tp[0] != t[0] || tp[1] != t[1] || tp[2] != t[2] || tp[3] != t[3];
+    }
+    flag[k] = start;
+}
+
+// run r covers sorted positions [run_start[r], run_start[r + 1]); run_start[n_runs] = n;
+// run_of_start[k] = r where k starts run r, -1 elsewhere
+__global__ void k_run_starts(const int *__restrict__ flag, const int *__restrict__ pre, int n,
+                             int *__restrict__ run_start, int *__restrict__ run_of_start)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    run_of_start[k] = flag[k] ? pre[k] : -1;
+    if (flag[k]) run_start[pre[k]] = k;
+    if (k == n - 1) run_start[pre[n]] = n;
+}
+
+// the 10 incidences of every run: key = block of (tuple[s], tuple[t]) in the
+// BSR pattern, value = run << 4 | s << 2 | t (s <= t, so tuple[s] is the row
+// node: the block is upper or diagonal)
+__global__ void k_inc_gen(int n_runs, const int *__restrict__ run_start, const ushort4 *__restrict__ sidx,
+                          const int *__restrict__ row_ptr, const int *__restrict__ col, uint32_t *__restrict__ key,
+                          uint32_t *__restrict__ val, int *__restrict__ status)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_runs) return;
+    const ushort4 q = sidx[run_start[r]];
+    const int t4[4] = {q.x, q.y, q.z, q.w};
+    int e = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int t = s; t < 4; ++t) {
+            const int b = find_block(row_ptr, col, t4[s], t4[t]);
+            if (b < 0) atomicCAS(status, ED_OK, ED_ERR_STATE);
+            key[10L * r + e] = (uint32_t)(b < 0 ? 0 : b);
+            val[10L * r + e] = ((uint32_t)r << 4) | ((uint32_t)s << 2) | (uint32_t)t;
+            ++e;
+        }
+}
+
+
+// the assembly's record of every upper block u, fixed for the frame (one load
+// for what its warps would otherwise fetch in dependent steps):
+//   off-diagonal: {b, j, l, transpose position}, {first incidence, incidences,
+//                 graph-edge flags (j -> l: 1, l -> j: 2), 0}
+//   diagonal:     {b, j, j, row start}, {first incidence, incidences, row length, 0}
 __global__ void k_fin_pack(int nnzb, int m, int kg, const int *__restrict__ up_list, const int *__restrict__ flag_b,
                            const int *__restrict__ brow, const int *__restrict__ col, const int *__restrict__ tpos,
-                           const int *__restrict__ row_ptr, const int *__restrict__ cnt,
-                           const int *__restrict__ cstart0, const int *__restrict__ cstart1,
+                           const int *__restrict__ row_ptr, const int *__restrict__ inc_start,
                            const int *__restrict__ nbr, int4 *__restrict__ info)
 {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= m + flag_b[nnzb]) return;   // the upper-block count
     const int b = up_list[u];
-    const int j = brow[b], l = col[b], n = cnt[b];
-    const int c0 = cstart0[b], nch = (n + ED_CHUNK - 1) / ED_CHUNK;
+    const int j = brow[b], l = col[b];
+    const int i0 = inc_start[b], ni = inc_start[b + 1] - i0;
     if (j == l) {
-        const int base1 = (cstart0[nnzb] + 31) & ~31;   // role-1 chunks start warp-aligned
         const int rp0 = row_ptr[j], len = row_ptr[j + 1] - rp0;
         info[2 * u] = make_int4(b, j, l, rp0);
-        info[2 * u + 1] = make_int4(c0, nch, base1 + cstart1[b], ((n + ED_CHUNK1 - 1) / ED_CHUNK1) | (len << 16));
+        info[2 * u + 1] = make_int4(i0, ni, len, 0);
     } else {
         int flags = 0;
         for (int s = 0; s < kg; ++s) {
@@ -744,23 +981,8 @@ __global__ void k_fin_pack(int nnzb, int m, int kg, const int *__restrict__ up_l
             if (nbr[l * kg + s] == j) flags |= 2;
         }
         info[2 * u] = make_int4(b, j, l, tpos[b]);
-        info[2 * u + 1] = make_int4(c0, nch, flags, 0);
+        info[2 * u + 1] = make_int4(i0, ni, flags, 0);
     }
-}
-
-// per-entry geometry, fixed for the frame: geo[e] = (v_i - g_j, w_s w_t) for the
-// entry e (point i, slots s, t) of upper block (j, l)
-__global__ void k_entry_geo(int ne, const uint32_t *__restrict__ key, const uint32_t *__restrict__ ent,
-                            const int *__restrict__ brow, const float4 *__restrict__ pos, const float *__restrict__ wts,
-                            const float4 *__restrict__ g, float4 *__restrict__ geo)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    const uint32_t v = ent[e];
-    const int i = (int)(v >> 4), sr = (v >> 2) & 3, sc = v & 3;
-    const float4 gj = g[brow[key[e]]];
-    const float4 p = pos[i];
-    geo[e] = make_float4(p.x - gj.x, p.y - gj.y, p.z - gj.z, wts[4 * i + sr] * wts[4 * i + sc]);
 }
 
 // ---------------------------------------------------------------------------
@@ -873,8 +1095,9 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             int *cell_pick = ctx->cell_pick;
             unsigned *bar = (unsigned *)(ctx->misc + MI_BAR_GRAPH);
             int *status = ctx->misc + MI_STATUS;
+            unsigned long long wait_ns = ctx->wait_ns;
             void *args[] = {(void *)&P4, (void *)&bucket_c, (void *)&pstart_c, (void *)&misc_c, (void *)&fmisc_c,
-                            (void *)&cell_pick, (void *)&bar, (void *)&status};
+                            (void *)&cell_pick, (void *)&bar, (void *)&status, (void *)&wait_ns};
             ed_note_launch();
             ED_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_poisson_all, pick_grid, POISSON_T, args, 0, st));
         }
@@ -940,6 +1163,47 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
+    // ---- the points sorted by their node tuple, and the runs of equal tuples
+    // (queued before the node count is waited for: they need only the nearest
+    // nodes; the number of runs goes to the host with the block count) ----
+    {
+        int fb = 1;
+        while ((1 << fb) < max_nodes) ++fb;
+        const ushort4 *I4 = (const ushort4 *)graph->idx;
+        if ((long)NT <= 512L * max_nodes) {
+            // buckets by smallest node (a few hundred points each at the node
+            // densities of the path), each ordered by ranks
+            ED_CUDA_TRY(cudaMemsetAsync(ctx->bcnt, 0, sizeof(int) * 2 * ((size_t)max_nodes + 1), st));
+            int *bfill = ctx->bcnt + max_nodes + 1;
+            k_tb_count<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, ctx->bcnt); ed_note_launch();
+            ED_LAUNCH_CHECK();
+            if ((s = ed_scan_exclusive(ctx, ctx->bcnt, ctx->bstart, max_nodes, st)) != ED_OK) return s;
+            k_tb_place<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, ctx->bstart, bfill, ctx->ent_key); ed_note_launch();
+            k_tb_sort<<<max_nodes, TB_T, 0, st>>>(I4, ctx->bstart, max_nodes, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+            ED_LAUNCH_CHECK();
+        } else {
+            // few nodes for many points: large buckets; a stable radix sort by the full key
+            k_tuple_lo<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+            ED_LAUNCH_CHECK();
+            if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, NT, 4 * fb < 32 ? 4 * fb : 32, st)) != ED_OK)
+                return s;
+            if (4 * fb > 32) {
+                k_tuple_hi<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, fb, ctx->ent_val, ctx->ent_key); ed_note_launch();
+                ED_LAUNCH_CHECK();
+                if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, NT, 4 * fb - 32, st)) != ED_OK) return s;
+            }
+        }
+        const float4 *NR = ctx->n_kp > 0 ? (const float4 *)ctx->comb_nrm : (const float4 *)nrm;
+        k_tuple_gather<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->ent_val, NT, I4, (const float4 *)graph->weights, PT, NR,
+                                                           ctx->perm, ctx->spos, ctx->snrm, ctx->sidx, ctx->sw,
+                                                           ctx->sidx_d, ctx->sw_d, ctx->flag_a); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, NT, st)) != ED_OK) return s;
+        k_run_starts<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->flag_a, ctx->flag_b, NT, ctx->run_start,
+                                                         ctx->run_of_start); ed_note_launch();
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 1, ctx->flag_b + NT, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        ED_LAUNCH_CHECK();
+    }
     // every later launch on the caller's stream (and every return) follows the node graph
     ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
@@ -950,29 +1214,32 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
 
     // ---- block pattern ----
     const int words = ed_div_up(m, 32);
-    int nnzb;
+    int nnzb, n_runs;
     {
         ED_CUDA_TRY(cudaMemsetAsync(ctx->bitmap, 0, sizeof(uint32_t) * (size_t)m * words, st));
-        k_pairs_points<<<ed_div_up(NT, 256), 256, 0, st>>>((const ushort4 *)graph->idx, NT, ctx->bitmap, words); ed_note_launch();
+        // (the pairs of the points come from their runs: n_runs is on the device, the
+        // grid covers every point)
+        k_pairs_runs_dev<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->misc + MI_READ + 1, ctx->run_start, ctx->sidx,
+                                                             ctx->bitmap, words); ed_note_launch();
         k_pairs_graph<<<ed_div_up(m, 256), 256, 0, st>>>(graph->nbr, m, prm->k_graph, ctx->bitmap, words); ed_note_launch();
-        k_row_count<<<ed_div_up(m, 128), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
+        k_row_count<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->row_cnt, ctx->row_ptr, m, st)) != ED_OK) return s;
-        // the block count goes to the host (pinned copy + event) while the
-        // kernels that need only the row pointer run: the block lists and the
-        // (point, block) entries, both checking the count against the capacity
+        // the block count and the number of runs go to the host (pinned copy +
+        // event) while the block lists, which need only the row pointer, are
+        // filled (checking the count against the capacity)
         int *nz_host = ctx->pinned + ED_MAX_PCG_GRID + 6;
-        ED_CUDA_TRY(cudaMemcpyAsync(nz_host, ctx->row_ptr + m, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ, ctx->row_ptr + m, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        ED_CUDA_TRY(cudaMemcpyAsync(nz_host, ctx->misc + MI_READ, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
-        k_row_fill<<<ed_div_up(m, 128), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
-                                                      ctx->diag_pos, ctx->max_nnzb, ctx->misc + MI_STATUS); ed_note_launch();
-        k_entries_gen<<<ed_div_up(NT, EG_T), EG_T, 0, st>>>((const ushort4 *)graph->idx, NT, ctx->row_ptr, ctx->col,
-                                                          ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS, m,
-                                                          ctx->max_nnzb); ed_note_launch();
+        k_row_fill<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
+                                                    ctx->diag_pos, ctx->max_nnzb, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
-        nnzb = *nz_host;
+        nnzb = nz_host[0];
+        n_runs = nz_host[1];
         if (nnzb > ctx->max_nnzb) return ED_ERR_CAPACITY;
+        if (n_runs < 1 || n_runs > NT) return ED_ERR_STATE;
         k_tpos<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, nnzb, st)) != ED_OK) return s;
@@ -981,50 +1248,36 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH_CHECK();
     }
 
-    // ---- per-block point lists (stable: point order inside each block) ----
-    const int ne = 10 * NT;
-    int nchunks, n_upper = 0;
+    // ---- incidences (block, run), sorted by block (stable: run order within a
+    // block), and the assembly's per-block records ----
+    const int ne = 10 * n_runs;
+    int n_upper = 0;
     {
-        int bits = 1;
-        while ((1 << bits) < nnzb) ++bits;
-        if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, ne, bits, st)) != ED_OK) return s;
-        k_ent_bounds<<<ed_div_up(ne + 1, 256), 256, 0, st>>>(ctx->ent_key, ne, nnzb, ctx->ent_start); ed_note_launch();
-        k_chunk_count<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_start, ctx->ent_cnt, ctx->brow, ctx->col,
-                                                            ctx->chunk_cnt, ctx->chunk_cnt1); ed_note_launch();
+        k_inc_gen<<<ed_div_up(n_runs, 128), 128, 0, st>>>(n_runs, ctx->run_start, ctx->sidx, ctx->row_ptr, ctx->col,
+                                                          ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt, ctx->chunk_start, nnzb, st)) != ED_OK) return s;
-        if ((s = ed_scan_exclusive(ctx, ctx->chunk_cnt1, ctx->chunk_start1, nnzb, st)) != ED_OK) return s;
-        // one host read for what the rest of the build needs: chunk totals,
-        // upper-block count (gathered into misc) and the row pointer (pinned)
-        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ, ctx->chunk_start + nnzb, sizeof(int), cudaMemcpyDeviceToDevice, st));
-        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 1, ctx->chunk_start1 + nnzb, sizeof(int),
-                                    cudaMemcpyDeviceToDevice, st));
+        // by block, each block's list in run order
+        ED_CUDA_TRY(cudaMemsetAsync(ctx->icnt, 0, sizeof(int) * 2 * (size_t)(nnzb + 1), st));
+        int *ifill = ctx->icnt + nnzb + 1;
+        k_ic_count<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->icnt); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        if ((s = ed_scan_exclusive(ctx, ctx->icnt, ctx->ent_start, nnzb, st)) != ED_OK) return s;
+        k_ic_place<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->ent_start, ifill, ctx->inc); ed_note_launch();
+        k_ic_sort<<<ed_div_up(nnzb, 4), 128, 0, st>>>(nnzb, ctx->ent_start, ctx->inc); ed_note_launch();
+        k_fin_pack<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow,
+                                                         ctx->col, ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr,
+                                                         ctx->fin_info); ed_note_launch();
+        ED_LAUNCH_CHECK();
+        // one host read for what the rest of the build needs: the upper-block
+        // count (gathered into misc) and the row pointer (pinned)
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 2, ctx->flag_b + nnzb, sizeof(int), cudaMemcpyDeviceToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->row_ptr_host, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
-        // the chunk table and the entry geometry need no host value: queued
-        // before the wait (the chunk table checks its capacity itself)
-        k_chunk_fill<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->ent_cnt, ctx->ent_start, ctx->brow, ctx->col,
-                                                           ctx->chunk_start, ctx->chunk_start1, ctx->chunks,
-                                                           ctx->max_chunks, ctx->misc + MI_STATUS); ed_note_launch();
-        k_entry_geo<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->brow, PT, graph->weights,
-                                                         G4, ctx->ent_geo); ed_note_launch();
-        k_fin_pack<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow,
-                                                         ctx->col, ctx->tpos, ctx->row_ptr, ctx->ent_cnt,
-                                                         ctx->chunk_start, ctx->chunk_start1, graph->nbr,
-                                                         ctx->fin_info); ed_note_launch();
-        ED_LAUNCH_CHECK();
         ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
         memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
-        const int nc01[2] = {hm[MI_READ], hm[MI_READ + 1]};
         n_upper = hm[MI_READ + 2];
         if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
-        const int base1 = (nc01[0] + 31) & ~31;
-        nchunks = base1 + nc01[1];
-        ctx->n_chunks0 = nc01[0];
-        ctx->chunk_base1 = base1;
-        if (nchunks > ctx->max_chunks) return ED_ERR_CAPACITY;
         ctx->pinned[ED_MAX_PCG_GRID + 1] = nnzb;
         ctx->pinned[ED_MAX_PCG_GRID + 2] = 0;
         ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, ctx->pinned + ED_MAX_PCG_GRID + 1, 2 * sizeof(int),
@@ -1047,8 +1300,8 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     ctx->m = m;
     ctx->nnzb = nnzb;
     ctx->n_upper = n_upper;
-    ctx->n_entries = ne;
-    ctx->n_chunks = nchunks;
+    ctx->n_entries = 10 * NT;
+    ctx->n_runs = n_runs;
     ctx->have_graph = 1;
     return ED_OK;
 }

@@ -3,9 +3,9 @@
 //
 // Some callers of this library cannot call cudaMalloc at all: code running
 // inside a host framework that owns every device allocation (a plugin that
-// may only touch the buffers it is handed), code that runs while a CUDA graph
-// is being captured, or a real-time loop that forbids allocation after start
-// up.  ed_energy_noalloc serves them: it needs no context and no workspace.
+// may only touch the buffers it is handed), or a real-time loop that forbids
+// allocation after start up.  ed_energy_noalloc serves them: it needs no
+// context and no workspace.
 // Its only scratch -- the per-CTA partial sums of the reduction -- lives in a
 // fixed-size array in device global memory, defined at file scope below.
 // Every GPU that loads the library holds that array until the process exits.
@@ -118,17 +118,26 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_nodes(int m, int kg, const in
     }
 }
 
-// partial sums in CTA order, pose priors, six outputs
-__global__ void k_na_final(const double *__restrict__ pp, int np, const double *__restrict__ pn, int nn,
-                           const double *__restrict__ pose, ed_solver_params prm, double *__restrict__ out)
+// the partial sums (lane k adds the CTAs k, k + 32, ... in order, then a
+// fixed butterfly over the warp: deterministic), pose priors, six outputs
+__global__ void __launch_bounds__(32) k_na_final(const double *__restrict__ pp, int np, const double *__restrict__ pn,
+                                                 int nn, const double *__restrict__ pose, ed_solver_params prm,
+                                                 double *__restrict__ out)
 {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     double ed = 0.0, erot = 0.0, ereg = 0.0, er = 0.0, ep = 0.0;
-    for (int b = 0; b < np; ++b) ed += pp[2 * b];
-    for (int b = 0; b < nn; ++b) {
+    for (int b = lane; b < np; b += 32) ed += pp[2 * b];
+    for (int b = lane; b < nn; b += 32) {
         erot += pn[2 * b];
         ereg += pn[2 * b + 1];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ed += __shfl_xor_sync(0xffffffffu, ed, o);
+        erot += __shfl_xor_sync(0xffffffffu, erot, o);
+        ereg += __shfl_xor_sync(0xffffffffu, ereg, o);
+    }
+    if (lane != 0) return;
     for (int q = 0; q < 6; ++q) {
         const double d = pose[q] - prm.prior[q];
         if (q < 3) er += prm.w_r * d * d;

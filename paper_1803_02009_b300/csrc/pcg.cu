@@ -53,12 +53,15 @@ struct PcgArgs {
     int load_before_wait;    // 1: the set-up's loads come before the wait for the stream predecessor (which
                              // then must be k_fin_totals: everything these loads read is two kernels back)
     unsigned *bar;           // arrival count
+    unsigned bar_extra;      // arrivals expected beyond the CTAs (0; > 0 only in tests of the bounded wait)
+    unsigned long long wait_ns;   // limit of every device wait
     int *status;
     ed_stats *stats;
 };
 
 // Accumulation of the PCG dot products and norms.  FP32 mode: float.  Mixed
-// mode: float-float (hi + lo, about 44 significant bits) on the FP32 pipe --
+// FP64 mode: double.  Mixed mode: float-float (hi + lo, about 44 significant
+// bits) on the FP32 pipe --
 // each product is formed exactly (a b = p + e with e = fma(a, b, -p)) and
 // summed by error-free two-sums; on B300 the FP64 rate is a small fraction of
 // the FP32 rate, so the extended precision is kept off the FP64 units (the
@@ -74,6 +77,18 @@ template <> struct PcgAcc<float> {
     static __device__ __forceinline__ T shfl(T x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
     static __device__ __forceinline__ T shfl_down(T x, int o) { return __shfl_down_sync(0xffffffffu, x, o); }
     static __device__ __forceinline__ float to_float(T x) { return x; }
+};
+
+// FP64 accumulation (ED_PRECISION_MIXED_FP64): products and sums in double
+struct PcgFp64 {};
+template <> struct PcgAcc<PcgFp64> {
+    typedef double T;
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T madd(T acc, float a, float b) { return fma((double)a, (double)b, acc); }
+    static __device__ __forceinline__ T add(T x, T y) { return x + y; }
+    static __device__ __forceinline__ T shfl(T x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+    static __device__ __forceinline__ T shfl_down(T x, int o) { return __shfl_down_sync(0xffffffffu, x, o); }
+    static __device__ __forceinline__ float to_float(T x) { return (float)x; }
 };
 
 template <> struct PcgAcc<double> {
@@ -386,7 +401,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             }
         }
     }
-    if (!ed_mbar_wait(&s_mbar[0], 0)) {
+    // (after a wait that gave up, the copies still in flight are waited for
+    // with the default limit, which a shortened wait limit does not shorten)
+    if (!ed_mbar_wait(&s_mbar[0], 0, a.wait_ns)) {
         atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
         ed_mbar_wait(&s_mbar[0], 0);
         ed_mbar_wait(&s_mbar[1], 0);
@@ -488,7 +505,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         AT vv[1] = {rr0};
         block_sum_n<DT, NT, 1>(vv, s_red);
         if (t == 0) *part_at<DT>(a.part, 0, cta) = block_sum_get<DT, NT>(s_red, 0);
-        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
+        if (!ed_grid_sync(a.bar, a.status, nb + a.bar_extra, target, &s_flag, a.wait_ns)) {
             fail();
             return;
         }
@@ -556,7 +573,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         double *part = a.part + (size_t)(it & 1) * ED_MAX_PCG_GRID * PCG_NC;   // partials (double buffer)
         __syncthreads();
         if (!h_ready) {   // the blocks, copied during the set-up
-            if (!ed_mbar_wait(&s_mbar[1], 0)) {
+            if (!ed_mbar_wait(&s_mbar[1], 0, a.wait_ns)) {
                 atomicCAS(a.status, ED_OK, ED_ERR_TIMEOUT);
                 ed_mbar_wait(&s_mbar[1], 0);
                 fail();
@@ -653,7 +670,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
             block_sum_bfly<DT, NT, PCG_NC>(vv, s_red);
             if (t < PCG_NC) *part_at<DT>(part, t, cta) = block_sum_get<DT, NT>(s_red, t);
         }
-        if (!ed_grid_sync(a.bar, a.status, nb, target, &s_flag)) {
+        if (!ed_grid_sync(a.bar, a.status, nb + a.bar_extra, target, &s_flag, a.wait_ns)) {
             fail();
             return;
         }
@@ -754,8 +771,12 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
     __syncthreads();
     // solution of the CTA's rows (and of the pose: CTA 0), and the update
     // x += d, pose += d_pose unless the solve broke down.  No wait follows the
-    // last barrier, so either every CTA gets here or none does: the update is
-    // never partial.
+    // last barrier, so in normal operation either every CTA gets here or none
+    // does; an error reported meanwhile (a wait elsewhere that ran out) also
+    // withholds the update.
+    if (t == 0) s_flag = *(volatile int *)a.status == ED_OK;
+    __syncthreads();
+    if (!s_flag) breakdown = true;
     for (int i = t; i < rows * 12; i += NT) {
         const size_t gi = 12 * (size_t)r0 + i;
         const float dv = ds[i];
@@ -826,6 +847,10 @@ static ed_status pcg_set_attributes()
     ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
     ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<PcgFp64, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg<PcgFp64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<PcgFp64, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch<PcgFp64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, small));
     g_attr_done[dev] = true;
     return ED_OK;
 }
@@ -893,7 +918,7 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
 {
     if (!x || !pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
     a.x = x;
-    a.xm = prm->precision == ED_PRECISION_MIXED ? xm : nullptr;
+    a.xm = ed_is_mixed(prm->precision) ? xm : nullptr;
     a.pose = pose;
     const size_t P = ctx->vec_stride;
     a.m = ctx->m;
@@ -915,6 +940,8 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     a.s1 = ctx->vec + 4 * P;
     a.part = ctx->pcg_part;
     a.bar = (unsigned *)(ctx->misc + MI_BAR);
+    a.bar_extra = (unsigned)ctx->bar_extra;
+    a.wait_ns = ctx->wait_ns;
     a.status = ctx->misc + MI_STATUS;
     a.stats = stats;
     a.load_before_wait = 0;
@@ -948,7 +975,6 @@ static cudaError_t launch_coop(const void *fn, int grid, int nt, void **args, si
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,
                        ed_stats *stats, cudaStream_t st)
 {
-    const bool mixed = prm->precision == ED_PRECISION_MIXED;
     if (ctx->pcg.grid <= 0) return ED_ERR_STATE;
     PcgArgs a;
     ed_status s = pcg_fill_args(ctx, ctx->pcg, ctx->pcg_rows, prm, x, xm, pose, stats, a);
@@ -960,7 +986,9 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, d
     void *args[] = {&a};
     ed_tm_begin(ctx, ED_KERNEL_PCG, st);
     ed_note_launch();
-    const void *fn = mixed ? (const void *)k_pcg<double, 512> : (const void *)k_pcg<float, 512>;
+    const void *fn = prm->precision == ED_PRECISION_MIXED        ? (const void *)k_pcg<double, 512>
+                     : prm->precision == ED_PRECISION_MIXED_FP64 ? (const void *)k_pcg<PcgFp64, 512>
+                                                                 : (const void *)k_pcg<float, 512>;
     cudaError_t e = launch_coop(fn, ctx->pcg.grid, 512, args, ctx->pcg.smem, st, true);
     ed_tm_end(ctx, ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
@@ -1034,13 +1062,13 @@ ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t 
                              cudaStream_t st)
 {
     const int count = bp->count;
-    const bool mixed = prm[0]->precision == ED_PRECISION_MIXED;
+    const int prec = prm[0]->precision;
     PcgBatchParams b;
     memset(&b, 0, sizeof(b));
     b.count = count;
     for (int p = 0; p <= count; ++p) b.cta_first[p] = bp->cta_first[p];
     for (int p = 0; p < count; ++p) {
-        if ((prm[p]->precision == ED_PRECISION_MIXED) != mixed) return ED_ERR_ARG;
+        if (prm[p]->precision != prec) return ED_ERR_ARG;
         ed_status s = pcg_fill_args(ctxs[p], bp->plan[p], ctxs[p]->pcg_rows_b, prm[p], x[p], xm[p], pose[p], stats[p],
                                     b.probs[p]);
         if (s != ED_OK) return s;
@@ -1048,8 +1076,14 @@ ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t 
     }
     void *args[] = {&b};
     const void *fn;
-    if (bp->nt == 512) fn = mixed ? (const void *)k_pcg_batch<double, 512> : (const void *)k_pcg_batch<float, 512>;
-    else fn = mixed ? (const void *)k_pcg_batch<double, 256> : (const void *)k_pcg_batch<float, 256>;
+    if (bp->nt == 512)
+        fn = prec == ED_PRECISION_MIXED        ? (const void *)k_pcg_batch<double, 512>
+             : prec == ED_PRECISION_MIXED_FP64 ? (const void *)k_pcg_batch<PcgFp64, 512>
+                                               : (const void *)k_pcg_batch<float, 512>;
+    else
+        fn = prec == ED_PRECISION_MIXED        ? (const void *)k_pcg_batch<double, 256>
+             : prec == ED_PRECISION_MIXED_FP64 ? (const void *)k_pcg_batch<PcgFp64, 256>
+                                               : (const void *)k_pcg_batch<float, 256>;
     ed_note_launch();
     cudaError_t e = launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st, false);
     if (e != cudaSuccess) {

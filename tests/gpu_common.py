@@ -1,6 +1,8 @@
 """Shared set-up of the GPU parity tests: the same seeded scene goes to the
 CUDA path (through the C ABI) and to the FP64 oracle."""
 import functools
+import json
+import os
 
 import numpy as np
 
@@ -81,3 +83,25 @@ def blocks_dict(row_ptr, col, blk):
         for t in range(row_ptr[j], row_ptr[j + 1]):
             out[(j, int(col[t]))] = blk[t]
     return out
+
+
+def report(name, data):
+    """Prints a test's figures and, with ED_REPORT_DIR set, writes them there as JSON."""
+    d = os.environ.get("ED_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, name + ".json"), "w") as f:
+            json.dump(data, f, indent=1, default=float)
+    print(name, json.dumps(data, default=float))
+
+
+def block_errors(got, ref, floor_rel=1e-6):
+    """Per 12x12 block: the largest entry error over the block's own largest
+    entry (blocks of the FP32 system against the FP64 one).  A block whose
+    entries are all (near) zero is measured against floor_rel times the
+    largest entry of the whole system."""
+    got = np.asarray(got, dtype=np.float64).reshape(len(ref), -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(len(ref), -1)
+    # (an all-zero reference must be matched by zeros: any other value fails)
+    scale = np.maximum(np.maximum(np.abs(ref).max(1), floor_rel * np.abs(ref).max()), 1e-30)
+    return np.abs(got - ref).max(1) / scale

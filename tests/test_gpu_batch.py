@@ -207,3 +207,62 @@ def test_batch_member_matches_oracle_one_step(batch_env):
     x_ref = p["x0"].astype(np.float64) + d[:12 * m].reshape(m, 12)
     assert _close(env["xs"][k].cpu().numpy(), x_ref, C.TOL_X)
     assert _close(env["poses"][k].cpu().numpy(), p["pose0"] + d[12 * m:], C.TOL_X)
+
+
+def test_batch_full_size_members_match_oracle():
+    """A batch with members of the batched workload's larger sizes: a 640x480
+    problem with 2048 Poisson nodes, a 1280x720 problem with 4096 nodes and a
+    160x120 grid problem.  After one batched iteration under the default
+    schedule every member's association, energy and update are checked
+    against the oracle's FP64 normal equations and block-Jacobi PCG at the
+    GPU's association (the CTA shares of the larger members are the ones the
+    1280x720 / 4096-node sizes produce)."""
+    torch, E = _torch(), _E()
+    scenes = [C.scene("tissue_640x480_n2048"), C.scene("tissue_1280x720_n4096"), C.scene("tissue_160x120_n64")]
+    probs = []
+    for k, s in enumerate(scenes):
+        m = None if s.nodes is not None else s.cfg.node_count
+        G = C.gpu_setup(s, radius=None if m is None else C.radius_for(s.cfg.name), max_nodes=m)
+        rng = np.random.default_rng(200 + k)
+        mm = G["graph"].m
+        x0 = np.zeros((mm, 12))
+        x0[:, [0, 5, 10]] = 1.0
+        x0 = (x0 + rng.normal(0, 1e-3, x0.shape)).astype(np.float32)
+        pose0 = np.asarray(s.pose_prior) + rng.normal(0, 1e-3, 6)
+        prm = E.SolverParams(n_pcg=10, prior=tuple(float(v) for v in s.pose_prior))
+        wpos = torch.empty((s.N, 4), dtype=torch.float32, device="cuda")
+        wnrm = torch.empty_like(wpos)
+        pix = torch.empty(s.N, dtype=torch.int32, device="cuda")
+        G["ctx"].set_debug(wpos, wnrm, pix)
+        probs.append(dict(s=s, G=G, x0=x0, pose0=pose0, prm=prm, wpos=wpos, wnrm=wnrm, pix=pix))
+    B = E.Batch([p["G"]["ctx"] for p in probs])
+    xs = [torch.from_numpy(p["x0"]).cuda() for p in probs]
+    poses = [torch.from_numpy(p["pose0"].copy()).cuda() for p in probs]
+    stats = [E.new_stats(1) for _ in probs]
+    B.bind([p["G"]["frame"] for p in probs], [p["prm"] for p in probs], xs, poses, stats=stats)
+    B.gn_step()
+    torch.cuda.synchronize()
+    figures = {}
+    for k, p in enumerate(probs):
+        s, G = p["s"], p["G"]
+        G["ctx"].set_debug(None, None, None)
+        pix = p["pix"].cpu().numpy()
+        ref_pix = oracle.associate_f32(p["wpos"].cpu().numpy(), p["wnrm"].cpu().numpy(), s.tgt_depth,
+                                       G["nmap"].cpu().numpy(), s.intr)
+        assert np.array_equal(ref_pix, pix), k
+        P = C.oracle_problem_from_gpu(s, G)
+        Q = oracle.NormalEq(P, p["x0"].astype(np.float64), p["pose0"], pix_in=pix)
+        st = E.read_stats(stats[k])[0]
+        assert st["status"] == 0 and st["n_valid"] == Q.n_valid, k
+        assert st["energy"] == pytest.approx(Q.energy, rel=C.TOL_E), k
+        d, _, _, _ = Q.pcg(-Q.g, p["prm"].n_pcg, jitter=p["prm"].jitter)
+        m = P.m
+        x_ref = p["x0"].astype(np.float64) + d[:12 * m].reshape(m, 12)
+        xg = xs[k].cpu().numpy()
+        err = (np.abs(xg - x_ref) / np.maximum(1.0, np.abs(x_ref))).max()
+        figures[s.cfg.name] = dict(nodes=int(m), points=int(s.N), x_max_rel=float(err),
+                                   energy_rel=float(abs(st["energy"] - Q.energy) / Q.energy))
+        assert err <= C.TOL_X, (k, err)
+        assert _close(poses[k].cpu().numpy(), p["pose0"] + d[12 * m:], C.TOL_X), k
+    figures["schedule"] = B.schedule()
+    C.report("batch_full_size_members", figures)

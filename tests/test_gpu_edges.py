@@ -170,7 +170,7 @@ def test_block_capacity_is_an_error_not_a_fault():
     assert G["graph"].m > 0
 
 
-@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_fp64"])
 def test_zero_pcg_iterations_keep_the_parameters_and_report_b(precision):
     # n_pcg = 0: no PCG iteration, x and the pose unchanged, d = 0; ||b||
     # (the norm of the assembled gradient) is still reported, the same as a
@@ -179,7 +179,8 @@ def test_zero_pcg_iterations_keep_the_parameters_and_report_b(precision):
     s = C.scene(SMALL)
     G = C.gpu_setup(s)
     ctx, m = G["ctx"], G["graph"].m
-    prec = E.ED_PRECISION_MIXED if precision == "mixed" else E.ED_PRECISION_FP32
+    prec = {"fp32": E.ED_PRECISION_FP32, "mixed": E.ED_PRECISION_MIXED,
+            "mixed_fp64": E.ED_PRECISION_MIXED_FP64}[precision]
     x = ctx.identity_x()
     xm = x.double().clone()
     pose = torch.zeros(6, dtype=torch.float64, device="cuda")

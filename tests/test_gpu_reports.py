@@ -6,11 +6,12 @@ the oracle's FP64 energy (h = 1e-4) at 100 seeded node coordinates and the 6
 pose coordinates, and against the J^T r that the Gauss-Newton step assembles
 with its own kernels.
 
-Precision (160x120 over the whole 5-iteration trajectory, 1280x720 / 4096
-nodes for one iteration): plain FP32 and the mixed form (float-float PCG
-dot products, FP64 node-parameter master copy, compensated block reductions), each
-result's error against the oracle stated: energy, node parameters, warped
-points in mm.
+Precision (160x120 over the whole 5-iteration trajectory, 640x480 / 2048
+nodes over 3 iterations, 1280x720 / 4096 nodes for one iteration): plain
+FP32 and the two mixed forms (compensated block reductions and an FP64
+node-parameter master copy, with the PCG dot products and norms in
+float-float or in FP64), each result's error against the oracle stated:
+energy, node parameters, warped points in mm.
 
 With ED_REPORT_DIR set, every test also writes its figures there as JSON."""
 import json
@@ -139,7 +140,9 @@ def test_differentiation_full_size():
     assert rep["oracle_vs_fd_max_err_over_scale"] <= 1e-6
     assert rep["gpu_vs_fd_max_err_over_scale"] <= 3e-4
     assert rep["gpu_vs_oracle_grad_max_err_over_scale"] <= 3e-4
-    assert rep["backward_vs_2JTr_max_err_over_scale"] <= 3e-4
+    # the step and the energy take the same association from the same FP32 warp,
+    # and both sum the same products: they agree far below the FP32 accumulation error
+    assert rep["backward_vs_2JTr_max_err_over_scale"] <= 1e-5
 
 
 def _trajectory_errors(name, precision, n_it, radius=None, max_nodes=None):
@@ -186,12 +189,13 @@ def _trajectory_errors(name, precision, n_it, radius=None, max_nodes=None):
     return rows
 
 
-@pytest.mark.parametrize("name,n_it", [(SMALL, 5), (LARGE, 1)])
+@pytest.mark.parametrize("name,n_it", [(SMALL, 5), (METRIC, 3), (LARGE, 1)])
 def test_precision_report(name, n_it):
     out = {}
-    for precision, label in ((0, "fp32"), (1, "mixed")):
-        if name == LARGE:
-            rows = _trajectory_errors(name, precision, n_it, radius=C.radius_for(LARGE), max_nodes=4096)
+    for precision, label in ((0, "fp32"), (1, "mixed"), (2, "mixed_fp64")):
+        if name != SMALL:
+            m = 4096 if name == LARGE else 2048
+            rows = _trajectory_errors(name, precision, n_it, radius=C.radius_for(name), max_nodes=m)
         else:
             rows = _trajectory_errors(name, precision, n_it)
         out[label] = {"per_iteration": rows,

@@ -1,8 +1,8 @@
 """The allocation-free energy entry point against the context-based one.
 
 ed_energy_noalloc exists for callers that cannot allocate device memory
-(they are handed their buffers by a host framework, run during stream
-capture, or forbid allocation after start-up).  It keeps its reduction
+(they are handed their buffers by a host framework, or forbid allocation
+after start-up).  It keeps its reduction
 scratch in a fixed array inside the library; this test calls it through the
 C ABI twice in a row (the second call reuses the array the first one left
 behind) and checks both results against ed_energy within the energy
