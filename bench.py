@@ -36,6 +36,12 @@ METRIC = "ED Gauss-Newton iters/s @640x480, 2048 nodes; fraction of HBM roofline
 WORKLOAD = "tissue_640x480_n2048"
 
 
+def metric_for(W, H, nodes):
+    """The headline metric's name for a workload of W x H pixels and this many
+    nodes (the 640x480 / 2048-node workload gives METRIC itself)."""
+    return f"ED Gauss-Newton iters/s @{W}x{H}, {nodes} nodes; fraction of HBM roofline"
+
+
 
 @contextlib.contextmanager
 def gc_paused():
@@ -57,11 +63,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=WORKLOAD)
-    ap.add_argument("--workload", default="single", choices=["single", "batch16", "push_sequence"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch16", "push_sequence", "grad"],
                     help="batch16: 16 independent problems (320x240 / 640x480 / 1280x720, 200-4096 nodes) "
                          "as one batched, graph-captured GN iteration vs 16 sequential solves; push_sequence: "
                          "the frame loop (registration, fusion, downsampling, node regeneration) over a "
-                         "synthetic 640x480 push sequence, one frame per step")
+                         "synthetic 640x480 push sequence, one frame per step; grad: the differentiable "
+                         "energy, forward (ed_energy) and hand-written backward (ed_energy_grad), per step")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "mixed_fp64"],
                     help="mixed: float-float PCG dot products; mixed_fp64: FP64 PCG dot products (both with "
                          "compensated block reductions and FP64 master parameters)")
@@ -468,8 +475,8 @@ def run_ours(args, rank, world, local):
             traffic = tr.get("bytes_per_launch")
 
     out = {
-        "metric": METRIC, "value": value, "unit": "GN iters/s", "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True,
+        "metric": metric_for(W, H, cfg.node_count), "value": value, "unit": "GN iters/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f32+f64",
         "data": "synthetic (seeded stereo-scope tissue scene, no dataset)",
@@ -515,6 +522,157 @@ def kernel_rev():
         with open(os.path.join(d, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+# differentiation: forward energy + hand-written backward
+# ----------------------------------------------------------------------------
+
+def grad_bytes(n_points, n_valid, m):
+    """Algorithmic bytes of one evaluation: the forward point pass (position,
+    normal, node indices: 40 B per point, + depth and target normal 20 B per
+    associated point, association 4 B out), the backward point pass (the same
+    40 B + association 4 B in, two 16 B records out) and the per-node gradient
+    kernel (every point once for each of its 4 nodes: sorted position 4 B,
+    record 16 B, position 16 B, node indices 8 B; 48 B of parameters and 48 B
+    of gradient per node)."""
+    fwd = n_points * 44 + n_valid * 20
+    bwd = n_points * (44 + 32) + n_valid * 20
+    nodes = 4 * n_points * 44 + m * 96
+    return fwd, bwd, nodes
+
+
+def run_grad(args, rank, world, local):
+    import torch
+    import paper_1803_02009_b300 as E
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = synth.make_scene(args.config, seed=rank_seed(rank))
+    cfg = s.cfg
+    fx, fy, cx, cy, W, H = s.intr
+    dev = "cuda"
+    ctx = E.Context(max_points=s.N, max_nodes=max(cfg.node_count, 64), max_width=W, max_height=H,
+                    max_cells=1 << 24)
+    pos = torch.from_numpy(s.model_pos).to(dev)
+    nrm = torch.from_numpy(s.model_nrm).to(dev)
+    depth = torch.from_numpy(s.tgt_depth).to(dev)
+    nmap = ctx.compute_normals(depth, s.intr, cfg.normal_half_width)
+    frame = E.make_frame(depth, nmap, s.intr)
+    radius = E.calibrate_radius(ctx, pos, nrm, cfg.node_count)
+    g = ctx.build_graph(pos, nrm, node_radius=radius, max_nodes=cfg.node_count, sigma=radius)
+    prm = E.SolverParams(n_pcg=cfg.n_pcg, prior=tuple(float(v) for v in s.pose_prior))
+    # the evaluation point: three Gauss-Newton steps from the identity (a
+    # representative association), then fixed
+    x = ctx.identity_x()
+    pose = torch.tensor(s.pose_prior, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        ctx.gn_step(frame, prm, x, pose)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    e_out = torch.empty(6, dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.energy(frame, prm, x, pose, out=e_out)
+        return ctx.energy_grad(frame, prm, x, pose)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    tm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    ctx.set_timing(E.ED_KERNEL_GRAD, tm_ev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = E.launch_count()
+    step_ms = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with gc_paused():
+        for k in range(K):
+            flush.fill_(k & 0xff)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            step()
+            ev1.record()
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    launches = E.launch_count() - l0
+    clk = clocks.stop()
+    n_rec = ctx.timing_count()
+    ctx.set_timing(E.ED_KERNEL_GRAD, [])
+
+    # end to end: the node parameters and the pose come from pinned host
+    # memory every step, the energy and both gradients go back to it
+    h_x = x.cpu().pin_memory()
+    h_pose = pose.cpu().pin_memory()
+    h_e = torch.empty(6, dtype=torch.float64).pin_memory()
+    h_gx = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+    h_gp = torch.empty(6, dtype=torch.float32).pin_memory()
+    d_x, d_pose = torch.empty_like(x), torch.empty_like(pose)
+
+    def e2e_step():
+        d_x.copy_(h_x, non_blocking=True)
+        d_pose.copy_(h_pose, non_blocking=True)
+        ctx.energy(frame, prm, d_x, d_pose, out=e_out)
+        gx, gp = ctx.energy_grad(frame, prm, d_x, d_pose)
+        h_e.copy_(e_out, non_blocking=True)
+        h_gx.copy_(gx, non_blocking=True)
+        h_gp.copy_(gp, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    with gc_paused():
+        for k in range(K):
+            flush.fill_(k & 0xff)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            e2e_step()
+            ev1.record()
+            ev1.synchronize()
+            e2e_ms.append(ev0.elapsed_time(ev1))
+    e2e_value = world * K / max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
+    h2d = h_x.numel() * 4 + h_pose.numel() * 8
+    d2h = h_e.numel() * 8 + h_gx.numel() * 4 + h_gp.numel() * 4
+    kern_us = statistics.median([tm_ev[2 * i].elapsed_time(tm_ev[2 * i + 1]) * 1e3 for i in range(n_rec)])
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = world * K / total_s
+    st = E.new_stats()
+    ctx.gn_step(frame, prm, x.clone(), pose.clone(), stats=st)   # (only to read the association's size)
+    n_valid = E.read_stats(st)[0]["n_valid"]
+    fwd, bwd, nodes_b = grad_bytes(s.N, n_valid, g.m)
+    peak, peak_kind = measured_peaks()
+    achieved = nodes_b / (kern_us * 1e-6) / 1e9
+    return {
+        "metric": f"ED energy + gradient evaluations/s @{W}x{H}, {cfg.node_count} nodes "
+                  "(forward + hand-written backward)",
+        "value": value, "unit": "evaluations/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_s * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded stereo-scope tissue scene, no dataset)",
+        "config": {"workload": args.config, "model_points": s.N, "nodes": g.m, "unknowns": 12 * g.m + 6,
+                   "evaluation_point": "after 3 Gauss-Newton steps from the identity",
+                   "skinning_weights": "recomputed from the node indices in both passes (not stored)",
+                   "l2": "flushed between steps (512 MB write)"},
+        "gpu_launches": launches, "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "evaluations/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "node parameters and pose copied in from pinned host memory every step, energy and "
+                        "gradients copied back; L2 flushed before every step (outside the events)"},
+        "algorithmic_bytes": {"forward": fwd, "backward_points": bwd, "backward_nodes": nodes_b,
+                              "valid_points": n_valid},
+        "roofline": {"kernel": "k_grad_nodes (per-node gradient)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "avg_launch_us": kern_us, "launches_timed": n_rec, "traffic": None},
+        "evaluation_roofline": {"bound": "hbm", "algorithmic_bytes": fwd + bwd + nodes_b,
+                                "achieved": (fwd + bwd + nodes_b) * value / world / 1e9, "peak": peak,
+                                "frac": (fwd + bwd + nodes_b) * value / world / 1e9 / peak, "unit": "GB/s"},
+    }
 
 
 # ----------------------------------------------------------------------------
@@ -632,6 +790,65 @@ def run_batch(args, rank, world, local):
     gn_bytes = sum(gn_bytes_per_iteration(p["s"].N, int(q["n_valid"]), p["g"].m, (p["g"].nnzb + p["g"].m) // 2, n_pcg)
                    for p, q in zip(probs, st))
     achieved = gn_bytes * (value / len(probs)) / world / 1e9    # batched iterations per second per GPU
+
+    # the batched PCG launches (one per group of problems) timed by the
+    # library's events in two uncaptured batched iterations
+    evs = []
+    for p in probs:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        p["ctx"].set_timing(E.ED_KERNEL_PCG, ev)
+        evs.append(ev)
+    for k in range(2):
+        reset()
+        flush.fill_(k & 0xff)
+        B.gn_step()
+    torch.cuda.synchronize()
+    pcg_us = 0.0
+    for p, ev in zip(probs, evs):
+        n_r = p["ctx"].timing_count()
+        p["ctx"].set_timing(E.ED_KERNEL_PCG, [])
+        if n_r:
+            pcg_us += statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) * 1e3 for i in range(n_r))
+    pcg_byt = sum(pcg_bytes_per_launch(p["g"].m, (p["g"].nnzb + p["g"].m) // 2, n_pcg) for p in probs)
+    pcg_achieved = pcg_byt / (pcg_us * 1e-6) / 1e9
+
+    # end to end: every member's depth map copied in from pinned host memory
+    # and its normal map recomputed, the parameters reset from host copies,
+    # the captured iterations replayed, the parameters and statistics read back
+    h_depth = [torch.from_numpy(p["s"].tgt_depth).pin_memory() for p in probs]
+    h_x0 = [p["x0"].cpu().pin_memory() for p in probs]
+    h_p0 = [p["pose0"].cpu().pin_memory() for p in probs]
+    h_x = [torch.empty(p["x0"].shape, dtype=torch.float32).pin_memory() for p in probs]
+    h_st = [torch.empty(b.shape, dtype=b.dtype).pin_memory() for b in stats]
+
+    def e2e_step():
+        for p, hd, hx, hp, x, q in zip(probs, h_depth, h_x0, h_p0, xs, poses):
+            depth, nmap = p["keep"][2], p["keep"][3]
+            depth.copy_(hd, non_blocking=True)
+            p["ctx"].compute_normals(depth, p["s"].intr, p["s"].cfg.normal_half_width, out=nmap)
+            x.copy_(hx, non_blocking=True)
+            q.copy_(hp, non_blocking=True)
+        B.launch()
+        for x, hx, b, hb in zip(xs, h_x, stats, h_st):
+            hx.copy_(x, non_blocking=True)
+            hb.copy_(b, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    with gc_paused():
+        for k in range(K):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            e2e_step()
+            e1.record()
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = whole_job_rate(world, K, units, max_over_ranks(sum(e2e_ms) / 1e3, dist, "cuda"))
+    h2d = sum(t.numel() * t.element_size() for t in h_depth + h_x0 + h_p0)
+    d2h = sum(t.numel() * t.element_size() for t in h_x + h_st)
     return {
         "metric": "batched ED GN iters/s (16 independent problems, one CUDA graph per frame)",
         "value": value, "unit": "GN iters/s (summed over problems)", "n_gpus": world, "steps": K,
@@ -649,6 +866,17 @@ def run_batch(args, rank, world, local):
                                         "note": "different PCG reduction partitions; later iterations re-associate"},
         "gpu_launches": launches,
         "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "GN iters/s (summed over problems)", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "note": "per step: 16 depth maps in from pinned host memory, normal maps recomputed, parameters "
+                        "reset from host copies, the captured iterations replayed, parameters and statistics "
+                        "back; L2 flushed before every step (outside the events)"},
+        "roofline": {"kernel": "k_pcg_batch (batched persistent block-Jacobi PCG, one launch per group)",
+                     "bound": "hbm", "achieved": pcg_achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": pcg_achieved / peak, "traffic": None, "algorithmic_bytes_per_iteration": pcg_byt,
+                     "launch_us_per_iteration": pcg_us,
+                     "note": "sum over the 16 problems of the single-problem PCG bytes, over the summed device "
+                             "time of the batched launches of one iteration"},
         "gn_iteration_roofline": {"bound": "hbm", "algorithmic_bytes_per_batched_iteration": gn_bytes,
                                   "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                                   "frac": achieved / peak},
@@ -927,7 +1155,7 @@ def run_reference(args, rank, world):
              for _ in range(args.steps)]
     tot = sum(times)
     value = args.steps * s.cfg.n_gn / tot
-    return {"metric": METRIC, "value": value, "unit": "GN iters/s", "n_gpus": world, "steps": args.steps,
+    return {"metric": metric_for(s.cfg.W, s.cfg.H, s.cfg.node_count), "value": value, "unit": "GN iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
@@ -953,6 +1181,11 @@ def main():
         return
     if args.workload == "batch16":
         out = run_batch(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.workload == "grad":
+        out = run_grad(args, rank, world, local)
         if rank == 0:
             print(json.dumps(out))
         return

@@ -294,12 +294,17 @@ ed_status ed_set_barrier_test(ed_context *ctx, int extra_arrivals);
  * created cudaEvent_t, host array) on the launching stream immediately before
  * and after the k-th launch of the selected kernel, for k < n_pairs; the count
  * recorded so far goes to *recorded (host int, may be NULL).  kernel_id:
- * ED_KERNEL_PCG (the persistent PCG solve of ed_gn_step), ED_KERNEL_POINTS
- * (warp + association + residual pass), ED_KERNEL_ASSEMBLE, ED_KERNEL_FINALIZE.
+ * ED_KERNEL_PCG (the persistent PCG solve of ed_gn_step; in ed_batch_gn_step,
+ * the batched PCG launch of each group, recorded on the group's first context),
+ * ED_KERNEL_POINTS
+ * (warp + association + residual pass and the compaction of its valid rows),
+ * ED_KERNEL_ASSEMBLE (the block assembly and the diagonal blocks'
+ * finalisation), ED_KERNEL_FINALIZE (the energy totals), ED_KERNEL_GRAD (the
+ * per-node gradient kernel of ed_energy_grad).
  * n_pairs = 0 switches the hook off.  The paper has no counterpart: this is
  * instrumentation for roofline measurements.
  */
-enum { ED_KERNEL_PCG = 0, ED_KERNEL_POINTS = 1, ED_KERNEL_ASSEMBLE = 2, ED_KERNEL_FINALIZE = 3 };
+enum { ED_KERNEL_PCG = 0, ED_KERNEL_POINTS = 1, ED_KERNEL_ASSEMBLE = 2, ED_KERNEL_FINALIZE = 3, ED_KERNEL_GRAD = 4 };
 ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded);
 
 /* Kernel launches the library has issued in this process so far (host out).

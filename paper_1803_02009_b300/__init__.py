@@ -131,7 +131,7 @@ _SIGS = {
     "ed_batch_launch": [_vp, _vp],
     "ed_batch_autotune": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(BatchSchedule), C.POINTER(C.c_float)],
 }
-ED_KERNEL_PCG, ED_KERNEL_POINTS, ED_KERNEL_ASSEMBLE, ED_KERNEL_FINALIZE = 0, 1, 2, 3
+ED_KERNEL_PCG, ED_KERNEL_POINTS, ED_KERNEL_ASSEMBLE, ED_KERNEL_FINALIZE, ED_KERNEL_GRAD = 0, 1, 2, 3, 4
 
 
 def lib():

@@ -287,7 +287,7 @@ extern "C" ed_status ed_launch_count(unsigned long long *count)
 
 extern "C" ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded)
 {
-    if (!ctx || n_pairs < 0 || (n_pairs > 0 && !events) || kernel_id < 0 || kernel_id > 3) return ED_ERR_ARG;
+    if (!ctx || n_pairs < 0 || (n_pairs > 0 && !events) || kernel_id < 0 || kernel_id > ED_KERNEL_GRAD) return ED_ERR_ARG;
     ctx->tm_kernel = kernel_id;
     ctx->tm_events = n_pairs > 0 ? events : nullptr;
     ctx->tm_pairs = n_pairs;

@@ -1688,6 +1688,7 @@ extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const e
     ed_status s = check_frame(ctx, fr);
     if (s != ED_OK) return s;
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_GRAD, st)) != ED_OK) return s;
+    ed_tm_begin(ctx, ED_KERNEL_GRAD, st);
     k_grad_nodes<<<ed_div_up(ctx->m, 4), 128, 0, st>>>(ctx->m, ctx->k_graph, ctx->graph.nbr, ctx->row_ptr, ctx->col,
                                                        ctx->diag_pos, ctx->ent_start, ctx->inc, ctx->run_start,
                                                        ctx->perm,
@@ -1696,6 +1697,7 @@ extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const e
                                                        (const ushort4 *)ctx->graph.idx,
                                                        ctx->weight_mode == ED_WEIGHT_GAUSSIAN, ctx->sigma, ctx->gpts,
                                                        prm->w_rot, prm->w_reg, grad_scale, grad_x); ed_note_launch();
+    ed_tm_end(ctx, ED_KERNEL_GRAD, st);
     k_grad_pose<<<1, 192, 0, st>>>(ctx->k1_part, k1_grid(ctx), ctx->max_k1_ctas, pose, *prm, grad_scale, grad_pose); ed_note_launch();
     ED_LAUNCH_CHECK();
     return ED_OK;

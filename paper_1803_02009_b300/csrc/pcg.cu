@@ -1085,7 +1085,10 @@ ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t 
              : prec == ED_PRECISION_MIXED_FP64 ? (const void *)k_pcg_batch<PcgFp64, 256>
                                                : (const void *)k_pcg_batch<float, 256>;
     ed_note_launch();
+    // (a timing hook set on the group's first context brackets the launch)
+    ed_tm_begin(ctxs[0], ED_KERNEL_PCG, st);
     cudaError_t e = launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st, false);
+    if (e == cudaSuccess) ed_tm_end(ctxs[0], ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: batched PCG launch failed: %s\n", cudaGetErrorString(e));
         return ED_ERR_CUDA;
