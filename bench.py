@@ -306,8 +306,16 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
     gn_ev = []
+    ph_ev = []
+
+    def ev_now():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
 
     def step(record_gn=False, depth=depth, color=color, frame=frame, while_solving=None):
+        if record_gn:
+            p0 = ev_now()
         ctx.compute_normals(depth, s.intr, cfg.normal_half_width, out=nmap)
         if nodes_t is not None:
             g = ctx.build_graph(pos, nrm, nodes=nodes_t, sigma=s.sigma, weight_mode=wmode, reuse=True)
@@ -331,6 +339,8 @@ def run_ours(args, rank, world, local):
             gn_ev.append((e0, e1))
         ctx.warp(x[:m], pose, pos, nrm, wpos, wnrm)
         ctx.fuse(pos, nrm, col, tst, wpos, wnrm, frame, F, cap_pts, out=fout)
+        if record_gn:
+            ph_ev.append((p0, e0, e1, ev_now()))
         return g
 
     def barrier():
@@ -372,6 +382,12 @@ def run_ours(args, rank, world, local):
     ctx.set_timing(E.ED_KERNEL_PCG, [])
     pcg_ms = [tm_ev[2 * i].elapsed_time(tm_ev[2 * i + 1]) for i in range(n_rec)]
     gn_ms = [a.elapsed_time(b) for a, b in gn_ev[-K:]]
+    phases_us = {
+        "normals_and_graph_build": statistics.median(a.elapsed_time(b) * 1e3 for a, b, _, _ in ph_ev[-K:]),
+        "gauss_newton": statistics.median(b.elapsed_time(c) * 1e3 for _, b, c, _ in ph_ev[-K:]),
+        "warp_and_fuse": statistics.median(c.elapsed_time(d) * 1e3 for _, _, c, d in ph_ev[-K:]),
+        "note": "median over the timed steps of CUDA events between the step's phases (the build's "
+                "parameter reset included in the first)"}
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
     value = whole_job_rate(world, K, cfg.n_gn, total_s)
 
@@ -488,6 +504,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between steps (512 MB write)",
                    "step": "normals + build_graph + 10 x gn_step + warp + fuse"},
         "gn_only_iters_per_s": gn_rate,
+        "step_phases_us": phases_us,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms),
                     "note": "this rank's timed steps one by one (CUDA events)"},
         "gpu_launches": launches,

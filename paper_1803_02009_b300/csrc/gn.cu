@@ -341,36 +341,12 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
 // points are the runs of the tuples that hold both of its nodes (its
 // incidences).  A warp streams them, one point per lane and round, the lanes
 // of a round taking consecutive points of the concatenated runs, accumulates
-// in registers, sums over the warp by recursive halving (fixed order:
+// in registers, sums over the warp through shared memory (fixed order:
 // deterministic; two-sum compensated in mixed precision) and finalises the
 // block in the same kernel: E_rot and E_reg terms, the transposed copy, and
 // for a diagonal block the gradient, the node energies and the block-Jacobi
 // inverse.
 // ---------------------------------------------------------------------------
-
-// Recursive halving of NV float2 values per lane across the warp (fixed order,
-// so the result is deterministic): after the step with offset o every lane
-// keeps the half selected by bit o of its lane index and adds the partner's
-// copy of it.  At the end lane k holds the sums of float2 values
-// (NV/32) k ... (NV/32) k + NV/32 - 1.
-template <int NV>
-__device__ __forceinline__ void warp_halving2(float2 (&v)[NV])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 16, n = NV; o > 0; o >>= 1, n >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int k = 0; k < n / 2; ++k) {
-            const float2 keep = hi ? v[k + n / 2] : v[k];
-            const float2 give = hi ? v[k] : v[k + n / 2];
-            float2 recv;
-            recv.x = __shfl_xor_sync(0xffffffffu, give.x, o);
-            recv.y = __shfl_xor_sync(0xffffffffu, give.y, o);
-            v[k] = __fadd2_rn(keep, recv);
-        }
-    }
-}
 
 // error-free sum a + b = s + e (Knuth's two-sum)
 __device__ __forceinline__ float two_sum(float a, float b, float &e)
@@ -381,37 +357,44 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e)
     return s;
 }
 
-// the same halving with every addition error-free (two-sum) and the errors
-// carried along: the compensated block reduction of the mixed-precision form.
-// Lane k ends with value + error of slot k (NV = 32).
-template <int NV>
-__device__ __forceinline__ void warp_halving2_ff(float2 (&v)[NV])
+// The column sums of NS float2 slots per lane over the warp through shared
+// memory: every lane stores its slots as row `lane` of red (row stride RED_RS
+// float2: an odd stride keeps both the 64-bit row stores and the column loads
+// free of bank conflicts), then lane k < NS adds column k over the rows in
+// order 0..31 (fixed order: deterministic; in mixed precision every addition
+// is an error-free two-sum with the errors carried along) and returns it.
+// About NS stores + 31 loads and adds per lane, against some 7 instructions
+// per exchanged pair of the recursive halving.
+#define RED_RS 31
+template <int NS>
+__device__ __forceinline__ float2 warp_sum_cols(const float2 (&v)[32], float2 *__restrict__ red, bool mixed)
 {
     const int lane = threadIdx.x & 31;
-    float2 err[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) err[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int o = 16, n = NV; o > 0; o >>= 1, n >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int k = 0; k < n / 2; ++k) {
-            const float2 keep = hi ? v[k + n / 2] : v[k], keep_e = hi ? err[k + n / 2] : err[k];
-            const float2 give = hi ? v[k] : v[k + n / 2], give_e = hi ? err[k] : err[k + n / 2];
-            float2 recv, recv_e;
-            recv.x = __shfl_xor_sync(0xffffffffu, give.x, o);
-            recv.y = __shfl_xor_sync(0xffffffffu, give.y, o);
-            recv_e.x = __shfl_xor_sync(0xffffffffu, give_e.x, o);
-            recv_e.y = __shfl_xor_sync(0xffffffffu, give_e.y, o);
-            float ex, ey;
-            v[k].x = two_sum(keep.x, recv.x, ex);
-            v[k].y = two_sum(keep.y, recv.y, ey);
-            err[k].x = __fadd_rn(__fadd_rn(keep_e.x, recv_e.x), ex);
-            err[k].y = __fadd_rn(__fadd_rn(keep_e.y, recv_e.y), ey);
+    for (int k = 0; k < NS; ++k) red[lane * RED_RS + k] = v[k];
+    __syncwarp();
+    float2 s = make_float2(0.f, 0.f);
+    if (lane < NS) {
+        s = red[lane];
+        if (mixed) {
+            float2 e = make_float2(0.f, 0.f);
+            for (int L = 1; L < 32; ++L) {
+                const float2 y = red[L * RED_RS + lane];
+                float ex, ey;
+                s.x = two_sum(s.x, y.x, ex);
+                s.y = two_sum(s.y, y.y, ey);
+                e.x = __fadd_rn(e.x, ex);
+                e.y = __fadd_rn(e.y, ey);
+            }
+            s.x = __fadd_rn(s.x, e.x);
+            s.y = __fadd_rn(s.y, e.y);
+        } else {
+#pragma unroll 8
+            for (int L = 1; L < 32; ++L) s = __fadd2_rn(s, red[L * RED_RS + lane]);
         }
     }
-    v[0].x = __fadd_rn(v[0].x, err[0].x);
-    v[0].y = __fadd_rn(v[0].y, err[0].y);
+    __syncwarp();   // red is reused by the warp's next sum
+    return s;
 }
 
 __device__ __forceinline__ float pick4(float v0, float v1, float v2, float v3, int i)
@@ -516,7 +499,8 @@ __device__ __forceinline__ void moments_add(float2 (&v)[32], float4 P, float4 W,
     }
 }
 
-__device__ __forceinline__ void role0(const AsmArgs &a, int i0, int n, int phase, int stride, float4 gj, float *M)
+__device__ __forceinline__ void role0(const AsmArgs &a, int i0, int n, int phase, int stride, float4 gj, float *M,
+                                      float2 *red)
 {
     float2 v[32];
 #pragma unroll
@@ -531,10 +515,9 @@ __device__ __forceinline__ void role0(const AsmArgs &a, int i0, int n, int phase
         moments_add(v, P0, W0, B0, s0, gj);
         moments_add(v, P1, W1, B1, s1, gj);
     });
-    if (a.mixed) warp_halving2_ff<32>(v);
-    else warp_halving2<32>(v);
+    const float2 t = warp_sum_cols<30>(v, red, a.mixed != 0);
     const int lane = threadIdx.x & 31;
-    if (lane < 30) reinterpret_cast<float2 *>(M)[lane] = v[0];
+    if (lane < 30) reinterpret_cast<float2 *>(M)[lane] = t;
 }
 
 // role 1 (diagonal block of node j): J^T r (12) and the pose-node block (6 x
@@ -578,7 +561,8 @@ __device__ __forceinline__ void role1_add(float2 (&v)[32], float4 P, float4 W, f
 }
 
 template <int H>
-__device__ __forceinline__ void role1(const AsmArgs &a, int i0, int n, float4 gj, const float *R, float *G)
+__device__ __forceinline__ void role1(const AsmArgs &a, int i0, int n, float4 gj, const float *R, float *G,
+                                      float2 *red)
 {
     float2 v[32];
 #pragma unroll
@@ -596,11 +580,10 @@ __device__ __forceinline__ void role1(const AsmArgs &a, int i0, int n, float4 gj
         role1_add<H>(v, P0, W0, B0, J0, s0 >> 2, gj, R);
         role1_add<H>(v, P1, W1, B1, J1, s1 >> 2, gj, R);
     });
-    if (a.mixed) warp_halving2_ff<32>(v);
-    else warp_halving2<32>(v);
-    const int lane = threadIdx.x & 31;
     constexpr int NSLOT = H == 0 ? 24 : 18;
-    if (lane < NSLOT) reinterpret_cast<float2 *>(G)[lane] = v[0];   // G: this half's slots
+    const float2 t = warp_sum_cols<NSLOT>(v, red, a.mixed != 0);
+    const int lane = threadIdx.x & 31;
+    if (lane < NSLOT) reinterpret_cast<float2 *>(G)[lane] = t;   // G: this half's slots
 }
 
 __device__ __forceinline__ int sym3(int a, int b)
@@ -887,6 +870,7 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
 {
     __shared__ __align__(16) float sM[ASM_WARPS][84];
     __shared__ float s_R[ASM_WARPS][9];
+    __shared__ __align__(16) float2 s_red[ASM_WARPS][32 * RED_RS];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = (int)blockIdx.x * ASM_WARPS + wid;
     const int m = a.m;
@@ -901,16 +885,17 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
     ed_pdl_trigger();
     if (!has) return;
     float *M = sM[wid];   // (every warp works alone from here: warp-level synchronisation only)
+    float2 *red = s_red[wid];
     if (kind == 0) {
-        role0(a, i1.x, i1.y, 0, 1, gj, M);
+        role0(a, i1.x, i1.y, 0, 1, gj, M, red);
         __syncwarp();
         for (int q = lane; q < 60; q += 32) a.dmom[(long)u * 72 + q] = M[q];
     } else if (kind == 1) {
         const int h = (w - m) & 1;
         if (lane < 9) s_R[wid][lane] = __ldcg(a.pose_R + lane);
         __syncwarp();
-        if (h == 0) role1<0>(a, i1.x, i1.y, gj, s_R[wid], M);   // J^T r (12), pose rows 0..2 (36)
-        else role1<1>(a, i1.x, i1.y, gj, s_R[wid], M);          // pose rows 3..5 (36)
+        if (h == 0) role1<0>(a, i1.x, i1.y, gj, s_R[wid], M, red);   // J^T r (12), pose rows 0..2 (36)
+        else role1<1>(a, i1.x, i1.y, gj, s_R[wid], M, red);          // pose rows 3..5 (36)
         __syncwarp();
         float *pn = a.pnode + (long)i0.y * 72;
         if (h == 0) {
@@ -920,7 +905,7 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
             for (int q = lane; q < 36; q += 32) pn[36 + q] = M[q];
         }
     } else {
-        role0(a, i1.x, i1.y, 0, 1, gj, M);
+        role0(a, i1.x, i1.y, 0, 1, gj, M, red);
         __syncwarp();
         fin_offdiag(a, i0, i1, M);
     }
