@@ -96,6 +96,7 @@ size_t carve(ed_context *c, char *base)
     c->minv = k.take<float>(M * 144);
     c->pose_blk = k.take<float>(72);
     c->dmom = k.take<float>(M * 72);
+    c->fin_cnt = k.take<int>(M);
     c->bsr_s = k.take<float>(nnzb * 144);
     c->grad_s = k.take<float>(P);
     c->pnode_s = k.take<float>(M * 72);
@@ -104,12 +105,11 @@ size_t carve(ed_context *c, char *base)
     c->xm_prev = k.take<double>(M * 12);
     c->pose_prev = k.take<double>(6);
     c->node_energy = k.take<float2>(M);
-    c->rec0 = k.take<float4>(N);
-    c->rec1 = k.take<float4>(N);
     c->pix = k.take<int>(N);
     c->max_k1_ctas = (int)((N + ED_K1_THREADS - 1) / ED_K1_THREADS) + 1;
     c->k1_part = k.take<float2>((size_t)c->max_k1_ctas * ED_K1_PART);
-    c->vcount = k.take<int>((size_t)c->max_k1_ctas);
+    c->lb_ticket = k.take<unsigned long long>(1);
+    c->lb_state = k.take<unsigned long long>((size_t)c->max_k1_ctas);
     c->vec_stride = (P + 63) / 64 * 64;
     c->vec = k.take<float>(6 * c->vec_stride);
     c->pcg_part = k.take<double>(2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART);
@@ -179,6 +179,9 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess ||
         cudaMemset(c->dmisc, 0, sizeof(double) * 64) != cudaSuccess ||
         cudaMemset(c->pcg_part, 0, sizeof(double) * 2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART) != cudaSuccess ||
+        cudaMemset(c->fin_cnt, 0, sizeof(int) * (size_t)c->lim.max_nodes) != cudaSuccess ||
+        cudaMemset(c->lb_ticket, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->lb_state, 0, sizeof(unsigned long long) * (size_t)c->max_k1_ctas) != cudaSuccess ||
         cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_state_len) != cudaSuccess ||
         cudaMemset(c->scan_ticket, 0, sizeof(unsigned)) != cudaSuccess) {
         cudaFreeHost(c->row_ptr_host);

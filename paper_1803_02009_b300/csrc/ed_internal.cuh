@@ -138,7 +138,6 @@ struct ed_context {
     // a step's valid rows, compacted in sorted order (k_compact)
     float4 *crec0, *crec1, *cpos, *csw;   // [N] records, position, tuple weights
     int *vrun_start;         // [N + 1] first compacted row of every run
-    int *vcount;             // [max_k1_ctas] valid rows of every point-pass chunk
     float *pose_R;           // [16] R of the step's pose (from the point pass)
     // normal equations
     float *bsr;              // [max_nnzb][144]
@@ -147,6 +146,9 @@ struct ed_context {
     float *minv;             // [m][144] block-Jacobi inverses
     float *pose_blk;         // [36] pose block, [36..72) its inverse
     float *dmom;             // [m][72] moments (60) and J^T r (12) of the diagonal blocks, per step
+    int *fin_cnt;            // [m] arrivals of a node's two diagonal warps in the assembly (0 between steps)
+    unsigned long long *lb_ticket;   // point pass of a step: epoch << 32 | chunks handed out
+    unsigned long long *lb_state;    // [max_k1_ctas] per chunk: epoch << 34 | flag << 32 | valid rows
     // Levenberg-Marquardt: the undamped system and the parameters of the last
     // accepted point (restored when a step raises the energy)
     float *bsr_s;            // [max_nnzb][144]
@@ -157,8 +159,6 @@ struct ed_context {
     double *xm_prev;         // [m][12]
     double *pose_prev;       // [6]
     float2 *node_energy;     // [m] (rot, reg) of every node
-    float4 *rec0;            // [N] (sqrt(w) R^T n(u), r), sorted order in a Gauss-Newton step
-    float4 *rec1;            // [N] (d r / d angles, 0), likewise
     int *pix;                // [N] association of the last evaluation
     float2 *k1_part;         // [ED_K1_PART][max_k1_ctas] float-float partials, component-major
     int max_k1_ctas;
@@ -450,6 +450,18 @@ __device__ __forceinline__ unsigned ed_atom_add_release(unsigned *p, unsigned v)
 __device__ __forceinline__ void ed_st_release(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ed_ld_acquire64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void ed_st_release64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void ed_red_add_release(unsigned *p, unsigned v)

@@ -31,128 +31,111 @@ struct PointArgs {
     float4 *rec0, *rec1;
     float2 *part;      // [ED_K1_PART][pstride] float-float partials, component-major
     int pstride;
-    int chunk;         // > 0: CTA c takes the contiguous positions [c chunk, (c + 1) chunk) (STEP);
-                       // 0: a grid-stride loop
-    int *vcount;       // STEP: valid rows of every CTA's chunk (for the compaction), or NULL
     float *pose_R;     // STEP: R of the step's pose (9 floats, written by CTA 0), or NULL
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
 };
 
-// Per point: Eq. (1) warp, visible-point gate, data residual r = n(u).(v~ - Gamma)
-// and its derivative factors; per-CTA sums of E_data, the count, the 6x6 pose
-// block and the pose gradient (fixed grid-stride order: deterministic).
-__global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
+// Per point at position k (node-tuple order in a Gauss-Newton step, model
+// order otherwise): Eq. (1) warp, visible-point gate, data residual
+// r = n(u).(v~ - Gamma) and its derivative factors r0 = [sqrt(w) R^T n(u); r],
+// r1 = [d r / d angles; 1] (zero on invalid rows); E_data, the count, the 6x6
+// pose block, the pose gradient, the non-finite count, E_corr and the valid
+// rows are added to acc.  Returns whether the row is valid.
+__device__ __forceinline__ bool point_eval(const PointArgs &a, const ed_pose_f &P, int k, float (&acc)[32],
+                                           float4 &r0, float4 &r1)
 {
-    ed_pdl_wait();
-    ed_pdl_trigger();
-    // a Gauss-Newton step starts with a clear status word: nothing before this
-    // kernel's end reads it, and no thread of this kernel writes it otherwise
-    if (a.status_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.status_reset = ED_OK;
-    __shared__ ed_pose_f P;
-    __shared__ float red[ED_K1_THREADS / 32][32];
-    if (threadIdx.x == 0) {
-        ed_pose_eval(a.pose, P);
-        if (a.pose_R && blockIdx.x == 0)
-            for (int q = 0; q < 9; ++q) a.pose_R[q] = P.R[q];
-    }
-    __syncthreads();
-    // 0 E_data, 1 count, 2..22 pose block, 23..28 pose gradient, 29 non-finite, 30 E_corr,
-    // 31 valid rows (model and key-point rows: the compaction's count)
-    float acc[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.f;
-    const int k_first = a.chunk ? blockIdx.x * a.chunk + threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
-    const int k_end = a.chunk ? min(a.n, (int)(blockIdx.x + 1) * a.chunk) : a.n;
-    const int k_step = a.chunk ? blockDim.x : gridDim.x * blockDim.x;
-    for (int k = k_first; k < k_end; k += k_step) {
-        const int i = a.perm ? __ldg(a.perm + k) : k;
-        const float4 p = a.pos[k], nr = a.nrm[k];
-        const ushort4 id = a.idx[k];
-        const float4 wi = a.recompute_w ? ed_gauss_weights(p, id, a.g, a.m, a.sigma) : a.w[k];
-        const ed_warped W = ed_warp_point(p, nr, id, wi, a.g, a.x4, P.R, P.T);
-        const bool kp = i >= a.n_model;
-        // the plane of the residual: target point G and normal tn (the pixel's
-        // back-projection and normal, or a key point's target and a camera axis)
-        bool valid;
-        float G[3];
-        float4 tn;
-        float sw;
-        if (!kp) {
-            int q;
-            if (a.mode == PASS_GRAD) q = a.pix[i];
-            else {
-                q = ed_associate(W, a.depth, a.nmap, a.K, a.eps2, a.cos_eps_n);
-                if (a.mode == PASS_ENERGY) a.pix[i] = q;
-                if (a.dbg_pix) {
-                    a.dbg_pix[i] = q;
-                    reinterpret_cast<float4 *>(a.dbg_wpos)[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
-                    reinterpret_cast<float4 *>(a.dbg_wnrm)[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
-                }
+    const int i = a.perm ? __ldg(a.perm + k) : k;
+    const float4 p = a.pos[k], nr = a.nrm[k];
+    const ushort4 id = a.idx[k];
+    const float4 wi = a.recompute_w ? ed_gauss_weights(p, id, a.g, a.m, a.sigma) : a.w[k];
+    const ed_warped W = ed_warp_point(p, nr, id, wi, a.g, a.x4, P.R, P.T);
+    const bool kp = i >= a.n_model;
+    // the plane of the residual: target point G and normal tn (the pixel's
+    // back-projection and normal, or a key point's target and a camera axis)
+    bool valid;
+    float G[3];
+    float4 tn;
+    float sw;
+    if (!kp) {
+        int q;
+        if (a.mode == PASS_GRAD) q = a.pix[i];
+        else {
+            q = ed_associate(W, a.depth, a.nmap, a.K, a.eps2, a.cos_eps_n);
+            if (a.mode == PASS_ENERGY) a.pix[i] = q;
+            if (a.dbg_pix) {
+                a.dbg_pix[i] = q;
+                reinterpret_cast<float4 *>(a.dbg_wpos)[i] = make_float4(W.v.x, W.v.y, W.v.z, p.w);
+                reinterpret_cast<float4 *>(a.dbg_wnrm)[i] = make_float4(W.n.x, W.n.y, W.n.z, nr.w);
             }
-            valid = q >= 0;
-            if (valid) {
-                const int u = q % a.K.width, v = q / a.K.width;
-                const float D = __ldg(a.depth + q);
-                tn = __ldg(a.nmap + q);
-                G[0] = ((float)u - a.K.cx) * D / a.K.fx;
-                G[1] = ((float)v - a.K.cy) * D / a.K.fy;
-                G[2] = D;
-            }
-            sw = a.sw;
-        } else {
-            const int t = i - a.n_model, c = t % 3;
-            const float4 T = __ldg(a.kp_tgt + t / 3);
-            valid = T.w != 0.f;
-            G[0] = T.x;
-            G[1] = T.y;
-            G[2] = T.z;
-            tn = make_float4(c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f, 1.f);
-            sw = a.sw_corr;
         }
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        valid = q >= 0;
         if (valid) {
-            const float r = sw * (tn.x * (W.v.x - G[0]) + tn.y * (W.v.y - G[1]) + tn.z * (W.v.z - G[2]));
-            const float *R = P.R;
-            // R^T n(u), scaled by the residual's sqrt(w)
-            const float b0 = sw * (R[0] * tn.x + R[3] * tn.y + R[6] * tn.z);
-            const float b1 = sw * (R[1] * tn.x + R[4] * tn.y + R[7] * tn.z);
-            const float b2 = sw * (R[2] * tn.x + R[5] * tn.y + R[8] * tn.z);
-            float jp[6];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const float *d = P.dR + 9 * t;
-                const float e0 = d[0] * W.s.x + d[1] * W.s.y + d[2] * W.s.z;
-                const float e1 = d[3] * W.s.x + d[4] * W.s.y + d[5] * W.s.z;
-                const float e2 = d[6] * W.s.x + d[7] * W.s.y + d[8] * W.s.z;
-                jp[t] = sw * (tn.x * e0 + tn.y * e1 + tn.z * e2);
-            }
-            jp[3] = sw * tn.x;
-            jp[4] = sw * tn.y;
-            jp[5] = sw * tn.z;
-            r0 = make_float4(b0, b1, b2, r);
-            r1 = make_float4(jp[0], jp[1], jp[2], 1.0f);
-            if (kp) {
-                acc[30] += r * r;
-            } else {
-                acc[0] += r * r;
-                acc[1] += 1.0f;
-            }
-            acc[31] += 1.0f;
-            int ka = 2;
-#pragma unroll
-            for (int t = 0; t < 6; ++t)
-#pragma unroll
-                for (int s = t; s < 6; ++s) acc[ka++] += jp[t] * jp[s];
-#pragma unroll
-            for (int t = 0; t < 6; ++t) acc[23 + t] += r * jp[t];
-            if (!isfinite(r)) acc[29] += 1.0f;
+            const int u = q % a.K.width, v = q / a.K.width;
+            const float D = __ldg(a.depth + q);
+            tn = __ldg(a.nmap + q);
+            G[0] = ((float)u - a.K.cx) * D / a.K.fx;
+            G[1] = ((float)v - a.K.cy) * D / a.K.fy;
+            G[2] = D;
         }
-        if (a.mode != PASS_ENERGY) {
-            a.rec0[k] = r0;
-            a.rec1[k] = r1;
-        }
+        sw = a.sw;
+    } else {
+        const int t = i - a.n_model, c = t % 3;
+        const float4 T = __ldg(a.kp_tgt + t / 3);
+        valid = T.w != 0.f;
+        G[0] = T.x;
+        G[1] = T.y;
+        G[2] = T.z;
+        tn = make_float4(c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f, 1.f);
+        sw = a.sw_corr;
     }
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1 = r0;
+    if (valid) {
+        const float r = sw * (tn.x * (W.v.x - G[0]) + tn.y * (W.v.y - G[1]) + tn.z * (W.v.z - G[2]));
+        const float *R = P.R;
+        // R^T n(u), scaled by the residual's sqrt(w)
+        const float b0 = sw * (R[0] * tn.x + R[3] * tn.y + R[6] * tn.z);
+        const float b1 = sw * (R[1] * tn.x + R[4] * tn.y + R[7] * tn.z);
+        const float b2 = sw * (R[2] * tn.x + R[5] * tn.y + R[8] * tn.z);
+        float jp[6];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const float *d = P.dR + 9 * t;
+            const float e0 = d[0] * W.s.x + d[1] * W.s.y + d[2] * W.s.z;
+            const float e1 = d[3] * W.s.x + d[4] * W.s.y + d[5] * W.s.z;
+            const float e2 = d[6] * W.s.x + d[7] * W.s.y + d[8] * W.s.z;
+            jp[t] = sw * (tn.x * e0 + tn.y * e1 + tn.z * e2);
+        }
+        jp[3] = sw * tn.x;
+        jp[4] = sw * tn.y;
+        jp[5] = sw * tn.z;
+        r0 = make_float4(b0, b1, b2, r);
+        r1 = make_float4(jp[0], jp[1], jp[2], 1.0f);
+        if (kp) {
+            acc[30] += r * r;
+        } else {
+            acc[0] += r * r;
+            acc[1] += 1.0f;
+        }
+        acc[31] += 1.0f;
+        int ka = 2;
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+#pragma unroll
+            for (int s = t; s < 6; ++s) acc[ka++] += jp[t] * jp[s];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) acc[23 + t] += r * jp[t];
+        if (!isfinite(r)) acc[29] += 1.0f;
+    }
+    return valid;
+}
+
+// The CTA's sums of acc[0..31) (float-float over the warps, in order) to
+// part[c][slot], component-major (c < 31; acc[31] is the caller's).
+__device__ __forceinline__ void point_partials(float (&acc)[32], float (*red)[32], float2 *__restrict__ part,
+                                               int pstride, int slot)
+{
     // block reduction: for each half of the 32 sums a butterfly over the warp
     // that halves the values a lane carries at every shuffle step (lane bit o
     // keeps the upper or the lower half and receives that half from its
@@ -183,81 +166,171 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
     if (threadIdx.x < 31) {
         float2 s = make_float2(0.f, 0.f);
         for (int w = 0; w < ED_K1_THREADS / 32; ++w) s = ed_ff_add1(s, red[w][threadIdx.x]);
-        a.part[(size_t)threadIdx.x * a.pstride + blockIdx.x] = s;
-    } else if (threadIdx.x == 31 && a.vcount) {
-        float c = 0.f;   // (integers below 2^24: exact)
-        for (int w = 0; w < ED_K1_THREADS / 32; ++w) c += red[w][31];
-        a.vcount[blockIdx.x] = (int)c;
+        part[(size_t)threadIdx.x * pstride + slot] = s;
     }
 }
 
-// stable compaction of the valid rows of a step's point records (sorted
-// order kept): CTA c takes the chunk the point pass's CTA c took, its first
-// output position the valid rows of the chunks before it (from the point
-// pass's counts, summed by warp 0: no look-back); also the first compacted
-// position of every run (vrun_start) and, from the last CTA, the total
-#define CP_CHUNK 512
-__global__ void __launch_bounds__(256) k_compact(const int *__restrict__ vcount, int nchunks, int n,
-                                                 const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                                 const float4 *__restrict__ spos, const float4 *__restrict__ sw,
-                                                 const int *__restrict__ run_of_start, int n_runs,
-                                                 float4 *__restrict__ crec0, float4 *__restrict__ crec1,
-                                                 float4 *__restrict__ cpos, float4 *__restrict__ csw,
-                                                 int *__restrict__ vrun_start)
+
+// Energy and gradient passes: the points in model order, grid-stride (fixed
+// order per CTA: deterministic); records written in the gradient pass.
+__global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
 {
-    __shared__ int s_base, s_total, s_warp[8];
     ed_pdl_wait();
     ed_pdl_trigger();
-    const int c = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x < 32) {
-        int pre = 0, tot = 0;
-        for (int i = lane; i < nchunks; i += 32) {
-            const int v = __ldcg(vcount + i);
-            tot += v;
-            if (i < c) pre += v;
-        }
+    __shared__ ed_pose_f P;
+    __shared__ float red[ED_K1_THREADS / 32][32];
+    if (threadIdx.x == 0) ed_pose_eval(a.pose, P);
+    __syncthreads();
+    // 0 E_data, 1 count, 2..22 pose block, 23..28 pose gradient, 29 non-finite, 30 E_corr, 31 valid rows
+    float acc[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            pre += __shfl_xor_sync(0xffffffffu, pre, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        }
-        if (lane == 0) {
-            s_base = pre;
-            s_total = tot;
+    for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
+        float4 r0, r1;
+        point_eval(a, P, k, acc, r0, r1);
+        if (a.mode != PASS_ENERGY) {
+            a.rec0[k] = r0;
+            a.rec1[k] = r1;
         }
     }
+    point_partials(acc, red, a.part, a.pstride, blockIdx.x);
+}
+
+// the compaction of a step's valid rows, fused into its point pass
+struct CompactArgs {
+    unsigned long long *ticket;   // epoch << 32 | chunks handed out in this step
+    unsigned long long *state;    // per chunk: epoch << 34 | 1 << 32 | its count of valid rows
+    const float4 *sw;             // tuple-order weights (copied for the valid rows)
+    const int *run_of_start;      // [N] run starting at a position, or -1
+    int n_runs;
+    float4 *crec0, *crec1, *cpos, *csw;   // compacted valid rows (records, position, tuple weights)
+    int *vrun_start;              // [n_runs + 1] first compacted row of every run; the total
+    int *status;
+    unsigned long long wait_ns;
+};
+
+#define CP_CHUNK 512
+
+// Exclusive prefix of the valid rows of the chunks before `chunk`: every
+// thread of the CTA waits for and adds the published counts of the chunks
+// t, t + blockDim, ... below `chunk` (all in flight at once: one L2 round
+// trip after the last of them is published, no chain through the
+// predecessors' prefixes), then a CTA sum in a fixed order.  Chunks are
+// handed out in ticket order, so every predecessor is running or done, and
+// every one publishes its count before it waits for anything.  A wait gives
+// up after the wait limit (ED_ERR_TIMEOUT; the prefix then misses that
+// count, so every write stays in bounds).  All threads call it.
+__device__ __forceinline__ int chunk_prefix(const CompactArgs &c, int chunk, unsigned long long E, int *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int pre = 0;
+    const unsigned long long t0 = ed_gtimer();
+    unsigned spins = 0;
+    for (int q = threadIdx.x; q < chunk; q += blockDim.x) {
+        for (;;) {
+            const unsigned long long v = ed_ld_acquire64(c.state + q);
+            if ((v >> 34) == (E >> 34) && ((v >> 32) & 3ull) != 0ull) {
+                pre += (int)(v & 0xffffffffull);
+                break;
+            }
+            if ((++spins & 63u) == 0u && ed_gtimer() - t0 > c.wait_ns) {
+                atomicCAS(c.status, ED_OK, ED_ERR_TIMEOUT);
+                break;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    if (lane == 0) sh[wid] = pre;
     __syncthreads();
-    int base = s_base;
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    return tot;
+}
+
+// The point pass of a Gauss-Newton step over the points in node-tuple order:
+// each CTA takes the chunk of CP_CHUNK positions of its ticket, evaluates its
+// points (point_eval), stages the valid rows (records, position, tuple
+// weights) in shared memory in position order, publishes its count, writes
+// its sums (per-chunk slot: the pose pass adds them in chunk order), adds up
+// the counts of the chunks before it and writes its rows after them,
+// with the first compacted row of every run that starts in the chunk (the
+// last chunk also the total).  The last ticket holder starts the next epoch.
+__global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, CompactArgs c)
+{
+    const unsigned full = 0xffffffffu;
+    __shared__ ed_pose_f P;
+    __shared__ float red[ED_K1_THREADS / 32][32];
+    __shared__ __align__(16) float4 stage[4][CP_CHUNK];
+    __shared__ int s_warp[ED_K1_THREADS / 32], s_chunk;
+    __shared__ unsigned long long s_epoch;
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    // a Gauss-Newton step starts with a clear status word: nothing before this
+    // kernel's end reads it, and only a look-back that gives up writes it
+    if (a.status_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.status_reset = ED_OK;
+    if (threadIdx.x == 0) {
+        const unsigned long long old = atomicAdd(c.ticket, 1ull);
+        const int chunk = (int)(old & 0xffffffffull);
+        const unsigned long long epoch = old >> 32;
+        if (chunk == (int)gridDim.x - 1) atomicExch(c.ticket, (epoch + 1ull) << 32);
+        s_chunk = chunk;
+        s_epoch = (epoch & 0x3fffffffull) << 34;
+        ed_pose_eval(a.pose, P);
+    }
+    __syncthreads();
+    const int chunk = s_chunk;
+    const unsigned long long E = s_epoch;
+    if (chunk == 0 && a.pose_R && threadIdx.x < 9) a.pose_R[threadIdx.x] = P.R[threadIdx.x];
+    float acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int e = 0; e < CP_CHUNK / 256; ++e) {
-        const int k = c * CP_CHUNK + e * 256 + threadIdx.x;
-        const bool in = k < n;
-        const bool v = in && __ldcg(rec1 + k).w != 0.f;   // (w = 1 on valid rows, 0 otherwise)
-        const unsigned bal = __ballot_sync(0xffffffffu, v);
+    constexpr int ROUNDS = CP_CHUNK / ED_K1_THREADS;
+    int nvalid = 0, run_r[ROUNDS], run_l[ROUNDS];
+#pragma unroll
+    for (int e = 0; e < ROUNDS; ++e) {
+        const int k = chunk * CP_CHUNK + e * ED_K1_THREADS + threadIdx.x;
+        const bool in = k < a.n;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        const bool valid = in && point_eval(a, P, k, acc, r0, r1);
+        const unsigned bal = __ballot_sync(full, valid);
         if (lane == 0) s_warp[wid] = __popc(bal);
         __syncthreads();
         int wpre = 0, btot = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < ED_K1_THREADS / 32; ++q) {
             const int t = s_warp[q];
             if (q < wid) wpre += t;
             btot += t;
         }
-        const int excl = base + wpre + __popc(bal & lt);
-        if (in) {
-            if (v) {
-                crec0[excl] = __ldcg(rec0 + k);
-                crec1[excl] = __ldcg(rec1 + k);
-                cpos[excl] = __ldg(spos + k);
-                csw[excl] = __ldg(sw + k);
-            }
-            const int r = __ldg(run_of_start + k);
-            if (r >= 0) vrun_start[r] = excl;
+        const int lr = nvalid + wpre + __popc(bal & lt);
+        if (valid) {
+            stage[0][lr] = r0;
+            stage[1][lr] = r1;
+            stage[2][lr] = a.pos[k];
+            stage[3][lr] = __ldg(c.sw + k);
         }
-        base += btot;
+        run_r[e] = in ? __ldg(c.run_of_start + k) : -1;
+        run_l[e] = lr;
+        nvalid += btot;
         __syncthreads();   // (s_warp is rewritten by the next round)
     }
-    if (c == nchunks - 1 && threadIdx.x == 0) vrun_start[n_runs] = s_total;
+    if (threadIdx.x == 0)   // the chunk's count, for the chunks after it
+        ed_st_release64(c.state + chunk, E | (1ull << 32) | (unsigned long long)(unsigned)nvalid);
+    point_partials(acc, red, a.part, a.pstride, chunk);
+    const int base = chunk_prefix(c, chunk, E, s_warp);
+    for (int i = threadIdx.x; i < nvalid; i += ED_K1_THREADS) {
+        c.crec0[base + i] = stage[0][i];
+        c.crec1[base + i] = stage[1][i];
+        c.cpos[base + i] = stage[2][i];
+        c.csw[base + i] = stage[3][i];
+    }
+#pragma unroll
+    for (int e = 0; e < ROUNDS; ++e)
+        if (run_r[e] >= 0) c.vrun_start[run_r[e]] = base + run_l[e];
+    if (chunk == (int)gridDim.x - 1 && threadIdx.x == 0) c.vrun_start[c.n_runs] = base + nvalid;
 }
 
 // CTAs of a step's point pass: one per contiguous chunk of CP_CHUNK positions
@@ -305,26 +378,35 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
     a.sw_corr = sqrtf(ctx->w_corr);
     a.pix = ctx->pix;
     a.status_reset = mode == PASS_STEP ? ctx->misc + MI_STATUS : nullptr;
-    a.rec0 = mode == PASS_GRAD ? ctx->gpts : ctx->rec0;
-    a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : ctx->rec1;
+    a.rec0 = mode == PASS_GRAD ? ctx->gpts : nullptr;   // (records: the gradient pass only)
+    a.rec1 = mode == PASS_GRAD ? ctx->gpts + ctx->lim.max_points : nullptr;
     a.part = ctx->k1_part;
     a.pstride = ctx->max_k1_ctas;
     a.dbg_wpos = ctx->dbg_wpos;
     a.dbg_wnrm = ctx->dbg_wnrm;
     a.dbg_pix = (mode == PASS_STEP && ctx->dbg_wpos && ctx->dbg_wnrm) ? ctx->dbg_pix : nullptr;
-    a.chunk = step ? CP_CHUNK : 0;
-    a.vcount = step ? ctx->vcount : nullptr;
     a.pose_R = step ? ctx->pose_R : nullptr;
     const int grid = step ? k1_grid_step(ctx) : k1_grid(ctx);
-    if (mode == PASS_STEP) ed_tm_begin(ctx, ED_KERNEL_POINTS, st);
-    ED_CUDA_TRY(ed_launch_pdl(k_points, dim3(grid), dim3(ED_K1_THREADS), 0, st, a)); ed_note_launch();
-    if (step) {   // the valid rows compacted for the assembly
-        ED_CUDA_TRY(ed_launch_pdl(k_compact, dim3(grid), dim3(256), 0, st, (const int *)ctx->vcount, grid, ctx->N,
-                                  (const float4 *)ctx->rec0, (const float4 *)ctx->rec1, (const float4 *)ctx->spos,
-                                  (const float4 *)ctx->sw, (const int *)ctx->run_of_start, ctx->n_runs, ctx->crec0,
-                                  ctx->crec1, ctx->cpos, ctx->csw, ctx->vrun_start)); ed_note_launch();
+    if (!step) {
+        ED_CUDA_TRY(ed_launch_pdl(k_points, dim3(grid), dim3(ED_K1_THREADS), 0, st, a)); ed_note_launch();
+    } else {   // with the compaction of the valid rows for the assembly
+        CompactArgs c;
+        c.ticket = ctx->lb_ticket;
+        c.state = ctx->lb_state;
+        c.sw = ctx->sw;
+        c.run_of_start = ctx->run_of_start;
+        c.n_runs = ctx->n_runs;
+        c.crec0 = ctx->crec0;
+        c.crec1 = ctx->crec1;
+        c.cpos = ctx->cpos;
+        c.csw = ctx->csw;
+        c.vrun_start = ctx->vrun_start;
+        c.status = ctx->misc + MI_STATUS;
+        c.wait_ns = ctx->wait_ns;
+        ed_tm_begin(ctx, ED_KERNEL_POINTS, st);
+        ED_CUDA_TRY(ed_launch_pdl(k_points_step, dim3(grid), dim3(ED_K1_THREADS), 0, st, a, c)); ed_note_launch();
+        ed_tm_end(ctx, ED_KERNEL_POINTS, st);
     }
-    if (mode == PASS_STEP) ed_tm_end(ctx, ED_KERNEL_POINTS, st);
     ED_LAUNCH_CHECK();
     return ED_OK;
 }
@@ -461,6 +543,56 @@ __device__ __forceinline__ void block_points(const uint32_t *__restrict__ inc, c
     }
 }
 
+// The same over the 16-lane half of the warp that holds the calling lane
+// (two blocks per warp, one per half): lane L of the half takes points
+// 32 R + 2 L and 32 R + 2 L + 1 of its block in round R.  Both halves run
+// the warp-uniform maximum of their batch and round counts; past its own
+// end a half gets positions -1.
+template <typename F>
+__device__ __forceinline__ void block_points_seg(const uint32_t *__restrict__ inc, const int *__restrict__ run_start,
+                                                 int i0, int n, F &&f)
+{
+    const unsigned full = 0xffffffffu;
+    const int sl = threadIdx.x & 15;
+    const int nmax = max(n, __shfl_xor_sync(full, n, 16));
+    for (int ib = 0; ib < nmax; ib += 16) {
+        int st = 0, len = 0, sc = 0;
+        if (ib + sl < n) {
+            const uint32_t v = __ldg(inc + i0 + ib + sl);   // fixed for the frame
+            const int r = (int)(v >> 4);
+            st = __ldcg(run_start + r);   // (the compacted starts change every step)
+            len = __ldcg(run_start + r + 1) - st;
+            sc = (int)(v & 15u);
+        }
+        int incl = len;   // inclusive scan of the run lengths over the half
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            const int y = __shfl_up_sync(full, incl, o, 16);
+            if (sl >= o) incl += y;
+        }
+        const int total = __shfl_sync(full, incl, 15, 16);
+        const int tmax = max(total, __shfl_xor_sync(full, total, 16));
+        for (int v0 = 0; v0 < tmax; v0 += 32) {
+            const int vv = v0 + 2 * sl;
+            int lo = 0, lo1 = 0;
+#pragma unroll
+            for (int step = 8; step > 0; step >>= 1) {
+                const int e = __shfl_sync(full, incl, lo + step - 1, 16);
+                if (e <= vv) lo += step;
+                const int e1 = __shfl_sync(full, incl, lo1 + step - 1, 16);
+                if (e1 <= vv + 1) lo1 += step;
+            }
+            const int o_st = __shfl_sync(full, st, lo, 16), o_in = __shfl_sync(full, incl, lo, 16);
+            const int o_len = __shfl_sync(full, len, lo, 16), o_sc = __shfl_sync(full, sc, lo, 16);
+            const int n_st = __shfl_sync(full, st, lo1, 16), n_in = __shfl_sync(full, incl, lo1, 16);
+            const int n_len = __shfl_sync(full, len, lo1, 16), n_sc = __shfl_sync(full, sc, lo1, 16);
+            const int k0 = vv < total ? o_st + vv - (o_in - o_len) : -1;
+            const int k1 = vv + 1 < total ? n_st + vv + 1 - (n_in - n_len) : -1;
+            f(k0, o_sc, k1, n_sc);
+        }
+    }
+}
+
 struct AsmArgs {
     const int4 *info;        // [n_upper][2] records of the upper blocks (k_fin_pack)
     const uint32_t *inc;     // incidences run << 4 | s << 2 | t, sorted by block
@@ -475,6 +607,7 @@ struct AsmArgs {
     float w_rot, w_reg, lambda, jitter;
     float *bsr, *grad, *pnode, *minv;
     float *dmom;             // [m][72]: moments of the diagonal blocks (60) and their J^T r (12)
+    int *fin_cnt;            // [m]: arrivals of the node's two diagonal warps (reset by the finaliser)
     float2 *node_energy;
     int *status;
 };
@@ -518,6 +651,52 @@ __device__ __forceinline__ void role0(const AsmArgs &a, int i0, int n, int phase
     const float2 t = warp_sum_cols<30>(v, red, a.mixed != 0);
     const int lane = threadIdx.x & 31;
     if (lane < 30) reinterpret_cast<float2 *>(M)[lane] = t;
+}
+
+// role 0 for two off-diagonal blocks per warp (one per 16-lane half): the 60
+// moments of the half's block go to M[60 h .. 60 h + 60) (M: 120 floats), the
+// sums over the half's 16 rows in order (two-sum compensated in mixed
+// precision)
+__device__ __forceinline__ void role0_seg(const AsmArgs &a, int i0, int n, float4 gj, float *M, float2 *red)
+{
+    float2 v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = make_float2(0.f, 0.f);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    block_points_seg(a.inc, a.run_start, i0, n, [&](int k0, int s0, int k1, int s1) {
+        const float4 B0 = k0 >= 0 ? __ldcg(a.rec0 + k0) : z4, B1 = k1 >= 0 ? __ldcg(a.rec0 + k1) : z4;
+        const float4 P0 = k0 >= 0 ? __ldcg(a.spos + k0) : z4, P1 = k1 >= 0 ? __ldcg(a.spos + k1) : z4;
+        const float4 W0 = k0 >= 0 ? __ldcg(a.sw + k0) : z4, W1 = k1 >= 0 ? __ldcg(a.sw + k1) : z4;
+        moments_add(v, P0, W0, B0, s0, gj);
+        moments_add(v, P1, W1, B1, s1, gj);
+    });
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 30; ++k) red[lane * RED_RS + k] = v[k];
+    __syncwarp();
+    for (int cc = lane; cc < 60; cc += 32) {   // column k of half h: rows 16 h .. 16 h + 15
+        const int h = cc >= 30 ? 1 : 0, k = cc - 30 * h;
+        const float2 *col = red + 16 * h * RED_RS + k;
+        float2 t = col[0];
+        if (a.mixed) {
+            float2 e = make_float2(0.f, 0.f);
+            for (int L = 1; L < 16; ++L) {
+                const float2 y = col[L * RED_RS];
+                float ex, ey;
+                t.x = two_sum(t.x, y.x, ex);
+                t.y = two_sum(t.y, y.y, ey);
+                e.x = __fadd_rn(e.x, ex);
+                e.y = __fadd_rn(e.y, ey);
+            }
+            t.x = __fadd_rn(t.x, e.x);
+            t.y = __fadd_rn(t.y, e.y);
+        } else {
+#pragma unroll
+            for (int L = 1; L < 16; ++L) t = __fadd2_rn(t, col[L * RED_RS]);
+        }
+        reinterpret_cast<float2 *>(M + 60 * h)[k] = t;
+    }
+    __syncwarp();
 }
 
 // role 1 (diagonal block of node j): J^T r (12) and the pose-node block (6 x
@@ -689,37 +868,35 @@ __device__ __forceinline__ void block_entry_moments(int R, int Cc, int &mi, int 
     m3 = a + sym4(c, 3);
 }
 
-// an off-diagonal upper block (j, l) from its moments M: the 144 entries
-// (lane L < 24 takes column C = L % 12 of the rows R = L / 12 + 2 k, k < 6)
-// with d^_l = d^_j + [g_j - g_l; 0], plus the E_reg terms of the graph edges
-// j -> l and l -> j; the block and its transpose are written
-__device__ __forceinline__ void fin_offdiag(const AsmArgs &a, int4 i0, int4 i1, const float *M)
+// an off-diagonal upper block (j, l) from its moments M, by one 16-lane half
+// of the warp (lane L < 12 of the half takes column L of all 12 rows): the
+// 144 entries with d^_l = d^_j + [g_j - g_l; 0], plus the E_reg terms of the
+// graph edges j -> l and l -> j; the block and its transpose are written
+__device__ __forceinline__ void fin_offdiag_seg(const AsmArgs &a, int4 i0, int4 i1, float4 gj, float4 gl, const float *M)
 {
-    const int lane = threadIdx.x & 31;
-    const int b = i0.x, j = i0.y, l = i0.z, tb = i0.w;
+    const int sl = threadIdx.x & 15;
+    const int b = i0.x, tb = i0.w;
     if (tb < 0) {
-        if (lane == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
+        if (sl == 0) atomicCAS(a.status, 0, ED_ERR_STATE);
         return;
     }
-    if (lane >= 24) return;
-    const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
+    if (sl >= 12) return;
+    const int Cc = sl, rp = Cc >> 2, cp = Cc & 3;
     const float wr = a.w_reg;
     const bool e_jl = (i1.z & 1) != 0, e_lj = (i1.z & 2) != 0;   // graph edges j -> l, l -> j
-    const float4 gj = a.g[j], gl = a.g[l];
     const float dlc = pick4(gj.x - gl.x, gj.y - gl.y, gj.z - gl.z, 0.f, cp);
     const float hx = gl.x - gj.x, hy = gl.y - gj.y, hz = gl.z - gj.z;
-    // E_reg, edge l -> j (d e / d t_j = -I): column quantity of the rows c = 3
     const float reg_lj = e_lj ? -wr * (cp < 3 ? -pick4(hx, hy, hz, 1.f, cp) : 1.0f) : 0.f;
     float *dst = a.bsr + (long)b * 144 + Cc;
     float *dstT = a.bsr + (long)tb * 144 + Cc * 12;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const int R = h0 + 2 * k, r = R >> 2, c = R & 3;
+    for (int R = 0; R < 12; ++R) {
+        const int r = R >> 2, c = R & 3;
         int mi, m3;
         block_entry_moments(R, Cc, mi, m3);
         float h = M[mi];
         if (cp < 3) h += dlc * M[m3];
-        if (r == rp) {   // E_reg, edge j -> l (d e / d t_l = -I) on the t column
+        if (r == rp) {
             if (e_jl && cp == 3) h -= wr * pick4(hx, hy, hz, 1.f, c);
             if (c == 3) h += reg_lj;
         }
@@ -860,36 +1037,69 @@ __device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, con
 
 #define ASM_WARPS 4
 
+// The diagonal block of node j needs the moments (warp of kind 0) and J^T r
+// (first node-row warp): each of the two warps, after writing its part to
+// dmom[j], arrives on fin_cnt[j] (fence, then the atomic); the second one to
+// arrive finalises the block (fin_diag) while the rest of the assembly runs,
+// and resets the count for the next step.  Its shared scratch is the warp's
+// column-sum buffer `red` (free by then, 524 of its 1,984 floats).
+template <bool INV>
+__device__ __forceinline__ void diag_arrive(const AsmArgs &a, int4 i0, int4 i1, float2 *red)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = i0.y;
+    __threadfence();   // this lane's part of dmom[j] before the arrival
+    __syncwarp();
+    int prev = 0;
+    if (lane == 0) prev = atomicAdd(a.fin_cnt + j, 1);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev == 0) return;   // the other warp finalises
+    if (lane == 0) a.fin_cnt[j] = 0;
+    __threadfence();   // the other warp's part, observed through its arrival
+    float *F = reinterpret_cast<float *>(red);
+    float *sM = F, *sH = F + 72, *sL = F + 216, *sX = F + 360, *sS = F + 372, *sNx = F + 388;
+    float4 *sNg = reinterpret_cast<float4 *>(F + 484);
+    int *sNk = reinterpret_cast<int *>(F + 516);
+    for (int q = lane; q < 72; q += 32) sM[q] = __ldcg(a.dmom + (long)j * 72 + q);
+    __syncwarp();
+    fin_diag<INV>(a, i0, i1, sM, sM + 60, sH, sX, sS, sL, sNk, sNg, sNx);
+}
+
 // One warp per work item, four per CTA, in this order: the moments of the m
-// diagonal blocks (to dmom[j][0..60), finalised by k_fin_diag), the two
-// halves of J^T r and the pose-node block of every node (J^T r to
-// dmom[j][60..72), the pose-node block to pnode), then the off-diagonal upper
-// blocks, each finalised by its warp.
+// diagonal blocks (to dmom[j][0..60)), the two halves of J^T r and the
+// pose-node block of every node (J^T r to dmom[j][60..72), the pose-node
+// block to pnode) -- the later of a node's two dmom writers finalises its
+// diagonal block -- then the off-diagonal upper
+// blocks, two per warp (one per 16-lane half: they hold a few dozen points
+// each), each finalised by its half.
 template <bool INV>
 __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
 {
-    __shared__ __align__(16) float sM[ASM_WARPS][84];
+    __shared__ __align__(16) float sM[ASM_WARPS][120];
     __shared__ float s_R[ASM_WARPS][9];
     __shared__ __align__(16) float2 s_red[ASM_WARPS][32 * RED_RS];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = (int)blockIdx.x * ASM_WARPS + wid;
     const int m = a.m;
-    const int kind = w < m ? 0 : (w < 3 * m ? 1 : 2);   // diagonal moments, node rows, off-diagonal block
-    const int u = kind == 0 ? w : (kind == 1 ? (w - m) >> 1 : m + (w - 3 * m));
-    const bool has = kind < 2 || u < m + a.n_off;
-    // the block's records and node position are fixed for the frame: loaded
+    const int kind = w < m ? 0 : (w < 3 * m ? 1 : 2);   // diagonal moments, node rows, off-diagonal blocks
+    const int u = kind == 0 ? w : (kind == 1 ? (w - m) >> 1 : m + 2 * (w - 3 * m) + (lane >> 4));
+    const bool has = kind < 2 || u < m + a.n_off;   // (per half for off-diagonal blocks)
+    // the block's records and node positions are fixed for the frame: loaded
     // before the wait for the point pass (whose records come after)
     const int4 i0 = has ? a.info[2 * u] : make_int4(0, 0, 0, 0), i1 = has ? a.info[2 * u + 1] : make_int4(0, 0, 0, 0);
-    const float4 gj = has ? a.g[i0.y] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 gj = has ? a.g[i0.y] : z4;
+    const float4 gl = has && kind == 2 ? a.g[i0.z] : z4;
     ed_pdl_wait();
     ed_pdl_trigger();
-    if (!has) return;
+    if (!__any_sync(0xffffffffu, has)) return;
     float *M = sM[wid];   // (every warp works alone from here: warp-level synchronisation only)
     float2 *red = s_red[wid];
     if (kind == 0) {
         role0(a, i1.x, i1.y, 0, 1, gj, M, red);
         __syncwarp();
         for (int q = lane; q < 60; q += 32) a.dmom[(long)u * 72 + q] = M[q];
+        diag_arrive<INV>(a, i0, i1, red);
     } else if (kind == 1) {
         const int h = (w - m) & 1;
         if (lane < 9) s_R[wid][lane] = __ldcg(a.pose_R + lane);
@@ -901,34 +1111,14 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
         if (h == 0) {
             if (lane < 12) a.dmom[(long)u * 72 + 60 + lane] = M[lane];
             for (int q = lane; q < 36; q += 32) pn[q] = M[12 + q];
+            diag_arrive<INV>(a, i0, i1, red);
         } else {
             for (int q = lane; q < 36; q += 32) pn[36 + q] = M[q];
         }
     } else {
-        role0(a, i1.x, i1.y, 0, 1, gj, M, red);
-        __syncwarp();
-        fin_offdiag(a, i0, i1, M);
+        role0_seg(a, i1.x, has ? i1.y : 0, gj, M, red);
+        if (has) fin_offdiag_seg(a, i0, i1, gj, gl, M + 60 * (lane >> 4));
     }
-}
-
-// the diagonal blocks from their moments and J^T r (dmom), one warp per node
-template <bool INV>
-__global__ void __launch_bounds__(32 * ASM_WARPS) k_fin_diag(AsmArgs a)
-{
-    __shared__ __align__(16) float sM[ASM_WARPS][72];
-    __shared__ float sH[ASM_WARPS][144], sL[ASM_WARPS][144], sX[ASM_WARPS][12], sS[ASM_WARPS][16];
-    __shared__ int sNk[ASM_WARPS][ED_MAX_KG];
-    __shared__ float4 sNg[ASM_WARPS][ED_MAX_KG];
-    __shared__ __align__(16) float sNx[ASM_WARPS][12 * ED_MAX_KG];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = (int)blockIdx.x * ASM_WARPS + wid;
-    const int4 i0 = j < a.m ? a.info[2 * j] : make_int4(0, 0, 0, 0), i1 = j < a.m ? a.info[2 * j + 1] : make_int4(0, 0, 0, 0);
-    ed_pdl_wait();
-    ed_pdl_trigger();
-    if (j >= a.m) return;
-    for (int q = lane; q < 72; q += 32) sM[wid][q] = __ldcg(a.dmom + (long)j * 72 + q);
-    __syncwarp();
-    fin_diag<INV>(a, i0, i1, sM[wid], sM[wid] + 60, sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid]);
 }
 
 #define FIN_WARPS 4
@@ -1409,14 +1599,13 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     aa.node_energy = ctx->node_energy;
     aa.status = ctx->misc + MI_STATUS;
     aa.dmom = ctx->dmom;
+    aa.fin_cnt = ctx->fin_cnt;
     {
-        // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks
-        const int grid = ed_div_up(3 * m + aa.n_off, ASM_WARPS);
+        // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks in pairs
+        const int grid = ed_div_up(3 * m + (aa.n_off + 1) / 2, ASM_WARPS);
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_CUDA_TRY(ed_launch_pdl(lm ? k_assemble<false> : k_assemble<true>, dim3(grid), dim3(32 * ASM_WARPS), 0, st,
                                   aa)); ed_note_launch();
-        ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS)),
-                                  dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();
     }

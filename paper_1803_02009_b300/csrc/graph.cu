@@ -1285,6 +1285,8 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         n_upper += m;   // strictly upper blocks + the diagonal
         if (2 * n_upper != nnzb + m) return ED_ERR_STATE;   // the pattern must be symmetric with a full diagonal
     }
+    // (the assembly's per-node arrival counts start the frame at zero)
+    ED_CUDA_TRY(cudaMemsetAsync(ctx->fin_cnt, 0, sizeof(int) * (size_t)m, st));
     // row partition and shared-memory plan of the PCG solve
     ctx->m = m;
     if ((s = ed_pcg_plan(ctx, ctx->row_ptr_host, st)) != ED_OK) return s;
