@@ -339,9 +339,9 @@ __device__ __forceinline__ void ds_store(unsigned long long *p, unsigned epoch, 
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-__global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int n, unsigned long long *state,
-                                                   unsigned *ticket, unsigned ticket_base, unsigned epoch,
-                                                   int *status, unsigned long long wait_ns)
+__global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int n, int *total2,
+                                                   unsigned long long *state, unsigned *ticket, unsigned ticket_base,
+                                                   unsigned epoch, int *status, unsigned long long wait_ns)
 {
     __shared__ int s_tile, s_excl, s_warp[DS_T / 32];
     if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ticket, 1u) - ticket_base);
@@ -420,16 +420,23 @@ __global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int 
     for (int e = 0; e < DS_PER; ++e) {
         if (base + e < n) out[base + e] = run;
         run += v[e];
-        if (base + e == n - 1) out[n] = run;
+        if (base + e == n - 1) {
+            out[n] = run;
+            if (total2) *total2 = run;
+        }
     }
 }
 
-__global__ void k_set_zero_at(int *p) { *p = 0; }
+__global__ void k_set_zero_at(int *p, int *p2)
+{
+    *p = 0;
+    if (p2) *p2 = 0;
+}
 
-ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st)
+ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st, int *total2)
 {
     if (n <= 0) {
-        k_set_zero_at<<<1, 1, 0, st>>>(out); ed_note_launch();
+        k_set_zero_at<<<1, 1, 0, st>>>(out, total2); ed_note_launch();
         ED_LAUNCH_CHECK();
         return ED_OK;
     }
@@ -440,7 +447,7 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
         ED_CUDA_TRY(cudaMemsetAsync(ctx->scan_state, 0, sizeof(unsigned long long) * ctx->scan_state_len, st));
         ctx->scan_epoch = epoch = 1;
     }
-    k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
+    k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, total2, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
                                        ctx->misc + MI_STATUS, ctx->wait_ns); ed_note_launch();
     ctx->scan_ticket_base += (unsigned)tiles;
     ED_LAUNCH_CHECK();

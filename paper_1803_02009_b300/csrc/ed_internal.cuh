@@ -687,7 +687,9 @@ __device__ __forceinline__ int ed_associate(const ed_warped &W, const float *__r
 // internal entry points shared between translation units
 // ---------------------------------------------------------------------------
 
-ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st);
+// exclusive scan of n ints (out[n] = the total, also stored to *total2 when given)
+ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st,
+                            int *total2 = nullptr);
 ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
 ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_t st);
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,

@@ -711,6 +711,73 @@ __global__ void k_tb_place(const ushort4 *__restrict__ idx, int n, const int *__
 // against shared-memory tiles instead
 #define TB_T 256
 #define TB_MAX 2048
+// The same ordering with the key and the point index packed into one 64-bit
+// word (rest of the tuple << pb | point: unique, so the order is total; for
+// 3 fb + pb <= 64): one compare-exchange pair per thread and step of the
+// bitonic network (TB64_T = 128 threads: a bucket of 256 padded entries
+// takes every thread once per step), and one 8-byte array in shared memory.
+// Buckets above TB_MAX entries are ranked: every entry counts the smaller
+// keys, in tiles of TB_MAX.
+#define TB64_T 128
+__global__ void __launch_bounds__(TB64_T) k_tb_sort64(const ushort4 *__restrict__ idx, const int *__restrict__ start,
+                                                      int nb, int fb, int pb, const uint32_t *__restrict__ order,
+                                                      uint32_t *__restrict__ out)
+{
+    __shared__ unsigned long long s_k[TB_MAX];
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int b0 = start[b], n = start[b + 1] - b0;
+    if (n == 0) return;
+    if (n == 1) {
+        if (threadIdx.x == 0) out[b0] = order[b0];
+        return;
+    }
+    const unsigned long long pmask = (1ull << pb) - 1ull;
+    auto packed = [&](uint32_t i) {
+        int t[4], sl[4];
+        tuple_of(idx[i], t, sl);
+        const unsigned long long k3 =
+            ((unsigned long long)t[1] << (2 * fb)) | ((unsigned long long)t[2] << fb) | (unsigned long long)t[3];
+        return (k3 << pb) | (unsigned long long)i;
+    };
+    if (n <= TB_MAX) {
+        int P = 2;
+        while (P < n) P <<= 1;
+        for (int q = threadIdx.x; q < P; q += TB64_T) s_k[q] = q < n ? packed(order[b0 + q]) : ~0ull;   // padding last
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < (P >> 1); i += TB64_T) {
+                    const int q = ((i & ~(j - 1)) << 1) | (i & (j - 1)), o = q | j;
+                    const bool up = (q & k) == 0;
+                    const unsigned long long kq = s_k[q], ko = s_k[o];
+                    if ((kq > ko) == up) {
+                        s_k[q] = ko;
+                        s_k[o] = kq;
+                    }
+                }
+                __syncthreads();
+            }
+        for (int q = threadIdx.x; q < n; q += TB64_T) out[b0 + q] = (uint32_t)(s_k[q] & pmask);
+        return;
+    }
+    for (int e0 = 0; e0 < n; e0 += TB64_T) {
+        const int e = e0 + threadIdx.x;
+        const unsigned long long ke = e < n ? packed(order[b0 + e]) : 0ull;
+        int rank = 0;
+        for (int t0 = 0; t0 < n; t0 += TB_MAX) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < TB_MAX && t0 + q < n; q += TB64_T) s_k[q] = packed(order[b0 + t0 + q]);
+            __syncthreads();
+            if (e < n) {
+                const int lim = min(TB_MAX, n - t0);
+                for (int q = 0; q < lim; ++q) rank += s_k[q] < ke;
+            }
+        }
+        if (e < n) out[b0 + rank] = (uint32_t)(ke & pmask);
+    }
+}
+
 __global__ void __launch_bounds__(TB_T) k_tb_sort(const ushort4 *__restrict__ idx, const int *__restrict__ start,
                                                   int nb, int fb, const uint32_t *__restrict__ order,
                                                   uint32_t *__restrict__ out)
@@ -999,11 +1066,14 @@ __global__ void k_kp_expand(const float4 *__restrict__ kp, int nk, int n_model, 
 }
 
 // node counts of the sampled graph: counts[0] = min(sampled, max_nodes), counts[1] = sampled
-__global__ void k_set_counts(const int *__restrict__ misc, int max_nodes, int *__restrict__ counts)
+// (and the count in use to misc[MI_M], which goes to the host with the other misc words)
+__global__ void k_set_counts(int *__restrict__ misc, int max_nodes, int *__restrict__ counts)
 {
     const int mt = misc[MI_PHASE_BASE];
-    counts[0] = mt < max_nodes ? mt : max_nodes;
+    const int mu = mt < max_nodes ? mt : max_nodes;
+    counts[0] = mu;
     counts[1] = mt;
+    misc[MI_M] = mu;
 }
 
 // bounding box of n points into misc[MI_BBOX .. MI_BBOX + 5] (ordered ints)
@@ -1122,10 +1192,9 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         int *flags = ctx->cell_node, *pre = ctx->kcell_start;   // cells (+ 1) ints each
         k_node_flags<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, flags); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, flags, pre, tot, st)) != ED_OK) return s;
+        if ((s = ed_scan_exclusive(ctx, flags, pre, tot, st, ctx->misc + MI_PHASE_BASE)) != ED_OK) return s;
         k_node_write<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, pre, P4, G4, max_nodes); ed_note_launch();
         ED_LAUNCH_CHECK();
-        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_PHASE_BASE, pre + tot, sizeof(int), cudaMemcpyDeviceToDevice, st));
         k_set_counts<<<1, 1, 0, st>>>(ctx->misc, max_nodes, graph->counts); ed_note_launch();
     } else {
         ctx->pinned[ED_MAX_PCG_GRID + 3] = m_in;
@@ -1136,8 +1205,6 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     // the node count goes to the host while the next kernels run: they read it
     // from graph->counts and are sized for max_nodes
     ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
-    ED_CUDA_TRY(cudaMemcpyAsync(ctx->pinned + ED_MAX_PCG_GRID + 5, graph->counts, 2 * sizeof(int),
-                                cudaMemcpyDeviceToHost, st));
     ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
 
     // ---- node graph on the context's second stream (it needs only the nodes;
@@ -1179,7 +1246,13 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             ED_LAUNCH_CHECK();
             if ((s = ed_scan_exclusive(ctx, ctx->bcnt, ctx->bstart, max_nodes, st)) != ED_OK) return s;
             k_tb_place<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, ctx->bstart, bfill, ctx->ent_key); ed_note_launch();
-            k_tb_sort<<<max_nodes, TB_T, 0, st>>>(I4, ctx->bstart, max_nodes, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+            int pb = 1;
+            while ((1L << pb) < (long)NT) ++pb;
+            if (3 * fb + pb <= 64) {
+                k_tb_sort64<<<max_nodes, TB64_T, 0, st>>>(I4, ctx->bstart, max_nodes, fb, pb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+            } else {
+                k_tb_sort<<<max_nodes, TB_T, 0, st>>>(I4, ctx->bstart, max_nodes, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+            }
             ED_LAUNCH_CHECK();
         } else {
             // few nodes for many points: large buckets; a stable radix sort by the full key
@@ -1198,10 +1271,9 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                                            ctx->perm, ctx->spos, ctx->snrm, ctx->sidx, ctx->sw,
                                                            ctx->sidx_d, ctx->sw_d, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, NT, st)) != ED_OK) return s;
+        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, NT, st, ctx->misc + MI_READ + 1)) != ED_OK) return s;
         k_run_starts<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->flag_a, ctx->flag_b, NT, ctx->run_start,
                                                          ctx->run_of_start); ed_note_launch();
-        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 1, ctx->flag_b + NT, sizeof(int), cudaMemcpyDeviceToDevice, st));
         ED_LAUNCH_CHECK();
     }
     // every later launch on the caller's stream (and every return) follows the node graph
@@ -1209,7 +1281,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
     memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
     if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
-    m = ctx->pinned[ED_MAX_PCG_GRID + 5];
+    m = m_in > 0 ? m_in : hm[MI_M];
     if (m < ED_K || (prm->weight_mode == ED_WEIGHT_EQ2 && m < ED_K + 1) || m <= prm->k_graph) return ED_ERR_ARG;
 
     // ---- block pattern ----
@@ -1224,12 +1296,11 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         k_pairs_graph<<<ed_div_up(m, 256), 256, 0, st>>>(graph->nbr, m, prm->k_graph, ctx->bitmap, words); ed_note_launch();
         k_row_count<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->row_cnt, ctx->row_ptr, m, st)) != ED_OK) return s;
+        if ((s = ed_scan_exclusive(ctx, ctx->row_cnt, ctx->row_ptr, m, st, ctx->misc + MI_READ)) != ED_OK) return s;
         // the block count and the number of runs go to the host (pinned copy +
         // event) while the block lists, which need only the row pointer, are
         // filled (checking the count against the capacity)
         int *nz_host = ctx->pinned + ED_MAX_PCG_GRID + 6;
-        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ, ctx->row_ptr + m, sizeof(int), cudaMemcpyDeviceToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(nz_host, ctx->misc + MI_READ, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
         k_row_fill<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
@@ -1242,7 +1313,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         if (n_runs < 1 || n_runs > NT) return ED_ERR_STATE;
         k_tpos<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, nnzb, st)) != ED_OK) return s;
+        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, nnzb, st, ctx->misc + MI_READ + 2)) != ED_OK) return s;
         k_compact_upper<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, ctx->flag_a, ctx->flag_b, ctx->diag_pos,
                                                                ctx->up_list); ed_note_launch();
         ED_LAUNCH_CHECK();
@@ -1270,7 +1341,6 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH_CHECK();
         // one host read for what the rest of the build needs: the upper-block
         // count (gathered into misc) and the row pointer (pinned)
-        ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc + MI_READ + 2, ctx->flag_b + nnzb, sizeof(int), cudaMemcpyDeviceToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->row_ptr_host, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
