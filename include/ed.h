@@ -142,8 +142,18 @@ typedef struct ed_graph {
  *   contribute to it, used by ed_gn_step.
  * pos/nrm [N][4] are the model (they must stay valid until the next
  * ed_build_graph); the graph buffers are retained by the context likewise.
- * Synchronises the stream four times (it reads back the grid, node, block and
- * chunk counts); the last kernels of the build are still queued on return.
+ * The host waits twice, each time for an event queued early enough that the
+ * GPU keeps working meanwhile (the grid sizes, queued before the Poisson
+ * sampler's launch; the node count m, queued before the nearest-node search
+ * and the tuple sort); everything after the node count -- the block pattern,
+ * the incidences, the assembly's records -- is sized on the device, and the
+ * call returns with it still queued.  The pattern's sizes (nnzb, runs) and the
+ * PCG plan are read once, at the first later call that needs them
+ * (ed_gn_step, ed_energy, ed_energy_grad, ed_graph_info asking for nnzb,
+ * n_entries or n_runs, ed_batch_query_workspace); an error the build's
+ * kernels report (ED_ERR_CAPACITY when the pattern exceeds max_nnzb,
+ * ED_ERR_STATE for an inconsistent pattern) is returned by that call, and the
+ * context has no graph afterwards.
  */
 ed_status ed_build_graph(ed_context *ctx, const float *pos, const float *nrm, int n_points, int m_in,
                          const ed_graph_params *params, const ed_graph *graph, cudaStream_t stream);
@@ -168,8 +178,10 @@ ed_status ed_set_keypoints(ed_context *ctx, const float *kp_pos, const float *kp
 /* Host-side sizes of the graph built last (host out; NULL entries skipped):
  * nodes m, stored 12x12 blocks nnzb (both triangles), the (block, point)
  * pairs the assembly visits per step (10 per point) and the runs of points
- * that share their four nearest nodes. */
-ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs);
+ * that share their four nearest nodes.  m alone is known when ed_build_graph
+ * returns; asking for any of the others waits for the build's queued work
+ * (and returns the build's error, if its kernels reported one). */
+ed_status ed_graph_info(ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs);
 
 typedef struct ed_frame {
     const float *depth;    /* [H][W] target depth D (mm), 0 = hole */

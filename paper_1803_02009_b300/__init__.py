@@ -9,6 +9,7 @@ device, raises.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 import dataclasses
 import math
 import os
@@ -236,7 +237,19 @@ class Graph:
     nbr: torch.Tensor       # int32 [max_nodes, kg]
     counts: torch.Tensor    # int32 [4]
     m: int = 0
-    nnzb: int = 0
+    _nnzb: Optional[int] = None     # read from the context on first use
+    _owner: Optional[object] = None  # weak reference to the building context
+
+    @property
+    def nnzb(self) -> int:
+        """Stored 12x12 blocks (both triangles).  Reading it waits for the
+        build's queued pattern work (ed_graph_info)."""
+        if self._nnzb is None:
+            ctx = self._owner() if self._owner is not None else None
+            if ctx is None:
+                raise RuntimeError("the context that built this graph is gone")
+            self._nnzb = ctx._pattern_counts()[0]
+        return self._nnzb
 
     def idx_long(self):
         return self.idx.to(torch.int32) & 0xFFFF
@@ -258,6 +271,7 @@ class Context:
         _check("ed_create", L.ed_create(C.byref(self.limits), _ptr(self.ws), nbytes.value, C.byref(h)))
         self.h = h
         self.graph: Optional[Graph] = None
+        self._counts = None
         self._keep = []
         self.n_keypoints = 0
         self._kp = None
@@ -322,13 +336,32 @@ class Context:
                       g.counts.data_ptr())
         _check("ed_build_graph", lib().ed_build_graph(self.h, _ptr(pos), _ptr(nrm), int(N), int(m_in),
                                                       C.byref(prm), C.byref(gb), _stream(stream)))
-        m, nnzb, ne, nc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        _check("ed_graph_info", lib().ed_graph_info(self.h, C.byref(m), C.byref(nnzb), C.byref(ne), C.byref(nc)))
-        g.m, g.nnzb = m.value, nnzb.value
-        self.n_entries, self.n_runs = ne.value, nc.value
+        # the node count is known at return; the pattern's sizes are read on
+        # first use (the build's last kernels are still queued)
+        m = C.c_int()
+        _check("ed_graph_info", lib().ed_graph_info(self.h, C.byref(m), None, None, None))
+        g.m = m.value
+        g._nnzb, g._owner = None, weakref.ref(self)
+        self._counts = None
         self.graph = g
         self._keep = [pos, nrm]          # the context reads them until the next build
         return g
+
+    def _pattern_counts(self):
+        """(nnzb, n_entries, n_runs) of the last build (waits for its queued work)."""
+        if self._counts is None:
+            nnzb, ne, nc = C.c_int(), C.c_int(), C.c_int()
+            _check("ed_graph_info", lib().ed_graph_info(self.h, None, C.byref(nnzb), C.byref(ne), C.byref(nc)))
+            self._counts = (nnzb.value, ne.value, nc.value)
+        return self._counts
+
+    @property
+    def n_entries(self) -> int:
+        return self._pattern_counts()[1]
+
+    @property
+    def n_runs(self) -> int:
+        return self._pattern_counts()[2]
 
     def identity_x(self, m=None):
         m = self.graph.m if m is None else m

@@ -193,11 +193,13 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_misc, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_build, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost((void **)&c->misc_host, sizeof(int) * MI_COUNT) != cudaSuccess) {
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         if (c->ev_join) cudaEventDestroy(c->ev_join);
         if (c->ev_misc) cudaEventDestroy(c->ev_misc);
+        if (c->ev_build) cudaEventDestroy(c->ev_build);
         cudaFreeHost(c->row_ptr_host);
         cudaFreeHost(c->pinned);
         free(c);
@@ -210,11 +212,13 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
 extern "C" ed_status ed_destroy(ed_context *ctx)
 {
     if (!ctx) return ED_ERR_ARG;
+    if (ctx->build_pending) cudaEventSynchronize(ctx->ev_build);   // (its copies into pinned memory)
     cudaStreamSynchronize(ctx->aux);
     cudaStreamDestroy(ctx->aux);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
     cudaEventDestroy(ctx->ev_misc);
+    cudaEventDestroy(ctx->ev_build);
     cudaFreeHost(ctx->misc_host);
     cudaFreeHost(ctx->row_ptr_host);
     cudaFreeHost(ctx->pinned);
@@ -300,10 +304,15 @@ extern "C" ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *
     return ED_OK;
 }
 
-extern "C" ed_status ed_graph_info(const ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs)
+extern "C" ed_status ed_graph_info(ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs)
 {
     if (!ctx) return ED_ERR_ARG;
     if (!ctx->have_graph) return ED_ERR_STATE;
+    if (nnzb || n_entries || n_runs) {   // the pattern's counts: the build's queued work must have reached them
+        ed_status s = ed_graph_ready(ctx, 0);
+        if (s != ED_OK) return s;
+        ED_CUDA_TRY(cudaStreamSynchronize(0));   // (the plan's copy on the legacy stream)
+    }
     if (m) *m = ctx->m;
     if (nnzb) *nnzb = ctx->nnzb;
     if (n_entries) *n_entries = ctx->n_entries;
@@ -339,7 +348,7 @@ __device__ __forceinline__ void ds_store(unsigned long long *p, unsigned epoch, 
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-__global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int n, int *total2,
+__global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int n, const int *n_dev, int *total2,
                                                    unsigned long long *state, unsigned *ticket, unsigned ticket_base,
                                                    unsigned epoch, int *status, unsigned long long wait_ns)
 {
@@ -347,6 +356,18 @@ __global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int 
     if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ticket, 1u) - ticket_base);
     __syncthreads();
     const int tile = s_tile;
+    if (n_dev) {   // the length read on the device (n: the launch's capacity); later tiles only take a ticket
+        const int nd = *n_dev;
+        n = nd <= n ? nd : 0;   // (a length above the capacity is an error reported elsewhere: nothing scanned)
+        if (n <= 0) {
+            if (tile == 0 && threadIdx.x == 0) {
+                out[0] = 0;
+                if (total2) *total2 = 0;
+            }
+            return;
+        }
+        if ((long)tile * DS_TILE >= n) return;
+    }
     const long base = (long)tile * DS_TILE + (long)threadIdx.x * DS_PER;
     int v[DS_PER], sum = 0;
     if (base + DS_PER <= n && !((uintptr_t)(in + base) & 15)) {
@@ -433,7 +454,8 @@ __global__ void k_set_zero_at(int *p, int *p2)
     if (p2) *p2 = 0;
 }
 
-ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st, int *total2)
+ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st, int *total2,
+                            const int *n_dev)
 {
     if (n <= 0) {
         k_set_zero_at<<<1, 1, 0, st>>>(out, total2); ed_note_launch();
@@ -447,7 +469,7 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
         ED_CUDA_TRY(cudaMemsetAsync(ctx->scan_state, 0, sizeof(unsigned long long) * ctx->scan_state_len, st));
         ctx->scan_epoch = epoch = 1;
     }
-    k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, total2, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
+    k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, n_dev, total2, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
                                        ctx->misc + MI_STATUS, ctx->wait_ns); ed_note_launch();
     ctx->scan_ticket_base += (unsigned)tiles;
     ED_LAUNCH_CHECK();

@@ -157,8 +157,12 @@ static ed_status check_args(const ed_batch *b, const ed_frame *frames, const ed_
 extern "C" ed_status ed_batch_query_workspace(ed_context *const *ctxs, int count, size_t *bytes)
 {
     if (!ctxs || !bytes || count < 1 || count > ED_MAX_BATCH) return ED_ERR_ARG;
-    for (int p = 0; p < count; ++p)
-        if (!ctxs[p] || !ctxs[p]->have_graph) return ED_ERR_STATE;
+    for (int p = 0; p < count; ++p) {
+        if (!ctxs[p]) return ED_ERR_ARG;
+        ed_status s = ed_graph_ready(ctxs[p], 0);
+        if (s != ED_OK) return s;
+    }
+    ED_CUDA_TRY(cudaStreamSynchronize(0));   // (the plans' copies on the legacy stream)
     *bytes = save_need(ctxs, count);
     return ED_OK;
 }

@@ -183,6 +183,7 @@ struct ed_context {
 
     // ---- graph state (host) ----
     int have_graph;
+    int build_pending;       // the last build's pattern counts and PCG plan not read yet (ed_graph_ready)
     // sparse key correspondences (ed_set_keypoints); rows n_model .. N of the
     // point set are the key points, three rows each
     const float4 *kp_pos, *kp_tgt;
@@ -215,6 +216,7 @@ struct ed_context {
     // the misc words copied to the host without draining the stream
     int *misc_host;          // [MI_COUNT] pinned
     cudaEvent_t ev_misc;
+    cudaEvent_t ev_build;    // the end of the last build's queued work (its copies to pinned memory)
 
     float *dbg_wpos, *dbg_wnrm;
     int *dbg_pix;
@@ -687,9 +689,15 @@ __device__ __forceinline__ int ed_associate(const ed_warped &W, const float *__r
 // internal entry points shared between translation units
 // ---------------------------------------------------------------------------
 
-// exclusive scan of n ints (out[n] = the total, also stored to *total2 when given)
+// the counts and PCG plan of the last build (one host wait at the first call
+// after the build that needs them); ED_ERR_STATE without a graph
+ed_status ed_graph_ready(ed_context *ctx, cudaStream_t st);
+
+// exclusive scan of n ints (out[n] = the total, also stored to *total2 when
+// given); with n_dev, of *n_dev ints, the length read on the device (none
+// when it exceeds n, the capacity the launch is sized for)
 ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cudaStream_t st,
-                            int *total2 = nullptr);
+                            int *total2 = nullptr, const int *n_dev = nullptr);
 ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, int n, int key_bits, cudaStream_t st);
 ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_t st);
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,

@@ -202,7 +202,7 @@ struct CompactArgs {
     unsigned long long *state;    // per chunk: epoch << 34 | 1 << 32 | its count of valid rows
     const float4 *sw;             // tuple-order weights (copied for the valid rows)
     const int *run_of_start;      // [N] run starting at a position, or -1
-    int n_runs;
+    const int *n_runs;            // the number of runs (device)
     float4 *crec0, *crec1, *cpos, *csw;   // compacted valid rows (records, position, tuple weights)
     int *vrun_start;              // [n_runs + 1] first compacted row of every run; the total
     int *status;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, C
 #pragma unroll
     for (int e = 0; e < ROUNDS; ++e)
         if (run_r[e] >= 0) c.vrun_start[run_r[e]] = base + run_l[e];
-    if (chunk == (int)gridDim.x - 1 && threadIdx.x == 0) c.vrun_start[c.n_runs] = base + nvalid;
+    if (chunk == (int)gridDim.x - 1 && threadIdx.x == 0) c.vrun_start[*c.n_runs] = base + nvalid;
 }
 
 // CTAs of a step's point pass: one per contiguous chunk of CP_CHUNK positions
@@ -395,7 +395,7 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
         c.state = ctx->lb_state;
         c.sw = ctx->sw;
         c.run_of_start = ctx->run_of_start;
-        c.n_runs = ctx->n_runs;
+        c.n_runs = ctx->misc + MI_READ + 1;   // (the build's run count, on the device)
         c.crec0 = ctx->crec0;
         c.crec1 = ctx->crec1;
         c.cpos = ctx->cpos;
@@ -1550,8 +1550,11 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
         (prm->lm_accept != 0 && prm->lm_accept != 1))
         return ED_ERR_ARG;
     const int m = ctx->m;
-    // (the point pass clears the device status word)
+    // (the point pass clears the device status word; it needs none of the
+    // pattern's counts, so the first step after a build queues it before
+    // waiting for them)
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_STEP, st)) != ED_OK) return s;
+    if ((s = ed_graph_ready(ctx, st)) != ED_OK) return s;
     const bool lm = prm->lm_accept != 0;
     // the pose pass (pose block, its inverse, pose gradient, prior energies,
     // the point-pass sums) needs only the point pass: it runs on the context's
@@ -1730,8 +1733,9 @@ extern "C" ed_status ed_energy(ed_context *ctx, const ed_frame *fr, const ed_sol
                                const double *pose, double *energy_out, cudaStream_t st)
 {
     if (!ctx || !prm || !x || !pose || !energy_out || ((uintptr_t)x & 15)) return ED_ERR_ARG;
-    if (!ctx->have_graph) return ED_ERR_STATE;
-    ed_status s = check_frame(ctx, fr);
+    ed_status s = ed_graph_ready(ctx, st);
+    if (s != ED_OK) return s;
+    s = check_frame(ctx, fr);
     if (s != ED_OK) return s;
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_ENERGY, st)) != ED_OK) return s;
     k_node_energy<<<ed_div_up(ctx->m, 128), 128, 0, st>>>(ctx->m, ctx->k_graph, ctx->graph.nbr,
@@ -1858,8 +1862,10 @@ extern "C" ed_status ed_energy_grad(ed_context *ctx, const ed_frame *fr, const e
                                     cudaStream_t st)
 {
     if (!ctx || !prm || !x || !pose || !grad_x || !grad_pose || ((uintptr_t)x & 15)) return ED_ERR_ARG;
-    if (!ctx->have_graph || !ctx->have_energy) return ED_ERR_STATE;
-    ed_status s = check_frame(ctx, fr);
+    ed_status s = ed_graph_ready(ctx, st);
+    if (s != ED_OK) return s;
+    if (!ctx->have_energy) return ED_ERR_STATE;
+    s = check_frame(ctx, fr);
     if (s != ED_OK) return s;
     if ((s = ed_point_pass(ctx, fr, prm, x, pose, PASS_GRAD, st)) != ED_OK) return s;
     ed_tm_begin(ctx, ED_KERNEL_GRAD, st);

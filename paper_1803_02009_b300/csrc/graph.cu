@@ -4,6 +4,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "ed_internal.cuh"
 
 __global__ void k_bbox_init(int *misc)
@@ -615,25 +617,34 @@ __device__ __forceinline__ int find_block(const int *__restrict__ row_ptr, const
     return -1;
 }
 
-__global__ void k_tpos(int nnzb, const int *__restrict__ row_ptr, const int *__restrict__ col,
-                       const int *__restrict__ brow, int *__restrict__ tpos, int *__restrict__ upper_flag)
+// (the block count nnzb is read on the device; nothing runs when it exceeds
+// the capacity -- the row fill has reported ED_ERR_CAPACITY then)
+__global__ void k_tpos(const int *__restrict__ nnzb_dev, int cap, const int *__restrict__ row_ptr,
+                       const int *__restrict__ col, const int *__restrict__ brow, int *__restrict__ tpos,
+                       int *__restrict__ upper_flag)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnzb) return;
-    const int j = brow[b], l = col[b];
-    tpos[b] = find_block(row_ptr, col, l, j);
-    upper_flag[b] = l > j;   // strictly upper: the diagonal blocks go first in the list
+    const int nnzb = *nnzb_dev;
+    if (nnzb > cap) return;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nnzb; b += gridDim.x * blockDim.x) {
+        const int j = brow[b], l = col[b];
+        tpos[b] = find_block(row_ptr, col, l, j);
+        upper_flag[b] = l > j;   // strictly upper: the diagonal blocks go first in the list
+    }
 }
 
 // finalisation work list: the m diagonal blocks (long warps) first, then the
 // strictly upper blocks in row order
-__global__ void k_compact_upper(int nnzb, int m, const int *__restrict__ flag, const int *__restrict__ pre,
-                                const int *__restrict__ diag_pos, int *__restrict__ up_list)
+__global__ void k_compact_upper(const int *__restrict__ nnzb_dev, int cap, int m, const int *__restrict__ flag,
+                                const int *__restrict__ pre, const int *__restrict__ diag_pos,
+                                int *__restrict__ up_list)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < m) up_list[b] = diag_pos[b];
-    if (b >= nnzb) return;
-    if (flag[b]) up_list[m + pre[b]] = b;
+    const int nnzb = *nnzb_dev;
+    if (nnzb > cap) return;
+    const int n = nnzb > m ? nnzb : m;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        if (b < m) up_list[b] = diag_pos[b];
+        if (b < nnzb && flag[b]) up_list[m + pre[b]] = b;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -865,28 +876,38 @@ __global__ void __launch_bounds__(TB_T) k_tb_sort(const ushort4 *__restrict__ id
 // the incidences of every block in run order: counted by block, placed (in
 // any order), then each block's short list ordered by run (a run meets a
 // block at most once)
-__global__ void k_ic_count(int ne, const uint32_t *__restrict__ key, int *__restrict__ cnt)
+// (10 incidences per run, the run count read on the device; a warp's lanes
+// take consecutive incidences, so every warp runs the same trip count)
+__global__ void k_ic_count(const int *__restrict__ nruns_dev, const int *__restrict__ nnzb_dev, int cap,
+                           const uint32_t *__restrict__ key, int *__restrict__ cnt)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    warp_bucket_add(cnt, e < ne ? (int)key[e] : 0, e < ne);
+    if (*nnzb_dev > cap) return;
+    const int ne = 10 * *nruns_dev;
+    for (int e0 = blockIdx.x * blockDim.x; e0 < ne; e0 += gridDim.x * blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        warp_bucket_add(cnt, e < ne ? (int)key[e] : 0, e < ne);
+    }
 }
 
-__global__ void k_ic_place(int ne, const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+__global__ void k_ic_place(const int *__restrict__ nruns_dev, const int *__restrict__ nnzb_dev, int cap,
+                           const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                            const int *__restrict__ start, int *__restrict__ fill, uint32_t *__restrict__ out)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = e < ne ? (int)key[e] : 0;
-    const int pos = warp_bucket_add(fill, b, e < ne);
-    if (e < ne) out[start[b] + pos] = val[e];
+    if (*nnzb_dev > cap) return;
+    const int ne = 10 * *nruns_dev;
+    for (int e0 = blockIdx.x * blockDim.x; e0 < ne; e0 += gridDim.x * blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        const int b = e < ne ? (int)key[e] : 0;
+        const int pos = warp_bucket_add(fill, b, e < ne);
+        if (e < ne) out[start[b] + pos] = val[e];
+    }
 }
 
 // one warp per block: up to 64 incidences (two per lane) by a bitonic sort
 // over the warp on the run field; longer lists (rare) by insertion in place
-__global__ void __launch_bounds__(128) k_ic_sort(int nnzb, const int *__restrict__ start, uint32_t *__restrict__ list)
+__device__ __forceinline__ void ic_sort_block(const int *__restrict__ start, uint32_t *__restrict__ list, int b,
+                                              int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= nnzb) return;
     const int b0 = start[b], n = start[b + 1] - b0;
     if (n <= 1) return;
     if (n > 64) {
@@ -926,6 +947,17 @@ __global__ void __launch_bounds__(128) k_ic_sort(int nnzb, const int *__restrict
 #pragma unroll
     for (int u = 0; u < 2; ++u)
         if (2 * lane + u < n) list[b0 + 2 * lane + u] = v[u];
+}
+
+// (warps over the blocks, the block count read on the device)
+__global__ void __launch_bounds__(128) k_ic_sort(const int *__restrict__ nnzb_dev, int cap,
+                                                 const int *__restrict__ start, uint32_t *__restrict__ list)
+{
+    const int nnzb = *nnzb_dev;
+    if (nnzb > cap) return;
+    const int lane = threadIdx.x & 31;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nnzb; b += (gridDim.x * blockDim.x) >> 5)
+        ic_sort_block(start, list, b, lane);
 }
 
 // low 32 bits of every point's key, value = point index (the first pass of a
@@ -1000,12 +1032,11 @@ __global__ void k_run_starts(const int *__restrict__ flag, const int *__restrict
 // the 10 incidences of every run: key = block of (tuple[s], tuple[t]) in the
 // BSR pattern, value = run << 4 | s << 2 | t (s <= t, so tuple[s] is the row
 // node: the block is upper or diagonal)
-__global__ void k_inc_gen(int n_runs, const int *__restrict__ run_start, const ushort4 *__restrict__ sidx,
-                          const int *__restrict__ row_ptr, const int *__restrict__ col, uint32_t *__restrict__ key,
-                          uint32_t *__restrict__ val, int *__restrict__ status)
+__device__ __forceinline__ void inc_gen_run(int r, const int *__restrict__ run_start, const ushort4 *__restrict__ sidx,
+                                            const int *__restrict__ row_ptr, const int *__restrict__ col,
+                                            uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                                            int *__restrict__ status)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_runs) return;
     const ushort4 q = sidx[run_start[r]];
     const int t4[4] = {q.x, q.y, q.z, q.w};
     int e = 0;
@@ -1021,19 +1052,30 @@ __global__ void k_inc_gen(int n_runs, const int *__restrict__ run_start, const u
         }
 }
 
+__global__ void k_inc_gen(const int *__restrict__ nruns_dev, const int *__restrict__ nnzb_dev, int cap,
+                          const int *__restrict__ run_start, const ushort4 *__restrict__ sidx,
+                          const int *__restrict__ row_ptr, const int *__restrict__ col, uint32_t *__restrict__ key,
+                          uint32_t *__restrict__ val, int *__restrict__ status)
+{
+    if (*nnzb_dev > cap) return;
+    const int n_runs = *nruns_dev;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_runs; r += gridDim.x * blockDim.x)
+        inc_gen_run(r, run_start, sidx, row_ptr, col, key, val, status);
+}
+
+
 
 // the assembly's record of every upper block u, fixed for the frame (one load
 // for what its warps would otherwise fetch in dependent steps):
 //   off-diagonal: {b, j, l, transpose position}, {first incidence, incidences,
 //                 graph-edge flags (j -> l: 1, l -> j: 2), 0}
 //   diagonal:     {b, j, j, row start}, {first incidence, incidences, row length, 0}
-__global__ void k_fin_pack(int nnzb, int m, int kg, const int *__restrict__ up_list, const int *__restrict__ flag_b,
-                           const int *__restrict__ brow, const int *__restrict__ col, const int *__restrict__ tpos,
-                           const int *__restrict__ row_ptr, const int *__restrict__ inc_start,
-                           const int *__restrict__ nbr, int4 *__restrict__ info)
+__device__ __forceinline__ void fin_pack_one(int u, int m, int kg, const int *__restrict__ up_list,
+                                             const int *__restrict__ brow, const int *__restrict__ col,
+                                             const int *__restrict__ tpos, const int *__restrict__ row_ptr,
+                                             const int *__restrict__ inc_start, const int *__restrict__ nbr,
+                                             int4 *__restrict__ info)
 {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= m + flag_b[nnzb]) return;   // the upper-block count
     const int b = up_list[u];
     const int j = brow[b], l = col[b];
     const int i0 = inc_start[b], ni = inc_start[b + 1] - i0;
@@ -1051,6 +1093,19 @@ __global__ void k_fin_pack(int nnzb, int m, int kg, const int *__restrict__ up_l
         info[2 * u + 1] = make_int4(i0, ni, flags, 0);
     }
 }
+
+__global__ void k_fin_pack(const int *__restrict__ nnzb_dev, int cap, int m, int kg, const int *__restrict__ up_list,
+                           const int *__restrict__ flag_b, const int *__restrict__ brow, const int *__restrict__ col,
+                           const int *__restrict__ tpos, const int *__restrict__ row_ptr,
+                           const int *__restrict__ inc_start, const int *__restrict__ nbr, int4 *__restrict__ info)
+{
+    const int nnzb = *nnzb_dev;
+    if (nnzb > cap) return;
+    const int nu = m + flag_b[nnzb];   // the upper-block count
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x)
+        fin_pack_one(u, m, kg, up_list, brow, col, tpos, row_ptr, inc_start, nbr, info);
+}
+
 
 // ---------------------------------------------------------------------------
 
@@ -1074,6 +1129,13 @@ __global__ void k_set_counts(int *__restrict__ misc, int max_nodes, int *__restr
     counts[0] = mu;
     counts[1] = mt;
     misc[MI_M] = mu;
+}
+
+// the block count into the graph's counts[2] (counts[3] = 0)
+__global__ void k_counts_pattern(const int *__restrict__ misc, int *__restrict__ counts)
+{
+    counts[2] = misc[MI_READ];
+    counts[3] = 0;
 }
 
 // bounding box of n points into misc[MI_BBOX .. MI_BBOX + 5] (ordered ints)
@@ -1286,7 +1348,9 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
 
     // ---- block pattern ----
     const int words = ed_div_up(m, 32);
-    int nnzb, n_runs;
+    const int cap = ctx->max_nnzb;
+    const int *nnzb_dev = ctx->misc + MI_READ, *nruns_dev = ctx->misc + MI_READ + 1;
+    const int g256 = 4 * ctx->num_sms;   // grid of the grid-stride launches over blocks and runs
     {
         ED_CUDA_TRY(cudaMemsetAsync(ctx->bitmap, 0, sizeof(uint32_t) * (size_t)m * words, st));
         // (the pairs of the points come from their runs: n_runs is on the device, the
@@ -1300,66 +1364,50 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         // the block count and the number of runs go to the host (pinned copy +
         // event) while the block lists, which need only the row pointer, are
         // filled (checking the count against the capacity)
-        int *nz_host = ctx->pinned + ED_MAX_PCG_GRID + 6;
-        ED_CUDA_TRY(cudaMemcpyAsync(nz_host, ctx->misc + MI_READ, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
         k_row_fill<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
                                                     ctx->diag_pos, ctx->max_nnzb, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
-        ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
-        nnzb = nz_host[0];
-        n_runs = nz_host[1];
-        if (nnzb > ctx->max_nnzb) return ED_ERR_CAPACITY;
-        if (n_runs < 1 || n_runs > NT) return ED_ERR_STATE;
-        k_tpos<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
+        // from here on the block count (misc[MI_READ]) and the run count
+        // (misc[MI_READ + 1]) are read on the device: the launches are sized
+        // for the capacities, grid-stride, and nothing runs past a block count
+        // above the capacity (the row fill reported ED_ERR_CAPACITY)
+        k_tpos<<<g256, 256, 0, st>>>(nnzb_dev, cap, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, nnzb, st, ctx->misc + MI_READ + 2)) != ED_OK) return s;
-        k_compact_upper<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, ctx->flag_a, ctx->flag_b, ctx->diag_pos,
-                                                               ctx->up_list); ed_note_launch();
+        if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, cap, st, ctx->misc + MI_READ + 2, nnzb_dev)) != ED_OK)
+            return s;
+        k_compact_upper<<<g256, 256, 0, st>>>(nnzb_dev, cap, m, ctx->flag_a, ctx->flag_b, ctx->diag_pos, ctx->up_list); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
 
     // ---- incidences (block, run), sorted by block (stable: run order within a
     // block), and the assembly's per-block records ----
-    const int ne = 10 * n_runs;
-    int n_upper = 0;
     {
-        k_inc_gen<<<ed_div_up(n_runs, 128), 128, 0, st>>>(n_runs, ctx->run_start, ctx->sidx, ctx->row_ptr, ctx->col,
-                                                          ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
+        k_inc_gen<<<g256, 256, 0, st>>>(nruns_dev, nnzb_dev, cap, ctx->run_start, ctx->sidx, ctx->row_ptr, ctx->col,
+                                        ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         // by block, each block's list in run order
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->icnt, 0, sizeof(int) * 2 * (size_t)(nnzb + 1), st));
-        int *ifill = ctx->icnt + nnzb + 1;
-        k_ic_count<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->icnt); ed_note_launch();
+        ED_CUDA_TRY(cudaMemsetAsync(ctx->icnt, 0, sizeof(int) * 2 * (size_t)(cap + 1), st));
+        int *ifill = ctx->icnt + cap + 1;
+        k_ic_count<<<4 * g256, 256, 0, st>>>(nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->icnt); ed_note_launch();
         ED_LAUNCH_CHECK();
-        if ((s = ed_scan_exclusive(ctx, ctx->icnt, ctx->ent_start, nnzb, st)) != ED_OK) return s;
-        k_ic_place<<<ed_div_up(ne, 256), 256, 0, st>>>(ne, ctx->ent_key, ctx->ent_val, ctx->ent_start, ifill, ctx->inc); ed_note_launch();
-        k_ic_sort<<<ed_div_up(nnzb, 4), 128, 0, st>>>(nnzb, ctx->ent_start, ctx->inc); ed_note_launch();
-        k_fin_pack<<<ed_div_up(nnzb, 256), 256, 0, st>>>(nnzb, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow,
-                                                         ctx->col, ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr,
-                                                         ctx->fin_info); ed_note_launch();
+        if ((s = ed_scan_exclusive(ctx, ctx->icnt, ctx->ent_start, cap, st, nullptr, nnzb_dev)) != ED_OK) return s;
+        k_ic_place<<<4 * g256, 256, 0, st>>>(nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->ent_val, ctx->ent_start,
+                                              ifill, ctx->inc); ed_note_launch();
+        k_ic_sort<<<std::min(ed_div_up(cap, 4), 32 * ctx->num_sms), 128, 0, st>>>(nnzb_dev, cap, ctx->ent_start,
+                                                                                  ctx->inc); ed_note_launch();
+        k_fin_pack<<<g256, 256, 0, st>>>(nnzb_dev, cap, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow, ctx->col,
+                                         ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr, ctx->fin_info); ed_note_launch();
+        k_counts_pattern<<<1, 1, 0, st>>>(ctx->misc, graph->counts); ed_note_launch();
         ED_LAUNCH_CHECK();
-        // one host read for what the rest of the build needs: the upper-block
-        // count (gathered into misc) and the row pointer (pinned)
+        // what the host needs later (the counts, the row pointer of the PCG
+        // plan) goes to pinned memory; ed_graph_ready reads it at the first
+        // call that needs it
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->row_ptr_host, ctx->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
-        ED_CUDA_TRY(cudaEventRecord(ctx->ev_misc, st));
-        ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
-        memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
-        n_upper = hm[MI_READ + 2];
-        if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
-        ctx->pinned[ED_MAX_PCG_GRID + 1] = nnzb;
-        ctx->pinned[ED_MAX_PCG_GRID + 2] = 0;
-        ED_CUDA_TRY(cudaMemcpyAsync(graph->counts + 2, ctx->pinned + ED_MAX_PCG_GRID + 1, 2 * sizeof(int),
-                                    cudaMemcpyHostToDevice, st));
-        n_upper += m;   // strictly upper blocks + the diagonal
-        if (2 * n_upper != nnzb + m) return ED_ERR_STATE;   // the pattern must be symmetric with a full diagonal
+        ED_CUDA_TRY(cudaEventRecord(ctx->ev_build, st));
     }
     // (the assembly's per-node arrival counts start the frame at zero)
     ED_CUDA_TRY(cudaMemsetAsync(ctx->fin_cnt, 0, sizeof(int) * (size_t)m, st));
-    // row partition and shared-memory plan of the PCG solve
-    ctx->m = m;
-    if ((s = ed_pcg_plan(ctx, ctx->row_ptr_host, st)) != ED_OK) return s;
 
     ctx->pos = ctx->n_kp > 0 ? (const float *)ctx->comb_pos : pos;
     ctx->nrm = ctx->n_kp > 0 ? (const float *)ctx->comb_nrm : nrm;
@@ -1370,10 +1418,36 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     ctx->weight_mode = prm->weight_mode;
     ctx->sigma = prm->sigma;
     ctx->m = m;
+    ctx->n_entries = 10 * NT;
+    ctx->build_pending = 1;
+    ctx->have_graph = 1;
+    return ED_OK;
+}
+
+// The pattern's counts and the PCG plan of the last build, once its queued
+// work has reached the copies of ed_build_graph's end (one host wait, at the
+// first call that needs them).  An error the build's kernels reported is
+// returned here, and the context then has no graph.
+ed_status ed_graph_ready(ed_context *ctx, cudaStream_t st)
+{
+    if (!ctx->have_graph) return ED_ERR_STATE;
+    if (!ctx->build_pending) return ED_OK;
+    ctx->build_pending = 0;
+    ctx->have_graph = 0;
+    ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_build));
+    int hm[MI_COUNT];
+    memcpy(hm, ctx->misc_host, sizeof(int) * MI_COUNT);
+    if (hm[MI_STATUS] != ED_OK) return (ed_status)hm[MI_STATUS];
+    const int m = ctx->m, nnzb = hm[MI_READ], n_runs = hm[MI_READ + 1], n_upper = hm[MI_READ + 2] + m;
+    if (nnzb > ctx->max_nnzb) return ED_ERR_CAPACITY;
+    if (n_runs < 1 || n_runs > ctx->N) return ED_ERR_STATE;
+    if (2 * n_upper != nnzb + m) return ED_ERR_STATE;   // the pattern must be symmetric with a full diagonal
     ctx->nnzb = nnzb;
     ctx->n_upper = n_upper;
-    ctx->n_entries = 10 * NT;
     ctx->n_runs = n_runs;
+    // row partition and shared-memory plan of the PCG solve
+    ed_status s = ed_pcg_plan(ctx, ctx->row_ptr_host, st);
+    if (s != ED_OK) return s;
     ctx->have_graph = 1;
     return ED_OK;
 }

@@ -1046,7 +1046,7 @@ ed_status ed_pcg_batch_plan(ed_context *const *ctxs, int count, int nt, int grid
     static thread_local int rows_start[ED_MAX_PCG_GRID + 1];
     for (int p = 0; p < count; ++p) {
         ed_context *c = ctxs[p];
-        if (!c->have_graph) return ED_ERR_STATE;
+        if (!c->have_graph || c->build_pending) return ED_ERR_STATE;   // (the batch read the counts at creation)
         if ((s = ed_pcg_make_plan(c->row_ptr_host, c->m, alloc[p], nt, &bp->plan[p], rows_start)) != ED_OK) return s;
         ED_CUDA_TRY(cudaMemcpy(c->pcg_rows_b, rows_start, sizeof(int) * (alloc[p] + 1), cudaMemcpyHostToDevice));
         bp->cta_first[p + 1] = bp->cta_first[p] + alloc[p];

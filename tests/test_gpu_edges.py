@@ -153,8 +153,12 @@ def test_block_capacity_is_an_error_not_a_fault():
     pos = torch.from_numpy(s.model_pos).cuda()
     nrm = torch.from_numpy(s.model_nrm).cuda()
     r = C.radius_for(SMALL)
+    # the build queues the pattern and returns; the capacity error comes with
+    # the first read of the pattern's size
+    g = ctx.build_graph(pos, nrm, node_radius=r, max_nodes=64, sigma=r)
+    assert g.m > 0
     with pytest.raises(E.EDError) as ei:
-        ctx.build_graph(pos, nrm, node_radius=r, max_nodes=64, sigma=r)
+        g.nnzb
     assert ei.value.status == 3
     depth = torch.from_numpy(s.tgt_depth).cuda()
     nmap = ctx.compute_normals(depth, s.intr, s.cfg.normal_half_width)
