@@ -53,7 +53,7 @@ size_t carve(ed_context *c, char *base)
     c->cell_node = k.take<int>(cells);
     c->kcell_start = k.take<int>(cells + 1);
     c->kcell_cnt = k.take<int>(cells + 1);
-    c->kcell_nodes = k.take<int>(M);
+    c->kcell_pos = k.take<float4>(M);
     c->bm_words = (int)((M + 31) / 32);
     c->bitmap = k.take<uint32_t>(M * (size_t)c->bm_words);
     c->row_ptr = k.take<int>(M + 1);

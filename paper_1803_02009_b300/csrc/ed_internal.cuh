@@ -103,7 +103,7 @@ struct ed_context {
     int *cell_node;          // [cells]
     int *kcell_start;        // [cells + 1]
     int *kcell_cnt;          // [cells]
-    int *kcell_nodes;        // [max_nodes]
+    float4 *kcell_pos;       // [max_nodes] node positions by search cell (w: the node index as int bits)
     // pattern
     uint32_t *bitmap;        // [max_nodes * words]
     int bm_words;

@@ -350,13 +350,18 @@ __global__ void k_kcell_count(const float4 *__restrict__ nodes, const int *__res
     atomicAdd(&cnt[L], 1);
 }
 
-__global__ void k_kcell_fill(const int *__restrict__ m_dev, const int *__restrict__ start, int *__restrict__ fill,
-                             const int *__restrict__ cell_of_node, int *__restrict__ kn)
+// every node's position, its index in w (as int bits), in its search cell's
+// range (the order inside a cell is immaterial: the search orders by key and
+// index)
+__global__ void k_kcell_fill(const int *__restrict__ m_dev, const float4 *__restrict__ nodes,
+                             const int *__restrict__ start, int *__restrict__ fill, const int *__restrict__ cell_of_node,
+                             float4 *__restrict__ kpos)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= *m_dev) return;
     const int L = cell_of_node[j];
-    kn[start[L] + atomicAdd(&fill[L], 1)] = j;
+    const float4 g = nodes[j];
+    kpos[start[L] + atomicAdd(&fill[L], 1)] = make_float4(g.x, g.y, g.z, __int_as_float(j));
 }
 
 #define KNN_S 5   // K + 1 nearest (Eq. 2 needs the (K+1)-th distance)
@@ -379,7 +384,7 @@ __device__ __forceinline__ void topk_ins(float *kk, int *ii, float key, int id)
 // node outside rings 0..R is at least R cells away.  Then the weights.
 __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__restrict__ nodes,
                       const int *__restrict__ m_dev, const int *__restrict__ misc, const float *__restrict__ fmisc,
-                      const int *__restrict__ start, const int *__restrict__ kn, int mode, float sigma,
+                      const int *__restrict__ start, const float4 *__restrict__ kpos, int mode, float sigma,
                       ushort4 *__restrict__ idx_out, float4 *__restrict__ w_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,9 +418,8 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
                     if (ax >= 0 && ax < dims[0]) {
                         const int L = ax + dims[0] * (ay + dims[1] * az);
                         for (int t = start[L]; t < start[L + 1]; ++t) {
-                            const int j = kn[t];
-                            const float4 g = __ldg(nodes + j);
-                            topk_ins(kk, ii, ed_key(p.x, p.y, p.z, g.x, g.y, g.z), j);
+                            const float4 g = __ldg(kpos + t);
+                            topk_ins(kk, ii, ed_key(p.x, p.y, p.z, g.x, g.y, g.z), __float_as_int(g.w));
                         }
                     }
                     if (R == 0) break;
@@ -1285,10 +1289,10 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->kcell_cnt, ctx->kcell_start, kcells, st)) != ED_OK) return s;
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
-        k_kcell_fill<<<ed_div_up(max_nodes, 256), 256, 0, st>>>(m_dev, ctx->kcell_start, ctx->kcell_cnt, cell_of_node,
-                                                                ctx->kcell_nodes); ed_note_launch();
+        k_kcell_fill<<<ed_div_up(max_nodes, 256), 256, 0, st>>>(m_dev, G4, ctx->kcell_start, ctx->kcell_cnt,
+                                                                cell_of_node, ctx->kcell_pos); ed_note_launch();
         k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_start,
-                                                  ctx->kcell_nodes, prm->weight_mode, prm->sigma,
+                                                  ctx->kcell_pos, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
