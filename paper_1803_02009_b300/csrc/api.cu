@@ -96,7 +96,6 @@ size_t carve(ed_context *c, char *base)
     c->minv = k.take<float>(M * 144);
     c->pose_blk = k.take<float>(72);
     c->dmom = k.take<float>(M * 72);
-    c->fin_cnt = k.take<int>(M);
     c->bsr_s = k.take<float>(nnzb * 144);
     c->grad_s = k.take<float>(P);
     c->pnode_s = k.take<float>(M * 72);
@@ -179,7 +178,6 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
         cudaMemset(c->misc, 0, sizeof(int) * MI_COUNT) != cudaSuccess ||
         cudaMemset(c->dmisc, 0, sizeof(double) * 64) != cudaSuccess ||
         cudaMemset(c->pcg_part, 0, sizeof(double) * 2 * (size_t)ED_MAX_PCG_GRID * ED_PCG_PART) != cudaSuccess ||
-        cudaMemset(c->fin_cnt, 0, sizeof(int) * (size_t)c->lim.max_nodes) != cudaSuccess ||
         cudaMemset(c->lb_ticket, 0, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(c->lb_state, 0, sizeof(unsigned long long) * (size_t)c->max_k1_ctas) != cudaSuccess ||
         cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_state_len) != cudaSuccess ||

@@ -146,7 +146,6 @@ struct ed_context {
     float *minv;             // [m][144] block-Jacobi inverses
     float *pose_blk;         // [36] pose block, [36..72) its inverse
     float *dmom;             // [m][72] moments (60) and J^T r (12) of the diagonal blocks, per step
-    int *fin_cnt;            // [m] arrivals of a node's two diagonal warps in the assembly (0 between steps)
     unsigned long long *lb_ticket;   // point pass of a step: epoch << 32 | chunks handed out
     unsigned long long *lb_state;    // [max_k1_ctas] per chunk: epoch << 34 | flag << 32 | valid rows
     // Levenberg-Marquardt: the undamped system and the parameters of the last

@@ -607,7 +607,6 @@ struct AsmArgs {
     float w_rot, w_reg, lambda, jitter;
     float *bsr, *grad, *pnode, *minv;
     float *dmom;             // [m][72]: moments of the diagonal blocks (60) and their J^T r (12)
-    int *fin_cnt;            // [m]: arrivals of the node's two diagonal warps (reset by the finaliser)
     float2 *node_energy;
     int *status;
 };
@@ -1037,39 +1036,12 @@ __device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, con
 
 #define ASM_WARPS 4
 
-// The diagonal block of node j needs the moments (warp of kind 0) and J^T r
-// (first node-row warp): each of the two warps, after writing its part to
-// dmom[j], arrives on fin_cnt[j] (fence, then the atomic); the second one to
-// arrive finalises the block (fin_diag) while the rest of the assembly runs,
-// and resets the count for the next step.  Its shared scratch is the warp's
-// column-sum buffer `red` (free by then, 524 of its 1,984 floats).
-template <bool INV>
-__device__ __forceinline__ void diag_arrive(const AsmArgs &a, int4 i0, int4 i1, float2 *red)
-{
-    const int lane = threadIdx.x & 31;
-    const int j = i0.y;
-    __threadfence();   // this lane's part of dmom[j] before the arrival
-    __syncwarp();
-    int prev = 0;
-    if (lane == 0) prev = atomicAdd(a.fin_cnt + j, 1);
-    prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev == 0) return;   // the other warp finalises
-    if (lane == 0) a.fin_cnt[j] = 0;
-    __threadfence();   // the other warp's part, observed through its arrival
-    float *F = reinterpret_cast<float *>(red);
-    float *sM = F, *sH = F + 72, *sL = F + 216, *sX = F + 360, *sS = F + 372, *sNx = F + 388;
-    float4 *sNg = reinterpret_cast<float4 *>(F + 484);
-    int *sNk = reinterpret_cast<int *>(F + 516);
-    for (int q = lane; q < 72; q += 32) sM[q] = __ldcg(a.dmom + (long)j * 72 + q);
-    __syncwarp();
-    fin_diag<INV>(a, i0, i1, sM, sM + 60, sH, sX, sS, sL, sNk, sNg, sNx);
-}
 
 // One warp per work item, four per CTA, in this order: the moments of the m
 // diagonal blocks (to dmom[j][0..60)), the two halves of J^T r and the
 // pose-node block of every node (J^T r to dmom[j][60..72), the pose-node
-// block to pnode) -- the later of a node's two dmom writers finalises its
-// diagonal block -- then the off-diagonal upper
+// block to pnode; k_fin_diag finalises the diagonal blocks from dmom), then
+// the off-diagonal upper
 // blocks, two per warp (one per 16-lane half: they hold a few dozen points
 // each), each finalised by its half.
 template <bool INV>
@@ -1099,7 +1071,6 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
         role0(a, i1.x, i1.y, 0, 1, gj, M, red);
         __syncwarp();
         for (int q = lane; q < 60; q += 32) a.dmom[(long)u * 72 + q] = M[q];
-        diag_arrive<INV>(a, i0, i1, red);
     } else if (kind == 1) {
         const int h = (w - m) & 1;
         if (lane < 9) s_R[wid][lane] = __ldcg(a.pose_R + lane);
@@ -1111,7 +1082,6 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
         if (h == 0) {
             if (lane < 12) a.dmom[(long)u * 72 + 60 + lane] = M[lane];
             for (int q = lane; q < 36; q += 32) pn[q] = M[12 + q];
-            diag_arrive<INV>(a, i0, i1, red);
         } else {
             for (int q = lane; q < 36; q += 32) pn[36 + q] = M[q];
         }
@@ -1119,6 +1089,29 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
         role0_seg(a, i1.x, has ? i1.y : 0, gj, M, red);
         if (has) fin_offdiag_seg(a, i0, i1, gj, gl, M + 60 * (lane >> 4));
     }
+}
+
+
+// the diagonal blocks from their moments and J^T r (dmom), one warp per node:
+// E_rot and E_reg terms, the gradient, the node energies and (INV) the
+// block-Jacobi inverse (fin_diag)
+template <bool INV>
+__global__ void __launch_bounds__(32 * ASM_WARPS) k_fin_diag(AsmArgs a)
+{
+    __shared__ __align__(16) float sM[ASM_WARPS][72];
+    __shared__ float sH[ASM_WARPS][144], sL[ASM_WARPS][144], sX[ASM_WARPS][12], sS[ASM_WARPS][16];
+    __shared__ int sNk[ASM_WARPS][ED_MAX_KG];
+    __shared__ float4 sNg[ASM_WARPS][ED_MAX_KG];
+    __shared__ __align__(16) float sNx[ASM_WARPS][12 * ED_MAX_KG];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = (int)blockIdx.x * ASM_WARPS + wid;
+    const int4 i0 = j < a.m ? a.info[2 * j] : make_int4(0, 0, 0, 0), i1 = j < a.m ? a.info[2 * j + 1] : make_int4(0, 0, 0, 0);
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    if (j >= a.m) return;
+    for (int q = lane; q < 72; q += 32) sM[wid][q] = __ldcg(a.dmom + (long)j * 72 + q);
+    __syncwarp();
+    fin_diag<INV>(a, i0, i1, sM[wid], sM[wid] + 60, sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid]);
 }
 
 #define FIN_WARPS 4
@@ -1602,13 +1595,14 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     aa.node_energy = ctx->node_energy;
     aa.status = ctx->misc + MI_STATUS;
     aa.dmom = ctx->dmom;
-    aa.fin_cnt = ctx->fin_cnt;
     {
         // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks in pairs
         const int grid = ed_div_up(3 * m + (aa.n_off + 1) / 2, ASM_WARPS);
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_CUDA_TRY(ed_launch_pdl(lm ? k_assemble<false> : k_assemble<true>, dim3(grid), dim3(32 * ASM_WARPS), 0, st,
                                   aa)); ed_note_launch();
+        ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS)),
+                                  dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();
     }

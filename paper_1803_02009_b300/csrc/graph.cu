@@ -1410,8 +1410,6 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->misc_host, ctx->misc, sizeof(int) * MI_COUNT, cudaMemcpyDeviceToHost, st));
         ED_CUDA_TRY(cudaEventRecord(ctx->ev_build, st));
     }
-    // (the assembly's per-node arrival counts start the frame at zero)
-    ED_CUDA_TRY(cudaMemsetAsync(ctx->fin_cnt, 0, sizeof(int) * (size_t)m, st));
 
     ctx->pos = ctx->n_kp > 0 ? (const float *)ctx->comb_pos : pos;
     ctx->nrm = ctx->n_kp > 0 ? (const float *)ctx->comb_nrm : nrm;
