@@ -1115,6 +1115,7 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_fin_diag(AsmArgs a)
 }
 
 #define FIN_WARPS 4
+#define TOT_WARPS 16   // k_fin_totals: 512 threads over the node energies
 
 // arguments of k_fin_totals: the energy totals of the step from the node
 // energies and the pose pass's sums
@@ -1132,14 +1133,14 @@ struct FinArgs {
 // (float-float), the energy of Eq. (3) from them and the pose pass's sums,
 // the non-finite check, the step's statistics; it also clears the arrival
 // count of the step's PCG
-__global__ void __launch_bounds__(32 * FIN_WARPS) k_fin_totals(FinArgs a)
+__global__ void __launch_bounds__(32 * TOT_WARPS) k_fin_totals(FinArgs a)
 {
     ed_pdl_wait();
     ed_pdl_trigger();
-    __shared__ float2 s_w[FIN_WARPS][2];
+    __shared__ float2 s_w[TOT_WARPS][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float2 er = make_float2(0.f, 0.f), eg = er;
-    for (int j = threadIdx.x; j < a.m; j += 32 * FIN_WARPS) {
+    for (int j = threadIdx.x; j < a.m; j += 32 * TOT_WARPS) {
         const float2 e = __ldcg(a.node_energy + j);
         er = ed_ff_add1(er, e.x);
         eg = ed_ff_add1(eg, e.y);
@@ -1153,7 +1154,7 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_fin_totals(FinArgs a)
     __syncthreads();
     if (threadIdx.x == 0) {
         float2 a0 = s_w[0][0], a1 = s_w[0][1];
-        for (int k = 1; k < FIN_WARPS; ++k) {
+        for (int k = 1; k < TOT_WARPS; ++k) {
             a0 = ed_ff_add(a0, s_w[k][0]);
             a1 = ed_ff_add(a1, s_w[k][1]);
         }
@@ -1618,9 +1619,9 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     if (fork_pose) {
         // (after the join with the pose stream: a normal launch)
         ED_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-        k_fin_totals<<<1, 32 * FIN_WARPS, 0, st>>>(fa); ed_note_launch();
+        k_fin_totals<<<1, 32 * TOT_WARPS, 0, st>>>(fa); ed_note_launch();
     } else {
-        ED_CUDA_TRY(ed_launch_pdl(k_fin_totals, dim3(1), dim3(32 * FIN_WARPS), 0, st, fa)); ed_note_launch();
+        ED_CUDA_TRY(ed_launch_pdl(k_fin_totals, dim3(1), dim3(32 * TOT_WARPS), 0, st, fa)); ed_note_launch();
     }
     ed_tm_end(ctx, ED_KERNEL_FINALIZE, st);
     ED_LAUNCH_CHECK();
