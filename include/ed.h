@@ -478,6 +478,9 @@ typedef struct ed_batch_schedule {
     int problems_per_launch;  /* problems sharing one persistent PCG launch (1..32); more
                                  problems per launch means fewer CTAs (more node rows) each */
     int streams;              /* internal streams for the per-problem kernels */
+    int asm_blocks_per_warp;  /* off-diagonal 12x12 blocks per assembly warp: 2 (one per
+                                 16-lane half) or 1 (the whole warp streams one block) */
+    int point_chunk;          /* points per CTA of the step's point pass: 512 or 256 */
 } ed_batch_schedule;
 
 /*
@@ -493,7 +496,10 @@ ed_status ed_batch_query_workspace(ed_context *const *ctxs, int count, size_t *b
  * size), which must outlive the batch.  Creates `count` internal streams and
  * events (no device memory is allocated).  The default schedule is 512-thread
  * PCG CTAs, the largest power-of-two number of problems per launch whose CTA
- * shares fit in shared memory, and min(count, 16) streams.  Rebuilding the
+ * shares fit in shared memory, min(count, 16) streams, two off-diagonal blocks
+ * per assembly warp and 512 points per point-pass CTA.  A schedule's assembly
+ * and point-pass choices are written into the member contexts (their own
+ * ed_gn_step calls use them as well; a context starts with 2 and 512).  Rebuilding the
  * graph of a member context invalidates the batch: destroy and create it
  * again.  Returns ED_ERR_CAPACITY if no grouping fits.
  */
@@ -503,8 +509,9 @@ ed_status ed_batch_destroy(ed_batch *batch);
 
 /*
  * Sets the schedule (synchronises the device; drops a captured graph).
- * ED_ERR_CAPACITY if a problem's CTA share does not fit in shared memory
- * under it; the previous schedule then stays in force.
+ * ED_ERR_ARG for a field outside its listed values; ED_ERR_CAPACITY if a
+ * problem's CTA share does not fit in shared memory under it; the previous
+ * schedule then stays in force.
  */
 ed_status ed_batch_set_schedule(ed_batch *batch, const ed_batch_schedule *schedule);
 ed_status ed_batch_get_schedule(const ed_batch *batch, ed_batch_schedule *schedule);
@@ -539,10 +546,12 @@ ed_status ed_batch_capture(ed_batch *batch, const ed_frame *frames, const ed_sol
 ed_status ed_batch_launch(ed_batch *batch, cudaStream_t stream);
 
 /*
- * Autotuner: times one captured batched iteration under every feasible
+ * Autotuner: times one captured batched iteration under every feasible PCG
  * schedule (PCG threads 512 / 256; problems per launch 1, 2, 4, ... up to
- * all; 4 or up to 16 streams), restoring every problem's x, x_master and
- * pose after each run, and keeps the fastest, returned in `chosen` (with its
+ * all; 4 or up to 16 streams) with the default assembly, then under the
+ * assembly and point-pass choices (off-diagonal blocks per warp 2 / 1, points
+ * per CTA 512 / 256) with the best PCG schedule, restoring every problem's x,
+ * x_master and pose after each run, and keeps the fastest, returned in `chosen` (with its
  * time in ms in best_ms; either may be NULL).  Synchronises `stream` and the
  * device; drops a captured graph; `stream` must be a created stream.  Run it with the arguments of the real
  * iterations (the timings depend on the association of the current x).

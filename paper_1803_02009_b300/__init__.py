@@ -89,11 +89,13 @@ class DownsampleParamsC(C.Structure):
 
 
 class BatchSchedule(C.Structure):
-    _fields_ = [("pcg_threads", C.c_int), ("problems_per_launch", C.c_int), ("streams", C.c_int)]
+    _fields_ = [("pcg_threads", C.c_int), ("problems_per_launch", C.c_int), ("streams", C.c_int),
+                ("asm_blocks_per_warp", C.c_int), ("point_chunk", C.c_int)]
 
     def as_dict(self):
         return {"pcg_threads": self.pcg_threads, "problems_per_launch": self.problems_per_launch,
-                "streams": self.streams}
+                "streams": self.streams, "asm_blocks_per_warp": self.asm_blocks_per_warp,
+                "point_chunk": self.point_chunk}
 
 
 _vp = C.c_void_p
@@ -670,8 +672,11 @@ class Batch:
         _check("ed_batch_get_schedule", lib().ed_batch_get_schedule(self.h, C.byref(sch)))
         return sch.as_dict()
 
-    def set_schedule(self, pcg_threads, problems_per_launch, streams):
-        sch = BatchSchedule(int(pcg_threads), int(problems_per_launch), int(streams))
+    def set_schedule(self, pcg_threads, problems_per_launch, streams, asm_blocks_per_warp=2, point_chunk=512):
+        """ed_batch_set_schedule; the assembly and point-pass choices are written
+        into the member contexts (their own ed_gn_step calls use them too)."""
+        sch = BatchSchedule(int(pcg_threads), int(problems_per_launch), int(streams), int(asm_blocks_per_warp),
+                            int(point_chunk))
         _check("ed_batch_set_schedule", lib().ed_batch_set_schedule(self.h, C.byref(sch)))
 
 

@@ -172,6 +172,8 @@ extern "C" ed_status ed_create(const ed_limits *limits, void *workspace, size_t 
     c->ws = (char *)workspace;
     c->ws_bytes = workspace_bytes;
     c->wait_ns = ED_BAR_TIMEOUT_NS;
+    c->asm_pairs = 2;
+    c->pt_chunk = 512;
     c->bar_extra = 0;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||

@@ -52,7 +52,8 @@ static ed_status batch_plan(ed_batch *b, const ed_batch_schedule &s)
 {
     const int count = b->count;
     if ((s.pcg_threads != 256 && s.pcg_threads != 512) || s.problems_per_launch < 1 ||
-        s.problems_per_launch > ED_MAX_BATCH_LAUNCH || s.streams < 1)
+        s.problems_per_launch > ED_MAX_BATCH_LAUNCH || s.streams < 1 ||
+        (s.asm_blocks_per_warp != 1 && s.asm_blocks_per_warp != 2) || (s.point_chunk != 256 && s.point_chunk != 512))
         return ED_ERR_ARG;
     // the row starts of a batched launch are rewritten below: nothing may run
     if (cudaDeviceSynchronize() != cudaSuccess) return ED_ERR_CUDA;
@@ -81,6 +82,10 @@ static ed_status batch_plan(ed_batch *b, const ed_batch_schedule &s)
     }
     b->group_first[ng] = k;
     b->n_groups = ng;
+    for (int p = 0; p < count; ++p) {   // the assembly and point-pass schedule of every member
+        b->ctx[p]->asm_pairs = s.asm_blocks_per_warp;
+        b->ctx[p]->pt_chunk = s.point_chunk;
+    }
     b->sched = s;
     b->sched.problems_per_launch = ppl;
     b->sched.streams = std::min(s.streams, count);
@@ -212,6 +217,8 @@ extern "C" ed_status ed_batch_create(ed_context *const *ctxs, int count, void *w
     ed_batch_schedule d;
     d.pcg_threads = 512;
     d.streams = std::min(count, 16);
+    d.asm_blocks_per_warp = 2;
+    d.point_chunk = 512;
     s = ED_ERR_CAPACITY;
     for (int ppl = std::min(count, ED_MAX_BATCH_LAUNCH); ppl >= 1 && s == ED_ERR_CAPACITY; ppl = ppl > 1 ? ppl / 2 : 0) {
         d.problems_per_launch = ppl;
@@ -347,10 +354,13 @@ static ed_status batch_save(ed_batch *b, float *const *x, double *const *xm, dou
     return ED_OK;
 }
 
-// Times every feasible schedule (PCG threads 512 / 256; problems per launch
-// 1, 2, 4, ... up to all; 4 or up to 16 streams) as a captured one-iteration
-// graph, the problems' x, x_master and pose restored after each run, and keeps
-// the fastest.  Any graph captured before is dropped.
+// Times schedules as captured one-iteration graphs, the problems' x, x_master
+// and pose restored after each run, and keeps the fastest: first every
+// feasible PCG schedule (threads 512 / 256; problems per launch 1, 2, 4, ...
+// up to all; 4 or up to 16 streams) with the default assembly, then, with the
+// best of those, the assembly and point-pass schedules (off-diagonal blocks
+// per warp 2 / 1, points per CTA 512 / 256).  Any graph captured before is
+// dropped.
 extern "C" ed_status ed_batch_autotune(ed_batch *b, const ed_frame *frames, const ed_solver_params *params,
                                        float *const *x, double *const *x_master, double *const *pose,
                                        ed_stats *const *stats, cudaStream_t st, ed_batch_schedule *chosen,
@@ -377,6 +387,8 @@ extern "C" ed_status ed_batch_autotune(ed_batch *b, const ed_frame *frames, cons
                 c.pcg_threads = nt;
                 c.problems_per_launch = ppl;
                 c.streams = w;
+                c.asm_blocks_per_warp = 2;
+                c.point_chunk = 512;
                 cands.push_back(c);
             }
     cudaEvent_t e0, e1;
@@ -385,27 +397,41 @@ extern "C" ed_status ed_batch_autotune(ed_batch *b, const ed_frame *frames, cons
     if ((s = batch_save(b, x, x_master, pose, true, st)) != ED_OK) return s;
     float best = -1.f;
     ed_batch_schedule best_s = orig;
-    for (const ed_batch_schedule &c : cands) {
-        if (batch_plan(b, c) != ED_OK) continue;   // infeasible: a CTA share does not fit
-        cudaGraphExec_t ex = nullptr;
-        unsigned long long nk = 0;
-        if (batch_capture(b, frames, params, x, x_master, pose, stats, 1, st, &ex, &nk) != ED_OK) continue;
-        float ms = -1.f;
-        bool ok = cudaGraphLaunch(ex, st) == cudaSuccess;                     // warm-up
-        ok = ok && batch_save(b, x, x_master, pose, false, st) == ED_OK;
-        ok = ok && cudaEventRecord(e0, st) == cudaSuccess && cudaGraphLaunch(ex, st) == cudaSuccess &&
-             cudaEventRecord(e1, st) == cudaSuccess;
-        ok = ok && batch_save(b, x, x_master, pose, false, st) == ED_OK;
-        ok = ok && cudaStreamSynchronize(st) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-        ed_note_launches(2 * nk);
-        cudaGraphExecDestroy(ex);
-        if (!ok) {
-            s = ED_ERR_CUDA;
-            break;
+    for (int stage = 0; stage < 2 && s == ED_OK; ++stage) {
+        if (stage == 1) {   // the assembly and point-pass options on the best PCG schedule
+            if (best < 0.f) break;
+            cands.clear();
+            for (int bpw = 2; bpw >= 1; --bpw)
+                for (int ch = 512; ch >= 256; ch /= 2) {
+                    if (bpw == best_s.asm_blocks_per_warp && ch == best_s.point_chunk) continue;
+                    ed_batch_schedule c = best_s;
+                    c.asm_blocks_per_warp = bpw;
+                    c.point_chunk = ch;
+                    cands.push_back(c);
+                }
         }
-        if (best < 0.f || ms < best) {
-            best = ms;
-            best_s = b->sched;
+        for (const ed_batch_schedule &c : cands) {
+            if (batch_plan(b, c) != ED_OK) continue;   // infeasible: a CTA share does not fit
+            cudaGraphExec_t ex = nullptr;
+            unsigned long long nk = 0;
+            if (batch_capture(b, frames, params, x, x_master, pose, stats, 1, st, &ex, &nk) != ED_OK) continue;
+            float ms = -1.f;
+            bool ok = cudaGraphLaunch(ex, st) == cudaSuccess;                     // warm-up
+            ok = ok && batch_save(b, x, x_master, pose, false, st) == ED_OK;
+            ok = ok && cudaEventRecord(e0, st) == cudaSuccess && cudaGraphLaunch(ex, st) == cudaSuccess &&
+                 cudaEventRecord(e1, st) == cudaSuccess;
+            ok = ok && batch_save(b, x, x_master, pose, false, st) == ED_OK;
+            ok = ok && cudaStreamSynchronize(st) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            ed_note_launches(2 * nk);
+            cudaGraphExecDestroy(ex);
+            if (!ok) {
+                s = ED_ERR_CUDA;
+                break;
+            }
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_s = b->sched;
+            }
         }
     }
     cudaEventDestroy(e0);

@@ -183,6 +183,8 @@ struct ed_context {
     // ---- graph state (host) ----
     int have_graph;
     int build_pending;       // the last build's pattern counts and PCG plan not read yet (ed_graph_ready)
+    int asm_pairs;           // off-diagonal blocks per assembly warp (2, or 1 in a batch schedule)
+    int pt_chunk;            // points per CTA of a step's point pass (512, or 256 in a batch schedule)
     // sparse key correspondences (ed_set_keypoints); rows n_model .. N of the
     // point set are the key points, three rows each
     const float4 *kp_pos, *kp_tgt;

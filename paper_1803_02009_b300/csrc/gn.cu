@@ -209,7 +209,6 @@ struct CompactArgs {
     unsigned long long wait_ns;
 };
 
-#define CP_CHUNK 512
 
 // Exclusive prefix of the valid rows of the chunks before `chunk`: every
 // thread of the CTA waits for and adds the published counts of the chunks
@@ -249,19 +248,21 @@ __device__ __forceinline__ int chunk_prefix(const CompactArgs &c, int chunk, uns
 }
 
 // The point pass of a Gauss-Newton step over the points in node-tuple order:
-// each CTA takes the chunk of CP_CHUNK positions of its ticket, evaluates its
+// each CTA takes the chunk of CHUNK positions of its ticket (512 by default,
+// 256 in a batch schedule that picks it), evaluates its
 // points (point_eval), stages the valid rows (records, position, tuple
 // weights) in shared memory in position order, publishes its count, writes
 // its sums (per-chunk slot: the pose pass adds them in chunk order), adds up
 // the counts of the chunks before it and writes its rows after them,
 // with the first compacted row of every run that starts in the chunk (the
 // last chunk also the total).  The last ticket holder starts the next epoch.
+template <int CHUNK>
 __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, CompactArgs c)
 {
     const unsigned full = 0xffffffffu;
     __shared__ ed_pose_f P;
     __shared__ float red[ED_K1_THREADS / 32][32];
-    __shared__ __align__(16) float4 stage[4][CP_CHUNK];
+    __shared__ __align__(16) float4 stage[4][CHUNK];
     __shared__ int s_warp[ED_K1_THREADS / 32], s_chunk;
     __shared__ unsigned long long s_epoch;
     ed_pdl_wait();
@@ -287,11 +288,11 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, C
     for (int k = 0; k < 32; ++k) acc[k] = 0.f;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    constexpr int ROUNDS = CP_CHUNK / ED_K1_THREADS;
+    constexpr int ROUNDS = CHUNK / ED_K1_THREADS;
     int nvalid = 0, run_r[ROUNDS], run_l[ROUNDS];
 #pragma unroll
     for (int e = 0; e < ROUNDS; ++e) {
-        const int k = chunk * CP_CHUNK + e * ED_K1_THREADS + threadIdx.x;
+        const int k = chunk * CHUNK + e * ED_K1_THREADS + threadIdx.x;
         const bool in = k < a.n;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         const bool valid = in && point_eval(a, P, k, acc, r0, r1);
@@ -333,8 +334,8 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, C
     if (chunk == (int)gridDim.x - 1 && threadIdx.x == 0) c.vrun_start[*c.n_runs] = base + nvalid;
 }
 
-// CTAs of a step's point pass: one per contiguous chunk of CP_CHUNK positions
-static int k1_grid_step(const ed_context *ctx) { return ed_div_up(ctx->N > 0 ? ctx->N : 1, CP_CHUNK); }
+// CTAs of a step's point pass: one per contiguous chunk of pt_chunk positions
+static int k1_grid_step(const ed_context *ctx) { return ed_div_up(ctx->N > 0 ? ctx->N : 1, ctx->pt_chunk); }
 
 static int k1_grid(const ed_context *ctx)
 {
@@ -404,7 +405,8 @@ ed_status ed_point_pass(ed_context *ctx, const ed_frame *fr, const ed_solver_par
         c.status = ctx->misc + MI_STATUS;
         c.wait_ns = ctx->wait_ns;
         ed_tm_begin(ctx, ED_KERNEL_POINTS, st);
-        ED_CUDA_TRY(ed_launch_pdl(k_points_step, dim3(grid), dim3(ED_K1_THREADS), 0, st, a, c)); ed_note_launch();
+        ED_CUDA_TRY(ed_launch_pdl(ctx->pt_chunk == 256 ? k_points_step<256> : k_points_step<512>, dim3(grid),
+                                  dim3(ED_K1_THREADS), 0, st, a, c)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_POINTS, st);
     }
     ED_LAUNCH_CHECK();
@@ -1044,7 +1046,7 @@ __device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, con
 // the off-diagonal upper
 // blocks, two per warp (one per 16-lane half: they hold a few dozen points
 // each), each finalised by its half.
-template <bool INV>
+template <bool INV, int PAIRS>
 __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
 {
     __shared__ __align__(16) float sM[ASM_WARPS][120];
@@ -1054,7 +1056,7 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
     const int w = (int)blockIdx.x * ASM_WARPS + wid;
     const int m = a.m;
     const int kind = w < m ? 0 : (w < 3 * m ? 1 : 2);   // diagonal moments, node rows, off-diagonal blocks
-    const int u = kind == 0 ? w : (kind == 1 ? (w - m) >> 1 : m + 2 * (w - 3 * m) + (lane >> 4));
+    const int u = kind == 0 ? w : (kind == 1 ? (w - m) >> 1 : (PAIRS == 2 ? m + 2 * (w - 3 * m) + (lane >> 4) : m + (w - 3 * m)));
     const bool has = kind < 2 || u < m + a.n_off;   // (per half for off-diagonal blocks)
     // the block's records and node positions are fixed for the frame: loaded
     // before the wait for the point pass (whose records come after)
@@ -1086,8 +1088,14 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
             for (int q = lane; q < 36; q += 32) pn[36 + q] = M[q];
         }
     } else {
-        role0_seg(a, i1.x, has ? i1.y : 0, gj, M, red);
-        if (has) fin_offdiag_seg(a, i0, i1, gj, gl, M + 60 * (lane >> 4));
+        if (PAIRS == 2) {
+            role0_seg(a, i1.x, has ? i1.y : 0, gj, M, red);
+            if (has) fin_offdiag_seg(a, i0, i1, gj, gl, M + 60 * (lane >> 4));
+        } else {   // one block per warp (has is warp-uniform then)
+            role0(a, i1.x, i1.y, 0, 1, gj, M, red);
+            __syncwarp();
+            if (lane < 16) fin_offdiag_seg(a, i0, i1, gj, gl, M);
+        }
     }
 }
 
@@ -1597,11 +1605,14 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
     aa.status = ctx->misc + MI_STATUS;
     aa.dmom = ctx->dmom;
     {
-        // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks in pairs
-        const int grid = ed_div_up(3 * m + (aa.n_off + 1) / 2, ASM_WARPS);
+        // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks
+        // (two per warp by default; one per warp in a batch schedule that picks it)
+        const bool pairs = ctx->asm_pairs == 2;
+        const int grid = ed_div_up(3 * m + (pairs ? (aa.n_off + 1) / 2 : aa.n_off), ASM_WARPS);
+        void (*ka)(AsmArgs) = lm ? (pairs ? k_assemble<false, 2> : k_assemble<false, 1>)
+                                 : (pairs ? k_assemble<true, 2> : k_assemble<true, 1>);
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
-        ED_CUDA_TRY(ed_launch_pdl(lm ? k_assemble<false> : k_assemble<true>, dim3(grid), dim3(32 * ASM_WARPS), 0, st,
-                                  aa)); ed_note_launch();
+        ED_CUDA_TRY(ed_launch_pdl(ka, dim3(grid), dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS)),
                                   dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);

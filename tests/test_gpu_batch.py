@@ -164,11 +164,27 @@ def test_batch_schedules_agree_and_autotune_restores_state(batch_env):
             results[(nt, ppl)] = [x.cpu().numpy() for x in env["xs"]]
             for k in range(n):
                 assert _close(results[(nt, ppl)][k], env["single"][k][0], C.TOL_X), (nt, ppl, k)
+    # the assembly and point-pass choices of a schedule (written into the member contexts)
+    for bpw in (2, 1):
+        for chunk in (512, 256):
+            B.set_schedule(512, n, 4, bpw, chunk)
+            assert B.schedule()["asm_blocks_per_warp"] == bpw and B.schedule()["point_chunk"] == chunk
+            _reset(env)
+            for _ in range(N_IT):
+                B.gn_step()
+            torch.cuda.synchronize()
+            for k in range(n):
+                assert _close(env["xs"][k].cpu().numpy(), env["single"][k][0], C.TOL_X), (bpw, chunk, k)
+    for bad in ((512, 1, 4, 3, 512), (512, 1, 4, 2, 384)):
+        with pytest.raises(E.EDError):
+            B.set_schedule(*bad)
+    B.set_schedule(512, n, 4)
     _reset(env)
     before = [(x.cpu().numpy(), q.cpu().numpy()) for x, q in zip(env["xs"], env["poses"])]
     sched, ms = B.autotune()
     torch.cuda.synchronize()
     assert sched["pcg_threads"] in (256, 512) and 1 <= sched["problems_per_launch"] <= n and ms > 0
+    assert sched["asm_blocks_per_warp"] in (1, 2) and sched["point_chunk"] in (256, 512)
     for k, (x, q) in enumerate(zip(env["xs"], env["poses"])):
         assert np.array_equal(x.cpu().numpy(), before[k][0])
         assert np.array_equal(q.cpu().numpy(), before[k][1])
