@@ -461,6 +461,20 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         }
         for (int g = tot + t; g < NG; g += 32) s_grow[g] = -1;
     }
+    __syncthreads();   // (the group map above, read below)
+    // the group's row and block range for q = H p, the same in every iteration
+    // (split rows: one pass; otherwise formed per pass in the loop)
+    int g_jl = -1, g_sp = 0, g_S = 1, g_bb0 = 0, g_bb1 = 0;
+    if (split_rows && in_grp) {
+        g_jl = s_grow[grp];
+        g_sp = s_gsp[grp];
+        g_S = g_jl >= 0 ? s_rcnt[g_jl] : 1;
+        if (g_jl >= 0) {
+            g_bb0 = a.row_ptr[r0 + g_jl] - b0;
+            g_bb1 = a.row_ptr[r0 + g_jl + 1] - b0;
+        }
+    }
+    const bool all_cached = ncache >= nblk;
 
 
     // dst = M^-1 src for the own rows (thread = one output row of a node),
@@ -592,24 +606,46 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int cta, const 
         // the S splits of a row's blocks), partials C p of the pose rows ----
         AT cp[6] = {A::zero(), A::zero(), A::zero(), A::zero(), A::zero(), A::zero()};
         for (int j0 = 0; j0 < rows; j0 += NG) {
-            int jl = j0 + grp, sp = 0, S = 1;
-            if (split_rows && in_grp) {
-                jl = s_grow[grp];
-                sp = s_gsp[grp];
-                S = jl >= 0 ? s_rcnt[jl] : 1;
+            int jl = j0 + grp, sp = 0, S = 1, bb0 = g_bb0, bb1 = g_bb1;
+            if (split_rows && in_grp) {   // (one pass: the group's row and block range, formed before the loop)
+                jl = g_jl;
+                sp = g_sp;
+                S = g_S;
+            } else if (in_grp && jl < rows) {
+                bb0 = a.row_ptr[r0 + jl] - b0;
+                bb1 = a.row_ptr[r0 + jl + 1] - b0;
             }
             if (in_grp && jl >= 0 && jl < rows) {
-                const int j = r0 + jl;
-                const int bb0 = a.row_ptr[j] - b0, bb1 = a.row_ptr[j + 1] - b0;
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-                auto hrow_of = [&](int lb) {
-                    return lb < ncache ? reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12)
-                                       : reinterpret_cast<const float4 *>(a.bsr + (size_t)(b0 + lb) * 144 + rr * 12);
-                };
                 auto madd4 = [](float acc, float4 h, float4 p) {
                     return fmaf(h.w, p.w, fmaf(h.z, p.z, fmaf(h.y, p.y, fmaf(h.x, p.x, acc))));
                 };
                 int lb = bb0 + sp;
+                if (all_cached) {   // every block in shared memory: shared-memory loads only
+                    for (; lb + S < bb1; lb += 2 * S) {
+                        const float4 *ha = reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12);
+                        const float4 *hb = reinterpret_cast<const float4 *>(Hs + (size_t)(lb + S) * 144 + rr * 12);
+                        const float4 *pa = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
+                        const float4 *pbb = reinterpret_cast<const float4 *>(pb + (size_t)(lb + S) * 12);
+                        const float4 ha0 = ha[0], ha1 = ha[1], ha2 = ha[2], hb0 = hb[0], hb1 = hb[1], hb2 = hb[2];
+                        const float4 pa0 = pa[0], pa1 = pa[1], pa2 = pa[2], pb0 = pbb[0], pb1 = pbb[1], pb2 = pbb[2];
+                        acc0 = madd4(madd4(acc0, ha0, pa0), hb0, pb0);
+                        acc1 = madd4(madd4(acc1, ha1, pa1), hb1, pb1);
+                        acc2 = madd4(madd4(acc2, ha2, pa2), hb2, pb2);
+                    }
+                    if (lb < bb1) {
+                        const float4 *ha = reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12);
+                        const float4 *pa = reinterpret_cast<const float4 *>(pb + (size_t)lb * 12);
+                        acc0 = madd4(acc0, ha[0], pa[0]);
+                        acc1 = madd4(acc1, ha[1], pa[1]);
+                        acc2 = madd4(acc2, ha[2], pa[2]);
+                    }
+                    lb = bb1;
+                }
+                auto hrow_of = [&](int lb) {
+                    return lb < ncache ? reinterpret_cast<const float4 *>(Hs + (size_t)lb * 144 + rr * 12)
+                                       : reinterpret_cast<const float4 *>(a.bsr + (size_t)(b0 + lb) * 144 + rr * 12);
+                };
                 // two blocks per step, every load of both before the first product
                 for (; lb + S < bb1; lb += 2 * S) {
                     const float4 *ha = hrow_of(lb), *hb = hrow_of(lb + S);
