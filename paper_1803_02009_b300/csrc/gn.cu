@@ -42,6 +42,7 @@ struct PointArgs {
 // r1 = [d r / d angles; 1] (zero on invalid rows); E_data, the count, the 6x6
 // pose block, the pose gradient, the non-finite count, E_corr and the valid
 // rows are added to acc.  Returns whether the row is valid.
+template <bool ACC>
 __device__ __forceinline__ bool point_eval(const PointArgs &a, const ed_pose_f &P, int k, float (&acc)[32],
                                            float4 &r0, float4 &r1)
 {
@@ -111,7 +112,8 @@ __device__ __forceinline__ bool point_eval(const PointArgs &a, const ed_pose_f &
         jp[4] = sw * tn.y;
         jp[5] = sw * tn.z;
         r0 = make_float4(b0, b1, b2, r);
-        r1 = make_float4(jp[0], jp[1], jp[2], 1.0f);
+        r1 = make_float4(jp[0], jp[1], jp[2], kp ? 2.0f : 1.0f);   // (w: 1 a data row, 2 a key-point row)
+        if (!ACC) return valid;
         if (kp) {
             acc[30] += r * r;
         } else {
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
     for (int k = 0; k < 32; ++k) acc[k] = 0.f;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
         float4 r0, r1;
-        point_eval(a, P, k, acc, r0, r1);
+        point_eval<true>(a, P, k, acc, r0, r1);
         if (a.mode != PASS_ENERGY) {
             a.rec0[k] = r0;
             a.rec1[k] = r1;
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, C
         const int k = chunk * CHUNK + e * ED_K1_THREADS + threadIdx.x;
         const bool in = k < a.n;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        const bool valid = in && point_eval(a, P, k, acc, r0, r1);
+        const bool valid = in && point_eval<false>(a, P, k, acc, r0, r1);
         const unsigned bal = __ballot_sync(full, valid);
         if (lane == 0) s_warp[wid] = __popc(bal);
         __syncthreads();
@@ -320,6 +322,31 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, C
     }
     if (threadIdx.x == 0)   // the chunk's count, for the chunks after it
         ed_st_release64(c.state + chunk, E | (1ull << 32) | (unsigned long long)(unsigned)nvalid);
+    // the chunk's sums from its staged rows (every row once, in position
+    // order per thread): the angle derivatives are r1.xyz, the translation
+    // derivatives sqrt(w) n(u) = R b with b = r0.xyz
+    for (int q = threadIdx.x; q < nvalid; q += ED_K1_THREADS) {
+        const float4 r0 = stage[0][q], r1 = stage[1][q];
+        const float r = r0.w;
+        const float *R = P.R;
+        const float jp[6] = {r1.x, r1.y, r1.z, R[0] * r0.x + R[1] * r0.y + R[2] * r0.z,
+                             R[3] * r0.x + R[4] * r0.y + R[5] * r0.z, R[6] * r0.x + R[7] * r0.y + R[8] * r0.z};
+        if (r1.w > 1.5f) {
+            acc[30] += r * r;
+        } else {
+            acc[0] += r * r;
+            acc[1] += 1.0f;
+        }
+        acc[31] += 1.0f;
+        int ka = 2;
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+#pragma unroll
+            for (int u = t; u < 6; ++u) acc[ka++] += jp[t] * jp[u];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) acc[23 + t] += r * jp[t];
+        if (!isfinite(r)) acc[29] += 1.0f;
+    }
     point_partials(acc, red, a.part, a.pstride, chunk);
     const int base = chunk_prefix(c, chunk, E, s_warp);
     for (int i = threadIdx.x; i < nvalid; i += ED_K1_THREADS) {
