@@ -352,6 +352,8 @@ __global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int 
                                                    unsigned long long *state, unsigned *ticket, unsigned ticket_base,
                                                    unsigned epoch, int *status, unsigned long long wait_ns)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ int s_tile, s_excl, s_warp[DS_T / 32];
     if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ticket, 1u) - ticket_base);
     __syncthreads();
@@ -450,6 +452,8 @@ __global__ void __launch_bounds__(DS_T) k_scan_dlb(const int *in, int *out, int 
 
 __global__ void k_set_zero_at(int *p, int *p2)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     *p = 0;
     if (p2) *p2 = 0;
 }
@@ -458,7 +462,7 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
                             const int *n_dev)
 {
     if (n <= 0) {
-        k_set_zero_at<<<1, 1, 0, st>>>(out, total2); ed_note_launch();
+        ED_LAUNCH(k_set_zero_at, 1, 1, st, out, total2); ed_note_launch();
         ED_LAUNCH_CHECK();
         return ED_OK;
     }
@@ -469,7 +473,7 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
         ED_CUDA_TRY(cudaMemsetAsync(ctx->scan_state, 0, sizeof(unsigned long long) * ctx->scan_state_len, st));
         ctx->scan_epoch = epoch = 1;
     }
-    k_scan_dlb<<<tiles, DS_T, 0, st>>>(in, out, n, n_dev, total2, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
+    ED_LAUNCH(k_scan_dlb, tiles, DS_T, st, in, out, n, n_dev, total2, ctx->scan_state, ctx->scan_ticket, ctx->scan_ticket_base, epoch,
                                        ctx->misc + MI_STATUS, ctx->wait_ns); ed_note_launch();
     ctx->scan_ticket_base += (unsigned)tiles;
     ED_LAUNCH_CHECK();
@@ -484,6 +488,8 @@ ed_status ed_scan_exclusive(ed_context *ctx, const int *in, int *out, int n, cud
 
 __global__ void k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift, int ntiles, int *__restrict__ cnt)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -502,6 +508,8 @@ __global__ void __launch_bounds__(32) k_radix_scatter(const uint32_t *__restrict
                                                       const int *__restrict__ offs, uint32_t *__restrict__ ko,
                                                       uint32_t *__restrict__ vo)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ int c[256];
     const int tile = blockIdx.x;
     const int lane = threadIdx.x;
@@ -542,11 +550,11 @@ ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, i
     uint32_t *ka = keys, *va = vals, *kb = ctx->ent_key2, *vb = ctx->ent_val2;
     int passes = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
-        k_radix_hist<<<ntiles, 256, 0, st>>>(ka, n, shift, ntiles, ctx->radix_cnt); ed_note_launch();
+        ED_LAUNCH(k_radix_hist, ntiles, 256, st, ka, n, shift, ntiles, ctx->radix_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
         ed_status s = ed_scan_exclusive(ctx, ctx->radix_cnt, ctx->radix_cnt, 256 * ntiles, st);
         if (s != ED_OK) return s;
-        k_radix_scatter<<<ntiles, 32, 0, st>>>(ka, va, n, shift, ntiles, ctx->radix_cnt, kb, vb); ed_note_launch();
+        ED_LAUNCH(k_radix_scatter, ntiles, 32, st, ka, va, n, shift, ntiles, ctx->radix_cnt, kb, vb); ed_note_launch();
         ED_LAUNCH_CHECK();
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
@@ -565,6 +573,8 @@ ed_status ed_radix_sort_pairs(ed_context *ctx, uint32_t *keys, uint32_t *vals, i
 
 __global__ void k_normals(const float *__restrict__ depth, ed_intrinsics K, int h, float4 *__restrict__ nmap)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= K.width || v >= K.height) return;
@@ -601,7 +611,7 @@ extern "C" ed_status ed_compute_normals(ed_context *ctx, const float *depth, ed_
         !(intr.fx > 0.f) || !(intr.fy > 0.f) || ((uintptr_t)nmap & 15))
         return ED_ERR_ARG;
     dim3 b(32, 8), g(ed_div_up(intr.width, 32), ed_div_up(intr.height, 8));
-    k_normals<<<g, b, 0, stream>>>(depth, intr, half_width, (float4 *)nmap); ed_note_launch();
+    ED_LAUNCH(k_normals, g, b, stream, depth, intr, half_width, (float4 *)nmap); ed_note_launch();
     ED_LAUNCH_CHECK();
     return ED_OK;
 }
@@ -614,6 +624,8 @@ __global__ void k_warp(const float4 *__restrict__ pos, const float4 *__restrict_
                        const float4 *__restrict__ w, const float4 *__restrict__ g, const float4 *__restrict__ x4,
                        const double *__restrict__ pose, int n, float4 *__restrict__ pos_out, float4 *__restrict__ nrm_out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ ed_pose_f P;
     if (threadIdx.x == 0) ed_pose_eval(pose, P);
     __syncthreads();
@@ -634,6 +646,8 @@ struct ResetPose {
 __global__ void k_reset_params(int m, float *__restrict__ x, double *__restrict__ xm, double *__restrict__ pose,
                                ResetPose prior)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 12 * m) {
         const int e = i % 12;
@@ -653,7 +667,7 @@ extern "C" ed_status ed_reset_params(ed_context *ctx, float *x, double *x_master
     ResetPose pr;
     for (int k = 0; k < 6; ++k) pr.v[k] = prior_host ? prior_host[k] : 0.0;
     const int m = ctx->m;
-    k_reset_params<<<ed_div_up(12 * m + 6, 256), 256, 0, st>>>(m, x, x_master, pose, pr); ed_note_launch();
+    ED_LAUNCH(k_reset_params, ed_div_up(12 * m + 6, 256), 256, st, m, x, x_master, pose, pr); ed_note_launch();
     ED_LAUNCH_CHECK();
     return ED_OK;
 }
@@ -665,7 +679,7 @@ extern "C" ed_status ed_warp(ed_context *ctx, const float *x, const double *pose
     if (!ctx->have_graph) return ED_ERR_STATE;
     if (n_points > ctx->N) return ED_ERR_ARG;   // the skinning of the graph covers the model points
     if (n_points == 0) return ED_OK;
-    k_warp<<<ed_div_up(n_points, 256), 256, 0, stream>>>(
+    ED_LAUNCH(k_warp, ed_div_up(n_points, 256), 256, stream, 
         (const float4 *)pos_in, (const float4 *)nrm_in, (const ushort4 *)ctx->graph.idx,
         (const float4 *)ctx->graph.weights, (const float4 *)ctx->graph.nodes, (const float4 *)x, pose, n_points,
         (float4 *)pos_out, (float4 *)nrm_out); ed_note_launch();

@@ -422,6 +422,31 @@ static inline cudaError_t ed_launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// ed_launch_pdl with no dynamic shared memory, returning from the enclosing
+// ed_status function on a launch error (the kernel starts with ed_pdl_wait)
+#define ED_LAUNCH(kern, grid, block, st, ...) \
+    ED_CUDA_TRY(ed_launch_pdl(kern, dim3(grid), dim3(block), 0, st, __VA_ARGS__))
+
+// a cooperative launch (co-resident CTAs), as a programmatic dependent launch
+// when pdl is set (the kernel then starts with ed_pdl_wait)
+static inline cudaError_t ed_launch_coop(const void *fn, int grid, int nt, void **args, size_t smem, cudaStream_t st,
+                                         bool pdl)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // ---------------------------------------------------------------------------
 // grid barrier of a cooperative (co-resident) launch, with a bounded wait
 // ---------------------------------------------------------------------------

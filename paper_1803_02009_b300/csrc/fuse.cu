@@ -3,8 +3,21 @@
 #include "ed_internal.cuh"
 
 // Reg, step 1: z-buffer of the warped points, key = (z bits, point index)
+// the z-buffer and the fused-pixel marks of the old points cleared to all
+// ones (empty pixel, no pixel)
+__global__ void k_fuse_init(unsigned long long *__restrict__ zb, int npx, int *__restrict__ fused_pix, int n)
+{
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npx) zb[i] = ~0ull;
+    if (i < n) fused_pix[i] = -1;
+}
+
 __global__ void k_fuse_zbuf(const float4 *__restrict__ wpos, int n, ed_intrinsics K, unsigned long long *__restrict__ zb)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 p = wpos[i];
@@ -20,6 +33,8 @@ __global__ void k_fuse_reg(const unsigned long long *__restrict__ zb, const floa
                            const float4 *__restrict__ nmap, int npx, float tau_d, float cos_delta,
                            int *__restrict__ reg, int *__restrict__ fused_pix, int *__restrict__ lift)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= npx) return;
     const unsigned long long key = zb[q];
@@ -43,6 +58,8 @@ __global__ void k_fuse_keep(const float4 *__restrict__ pos, const int *__restric
                             const int *__restrict__ fused_pix, int n, int frame, int tau_time, float tau_weight,
                             int *__restrict__ keep)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool del = fused_pix[i] < 0 && (frame - tstamp[i]) > tau_time && pos[i].w < tau_weight;
@@ -57,6 +74,8 @@ __global__ void k_fuse_write_old(const float4 *__restrict__ pos, const float4 *_
                                  int capacity, float4 *__restrict__ pos_out, float4 *__restrict__ nrm_out,
                                  float4 *__restrict__ col_out, int *__restrict__ t_out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = keep_scan[i];
@@ -98,6 +117,8 @@ __global__ void k_fuse_write_new(const int *__restrict__ lift_scan, int npx, con
                                  float4 *__restrict__ pos_out, float4 *__restrict__ nrm_out, float4 *__restrict__ col_out,
                                  int *__restrict__ t_out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= npx) return;
     if (lift_scan[q + 1] == lift_scan[q]) return;
@@ -115,6 +136,8 @@ __global__ void k_fuse_write_new(const int *__restrict__ lift_scan, int npx, con
 __global__ void k_fuse_count(const int *__restrict__ kept_total, const int *__restrict__ lift_total, int capacity,
                              int *__restrict__ out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const long tot = (long)*kept_total + *lift_total;
     out[0] = (int)(tot < capacity ? tot : capacity);
     out[1] = tot > capacity ? ED_ERR_CAPACITY : ED_OK;
@@ -136,35 +159,35 @@ extern "C" ed_status ed_fuse(ed_context *ctx, const float *pos, const float *nrm
     const int npx = fr->intr.width * fr->intr.height;
     int *reg = reg_out ? reg_out : ctx->regpix;
     int *keep = ctx->flag_a, *lift = ctx->flag_b;
-    ED_CUDA_TRY(cudaMemsetAsync(ctx->zbuf, 0xff, sizeof(unsigned long long) * npx, st));
-    if (n_in > 0) ED_CUDA_TRY(cudaMemsetAsync(ctx->fused_pix, 0xff, sizeof(int) * n_in, st));
+    ED_LAUNCH(k_fuse_init, ed_div_up(npx > n_in ? npx : n_in, 256), 256, st, ctx->zbuf, npx, ctx->fused_pix, n_in);
+    ed_note_launch();
     if (n_in > 0) {
-        k_fuse_zbuf<<<ed_div_up(n_in, 256), 256, 0, st>>>((const float4 *)wpos, n_in, fr->intr, ctx->zbuf); ed_note_launch();
+        ED_LAUNCH(k_fuse_zbuf, ed_div_up(n_in, 256), 256, st, (const float4 *)wpos, n_in, fr->intr, ctx->zbuf); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
-    k_fuse_reg<<<ed_div_up(npx, 256), 256, 0, st>>>(ctx->zbuf, (const float4 *)wpos, (const float4 *)wnrm, fr->depth,
+    ED_LAUNCH(k_fuse_reg, ed_div_up(npx, 256), 256, st, ctx->zbuf, (const float4 *)wpos, (const float4 *)wnrm, fr->depth,
                                                     (const float4 *)fr->nmap, npx, F->tau_d, F->cos_delta, reg,
                                                     ctx->fused_pix, lift); ed_note_launch();
     ED_LAUNCH_CHECK();
     ed_status s;
     if (n_in > 0) {
-        k_fuse_keep<<<ed_div_up(n_in, 256), 256, 0, st>>>((const float4 *)pos, tstamp, ctx->fused_pix, n_in, F->frame,
+        ED_LAUNCH(k_fuse_keep, ed_div_up(n_in, 256), 256, st, (const float4 *)pos, tstamp, ctx->fused_pix, n_in, F->frame,
                                                           F->tau_time, F->tau_weight, keep); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
     if ((s = ed_scan_exclusive(ctx, keep, keep, n_in, st)) != ED_OK) return s;
     if ((s = ed_scan_exclusive(ctx, lift, lift, npx, st)) != ED_OK) return s;
     if (n_in > 0) {
-        k_fuse_write_old<<<ed_div_up(n_in, 256), 256, 0, st>>>(
+        ED_LAUNCH(k_fuse_write_old, ed_div_up(n_in, 256), 256, st, 
             (const float4 *)pos, (const float4 *)col, tstamp, (const float4 *)wpos, (const float4 *)wnrm, ctx->fused_pix,
             keep, n_in, fr->depth, (const float4 *)fr->nmap, (const float4 *)fr->color, *F, capacity, (float4 *)pos_out,
             (float4 *)nrm_out, (float4 *)col_out, t_out); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
-    k_fuse_write_new<<<ed_div_up(npx, 256), 256, 0, st>>>(lift, npx, keep + n_in, fr->depth, (const float4 *)fr->nmap,
+    ED_LAUNCH(k_fuse_write_new, ed_div_up(npx, 256), 256, st, lift, npx, keep + n_in, fr->depth, (const float4 *)fr->nmap,
                                                           (const float4 *)fr->color, fr->intr, *F, capacity,
                                                           (float4 *)pos_out, (float4 *)nrm_out, (float4 *)col_out, t_out); ed_note_launch();
-    k_fuse_count<<<1, 1, 0, st>>>(keep + n_in, lift + npx, capacity, counts_out); ed_note_launch();
+    ED_LAUNCH(k_fuse_count, 1, 1, st, keep + n_in, lift + npx, capacity, counts_out); ed_note_launch();
     ED_LAUNCH_CHECK();
     return ED_OK;
 }

@@ -16,8 +16,24 @@ __global__ void k_bbox_init(int *misc)
     }
 }
 
+// the first kernel of a build: the misc words cleared (the bounding box at
+// its empty extremes) and the count arrays of the tuple buckets and the
+// incidences zeroed (grid-stride)
+__global__ void k_build_init(int *__restrict__ misc, int *__restrict__ z0, int n0, int *__restrict__ z1, int n1)
+{
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int i = t; i < MI_COUNT; i += stride)
+        misc[i] = i >= MI_BBOX && i < MI_BBOX + 3 ? 0x7fffffff : (i >= MI_BBOX + 3 && i < MI_BBOX + 6 ? (int)0x80000000 : 0);
+    for (int i = t; i < n0; i += stride) z0[i] = 0;
+    for (int i = t; i < n1; i += stride) z1[i] = 0;
+}
+
 __global__ void __launch_bounds__(256) k_bbox(const float4 *__restrict__ pos, int n, int *misc)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ float smn[3][8], smx[3][8];
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -55,6 +71,8 @@ __global__ void __launch_bounds__(256) k_bbox(const float4 *__restrict__ pos, in
 // search grid (edge kc), by the same FP32 operations as the oracle
 __global__ void k_grid_setup(int *misc, float *fmisc, float r, float kc, long max_cells, int sampling)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     float mn[3], mx[3];
     for (int d = 0; d < 3; ++d) {
         mn[d] = o2f(misc[MI_BBOX + d]);
@@ -108,6 +126,8 @@ __device__ __forceinline__ int3 cell3(float x, float y, float z, const float *fm
 // every cell of the sampling grid without a bid (the cell count from the set-up)
 __global__ void k_fill_cells(int *__restrict__ cell_pick, const int *__restrict__ misc)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (misc[MI_STATUS] != ED_OK) return;
     const int cells = misc[MI_DIMS + 3];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += gridDim.x * blockDim.x) cell_pick[c] = NO_BID;
@@ -116,6 +136,8 @@ __global__ void k_fill_cells(int *__restrict__ cell_pick, const int *__restrict_
 __global__ void k_cell_of(const float4 *__restrict__ pos, int n, const int *__restrict__ misc,
                           const float *__restrict__ fmisc, int *__restrict__ cell_of)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || misc[MI_STATUS] != ED_OK) return;   // no grid when the set-up failed
     const int dims[3] = {misc[MI_DIMS], misc[MI_DIMS + 1], misc[MI_DIMS + 2]};
@@ -142,6 +164,8 @@ __device__ __forceinline__ int cell_phase(int c, int nx, int ny)
 __global__ void k_phase_count(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
                               int *__restrict__ cnt)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (misc[MI_STATUS] != ED_OK) return;
     __shared__ int h[27];
     if (threadIdx.x < 27) h[threadIdx.x] = 0;
@@ -156,6 +180,8 @@ __global__ void k_phase_count(const int *__restrict__ cell_of, int n, const int 
 // exclusive scan of the 27 phase counts (start[27] = n); fill counters cleared
 __global__ void k_phase_scan(const int *__restrict__ cnt, int *__restrict__ start, int *__restrict__ fill)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (threadIdx.x != 0) return;
     int s = 0;
     for (int p = 0; p < 27; ++p) {
@@ -169,6 +195,8 @@ __global__ void k_phase_scan(const int *__restrict__ cnt, int *__restrict__ star
 __global__ void k_phase_scatter(const int *__restrict__ cell_of, int n, const int *__restrict__ misc,
                                 const int *__restrict__ start, int *__restrict__ fill, int2 *__restrict__ bucket)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (misc[MI_STATUS] != ED_OK) return;
     __shared__ int h[27], base[27];
     const int nx = misc[MI_DIMS], ny = misc[MI_DIMS + 1];
@@ -274,6 +302,8 @@ __global__ void __launch_bounds__(POISSON_T) k_poisson_all(const float4 *__restr
                                                            const float *__restrict__ fmisc, int *cell_pick, unsigned *bar,
                                                            int *status, unsigned long long wait_ns)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ int s_flag;
     if (*(volatile int *)status != ED_OK) return;   // every CTA: no grid when the set-up failed
     const int nx = misc_in[MI_DIMS], ny = misc_in[MI_DIMS + 1], nz = misc_in[MI_DIMS + 2];
@@ -309,6 +339,8 @@ __device__ __forceinline__ int phase_cell(const PhaseTable &T, int t, int nx, in
 __global__ void k_node_flags(PhaseTable T, int total, const int *__restrict__ misc, const int *__restrict__ cell_pick,
                              int *__restrict__ flag)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     int ph;
@@ -320,6 +352,8 @@ __global__ void k_node_write(PhaseTable T, int total, const int *__restrict__ mi
                              const int *__restrict__ pre, const float4 *__restrict__ pos, float4 *__restrict__ nodes,
                              int max_nodes)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total || pre[t + 1] == pre[t]) return;
     const int id = pre[t];
@@ -340,6 +374,8 @@ __global__ void k_kcell_count(const float4 *__restrict__ nodes, const int *__res
                               const int *__restrict__ misc, const float *__restrict__ fmisc, int *__restrict__ cnt,
                               int *__restrict__ cell_of_node)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= *m_dev) return;
     const int dims[3] = {misc[MI_KDIMS], misc[MI_KDIMS + 1], misc[MI_KDIMS + 2]};
@@ -351,17 +387,19 @@ __global__ void k_kcell_count(const float4 *__restrict__ nodes, const int *__res
 }
 
 // every node's position, its index in w (as int bits), in its search cell's
-// range (the order inside a cell is immaterial: the search orders by key and
-// index)
+// range, the slots taken by counting the cell's count down to 0 (the order
+// inside a cell is immaterial: the search orders by key and index)
 __global__ void k_kcell_fill(const int *__restrict__ m_dev, const float4 *__restrict__ nodes,
                              const int *__restrict__ start, int *__restrict__ fill, const int *__restrict__ cell_of_node,
                              float4 *__restrict__ kpos)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= *m_dev) return;
     const int L = cell_of_node[j];
     const float4 g = nodes[j];
-    kpos[start[L] + atomicAdd(&fill[L], 1)] = make_float4(g.x, g.y, g.z, __int_as_float(j));
+    kpos[start[L] + atomicSub(&fill[L], 1) - 1] = make_float4(g.x, g.y, g.z, __int_as_float(j));
 }
 
 #define KNN_S 5   // K + 1 nearest (Eq. 2 needs the (K+1)-th distance)
@@ -387,6 +425,8 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
                       const int *__restrict__ start, const float4 *__restrict__ kpos, int mode, float sigma,
                       ushort4 *__restrict__ idx_out, float4 *__restrict__ w_out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int m = *m_dev;
@@ -470,9 +510,13 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
 #define NG_TILE 2048
 __global__ void __launch_bounds__(32 * NG_WARPS) k_node_graph(const float4 *__restrict__ nodes,
                                                               const int *__restrict__ m_dev, int kg,
-                                                              int *__restrict__ nbr)
+                                                              int *__restrict__ nbr, uint32_t *__restrict__ bm,
+                                                              int bm_n)
 {
     __shared__ float4 s_nodes[NG_TILE];
+    // the pair bitmap of the block pattern zeroed for this build (its first
+    // bm_n words: every row of the node count's stride)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bm_n; i += gridDim.x * blockDim.x) bm[i] = 0u;
     const int m = *m_dev;
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * NG_WARPS + (threadIdx.x >> 5);
@@ -531,6 +575,8 @@ __device__ __forceinline__ void set_bit(uint32_t *bm, int words, int a, int b)
 __global__ void k_pairs_runs_dev(const int *__restrict__ n_runs_dev, const int *__restrict__ run_start,
                                  const ushort4 *__restrict__ sidx, uint32_t *bm, int words)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= *n_runs_dev) return;
     const ushort4 q = sidx[run_start[r]];
@@ -544,6 +590,8 @@ __global__ void k_pairs_runs_dev(const int *__restrict__ n_runs_dev, const int *
 
 __global__ void k_pairs_graph(const int *__restrict__ nbr, int m, int kg, uint32_t *bm, int words)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     set_bit(bm, words, j, j);
@@ -558,6 +606,8 @@ __global__ void k_pairs_graph(const int *__restrict__ nbr, int m, int kg, uint32
 // one warp per node row: the set bits of its bitmap words
 __global__ void k_row_count(const uint32_t *__restrict__ bm, int m, int words, int *__restrict__ cnt)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= m) return;
@@ -574,6 +624,8 @@ __global__ void k_row_fill(const uint32_t *__restrict__ bm, int m, int words, co
                            int *__restrict__ col, int *__restrict__ brow, int *__restrict__ diag_pos, int max_nnzb,
                            int *__restrict__ status)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     // one warp per node row: the words in rounds of 32, a lane's bits placed
     // after the bits of the lanes (and rounds) before it: ascending columns
     const int lane = threadIdx.x & 31;
@@ -627,6 +679,8 @@ __global__ void k_tpos(const int *__restrict__ nnzb_dev, int cap, const int *__r
                        const int *__restrict__ col, const int *__restrict__ brow, int *__restrict__ tpos,
                        int *__restrict__ upper_flag)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int nnzb = *nnzb_dev;
     if (nnzb > cap) return;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nnzb; b += gridDim.x * blockDim.x) {
@@ -642,6 +696,8 @@ __global__ void k_compact_upper(const int *__restrict__ nnzb_dev, int cap, int m
                                 const int *__restrict__ pre, const int *__restrict__ diag_pos,
                                 int *__restrict__ up_list)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int nnzb = *nnzb_dev;
     if (nnzb > cap) return;
     const int n = nnzb > m ? nnzb : m;
@@ -704,6 +760,8 @@ __device__ __forceinline__ int warp_bucket_add(int *ctr, int bucket, bool active
 
 __global__ void k_tb_count(const ushort4 *__restrict__ idx, int n, int *__restrict__ cnt)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int t[4] = {0, 0, 0, 0}, sl[4];
     if (i < n) tuple_of(idx[i], t, sl);
@@ -713,6 +771,8 @@ __global__ void k_tb_count(const ushort4 *__restrict__ idx, int n, int *__restri
 __global__ void k_tb_place(const ushort4 *__restrict__ idx, int n, const int *__restrict__ start,
                            int *__restrict__ fill, uint32_t *__restrict__ order)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int t[4] = {0, 0, 0, 0}, sl[4];
     if (i < n) tuple_of(idx[i], t, sl);
@@ -738,6 +798,8 @@ __global__ void __launch_bounds__(TB64_T) k_tb_sort64(const ushort4 *__restrict_
                                                       int nb, int fb, int pb, const uint32_t *__restrict__ order,
                                                       uint32_t *__restrict__ out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ unsigned long long s_k[TB_MAX];
     const int b = blockIdx.x;
     if (b >= nb) return;
@@ -797,6 +859,8 @@ __global__ void __launch_bounds__(TB_T) k_tb_sort(const ushort4 *__restrict__ id
                                                   int nb, int fb, const uint32_t *__restrict__ order,
                                                   uint32_t *__restrict__ out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     __shared__ unsigned long long s_key[TB_MAX];
     __shared__ uint32_t s_pt[TB_MAX];
     const int b = blockIdx.x;
@@ -885,6 +949,8 @@ __global__ void __launch_bounds__(TB_T) k_tb_sort(const ushort4 *__restrict__ id
 __global__ void k_ic_count(const int *__restrict__ nruns_dev, const int *__restrict__ nnzb_dev, int cap,
                            const uint32_t *__restrict__ key, int *__restrict__ cnt)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (*nnzb_dev > cap) return;
     const int ne = 10 * *nruns_dev;
     for (int e0 = blockIdx.x * blockDim.x; e0 < ne; e0 += gridDim.x * blockDim.x) {
@@ -897,6 +963,8 @@ __global__ void k_ic_place(const int *__restrict__ nruns_dev, const int *__restr
                            const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                            const int *__restrict__ start, int *__restrict__ fill, uint32_t *__restrict__ out)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (*nnzb_dev > cap) return;
     const int ne = 10 * *nruns_dev;
     for (int e0 = blockIdx.x * blockDim.x; e0 < ne; e0 += gridDim.x * blockDim.x) {
@@ -957,6 +1025,8 @@ __device__ __forceinline__ void ic_sort_block(const int *__restrict__ start, uin
 __global__ void __launch_bounds__(128) k_ic_sort(const int *__restrict__ nnzb_dev, int cap,
                                                  const int *__restrict__ start, uint32_t *__restrict__ list)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int nnzb = *nnzb_dev;
     if (nnzb > cap) return;
     const int lane = threadIdx.x & 31;
@@ -969,6 +1039,8 @@ __global__ void __launch_bounds__(128) k_ic_sort(const int *__restrict__ nnzb_de
 __global__ void k_tuple_lo(const ushort4 *__restrict__ idx, int n, int fb, uint32_t *__restrict__ key,
                            uint32_t *__restrict__ val)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int t[4], sl[4];
@@ -981,6 +1053,8 @@ __global__ void k_tuple_lo(const ushort4 *__restrict__ idx, int n, int fb, uint3
 __global__ void k_tuple_hi(const ushort4 *__restrict__ idx, int n, int fb, const uint32_t *__restrict__ val,
                            uint32_t *__restrict__ key)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     int t[4], sl[4];
@@ -997,6 +1071,8 @@ __global__ void k_tuple_gather(const uint32_t *__restrict__ val, int n, const us
                                float4 *__restrict__ snrm, ushort4 *__restrict__ sidx, float4 *__restrict__ sw,
                                ushort4 *__restrict__ sidx_d, float4 *__restrict__ sw_d, int *__restrict__ flag)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int i = (int)val[k];
@@ -1026,6 +1102,8 @@ __global__ void k_tuple_gather(const uint32_t *__restrict__ val, int n, const us
 __global__ void k_run_starts(const int *__restrict__ flag, const int *__restrict__ pre, int n,
                              int *__restrict__ run_start, int *__restrict__ run_of_start)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     run_of_start[k] = flag[k] ? pre[k] : -1;
@@ -1061,6 +1139,8 @@ __global__ void k_inc_gen(const int *__restrict__ nruns_dev, const int *__restri
                           const int *__restrict__ row_ptr, const int *__restrict__ col, uint32_t *__restrict__ key,
                           uint32_t *__restrict__ val, int *__restrict__ status)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     if (*nnzb_dev > cap) return;
     const int n_runs = *nruns_dev;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_runs; r += gridDim.x * blockDim.x)
@@ -1103,6 +1183,8 @@ __global__ void k_fin_pack(const int *__restrict__ nnzb_dev, int cap, int m, int
                            const int *__restrict__ tpos, const int *__restrict__ row_ptr,
                            const int *__restrict__ inc_start, const int *__restrict__ nbr, int4 *__restrict__ info)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int nnzb = *nnzb_dev;
     if (nnzb > cap) return;
     const int nu = m + flag_b[nnzb];   // the upper-block count
@@ -1117,6 +1199,8 @@ __global__ void k_fin_pack(const int *__restrict__ nnzb_dev, int cap, int m, int
 __global__ void k_kp_expand(const float4 *__restrict__ kp, int nk, int n_model, float4 *__restrict__ pos,
                             float4 *__restrict__ nrm)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nk) return;
     const float4 p = kp[t / 3];
@@ -1128,6 +1212,8 @@ __global__ void k_kp_expand(const float4 *__restrict__ kp, int nk, int n_model, 
 // (and the count in use to misc[MI_M], which goes to the host with the other misc words)
 __global__ void k_set_counts(int *__restrict__ misc, int max_nodes, int *__restrict__ counts)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     const int mt = misc[MI_PHASE_BASE];
     const int mu = mt < max_nodes ? mt : max_nodes;
     counts[0] = mu;
@@ -1138,6 +1224,8 @@ __global__ void k_set_counts(int *__restrict__ misc, int max_nodes, int *__restr
 // the block count into the graph's counts[2] (counts[3] = 0)
 __global__ void k_counts_pattern(const int *__restrict__ misc, int *__restrict__ counts)
 {
+    ed_pdl_wait();
+    ed_pdl_trigger();
     counts[2] = misc[MI_READ];
     counts[3] = 0;
 }
@@ -1147,7 +1235,7 @@ ed_status ed_bbox_enqueue(ed_context *ctx, const float4 *pos, int n, cudaStream_
 {
     k_bbox_init<<<1, 32, 0, st>>>(ctx->misc); ed_note_launch();
     if (n > 0) {
-        k_bbox<<<min(ed_div_up(n, 256), 4 * ctx->num_sms), 256, 0, st>>>(pos, n, ctx->misc); ed_note_launch();
+        ED_LAUNCH(k_bbox, min(ed_div_up(n, 256), 4 * ctx->num_sms), 256, st, pos, n, ctx->misc); ed_note_launch();
     }
     ED_LAUNCH_CHECK();
     return ED_OK;
@@ -1180,21 +1268,20 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     if (ctx->n_kp > 0) {
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->comb_pos, pos, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
         ED_CUDA_TRY(cudaMemcpyAsync(ctx->comb_nrm, nrm, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
-        k_kp_expand<<<ed_div_up(3 * ctx->n_kp, 256), 256, 0, st>>>(ctx->kp_pos, ctx->n_kp, N, ctx->comb_pos,
+        ED_LAUNCH(k_kp_expand, ed_div_up(3 * ctx->n_kp, 256), 256, st, ctx->kp_pos, ctx->n_kp, N, ctx->comb_pos,
                                                                    ctx->comb_nrm); ed_note_launch();
         PT = ctx->comb_pos;
     }
     float4 *G4 = (float4 *)graph->nodes;
     int hm[MI_COUNT];
     ed_status s;
-    ED_CUDA_TRY(cudaMemsetAsync(ctx->misc, 0, sizeof(int) * MI_COUNT, st));
-
     // ---- bounding box and grids ----
-    k_bbox_init<<<1, 32, 0, st>>>(ctx->misc); ed_note_launch();
-    k_bbox<<<min(ed_div_up(N, 256), 4 * ctx->num_sms), 256, 0, st>>>(P4, N, ctx->misc); ed_note_launch();
+    ED_LAUNCH(k_build_init, 2 * ctx->num_sms, 256, st, ctx->misc, ctx->bcnt, 2 * (max_nodes + 1), ctx->icnt,
+              2 * (ctx->max_nnzb + 1)); ed_note_launch();
+    ED_LAUNCH(k_bbox, min(ed_div_up(N, 256), 4 * ctx->num_sms), 256, st, P4, N, ctx->misc); ed_note_launch();
     float kc = prm->search_cell;
     if (!(kc > 0.f)) kc = m_in > 0 ? (prm->sigma > 0.f ? prm->sigma : 1.0f) : 2.0f * prm->node_radius;
-    k_grid_setup<<<1, 1, 0, st>>>(ctx->misc, ctx->fmisc, m_in > 0 ? 1.0f : prm->node_radius, kc, ctx->lim.max_cells,
+    ED_LAUNCH(k_grid_setup, 1, 1, st, ctx->misc, ctx->fmisc, m_in > 0 ? 1.0f : prm->node_radius, kc, ctx->lim.max_cells,
                                   m_in == 0); ed_note_launch();
     ED_LAUNCH_CHECK();
     // the grid dims go to the host without draining the stream
@@ -1208,12 +1295,12 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     int *pcnt = ctx->misc + MI_PHASES, *pstart = ctx->misc + MI_PHASES + 32, *pfill = ctx->misc + MI_PHASES + 64;
     if (m_in == 0) {
         int2 *bucket = reinterpret_cast<int2 *>(ctx->ent_key);  // N (point, cell) pairs; the entry keys come later
-        k_fill_cells<<<4 * ctx->num_sms, 256, 0, st>>>(ctx->cell_pick, ctx->misc); ed_note_launch();
+        ED_LAUNCH(k_fill_cells, 4 * ctx->num_sms, 256, st, ctx->cell_pick, ctx->misc); ed_note_launch();
         const int pg = min(ed_div_up(N, 256), 4 * ctx->num_sms);
-        k_cell_of<<<ed_div_up(N, 256), 256, 0, st>>>(P4, N, ctx->misc, ctx->fmisc, ctx->cell_of); ed_note_launch();
-        k_phase_count<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pcnt); ed_note_launch();
-        k_phase_scan<<<1, 32, 0, st>>>(pcnt, pstart, pfill); ed_note_launch();
-        k_phase_scatter<<<pg, 256, 0, st>>>(ctx->cell_of, N, ctx->misc, pstart, pfill, bucket); ed_note_launch();
+        ED_LAUNCH(k_cell_of, ed_div_up(N, 256), 256, st, P4, N, ctx->misc, ctx->fmisc, ctx->cell_of); ed_note_launch();
+        ED_LAUNCH(k_phase_count, pg, 256, st, ctx->cell_of, N, ctx->misc, pcnt); ed_note_launch();
+        ED_LAUNCH(k_phase_scan, 1, 32, st, pcnt, pstart, pfill); ed_note_launch();
+        ED_LAUNCH(k_phase_scatter, pg, 256, st, ctx->cell_of, N, ctx->misc, pstart, pfill, bucket); ed_note_launch();
         ED_LAUNCH_CHECK();
         // one cooperative launch for the 27 phases: one CTA per SM (fewer
         // barrier arrivals), sized down for small inputs.  A phase's points are
@@ -1235,7 +1322,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             void *args[] = {(void *)&P4, (void *)&bucket_c, (void *)&pstart_c, (void *)&misc_c, (void *)&fmisc_c,
                             (void *)&cell_pick, (void *)&bar, (void *)&status, (void *)&wait_ns};
             ed_note_launch();
-            ED_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_poisson_all, pick_grid, POISSON_T, args, 0, st));
+            ED_CUDA_TRY(ed_launch_coop((const void *)k_poisson_all, pick_grid, POISSON_T, args, 0, st, true));
         }
     }
     ED_CUDA_TRY(cudaEventSynchronize(ctx->ev_misc));
@@ -1256,12 +1343,12 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         }
         T.off[27] = tot;
         int *flags = ctx->cell_node, *pre = ctx->kcell_start;   // cells (+ 1) ints each
-        k_node_flags<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, flags); ed_note_launch();
+        ED_LAUNCH(k_node_flags, ed_div_up(tot, 256), 256, st, T, tot, ctx->misc, ctx->cell_pick, flags); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, flags, pre, tot, st, ctx->misc + MI_PHASE_BASE)) != ED_OK) return s;
-        k_node_write<<<ed_div_up(tot, 256), 256, 0, st>>>(T, tot, ctx->misc, ctx->cell_pick, pre, P4, G4, max_nodes); ed_note_launch();
+        ED_LAUNCH(k_node_write, ed_div_up(tot, 256), 256, st, T, tot, ctx->misc, ctx->cell_pick, pre, P4, G4, max_nodes); ed_note_launch();
         ED_LAUNCH_CHECK();
-        k_set_counts<<<1, 1, 0, st>>>(ctx->misc, max_nodes, graph->counts); ed_note_launch();
+        ED_LAUNCH(k_set_counts, 1, 1, st, ctx->misc, max_nodes, graph->counts); ed_note_launch();
     } else {
         ctx->pinned[ED_MAX_PCG_GRID + 3] = m_in;
         ctx->pinned[ED_MAX_PCG_GRID + 4] = m_in;
@@ -1278,20 +1365,20 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     const int *m_dev = graph->counts;
     ED_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
     ED_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-    k_node_graph<<<ed_div_up(max_nodes, NG_WARPS), 32 * NG_WARPS, 0, ctx->aux>>>(G4, m_dev, prm->k_graph, graph->nbr); ed_note_launch();
+    k_node_graph<<<ed_div_up(max_nodes, NG_WARPS), 32 * NG_WARPS, 0, ctx->aux>>>(G4, m_dev, prm->k_graph, graph->nbr, ctx->bitmap,
+                                                                                   max_nodes * ed_div_up(max_nodes, 32)); ed_note_launch();
     ED_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
     {
         const int kcells = hm[MI_KDIMS + 3];
         ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
         int *cell_of_node = ctx->row_cnt;   // scratch (m + 1 ints)
-        k_kcell_count<<<ed_div_up(max_nodes, 256), 256, 0, st>>>(G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_cnt,
+        ED_LAUNCH(k_kcell_count, ed_div_up(max_nodes, 256), 256, st, G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_cnt,
                                                                  cell_of_node); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->kcell_cnt, ctx->kcell_start, kcells, st)) != ED_OK) return s;
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->kcell_cnt, 0, sizeof(int) * (kcells + 1), st));
-        k_kcell_fill<<<ed_div_up(max_nodes, 256), 256, 0, st>>>(m_dev, G4, ctx->kcell_start, ctx->kcell_cnt,
+        ED_LAUNCH(k_kcell_fill, ed_div_up(max_nodes, 256), 256, st, m_dev, G4, ctx->kcell_start, ctx->kcell_cnt,
                                                                 cell_of_node, ctx->kcell_pos); ed_note_launch();
-        k_knn<<<ed_div_up(NT, 128), 128, 0, st>>>(PT, NT, G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_start,
+        ED_LAUNCH(k_knn, ed_div_up(NT, 128), 128, st, PT, NT, G4, m_dev, ctx->misc, ctx->fmisc, ctx->kcell_start,
                                                   ctx->kcell_pos, prm->weight_mode, prm->sigma,
                                                   (ushort4 *)graph->idx, (float4 *)graph->weights); ed_note_launch();
         ED_LAUNCH_CHECK();
@@ -1306,23 +1393,23 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         if ((long)NT <= 512L * max_nodes) {
             // buckets by smallest node (a few hundred points each at the node
             // densities of the path), each ordered by ranks
-            ED_CUDA_TRY(cudaMemsetAsync(ctx->bcnt, 0, sizeof(int) * 2 * ((size_t)max_nodes + 1), st));
+            // (bcnt and its fill counters were zeroed by k_build_init)
             int *bfill = ctx->bcnt + max_nodes + 1;
-            k_tb_count<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, ctx->bcnt); ed_note_launch();
+            ED_LAUNCH(k_tb_count, ed_div_up(NT, 256), 256, st, I4, NT, ctx->bcnt); ed_note_launch();
             ED_LAUNCH_CHECK();
             if ((s = ed_scan_exclusive(ctx, ctx->bcnt, ctx->bstart, max_nodes, st)) != ED_OK) return s;
-            k_tb_place<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, ctx->bstart, bfill, ctx->ent_key); ed_note_launch();
+            ED_LAUNCH(k_tb_place, ed_div_up(NT, 256), 256, st, I4, NT, ctx->bstart, bfill, ctx->ent_key); ed_note_launch();
             int pb = 1;
             while ((1L << pb) < (long)NT) ++pb;
             if (3 * fb + pb <= 64) {
-                k_tb_sort64<<<max_nodes, TB64_T, 0, st>>>(I4, ctx->bstart, max_nodes, fb, pb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+                ED_LAUNCH(k_tb_sort64, max_nodes, TB64_T, st, I4, ctx->bstart, max_nodes, fb, pb, ctx->ent_key, ctx->ent_val); ed_note_launch();
             } else {
-                k_tb_sort<<<max_nodes, TB_T, 0, st>>>(I4, ctx->bstart, max_nodes, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+                ED_LAUNCH(k_tb_sort, max_nodes, TB_T, st, I4, ctx->bstart, max_nodes, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
             }
             ED_LAUNCH_CHECK();
         } else {
             // few nodes for many points: large buckets; a stable radix sort by the full key
-            k_tuple_lo<<<ed_div_up(NT, 256), 256, 0, st>>>(I4, NT, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
+            ED_LAUNCH(k_tuple_lo, ed_div_up(NT, 256), 256, st, I4, NT, fb, ctx->ent_key, ctx->ent_val); ed_note_launch();
             ED_LAUNCH_CHECK();
             if ((s = ed_radix_sort_pairs(ctx, ctx->ent_key, ctx->ent_val, NT, 4 * fb < 32 ? 4 * fb : 32, st)) != ED_OK)
                 return s;
@@ -1333,12 +1420,12 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
             }
         }
         const float4 *NR = ctx->n_kp > 0 ? (const float4 *)ctx->comb_nrm : (const float4 *)nrm;
-        k_tuple_gather<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->ent_val, NT, I4, (const float4 *)graph->weights, PT, NR,
+        ED_LAUNCH(k_tuple_gather, ed_div_up(NT, 256), 256, st, ctx->ent_val, NT, I4, (const float4 *)graph->weights, PT, NR,
                                                            ctx->perm, ctx->spos, ctx->snrm, ctx->sidx, ctx->sw,
                                                            ctx->sidx_d, ctx->sw_d, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, NT, st, ctx->misc + MI_READ + 1)) != ED_OK) return s;
-        k_run_starts<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->flag_a, ctx->flag_b, NT, ctx->run_start,
+        ED_LAUNCH(k_run_starts, ed_div_up(NT, 256), 256, st, ctx->flag_a, ctx->flag_b, NT, ctx->run_start,
                                                          ctx->run_of_start); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
@@ -1356,52 +1443,52 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     const int *nnzb_dev = ctx->misc + MI_READ, *nruns_dev = ctx->misc + MI_READ + 1;
     const int g256 = 4 * ctx->num_sms;   // grid of the grid-stride launches over blocks and runs
     {
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->bitmap, 0, sizeof(uint32_t) * (size_t)m * words, st));
+        // (the bitmap was zeroed by k_node_graph: m x words <= max_nodes x words(max_nodes))
         // (the pairs of the points come from their runs: n_runs is on the device, the
         // grid covers every point)
         k_pairs_runs_dev<<<ed_div_up(NT, 256), 256, 0, st>>>(ctx->misc + MI_READ + 1, ctx->run_start, ctx->sidx,
                                                              ctx->bitmap, words); ed_note_launch();
-        k_pairs_graph<<<ed_div_up(m, 256), 256, 0, st>>>(graph->nbr, m, prm->k_graph, ctx->bitmap, words); ed_note_launch();
-        k_row_count<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
+        ED_LAUNCH(k_pairs_graph, ed_div_up(m, 256), 256, st, graph->nbr, m, prm->k_graph, ctx->bitmap, words); ed_note_launch();
+        ED_LAUNCH(k_row_count, ed_div_up(m, 4), 128, st, ctx->bitmap, m, words, ctx->row_cnt); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->row_cnt, ctx->row_ptr, m, st, ctx->misc + MI_READ)) != ED_OK) return s;
         // the block count and the number of runs go to the host (pinned copy +
         // event) while the block lists, which need only the row pointer, are
         // filled (checking the count against the capacity)
-        k_row_fill<<<ed_div_up(m, 4), 128, 0, st>>>(ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
+        ED_LAUNCH(k_row_fill, ed_div_up(m, 4), 128, st, ctx->bitmap, m, words, ctx->row_ptr, ctx->col, ctx->brow,
                                                     ctx->diag_pos, ctx->max_nnzb, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         // from here on the block count (misc[MI_READ]) and the run count
         // (misc[MI_READ + 1]) are read on the device: the launches are sized
         // for the capacities, grid-stride, and nothing runs past a block count
         // above the capacity (the row fill reported ED_ERR_CAPACITY)
-        k_tpos<<<g256, 256, 0, st>>>(nnzb_dev, cap, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
+        ED_LAUNCH(k_tpos, g256, 256, st, nnzb_dev, cap, ctx->row_ptr, ctx->col, ctx->brow, ctx->tpos, ctx->flag_a); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->flag_a, ctx->flag_b, cap, st, ctx->misc + MI_READ + 2, nnzb_dev)) != ED_OK)
             return s;
-        k_compact_upper<<<g256, 256, 0, st>>>(nnzb_dev, cap, m, ctx->flag_a, ctx->flag_b, ctx->diag_pos, ctx->up_list); ed_note_launch();
+        ED_LAUNCH(k_compact_upper, g256, 256, st, nnzb_dev, cap, m, ctx->flag_a, ctx->flag_b, ctx->diag_pos, ctx->up_list); ed_note_launch();
         ED_LAUNCH_CHECK();
     }
 
     // ---- incidences (block, run), sorted by block (stable: run order within a
     // block), and the assembly's per-block records ----
     {
-        k_inc_gen<<<g256, 256, 0, st>>>(nruns_dev, nnzb_dev, cap, ctx->run_start, ctx->sidx, ctx->row_ptr, ctx->col,
+        ED_LAUNCH(k_inc_gen, g256, 256, st, nruns_dev, nnzb_dev, cap, ctx->run_start, ctx->sidx, ctx->row_ptr, ctx->col,
                                         ctx->ent_key, ctx->ent_val, ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH_CHECK();
         // by block, each block's list in run order
-        ED_CUDA_TRY(cudaMemsetAsync(ctx->icnt, 0, sizeof(int) * 2 * (size_t)(cap + 1), st));
+        // (icnt and its fill counters were zeroed by k_build_init)
         int *ifill = ctx->icnt + cap + 1;
-        k_ic_count<<<4 * g256, 256, 0, st>>>(nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->icnt); ed_note_launch();
+        ED_LAUNCH(k_ic_count, 4 * g256, 256, st, nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->icnt); ed_note_launch();
         ED_LAUNCH_CHECK();
         if ((s = ed_scan_exclusive(ctx, ctx->icnt, ctx->ent_start, cap, st, nullptr, nnzb_dev)) != ED_OK) return s;
-        k_ic_place<<<4 * g256, 256, 0, st>>>(nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->ent_val, ctx->ent_start,
+        ED_LAUNCH(k_ic_place, 4 * g256, 256, st, nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->ent_val, ctx->ent_start,
                                               ifill, ctx->inc); ed_note_launch();
-        k_ic_sort<<<std::min(ed_div_up(cap, 4), 32 * ctx->num_sms), 128, 0, st>>>(nnzb_dev, cap, ctx->ent_start,
+        ED_LAUNCH(k_ic_sort, std::min(ed_div_up(cap, 4), 32 * ctx->num_sms), 128, st, nnzb_dev, cap, ctx->ent_start,
                                                                                   ctx->inc); ed_note_launch();
-        k_fin_pack<<<g256, 256, 0, st>>>(nnzb_dev, cap, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow, ctx->col,
+        ED_LAUNCH(k_fin_pack, g256, 256, st, nnzb_dev, cap, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow, ctx->col,
                                          ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr, ctx->fin_info); ed_note_launch();
-        k_counts_pattern<<<1, 1, 0, st>>>(ctx->misc, graph->counts); ed_note_launch();
+        ED_LAUNCH(k_counts_pattern, 1, 1, st, ctx->misc, graph->counts); ed_note_launch();
         ED_LAUNCH_CHECK();
         // what the host needs later (the counts, the row pointer of the PCG
         // plan) goes to pinned memory; ed_graph_ready reads it at the first

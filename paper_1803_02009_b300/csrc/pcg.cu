@@ -989,24 +989,6 @@ static ed_status pcg_fill_args(ed_context *ctx, const ed_pcg_plan_t &pl, const i
     return ED_OK;
 }
 
-// cooperative launch; pdl: also programmatic dependent launch (the kernel
-// waits for its stream predecessor before anything else)
-static cudaError_t launch_coop(const void *fn, int grid, int nt, void **args, size_t smem, cudaStream_t st, bool pdl)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(nt);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 2 : 1;
-    return cudaLaunchKernelExC(&cfg, fn, args);
-}
 
 ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, double *xm, double *pose,
                        ed_stats *stats, cudaStream_t st)
@@ -1025,7 +1007,7 @@ ed_status ed_pcg_solve(ed_context *ctx, const ed_solver_params *prm, float *x, d
     const void *fn = prm->precision == ED_PRECISION_MIXED        ? (const void *)k_pcg<double, 512>
                      : prm->precision == ED_PRECISION_MIXED_FP64 ? (const void *)k_pcg<PcgFp64, 512>
                                                                  : (const void *)k_pcg<float, 512>;
-    cudaError_t e = launch_coop(fn, ctx->pcg.grid, 512, args, ctx->pcg.smem, st, true);
+    cudaError_t e = ed_launch_coop(fn, ctx->pcg.grid, 512, args, ctx->pcg.smem, st, true);
     ed_tm_end(ctx, ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: PCG launch failed: %s\n", cudaGetErrorString(e));
@@ -1123,7 +1105,7 @@ ed_status ed_pcg_solve_batch(ed_context *const *ctxs, const ed_pcg_batch_plan_t 
     ed_note_launch();
     // (a timing hook set on the group's first context brackets the launch)
     ed_tm_begin(ctxs[0], ED_KERNEL_PCG, st);
-    cudaError_t e = launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st, false);
+    cudaError_t e = ed_launch_coop(fn, bp->grid, bp->nt, args, bp->smem, st, false);
     if (e == cudaSuccess) ed_tm_end(ctxs[0], ED_KERNEL_PCG, st);
     if (e != cudaSuccess) {
         fprintf(stderr, "libed: batched PCG launch failed: %s\n", cudaGetErrorString(e));
