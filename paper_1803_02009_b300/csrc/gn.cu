@@ -933,57 +933,60 @@ __device__ __forceinline__ void fin_offdiag_seg(const AsmArgs &a, int4 i0, int4 
     }
 }
 
-// a diagonal block (j, j) from its moments M and J^T r G (12 floats; the
-// pose-node block was written by the role-1 warps): one warp adds E_rot and
-// E_reg (out-edges j -> k: S = sum h h^T, h = [g_k - g_j; 1]; in-edges k -> j
-// on the t rows), writes the block, the gradient and the node's energies, and
-// (INV) the inverse of the jittered block
-template <bool INV>
-__device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, const float *M, const float *G, float *H,
-                                         float *X, float *S, float *Lw, int *Nk, float4 *Ng, float *Nx)
+// The finalisation of the diagonal block (j, j) by two warps of one CTA (a
+// node pair of warps).  Both first take the frame's graph data (the out-edges
+// j -> k and their positions, the in-edges k -> j of row j: the pattern and
+// the node positions are fixed for the frame, so these loads come before the
+// wait for the assembly).  The block warp then adds E_rot and E_reg (out-edges:
+// S = sum h h^T, h = [g_k - g_j; 1]; in-edges on the t rows) to the moments,
+// writes the block and (INV) the inverse of the jittered block; the gradient
+// warp forms the rot and reg residuals once, the gradient (data + E_rot +
+// E_reg) and the node's energies.
+struct FinGraph {
+    int nk;                 // this lane's out-edge node (lane < kg; -1 none)
+    float4 gk;              // its position
+    int kin;                // this lane's in-edge node (row entry rp0 + lane; -1 none)
+    float4 gkin;
+    bool more;              // row j has more than 32 entries (the rest is taken after the wait)
+};
+
+__device__ __forceinline__ FinGraph fin_graph(const AsmArgs &a, int j, int rp0, int rp1)
 {
     const int lane = threadIdx.x & 31;
-    const int b = i0.x, j = i0.y;
-    const int rp0 = i0.w, rp1 = rp0 + i1.z;   // row j of the block pattern
-    const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
-    const bool ent_lane = lane < 24;
-    const float wr = a.w_reg;
-    if (lane < a.kg) {   // out-edges j -> k: index, position and parameters of k, loaded once
-        const int k = a.nbr[j * a.kg + lane];
-        Nk[lane] = k;
-        if (k >= 0) {
-            Ng[lane] = a.g[k];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) reinterpret_cast<float4 *>(Nx + 12 * lane)[q] = a.x4[3 * k + q];
-        }
+    FinGraph f;
+    f.nk = -1;
+    f.gk = make_float4(0.f, 0.f, 0.f, 0.f);
+    f.kin = -1;
+    f.gkin = f.gk;
+    f.more = rp1 - rp0 > 32;
+    if (lane < a.kg) {
+        f.nk = a.nbr[j * a.kg + lane];
+        if (f.nk >= 0) f.gk = a.g[f.nk];
     }
-    if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
-    const float4 gj = a.g[j];
-    __syncwarp();
-    if (lane < 16) {
-        const int c = lane >> 2, cq = lane & 3;
-        float v = 0.f;
-        for (int s = 0; s < a.kg; ++s) {
-            if (Nk[s] < 0) continue;
-            const float4 gk = Ng[s];
-            const float hx = gk.x - gj.x, hy = gk.y - gj.y, hz = gk.z - gj.z;
-            v += pick4(hx, hy, hz, 1.f, c) * pick4(hx, hy, hz, 1.f, cq);
-        }
-        S[lane] = v;
-    }
-    // in-edges k -> j (they lie in row j): count and summed residuals
-    float nin = 0.f, ein0 = 0.f, ein1 = 0.f, ein2 = 0.f;
-    for (int t = rp0 + lane; t < rp1; t += 32) {
+    const int t = rp0 + lane;
+    if (t < rp1) {
         const int k = a.col[t];
-        int nb[ED_MAX_KG];
-#pragma unroll
-        for (int s = 0; s < ED_MAX_KG; ++s) nb[s] = s < a.kg ? a.nbr[k * a.kg + s] : -1;
-        const float4 gk = a.g[k];
-        const float4 xk0 = a.x4[3 * k], xk1 = a.x4[3 * k + 1], xk2 = a.x4[3 * k + 2];
         bool in = false;
 #pragma unroll
-        for (int s = 0; s < ED_MAX_KG; ++s) in |= nb[s] == j;
-        if (k == j || !in) continue;
+        for (int s = 0; s < ED_MAX_KG; ++s) in |= s < a.kg && a.nbr[k * a.kg + s] == j;
+        if (k != j && in) {
+            f.kin = k;
+            f.gkin = a.g[k];
+        }
+    }
+    return f;
+}
+
+// the in-edge count and summed reg residuals of row j (lane sums over the
+// entries t = rp0 + lane, rp0 + lane + 32, ..., then a butterfly)
+__device__ __forceinline__ void fin_in_edges(const AsmArgs &a, const FinGraph &f, int j, int rp0, int rp1, float4 gj,
+                                             const float *X, float &nin, float &ein0, float &ein1, float &ein2)
+{
+    const int lane = threadIdx.x & 31;
+    nin = 0.f;
+    ein0 = ein1 = ein2 = 0.f;
+    auto add = [&](int k, float4 gk) {
+        const float4 xk0 = a.x4[3 * k], xk1 = a.x4[3 * k + 1], xk2 = a.x4[3 * k + 2];
         const float hh[3] = {gj.x - gk.x, gj.y - gk.y, gj.z - gk.z};
         const float x0[4] = {xk0.x, xk0.y, xk0.z, xk0.w}, x1[4] = {xk1.x, xk1.y, xk1.z, xk1.w};
         const float x2[4] = {xk2.x, xk2.y, xk2.z, xk2.w};
@@ -991,6 +994,16 @@ __device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, con
         ein0 += ed_reg_residual(x0, 0, hh, X[3]);
         ein1 += ed_reg_residual(x1, 1, hh, X[7]);
         ein2 += ed_reg_residual(x2, 2, hh, X[11]);
+    };
+    if (f.kin >= 0) add(f.kin, f.gkin);
+    if (f.more) {   // (rows of more than 32 blocks: rare)
+        for (int t = rp0 + lane + 32; t < rp1; t += 32) {
+            const int k = a.col[t];
+            bool in = false;
+#pragma unroll
+            for (int s = 0; s < ED_MAX_KG; ++s) in |= s < a.kg && a.nbr[k * a.kg + s] == j;
+            if (k != j && in) add(k, a.g[k]);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -999,9 +1012,20 @@ __device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, con
         ein1 += __shfl_xor_sync(0xffffffffu, ein1, o);
         ein2 += __shfl_xor_sync(0xffffffffu, ein2, o);
     }
-    __syncwarp();
-    // the 144 entries: data moments + E_rot + E_reg (out-edges S, in-edges on t)
-    if (ent_lane) {
+}
+
+// block warp: the 144 entries of the diagonal block (data moments M + E_rot +
+// E_reg: out-edges S, in-edges on t), the block to bsr and H, and (INV) its
+// jittered inverse
+template <bool INV>
+__device__ __forceinline__ void fin_diag_block(const AsmArgs &a, int4 i0, const float *M, const float *X, const float *S,
+                                               float nin, float *H, float *Lw)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = i0.x, j = i0.y;
+    const int Cc = lane % 12, h0 = lane < 12 ? 0 : 1, rp = Cc >> 2, cp = Cc & 3;
+    const float wr = a.w_reg;
+    if (lane < 24) {
         float *dst = a.bsr + (long)b * 144 + Cc;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -1018,44 +1042,6 @@ __device__ __forceinline__ void fin_diag(const AsmArgs &a, int4 i0, int4 i1, con
             H[R * 12 + Cc] = h;
             dst[R * 12] = h;
         }
-    }
-    // gradient: data + E_rot + E_reg (out-edges, in-edges)
-    if (lane < 12) {
-        const int r = lane >> 2, c = lane & 3;
-        float g = G[lane];
-        if (c < 3) {
-            float v = 0.f;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v += rot_res(X, q) * rot_jac(X, q, r, c);
-            g += a.w_rot * v;
-        }
-        for (int s = 0; s < a.kg; ++s) {
-            if (Nk[s] < 0) continue;
-            const float4 gk = Ng[s];
-            const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
-            const float er = ed_reg_residual(X + 4 * r, r, hh, Nx[12 * s + 4 * r + 3]);
-            g += wr * er * pick4(hh[0], hh[1], hh[2], 1.f, c);
-        }
-        if (c == 3) g -= wr * (r == 0 ? ein0 : (r == 1 ? ein1 : ein2));
-        a.grad[12 * j + lane] = g;
-    }
-    // energies of node j: Rot(A_j), and its out-edges
-    if (lane == 0) {
-        float erot = 0.f, ereg = 0.f;
-        for (int q = 0; q < 6; ++q) {
-            const float rho = rot_res(X, q);
-            erot += a.w_rot * rho * rho;
-        }
-        for (int s = 0; s < a.kg; ++s) {
-            if (Nk[s] < 0) continue;
-            const float4 gk = Ng[s];
-            const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
-            for (int r = 0; r < 3; ++r) {
-                const float e = ed_reg_residual(X + 4 * r, r, hh, Nx[12 * s + 4 * r + 3]);
-                ereg += wr * e * e;
-            }
-        }
-        a.node_energy[j] = make_float2(erot, ereg);
     }
     __syncwarp();
     if (!INV) return;
@@ -1127,26 +1113,127 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
 }
 
 
-// the diagonal blocks from their moments and J^T r (dmom), one warp per node:
-// E_rot and E_reg terms, the gradient, the node energies and (INV) the
-// block-Jacobi inverse (fin_diag)
+// the diagonal blocks from their moments and J^T r (dmom), two warps per node
+// (fin_graph, fin_diag_block, the gradient and energies below): E_rot and
+// E_reg terms, the gradient, the node energies and (INV) the block-Jacobi
+// inverse
 template <bool INV>
 __global__ void __launch_bounds__(32 * ASM_WARPS) k_fin_diag(AsmArgs a)
 {
-    __shared__ __align__(16) float sM[ASM_WARPS][72];
-    __shared__ float sH[ASM_WARPS][144], sL[ASM_WARPS][144], sX[ASM_WARPS][12], sS[ASM_WARPS][16];
-    __shared__ int sNk[ASM_WARPS][ED_MAX_KG];
-    __shared__ float4 sNg[ASM_WARPS][ED_MAX_KG];
-    __shared__ __align__(16) float sNx[ASM_WARPS][12 * ED_MAX_KG];
+    constexpr int NPC = ASM_WARPS / 2;   // nodes per CTA
+    __shared__ __align__(16) float sM[NPC][72];
+    __shared__ float sH[NPC][144], sL[NPC][144], sX[NPC][2][12], sS[NPC][16];
+    __shared__ float4 sNg[NPC][2][ED_MAX_KG];
+    __shared__ __align__(16) float sNx[NPC][12 * ED_MAX_KG];
+    __shared__ float sRho[NPC][6], sEr[NPC][3 * ED_MAX_KG];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = (int)blockIdx.x * ASM_WARPS + wid;
-    const int4 i0 = j < a.m ? a.info[2 * j] : make_int4(0, 0, 0, 0), i1 = j < a.m ? a.info[2 * j + 1] : make_int4(0, 0, 0, 0);
+    const int q = wid >> 1, role = wid & 1;   // role 0: the block, role 1: gradient and energies
+    const int j = (int)blockIdx.x * NPC + q;
+    const bool act = j < a.m;
+    const int4 i0 = act ? a.info[2 * j] : make_int4(0, 0, 0, 0), i1 = act ? a.info[2 * j + 1] : make_int4(0, 0, 0, 0);
+    const int rp0 = i0.w, rp1 = rp0 + i1.z;   // row j of the block pattern
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the frame's graph data: before the wait
+    const float4 gj = act ? a.g[j] : z4;
+    FinGraph fg;
+    fg.nk = -1;
+    fg.kin = -1;
+    fg.more = false;
+    if (act) fg = fin_graph(a, j, rp0, rp1);
     ed_pdl_wait();
     ed_pdl_trigger();
-    if (j >= a.m) return;
-    for (int q = lane; q < 72; q += 32) sM[wid][q] = __ldcg(a.dmom + (long)j * 72 + q);
+    if (!act) return;
+    const float wr = a.w_reg;
+    const unsigned has_k = __ballot_sync(0xffffffffu, lane < a.kg && fg.nk >= 0);   // bit s: out-edge s exists
+    float *X = sX[q][role];
+    if (lane < 12) X[lane] = (&a.x4[3 * j].x)[lane];
+    if (lane < a.kg) sNg[q][role][lane] = fg.gk;
+    if (role == 0) {
+        for (int e = lane; e < 60; e += 32) sM[q][e] = __ldcg(a.dmom + (long)j * 72 + e);
+        __syncwarp();
+        if (lane < 16) {   // S = sum over the out-edges of h h^T
+            const int c = lane >> 2, cq = lane & 3;
+            float v = 0.f;
+            for (int s = 0; s < a.kg; ++s) {
+                if (!(has_k >> s & 1u)) continue;
+                const float4 gk = sNg[q][0][s];
+                const float hx = gk.x - gj.x, hy = gk.y - gj.y, hz = gk.z - gj.z;
+                v += pick4(hx, hy, hz, 1.f, c) * pick4(hx, hy, hz, 1.f, cq);
+            }
+            sS[q][lane] = v;
+        }
+        // in-edge count: the block needs only nin (the residual sums are the gradient warp's)
+        float nin = fg.kin >= 0 ? 1.f : 0.f;
+        if (fg.more)
+            for (int t = rp0 + lane + 32; t < rp1; t += 32) {
+                const int k = a.col[t];
+                bool in = false;
+#pragma unroll
+                for (int s = 0; s < ED_MAX_KG; ++s) in |= s < a.kg && a.nbr[k * a.kg + s] == j;
+                if (k != j && in) nin += 1.f;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(0xffffffffu, nin, o);
+        __syncwarp();
+        fin_diag_block<INV>(a, i0, sM[q], X, sS[q], nin, sH[q], sL[q]);
+        return;
+    }
+    // gradient warp: J^T r of the moments pass, the node parameters of the
+    // out-edges, the residuals once
+    float G = lane < 12 ? __ldcg(a.dmom + (long)j * 72 + 60 + lane) : 0.f;
+    if (lane < a.kg && fg.nk >= 0) {
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) reinterpret_cast<float4 *>(sNx[q] + 12 * lane)[c3] = a.x4[3 * fg.nk + c3];
+    }
     __syncwarp();
-    fin_diag<INV>(a, i0, i1, sM[wid], sM[wid] + 60, sH[wid], sX[wid], sS[wid], sL[wid], sNk[wid], sNg[wid], sNx[wid]);
+    float nin, ein0, ein1, ein2;
+    fin_in_edges(a, fg, j, rp0, rp1, gj, X, nin, ein0, ein1, ein2);
+    if (lane < 6) sRho[q][lane] = rot_res(X, lane);
+    if (lane >= 8 && lane < 8 + 3 * a.kg) {   // reg residual of out-edge s, row r
+        const int e = lane - 8, s = e / 3, r = e - 3 * s;
+        float er = 0.f;
+        if (has_k >> s & 1u) {
+            const float4 gk = sNg[q][1][s];
+            const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
+            er = ed_reg_residual(X + 4 * r, r, hh, sNx[q][12 * s + 4 * r + 3]);
+        }
+        sEr[q][e] = er;
+    }
+    __syncwarp();
+    if (lane < 12) {
+        const int r = lane >> 2, c = lane & 3;
+        float g = G;
+        if (c < 3) {
+            float v = 0.f;
+#pragma unroll
+            for (int q6 = 0; q6 < 6; ++q6) v += sRho[q][q6] * rot_jac(X, q6, r, c);
+            g += a.w_rot * v;
+        }
+        for (int s = 0; s < a.kg; ++s) {
+            if (!(has_k >> s & 1u)) continue;
+            const float4 gk = sNg[q][1][s];
+            const float hh[3] = {gk.x - gj.x, gk.y - gj.y, gk.z - gj.z};
+            g += wr * sEr[q][3 * s + r] * pick4(hh[0], hh[1], hh[2], 1.f, c);
+        }
+        if (c == 3) g -= wr * (r == 0 ? ein0 : (r == 1 ? ein1 : ein2));
+        a.grad[12 * j + lane] = g;
+    }
+    // energies of node j: Rot(A_j), and its out-edges (the residuals above, in order)
+    if (lane == 0) {
+        float erot = 0.f, ereg = 0.f;
+        for (int q6 = 0; q6 < 6; ++q6) {
+            const float rho = sRho[q][q6];
+            erot += a.w_rot * rho * rho;
+        }
+        for (int s = 0; s < a.kg; ++s) {
+            if (!(has_k >> s & 1u)) continue;
+            for (int r = 0; r < 3; ++r) {
+                const float e = sEr[q][3 * s + r];
+                ereg += wr * e * e;
+            }
+        }
+        a.node_energy[j] = make_float2(erot, ereg);
+    }
 }
 
 #define FIN_WARPS 4
@@ -1640,7 +1727,7 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
                                  : (pairs ? k_assemble<true, 2> : k_assemble<true, 1>);
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_CUDA_TRY(ed_launch_pdl(ka, dim3(grid), dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
-        ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS)),
+        ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS / 2)),
                                   dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
         ED_LAUNCH_CHECK();
