@@ -793,16 +793,11 @@ __device__ __forceinline__ void role1(const AsmArgs &a, int i0, int n, float4 gj
     if (lane < NSLOT) reinterpret_cast<float2 *>(G)[lane] = t;   // G: this half's slots
 }
 
-__device__ __forceinline__ int sym3(int a, int b)
-{
-    if (a > b) { int t = a; a = b; b = t; }
-    return a == 0 ? b : (a == 1 ? 2 + b : 5);
-}
-__device__ __forceinline__ int sym4(int a, int b)
-{
-    if (a > b) { int t = a; a = b; b = t; }
-    return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
-}
+// index of the pair (a, b) among the unique entries of a symmetric 3x3
+// (xx xy xz yy yz zz) or 4x4 matrix (upper triangle row by row), from tables
+// of 4-bit entries indexed by 3 a + b / 4 a + b (no branches)
+__device__ __forceinline__ int sym3(int a, int b) { return (int)((0x542431210ull >> (4 * (3 * a + b))) & 15u); }
+__device__ __forceinline__ int sym4(int a, int b) { return (int)((0x9863875265413210ull >> (4 * (4 * a + b))) & 15u); }
 
 // derivative of the Rot(A) residual q (column pair ca, cb) with respect to
 // the parameter 4 r + c of [A | t]
@@ -842,15 +837,18 @@ __device__ __forceinline__ float rot_jtj(const float *X, int r, int c, int rp, i
 // warp): Gauss-Jordan elimination without pivoting on [H + jitter tr/12 I | I].
 // H is symmetric positive definite, so every pivot is positive (the pivots
 // are the squares of the Cholesky pivots).  Lane r < 24 keeps row r % 12 of
-// the left (r < 12) or the right half in registers; the pivot row and the
-// elimination factors travel by shuffles, so the 12 steps have no shared
-// memory traffic.  The right half, symmetrised through `scratch` (144
-// floats), goes to out (row-major); false, with out untouched, on a
+// the left (r < 12) or the right half in registers.  At step k the two lanes
+// of row k store it, and the left lanes their column-k entry, to `scratch`
+// (144 floats, 16-byte aligned; two buffers by the parity of k, so one warp
+// barrier per step), and every lane reads back its pivot, its factor and the
+// pivot row of its half (broadcast loads).  The right half, symmetrised
+// through `scratch`, goes to out (row-major); false, with out untouched, on a
 // non-positive pivot.
 __device__ __forceinline__ bool block_inverse12(const float *H, float *scratch, float jitter, float *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
-    const int r = lane < 24 ? lane % 12 : 0, half = lane >= 12 && lane < 24 ? 1 : 0;
+    const bool row_lane = lane < 24;
+    const int r = row_lane ? lane % 12 : 0, half = lane >= 12 && lane < 24 ? 1 : 0;
     float tr = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; ++k) tr += H[k * 13];
@@ -859,17 +857,27 @@ __device__ __forceinline__ bool block_inverse12(const float *H, float *scratch, 
 #pragma unroll
     for (int c = 0; c < 12; ++c) v[c] = half ? (c == r ? 1.0f : 0.0f) : H[r * 12 + c] + (c == r ? jd : 0.0f);
     bool ok = true;
+    __syncwarp();   // (scratch may hold the caller's data until here)
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        const float piv = __shfl_sync(0xffffffffu, v[k], k);   // row k, column k (left half)
-        const float fr = __shfl_sync(0xffffffffu, v[k], r);    // row r, column k (left half)
+        float *buf = scratch + (k & 1) * 36;   // [2 halves][12] pivot rows, [12] column k of the left half
+        if (row_lane && r == k) {
+            float4 *d4 = reinterpret_cast<float4 *>(buf + 12 * half);
+            d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+            d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+            d4[2] = make_float4(v[8], v[9], v[10], v[11]);
+        }
+        if (lane < 12) buf[24 + r] = v[k];
+        __syncwarp();
+        const float piv = buf[k];         // row k, column k (left half)
+        const float fr = buf[24 + r];     // row r, column k (left half)
         ok = ok && piv > 0.0f;
         const float ip = 1.0f / piv, f = -fr * ip;
+        const float4 *s4 = reinterpret_cast<const float4 *>(buf + 12 * half);   // the pivot row of this lane's half
+        const float4 q0 = s4[0], q1 = s4[1], q2 = s4[2];
+        const float pr[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            const float pc = __shfl_sync(0xffffffffu, v[c], k + 12 * half);   // pivot row, this lane's half
-            v[c] = r == k ? pc * ip : fmaf(f, pc, v[c]);
-        }
+        for (int c = 0; c < 12; ++c) v[c] = r == k ? pr[c] * ip : fmaf(f, pr[c], v[c]);
     }
     if (!ok) return false;
     __syncwarp();
@@ -1122,7 +1130,8 @@ __global__ void __launch_bounds__(32 * ASM_WARPS) k_fin_diag(AsmArgs a)
 {
     constexpr int NPC = ASM_WARPS / 2;   // nodes per CTA
     __shared__ __align__(16) float sM[NPC][72];
-    __shared__ float sH[NPC][144], sL[NPC][144], sX[NPC][2][12], sS[NPC][16];
+    __shared__ float sH[NPC][144], sX[NPC][2][12], sS[NPC][16];
+    __shared__ __align__(16) float sL[NPC][144];
     __shared__ float4 sNg[NPC][2][ED_MAX_KG];
     __shared__ __align__(16) float sNx[NPC][12 * ED_MAX_KG];
     __shared__ float sRho[NPC][6], sEr[NPC][3 * ED_MAX_KG];
@@ -1565,7 +1574,7 @@ __global__ void __launch_bounds__(32 * FIN_WARPS) k_lm_precond(const int *__rest
                                                                 int *__restrict__ misc)
 {
     __shared__ float sH[FIN_WARPS][144];
-    __shared__ float sL[FIN_WARPS][144];
+    __shared__ __align__(16) float sL[FIN_WARPS][144];
     __shared__ float sRinv[FIN_WARPS][12];
     if (misc[MI_STATUS] != ED_OK) return;
     const float f = 1.0f + (float)dmisc[DM_LAM];
