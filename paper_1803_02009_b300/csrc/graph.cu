@@ -789,11 +789,13 @@ __global__ void k_tb_place(const ushort4 *__restrict__ idx, int n, const int *__
 // The same ordering with the key and the point index packed into one 64-bit
 // word (rest of the tuple << pb | point: unique, so the order is total; for
 // 3 fb + pb <= 64): one compare-exchange pair per thread and step of the
-// bitonic network (TB64_T = 128 threads: a bucket of 256 padded entries
-// takes every thread once per step), and one 8-byte array in shared memory.
+// bitonic network (TB64_T = 512 threads: the largest buckets, near 700
+// entries padded to 1024, take every thread once per step; with 128 threads
+// those CTAs ran four passes per step and set the kernel's length), and one
+// 8-byte array in shared memory.
 // Buckets above TB_MAX entries are ranked: every entry counts the smaller
 // keys, in tiles of TB_MAX.
-#define TB64_T 128
+#define TB64_T 512
 __global__ void __launch_bounds__(TB64_T) k_tb_sort64(const ushort4 *__restrict__ idx, const int *__restrict__ start,
                                                       int nb, int fb, int pb, const uint32_t *__restrict__ order,
                                                       uint32_t *__restrict__ out)
@@ -995,11 +997,16 @@ __device__ __forceinline__ void ic_sort_block(const int *__restrict__ start, uin
             }
         return;
     }
-    // element q of 64 is held by lane q >> 1, slot q & 1; padding sorts last
+    // element q of 64 is held by lane q >> 1, slot q & 1; padding sorts last.
+    // The network spans the P = 2^k >= n first elements only (the others are
+    // padding, and a compare-exchange never pairs q < P with q >= P): a block
+    // holds 7.5 runs on average at 640x480
     uint32_t v[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) v[u] = 2 * lane + u < n ? list[b0 + 2 * lane + u] : 0xffffffffu;
-    for (int k = 2; k <= 64; k <<= 1)
+    int P = 2;
+    while (P < n) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
             // the partners' values, all read before any slot changes: for j = 1
             // the other slot of this lane, else lane ^ (j / 2), same slot
