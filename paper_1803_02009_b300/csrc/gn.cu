@@ -1057,10 +1057,11 @@ __device__ __forceinline__ void fin_diag_block(const AsmArgs &a, int4 i0, const 
         atomicCAS(a.status, 0, ED_ERR_BREAKDOWN);
 }
 
-#define ASM_WARPS 4
+#define ASM_WARPS 4     // k_fin_diag: four warps (two nodes) per CTA
+#define ASM_WARPS_A 2   // k_assemble: two warps per CTA (a CTA's slot frees when its slowest warp ends)
 
 
-// One warp per work item, four per CTA, in this order: the moments of the m
+// One warp per work item, two per CTA, in this order: the moments of the m
 // diagonal blocks (to dmom[j][0..60)), the two halves of J^T r and the
 // pose-node block of every node (J^T r to dmom[j][60..72), the pose-node
 // block to pnode; k_fin_diag finalises the diagonal blocks from dmom), then
@@ -1068,13 +1069,13 @@ __device__ __forceinline__ void fin_diag_block(const AsmArgs &a, int4 i0, const 
 // blocks, two per warp (one per 16-lane half: they hold a few dozen points
 // each), each finalised by its half.
 template <bool INV, int PAIRS>
-__global__ void __launch_bounds__(32 * ASM_WARPS) k_assemble(AsmArgs a)
+__global__ void __launch_bounds__(32 * ASM_WARPS_A) k_assemble(AsmArgs a)
 {
-    __shared__ __align__(16) float sM[ASM_WARPS][120];
-    __shared__ float s_R[ASM_WARPS][9];
-    __shared__ __align__(16) float2 s_red[ASM_WARPS][32 * RED_RS];
+    __shared__ __align__(16) float sM[ASM_WARPS_A][120];
+    __shared__ float s_R[ASM_WARPS_A][9];
+    __shared__ __align__(16) float2 s_red[ASM_WARPS_A][32 * RED_RS];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = (int)blockIdx.x * ASM_WARPS + wid;
+    const int w = (int)blockIdx.x * ASM_WARPS_A + wid;
     const int m = a.m;
     const int kind = w < m ? 0 : (w < 3 * m ? 1 : 2);   // diagonal moments, node rows, off-diagonal blocks
     const int u = kind == 0 ? w : (kind == 1 ? (w - m) >> 1 : (PAIRS == 2 ? m + 2 * (w - 3 * m) + (lane >> 4) : m + (w - 3 * m)));
@@ -1731,11 +1732,11 @@ ed_status ed_gn_pre(ed_context *ctx, const ed_frame *fr, const ed_solver_params 
         // warp items: m diagonal moments, 2 m node rows, the off-diagonal blocks
         // (two per warp by default; one per warp in a batch schedule that picks it)
         const bool pairs = ctx->asm_pairs == 2;
-        const int grid = ed_div_up(3 * m + (pairs ? (aa.n_off + 1) / 2 : aa.n_off), ASM_WARPS);
+        const int grid = ed_div_up(3 * m + (pairs ? (aa.n_off + 1) / 2 : aa.n_off), ASM_WARPS_A);
         void (*ka)(AsmArgs) = lm ? (pairs ? k_assemble<false, 2> : k_assemble<false, 1>)
                                  : (pairs ? k_assemble<true, 2> : k_assemble<true, 1>);
         ed_tm_begin(ctx, ED_KERNEL_ASSEMBLE, st);
-        ED_CUDA_TRY(ed_launch_pdl(ka, dim3(grid), dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
+        ED_CUDA_TRY(ed_launch_pdl(ka, dim3(grid), dim3(32 * ASM_WARPS_A), 0, st, aa)); ed_note_launch();
         ED_CUDA_TRY(ed_launch_pdl(lm ? k_fin_diag<false> : k_fin_diag<true>, dim3(ed_div_up(m, ASM_WARPS / 2)),
                                   dim3(32 * ASM_WARPS), 0, st, aa)); ed_note_launch();
         ed_tm_end(ctx, ED_KERNEL_ASSEMBLE, st);
