@@ -292,12 +292,23 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points_step(PointArgs a, C
     const unsigned lt = (1u << lane) - 1u;
     constexpr int ROUNDS = CHUNK / ED_K1_THREADS;
     int nvalid = 0, run_r[ROUNDS], run_l[ROUNDS];
+    // every round's points are evaluated before the first staging (no CTA
+    // barrier between the evaluations, so their loads overlap)
+    float4 R0[ROUNDS], R1[ROUNDS];
+    bool V[ROUNDS];
+#pragma unroll
+    for (int e = 0; e < ROUNDS; ++e) {
+        const int k = chunk * CHUNK + e * ED_K1_THREADS + threadIdx.x;
+        R0[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        R1[e] = R0[e];
+        V[e] = k < a.n && point_eval<false>(a, P, k, acc, R0[e], R1[e]);
+    }
 #pragma unroll
     for (int e = 0; e < ROUNDS; ++e) {
         const int k = chunk * CHUNK + e * ED_K1_THREADS + threadIdx.x;
         const bool in = k < a.n;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        const bool valid = in && point_eval<false>(a, P, k, acc, r0, r1);
+        const float4 r0 = R0[e], r1 = R1[e];
+        const bool valid = V[e];
         const unsigned bal = __ballot_sync(full, valid);
         if (lane == 0) s_warp[wid] = __popc(bal);
         __syncthreads();

@@ -404,17 +404,33 @@ __global__ void k_kcell_fill(const int *__restrict__ m_dev, const float4 *__rest
 
 #define KNN_S 5   // K + 1 nearest (Eq. 2 needs the (K+1)-th distance)
 
-__device__ __forceinline__ void topk_ins(float *kk, int *ii, float key, int id)
+// insertion of (key, id) into the sorted list (kk, ii) of the KNN_S best
+// (ties to the lower index): the new entry replaces the last one and moves up
+// by compare-exchanges with static indices, so the lists stay in registers
+__device__ __forceinline__ void topk_ins(float (&kk)[KNN_S], int (&ii)[KNN_S], float key, int id)
 {
     if (key > kk[KNN_S - 1] || (key == kk[KNN_S - 1] && id >= ii[KNN_S - 1])) return;
-    int p = KNN_S - 1;
-    while (p > 0 && (kk[p - 1] > key || (kk[p - 1] == key && ii[p - 1] > id))) {
-        kk[p] = kk[p - 1];
-        ii[p] = ii[p - 1];
-        --p;
+    kk[KNN_S - 1] = key;
+    ii[KNN_S - 1] = id;
+#pragma unroll
+    for (int p = KNN_S - 1; p > 0; --p) {
+        const bool up = kk[p - 1] > kk[p] || (kk[p - 1] == kk[p] && ii[p - 1] > ii[p]);
+        const float tk = kk[p - 1];
+        const int ti = ii[p - 1];
+        kk[p - 1] = up ? kk[p] : tk;
+        ii[p - 1] = up ? ii[p] : ti;
+        kk[p] = up ? tk : kk[p];
+        ii[p] = up ? ti : ii[p];
     }
-    kk[p] = key;
-    ii[p] = id;
+}
+
+// kk[q] for a run-time q < KNN_S, by static indices
+__device__ __forceinline__ float pick_k(const float (&kk)[KNN_S], int q)
+{
+    float v = kk[0];
+#pragma unroll
+    for (int s = 1; s < KNN_S; ++s) v = q == s ? kk[s] : v;
+    return v;
 }
 
 // K+1 nearest nodes by rings of search cells; a ring R is the last one needed
@@ -466,9 +482,10 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
                 }
             }
         }
-        if (need > 0 && kk[need - 1] < INFINITY) {
+        if (need > 0) {
+            const float kn = pick_k(kk, need - 1);
             const float b = (float)R * kc;
-            if (kk[need - 1] < b * b * 0.99999f) break;
+            if (kn < INFINITY && kn < b * b * 0.99999f) break;
         }
     }
     // weights (Eq. 1 normalised; Gaussian or Eq. 2); slots >= m hold no node
