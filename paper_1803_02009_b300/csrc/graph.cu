@@ -461,7 +461,35 @@ __global__ void k_knn(const float4 *__restrict__ pos, int n, const float4 *__res
     int maxR = dims[0];
     if (dims[1] > maxR) maxR = dims[1];
     if (dims[2] > maxR) maxR = dims[2];
-    for (int R = 0; R <= maxR; ++R) {
+    // rings 0 and 1 together (the stopping test after ring 0 never holds: its
+    // bound is 0), as the nine x-rows of the 3x3x3 block: each row is one
+    // contiguous range of the cell-sorted nodes, and every range bound is loaded
+    // before the first node (the order of the candidates does not change the
+    // result: the lists are ordered by key and index)
+    {
+        int lo[9], hi[9];
+        const int x0 = c.x > 0 ? c.x - 1 : 0, x1 = c.x + 1 < dims[0] ? c.x + 1 : dims[0] - 1;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const int ay = c.y + (r % 3) - 1, az = c.z + (r / 3) - 1;
+            const bool ok = ay >= 0 && ay < dims[1] && az >= 0 && az < dims[2];
+            const int Lb = dims[0] * (ay + dims[1] * az);
+            lo[r] = ok ? start[Lb + x0] : 0;
+            hi[r] = ok ? start[Lb + x1 + 1] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+            for (int t = lo[r]; t < hi[r]; ++t) {
+                const float4 g = __ldg(kpos + t);
+                topk_ins(kk, ii, ed_key(p.x, p.y, p.z, g.x, g.y, g.z), __float_as_int(g.w));
+            }
+    }
+    bool done = false;
+    if (need > 0) {
+        const float kn = pick_k(kk, need - 1);
+        done = kn < INFINITY && kn < kc * kc * 0.99999f;
+    }
+    for (int R = 2; R <= maxR && !done; ++R) {
         for (int dz = -R; dz <= R; ++dz) {
             const int az = c.z + dz;
             if (az < 0 || az >= dims[2]) continue;
