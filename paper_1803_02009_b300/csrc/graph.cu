@@ -1166,6 +1166,10 @@ __global__ void k_run_starts(const int *__restrict__ flag, const int *__restrict
 // the 10 incidences of every run: key = block of (tuple[s], tuple[t]) in the
 // BSR pattern, value = run << 4 | s << 2 | t (s <= t, so tuple[s] is the row
 // node: the block is upper or diagonal)
+// the ten incidences of run r: the blocks (t4[s], t4[t]), s <= t, of its
+// tuple, found by ten binary searches in the rows of the tuple's nodes that
+// advance in step (the loads of one step are independent: about log2(row
+// length) rounds of loads instead of ten searches one after another)
 __device__ __forceinline__ void inc_gen_run(int r, const int *__restrict__ run_start, const ushort4 *__restrict__ sidx,
                                             const int *__restrict__ row_ptr, const int *__restrict__ col,
                                             uint32_t *__restrict__ key, uint32_t *__restrict__ val,
@@ -1173,12 +1177,45 @@ __device__ __forceinline__ void inc_gen_run(int r, const int *__restrict__ run_s
 {
     const ushort4 q = sidx[run_start[r]];
     const int t4[4] = {q.x, q.y, q.z, q.w};
+    int r0[4], r1[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        r0[s] = row_ptr[t4[s]];
+        r1[s] = row_ptr[t4[s] + 1];
+    }
+    // search e = (s, t): the largest position of row t4[s] whose column is <= t4[t]
+    int base[10], len[10], tgt[10];
+    {
+        int e = 0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int t = s; t < 4; ++t) {
+                base[e] = r0[s];
+                len[e] = r1[s] - r0[s];
+                tgt[e] = t4[t];
+                ++e;
+            }
+    }
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int e = 0; e < 10; ++e) {
+            if (len[e] > 1) {
+                const int half = len[e] >> 1;
+                if (col[base[e] + half] <= tgt[e]) base[e] += half;
+                len[e] -= half;
+                more = true;
+            }
+        }
+        if (!more) break;
+    }
     int e = 0;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int t = s; t < 4; ++t) {
-            const int b = find_block(row_ptr, col, t4[s], t4[t]);
+            const int b = len[e] == 1 && col[base[e]] == tgt[e] ? base[e] : -1;
             if (b < 0) atomicCAS(status, ED_OK, ED_ERR_STATE);
             key[10L * r + e] = (uint32_t)(b < 0 ? 0 : b);
             val[10L * r + e] = ((uint32_t)r << 4) | ((uint32_t)s << 2) | (uint32_t)t;
