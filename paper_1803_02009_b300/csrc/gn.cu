@@ -39,9 +39,9 @@ struct PointArgs {
 // Per point at position k (node-tuple order in a Gauss-Newton step, model
 // order otherwise): Eq. (1) warp, visible-point gate, data residual
 // r = n(u).(v~ - Gamma) and its derivative factors r0 = [sqrt(w) R^T n(u); r],
-// r1 = [d r / d angles; 1] (zero on invalid rows); E_data, the count, the 6x6
-// pose block, the pose gradient, the non-finite count, E_corr and the valid
-// rows are added to acc.  Returns whether the row is valid.
+// r1 = [d r / d angles; 1] (zero on invalid rows); E_data, the count, the
+// pose gradient, the non-finite count, E_corr and the valid rows are added to
+// acc (ACC: the energy and gradient passes).  Returns whether the row is valid.
 template <bool ACC>
 __device__ __forceinline__ bool point_eval(const PointArgs &a, const ed_pose_f &P, int k, float (&acc)[32],
                                            float4 &r0, float4 &r1)
@@ -121,11 +121,9 @@ __device__ __forceinline__ bool point_eval(const PointArgs &a, const ed_pose_f &
             acc[1] += 1.0f;
         }
         acc[31] += 1.0f;
-        int ka = 2;
-#pragma unroll
-        for (int t = 0; t < 6; ++t)
-#pragma unroll
-            for (int s = t; s < 6; ++s) acc[ka++] += jp[t] * jp[s];
+        // (the energy and gradient passes use E_data, the counts and the pose
+        // gradient sums: the pose block entries 2..22 stay 0 here; a step forms
+        // them from its staged rows)
 #pragma unroll
         for (int t = 0; t < 6; ++t) acc[23 + t] += r * jp[t];
         if (!isfinite(r)) acc[29] += 1.0f;
@@ -183,7 +181,7 @@ __global__ void __launch_bounds__(ED_K1_THREADS, 4) k_points(PointArgs a)
     __shared__ float red[ED_K1_THREADS / 32][32];
     if (threadIdx.x == 0) ed_pose_eval(a.pose, P);
     __syncthreads();
-    // 0 E_data, 1 count, 2..22 pose block, 23..28 pose gradient, 29 non-finite, 30 E_corr, 31 valid rows
+    // 0 E_data, 1 count, 2..22 (pose block: 0 in these passes), 23..28 pose gradient, 29 non-finite, 30 E_corr, 31 valid rows
     float acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0.f;
