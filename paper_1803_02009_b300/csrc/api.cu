@@ -83,7 +83,8 @@ size_t carve(ed_context *c, char *base)
     c->run_of_start = k.take<int>(N);
     c->bcnt = k.take<int>(2 * (M + 1));
     c->bstart = k.take<int>(M + 1);
-    c->icnt = k.take<int>(2 * (nnzb + 1));
+    c->icnt = k.take<int>(2 * (nnzb + 1) + 2 * ED_ASM_BINS);
+    c->asm_bins = c->icnt + 2 * (nnzb + 1);
     c->crec0 = k.take<float4>(N);
     c->crec1 = k.take<float4>(N);
     c->cpos = k.take<float4>(N);

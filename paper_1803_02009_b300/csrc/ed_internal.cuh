@@ -18,6 +18,7 @@
 #define ED_PCG_PART 16         // doubles per PCG CTA partial (at most)
 #define ED_MAX_BATCH_LAUNCH 32 // problems in one batched PCG launch
 #define ED_MAX_PCG_GRID 1184   // 8 x 148
+#define ED_ASM_BINS 64         // incidence-count classes of the off-diagonal blocks (the last: 63 and more)
 #define ED_PINNED_INTS (ED_MAX_PCG_GRID + 1 + 16)
 
 // indices of the dmisc doubles: 0..7 energy terms of the current step
@@ -135,6 +136,7 @@ struct ed_context {
     int *bcnt;               // [2 (max_nodes + 1)] bucket counts and fill counters of the tuple grouping
     int *bstart;             // [max_nodes + 1] bucket starts
     int *icnt;               // [2 (max_nnzb + 1)] incidence counts and fill counters per block
+    int *asm_bins;           // [2 ED_ASM_BINS] off-diagonal blocks per incidence count, and fill counters (after icnt)
     // a step's valid rows, compacted in sorted order (k_compact)
     float4 *crec0, *crec1, *cpos, *csw;   // [N] records, position, tuple weights
     int *vrun_start;         // [N + 1] first compacted row of every run

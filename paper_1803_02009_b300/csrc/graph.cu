@@ -1247,7 +1247,7 @@ __device__ __forceinline__ void fin_pack_one(int u, int m, int kg, const int *__
                                              const int *__restrict__ brow, const int *__restrict__ col,
                                              const int *__restrict__ tpos, const int *__restrict__ row_ptr,
                                              const int *__restrict__ inc_start, const int *__restrict__ nbr,
-                                             int4 *__restrict__ info)
+                                             int4 *__restrict__ info, const int *s_base, int *bin_fill)
 {
     const int b = up_list[u];
     const int j = brow[b], l = col[b];
@@ -1262,23 +1262,58 @@ __device__ __forceinline__ void fin_pack_one(int u, int m, int kg, const int *__
             if (nbr[j * kg + s] == l) flags |= 1;
             if (nbr[l * kg + s] == j) flags |= 2;
         }
-        info[2 * u] = make_int4(b, j, l, tpos[b]);
-        info[2 * u + 1] = make_int4(i0, ni, flags, 0);
+        // off-diagonal records in decreasing order of their incidence counts
+        // (the assembly pairs neighbouring records on one warp and starts the
+        // long ones first; a block's sums do not depend on its slot)
+        const int bin = ni < ED_ASM_BINS - 1 ? ni : ED_ASM_BINS - 1;
+        const int d = m + s_base[bin] + atomicAdd(&bin_fill[bin], 1);
+        info[2 * d] = make_int4(b, j, l, tpos[b]);
+        info[2 * d + 1] = make_int4(i0, ni, flags, 0);
     }
+}
+
+// off-diagonal upper blocks per incidence-count class (for the order above)
+__global__ void k_inc_hist(const int *__restrict__ nnzb_dev, int cap, int m, const int *__restrict__ up_list,
+                           const int *__restrict__ flag_b, const int *__restrict__ inc_start, int *__restrict__ bins)
+{
+    ed_pdl_wait();
+    ed_pdl_trigger();
+    __shared__ int h[ED_ASM_BINS];
+    for (int q = threadIdx.x; q < ED_ASM_BINS; q += blockDim.x) h[q] = 0;
+    __syncthreads();
+    const int nnzb = *nnzb_dev;
+    const int nu = nnzb > cap ? m : m + flag_b[nnzb];
+    for (int u = m + blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
+        const int b = up_list[u];
+        const int ni = inc_start[b + 1] - inc_start[b];
+        atomicAdd(&h[ni < ED_ASM_BINS - 1 ? ni : ED_ASM_BINS - 1], 1);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < ED_ASM_BINS; q += blockDim.x)
+        if (h[q]) atomicAdd(&bins[q], h[q]);
 }
 
 __global__ void k_fin_pack(const int *__restrict__ nnzb_dev, int cap, int m, int kg, const int *__restrict__ up_list,
                            const int *__restrict__ flag_b, const int *__restrict__ brow, const int *__restrict__ col,
                            const int *__restrict__ tpos, const int *__restrict__ row_ptr,
-                           const int *__restrict__ inc_start, const int *__restrict__ nbr, int4 *__restrict__ info)
+                           const int *__restrict__ inc_start, const int *__restrict__ nbr, int4 *__restrict__ info,
+                           int *__restrict__ bins)
 {
     ed_pdl_wait();
     ed_pdl_trigger();
+    // first slot of every incidence-count class, largest class first
+    __shared__ int s_base[ED_ASM_BINS];
+    if (threadIdx.x < ED_ASM_BINS) {
+        int sum = 0;
+        for (int q = ED_ASM_BINS - 1; q > (int)threadIdx.x; --q) sum += bins[q];
+        s_base[threadIdx.x] = sum;
+    }
+    __syncthreads();
     const int nnzb = *nnzb_dev;
     if (nnzb > cap) return;
     const int nu = m + flag_b[nnzb];   // the upper-block count
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x)
-        fin_pack_one(u, m, kg, up_list, brow, col, tpos, row_ptr, inc_start, nbr, info);
+        fin_pack_one(u, m, kg, up_list, brow, col, tpos, row_ptr, inc_start, nbr, info, s_base, bins + ED_ASM_BINS);
 }
 
 
@@ -1366,7 +1401,7 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
     ed_status s;
     // ---- bounding box and grids ----
     ED_LAUNCH(k_build_init, 2 * ctx->num_sms, 256, st, ctx->misc, ctx->bcnt, 2 * (max_nodes + 1), ctx->icnt,
-              2 * (ctx->max_nnzb + 1)); ed_note_launch();
+              2 * (ctx->max_nnzb + 1) + 2 * ED_ASM_BINS); ed_note_launch();
     ED_LAUNCH(k_bbox, min(ed_div_up(N, 256), 4 * ctx->num_sms), 256, st, P4, N, ctx->misc); ed_note_launch();
     float kc = prm->search_cell;
     if (!(kc > 0.f)) kc = m_in > 0 ? (prm->sigma > 0.f ? prm->sigma : 1.0f) : 2.0f * prm->node_radius;
@@ -1575,8 +1610,10 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
                                               ifill, ctx->inc); ed_note_launch();
         ED_LAUNCH(k_ic_sort, std::min(ed_div_up(cap, 4), 32 * ctx->num_sms), 128, st, nnzb_dev, cap, ctx->ent_start,
                                                                                   ctx->inc); ed_note_launch();
+        ED_LAUNCH(k_inc_hist, g256, 256, st, nnzb_dev, cap, m, ctx->up_list, ctx->flag_b, ctx->ent_start, ctx->asm_bins);
+        ed_note_launch();
         ED_LAUNCH(k_fin_pack, g256, 256, st, nnzb_dev, cap, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow, ctx->col,
-                                         ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr, ctx->fin_info); ed_note_launch();
+                                         ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr, ctx->fin_info, ctx->asm_bins); ed_note_launch();
         ED_LAUNCH(k_counts_pattern, 1, 1, st, ctx->misc, graph->counts); ed_note_launch();
         ED_LAUNCH_CHECK();
         // what the host needs later (the counts, the row pointer of the PCG
