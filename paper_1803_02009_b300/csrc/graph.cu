@@ -1075,15 +1075,30 @@ __device__ __forceinline__ void ic_sort_block(const int *__restrict__ start, uin
 
 // (warps over the blocks, the block count read on the device)
 __global__ void __launch_bounds__(128) k_ic_sort(const int *__restrict__ nnzb_dev, int cap,
-                                                 const int *__restrict__ start, uint32_t *__restrict__ list)
+                                                 const int *__restrict__ start, uint32_t *__restrict__ list,
+                                                 const int *__restrict__ brow, const int *__restrict__ col,
+                                                 int *__restrict__ bins)
 {
     ed_pdl_wait();
     ed_pdl_trigger();
     const int nnzb = *nnzb_dev;
     if (nnzb > cap) return;
+    // and the off-diagonal upper blocks per incidence-count class (the order
+    // of the assembly records, k_fin_pack)
+    __shared__ int h[ED_ASM_BINS];
+    for (int q = threadIdx.x; q < ED_ASM_BINS; q += blockDim.x) h[q] = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nnzb; b += (gridDim.x * blockDim.x) >> 5)
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nnzb; b += (gridDim.x * blockDim.x) >> 5) {
         ic_sort_block(start, list, b, lane);
+        if (lane == 0 && brow[b] < col[b]) {
+            const int ni = start[b + 1] - start[b];
+            atomicAdd(&h[ni < ED_ASM_BINS - 1 ? ni : ED_ASM_BINS - 1], 1);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < ED_ASM_BINS; q += blockDim.x)
+        if (h[q]) atomicAdd(&bins[q], h[q]);
 }
 
 // low 32 bits of every point's key, value = point index (the first pass of a
@@ -1247,7 +1262,8 @@ __device__ __forceinline__ void fin_pack_one(int u, int m, int kg, const int *__
                                              const int *__restrict__ brow, const int *__restrict__ col,
                                              const int *__restrict__ tpos, const int *__restrict__ row_ptr,
                                              const int *__restrict__ inc_start, const int *__restrict__ nbr,
-                                             int4 *__restrict__ info, const int *s_base, int *bin_fill)
+                                             int4 *__restrict__ info, const int *s_base, int *bin_fill, int nu,
+                                             int *__restrict__ status)
 {
     const int b = up_list[u];
     const int j = brow[b], l = col[b];
@@ -1267,37 +1283,21 @@ __device__ __forceinline__ void fin_pack_one(int u, int m, int kg, const int *__
         // long ones first; a block's sums do not depend on its slot)
         const int bin = ni < ED_ASM_BINS - 1 ? ni : ED_ASM_BINS - 1;
         const int d = m + s_base[bin] + atomicAdd(&bin_fill[bin], 1);
+        if (d >= nu) {   // (the classes count the same strictly upper blocks: never)
+            atomicCAS(status, ED_OK, ED_ERR_STATE);
+            return;
+        }
         info[2 * d] = make_int4(b, j, l, tpos[b]);
         info[2 * d + 1] = make_int4(i0, ni, flags, 0);
     }
 }
 
-// off-diagonal upper blocks per incidence-count class (for the order above)
-__global__ void k_inc_hist(const int *__restrict__ nnzb_dev, int cap, int m, const int *__restrict__ up_list,
-                           const int *__restrict__ flag_b, const int *__restrict__ inc_start, int *__restrict__ bins)
-{
-    ed_pdl_wait();
-    ed_pdl_trigger();
-    __shared__ int h[ED_ASM_BINS];
-    for (int q = threadIdx.x; q < ED_ASM_BINS; q += blockDim.x) h[q] = 0;
-    __syncthreads();
-    const int nnzb = *nnzb_dev;
-    const int nu = nnzb > cap ? m : m + flag_b[nnzb];
-    for (int u = m + blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
-        const int b = up_list[u];
-        const int ni = inc_start[b + 1] - inc_start[b];
-        atomicAdd(&h[ni < ED_ASM_BINS - 1 ? ni : ED_ASM_BINS - 1], 1);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < ED_ASM_BINS; q += blockDim.x)
-        if (h[q]) atomicAdd(&bins[q], h[q]);
-}
 
 __global__ void k_fin_pack(const int *__restrict__ nnzb_dev, int cap, int m, int kg, const int *__restrict__ up_list,
                            const int *__restrict__ flag_b, const int *__restrict__ brow, const int *__restrict__ col,
                            const int *__restrict__ tpos, const int *__restrict__ row_ptr,
                            const int *__restrict__ inc_start, const int *__restrict__ nbr, int4 *__restrict__ info,
-                           int *__restrict__ bins)
+                           int *__restrict__ bins, int *__restrict__ status)
 {
     ed_pdl_wait();
     ed_pdl_trigger();
@@ -1313,7 +1313,8 @@ __global__ void k_fin_pack(const int *__restrict__ nnzb_dev, int cap, int m, int
     if (nnzb > cap) return;
     const int nu = m + flag_b[nnzb];   // the upper-block count
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x)
-        fin_pack_one(u, m, kg, up_list, brow, col, tpos, row_ptr, inc_start, nbr, info, s_base, bins + ED_ASM_BINS);
+        fin_pack_one(u, m, kg, up_list, brow, col, tpos, row_ptr, inc_start, nbr, info, s_base, bins + ED_ASM_BINS, nu,
+                     status);
 }
 
 
@@ -1609,11 +1610,10 @@ extern "C" ed_status ed_build_graph(ed_context *ctx, const float *pos, const flo
         ED_LAUNCH(k_ic_place, 4 * g256, 256, st, nruns_dev, nnzb_dev, cap, ctx->ent_key, ctx->ent_val, ctx->ent_start,
                                               ifill, ctx->inc); ed_note_launch();
         ED_LAUNCH(k_ic_sort, std::min(ed_div_up(cap, 4), 32 * ctx->num_sms), 128, st, nnzb_dev, cap, ctx->ent_start,
-                                                                                  ctx->inc); ed_note_launch();
-        ED_LAUNCH(k_inc_hist, g256, 256, st, nnzb_dev, cap, m, ctx->up_list, ctx->flag_b, ctx->ent_start, ctx->asm_bins);
-        ed_note_launch();
+                  ctx->inc, ctx->brow, ctx->col, ctx->asm_bins); ed_note_launch();
         ED_LAUNCH(k_fin_pack, g256, 256, st, nnzb_dev, cap, m, prm->k_graph, ctx->up_list, ctx->flag_b, ctx->brow, ctx->col,
-                                         ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr, ctx->fin_info, ctx->asm_bins); ed_note_launch();
+                                         ctx->tpos, ctx->row_ptr, ctx->ent_start, graph->nbr, ctx->fin_info, ctx->asm_bins,
+                                         ctx->misc + MI_STATUS); ed_note_launch();
         ED_LAUNCH(k_counts_pattern, 1, 1, st, ctx->misc, graph->counts); ed_note_launch();
         ED_LAUNCH_CHECK();
         // what the host needs later (the counts, the row pointer of the PCG
