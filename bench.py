@@ -353,11 +353,13 @@ def run_ours(args, rank, world, local):
     g = ctx.graph
     st_last = E.read_stats(stats)
 
-    # timed region
+    # timed region.  The roofline's PCG duration comes from events around the
+    # last PCG solve of every timed step (one pair per step: an event between
+    # two kernels ends their programmatic overlap, so the other launches of the
+    # step carry none); the phase breakdown comes from a separate pass below.
     K = args.steps
-    n_events = K * cfg.n_gn
-    tm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_events)]
-    ctx.set_timing(E.ED_KERNEL_PCG, tm_ev)
+    tm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    ctx.set_timing(E.ED_KERNEL_PCG, tm_ev, every=cfg.n_gn)
     clocks = ClockSampler(local)
     clocks.start()
     l0 = E.launch_count()
@@ -370,7 +372,7 @@ def run_ours(args, rank, world, local):
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record()
-            step(record_gn=True)
+            step()
             ev1.record()
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
@@ -381,13 +383,6 @@ def run_ours(args, rank, world, local):
     n_rec = ctx.timing_count()
     ctx.set_timing(E.ED_KERNEL_PCG, [])
     pcg_ms = [tm_ev[2 * i].elapsed_time(tm_ev[2 * i + 1]) for i in range(n_rec)]
-    gn_ms = [a.elapsed_time(b) for a, b in gn_ev[-K:]]
-    phases_us = {
-        "normals_and_graph_build": statistics.median(a.elapsed_time(b) * 1e3 for a, b, _, _ in ph_ev[-K:]),
-        "gauss_newton": statistics.median(b.elapsed_time(c) * 1e3 for _, b, c, _ in ph_ev[-K:]),
-        "warp_and_fuse": statistics.median(c.elapsed_time(d) * 1e3 for _, _, c, d in ph_ev[-K:]),
-        "note": "median over the timed steps of CUDA events between the step's phases (the build's "
-                "parameter reset included in the first)"}
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
     value = whole_job_rate(world, K, cfg.n_gn, total_s)
 
@@ -457,6 +452,21 @@ def run_ours(args, rank, world, local):
     e2e_s = max_over_ranks((ev0.elapsed_time(ev1) - flush_ms) / 1e3, dist, dev)
     e2e_value = whole_job_rate(world, K, cfg.n_gn, e2e_s)
 
+    # the step's phases: K more steps, the same as the timed ones, with events
+    # between the phases (outside the timed region: the events end the
+    # programmatic overlap of the kernels on either side)
+    for k in range(K):
+        flush.fill_(k & 0xff)
+        step(record_gn=True)
+    torch.cuda.synchronize()
+    gn_ms = [a.elapsed_time(b) for a, b in gn_ev[-K:]]
+    phases_us = {
+        "normals_and_graph_build": statistics.median(a.elapsed_time(b) * 1e3 for a, b, _, _ in ph_ev[-K:]),
+        "gauss_newton": statistics.median(b.elapsed_time(c) * 1e3 for _, b, c, _ in ph_ev[-K:]),
+        "warp_and_fuse": statistics.median(c.elapsed_time(d) * 1e3 for _, _, c, d in ph_ev[-K:]),
+        "note": "median over K steps run after the timed region with CUDA events between the step's phases "
+                "(the build's parameter reset included in the first)"}
+
     # per-kernel device time of a Gauss-Newton iteration (events recorded by
     # the library around each launch of one kernel; two extra steps per
     # kernel, outside the timed region)
@@ -476,7 +486,8 @@ def run_ours(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     n_upper = (g.nnzb + g.m) // 2          # symmetric pattern, every diagonal block present
-    byt = pcg_bytes_per_launch(g.m, n_upper, cfg.n_pcg)
+    n_pcg_last = int(st_last[-1]["pcg_iters"])   # (the timed launches: the last solve of a step)
+    byt = pcg_bytes_per_launch(g.m, n_upper, n_pcg_last)
     n_valid_last = int(st_last[-1]["n_valid"])
     gn_byt = gn_bytes_per_iteration(s.N, n_valid_last, g.m, n_upper, cfg.n_pcg)
     gn_rate = whole_job_rate(world, K, cfg.n_gn, max_over_ranks(sum(gn_ms) / 1e3, dist, dev)) if gn_ms else None
@@ -517,7 +528,10 @@ def run_ours(args, rank, world, local):
         "roofline": {"kernel": "k_pcg (persistent block-Jacobi PCG)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": byt,
-                     "avg_launch_us": avg_pcg_s * 1e6, "launches_timed": len(pcg_ms)},
+                     "avg_launch_us": avg_pcg_s * 1e6, "launches_timed": len(pcg_ms),
+                     "pcg_iters_per_launch": n_pcg_last,
+                     "note": "CUDA events around the last PCG solve of every timed step (one launch per step; "
+                             "the step's other launches carry no events)"},
         "gn_kernels_us": dict(kern_us, note="median device time per launch (library events on the launching "
                                              "stream, 2 extra steps outside the timed region)"),
         "gn_iteration_roofline": {"bound": "hbm", "algorithmic_bytes": gn_byt,
@@ -945,9 +959,10 @@ def run_sequence(args, rank, world, local):
         depth.copy_(h_depth[k])
         color.copy_(h_color[k])
         infos.append(T.process(depth, color, k + 1, truth_depth=truth[k]))
-    n_events = K * cfg.n_gn
-    tm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_events)]
-    ctx.set_timing(E.ED_KERNEL_PCG, tm_ev)
+    # (events around the last PCG solve of every frame only: an event between
+    # two kernels ends their programmatic overlap)
+    tm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    ctx.set_timing(E.ED_KERNEL_PCG, tm_ev, every=cfg.n_gn)
     clocks = ClockSampler(local)
     clocks.start()
     l0 = E.launch_count()
@@ -1011,7 +1026,9 @@ def run_sequence(args, rank, world, local):
         "roofline": {"kernel": "k_pcg (persistent block-Jacobi PCG)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "algorithmic_bytes_per_launch": byt, "avg_launch_us": avg_pcg_s * 1e6,
-                     "launches_timed": len(pcg_ms)},
+                     "launches_timed": len(pcg_ms),
+                     "note": "CUDA events around the last PCG solve of every timed frame (bytes: the last "
+                             "frame's graph)"},
     }, S, radius
 
 

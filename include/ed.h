@@ -319,6 +319,19 @@ ed_status ed_set_barrier_test(ed_context *ctx, int extra_arrivals);
 enum { ED_KERNEL_PCG = 0, ED_KERNEL_POINTS = 1, ED_KERNEL_ASSEMBLE = 2, ED_KERNEL_FINALIZE = 3, ED_KERNEL_GRAD = 4 };
 ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded);
 
+/*
+ * The same hook sampled: of the selected kernel's launches i = 0, 1, ... from
+ * now on, only those with i % every == every - 1 are recorded (pair k around
+ * launch k * every + every - 1).  An event recorded between two kernels ends
+ * their programmatic overlap, so a sampled hook keeps the other launches of a
+ * timed loop undisturbed (every = the Gauss-Newton iterations of a frame
+ * records the last PCG solve of every frame).  every >= 1 (ED_ERR_ARG
+ * otherwise); ed_set_timing is every = 1.  Instrumentation; the paper has no
+ * counterpart.
+ */
+ed_status ed_set_timing_every(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int every,
+                              int *recorded);
+
 /* Kernel launches the library has issued in this process so far (host out).
  * Instrumentation; the paper has no counterpart. */
 ed_status ed_launch_count(unsigned long long *count);

@@ -115,6 +115,7 @@ _SIGS = {
     "ed_energy": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, _vp, _vp],
     "ed_energy_grad": [_vp, C.POINTER(Frame), C.POINTER(SolverParamsC), _vp, _vp, C.c_float, _vp, _vp, _vp],
     "ed_set_timing": [_vp, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)],
+    "ed_set_timing_every": [_vp, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int)],
     "ed_launch_count": [C.POINTER(C.c_ulonglong)],
     "ed_set_wait_limit": [_vp, C.c_ulonglong],
     "ed_set_barrier_test": [_vp, C.c_int],
@@ -474,8 +475,9 @@ class Context:
                                         _ptr(out["counts"]), _ptr(reg), _stream(stream)))
         return out
 
-    def set_timing(self, kernel_id, events):
-        """Record torch.cuda.Event pairs around launches of one library kernel."""
+    def set_timing(self, kernel_id, events, every=1):
+        """Record torch.cuda.Event pairs around launches of one library kernel
+        (every `every`-th launch: launches every - 1, 2 every - 1, ...)."""
         self._tm_events = events
         n = len(events) // 2
         for e in events:          # torch creates the CUDA event at its first record
@@ -484,7 +486,8 @@ class Context:
             torch.cuda.synchronize()
         self._tm_arr = (C.c_void_p * max(1, len(events)))(*[e.cuda_event for e in events]) if n else None
         self._tm_rec = C.c_int(0)
-        _check("ed_set_timing", lib().ed_set_timing(self.h, int(kernel_id), self._tm_arr, n, C.byref(self._tm_rec)))
+        _check("ed_set_timing_every", lib().ed_set_timing_every(self.h, int(kernel_id), self._tm_arr, n, int(every),
+                                                                C.byref(self._tm_rec)))
 
     def timing_count(self):
         return self._tm_rec.value

@@ -293,16 +293,25 @@ extern "C" ed_status ed_launch_count(unsigned long long *count)
     return ED_OK;
 }
 
-extern "C" ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded)
+extern "C" ed_status ed_set_timing_every(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int every,
+                                        int *recorded)
 {
-    if (!ctx || n_pairs < 0 || (n_pairs > 0 && !events) || kernel_id < 0 || kernel_id > ED_KERNEL_GRAD) return ED_ERR_ARG;
+    if (!ctx || n_pairs < 0 || (n_pairs > 0 && !events) || kernel_id < 0 || kernel_id > ED_KERNEL_GRAD || every < 1)
+        return ED_ERR_ARG;
     ctx->tm_kernel = kernel_id;
     ctx->tm_events = n_pairs > 0 ? events : nullptr;
     ctx->tm_pairs = n_pairs;
     ctx->tm_count = 0;
+    ctx->tm_every = every;
+    ctx->tm_seen = 0;
     ctx->tm_recorded = recorded;
     if (recorded) *recorded = 0;
     return ED_OK;
+}
+
+extern "C" ed_status ed_set_timing(ed_context *ctx, int kernel_id, cudaEvent_t *events, int n_pairs, int *recorded)
+{
+    return ed_set_timing_every(ctx, kernel_id, events, n_pairs, 1, recorded);
 }
 
 extern "C" ed_status ed_graph_info(ed_context *ctx, int *m, int *nnzb, int *n_entries, int *n_runs)

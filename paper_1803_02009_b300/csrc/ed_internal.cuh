@@ -229,12 +229,14 @@ struct ed_context {
     unsigned long long wait_ns;
     int bar_extra;
 
-    // measurement hook (ed_set_timing)
+    // measurement hook (ed_set_timing, ed_set_timing_every)
     int tm_kernel;
     cudaEvent_t *tm_events;
     int tm_pairs;
     int tm_count;
     int *tm_recorded;
+    int tm_every;              // record launch i of the kernel when i % tm_every == tm_every - 1
+    long long tm_seen;         // launches of the kernel since the hook was set
 };
 
 // events around one launch of a kernel selected by ed_set_timing
@@ -248,19 +250,27 @@ static inline void ed_tm_record(ed_context *c, cudaEvent_t e, cudaStream_t st)
         c->tm_events = nullptr;
     }
 }
+// (an event between two kernels ends their programmatic overlap, so a
+// sampled hook -- every tm_every-th launch -- leaves the others undisturbed)
+static inline bool ed_tm_selected(const ed_context *c, int kid)
+{
+    return c->tm_events && c->tm_kernel == kid && c->tm_count < c->tm_pairs &&
+           c->tm_seen % c->tm_every == c->tm_every - 1;
+}
 static inline void ed_tm_begin(ed_context *c, int kid, cudaStream_t st)
 {
-    if (c->tm_events && c->tm_kernel == kid && c->tm_count < c->tm_pairs)
-        ed_tm_record(c, c->tm_events[2 * c->tm_count], st);
+    if (ed_tm_selected(c, kid)) ed_tm_record(c, c->tm_events[2 * c->tm_count], st);
 }
 static inline void ed_tm_end(ed_context *c, int kid, cudaStream_t st)
 {
-    if (c->tm_events && c->tm_kernel == kid && c->tm_count < c->tm_pairs) {
+    if (!c->tm_events || c->tm_kernel != kid) return;
+    if (ed_tm_selected(c, kid)) {
         ed_tm_record(c, c->tm_events[2 * c->tm_count + 1], st);
         if (!c->tm_events) return;
         c->tm_count++;
         if (c->tm_recorded) *c->tm_recorded = c->tm_count;
     }
+    c->tm_seen++;
 }
 
 // ---------------------------------------------------------------------------

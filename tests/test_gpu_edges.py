@@ -203,3 +203,37 @@ def test_zero_pcg_iterations_keep_the_parameters_and_report_b(precision):
     assert r1["status"] == 0 and r1["pcg_iters"] == 10
     assert r1["pcg_res0"] == pytest.approx(gnorm, rel=1e-5)
     assert r1["pcg_res"] < r1["pcg_res0"]
+
+
+def test_sampled_timing_hook_records_every_nth_launch():
+    """ed_set_timing_every: of 7 PCG solves with every = 3 only launches 2 and
+    5 are recorded (two pairs, each a positive duration); every = 0 is an
+    argument error; the solves' results do not depend on the hook."""
+    torch, E = _torch(), _E()
+    s = C.scene(SMALL)
+    G = C.gpu_setup(s)
+    ctx, g = G["ctx"], G["graph"]
+    prm = C.solver(s)
+
+    def run(events, every):
+        x = torch.empty((g.m, 12), dtype=torch.float32, device="cuda")
+        pose = torch.empty(6, dtype=torch.float64, device="cuda")
+        ctx.reset_params(x, pose, prior=s.pose_prior)
+        if events is not None:
+            ctx.set_timing(E.ED_KERNEL_PCG, events, every=every)
+        for _ in range(7):
+            ctx.gn_step(G["frame"], prm, x, pose)
+        torch.cuda.synchronize()
+        n = ctx.timing_count() if events is not None else 0
+        ctx.set_timing(E.ED_KERNEL_PCG, [])
+        return x.cpu(), n
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    x_hook, n = run(ev, 3)
+    assert n == 2
+    assert all(ev[2 * i].elapsed_time(ev[2 * i + 1]) > 0 for i in range(n))
+    x_plain, _ = run(None, 1)
+    assert torch.equal(x_hook, x_plain)
+    with pytest.raises(E.EDError) as ei:
+        ctx.set_timing(E.ED_KERNEL_PCG, ev, every=0)
+    assert ei.value.status == 1
