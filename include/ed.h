@@ -456,11 +456,11 @@ ed_status ed_energy_grad(ed_context *ctx, const ed_frame *frame, const ed_solver
  * process exits; no allocation routine is called.
  * Limits: n_points <= 2,097,152 and m <= 32,768; larger sizes return
  * ED_ERR_CAPACITY (with a message on stderr) before any launch.
- * The first call on a device looks up the device address of that array
- * (cudaGetSymbolAddress, with the device current) and keeps it for the rest
- * of the process; make that first call before any stream capture.  A device
- * reset (cudaDeviceReset) invalidates the kept address: do not call this
- * entry point again in a process after resetting the device.  Every call writes every scratch slot it reads,
+ * Every call made outside a stream capture looks up the device address of
+ * that array (cudaGetSymbolAddress, with the device current); a call made
+ * during a capture takes the address that the last call outside capture
+ * found, so make one plain call on the device before capturing (and again
+ * after a device reset).  Every call writes every scratch slot it reads,
  * so stale contents never matter, but all calls share the one array: calls
  * that overlap on the GPU (different streams, or different host threads on
  * one device) race and must be serialised by the caller.

@@ -151,17 +151,25 @@ __global__ void __launch_bounds__(32) k_na_final(const double *__restrict__ pp, 
     out[5] = ep;
 }
 
-// device address of the scratch array, looked up once per device
+// device address of the scratch array: looked up afresh by every call made
+// outside a stream capture (so a reloaded module after a device reset is
+// found again); a call made during a capture, where the lookup may not run,
+// takes the address the last call outside capture found
 static std::mutex g_na_mutex;
 static double *g_na_ptr[256];
 static bool g_na_ready[256];
 
-static ed_status na_scratch(double **out)
+static ed_status na_scratch(cudaStream_t st, double **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ED_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();   // (e.g. the legacy stream queried while another stream captures)
+        cs = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ready[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_na_ready[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess || !p) {
@@ -195,7 +203,7 @@ extern "C" ed_status ed_energy_noalloc(const float *pos, const float *nrm, const
         return ED_ERR_CAPACITY;
     }
     double *scratch = nullptr;
-    ed_status s = na_scratch(&scratch);
+    ed_status s = na_scratch(st, &scratch);
     if (s != ED_OK) return s;
     const int np = ed_div_up(n_points, NA_THREADS), nn = ed_div_up(m, NA_THREADS);
     double *pp = scratch, *pn = scratch + 2 * NA_MAX_POINT_CTAS;
